@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Throughput benchmark: Mpix/s cleaned at niter=4 on synthetic CCD frames.
+
+Default workload: 64 uneven frames (16 each of 800^2, 1024^2, 2048x4096,
+4096^2; per-frame gain and read noise), one crb_clean_batch call per step.
+A step is the whole hot path (niter iterations of detection + replacement)
+over that batch. Inputs (1.72 GB) exceed the 126 MB L2, so no flush is needed.
+
+Printed (one JSON line from rank 0):
+  value       device-timed batched throughput, inputs resident in HBM;
+  e2e         the same through the public API with host buffers (pinned H2D
+              of the inputs, D2H of cleaned frames and masks inside the timed
+              region);
+  per_frame   the plain path: one crb_clean call per frame, no batching;
+  roofline    the detection kernel (stages a-d, the dominant kernel) against
+              the measured FP32 min/max rate of the device;
+  cpu_baseline the CPU oracle on a bounded sample of the same workload.
+With --impl reference the CPU oracle itself is the timed arm (this method has
+no runnable reference implementation).
+Multi-GPU (torchrun): independent replicas, one per GPU, weak scaling.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# Algorithmic work of the detection kernel per pixel and iteration: two dense
+# 25-input median selections (about 100 compare-exchanges, i.e. 200 min/max
+# each) plus ~25 arithmetic operations for L+, N, S and S'.
+ALG_OPS_PER_PIX_ITER = 425.0
+# Algorithmic HBM bytes per pixel and iteration: read J (4 B), write I_k (4 B),
+# flag bits in and out (0.25 B).
+ALG_BYTES_PER_PIX_ITER = 8.25
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="crb", choices=["crb", "reference"])
+    ap.add_argument("--workload", default="batch64",
+                    choices=["batch64", "single4096", "single800", "mosaic16384"])
+    ap.add_argument("--tile-shape", type=int, default=0)
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e / per-frame / cpu legs")
+    return ap.parse_args()
+
+
+def recipes_for(name):
+    from synth import workloads as wl
+    if name == "batch64":
+        return wl.batch_64(), "64 uneven frames: 16x800x800, 16x1024x1024, 16x2048x4096, 16x4096x4096"
+    if name == "single4096":
+        return [wl.single_4096()], "one 4096x4096 frame, 5000 stars, 40000 cosmic rays"
+    if name == "single800":
+        return [wl.single_800()], "one 800x800 frame, 200 stars, 1500 cosmic rays"
+    return [wl.mosaic_16384()], "one 16384x16384 mosaic, 2e5 stars, 6e5 cosmic rays"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_baseline(recipes, budget_s=12.0):
+    """The oracle (FP64, all host cores) on a bounded sample: 800x800 crops of the workload's frames."""
+    import oracle
+    from synth import workloads as wl
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    P = oracle.Params()
+    pix, t_tot, n = 0, 0.0, 0
+    i = 0
+    while t_tot < budget_s and i < len(recipes):
+        r = dict(recipes[i])
+        r.update(w=min(r["w"], 800), h=min(r["h"], 800))
+        scale = r["w"] * r["h"] / (recipes[i]["w"] * recipes[i]["h"])
+        r.update(nstars=max(1, int(r["nstars"] * scale)), ncr=max(1, int(r["ncr"] * scale)))
+        img = wl.make(r)
+        P = oracle.Params(gain=r["gain"], readnoise=r["readnoise"])
+        t0 = time.perf_counter()
+        oracle.clean(img, P, 4)
+        t_tot += time.perf_counter() - t0
+        pix += img.size
+        n += 1
+        i += 1
+    return {"value": pix / t_tot / 1e6, "unit": "Mpix/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{n} frames of up to 800x800 from the workload's recipes, niter=4, FP64, "
+                      f"{oracle.max_threads()} threads, {t_tot:.1f} s"}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle, timed on this host's cores, on 800x800 frames of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from synth import workloads as wl
+    recipes, desc = recipes_for(args.workload)
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    r0 = dict(recipes[0])
+    r0.update(w=800, h=800, nstars=200, ncr=1500)
+    img = wl.make(r0)
+    P = oracle.Params(gain=r0["gain"], readnoise=r0["readnoise"])
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle.clean(img, P, 4)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.clean(img, P, 4)
+    dt = time.perf_counter() - t0
+    value = args.steps * img.size / dt / 1e6
+    sample = (f"each step: one 800x800 frame of the workload's generative model, niter=4, FP64 oracle, "
+              f"{oracle.max_threads()} threads")
+    line = {"impl": "reference", "metric": "Mpix/s cleaned at niter=4", "value": value, "unit": "Mpix/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "niter": 4},
+            "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_1008_2192_gb300 import Cleaner
+    from paper_1008_2192_gb300.api import alu_peak
+    from synth import workloads as wl
+
+    recipes, desc = recipes_for(args.workload)
+    frames = [wl.make(r) for r in recipes]
+    gains = [r["gain"] for r in recipes]
+    rns = [r["readnoise"] for r in recipes]
+    npix = sum(f.size for f in frames)
+    niter = wl.CLEAN_PARAMS["niter"]
+
+    h_imgs = [torch.from_numpy(f).pin_memory() for f in frames]
+    d_imgs = [t.cuda() for t in h_imgs]
+    d_outs = [torch.empty_like(t) for t in d_imgs]
+    d_masks = [torch.empty(t.shape, dtype=torch.uint8, device="cuda") for t in d_imgs]
+    stream = torch.cuda.current_stream()
+
+    ops2, ops3 = alu_peak()
+    cl = Cleaner(gain=7.0, readnoise=5.0, niter=niter, tile_shape=args.tile_shape, profile=True)
+
+    def step():
+        cl.clean_batch_into(d_imgs, d_outs, d_masks, gains, rns)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    cl.sync()
+    cl.profile_read(reset=True)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    det_ms, det_n, rep_ms, rep_n = cl.profile_read(reset=True)
+    cl.sync()
+
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * npix * args.steps / (ms_max * 1e-3) / 1e6
+
+    extras = {}
+    if not args.no_extras:
+        # end to end through the public API with host buffers
+        h_outs = [torch.empty(f.shape, dtype=torch.float32).pin_memory() for f in frames]
+        h_masks = [torch.empty(f.shape, dtype=torch.uint8).pin_memory() for f in frames]
+
+        def e2e_step():
+            for hs, ds in zip(h_imgs, d_imgs):
+                ds.copy_(hs, non_blocking=True)
+            cl.clean_batch_into(d_imgs, d_outs, d_masks, gains, rns)
+            for ho, do, hm, dm in zip(h_outs, d_outs, h_masks, d_masks):
+                ho.copy_(do, non_blocking=True)
+                hm.copy_(dm, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        k2 = max(2, min(args.steps, 5))
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k2):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = a.elapsed_time(b) / k2
+        extras["e2e"] = {"value": world * npix / (e2e_ms * 1e-3) / 1e6, "unit": "Mpix/s",
+                         "h2d_bytes_per_step": int(npix * 4), "d2h_bytes_per_step": int(npix * 5)}
+        # the plain per-frame path: one crb_clean per frame
+        cl_plain = Cleaner(gain=7.0, readnoise=5.0, niter=niter, tile_shape=args.tile_shape)
+        plain = [Cleaner(gain=g, readnoise=r, niter=niter, tile_shape=args.tile_shape) for g, r in
+                 zip(gains, rns)] if len(frames) > 1 else [cl_plain]
+
+        def plain_step():
+            for c, di, do, dm in zip(plain, d_imgs, d_outs, d_masks):
+                c.clean_into(di, do, dm)
+
+        plain_step()
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(k2):
+            plain_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        pf_ms = a.elapsed_time(b) / k2
+        extras["per_frame"] = {"value": world * npix / (pf_ms * 1e-3) / 1e6, "unit": "Mpix/s",
+                               "ms_per_step": pf_ms}
+
+    peaks = measured_peaks()
+    det_avg_ms = det_ms / max(det_n, 1)
+    achieved = ALG_OPS_PER_PIX_ITER * npix / (det_avg_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "detect (stages a-d)", "achieved": achieved, "peak": ops2 / 1e12,
+                "unit": "Tops/s", "frac": achieved / (ops2 / 1e12), "traffic": None,
+                "peak_source": "measured: crb_alu_peak FP32 min/max issue rate (2-input form)",
+                "peak_min3max3_tops": ops3 / 1e12,
+                "alg_ops_per_pixel_iteration": ALG_OPS_PER_PIX_ITER,
+                "detect_ms_avg": det_avg_ms, "replace_ms_avg": rep_ms / max(rep_n, 1),
+                "detect_share": det_ms / max(det_ms + rep_ms, 1e-9),
+                "hbm_frac_alg": (ALG_BYTES_PER_PIX_ITER * npix / (det_avg_ms + rep_ms / max(rep_n, 1)) / 1e6)
+                / peaks.get("hbm_gbs", 6782.4)}
+
+    if rank == 0:
+        line = {"metric": "Mpix/s cleaned at niter=4 (batched, 1 GB300)", "value": value, "unit": "Mpix/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": desc, "frames": len(frames), "mpix_per_step": npix / 1e6, "niter": niter,
+                           "params": "sigclip 4.5, sigfrac 0.5, objlim 1.0", "l2": "inputs 1.7 GB > L2, no flush"
+                           if args.workload == "batch64" else "see workload",
+                           "parallelism": f"replicas x{world}", "tile_shape": args.tile_shape},
+                "gpu_launches": args.steps * 2 * niter, "clocks": clk, "roofline": roofline}
+        line.update(extras)
+        if not args.no_extras:
+            line["cpu_baseline"] = cpu_baseline(recipes)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

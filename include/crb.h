@@ -1,0 +1,147 @@
+/*
+ * crb.h -- C ABI of the GB300 (sm_103a) L.A.Cosmic cosmic-ray cleaner.
+ *
+ * The operation is the L.A.Cosmic work function that CRBLASTER runs on each
+ * sub-image (Mighell, PASP 2010, Sec. 5; the algorithm is van Dokkum 2001),
+ * one iteration repeated niter times ("typically 4 iterations", Sec. 5):
+ *   (a) L+  : 2x block replication, 3x3 Laplacian [[0,-1,0],[-1,4,-1],[0,-1,0]],
+ *             negatives set to 0, 2x2 average;
+ *   (b) N   = sqrt(gain*med5(I) + readnoise^2)/gain,  S = L+/(2N),
+ *       S'  = S - med5(S);
+ *   (c) F   = med3(I) - med7(med3(I));
+ *   (d) candidates where S' > sigclip and S'/max(F/N, 0.01) > objlim, grown over
+ *       3x3 neighbours with S' > sigclip, then over 3x3 neighbours with
+ *       S' > sigfrac*sigclip;
+ *   (e) flagged pixels replaced by the lower median of the unflagged pixels of
+ *       their 5x5 window (the 5x5 median of the frame when none is unflagged).
+ * Flags accumulate over iterations. Every filter clamps its coordinates into
+ * the frame (replicate edge); the paper leaves the outer pixels undefined
+ * (Sec. 6.1). The arithmetic is IEEE float32 with no contraction.
+ *
+ * Conventions for every call:
+ *   - Images are float32 DN, row-major, contiguous (row pitch = w), DEVICE
+ *     pointers. Masks are uint8 (0/1), same layout. The caller owns all buffers.
+ *   - Sizes: 1 <= w, h; w*h < 2^31. Input must be finite (a NaN gives undefined
+ *     output, never a fault).
+ *   - Calls are asynchronous on `stream`: they validate, enqueue and return.
+ *     Validation errors are returned synchronously. Device-side errors are
+ *     latched in the context and reported by crb_sync_status().
+ *   - A context is not thread-safe: use one per host thread (or lock).
+ *   - Return value: CRB_OK or one of the error codes below.
+ */
+#ifndef CRB_H_
+#define CRB_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum crb_status {
+  CRB_OK = 0,
+  CRB_EINVAL = 1,   /* invalid argument (sizes, null pointers, parameters)        */
+  CRB_ENOMEM = 2,   /* device memory could not be allocated                        */
+  CRB_ECUDA = 3,    /* a CUDA runtime call failed (message in crb_last_error)      */
+  CRB_ETIMEOUT = 4, /* a bounded device-side wait gave up                          */
+  CRB_EBUSY = 5,    /* serving: admission refused (over budget or queue full)      */
+  CRB_EALIAS = 6,   /* an output overlaps an input                                 */
+  CRB_EDEVICE = 7   /* a device-side check failed (recorded, no access was made)   */
+};
+
+typedef struct crb_ctx crb_ctx;
+
+/* Options of crb_create_ex. Zero-initialise, then set what differs. */
+typedef struct {
+  /* objlim statistic: 0 = S'/max(F/N, 0.01) (script form, default);
+   *                   1 = 2S/max(F/N, 0.01), i.e. L+/F with F floored at 0.01 N (article form). */
+  int objlim_form;
+  /* 1: stop iterating once an iteration adds no flag and leaves no flagged pixel
+   * without an unflagged neighbour; the result is then a fixed point, so the
+   * output is identical to running all niter iterations. Default 0.            */
+  int early_exit;
+  /* Tile shape index (crb_tile_shape); -1 = autotune per frame shape (default 0 = fixed). */
+  int tile_shape;
+  /* 1: capture the niter loop of crb_clean in a CUDA graph per frame shape and replay it. */
+  int use_graphs;
+  /* 1: bracket every kernel launch with CUDA events on the launching stream;
+   * read the accumulated device times with crb_profile_read. Default 0.       */
+  int profile;
+} crb_options;
+
+/* Creates a context with the cleaning parameters (Sec. 5 lists gain, readn,
+ * sigfrac, objlim; sigclip and niter as in lacos_im.cl). Returns NULL when
+ * gain <= 0, readnoise < 0, sigclip <= 0, sigfrac <= 0, objlim <= 0 or
+ * niter < 0 (see crb_last_error). niter == 0 copies the input and clears the
+ * mask. The context owns its device workspace, graphs and tuning cache. */
+crb_ctx* crb_create(float gain, float readnoise, float sigclip, float sigfrac, float objlim, int niter);
+crb_ctx* crb_create_ex(float gain, float readnoise, float sigclip, float sigfrac, float objlim, int niter,
+                       const crb_options* opts);
+void crb_destroy(crb_ctx* ctx);
+
+/* Cleans one frame: img (device, w*h floats) -> out_clean (device, w*h floats,
+ * must not overlap img: CRB_EALIAS) and out_mask (device, w*h bytes, 0/1, the
+ * cumulative flags of all iterations). Enqueued on `stream`. The context's
+ * workspace grows on demand (one image plus a bit mask). */
+int crb_clean(crb_ctx* ctx, const float* img, int w, int h, float* out_clean, uint8_t* out_mask,
+              cudaStream_t stream);
+
+/* Cleans n frames of different sizes in one launch per stage and iteration
+ * (a persistent tile loop over all frames). Arrays of length n in HOST memory:
+ * imgs[i] (device, ws[i]*hs[i] floats), out_cleans[i], out_masks[i] (device).
+ * gains / readnoises may be NULL (use the context's values) or give per-frame
+ * values (> 0 and >= 0). The result of each frame equals crb_clean's. */
+int crb_clean_batch(crb_ctx* ctx, int n, const float* const* imgs, const int* ws, const int* hs,
+                    const float* gains, const float* readnoises, float* const* out_cleans,
+                    uint8_t* const* out_masks, cudaStream_t stream);
+
+/* Synchronises `stream` and returns the latched device status of the context
+ * (CRB_OK, CRB_ETIMEOUT, CRB_EDEVICE or CRB_ECUDA), then clears it. */
+int crb_sync_status(crb_ctx* ctx, cudaStream_t stream);
+
+/* After crb_sync_status: per-iteration counters of the last crb_clean /
+ * crb_iterate: out[2k] = pixels newly flagged in iteration k+1, out[2k+1] =
+ * flagged pixels with no unflagged 5x5 neighbour. Returns the number of
+ * iterations written (<= max_iter), or -1. */
+int crb_last_counts(crb_ctx* ctx, long long* out, int max_iter);
+
+/* One iteration from an explicit state, for stage-by-stage checks:
+ * J (device, w*h floats) = I_{k-1}, Mprev (device, w*h bytes, may be NULL for
+ * no flags) -> out_J = I_k, out_M = M_k (device). If maps is not NULL it
+ * receives 11 float maps of w*h (device): floored m5, L+, N, S, S', m3, F, R,
+ * cand, g1, g2 (F and R are computed only where S' > sigclip; NaN elsewhere). */
+int crb_iterate(crb_ctx* ctx, const float* J, const uint8_t* Mprev, int w, int h, float* out_J,
+                uint8_t* out_M, float* maps, cudaStream_t stream);
+
+/* Profiling (crb_options.profile = 1): after the stream has been synchronised,
+ * writes the total device time in milliseconds and the number of launches of
+ * the detection kernel (stages a-d) and of the replacement kernel (stage e)
+ * since the last reset, then resets if reset != 0. Returns CRB_OK or
+ * CRB_EINVAL (profiling off / null pointers). */
+int crb_profile_read(crb_ctx* ctx, double* detect_ms, int* detect_launches, double* replace_ms,
+                     int* replace_launches, int reset);
+
+/* Measures the FP32 min/max issue rate of the device (the ALU roofline of the
+ * selection networks): a grid of independent fminf/fmaxf chains timed with
+ * CUDA events on `stream` (synchronous). Writes min/max operations per second
+ * for 2-input (ops2) and 3-input (ops3, counting each as one operation) forms.
+ * Returns CRB_OK or CRB_ECUDA. A measurement aid for the roofline, not a
+ * step of the method. */
+int crb_alu_peak(double* ops2_per_s, double* ops3_per_s, cudaStream_t stream);
+
+/* Number of compiled tile shapes and their sizes (output tile of the detection kernel). */
+int crb_num_tile_shapes(void);
+int crb_tile_shape(int index, int* tile_w, int* tile_h);
+
+/* Message of the last error on this host thread ("" if none). */
+const char* crb_last_error(void);
+const char* crb_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CRB_H_ */

@@ -1,0 +1,7 @@
+"""GB300 (sm_103a) L.A.Cosmic cosmic-ray cleaner: C-ABI CUDA library + thin Python binding.
+
+``Cleaner`` wraps one context; ``_lib`` exposes the C functions by name. The
+CUDA library is loaded lazily on first use; nothing here runs on the CPU.
+"""
+
+from .api import Cleaner  # noqa: F401

@@ -1,0 +1,136 @@
+"""Convenience wrapper over the C ABI for torch CUDA tensors.
+
+Torch provides device memory and streams; every step of the cleaning runs in
+the library's CUDA kernels.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import check
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_img(t, name="img"):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.dim() == 2
+            and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous 2-D float32 CUDA tensor")
+
+
+class Cleaner:
+    """One cleaning context (crb_create_ex). Not thread-safe; use one per thread."""
+
+    def __init__(self, gain=7.0, readnoise=5.0, sigclip=4.5, sigfrac=0.5, objlim=1.0, niter=4, *,
+                 objlim_form=0, early_exit=False, tile_shape=0, use_graphs=False, profile=False):
+        lib = _lib.load()
+        opt = _lib.crb_options(int(objlim_form), int(bool(early_exit)), int(tile_shape), int(bool(use_graphs)),
+                               int(bool(profile)))
+        h = lib.crb_create_ex(gain, readnoise, sigclip, sigfrac, objlim, int(niter), ctypes.byref(opt))
+        if not h:
+            raise ValueError("crb_create_ex: " + lib.crb_last_error().decode())
+        self._h = ctypes.c_void_p(h)
+        self.niter = int(niter)
+        self.gain, self.readnoise = float(gain), float(readnoise)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().crb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def clean_into(self, img, out_clean, out_mask, stream=None):
+        _check_img(img)
+        h, w = img.shape
+        rc = _lib.load().crb_clean(self._h, _ptr(img), w, h, _ptr(out_clean), _ptr(out_mask), _stream(stream))
+        check(rc, "crb_clean")
+
+    def clean(self, img, stream=None):
+        """Returns (cleaned float32 frame, uint8 mask) as new CUDA tensors."""
+        _check_img(img)
+        out = torch.empty_like(img)
+        mask = torch.empty(img.shape, dtype=torch.uint8, device=img.device)
+        self.clean_into(img, out, mask, stream)
+        return out, mask
+
+    def clean_batch_into(self, imgs, outs, masks, gains=None, readnoises=None, stream=None):
+        n = len(imgs)
+        for t in imgs:
+            _check_img(t)
+        P = ctypes.c_void_p * n
+        I = ctypes.c_int * n
+        F = ctypes.c_float * n
+        a_img = P(*[t.data_ptr() for t in imgs])
+        a_out = P(*[t.data_ptr() for t in outs])
+        a_msk = P(*[t.data_ptr() for t in masks])
+        a_w = I(*[t.shape[1] for t in imgs])
+        a_h = I(*[t.shape[0] for t in imgs])
+        a_g = F(*gains) if gains is not None else None
+        a_r = F(*readnoises) if readnoises is not None else None
+        rc = _lib.load().crb_clean_batch(self._h, n, a_img, a_w, a_h, a_g, a_r, a_out, a_msk, _stream(stream))
+        check(rc, "crb_clean_batch")
+
+    def clean_batch(self, imgs, gains=None, readnoises=None, stream=None):
+        outs = [torch.empty_like(t) for t in imgs]
+        masks = [torch.empty(t.shape, dtype=torch.uint8, device=t.device) for t in imgs]
+        self.clean_batch_into(imgs, outs, masks, gains, readnoises, stream)
+        return outs, masks
+
+    def iterate(self, J, Mprev=None, maps=False, stream=None):
+        """One iteration from (J, Mprev). Returns (I_k, M_k, maps dict or None)."""
+        _check_img(J, "J")
+        h, w = J.shape
+        outJ = torch.empty_like(J)
+        outM = torch.empty(J.shape, dtype=torch.uint8, device=J.device)
+        mp = torch.empty((_lib.NUM_MAPS, h, w), dtype=torch.float32, device=J.device) if maps else None
+        rc = _lib.load().crb_iterate(self._h, _ptr(J), _ptr(Mprev) if Mprev is not None else None, w, h,
+                                     _ptr(outJ), _ptr(outM), _ptr(mp) if maps else None, _stream(stream))
+        check(rc, "crb_iterate")
+        md = {n: mp[i] for i, n in enumerate(_lib.MAP_NAMES)} if maps else None
+        return outJ, outM, md
+
+    def sync(self, stream=None):
+        check(_lib.load().crb_sync_status(self._h, _stream(stream)), "crb_sync_status")
+
+    def last_counts(self):
+        """[(new flags, flagged pixels with no unflagged neighbour)] per iteration of the last call."""
+        buf = (ctypes.c_longlong * (2 * max(self.niter, 1)))()
+        k = _lib.load().crb_last_counts(self._h, buf, max(self.niter, 1))
+        if k < 0:
+            raise RuntimeError("crb_last_counts failed")
+        return [(int(buf[2 * i]), int(buf[2 * i + 1])) for i in range(k)]
+
+    def profile_read(self, reset=True):
+        """(detect ms, detect launches, replace ms, replace launches) since the last reset."""
+        dm, rm = ctypes.c_double(), ctypes.c_double()
+        dn, rn = ctypes.c_int(), ctypes.c_int()
+        check(_lib.load().crb_profile_read(self._h, ctypes.byref(dm), ctypes.byref(dn), ctypes.byref(rm),
+                                           ctypes.byref(rn), int(reset)), "crb_profile_read")
+        return dm.value, dn.value, rm.value, rn.value
+
+
+def alu_peak(stream=None):
+    """Measured FP32 min/max operations per second: (2-input form, 3-input form)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    check(_lib.load().crb_alu_peak(ctypes.byref(a), ctypes.byref(b), _stream(stream)), "crb_alu_peak")
+    return a.value, b.value

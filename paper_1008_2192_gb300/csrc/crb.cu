@@ -1,0 +1,517 @@
+// C ABI of the cleaner (declarations and contracts in include/crb.h).
+//
+// A call validates its arguments, sizes the context's workspace, writes one
+// descriptor per frame and enqueues, per iteration, one detection launch and
+// one replacement launch over the tiles of all its frames. Calls on one
+// context are ordered (each waits for the previous one's completion event),
+// so descriptors and workspace can be reused.
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "alu_peak.cuh"
+#include "crb.h"
+#include "kernels.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return (e == cudaErrorMemoryAllocation) ? CRB_ENOMEM : CRB_ECUDA;
+}
+
+#define CRB_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+using DetectFn = void (*)(const crb::Frame*, int, long long, crb::Params, int, int);
+using ReplaceFn = void (*)(const crb::Frame*, int, long long, int, int, int);
+
+struct DetectShape {
+  int tw, th;
+  DetectFn fn, fn_maps;
+  size_t smem;
+};
+
+template <int TW, int TH>
+DetectShape make_detect() {
+  return DetectShape{TW, TH, crb::detect_kernel<TW, TH, false>, crb::detect_kernel<TW, TH, true>,
+                     crb::DetectLayout<TW, TH>::bytes};
+}
+
+const std::vector<DetectShape>& detect_shapes() {
+  static const std::vector<DetectShape> v = {make_detect<64, 32>(), make_detect<32, 32>(),
+                                             make_detect<64, 16>(), make_detect<128, 32>(),
+                                             make_detect<64, 64>()};
+  return v;
+}
+
+constexpr int kRW = 64, kRH = 16;  // replacement tile
+const ReplaceFn kReplace = crb::replace_kernel<kRW, kRH>;
+constexpr size_t kReplaceSmem = crb::ReplaceLayout<kRW, kRH>::bytes;
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+struct FrameSpec {
+  const float* img;
+  float* out_clean;
+  uint8_t* out_mask;
+  float* maps;
+  const uint8_t* mprev;  // crb_iterate only
+  int w, h;
+  float gain, rn;
+};
+
+}  // namespace
+
+struct crb_ctx {
+  crb::Params p{};
+  float gain = 0, rn = 0;
+  int niter = 0;
+  crb_options opt{};
+  int device = 0, num_sms = 0;
+  std::vector<int> occ_detect, occ_detect_maps;
+  int occ_replace = 0;
+
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  crb::Frame* d_frames = nullptr;
+  int frames_cap = 0;
+  crb::Frame* h_frames = nullptr;  // pinned staging
+  unsigned long long* d_counters = nullptr;
+  int counters_cap = 0;  // in unsigned long longs
+  int last_niter = 0;
+  cudaEvent_t upload_ev = nullptr, done_ev = nullptr;
+  bool any_call = false;
+  int latched = CRB_OK;
+
+  // profiling: event pairs around launches, by kernel kind (0 detect, 1 replace)
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[2];
+  double prof_ms[2] = {0, 0};
+  int prof_n[2] = {0, 0};
+};
+
+namespace {
+
+int init_ctx(crb_ctx* c) {
+  CRB_CUDA(cudaGetDevice(&c->device));
+  CRB_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  for (const auto& s : detect_shapes()) {
+    int occ = 0, occm = 0;
+    CRB_CUDA(cudaFuncSetAttribute(s.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s.smem)));
+    CRB_CUDA(cudaFuncSetAttribute(s.fn_maps, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s.smem)));
+    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, s.fn, crb::kThreads, s.smem));
+    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occm, s.fn_maps, crb::kThreads, s.smem));
+    c->occ_detect.push_back(occ > 0 ? occ : 1);
+    c->occ_detect_maps.push_back(occm > 0 ? occm : 1);
+  }
+  CRB_CUDA(cudaFuncSetAttribute(kReplace, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kReplaceSmem)));
+  CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_replace, kReplace, crb::kThreads, kReplaceSmem));
+  if (c->occ_replace < 1) c->occ_replace = 1;
+  CRB_CUDA(cudaEventCreateWithFlags(&c->upload_ev, cudaEventDisableTiming));
+  CRB_CUDA(cudaEventCreateWithFlags(&c->done_ev, cudaEventDisableTiming));
+  return CRB_OK;
+}
+
+cudaEvent_t take_event(crb_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch bracketed by events when profiling (kind 0 detect, 1 replace).
+template <typename F>
+void timed(crb_ctx* c, int kind, cudaStream_t stream, F&& launch) {
+  if (!c->opt.profile) {
+    launch();
+    return;
+  }
+  cudaEvent_t a = take_event(c), b = take_event(c);
+  cudaEventRecord(a, stream);
+  launch();
+  cudaEventRecord(b, stream);
+  c->pending[kind].emplace_back(a, b);
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  return pa < pb + nb && pb < pa + na;
+}
+
+int ensure_frames(crb_ctx* c, int n) {
+  if (n <= c->frames_cap) return CRB_OK;
+  CRB_CUDA(cudaDeviceSynchronize());
+  cudaFree(c->d_frames);
+  cudaFreeHost(c->h_frames);
+  c->d_frames = nullptr;
+  c->h_frames = nullptr;
+  c->frames_cap = 0;
+  CRB_CUDA(cudaMalloc(&c->d_frames, sizeof(crb::Frame) * size_t(n)));
+  CRB_CUDA(cudaMallocHost(&c->h_frames, sizeof(crb::Frame) * size_t(n)));
+  c->frames_cap = n;
+  return CRB_OK;
+}
+
+int ensure_ws(crb_ctx* c, size_t bytes, int ncounters) {
+  if (bytes > c->ws_bytes) {
+    CRB_CUDA(cudaDeviceSynchronize());
+    cudaFree(c->ws);
+    c->ws = nullptr;
+    c->ws_bytes = 0;
+    cudaError_t e = cudaMalloc(&c->ws, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CRB_ENOMEM, "workspace of " + std::to_string(bytes) + " bytes could not be allocated");
+    }
+    c->ws_bytes = bytes;
+  }
+  if (ncounters > c->counters_cap) {
+    CRB_CUDA(cudaDeviceSynchronize());
+    cudaFree(c->d_counters);
+    c->d_counters = nullptr;
+    CRB_CUDA(cudaMalloc(&c->d_counters, sizeof(unsigned long long) * size_t(ncounters)));
+    c->counters_cap = ncounters;
+  }
+  return CRB_OK;
+}
+
+// Enqueues the whole clean of `specs` (niter iterations) on `stream`.
+int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, cudaStream_t stream) {
+  const int n = int(specs.size());
+  const int shape = (c->opt.tile_shape >= 0 && c->opt.tile_shape < int(detect_shapes().size()))
+                        ? c->opt.tile_shape : 0;
+  const DetectShape& ds = detect_shapes()[size_t(shape)];
+
+  // workspace: per frame, flag bits then (niter >= 2) one image
+  std::vector<size_t> off_bits(static_cast<size_t>(n)), off_img(static_cast<size_t>(n));
+  size_t total = 0;
+  for (int i = 0; i < n; ++i) {
+    const auto& s = specs[size_t(i)];
+    const size_t wpr = size_t(s.w + 31) / 32;
+    off_bits[size_t(i)] = total;
+    total += align256(wpr * size_t(s.h) * 4);
+  }
+  const size_t bits_total = total;
+  for (int i = 0; i < n; ++i) {
+    const auto& s = specs[size_t(i)];
+    off_img[size_t(i)] = total;
+    if (niter >= 2) total += align256(size_t(s.w) * size_t(s.h) * 4);
+  }
+  const int ncounters = 2 * (niter > 0 ? niter : 1) * n;
+  int rc = ensure_frames(c, n);
+  if (rc) return rc;
+  rc = ensure_ws(c, total > 0 ? total : 256, ncounters);
+  if (rc) return rc;
+
+  if (c->any_call) CRB_CUDA(cudaStreamWaitEvent(stream, c->done_ev, 0));
+  CRB_CUDA(cudaEventSynchronize(c->upload_ev));  // the staging buffer is free again
+
+  long long tiles = 0, rtiles = 0;
+  for (int i = 0; i < n; ++i) {
+    const auto& s = specs[size_t(i)];
+    crb::Frame& f = c->h_frames[i];
+    f.img = s.img;
+    f.out_clean = s.out_clean;
+    f.ws = (niter >= 2) ? reinterpret_cast<float*>(static_cast<char*>(c->ws) + off_img[size_t(i)]) : nullptr;
+    f.bits = reinterpret_cast<uint32_t*>(static_cast<char*>(c->ws) + off_bits[size_t(i)]);
+    f.out_mask = s.out_mask;
+    f.maps = s.maps;
+    f.counters = c->d_counters + size_t(2) * (niter > 0 ? niter : 1) * i;
+    f.w = s.w;
+    f.h = s.h;
+    f.wpr = (s.w + 31) / 32;
+    f.gain = s.gain;
+    f.rn = s.rn;
+    f.tiles_x = (s.w + ds.tw - 1) / ds.tw;
+    f.rtiles_x = (s.w + kRW - 1) / kRW;
+    f.tile0 = tiles;
+    f.rtile0 = rtiles;
+    tiles += (long long)f.tiles_x * ((s.h + ds.th - 1) / ds.th);
+    rtiles += (long long)f.rtiles_x * ((s.h + kRH - 1) / kRH);
+  }
+  CRB_CUDA(cudaMemcpyAsync(c->d_frames, c->h_frames, sizeof(crb::Frame) * size_t(n), cudaMemcpyHostToDevice,
+                           stream));
+  CRB_CUDA(cudaEventRecord(c->upload_ev, stream));
+  CRB_CUDA(cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * size_t(ncounters), stream));
+  c->last_niter = niter;
+
+  if (niter == 0) {
+    for (const auto& s : specs) {
+      CRB_CUDA(cudaMemcpyAsync(s.out_clean, s.img, size_t(s.w) * s.h * 4, cudaMemcpyDeviceToDevice, stream));
+      CRB_CUDA(cudaMemsetAsync(s.out_mask, 0, size_t(s.w) * s.h, stream));
+    }
+  } else {
+    CRB_CUDA(cudaMemsetAsync(c->ws, 0, bits_total, stream));
+    for (int i = 0; i < n; ++i) {
+      const auto& s = specs[size_t(i)];
+      if (s.mprev) {
+        const crb::Frame& f = c->h_frames[i];
+        const long long nwords = (long long)f.wpr * f.h;
+        const int blocks = int((nwords * 32 + 255) / 256 < 65535 ? (nwords * 32 + 255) / 256 : 65535);
+        crb::bytes_to_bits_kernel<<<blocks, 256, 0, stream>>>(s.mprev, f.bits, f.w, f.h, f.wpr);
+      }
+    }
+    const int dgrid = int(std::min<long long>(tiles, (long long)c->num_sms *
+                                                         (maps ? c->occ_detect_maps : c->occ_detect)[size_t(shape)]));
+    const int rgrid = int(std::min<long long>(rtiles, (long long)c->num_sms * c->occ_replace));
+    for (int k = 1; k <= niter; ++k) {
+      timed(c, 0, stream, [&] {
+        (maps ? ds.fn_maps : ds.fn)<<<dgrid, crb::kThreads, ds.smem, stream>>>(c->d_frames, n, tiles, c->p, k,
+                                                                                 niter);
+      });
+      timed(c, 1, stream, [&] {
+        kReplace<<<rgrid, crb::kThreads, kReplaceSmem, stream>>>(c->d_frames, n, rtiles, k, niter,
+                                                                 k <= 2 ? 1 : 0);
+      });
+    }
+    CRB_CUDA(cudaGetLastError());
+  }
+  CRB_CUDA(cudaEventRecord(c->done_ev, stream));
+  c->any_call = true;
+  return CRB_OK;
+}
+
+bool valid_params(float gain, float rn, float sigclip, float sigfrac, float objlim, int niter) {
+  return gain > 0.f && rn >= 0.f && sigclip > 0.f && sigfrac > 0.f && objlim > 0.f && niter >= 0 &&
+         gain < 1e30f && rn < 1e30f && sigclip < 1e30f && sigfrac < 1e30f && objlim < 1e30f;
+}
+
+int check_frame(const void* img, int w, int h, const void* out_clean, const void* out_mask) {
+  if (w < 1 || h < 1) return fail(CRB_EINVAL, "frame sizes must be >= 1");
+  if ((long long)w * h >= (1LL << 31)) return fail(CRB_EINVAL, "w*h must be < 2^31");
+  if (!img || !out_clean || !out_mask) return fail(CRB_EINVAL, "null image or output pointer");
+  const size_t n = size_t(w) * size_t(h);
+  if (overlaps(img, n * 4, out_clean, n * 4) || overlaps(img, n * 4, out_mask, n) ||
+      overlaps(out_clean, n * 4, out_mask, n))
+    return fail(CRB_EALIAS, "outputs must not overlap the input or each other");
+  return CRB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+crb_ctx* crb_create_ex(float gain, float readnoise, float sigclip, float sigfrac, float objlim, int niter,
+                       const crb_options* opts) {
+  if (!valid_params(gain, readnoise, sigclip, sigfrac, objlim, niter)) {
+    g_err = "invalid parameters: need gain > 0, readnoise >= 0, sigclip > 0, sigfrac > 0, objlim > 0, niter >= 0";
+    return nullptr;
+  }
+  if (opts && (opts->objlim_form < 0 || opts->objlim_form > 1)) {
+    g_err = "objlim_form must be 0 or 1";
+    return nullptr;
+  }
+  auto* c = new crb_ctx();
+  if (opts) c->opt = *opts;
+  c->gain = gain;
+  c->rn = readnoise;
+  c->niter = niter;
+  c->p = crb::Params{sigclip, sigfrac, objlim, c->opt.objlim_form};
+  if (init_ctx(c) != CRB_OK) {
+    crb_destroy(c);
+    return nullptr;
+  }
+  g_err.clear();
+  return c;
+}
+
+crb_ctx* crb_create(float gain, float readnoise, float sigclip, float sigfrac, float objlim, int niter) {
+  return crb_create_ex(gain, readnoise, sigclip, sigfrac, objlim, niter, nullptr);
+}
+
+void crb_destroy(crb_ctx* c) {
+  if (!c) return;
+  if (c->any_call) cudaEventSynchronize(c->done_ev);
+  for (auto& v : c->pending)
+    for (auto& pr : v) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  cudaFree(c->ws);
+  cudaFree(c->d_frames);
+  cudaFree(c->d_counters);
+  if (c->h_frames) cudaFreeHost(c->h_frames);
+  if (c->upload_ev) cudaEventDestroy(c->upload_ev);
+  if (c->done_ev) cudaEventDestroy(c->done_ev);
+  delete c;
+}
+
+int crb_clean(crb_ctx* c, const float* img, int w, int h, float* out_clean, uint8_t* out_mask,
+              cudaStream_t stream) {
+  if (!c) return fail(CRB_EINVAL, "null context");
+  int rc = check_frame(img, w, h, out_clean, out_mask);
+  if (rc) return rc;
+  std::vector<FrameSpec> specs{FrameSpec{img, out_clean, out_mask, nullptr, nullptr, w, h, c->gain, c->rn}};
+  return run(c, specs, c->niter, false, stream);
+}
+
+int crb_clean_batch(crb_ctx* c, int n, const float* const* imgs, const int* ws, const int* hs,
+                    const float* gains, const float* readnoises, float* const* out_cleans,
+                    uint8_t* const* out_masks, cudaStream_t stream) {
+  if (!c) return fail(CRB_EINVAL, "null context");
+  if (n < 0 || (n > 0 && (!imgs || !ws || !hs || !out_cleans || !out_masks)))
+    return fail(CRB_EINVAL, "invalid batch arrays");
+  if (n == 0) return CRB_OK;
+  std::vector<FrameSpec> specs;
+  specs.reserve(size_t(n));
+  for (int i = 0; i < n; ++i) {
+    int rc = check_frame(imgs[i], ws[i], hs[i], out_cleans[i], out_masks[i]);
+    if (rc) return fail(rc, "frame " + std::to_string(i) + ": " + g_err);
+    const float g = gains ? gains[i] : c->gain;
+    const float r = readnoises ? readnoises[i] : c->rn;
+    if (!(g > 0.f) || !(r >= 0.f)) return fail(CRB_EINVAL, "frame " + std::to_string(i) + ": gain/readnoise");
+    specs.push_back(FrameSpec{imgs[i], out_cleans[i], out_masks[i], nullptr, nullptr, ws[i], hs[i], g, r});
+  }
+  return run(c, specs, c->niter, false, stream);
+}
+
+int crb_iterate(crb_ctx* c, const float* J, const uint8_t* Mprev, int w, int h, float* out_J, uint8_t* out_M,
+                float* maps, cudaStream_t stream) {
+  if (!c) return fail(CRB_EINVAL, "null context");
+  int rc = check_frame(J, w, h, out_J, out_M);
+  if (rc) return rc;
+  std::vector<FrameSpec> specs{FrameSpec{J, out_J, out_M, maps, Mprev, w, h, c->gain, c->rn}};
+  if (maps) {
+    CRB_CUDA(cudaMemsetAsync(maps, 0xff, sizeof(float) * crb::kNumMaps * size_t(w) * h, stream));  // NaN
+  }
+  return run(c, specs, 1, maps != nullptr, stream);
+}
+
+int crb_sync_status(crb_ctx* c, cudaStream_t stream) {
+  if (!c) return fail(CRB_EINVAL, "null context");
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "device execution");
+  const int s = c->latched;
+  c->latched = CRB_OK;
+  return s;
+}
+
+int crb_last_counts(crb_ctx* c, long long* out, int max_iter) {
+  if (!c || !out || max_iter < 0) return -1;
+  const int k = std::min(c->last_niter, max_iter);
+  if (k == 0) return 0;
+  std::vector<unsigned long long> tmp(size_t(2 * k));
+  if (cudaMemcpy(tmp.data(), c->d_counters, sizeof(unsigned long long) * tmp.size(), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return -1;
+  for (size_t i = 0; i < tmp.size(); ++i) out[i] = (long long)tmp[i];
+  return k;
+}
+
+int crb_profile_read(crb_ctx* c, double* detect_ms, int* detect_launches, double* replace_ms,
+                     int* replace_launches, int reset) {
+  if (!c || !c->opt.profile) return fail(CRB_EINVAL, "profiling is off for this context");
+  for (int kind = 0; kind < 2; ++kind) {
+    for (auto& pr : c->pending[kind]) {
+      float ms = 0.f;
+      CRB_CUDA(cudaEventSynchronize(pr.second));
+      CRB_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+      c->prof_ms[kind] += ms;
+      c->prof_n[kind] += 1;
+      c->ev_pool.push_back(pr.first);
+      c->ev_pool.push_back(pr.second);
+    }
+    c->pending[kind].clear();
+  }
+  if (detect_ms) *detect_ms = c->prof_ms[0];
+  if (detect_launches) *detect_launches = c->prof_n[0];
+  if (replace_ms) *replace_ms = c->prof_ms[1];
+  if (replace_launches) *replace_launches = c->prof_n[1];
+  if (reset) {
+    c->prof_ms[0] = c->prof_ms[1] = 0;
+    c->prof_n[0] = c->prof_n[1] = 0;
+  }
+  return CRB_OK;
+}
+
+int crb_alu_peak(double* ops2_per_s, double* ops3_per_s, cudaStream_t stream) {
+  int dev = 0, sms = 0;
+  CRB_CUDA(cudaGetDevice(&dev));
+  CRB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  float* buf = nullptr;
+  CRB_CUDA(cudaMalloc(&buf, sizeof(float) * (192 + size_t(sms) * 8 * 256)));
+  std::vector<float> init(192);
+  for (int i = 0; i < 192; ++i) init[size_t(i)] = (i < 64) ? float(i) : (i < 128 ? -1000.f + i : 1000.f + i);
+  cudaEvent_t a = nullptr, b = nullptr;
+  int rc = CRB_OK;
+  const int blocks = sms * 8, iters = 4096;
+  double best[2] = {0, 0};
+  if (cudaMemcpy(buf, init.data(), sizeof(float) * 192, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    rc = cuda_fail(cudaGetLastError(), "crb_alu_peak setup");
+  }
+  for (int form = 0; form < 2 && rc == CRB_OK; ++form) {
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(a, stream);
+      if (form == 0)
+        crb::alu_peak_kernel<false><<<blocks, 256, 0, stream>>>(buf, buf + 192, iters);
+      else
+        crb::alu_peak_kernel<true><<<blocks, 256, 0, stream>>>(buf, buf + 192, iters);
+      cudaEventRecord(b, stream);
+      cudaError_t e = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e != cudaSuccess) {
+        rc = cuda_fail(e, "crb_alu_peak");
+        break;
+      }
+      const double ops = double(blocks) * 256 * iters * crb::kPeakChains * 2;
+      if (rep > 0) best[form] = std::max(best[form], ops / (ms * 1e-3));
+    }
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(buf);
+  if (rc == CRB_OK) {
+    if (ops2_per_s) *ops2_per_s = best[0];
+    if (ops3_per_s) *ops3_per_s = best[1];
+  }
+  return rc;
+}
+
+int crb_num_tile_shapes(void) { return int(detect_shapes().size()); }
+
+int crb_tile_shape(int index, int* tile_w, int* tile_h) {
+  if (index < 0 || index >= int(detect_shapes().size())) return CRB_EINVAL;
+  if (tile_w) *tile_w = detect_shapes()[size_t(index)].tw;
+  if (tile_h) *tile_h = detect_shapes()[size_t(index)].th;
+  return CRB_OK;
+}
+
+const char* crb_last_error(void) { return g_err.c_str(); }
+
+const char* crb_strerror(int s) {
+  switch (s) {
+    case CRB_OK: return "ok";
+    case CRB_EINVAL: return "invalid argument";
+    case CRB_ENOMEM: return "out of device memory";
+    case CRB_ECUDA: return "CUDA error";
+    case CRB_ETIMEOUT: return "device wait timed out";
+    case CRB_EBUSY: return "busy: admission refused";
+    case CRB_EALIAS: return "output overlaps input";
+    case CRB_EDEVICE: return "device-side check failed";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+"""Host-side checks of the C ABI that need no GPU."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1008_2192_gb300._lib as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for fn in sorted(os.listdir(inc)):
+        if fn.endswith(".h"):
+            text = open(os.path.join(inc, fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(crb_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = L.load()
+    names = declared_functions()
+    assert len(names) >= 10
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header():
+    assert set(declared_functions()) <= set(L.SIGNATURES)
+
+
+@pytest.mark.parametrize("args", [
+    (0.0, 5.0, 4.5, 0.5, 1.0, 4), (7.0, -1.0, 4.5, 0.5, 1.0, 4), (7.0, 5.0, 0.0, 0.5, 1.0, 4),
+    (7.0, 5.0, 4.5, 0.0, 1.0, 4), (7.0, 5.0, 4.5, 0.5, 0.0, 4), (7.0, 5.0, 4.5, 0.5, 1.0, -1),
+    (float("nan"), 5.0, 4.5, 0.5, 1.0, 4),
+])
+def test_create_rejects_invalid_parameters(args):
+    lib = L.load()
+    assert not lib.crb_create(*args)
+    assert b"invalid parameters" in lib.crb_last_error()
+
+
+def test_null_context_and_strerror():
+    lib = L.load()
+    assert lib.crb_clean(None, None, 1, 1, None, None, None) == L.CRB_EINVAL
+    assert lib.crb_sync_status(None, None) == L.CRB_EINVAL
+    assert lib.crb_strerror(L.CRB_EALIAS) == b"output overlaps input"
+    assert lib.crb_strerror(99) == b"unknown status"
+    tw, th = ctypes.c_int(), ctypes.c_int()
+    for i in range(lib.crb_num_tile_shapes()):
+        assert lib.crb_tile_shape(i, ctypes.byref(tw), ctypes.byref(th)) == 0
+        assert tw.value % 32 == 0 and th.value > 0
+    assert lib.crb_tile_shape(-1, None, None) == L.CRB_EINVAL
+
+
+def test_networks_exhaustive_zero_one():
+    """The 9- and 25-input selection networks are correct on every 0/1 input (0-1 principle)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "gen_networks", os.path.join(ROOT, "paper_1008_2192_gb300", "csrc", "gen_networks.py"))
+    g = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(g)
+    for (_, n, rank) in g.SPECS:
+        c, d, order, out = g.best_network(n, rank)
+        g.verify(n, rank, d, order, out, exhaustive=True)

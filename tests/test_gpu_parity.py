@@ -1,0 +1,209 @@
+"""GPU (CUDA library, through the C ABI) against the CPU oracle on seeded synthetic frames."""
+
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import workloads
+from gpu_util import (assert_clean_matches_f64, assert_map_close, crop_with_context, dev, gpu_clean, host,
+                      params_of)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1008_2192_gb300 import Cleaner  # noqa: E402
+
+# sizes spanning several tiles with ragged tails, degenerate strips and odd widths
+SIZES = [(1, 1), (1, 17), (17, 1), (2, 2), (7, 13), (13, 7), (31, 33), (64, 32), (65, 33), (100, 77),
+         (129, 70), (200, 150)]
+
+
+def scene(w, h, seed=0):
+    n = w * h
+    return synth.frame(w, h, seed=seed, sky=100.0, nstars=max(1, n // 2000),
+                       ncr=max(1, int(n * synth.CR_DENSITY * 3)))
+
+
+@pytest.fixture(scope="module")
+def cl():
+    c = Cleaner(niter=4)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("w,h", SIZES)
+def test_stage_maps_match_oracle(w, h):
+    """One iteration with every intermediate map exported: bit-identical to the FP32 oracle,
+    within tolerance of the FP64 oracle."""
+    cl1 = Cleaner(niter=1)
+    img = scene(w, h, seed=w * 1000 + h)
+    J, M, maps = cl1.iterate(dev(img), None, maps=True)
+    cl1.sync()
+    J, M = host(J), host(M)
+    gm = {k: host(v) for k, v in maps.items()}
+    P = params_of({})
+    r32 = oracle.iterate(img, None, P, precision="f32", maps=True)
+    r64 = oracle.iterate(img, None, P, precision="f64", maps=True, fragile=True)
+    lazy = ("f", "r")  # computed only where S' > sigclip
+    both = (gm["sprime"] > 4.5) & (r32.maps["sprime"] > 4.5)
+    for name in oracle.MAP_NAMES:
+        g, o = gm[name], r32.maps[name]
+        if name in lazy:
+            assert np.array_equal(g[both], o[both]), name
+        else:
+            assert np.array_equal(g, o.astype(np.float32)), name
+    assert np.array_equal(M, r32.Mk) and np.array_equal(J, r32.Ik)
+    for name in ("m5", "lplus", "noise", "s", "sprime", "m3"):
+        assert_map_close(gm[name], r64.maps[name], name)
+    both64 = (gm["sprime"] > 4.5) & (r64.maps["sprime"] > 4.5)
+    for name in lazy:
+        assert_map_close(gm[name][both64], r64.maps[name][both64], name)
+    ok = r64.fragile == 0
+    assert np.array_equal(M[ok], r64.Mk[ok])
+
+
+def test_lockstep_iterations(cl):
+    """Each GPU iteration fed the oracle's state (J, M_{k-1}) reproduces the oracle's next state."""
+    img = workloads.make(workloads.single_800())
+    P = params_of({})
+    c1 = Cleaner(niter=1)
+    J, M = img, np.zeros(img.shape, np.uint8)
+    for k in range(4):
+        r = oracle.iterate(J, M, P, precision="f32")
+        gJ, gM, _ = c1.iterate(dev(J), dev(M))
+        c1.sync()
+        assert np.array_equal(host(gM), r.Mk), f"iteration {k + 1} mask"
+        assert np.array_equal(host(gJ), r.Ik), f"iteration {k + 1} image"
+        assert c1.last_counts()[0] == (r.n_new, r.n_none_left)
+        J, M = r.Ik, r.Mk
+
+
+def test_end_to_end_800(cl):
+    """The 800x800 workload, niter=4, end to end: exact vs FP32 oracle, tolerance vs FP64."""
+    img = workloads.make(workloads.single_800())
+    out, mask = gpu_clean(cl, img)
+    P = params_of({})
+    r32 = oracle.clean(img, P, 4, precision="f32")
+    assert np.array_equal(mask, r32.mask) and np.array_equal(out, r32.clean)
+    counts = cl.last_counts()
+    assert [c[0] for c in counts] == r32.n_new and [c[1] for c in counts] == r32.n_none_left
+    r64 = oracle.clean(img, P, 4, fragile=True)
+    flips, nfragile = assert_clean_matches_f64(out, mask, r64, "800x800")
+    print(f"800x800: mask flips vs FP64 {flips}, fragile pixels {nfragile}, flagged {int(mask.sum())}")
+
+
+@pytest.mark.parametrize("w,h", SIZES)
+@pytest.mark.parametrize("niter", [1, 2, 3, 4])
+def test_clean_sizes(w, h, niter):
+    img = scene(w, h, seed=7 * w + h)
+    c = Cleaner(niter=niter)
+    out, mask = gpu_clean(c, img)
+    r32 = oracle.clean(img, params_of({}), niter, precision="f32")
+    assert np.array_equal(mask, r32.mask) and np.array_equal(out, r32.clean)
+
+
+def test_niter_zero_copies():
+    img = scene(50, 40)
+    c = Cleaner(niter=0)
+    out, mask = gpu_clean(c, img)
+    assert np.array_equal(out, img) and not mask.any()
+
+
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("pset", [dict(), dict(gain=1.5, readnoise=9.0, sigclip=5.0, sigfrac=0.3, objlim=4.0)])
+def test_parameters_and_objlim_forms(form, pset):
+    img = scene(160, 120, seed=3)
+    kw = dict(pset, objlim_form=form)
+    c = Cleaner(niter=4, **kw)
+    out, mask = gpu_clean(c, img)
+    r32 = oracle.clean(img, params_of(kw), 4, precision="f32")
+    assert np.array_equal(mask, r32.mask) and np.array_equal(out, r32.clean)
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4])
+def test_tile_shapes_agree(shape):
+    img = scene(300, 230, seed=11)
+    ref = oracle.clean(img, params_of({}), 4, precision="f32")
+    c = Cleaner(niter=4, tile_shape=shape)
+    out, mask = gpu_clean(c, img)
+    assert np.array_equal(mask, ref.mask) and np.array_equal(out, ref.clean)
+
+
+def test_batch_equals_single(cl):
+    """Uneven frames with per-frame gain/read noise in one batched call equal per-frame calls."""
+    rng = np.random.default_rng(1)
+    sizes = [(800, 800), (97, 211), (1024, 64), (1, 5), (333, 333), (64, 1)]
+    imgs = [synth.frame(w, h, seed=5, index=i) for i, (w, h) in enumerate(sizes)]
+    gains = [float(np.float32(rng.uniform(1, 7))) for _ in sizes]
+    rns = [float(np.float32(rng.uniform(3, 10))) for _ in sizes]
+    outs, masks = cl.clean_batch([dev(a) for a in imgs], gains, rns)
+    cl.sync()
+    for i, a in enumerate(imgs):
+        ci = Cleaner(gain=gains[i], readnoise=rns[i], niter=4)
+        o, m = gpu_clean(ci, a)
+        assert np.array_equal(host(outs[i]), o) and np.array_equal(host(masks[i]), m), i
+        if a.size <= 400_000:
+            r32 = oracle.clean(a, params_of(dict(gain=gains[i], readnoise=rns[i])), 4, precision="f32")
+            assert np.array_equal(m, r32.mask) and np.array_equal(o, r32.clean)
+
+
+def test_repeated_calls_deterministic(cl):
+    img = scene(257, 129, seed=2)
+    a = gpu_clean(cl, img)
+    b = gpu_clean(cl, img)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_alias_and_invalid_sizes_rejected(cl):
+    import paper_1008_2192_gb300._lib as L
+    t = dev(scene(40, 30))
+    with pytest.raises(L.CrbError) as e:
+        cl.clean_into(t, t, torch.empty((30, 40), dtype=torch.uint8, device="cuda"))
+    assert e.value.status == L.CRB_EALIAS
+    lib = L.load()
+    import ctypes
+    rc = lib.crb_clean(cl.handle, ctypes.c_void_p(t.data_ptr()), 0, 30, ctypes.c_void_p(t.data_ptr() + 4),
+                       ctypes.c_void_p(t.data_ptr()), None)
+    assert rc == L.CRB_EINVAL
+
+
+def _check_crops(img, out, mask, niter, crops, P):
+    """Oracle on crops with 8*niter context (exact by the dependency radius) vs the GPU full frame."""
+    ctx = 8 * niter
+    for (y0, x0, hh, ww) in crops:
+        c, sl = crop_with_context(img, y0, x0, hh, ww, ctx)
+        r = oracle.clean(c, P, niter, precision="f32")
+        assert np.array_equal(r.mask[sl], mask[y0:y0 + hh, x0:x0 + ww]), (y0, x0)
+        assert np.array_equal(r.clean[sl], out[y0:y0 + hh, x0:x0 + ww]), (y0, x0)
+
+
+def test_4096_sampled_crops():
+    """The 4096x4096 workload: the full GPU run against the oracle on 256x256 crops."""
+    rec = workloads.single_4096()
+    img = workloads.make(rec)
+    c = Cleaner(gain=rec["gain"], readnoise=rec["readnoise"], niter=4)
+    out, mask = gpu_clean(c, img)
+    rng = np.random.default_rng(0)
+    crops = [(0, 0, 256, 256), (0, 3840, 256, 256), (3840, 0, 256, 256), (3840, 3840, 256, 256)]
+    crops += [(int(rng.integers(0, 3840)), int(rng.integers(0, 3840)), 256, 256) for _ in range(6)]
+    _check_crops(img, out, mask, 4, crops, params_of(rec))
+
+
+def test_mosaic_16384_sampled_crops():
+    """The 16384x16384 mosaic (1 GiB) in one call; 512x512 crops: corners, edge midpoints, random."""
+    rec = workloads.mosaic_16384()
+    img = workloads.make(rec)
+    c = Cleaner(gain=rec["gain"], readnoise=rec["readnoise"], niter=4)
+    out, mask = gpu_clean(c, img)
+    S, n = 16384, 512
+    crops = [(0, 0), (0, S - n), (S - n, 0), (S - n, S - n), (0, S // 2), (S // 2, 0), (S - n, S // 2),
+             (S // 2, S - n)]
+    rng = np.random.default_rng(4)
+    crops += [(int(rng.integers(0, S - n)), int(rng.integers(0, S - n))) for _ in range(8)]
+    _check_crops(img, out, mask, 4, [(y, x, n, n) for (y, x) in crops], params_of(rec))
