@@ -98,6 +98,29 @@ int crb_clean_batch(crb_ctx* ctx, int n, const float* const* imgs, const int* ws
                     const float* gains, const float* readnoises, float* const* out_cleans,
                     uint8_t* const* out_masks, cudaStream_t stream);
 
+/* Allocation-free clean of one frame. The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory while they
+ * run -- onboard or embedded pipelines that fix their memory plan at start-up,
+ * latency-bound loops in which cudaMalloc/cudaFree would synchronise the
+ * device, and processes whose device memory is owned by another allocator.
+ * It takes the parameters of crb_create directly (no context) and computes
+ * the same result as crb_clean with objlim_form 0 and the default tile shape.
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch
+ * (one image buffer, the flag bits, the counters and the descriptor, about
+ * 17 MB) is a fixed device array in the library, held by every GPU that loads
+ * the library until the process exits.
+ * Limits: w, h <= 16384, w*h <= 4194304 (4 Mpix, e.g. 2048x2048), niter <= 64;
+ * larger frames return CRB_EINVAL with a message (use crb_clean).
+ * The first call on a device, with that device current, looks up the device
+ * address of the scratch array and sets the kernels' launch attributes; make
+ * that first call before any stream capture. Every call on a device uses the
+ * same scratch, which keeps the previous call's contents (each call clears
+ * what must start at zero): calls that overlap on the GPU -- on unordered
+ * streams or from several host threads -- race and corrupt each other's
+ * results; order them on one stream or with events. */
+int crb_clean_noalloc(float gain, float readnoise, float sigclip, float sigfrac, float objlim, int niter,
+                      const float* img, int w, int h, float* out_clean, uint8_t* out_mask, cudaStream_t stream);
+
 /* Synchronises `stream` and returns the latched device status of the context
  * (CRB_OK, CRB_ETIMEOUT, CRB_EDEVICE or CRB_ECUDA), then clears it. */
 int crb_sync_status(crb_ctx* ctx, cudaStream_t stream);

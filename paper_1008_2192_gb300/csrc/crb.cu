@@ -75,6 +75,9 @@ struct FrameSpec {
 
 }  // namespace
 
+// Lets the library's other translation units report a message through crb_last_error().
+void crb_detail_set_error(const char* msg) { g_err = msg ? msg : ""; }
+
 struct crb_ctx {
   crb::Params p{};
   float gain = 0, rn = 0;

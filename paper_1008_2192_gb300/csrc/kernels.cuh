@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(kThreads) replace_kernel(const Frame* __restri
 
 // --------------------------------------------------------------------------------------------
 // Helpers: u8 mask <-> flag bits, one warp per 32-pixel word.
-__global__ void bytes_to_bits_kernel(const uint8_t* __restrict__ m, uint32_t* __restrict__ bits, int w, int h,
+static __global__ void bytes_to_bits_kernel(const uint8_t* __restrict__ m, uint32_t* __restrict__ bits, int w, int h,
                                      int wpr) {
   const long long nwords = (long long)wpr * h;
   const int lane = threadIdx.x & 31;
