@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="crb", choices=["crb", "reference"])
     ap.add_argument("--workload", default="batch64",
-                    choices=["batch64", "single4096", "single800", "mosaic16384"])
+                    choices=["batch64", "single4096", "single800", "mosaic16384", "triple4096"])
     ap.add_argument("--tile-shape", type=int, default=0)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / per-frame / cpu legs")
     return ap.parse_args()
@@ -64,6 +64,8 @@ def recipes_for(name):
         return wl.batch_64(), "64 uneven frames: 16x800x800, 16x1024x1024, 16x2048x4096, 16x4096x4096"
     if name == "single4096":
         return [wl.single_4096()], "one 4096x4096 frame, 5000 stars, 40000 cosmic rays"
+    if name == "triple4096":  # a small case above L2 size, for profiler captures
+        return wl.batch_64(sizes=[(4096, 4096)], per_size=3), "three 4096x4096 frames of the batch mix"
     if name == "single800":
         return [wl.single_800()], "one 800x800 frame, 200 stars, 1500 cosmic rays"
     return [wl.mosaic_16384()], "one 16384x16384 mosaic, 2e5 stars, 6e5 cosmic rays"

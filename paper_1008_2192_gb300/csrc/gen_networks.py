@@ -166,8 +166,40 @@ def verify(n, rank, d, order, out, exhaustive=True):
             assert np.array_equal(got, exp), f"0-1 inputs, n={n}"
 
 
+def fuse3(d, order, out):
+    """Pairs a min (max) node with a single-use min (max) operand: op(op(a, b), c) = op3(a, b, c).
+
+    Returns {node: (op, operands)} for every emitted node; operands has 2 or 3 entries.
+    The three-input form issues at the rate of the two-input one on sm_103a.
+    """
+    uses = {}
+    for v in order:
+        k = d.defs[v]
+        if k[0] in ("min", "max"):
+            for u in k[1:]:
+                uses[u] = uses.get(u, 0) + 1
+    uses[out] = uses.get(out, 0) + 1
+    absorbed = set()
+    emitted = {}
+    for v in reversed(order):  # from the output down, so a fused operand is never emitted twice
+        k = d.defs[v]
+        if k[0] not in ("min", "max") or v in absorbed:
+            continue
+        ops = [k[1], k[2]]
+        for idx, u in enumerate(ops):
+            ku = d.defs[u]
+            if ku[0] == k[0] and uses.get(u, 0) == 1 and u not in emitted:
+                absorbed.add(u)
+                ops = ops[:idx] + [ku[1], ku[2]] + ops[idx + 1:]
+                break
+        emitted[v] = (k[0], ops)
+    return emitted
+
+
 def emit(name, n, rank, d, order, out):
-    lines = [f"// rank {rank} (0-based) of {n} values; {count_ops(d, order)} min/max operations",
+    fused = fuse3(d, order, out)
+    lines = [f"// rank {rank} (0-based) of {n} values; {count_ops(d, order)} two-input min/max, "
+             f"{len(fused)} instructions with three-input forms",
              f"__device__ __forceinline__ float {name}(const float (&v)[{n}]) {{"]
     names = {}
     t = 0
@@ -175,23 +207,38 @@ def emit(name, n, rank, d, order, out):
         k = d.defs[v]
         if k[0] == "in":
             names[v] = f"v[{k[1]}]"
-        else:
-            fn = "fminf" if k[0] == "min" else "fmaxf"
+        elif v in fused:
+            op, ops = fused[v]
+            args = ", ".join(names[u] for u in ops)
+            fn = ("fminf" if op == "min" else "fmaxf") if len(ops) == 2 else ("min3f" if op == "min" else "max3f")
             names[v] = f"t{t}"
-            lines.append(f"  const float t{t} = {fn}({names[k[1]]}, {names[k[2]]});")
+            lines.append(f"  const float t{t} = {fn}({args});")
             t += 1
     lines.append(f"  return {names[out]};")
     lines.append("}")
     return "\n".join(lines)
 
 
-SPECS = [("sel_med9", 9, 4), ("sel_med25", 25, 12), ("sel_med49", 49, 24)]
+SPECS = [("sel_med5", 5, 2), ("sel_med9", 9, 4), ("sel_med25", 25, 12), ("sel_med49", 49, 24)]
+
+PRELUDE = """// Three-input min/max (PTX min.f32 / max.f32 with three sources, sm_100+).
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+"""
 
 
 def main(path, exhaustive=True):
     parts = ["// Generated by gen_networks.py -- do not edit.",
              "// Pruned Batcher odd-even merge selection networks (exact selections).",
-             "#pragma once", ""]
+             "#pragma once", "", PRELUDE]
     for (name, n, rank) in SPECS:
         c, d, order, out = best_network(n, rank)
         verify(n, rank, d, order, out, exhaustive)

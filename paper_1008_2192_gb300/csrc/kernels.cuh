@@ -93,65 +93,208 @@ __device__ __forceinline__ float noise_of(float m5f, float gain, float rn2) {
 }
 
 // --------------------------------------------------------------------------------------------
-// detect: stages (a)-(d) for one output tile of TW x TH pixels.
+// Appends idx to a shared-memory list when pred holds (warp-aggregated). Every
+// lane of the warp must call it: loops that use it are padded to whole blocks.
+__device__ __forceinline__ void push_if(bool pred, int idx, uint16_t* list, int* count) {
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (m == 0u) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = uint16_t(idx);
+}
+
+constexpr int round16(int b) { return (b + 15) / 16 * 16; }
+constexpr int imax(int a, int b) { return a > b ? a : b; }
+
+// --------------------------------------------------------------------------------------------
+// detect: stages (a)-(d) for one output tile of TW x TH pixels, computed only
+// where they can change a flag.
 //
-// Shared-memory regions, each centred on the tile, "Rk" = tile grown by k:
-//   sJ  (R6): J, clamped at load (replicate edge);
-//   sS  (R4): S = L+/(2N);        sM3 (R5): med3(J);
-//   sN  (R2): N (for F/N);        sSp (R2): S' (-inf outside the frame);
-//   sC  (R2): candidate flags;    sG1 (R1): first-growth flags.
+// Exact pruning. S >= 0 and med5(S) >= 0, so S' <= S (also after float
+// rounding). A flag needs a candidate within 2 px, a candidate needs
+// S' > sigclip, and a second-growth flag needs S' > sigfrac*sigclip. With an
+// upper bound S+ >= S, the only positions whose S' can matter are
+//   needS' = dilate5({S+ > sigclip}) and S+ > sigfrac*sigclip,
+// the exact S is needed on dilate5(needS'), and med3 on the 7x7
+// neighbourhoods of the positions with S' > sigclip. S' elsewhere is replaced
+// by -inf, which passes no threshold: the flags are unchanged.
+// S+ comes from a lower bound of the 5x5 median: at most two values of each
+// column lie below that column's median, so at most 10 of the 25 lie below the
+// smallest column median, which is therefore <= the median. The threshold test
+// S+ > t is evaluated as L+^2 gain^2 > 4 t^2 (1 - 1e-4) (gain m + rn^2): the
+// 1e-4 margin exceeds the few float roundings of either side, so the test
+// never rejects a position whose exact float32 S exceeds t.
+//
+// Shared memory, regions centred on the tile ("Rk" = tile grown by k px):
+//   sJ (R6) J, clamped at load; sCM (R2 rows x R4 columns) column medians,
+//   aliased by sS (R4) S; sM3 (R5) med3; sN, sSp (R2) N and S' (-inf unless
+//   computed); byte maps: flags (R2: bit 0 S+ > sigclip, bit 1 S+ > sigfrac*
+//   sigclip), near (R2), needS (R4), needM3 (R5), g1 (R1), g2 (tile); three
+//   index lists and their counters.
 template <int TW, int TH>
 struct DetectLayout {
   static constexpr int JW = TW + 12, JH = TH + 12;
-  static constexpr int W4 = TW + 8, H4 = TH + 8;
   static constexpr int W5 = TW + 10, H5 = TH + 10;
+  static constexpr int W4 = TW + 8, H4 = TH + 8;
   static constexpr int W2 = TW + 4, H2 = TH + 4;
   static constexpr int W1 = TW + 2, H1 = TH + 2;
-  static constexpr int oJ = 0;
+  static constexpr int oJ = 0;                               // floats
   static constexpr int oS = oJ + JW * JH;
-  static constexpr int oM3 = oS + W4 * H4;
+  static constexpr int oM3 = oS + imax(W4 * H4, H2 * W4);
   static constexpr int oN = oM3 + W5 * H5;
   static constexpr int oSp = oN + W2 * H2;
-  static constexpr int nFloats = oSp + W2 * H2;
-  static constexpr int oC = nFloats * 4;          // bytes
-  static constexpr int oG1 = oC + W2 * H2;
-  static constexpr size_t bytes = size_t(oG1 + W1 * H1 + 15) / 16 * 16;
+  static constexpr int nF = oSp + W2 * H2;
+  static constexpr int bFlag = round16(nF * 4);              // bytes
+  static constexpr int bNear = bFlag + W2 * H2;
+  static constexpr int bNeedS = bNear + W2 * H2;
+  static constexpr int bNeedM3 = bNeedS + W4 * H4;
+  static constexpr int bG1 = bNeedM3 + W5 * H5;
+  static constexpr int bG2 = bG1 + W1 * H1;
+  static constexpr int bEnd = round16(bG2 + TW * TH);
+  static constexpr int oL0 = bEnd;                           // uint16 lists
+  static constexpr int oL1 = oL0 + round16(W5 * H5 * 2);
+  static constexpr int oL2 = oL1 + round16(W2 * H2 * 2);
+  static constexpr int oCnt = oL2 + round16(W2 * H2 * 2);    // 8 ints
+  static constexpr size_t bytes = size_t(oCnt + 32);
 };
 
 template <int TW, int TH, bool kMaps>
-__device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, long long tile,
-                            char* smem) {
+__device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, long long tile, char* smem) {
   using L = DetectLayout<TW, TH>;
   float* sJ = reinterpret_cast<float*>(smem) + L::oJ;
   float* sS = reinterpret_cast<float*>(smem) + L::oS;
+  float* sCM = sS;  // column medians; dead before S is written
   float* sM3 = reinterpret_cast<float*>(smem) + L::oM3;
   float* sN = reinterpret_cast<float*>(smem) + L::oN;
   float* sSp = reinterpret_cast<float*>(smem) + L::oSp;
-  uint8_t* sC = reinterpret_cast<uint8_t*>(smem) + L::oC;
-  uint8_t* sG1 = reinterpret_cast<uint8_t*>(smem) + L::oG1;
+  uint8_t* bFlag = reinterpret_cast<uint8_t*>(smem) + L::bFlag;
+  uint8_t* bNear = reinterpret_cast<uint8_t*>(smem) + L::bNear;
+  uint8_t* bNeedS = reinterpret_cast<uint8_t*>(smem) + L::bNeedS;
+  uint8_t* bNeedM3 = reinterpret_cast<uint8_t*>(smem) + L::bNeedM3;
+  uint8_t* bG1 = reinterpret_cast<uint8_t*>(smem) + L::bG1;
+  uint8_t* bG2 = reinterpret_cast<uint8_t*>(smem) + L::bG2;
+  uint16_t* L0 = reinterpret_cast<uint16_t*>(smem + L::oL0);
+  uint16_t* L1 = reinterpret_cast<uint16_t*>(smem + L::oL1);
+  uint16_t* L2 = reinterpret_cast<uint16_t*>(smem + L::oL2);
+  int* cnt = reinterpret_cast<int*>(smem + L::oCnt);  // 0 needS, 1 hot, 2 needS', 3 needM3, 4 cand tests
 
   const int w = f.w, h = f.h;
   const int ty = int(tile / f.tiles_x), tx = int(tile - (long long)ty * f.tiles_x);
   const int x0 = tx * TW, y0 = ty * TH;
   const float* __restrict__ J = iter_src(f, k, niter);
-  const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn);
+  const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
   const float sigclip = p.sigclip, siglow = __fmul_rn(p.sigfrac, p.sigclip), objlim = p.objlim;
+  const float chot = 4.f * sigclip * sigclip * 0.9999f, clow = 4.f * siglow * siglow * 0.9999f;
   const bool edge = (x0 - 6 < 0) || (y0 - 6 < 0) || (x0 + TW + 6 > w) || (y0 + TH + 6 > h);
   const size_t npix = size_t(w) * size_t(h);
+  const int tid = threadIdx.x;
 
-  // 1. J over R6, replicate edge
-  for (int i = threadIdx.x; i < L::JW * L::JH; i += kThreads) {
+  // P0: clear byte maps and counters, S' = -inf, load J over R6 (replicate edge)
+  for (int i = tid; i < (L::bEnd - L::bFlag) / 16; i += kThreads)
+    reinterpret_cast<uint4*>(smem + L::bFlag)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (tid < 8) cnt[tid] = 0;
+  for (int i = tid; i < L::W2 * L::H2; i += kThreads) sSp[i] = -INFINITY;
+  for (int i = tid; i < L::JW * L::JH; i += kThreads) {
     const int iy = i / L::JW, ix = i - iy * L::JW;
     const int gx = clampi(x0 - 6 + ix, 0, w - 1), gy = clampi(y0 - 6 + iy, 0, h - 1);
     sJ[i] = __ldg(J + size_t(gy) * w + gx);
   }
   __syncthreads();
 
-  // 2. (a)+(b) over R4: m5, N, L+, S; med3 over R5
-  for (int i = threadIdx.x; i < L::W4 * L::H4; i += kThreads) {
+  // P1: medians of the 5 vertical values of every column of R4, rows of R2
+  for (int i = tid; i < L::H2 * L::W4; i += kThreads) {
     const int iy = i / L::W4, ix = i - iy * L::W4;
-    const int gx = x0 - 4 + ix, gy = y0 - 4 + iy;
-    if (gx < 0 || gx >= w || gy < 0 || gy >= h) continue;
+    float v[5];
+#pragma unroll
+    for (int d = 0; d < 5; ++d) v[d] = sJ[(iy + 2 + d) * L::JW + ix + 2];
+    sCM[i] = sel_med5(v);
+  }
+  __syncthreads();
+
+  // P2: L+ and the bound S+ on R2; list the positions with S+ > sigclip
+  for (int i0 = 0; i0 < L::W2 * L::H2; i0 += kThreads) {
+    const int i = i0 + tid;
+    bool hot = false;
+    if (i < L::W2 * L::H2) {
+      const int iy = i / L::W2, ix = i - iy * L::W2;
+      const int gx = x0 - 2 + ix, gy = y0 - 2 + iy;
+      if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
+        bool act;
+        if (kMaps) {
+          hot = act = true;
+        } else {
+          const float* c = sJ + (iy + 4) * L::JW + ix + 4;
+          const float lp = lplus(c[0], c[-L::JW], c[L::JW], c[-1], c[1]);
+          const float* cm = sCM + iy * L::W4 + ix;
+          const float mlow = min3f(min3f(cm[0], cm[1], cm[2]), cm[3], cm[4]);
+          const float den = gain * (mlow > 0.f ? mlow : 0.f) + rn2;
+          const float lhs = lp * lp * g2;
+          hot = lhs > chot * den;
+          act = lhs > clow * den;
+        }
+        bFlag[i] = uint8_t((hot ? 1 : 0) | (act ? 2 : 0));
+      }
+    }
+    push_if(hot, i, L1, &cnt[1]);
+  }
+  __syncthreads();
+
+  // P3: mark R2 positions within 2 px of a hot position
+  if (!kMaps) {
+    for (int j = tid; j < cnt[1]; j += kThreads) {
+      const int i = L1[j];
+      const int iy = i / L::W2, ix = i - iy * L::W2;
+      for (int dy = -2; dy <= 2; ++dy) {
+        const int yy = iy + dy;
+        if (yy < 0 || yy >= L::H2) continue;
+#pragma unroll
+        for (int dx = -2; dx <= 2; ++dx) {
+          const int xx = ix + dx;
+          if (xx >= 0 && xx < L::W2) bNear[yy * L::W2 + xx] = 1;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // P4: positions whose S' can matter; mark their 5x5 neighbourhoods (in R4)
+  for (int i0 = 0; i0 < L::W2 * L::H2; i0 += kThreads) {
+    const int i = i0 + tid;
+    bool need = false;
+    if (i < L::W2 * L::H2) {
+      need = (bFlag[i] & 2) && (kMaps || bNear[i]);
+      if (need && !kMaps) {
+        const int iy = i / L::W2, ix = i - iy * L::W2;
+#pragma unroll
+        for (int dy = 0; dy < 5; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 5; ++dx) bNeedS[(iy + dy) * L::W4 + ix + dx] = 1;
+      }
+    }
+    push_if(need, i, L2, &cnt[2]);
+  }
+  __syncthreads();
+
+  // P5: list the in-frame R4 positions that need the exact S
+  for (int i0 = 0; i0 < L::W4 * L::H4; i0 += kThreads) {
+    const int i = i0 + tid;
+    bool need = false;
+    if (i < L::W4 * L::H4) {
+      const int iy = i / L::W4, ix = i - iy * L::W4;
+      const int gx = x0 - 4 + ix, gy = y0 - 4 + iy;
+      need = gx >= 0 && gx < w && gy >= 0 && gy < h && (kMaps || bNeedS[i]);
+    }
+    push_if(need, i, L0, &cnt[0]);
+  }
+  __syncthreads();
+
+  // P6: (a)+(b) at the listed positions: m5, N, L+, S
+  for (int j = tid; j < cnt[0]; j += kThreads) {
+    const int i = L0[j];
+    const int iy = i / L::W4, ix = i - iy * L::W4;
     const int cx = ix + 2, cy = iy + 2;  // centre in sJ
     float v[25];
 #pragma unroll
@@ -166,18 +309,73 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
     sS[i] = s;
     if (ix >= 2 && ix < L::W4 - 2 && iy >= 2 && iy < L::H4 - 2) sN[(iy - 2) * L::W2 + ix - 2] = n;
     if (kMaps && ix >= 4 && ix < 4 + TW && iy >= 4 && iy < 4 + TH) {
-      const size_t o = size_t(gy) * w + gx;
+      const size_t o = size_t(y0 - 4 + iy) * w + (x0 - 4 + ix);
       f.maps[0 * npix + o] = m5f;
       f.maps[1 * npix + o] = lp;
       f.maps[2 * npix + o] = n;
       f.maps[3 * npix + o] = s;
     }
   }
-  for (int i = threadIdx.x; i < L::W5 * L::H5; i += kThreads) {
+  __syncthreads();
+  if (edge) {  // replicate the frame-edge S into out-of-frame entries
+    for (int i = tid; i < L::W4 * L::H4; i += kThreads) {
+      const int iy = i / L::W4, ix = i - iy * L::W4;
+      const int gx = x0 - 4 + ix, gy = y0 - 4 + iy;
+      if (gx >= 0 && gx < w && gy >= 0 && gy < h) continue;
+      const int sx = clampi(gx, 0, w - 1) - (x0 - 4), sy = clampi(gy, 0, h - 1) - (y0 - 4);
+      sS[i] = sS[sy * L::W4 + sx];
+    }
+    __syncthreads();
+  }
+
+  // P7: S' = S - med5(S) at the listed R2 positions; candidates to test; their 7x7 med3 needs
+  for (int j0 = 0; j0 < cnt[2]; j0 += kThreads) {
+    const int j = j0 + tid;
+    bool test = false;
+    int i = 0;
+    if (j < cnt[2]) {
+      i = L2[j];
+      const int iy = i / L::W2, ix = i - iy * L::W2;
+      const int cx = ix + 2, cy = iy + 2;  // centre in sS
+      float v[25];
+#pragma unroll
+      for (int dy = 0; dy < 5; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 5; ++dx) v[dy * 5 + dx] = sS[(cy - 2 + dy) * L::W4 + cx - 2 + dx];
+      const float sp = __fsub_rn(sS[cy * L::W4 + cx], sel_med25(v));
+      sSp[i] = sp;
+      test = sp > sigclip;
+      if (test && !kMaps) {
+#pragma unroll
+        for (int dy = 0; dy < 7; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 7; ++dx) bNeedM3[(iy + dy) * L::W5 + ix + dx] = 1;
+      }
+      if (kMaps && ix >= 2 && ix < 2 + TW && iy >= 2 && iy < 2 + TH)
+        f.maps[4 * npix + size_t(y0 - 2 + iy) * w + (x0 - 2 + ix)] = sp;
+    }
+    push_if(test, i, L1, &cnt[4]);
+  }
+  __syncthreads();
+
+  // P8: list the in-frame R5 positions that need med3
+  for (int i0 = 0; i0 < L::W5 * L::H5; i0 += kThreads) {
+    const int i = i0 + tid;
+    bool need = false;
+    if (i < L::W5 * L::H5) {
+      const int iy = i / L::W5, ix = i - iy * L::W5;
+      const int gx = x0 - 5 + ix, gy = y0 - 5 + iy;
+      need = gx >= 0 && gx < w && gy >= 0 && gy < h && (kMaps || bNeedM3[i]);
+    }
+    push_if(need, i, L0, &cnt[3]);
+  }
+  __syncthreads();
+
+  // P9: med3 at the listed positions
+  for (int j = tid; j < cnt[3]; j += kThreads) {
+    const int i = L0[j];
     const int iy = i / L::W5, ix = i - iy * L::W5;
-    const int gx = x0 - 5 + ix, gy = y0 - 5 + iy;
-    if (gx < 0 || gx >= w || gy < 0 || gy >= h) continue;
-    const int cx = ix + 1, cy = iy + 1;
+    const int cx = ix + 1, cy = iy + 1;  // centre in sJ
     float v[9];
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy)
@@ -185,18 +383,12 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
       for (int dx = 0; dx < 3; ++dx) v[dy * 3 + dx] = sJ[(cy - 1 + dy) * L::JW + cx - 1 + dx];
     const float m3 = sel_med9(v);
     sM3[i] = m3;
-    if (kMaps && ix >= 5 && ix < 5 + TW && iy >= 5 && iy < 5 + TH) f.maps[5 * npix + size_t(gy) * w + gx] = m3;
+    if (kMaps && ix >= 5 && ix < 5 + TW && iy >= 5 && iy < 5 + TH)
+      f.maps[5 * npix + size_t(y0 - 5 + iy) * w + (x0 - 5 + ix)] = m3;
   }
   __syncthreads();
-  if (edge) {  // replicate frame-edge values of S and m3 into their out-of-frame entries
-    for (int i = threadIdx.x; i < L::W4 * L::H4; i += kThreads) {
-      const int iy = i / L::W4, ix = i - iy * L::W4;
-      const int gx = x0 - 4 + ix, gy = y0 - 4 + iy;
-      if (gx >= 0 && gx < w && gy >= 0 && gy < h) continue;
-      const int sx = clampi(gx, 0, w - 1) - (x0 - 4), sy = clampi(gy, 0, h - 1) - (y0 - 4);
-      sS[i] = sS[sy * L::W4 + sx];
-    }
-    for (int i = threadIdx.x; i < L::W5 * L::H5; i += kThreads) {
+  if (edge) {
+    for (int i = tid; i < L::W5 * L::H5; i += kThreads) {
       const int iy = i / L::W5, ix = i - iy * L::W5;
       const int gx = x0 - 5 + ix, gy = y0 - 5 + iy;
       if (gx >= 0 && gx < w && gy >= 0 && gy < h) continue;
@@ -206,84 +398,67 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
     __syncthreads();
   }
 
-  // 3. (b)+(c)+(d) over R2: S' = S - med5(S); candidates with the lazy fine structure
-  for (int i = threadIdx.x; i < L::W2 * L::H2; i += kThreads) {
+  // P10: (c)+(d) at the candidate tests: F, the objlim statistic, and for each
+  // candidate the two growths it causes inside the tile
+  for (int j = tid; j < cnt[4]; j += kThreads) {
+    const int i = L1[j];
     const int iy = i / L::W2, ix = i - iy * L::W2;
-    const int gx = x0 - 2 + ix, gy = y0 - 2 + iy;
-    float sp = -INFINITY;
-    uint8_t cand = 0;
-    if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
-      const int cx = ix + 2, cy = iy + 2;  // centre in sS
-      float v[25];
+    const int mx = ix + 3, my = iy + 3;  // centre in sM3
+    float u[49];
 #pragma unroll
-      for (int dy = 0; dy < 5; ++dy)
+    for (int dy = 0; dy < 7; ++dy)
 #pragma unroll
-        for (int dx = 0; dx < 5; ++dx) v[dy * 5 + dx] = sS[(cy - 2 + dy) * L::W4 + cx - 2 + dx];
-      const float s = sS[cy * L::W4 + cx];
-      sp = __fsub_rn(s, sel_med25(v));
-      float fval = NAN, rval = NAN;
-      if (sp > sigclip) {
-        const int mx = ix + 3, my = iy + 3;  // centre in sM3
-        float u[49];
-#pragma unroll
-        for (int dy = 0; dy < 7; ++dy)
-#pragma unroll
-          for (int dx = 0; dx < 7; ++dx) u[dy * 7 + dx] = sM3[(my - 3 + dy) * L::W5 + mx - 3 + dx];
-        fval = __fsub_rn(sM3[my * L::W5 + mx], sel_med49(u));
-        const float fn = fmaxf(__fdiv_rn(fval, sN[i]), 0.01f);
-        rval = (p.objlim_form == 1) ? __fdiv_rn(__fmul_rn(2.f, s), fn) : __fdiv_rn(sp, fn);
-        cand = rval > objlim ? 1 : 0;
-      }
-      if (kMaps && ix >= 2 && ix < 2 + TW && iy >= 2 && iy < 2 + TH) {
-        const size_t o = size_t(gy) * w + gx;
-        f.maps[4 * npix + o] = sp;
-        f.maps[6 * npix + o] = fval;
-        f.maps[7 * npix + o] = rval;
-        f.maps[8 * npix + o] = float(cand);
-      }
+      for (int dx = 0; dx < 7; ++dx) u[dy * 7 + dx] = sM3[(my - 3 + dy) * L::W5 + mx - 3 + dx];
+    const float fval = __fsub_rn(sM3[my * L::W5 + mx], sel_med49(u));
+    const float fn = fmaxf(__fdiv_rn(fval, sN[i]), 0.01f);
+    const float sp = sSp[i];
+    const float rval = (p.objlim_form == 1) ? __fdiv_rn(__fmul_rn(2.f, sS[(iy + 2) * L::W4 + ix + 2]), fn)
+                                            : __fdiv_rn(sp, fn);
+    const bool cand = rval > objlim;
+    if (kMaps && ix >= 2 && ix < 2 + TW && iy >= 2 && iy < 2 + TH) {
+      const size_t o = size_t(y0 - 2 + iy) * w + (x0 - 2 + ix);
+      f.maps[6 * npix + o] = fval;
+      f.maps[7 * npix + o] = rval;
+      f.maps[8 * npix + o] = cand ? 1.f : 0.f;
     }
-    sSp[i] = sp;
-    sC[i] = cand;
-  }
-  __syncthreads();
-
-  // 4. first growth over R1: 3x3 dilation of the candidates, S' > sigclip
-  for (int i = threadIdx.x; i < L::W1 * L::H1; i += kThreads) {
-    const int iy = i / L::W1, ix = i - iy * L::W1;
-    const int cx = ix + 1, cy = iy + 1;  // centre in R2
-    uint8_t any = 0;
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) any |= sC[(cy + dy) * L::W2 + cx + dx];
-    const uint8_t g1 = (any && sSp[cy * L::W2 + cx] > sigclip) ? 1 : 0;
-    sG1[i] = g1;
-    if (kMaps && ix >= 1 && ix < 1 + TW && iy >= 1 && iy < 1 + TH) {
-      const int gx = x0 - 1 + ix, gy = y0 - 1 + iy;
-      if (gx < w && gy < h) f.maps[9 * npix + size_t(gy) * w + gx] = float(g1);
+    if (!cand) continue;
+    for (int ey = -1; ey <= 1; ++ey) {
+      const int qy = iy + ey;  // first-growth position (R2 coordinates)
+      if (qy < 1 || qy > L::H2 - 2) continue;
+      for (int ex = -1; ex <= 1; ++ex) {
+        const int qx = ix + ex;
+        if (qx < 1 || qx > L::W2 - 2) continue;
+        if (!(sSp[qy * L::W2 + qx] > sigclip)) continue;
+        if (kMaps) bG1[(qy - 1) * L::W1 + qx - 1] = 1;
+        for (int ry = qy - 1; ry <= qy + 1; ++ry) {
+          if (ry < 2 || ry >= 2 + TH) continue;
+          for (int rx = qx - 1; rx <= qx + 1; ++rx) {
+            if (rx < 2 || rx >= 2 + TW) continue;
+            if (sSp[ry * L::W2 + rx] > siglow) bG2[(ry - 2) * TW + rx - 2] = 1;
+          }
+        }
+      }
     }
   }
   __syncthreads();
 
-  // 5. second growth on the tile, one 32-pixel mask word per warp step
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // P11: the tile's flag words (one warp per 32-pixel word)
+  const int lane = tid & 31, warp = tid >> 5;
   constexpr int kWordsPerRow = TW / 32;
   unsigned int new_flags = 0;
   for (int wi = warp; wi < kWordsPerRow * TH; wi += kThreads / 32) {
     const int r = wi / kWordsPerRow, wc = wi - r * kWordsPerRow;
     const int lx = wc * 32 + lane, gx = x0 + lx, gy = y0 + r;
-    bool g2 = false;
+    bool g2v = false;
     if (gx < w && gy < h) {
-      const int cx = lx + 1, cy = r + 1;  // centre in R1
-      uint8_t any = 0;
-#pragma unroll
-      for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) any |= sG1[(cy + dy) * L::W1 + cx + dx];
-      g2 = any && sSp[(r + 2) * L::W2 + lx + 2] > siglow;
-      if (kMaps) f.maps[10 * npix + size_t(gy) * w + gx] = g2 ? 1.f : 0.f;
+      g2v = bG2[r * TW + lx] != 0;
+      if (kMaps) {
+        const size_t o = size_t(gy) * w + gx;
+        f.maps[9 * npix + o] = bG1[(r + 1) * L::W1 + lx + 1] ? 1.f : 0.f;
+        f.maps[10 * npix + o] = g2v ? 1.f : 0.f;
+      }
     }
-    const unsigned int word = __ballot_sync(0xffffffffu, g2);
+    const unsigned int word = __ballot_sync(0xffffffffu, g2v);
     if (lane == 0 && gy < h && (x0 >> 5) + wc < f.wpr) {
       uint32_t* wp = f.bits + size_t(gy) * f.wpr + (x0 >> 5) + wc;
       const uint32_t prev = *wp;
@@ -315,10 +490,14 @@ __global__ void __launch_bounds__(kThreads) detect_kernel(const Frame* __restric
 // entries are set to -inf and the other 12 - floor(n/2) to +inf: the median
 // (element 12) is then element 12 - a = ceil(n/2) - 1 of the unflagged values.
 // n = 0 falls back to the floored 5x5 median of the window.
+// A tile without flagged pixels only copies (dense iterations) or is skipped.
 template <int RW, int RH>
 struct ReplaceLayout {
   static constexpr int W = RW + 4, H = RH + 4;
-  static constexpr size_t bytes = size_t(W * H) * 4 + size_t(W * H);
+  static constexpr int oF = round16(W * H * 4);
+  static constexpr int oL = oF + round16(W * H);
+  static constexpr int oCnt = oL + round16(RW * RH * 2);
+  static constexpr size_t bytes = size_t(oCnt + 16);
 };
 
 __device__ __forceinline__ bool flag_at(const Frame& f, int x, int y) {
@@ -328,16 +507,44 @@ __device__ __forceinline__ bool flag_at(const Frame& f, int x, int y) {
 template <int RW, int RH>
 __device__ void replace_tile(const Frame& f, int k, int niter, int dense, long long tile, char* smem) {
   using L = ReplaceLayout<RW, RH>;
+  static_assert(RW % 32 == 0, "tile width must be whole flag words");
   float* sJ = reinterpret_cast<float*>(smem);
-  uint8_t* sF = reinterpret_cast<uint8_t*>(smem) + L::W * L::H * 4;
+  uint8_t* sF = reinterpret_cast<uint8_t*>(smem + L::oF);
+  uint16_t* list = reinterpret_cast<uint16_t*>(smem + L::oL);
+  int* cnt = reinterpret_cast<int*>(smem + L::oCnt);
   const int w = f.w, h = f.h;
   const int ty = int(tile / f.rtiles_x), tx = int(tile - (long long)ty * f.rtiles_x);
   const int x0 = tx * RW, y0 = ty * RH;
   const float* __restrict__ J = iter_src(f, k, niter);
   float* __restrict__ D = iter_dst(f, k, niter);
   const bool last = (k == niter);
+  const int tid = threadIdx.x;
 
-  for (int i = threadIdx.x; i < L::W * L::H; i += kThreads) {
+  // any flagged pixel in the tile?
+  constexpr int kWords = RW / 32;
+  bool any = false;
+  for (int wi = tid; wi < kWords * RH; wi += kThreads) {
+    const int r = wi / kWords, wc = wi - r * kWords;
+    const int gy = y0 + r, wx = (x0 >> 5) + wc;
+    if (gy < h && wx < f.wpr) any |= f.bits[size_t(gy) * f.wpr + wx] != 0u;
+  }
+  if (tid == 0) cnt[0] = 0;
+  any = __syncthreads_or(any);
+  if (!any) {
+    if (dense || (last && f.out_mask)) {
+      for (int i = tid; i < RW * RH; i += kThreads) {
+        const int ly = i / RW, lx = i - ly * RW;
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= w || gy >= h) continue;
+        const size_t o = size_t(gy) * w + gx;
+        if (dense) D[o] = __ldg(J + o);
+        if (last && f.out_mask) f.out_mask[o] = 0;
+      }
+    }
+    return;
+  }
+
+  for (int i = tid; i < L::W * L::H; i += kThreads) {
     const int iy = i / L::W, ix = i - iy * L::W;
     const int gx = clampi(x0 - 2 + ix, 0, w - 1), gy = clampi(y0 - 2 + iy, 0, h - 1);
     sJ[i] = __ldg(J + size_t(gy) * w + gx);
@@ -345,56 +552,64 @@ __device__ void replace_tile(const Frame& f, int k, int niter, int dense, long l
   }
   __syncthreads();
 
+  for (int i0 = 0; i0 < RW * RH; i0 += kThreads) {
+    const int i = i0 + tid;
+    bool flagged = false;
+    if (i < RW * RH) {
+      const int ly = i / RW, lx = i - ly * RW;
+      const int gx = x0 + lx, gy = y0 + ly;
+      if (gx < w && gy < h) {
+        const int c = (ly + 2) * L::W + lx + 2;
+        flagged = sF[c] != 0;
+        const size_t o = size_t(gy) * w + gx;
+        if (dense && !flagged) D[o] = sJ[c];
+        if (last && f.out_mask) f.out_mask[o] = flagged ? 1 : 0;
+      }
+    }
+    push_if(flagged, i, list, cnt);
+  }
+  __syncthreads();
+
   unsigned int none_left = 0;
-  for (int i = threadIdx.x; i < RW * RH; i += kThreads) {
+  for (int j = tid; j < cnt[0]; j += kThreads) {
+    const int i = list[j];
     const int ly = i / RW, lx = i - ly * RW;
-    const int gx = x0 + lx, gy = y0 + ly;
-    if (gx >= w || gy >= h) continue;
     const int c = (ly + 2) * L::W + lx + 2;
-    const bool flagged = sF[c];
-    const size_t o = size_t(gy) * w + gx;
-    float out = sJ[c];
-    if (flagged) {
-      int n = 0;
+    int n = 0;
+#pragma unroll
+    for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+      for (int dx = -2; dx <= 2; ++dx) n += sF[c + dy * L::W + dx] ? 0 : 1;
+    float v[25];
+    float out;
+    if (n > 0) {
+      const int a = 13 - (n + 1) / 2;  // flagged entries sent to -inf
+      int seen = 0;
 #pragma unroll
       for (int dy = -2; dy <= 2; ++dy)
 #pragma unroll
-        for (int dx = -2; dx <= 2; ++dx) n += sF[c + dy * L::W + dx] ? 0 : 1;
-      float v[25];
-      if (n > 0) {
-        const int a = 13 - (n + 1) / 2;  // flagged entries sent to -inf
-        int seen = 0;
-#pragma unroll
-        for (int dy = -2; dy <= 2; ++dy)
-#pragma unroll
-          for (int dx = -2; dx <= 2; ++dx) {
-            const int q = c + dy * L::W + dx;
-            float val = sJ[q];
-            if (sF[q]) {
-              val = (seen < a) ? -INFINITY : INFINITY;
-              ++seen;
-            }
-            v[(dy + 2) * 5 + dx + 2] = val;
+        for (int dx = -2; dx <= 2; ++dx) {
+          const int q = c + dy * L::W + dx;
+          float val = sJ[q];
+          if (sF[q]) {
+            val = (seen < a) ? -INFINITY : INFINITY;
+            ++seen;
           }
-        out = sel_med25(v);
-      } else {
+          v[(dy + 2) * 5 + dx + 2] = val;
+        }
+      out = sel_med25(v);
+    } else {
 #pragma unroll
-        for (int dy = -2; dy <= 2; ++dy)
+      for (int dy = -2; dy <= 2; ++dy)
 #pragma unroll
-          for (int dx = -2; dx <= 2; ++dx) v[(dy + 2) * 5 + dx + 2] = sJ[c + dy * L::W + dx];
-        out = floor_m5(sel_med25(v));
-        ++none_left;
-      }
-      D[o] = out;
-    } else if (dense) {
-      D[o] = out;
+        for (int dx = -2; dx <= 2; ++dx) v[(dy + 2) * 5 + dx + 2] = sJ[c + dy * L::W + dx];
+      out = floor_m5(sel_med25(v));
+      ++none_left;
     }
-    if (last && f.out_mask) f.out_mask[o] = flagged ? 1 : 0;
+    D[size_t(y0 + ly) * w + x0 + lx] = out;
   }
-  // warp-reduce the count of flagged pixels with no unflagged neighbour
   for (int off = 16; off; off >>= 1) none_left += __shfl_xor_sync(0xffffffffu, none_left, off);
-  if ((threadIdx.x & 31) == 0 && none_left)
-    atomicAdd(f.counters + 2 * (k - 1) + 1, (unsigned long long)none_left);
+  if ((tid & 31) == 0 && none_left) atomicAdd(f.counters + 2 * (k - 1) + 1, (unsigned long long)none_left);
 }
 
 template <int RW, int RH>
