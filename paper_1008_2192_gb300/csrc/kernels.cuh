@@ -351,8 +351,11 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
 #pragma unroll
           for (int dx = 0; dx < 7; ++dx) bNeedM3[(iy + dy) * L::W5 + ix + dx] = 1;
       }
-      if (kMaps && ix >= 2 && ix < 2 + TW && iy >= 2 && iy < 2 + TH)
-        f.maps[4 * npix + size_t(y0 - 2 + iy) * w + (x0 - 2 + ix)] = sp;
+      if (kMaps && ix >= 2 && ix < 2 + TW && iy >= 2 && iy < 2 + TH) {
+        const size_t o = size_t(y0 - 2 + iy) * w + (x0 - 2 + ix);
+        f.maps[4 * npix + o] = sp;
+        f.maps[8 * npix + o] = 0.f;  // overwritten below where the candidate test runs
+      }
     }
     push_if(test, i, L1, &cnt[4]);
   }
