@@ -106,8 +106,51 @@ __device__ __forceinline__ void push_if(bool pred, int idx, uint16_t* list, int*
   if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = uint16_t(idx);
 }
 
-constexpr int round16(int b) { return (b + 15) / 16 * 16; }
-constexpr int imax(int a, int b) { return a > b ? a : b; }
+__host__ __device__ constexpr int round16(int b) { return (b + 15) / 16 * 16; }
+__host__ __device__ constexpr int imax(int a, int b) { return a > b ? a : b; }
+
+// --------------------------------------------------------------------------------------------
+// Bit-row maps: one bit per pixel, word j of a row covers x0 - 32 + 32j ... + 31,
+// rows are the rows of R6 (y0 - 6 ...). x0 is a multiple of 32.
+
+// bits [lo, hi) of a word, clipped to [0, 32)
+__device__ __forceinline__ uint32_t bits_between(int lo, int hi) {
+  lo = max(lo, 0);
+  hi = min(hi, 32);
+  if (lo >= hi) return 0u;
+  const uint32_t m = (hi == 32) ? 0xffffffffu : ((1u << hi) - 1u);
+  return m & ~((1u << lo) - 1u);
+}
+
+// Exclusive prefix sum over the block (one value per thread); ws holds kThreads/32 + 1 ints.
+__device__ __forceinline__ int block_excl_scan(int v, int* ws, int& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kWarps = kThreads / 32;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int s = lane < kWarps ? ws[lane] : 0;
+    int inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane < kWarps) ws[lane] = inc - s;
+    if (lane == kWarps - 1) ws[kWarps] = inc;
+  }
+  __syncthreads();
+  total = ws[kWarps];
+  const int r = ws[warp] + x - v;
+  __syncthreads();
+  return r;
+}
 
 // --------------------------------------------------------------------------------------------
 // detect: stages (a)-(d) for one output tile of TW x TH pixels, computed only
@@ -127,13 +170,13 @@ constexpr int imax(int a, int b) { return a > b ? a : b; }
 // S+ > t is evaluated as L+^2 gain^2 > 4 t^2 (1 - 1e-4) (gain m + rn^2): the
 // 1e-4 margin exceeds the few float roundings of either side, so the test
 // never rejects a position whose exact float32 S exceeds t.
+// The sets are bit-row maps; dilations are word shifts and ORs, and the work
+// lists are read off the set bits with one block-wide prefix sum.
 //
 // Shared memory, regions centred on the tile ("Rk" = tile grown by k px):
 //   sJ (R6) J, clamped at load; sCM (R2 rows x R4 columns) column medians,
 //   aliased by sS (R4) S; sM3 (R5) med3; sN, sSp (R2) N and S' (-inf unless
-//   computed); byte maps: flags (R2: bit 0 S+ > sigclip, bit 1 S+ > sigfrac*
-//   sigclip), near (R2), needS (R4), needM3 (R5), g1 (R1), g2 (tile); three
-//   index lists and their counters.
+//   computed); 9 bit maps; three position lists and small counters.
 template <int TW, int TH>
 struct DetectLayout {
   static constexpr int JW = TW + 12, JH = TH + 12;
@@ -141,25 +184,98 @@ struct DetectLayout {
   static constexpr int W4 = TW + 8, H4 = TH + 8;
   static constexpr int W2 = TW + 4, H2 = TH + 4;
   static constexpr int W1 = TW + 2, H1 = TH + 2;
-  static constexpr int oJ = 0;                               // floats
+  static constexpr int NW = TW / 32 + 2;  // words per bit-map row
+  static constexpr int MW = NW * JH;      // words per bit map
+  static_assert(TW % 32 == 0 && 32 * NW <= 256 && JH <= 255, "list entries pack (row << 8 | bit column)");
+  static_assert(MW % 4 == 0, "bit maps are cleared as 16-byte vectors");
+  static constexpr int oJ = 0;  // floats
   static constexpr int oS = oJ + JW * JH;
   static constexpr int oM3 = oS + imax(W4 * H4, H2 * W4);
   static constexpr int oN = oM3 + W5 * H5;
   static constexpr int oSp = oN + W2 * H2;
   static constexpr int nF = oSp + W2 * H2;
-  static constexpr int bFlag = round16(nF * 4);              // bytes
-  static constexpr int bNear = bFlag + W2 * H2;
-  static constexpr int bNeedS = bNear + W2 * H2;
-  static constexpr int bNeedM3 = bNeedS + W4 * H4;
-  static constexpr int bG1 = bNeedM3 + W5 * H5;
-  static constexpr int bG2 = bG1 + W1 * H1;
-  static constexpr int bEnd = round16(bG2 + TW * TH);
-  static constexpr int oL0 = bEnd;                           // uint16 lists
+  static constexpr int kMaps = 9;  // hot, act, tmp, needS', needS, test, needM3, g1, g2
+  static constexpr int oBits = round16(nF * 4);  // bytes
+  static constexpr int oL0 = round16(oBits + kMaps * MW * 4);
   static constexpr int oL1 = oL0 + round16(W5 * H5 * 2);
   static constexpr int oL2 = oL1 + round16(W2 * H2 * 2);
-  static constexpr int oCnt = oL2 + round16(W2 * H2 * 2);    // 8 ints
-  static constexpr size_t bytes = size_t(oCnt + 32);
+  static constexpr int oCnt = oL2 + round16(W2 * H2 * 2);  // 16 ints: counters + scan scratch
+  static constexpr size_t bytes = size_t(oCnt + 16 * 4);
 };
+
+// positions with a set bit in `map` -> list entries (row << 8 | bit column); returns the count
+template <int NW, int MW>
+__device__ __forceinline__ int bits_to_list(const uint32_t* map, uint16_t* list, int* ws) {
+  constexpr int kPer = (MW + kThreads - 1) / kThreads;
+  const int t0 = threadIdx.x * kPer;
+  int c = 0;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q)
+    if (t0 + q < MW) c += __popc(map[t0 + q]);
+  int total = 0;
+  int off = block_excl_scan(c, ws, total);
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int t = t0 + q;
+    if (t >= MW) break;
+    uint32_t v = map[t];
+    const int row = t / NW, j = t - row * NW;
+    while (v) {
+      const int b = __ffs(v) - 1;
+      v &= v - 1u;
+      list[off++] = uint16_t((row << 8) | (32 * j + b));
+    }
+  }
+  return total;
+}
+
+// out = in dilated horizontally by r (each thread a word), then (after a
+// barrier) vertically by r, ANDed with region & frame of Rk (+ an optional
+// extra map). `tmp` is scratch.
+template <int TW, int TH, int R>
+__device__ __forceinline__ void dilate_map(const uint32_t* in, uint32_t* tmp, uint32_t* out, const uint32_t* and_map,
+                                           int kreg, int x0, int y0, int w, int h) {
+  using L = DetectLayout<TW, TH>;
+  for (int t = threadIdx.x; t < L::MW; t += kThreads) {
+    const int row = t / L::NW, j = t - row * L::NW;
+    const uint32_t v = in[t];
+    const uint32_t l = j > 0 ? in[t - 1] : 0u;
+    const uint32_t r = j < L::NW - 1 ? in[t + 1] : 0u;
+    uint32_t o = v;
+#pragma unroll
+    for (int d = 1; d <= R; ++d) o |= (v << d) | (l >> (32 - d)) | (v >> d) | (r << (32 - d));
+    tmp[t] = o;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < L::MW; t += kThreads) {
+    const int row = t / L::NW, j = t - row * L::NW;
+    uint32_t o = 0;
+#pragma unroll
+    for (int d = -R; d <= R; ++d) {
+      const int rr = row + d;
+      if (rr >= 0 && rr < L::JH) o |= tmp[rr * L::NW + j];
+    }
+    const int y = y0 - 6 + row;
+    const bool rowok = y >= imax(0, y0 - kreg) && y < min(h, y0 + TH + kreg);
+    const int xw = x0 - 32 + 32 * j;
+    const uint32_t m = rowok ? bits_between(imax(0, x0 - kreg) - xw, min(w, x0 + TW + kreg) - xw) : 0u;
+    out[t] = o & m & (and_map ? and_map[t] : 0xffffffffu);
+  }
+  __syncthreads();
+}
+
+// region & frame mask of Rk as a bit map (dense mode)
+template <int TW, int TH>
+__device__ __forceinline__ void region_map(uint32_t* out, int kreg, int x0, int y0, int w, int h) {
+  using L = DetectLayout<TW, TH>;
+  for (int t = threadIdx.x; t < L::MW; t += kThreads) {
+    const int row = t / L::NW, j = t - row * L::NW;
+    const int y = y0 - 6 + row;
+    const bool rowok = y >= imax(0, y0 - kreg) && y < min(h, y0 + TH + kreg);
+    const int xw = x0 - 32 + 32 * j;
+    out[t] = rowok ? bits_between(imax(0, x0 - kreg) - xw, min(w, x0 + TW + kreg) - xw) : 0u;
+  }
+}
 
 template <int TW, int TH, bool kMaps>
 __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, long long tile, char* smem) {
@@ -170,16 +286,20 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   float* sM3 = reinterpret_cast<float*>(smem) + L::oM3;
   float* sN = reinterpret_cast<float*>(smem) + L::oN;
   float* sSp = reinterpret_cast<float*>(smem) + L::oSp;
-  uint8_t* bFlag = reinterpret_cast<uint8_t*>(smem) + L::bFlag;
-  uint8_t* bNear = reinterpret_cast<uint8_t*>(smem) + L::bNear;
-  uint8_t* bNeedS = reinterpret_cast<uint8_t*>(smem) + L::bNeedS;
-  uint8_t* bNeedM3 = reinterpret_cast<uint8_t*>(smem) + L::bNeedM3;
-  uint8_t* bG1 = reinterpret_cast<uint8_t*>(smem) + L::bG1;
-  uint8_t* bG2 = reinterpret_cast<uint8_t*>(smem) + L::bG2;
+  uint32_t* bits = reinterpret_cast<uint32_t*>(smem + L::oBits);
+  uint32_t* mHot = bits + 0 * L::MW;
+  uint32_t* mAct = bits + 1 * L::MW;
+  uint32_t* mTmp = bits + 2 * L::MW;
+  uint32_t* mNeedSp = bits + 3 * L::MW;
+  uint32_t* mNeedS = bits + 4 * L::MW;
+  uint32_t* mTest = bits + 5 * L::MW;
+  uint32_t* mNeedM3 = bits + 6 * L::MW;
+  uint32_t* mG1 = bits + 7 * L::MW;
+  uint32_t* mG2 = bits + 8 * L::MW;
   uint16_t* L0 = reinterpret_cast<uint16_t*>(smem + L::oL0);
   uint16_t* L1 = reinterpret_cast<uint16_t*>(smem + L::oL1);
   uint16_t* L2 = reinterpret_cast<uint16_t*>(smem + L::oL2);
-  int* cnt = reinterpret_cast<int*>(smem + L::oCnt);  // 0 needS, 1 hot, 2 needS', 3 needM3, 4 cand tests
+  int* cnt = reinterpret_cast<int*>(smem + L::oCnt);  // [0] cand tests; [4..] scan scratch
 
   const int w = f.w, h = f.h;
   const int ty = int(tile / f.tiles_x), tx = int(tile - (long long)ty * f.tiles_x);
@@ -192,10 +312,10 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   const size_t npix = size_t(w) * size_t(h);
   const int tid = threadIdx.x;
 
-  // P0: clear byte maps and counters, S' = -inf, load J over R6 (replicate edge)
-  for (int i = tid; i < (L::bEnd - L::bFlag) / 16; i += kThreads)
-    reinterpret_cast<uint4*>(smem + L::bFlag)[i] = make_uint4(0u, 0u, 0u, 0u);
-  if (tid < 8) cnt[tid] = 0;
+  // P0: clear bit maps and counters, S' = -inf, load J over R6 (replicate edge)
+  for (int i = tid; i < L::kMaps * L::MW / 4; i += kThreads)
+    reinterpret_cast<uint4*>(bits)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (tid < 4) cnt[tid] = 0;
   for (int i = tid; i < L::W2 * L::H2; i += kThreads) sSp[i] = -INFINITY;
   for (int i = tid; i < L::JW * L::JH; i += kThreads) {
     const int iy = i / L::JW, ix = i - iy * L::JW;
@@ -204,97 +324,57 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   }
   __syncthreads();
 
-  // P1: medians of the 5 vertical values of every column of R4, rows of R2
-  for (int i = tid; i < L::H2 * L::W4; i += kThreads) {
-    const int iy = i / L::W4, ix = i - iy * L::W4;
-    float v[5];
+  if (kMaps) {
+    region_map<TW, TH>(mAct, 2, x0, y0, w, h);
+    region_map<TW, TH>(mNeedSp, 2, x0, y0, w, h);
+    region_map<TW, TH>(mNeedS, 4, x0, y0, w, h);
+    __syncthreads();
+  } else {
+    // P1: medians of the 5 vertical values of every column of R4, rows of R2
+    for (int i = tid; i < L::H2 * L::W4; i += kThreads) {
+      const int iy = i / L::W4, ix = i - iy * L::W4;
+      float v[5];
 #pragma unroll
-    for (int d = 0; d < 5; ++d) v[d] = sJ[(iy + 2 + d) * L::JW + ix + 2];
-    sCM[i] = sel_med5(v);
-  }
-  __syncthreads();
+      for (int d = 0; d < 5; ++d) v[d] = sJ[(iy + 2 + d) * L::JW + ix + 2];
+      sCM[i] = sel_med5(v);
+    }
+    __syncthreads();
 
-  // P2: L+ and the bound S+ on R2; list the positions with S+ > sigclip
-  for (int i0 = 0; i0 < L::W2 * L::H2; i0 += kThreads) {
-    const int i = i0 + tid;
-    bool hot = false;
-    if (i < L::W2 * L::H2) {
+    // P2: L+ and the bound S+ on R2 -> bits of S+ > sigclip (hot) and S+ > sigfrac*sigclip (act)
+    for (int i = tid; i < L::W2 * L::H2; i += kThreads) {
       const int iy = i / L::W2, ix = i - iy * L::W2;
       const int gx = x0 - 2 + ix, gy = y0 - 2 + iy;
-      if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
-        bool act;
-        if (kMaps) {
-          hot = act = true;
-        } else {
-          const float* c = sJ + (iy + 4) * L::JW + ix + 4;
-          const float lp = lplus(c[0], c[-L::JW], c[L::JW], c[-1], c[1]);
-          const float* cm = sCM + iy * L::W4 + ix;
-          const float mlow = min3f(min3f(cm[0], cm[1], cm[2]), cm[3], cm[4]);
-          const float den = gain * (mlow > 0.f ? mlow : 0.f) + rn2;
-          const float lhs = lp * lp * g2;
-          hot = lhs > chot * den;
-          act = lhs > clow * den;
-        }
-        bFlag[i] = uint8_t((hot ? 1 : 0) | (act ? 2 : 0));
-      }
-    }
-    push_if(hot, i, L1, &cnt[1]);
-  }
-  __syncthreads();
-
-  // P3: mark R2 positions within 2 px of a hot position
-  if (!kMaps) {
-    for (int j = tid; j < cnt[1]; j += kThreads) {
-      const int i = L1[j];
-      const int iy = i / L::W2, ix = i - iy * L::W2;
-      for (int dy = -2; dy <= 2; ++dy) {
-        const int yy = iy + dy;
-        if (yy < 0 || yy >= L::H2) continue;
-#pragma unroll
-        for (int dx = -2; dx <= 2; ++dx) {
-          const int xx = ix + dx;
-          if (xx >= 0 && xx < L::W2) bNear[yy * L::W2 + xx] = 1;
-        }
+      if (gx < 0 || gx >= w || gy < 0 || gy >= h) continue;
+      const float* c = sJ + (iy + 4) * L::JW + ix + 4;
+      const float lp = lplus(c[0], c[-L::JW], c[L::JW], c[-1], c[1]);
+      const float* cm = sCM + iy * L::W4 + ix;
+      const float mlow = min3f(min3f(cm[0], cm[1], cm[2]), cm[3], cm[4]);
+      const float den = gain * (mlow > 0.f ? mlow : 0.f) + rn2;
+      const float lhs = lp * lp * g2;
+      if (lhs > clow * den) {
+        const int xb = ix + 30, wd = (iy + 4) * L::NW + (xb >> 5);
+        const uint32_t bit = 1u << (xb & 31);
+        atomicOr(&mAct[wd], bit);
+        if (lhs > chot * den) atomicOr(&mHot[wd], bit);
       }
     }
     __syncthreads();
+
+    // needS' = dilate5(hot) & act;  needS = dilate5(needS') within R4 and the frame
+    dilate_map<TW, TH, 2>(mHot, mTmp, mNeedSp, mAct, 2, x0, y0, w, h);
+    dilate_map<TW, TH, 2>(mNeedSp, mTmp, mNeedS, nullptr, 4, x0, y0, w, h);
   }
 
-  // P4: positions whose S' can matter; mark their 5x5 neighbourhoods (in R4)
-  for (int i0 = 0; i0 < L::W2 * L::H2; i0 += kThreads) {
-    const int i = i0 + tid;
-    bool need = false;
-    if (i < L::W2 * L::H2) {
-      need = (bFlag[i] & 2) && (kMaps || bNear[i]);
-      if (need && !kMaps) {
-        const int iy = i / L::W2, ix = i - iy * L::W2;
-#pragma unroll
-        for (int dy = 0; dy < 5; ++dy)
-#pragma unroll
-          for (int dx = 0; dx < 5; ++dx) bNeedS[(iy + dy) * L::W4 + ix + dx] = 1;
-      }
-    }
-    push_if(need, i, L2, &cnt[2]);
-  }
-  __syncthreads();
-
-  // P5: list the in-frame R4 positions that need the exact S
-  for (int i0 = 0; i0 < L::W4 * L::H4; i0 += kThreads) {
-    const int i = i0 + tid;
-    bool need = false;
-    if (i < L::W4 * L::H4) {
-      const int iy = i / L::W4, ix = i - iy * L::W4;
-      const int gx = x0 - 4 + ix, gy = y0 - 4 + iy;
-      need = gx >= 0 && gx < w && gy >= 0 && gy < h && (kMaps || bNeedS[i]);
-    }
-    push_if(need, i, L0, &cnt[0]);
-  }
+  // lists: L0 <- needS (R4), L2 <- needS' (R2)
+  const int nS = bits_to_list<L::NW, L::MW>(mNeedS, L0, cnt + 4);
+  const int nSp = bits_to_list<L::NW, L::MW>(mNeedSp, L2, cnt + 4);
   __syncthreads();
 
   // P6: (a)+(b) at the listed positions: m5, N, L+, S
-  for (int j = tid; j < cnt[0]; j += kThreads) {
-    const int i = L0[j];
-    const int iy = i / L::W4, ix = i - iy * L::W4;
+  for (int j = tid; j < nS; j += kThreads) {
+    const int e = L0[j];
+    const int iy = (e >> 8) - 2, ix = (e & 255) - 28;  // R4 coordinates
+    const int i = iy * L::W4 + ix;
     const int cx = ix + 2, cy = iy + 2;  // centre in sJ
     float v[25];
 #pragma unroll
@@ -328,14 +408,15 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
     __syncthreads();
   }
 
-  // P7: S' = S - med5(S) at the listed R2 positions; candidates to test; their 7x7 med3 needs
-  for (int j0 = 0; j0 < cnt[2]; j0 += kThreads) {
+  // P7: S' = S - med5(S) at the listed R2 positions; list the candidate tests (S' > sigclip)
+  for (int j0 = 0; j0 < nSp; j0 += kThreads) {
     const int j = j0 + tid;
     bool test = false;
     int i = 0;
-    if (j < cnt[2]) {
-      i = L2[j];
-      const int iy = i / L::W2, ix = i - iy * L::W2;
+    if (j < nSp) {
+      const int e = L2[j];
+      const int iy = (e >> 8) - 4, ix = (e & 255) - 30;  // R2 coordinates
+      i = iy * L::W2 + ix;
       const int cx = ix + 2, cy = iy + 2;  // centre in sS
       float v[25];
 #pragma unroll
@@ -345,47 +426,39 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
       const float sp = __fsub_rn(sS[cy * L::W4 + cx], sel_med25(v));
       sSp[i] = sp;
       test = sp > sigclip;
-      if (test && !kMaps) {
-#pragma unroll
-        for (int dy = 0; dy < 7; ++dy)
-#pragma unroll
-          for (int dx = 0; dx < 7; ++dx) bNeedM3[(iy + dy) * L::W5 + ix + dx] = 1;
-      }
+      if (test) atomicOr(&mTest[(e >> 8) * L::NW + ((e & 255) >> 5)], 1u << (e & 31));
       if (kMaps && ix >= 2 && ix < 2 + TW && iy >= 2 && iy < 2 + TH) {
         const size_t o = size_t(y0 - 2 + iy) * w + (x0 - 2 + ix);
         f.maps[4 * npix + o] = sp;
         f.maps[8 * npix + o] = 0.f;  // overwritten below where the candidate test runs
       }
     }
-    push_if(test, i, L1, &cnt[4]);
+    push_if(test, i, L1, &cnt[0]);
   }
   __syncthreads();
 
-  // P8: list the in-frame R5 positions that need med3
-  for (int i0 = 0; i0 < L::W5 * L::H5; i0 += kThreads) {
-    const int i = i0 + tid;
-    bool need = false;
-    if (i < L::W5 * L::H5) {
-      const int iy = i / L::W5, ix = i - iy * L::W5;
-      const int gx = x0 - 5 + ix, gy = y0 - 5 + iy;
-      need = gx >= 0 && gx < w && gy >= 0 && gy < h && (kMaps || bNeedM3[i]);
-    }
-    push_if(need, i, L0, &cnt[3]);
+  // needM3 = dilate7(test) within R5 and the frame; list it
+  if (kMaps) {
+    region_map<TW, TH>(mNeedM3, 5, x0, y0, w, h);
+    __syncthreads();
+  } else {
+    dilate_map<TW, TH, 3>(mTest, mTmp, mNeedM3, nullptr, 5, x0, y0, w, h);
   }
+  const int nM3 = bits_to_list<L::NW, L::MW>(mNeedM3, L0, cnt + 4);
   __syncthreads();
 
   // P9: med3 at the listed positions
-  for (int j = tid; j < cnt[3]; j += kThreads) {
-    const int i = L0[j];
-    const int iy = i / L::W5, ix = i - iy * L::W5;
-    const int cx = ix + 1, cy = iy + 1;  // centre in sJ
+  for (int j = tid; j < nM3; j += kThreads) {
+    const int e = L0[j];
+    const int iy = (e >> 8) - 1, ix = (e & 255) - 27;  // R5 coordinates
+    const int cx = ix + 1, cy = iy + 1;                 // centre in sJ
     float v[9];
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
       for (int dx = 0; dx < 3; ++dx) v[dy * 3 + dx] = sJ[(cy - 1 + dy) * L::JW + cx - 1 + dx];
     const float m3 = sel_med9(v);
-    sM3[i] = m3;
+    sM3[iy * L::W5 + ix] = m3;
     if (kMaps && ix >= 5 && ix < 5 + TW && iy >= 5 && iy < 5 + TH)
       f.maps[5 * npix + size_t(y0 - 5 + iy) * w + (x0 - 5 + ix)] = m3;
   }
@@ -402,8 +475,9 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   }
 
   // P10: (c)+(d) at the candidate tests: F, the objlim statistic, and for each
-  // candidate the two growths it causes inside the tile
-  for (int j = tid; j < cnt[4]; j += kThreads) {
+  // candidate the two growths it causes inside the tile (bits of g2)
+  const int nT = cnt[0];
+  for (int j = tid; j < nT; j += kThreads) {
     const int i = L1[j];
     const int iy = i / L::W2, ix = i - iy * L::W2;
     const int mx = ix + 3, my = iy + 3;  // centre in sM3
@@ -432,12 +506,13 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
         const int qx = ix + ex;
         if (qx < 1 || qx > L::W2 - 2) continue;
         if (!(sSp[qy * L::W2 + qx] > sigclip)) continue;
-        if (kMaps) bG1[(qy - 1) * L::W1 + qx - 1] = 1;
+        if (kMaps) atomicOr(&mG1[(qy + 4) * L::NW + ((qx + 30) >> 5)], 1u << ((qx + 30) & 31));
         for (int ry = qy - 1; ry <= qy + 1; ++ry) {
           if (ry < 2 || ry >= 2 + TH) continue;
           for (int rx = qx - 1; rx <= qx + 1; ++rx) {
             if (rx < 2 || rx >= 2 + TW) continue;
-            if (sSp[ry * L::W2 + rx] > siglow) bG2[(ry - 2) * TW + rx - 2] = 1;
+            if (sSp[ry * L::W2 + rx] > siglow)
+              atomicOr(&mG2[(ry + 4) * L::NW + ((rx + 30) >> 5)], 1u << ((rx + 30) & 31));
           }
         }
       }
@@ -445,31 +520,31 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   }
   __syncthreads();
 
-  // P11: the tile's flag words (one warp per 32-pixel word)
-  const int lane = tid & 31, warp = tid >> 5;
+  // P11: the tile's flag words
   constexpr int kWordsPerRow = TW / 32;
   unsigned int new_flags = 0;
-  for (int wi = warp; wi < kWordsPerRow * TH; wi += kThreads / 32) {
+  for (int wi = tid; wi < kWordsPerRow * TH; wi += kThreads) {
     const int r = wi / kWordsPerRow, wc = wi - r * kWordsPerRow;
-    const int lx = wc * 32 + lane, gx = x0 + lx, gy = y0 + r;
-    bool g2v = false;
-    if (gx < w && gy < h) {
-      g2v = bG2[r * TW + lx] != 0;
-      if (kMaps) {
+    const int gy = y0 + r;
+    if (gy >= h || (x0 >> 5) + wc >= f.wpr) continue;
+    const uint32_t g2w = mG2[(r + 6) * L::NW + 1 + wc];  // x0 + 32 wc is word 1 + wc of the row
+    uint32_t* wp = f.bits + size_t(gy) * f.wpr + (x0 >> 5) + wc;
+    const uint32_t prev = *wp;
+    if (g2w) *wp = prev | g2w;
+    new_flags += __popc(g2w & ~prev);
+    if (kMaps) {
+      const uint32_t g1w = mG1[(r + 6) * L::NW + 1 + wc];
+      for (int b = 0; b < 32; ++b) {
+        const int gx = x0 + 32 * wc + b;
+        if (gx >= w) break;
         const size_t o = size_t(gy) * w + gx;
-        f.maps[9 * npix + o] = bG1[(r + 1) * L::W1 + lx + 1] ? 1.f : 0.f;
-        f.maps[10 * npix + o] = g2v ? 1.f : 0.f;
+        f.maps[9 * npix + o] = ((g1w >> b) & 1u) ? 1.f : 0.f;
+        f.maps[10 * npix + o] = ((g2w >> b) & 1u) ? 1.f : 0.f;
       }
     }
-    const unsigned int word = __ballot_sync(0xffffffffu, g2v);
-    if (lane == 0 && gy < h && (x0 >> 5) + wc < f.wpr) {
-      uint32_t* wp = f.bits + size_t(gy) * f.wpr + (x0 >> 5) + wc;
-      const uint32_t prev = *wp;
-      *wp = prev | word;
-      new_flags += __popc(word & ~prev);
-    }
   }
-  if (lane == 0 && new_flags) atomicAdd(f.counters + 2 * (k - 1), (unsigned long long)new_flags);
+  for (int off = 16; off; off >>= 1) new_flags += __shfl_xor_sync(0xffffffffu, new_flags, off);
+  if ((tid & 31) == 0 && new_flags) atomicAdd(f.counters + 2 * (k - 1), (unsigned long long)new_flags);
 }
 
 template <int TW, int TH, bool kMaps>
