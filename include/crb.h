@@ -70,6 +70,10 @@ typedef struct {
   /* 1: bracket every kernel launch with CUDA events on the launching stream;
    * read the accumulated device times with crb_profile_read. Default 0.       */
   int profile;
+  /* 1: run each iteration as two launches (detection, replacement) instead of
+   * fusing the replacement of iteration k-1 into the detection of iteration k
+   * (niter + 1 launches). Same results; for comparison. Default 0.            */
+  int no_fusion;
 } crb_options;
 
 /* Creates a context with the cleaning parameters (Sec. 5 lists gain, readn,
@@ -126,10 +130,18 @@ int crb_clean_noalloc(float gain, float readnoise, float sigclip, float sigfrac,
 int crb_sync_status(crb_ctx* ctx, cudaStream_t stream);
 
 /* After crb_sync_status: per-iteration counters of the last crb_clean /
- * crb_iterate: out[2k] = pixels newly flagged in iteration k+1, out[2k+1] =
- * flagged pixels with no unflagged 5x5 neighbour. Returns the number of
- * iterations written (<= max_iter), or -1. */
+ * crb_clean_batch / crb_iterate, summed over its frames: out[2k] = pixels newly
+ * flagged in iteration k+1, out[2k+1] = flagged pixels with no unflagged 5x5
+ * neighbour. Returns the number of iterations written (<= max_iter), or -1. */
 int crb_last_counts(crb_ctx* ctx, long long* out, int max_iter);
+
+/* After crb_sync_status: the work the detection kernel did in each iteration
+ * of the last call, summed over its frames: out[5k..5k+4] = positions at which
+ * it evaluated S (5x5 median of J), S' (5x5 median of S), med3, the candidate
+ * test (7x7 median of med3), and the dense upper-bound test. The stages are
+ * evaluated only where they can change a flag, so these counts are the
+ * method's work on this input. Returns the number of iterations, or -1. */
+int crb_last_work(crb_ctx* ctx, long long* out, int max_iter);
 
 /* One iteration from an explicit state, for stage-by-stage checks:
  * J (device, w*h floats) = I_{k-1}, Mprev (device, w*h bytes, may be NULL for

@@ -22,7 +22,8 @@ MAP_NAMES = ("m5", "lplus", "noise", "s", "sprime", "m3", "f", "r", "cand", "g1"
 
 class crb_options(ctypes.Structure):
     _fields_ = [("objlim_form", ctypes.c_int), ("early_exit", ctypes.c_int),
-                ("tile_shape", ctypes.c_int), ("use_graphs", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("tile_shape", ctypes.c_int), ("use_graphs", ctypes.c_int), ("profile", ctypes.c_int),
+                ("no_fusion", ctypes.c_int)]
 
 
 # (name, restype, argtypes)
@@ -39,6 +40,7 @@ SIGNATURES = {
     "crb_clean_noalloc": (_ci, [_cf, _cf, _cf, _cf, _cf, _ci, _vp, _ci, _ci, _vp, _vp, _vp]),
     "crb_sync_status": (_ci, [_vp, _vp]),
     "crb_last_counts": (_ci, [_vp, ctypes.POINTER(ctypes.c_longlong), _ci]),
+    "crb_last_work": (_ci, [_vp, ctypes.POINTER(ctypes.c_longlong), _ci]),
     "crb_iterate": (_ci, [_vp, _vp, _vp, _ci, _ci, _vp, _vp, _vp, _vp]),
     "crb_profile_read": (_ci, [_vp, ctypes.POINTER(ctypes.c_double), _PI, ctypes.POINTER(ctypes.c_double), _PI,
                                _ci]),

@@ -33,10 +33,11 @@ class Cleaner:
     """One cleaning context (crb_create_ex). Not thread-safe; use one per thread."""
 
     def __init__(self, gain=7.0, readnoise=5.0, sigclip=4.5, sigfrac=0.5, objlim=1.0, niter=4, *,
-                 objlim_form=0, early_exit=False, tile_shape=0, use_graphs=False, profile=False):
+                 objlim_form=0, early_exit=False, tile_shape=0, use_graphs=False, profile=False,
+                 fusion=True):
         lib = _lib.load()
         opt = _lib.crb_options(int(objlim_form), int(bool(early_exit)), int(tile_shape), int(bool(use_graphs)),
-                               int(bool(profile)))
+                               int(bool(profile)), int(not fusion))
         h = lib.crb_create_ex(gain, readnoise, sigclip, sigfrac, objlim, int(niter), ctypes.byref(opt))
         if not h:
             raise ValueError("crb_create_ex: " + lib.crb_last_error().decode())
@@ -119,6 +120,14 @@ class Cleaner:
         if k < 0:
             raise RuntimeError("crb_last_counts failed")
         return [(int(buf[2 * i]), int(buf[2 * i + 1])) for i in range(k)]
+
+    def last_work(self):
+        """Per iteration of the last call: positions given (S, S', med3, candidate test, bound test)."""
+        buf = (ctypes.c_longlong * (5 * max(self.niter, 1)))()
+        k = _lib.load().crb_last_work(self._h, buf, max(self.niter, 1))
+        if k < 0:
+            raise RuntimeError("crb_last_work failed")
+        return [tuple(int(buf[5 * i + j]) for j in range(5)) for i in range(k)]
 
     def profile_read(self, reset=True):
         """(detect ms, detect launches, replace ms, replace launches) since the last reset."""

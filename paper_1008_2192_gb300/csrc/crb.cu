@@ -40,14 +40,15 @@ using ReplaceFn = void (*)(const crb::Frame*, int, long long, int, int, int);
 
 struct DetectShape {
   int tw, th;
-  DetectFn fn, fn_maps;
-  size_t smem;
+  DetectFn fn, fn_maps, fn_fused;
+  size_t smem, smem_fused;
 };
 
 template <int TW, int TH>
 DetectShape make_detect() {
-  return DetectShape{TW, TH, crb::detect_kernel<TW, TH, false>, crb::detect_kernel<TW, TH, true>,
-                     crb::DetectLayout<TW, TH>::bytes};
+  return DetectShape{TW, TH, crb::detect_kernel<TW, TH, false, false>, crb::detect_kernel<TW, TH, true, false>,
+                     crb::detect_kernel<TW, TH, false, true>, crb::DetectLayout<TW, TH, false>::bytes,
+                     crb::DetectLayout<TW, TH, true>::bytes};
 }
 
 const std::vector<DetectShape>& detect_shapes() {
@@ -84,7 +85,7 @@ struct crb_ctx {
   int niter = 0;
   crb_options opt{};
   int device = 0, num_sms = 0;
-  std::vector<int> occ_detect, occ_detect_maps;
+  std::vector<int> occ_detect, occ_detect_maps, occ_fused;
   int occ_replace = 0;
 
   void* ws = nullptr;
@@ -95,6 +96,7 @@ struct crb_ctx {
   unsigned long long* d_counters = nullptr;
   int counters_cap = 0;  // in unsigned long longs
   int last_niter = 0;
+  int last_nframes = 0;
   cudaEvent_t upload_ev = nullptr, done_ev = nullptr;
   bool any_call = false;
   int latched = CRB_OK;
@@ -112,13 +114,16 @@ int init_ctx(crb_ctx* c) {
   CRB_CUDA(cudaGetDevice(&c->device));
   CRB_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
   for (const auto& s : detect_shapes()) {
-    int occ = 0, occm = 0;
+    int occ = 0, occm = 0, occf = 0;
     CRB_CUDA(cudaFuncSetAttribute(s.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s.smem)));
     CRB_CUDA(cudaFuncSetAttribute(s.fn_maps, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s.smem)));
+    CRB_CUDA(cudaFuncSetAttribute(s.fn_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s.smem_fused)));
     CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, s.fn, crb::kThreads, s.smem));
     CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occm, s.fn_maps, crb::kThreads, s.smem));
+    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occf, s.fn_fused, crb::kThreads, s.smem_fused));
     c->occ_detect.push_back(occ > 0 ? occ : 1);
     c->occ_detect_maps.push_back(occm > 0 ? occm : 1);
+    c->occ_fused.push_back(occf > 0 ? occf : 1);
   }
   CRB_CUDA(cudaFuncSetAttribute(kReplace, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kReplaceSmem)));
   CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_replace, kReplace, crb::kThreads, kReplaceSmem));
@@ -210,7 +215,7 @@ int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, c
     const auto& s = specs[size_t(i)];
     const size_t wpr = size_t(s.w + 31) / 32;
     off_bits[size_t(i)] = total;
-    total += align256(wpr * size_t(s.h) * 4);
+    total += 2 * align256(wpr * size_t(s.h) * 4);  // M for odd and for even iterations
   }
   const size_t bits_total = total;
   for (int i = 0; i < n; ++i) {
@@ -218,7 +223,8 @@ int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, c
     off_img[size_t(i)] = total;
     if (niter >= 2) total += align256(size_t(s.w) * size_t(s.h) * 4);
   }
-  const int ncounters = 2 * (niter > 0 ? niter : 1) * n;
+  const int nit = niter > 0 ? niter : 1;
+  const int ncounters = 7 * nit * n;  // per frame: 2 per iteration, then 5 per iteration of work
   int rc = ensure_frames(c, n);
   if (rc) return rc;
   rc = ensure_ws(c, total > 0 ? total : 256, ncounters);
@@ -234,10 +240,13 @@ int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, c
     f.img = s.img;
     f.out_clean = s.out_clean;
     f.ws = (niter >= 2) ? reinterpret_cast<float*>(static_cast<char*>(c->ws) + off_img[size_t(i)]) : nullptr;
-    f.bits = reinterpret_cast<uint32_t*>(static_cast<char*>(c->ws) + off_bits[size_t(i)]);
+    f.bits_a = reinterpret_cast<uint32_t*>(static_cast<char*>(c->ws) + off_bits[size_t(i)]);
+    f.bits_b = reinterpret_cast<uint32_t*>(static_cast<char*>(c->ws) + off_bits[size_t(i)] +
+                                           align256(size_t(s.w + 31) / 32 * size_t(s.h) * 4));
     f.out_mask = s.out_mask;
     f.maps = s.maps;
-    f.counters = c->d_counters + size_t(2) * (niter > 0 ? niter : 1) * i;
+    f.counters = c->d_counters + size_t(7) * nit * i;
+    f.work = f.counters + size_t(2) * nit;
     f.w = s.w;
     f.h = s.h;
     f.wpr = (s.w + 31) / 32;
@@ -255,6 +264,7 @@ int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, c
   CRB_CUDA(cudaEventRecord(c->upload_ev, stream));
   CRB_CUDA(cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * size_t(ncounters), stream));
   c->last_niter = niter;
+  c->last_nframes = n;
 
   if (niter == 0) {
     for (const auto& s : specs) {
@@ -269,21 +279,31 @@ int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, c
         const crb::Frame& f = c->h_frames[i];
         const long long nwords = (long long)f.wpr * f.h;
         const int blocks = int((nwords * 32 + 255) / 256 < 65535 ? (nwords * 32 + 255) / 256 : 65535);
-        crb::bytes_to_bits_kernel<<<blocks, 256, 0, stream>>>(s.mprev, f.bits, f.w, f.h, f.wpr);
+        crb::bytes_to_bits_kernel<<<blocks, 256, 0, stream>>>(s.mprev, f.bits_b, f.w, f.h, f.wpr);  // M_0
       }
     }
     const int dgrid = int(std::min<long long>(tiles, (long long)c->num_sms *
                                                          (maps ? c->occ_detect_maps : c->occ_detect)[size_t(shape)]));
     const int rgrid = int(std::min<long long>(rtiles, (long long)c->num_sms * c->occ_replace));
+    const bool fuse = !maps && !c->opt.no_fusion;
+    const int fgrid = int(std::min<long long>(tiles, (long long)c->num_sms * c->occ_fused[size_t(shape)]));
     for (int k = 1; k <= niter; ++k) {
-      timed(c, 0, stream, [&] {
-        (maps ? ds.fn_maps : ds.fn)<<<dgrid, crb::kThreads, ds.smem, stream>>>(c->d_frames, n, tiles, c->p, k,
-                                                                                 niter);
-      });
-      timed(c, 1, stream, [&] {
-        kReplace<<<rgrid, crb::kThreads, kReplaceSmem, stream>>>(c->d_frames, n, rtiles, k, niter,
-                                                                 k <= 2 ? 1 : 0);
-      });
+      if (fuse && k >= 2) {  // replacement of iteration k-1 fused in front of detection k
+        timed(c, 0, stream, [&] {
+          ds.fn_fused<<<fgrid, crb::kThreads, ds.smem_fused, stream>>>(c->d_frames, n, tiles, c->p, k, niter);
+        });
+      } else {
+        timed(c, 0, stream, [&] {
+          (maps ? ds.fn_maps : ds.fn)<<<dgrid, crb::kThreads, ds.smem, stream>>>(c->d_frames, n, tiles, c->p, k,
+                                                                                   niter);
+        });
+      }
+      if (!fuse || k == niter) {
+        timed(c, 1, stream, [&] {
+          kReplace<<<rgrid, crb::kThreads, kReplaceSmem, stream>>>(c->d_frames, n, rtiles, k, niter,
+                                                                   k <= 2 ? 1 : 0);
+        });
+      }
     }
     CRB_CUDA(cudaGetLastError());
   }
@@ -409,17 +429,32 @@ int crb_sync_status(crb_ctx* c, cudaStream_t stream) {
   return s;
 }
 
-int crb_last_counts(crb_ctx* c, long long* out, int max_iter) {
+namespace {
+// Sums, over the frames of the last call, `width` counters per iteration
+// stored at offset `base` (per iteration) of each frame's block.
+int read_counters(crb_ctx* c, long long* out, int max_iter, int base, int width) {
   if (!c || !out || max_iter < 0) return -1;
   const int k = std::min(c->last_niter, max_iter);
-  if (k == 0) return 0;
-  std::vector<unsigned long long> tmp(size_t(2 * k));
+  if (k == 0 || c->last_nframes == 0) return 0;
+  const int nit = c->last_niter;
+  std::vector<unsigned long long> tmp(size_t(7) * nit * c->last_nframes);
   if (cudaMemcpy(tmp.data(), c->d_counters, sizeof(unsigned long long) * tmp.size(), cudaMemcpyDeviceToHost) !=
       cudaSuccess)
     return -1;
-  for (size_t i = 0; i < tmp.size(); ++i) out[i] = (long long)tmp[i];
+  for (int it = 0; it < k; ++it)
+    for (int j = 0; j < width; ++j) {
+      long long s = 0;
+      for (int fr = 0; fr < c->last_nframes; ++fr)
+        s += (long long)tmp[size_t(7) * nit * fr + size_t(base) * nit + size_t(width) * it + j];
+      out[width * it + j] = s;
+    }
   return k;
 }
+}  // namespace
+
+int crb_last_counts(crb_ctx* c, long long* out, int max_iter) { return read_counters(c, out, max_iter, 0, 2); }
+
+int crb_last_work(crb_ctx* c, long long* out, int max_iter) { return read_counters(c, out, max_iter, 2, 5); }
 
 int crb_profile_read(crb_ctx* c, double* detect_ms, int* detect_launches, double* replace_ms,
                      int* replace_launches, int reset) {

@@ -35,10 +35,14 @@ struct Frame {
   const float* img;       // I_0 (input, read-only)
   float* out_clean;       // caller's output
   float* ws;              // workspace image of the same size
-  uint32_t* bits;         // cumulative flags: bit x&31 of word [y*wpr + x/32]
+  uint32_t* bits_a;       // cumulative flags M_k, bit x&31 of word [y*wpr + x/32]: in bits_a
+  uint32_t* bits_b;       // for odd k, in bits_b for even k (M_0 = bits_b); equal pointers
+                          // update the flags in place (detection and replacement as two launches)
   uint8_t* out_mask;      // caller's 0/1 mask, written by the last replacement
   float* maps;            // kNumMaps debug maps (crb_iterate) or nullptr
   unsigned long long* counters;  // 2 per iteration: new flags, no-unflagged-neighbour pixels
+  unsigned long long* work;      // nullable; 5 per iteration: positions given S, S', med3, a
+                                 // candidate test, and the dense bound test
   int w, h, wpr;
   float gain, rn;
   int tiles_x, rtiles_x;  // detect / replace tiles per row of tiles
@@ -57,6 +61,8 @@ __device__ __forceinline__ const float* iter_src(const Frame& f, int k, int nite
 __device__ __forceinline__ float* iter_dst(const Frame& f, int k, int niter) {
   return ((niter - k) % 2 == 0) ? f.out_clean : f.ws;
 }
+
+__device__ __forceinline__ uint32_t* mask_bits(const Frame& f, int k) { return (k & 1) ? f.bits_a : f.bits_b; }
 
 // Finds the frame of global tile t (frames sorted by first tile index).
 template <bool kReplace>
@@ -177,9 +183,12 @@ __device__ __forceinline__ int block_excl_scan(int v, int* ws, int& total) {
 //   sJ (R6) J, clamped at load; sCM (R2 rows x R4 columns) column medians,
 //   aliased by sS (R4) S; sM3 (R5) med3; sN, sSp (R2) N and S' (-inf unless
 //   computed); 9 bit maps; three position lists and small counters.
-template <int TW, int TH>
+template <int TW, int TH, bool kFused = false>
 struct DetectLayout {
-  static constexpr int JW = TW + 12, JH = TH + 12;
+  static constexpr int JW = TW + 12, JH = TH + 12;  // R6
+  // image buffer: R6 of J, or (fused) R8 of I_{k-2}, replaced in place on R6
+  static constexpr int JP = kFused ? TW + 16 : TW + 12, JR = kFused ? TH + 16 : TH + 12;
+  static constexpr int JOFF = kFused ? 2 * JP + 2 : 0;  // R6 origin inside the buffer
   static constexpr int W5 = TW + 10, H5 = TH + 10;
   static constexpr int W4 = TW + 8, H4 = TH + 8;
   static constexpr int W2 = TW + 4, H2 = TH + 4;
@@ -189,15 +198,18 @@ struct DetectLayout {
   static_assert(TW % 32 == 0 && 32 * NW <= 256 && JH <= 255, "list entries pack (row << 8 | bit column)");
   static_assert(MW % 4 == 0, "bit maps are cleared as 16-byte vectors");
   static constexpr int oJ = 0;  // floats
-  static constexpr int oS = oJ + JW * JH;
+  static constexpr int oS = oJ + JP * JR;
   static constexpr int oM3 = oS + imax(W4 * H4, H2 * W4);
   static constexpr int oN = oM3 + W5 * H5;
   static constexpr int oSp = oN + W2 * H2;
   static constexpr int nF = oSp + W2 * H2;
   static constexpr int kMaps = 9;  // hot, act, tmp, needS', needS, test, needM3, g1, g2
+  static constexpr int MWF = kFused ? NW * (TH + 16) : 0;  // flags of M_{k-1} over R8 rows
+  static_assert(MWF % 4 == 0, "bit maps are cleared as 16-byte vectors");
+  static_assert(imax(W4 * H4, H2 * W4) + W5 * H5 >= JW * JH, "replacement values fit in the S/med3 area");
   static constexpr int oBits = round16(nF * 4);  // bytes
-  static constexpr int oL0 = round16(oBits + kMaps * MW * 4);
-  static constexpr int oL1 = oL0 + round16(W5 * H5 * 2);
+  static constexpr int oL0 = round16(oBits + (kMaps * MW + MWF) * 4);
+  static constexpr int oL1 = oL0 + round16(imax(W5 * H5, JW * JH) * 2);
   static constexpr int oL2 = oL1 + round16(W2 * H2 * 2);
   static constexpr int oCnt = oL2 + round16(W2 * H2 * 2);  // 16 ints: counters + scan scratch
   static constexpr size_t bytes = size_t(oCnt + 16 * 4);
@@ -227,6 +239,15 @@ __device__ __forceinline__ int bits_to_list(const uint32_t* map, uint16_t* list,
     }
   }
   return total;
+}
+
+// bits of word j of bit-map row `row` (an R6 row) that lie in Rk and in the frame
+template <int TW, int TH>
+__device__ __forceinline__ uint32_t region_word(int kreg, int row, int j, int x0, int y0, int w, int h) {
+  const int y = y0 - 6 + row;
+  if (y < imax(0, y0 - kreg) || y >= min(h, y0 + TH + kreg)) return 0u;
+  const int xw = x0 - 32 + 32 * j;
+  return bits_between(imax(0, x0 - kreg) - xw, min(w, x0 + TW + kreg) - xw);
 }
 
 // out = in dilated horizontally by r (each thread a word), then (after a
@@ -277,10 +298,11 @@ __device__ __forceinline__ void region_map(uint32_t* out, int kreg, int x0, int 
   }
 }
 
-template <int TW, int TH, bool kMaps>
+template <int TW, int TH, bool kMaps, bool kFused>
 __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, long long tile, char* smem) {
-  using L = DetectLayout<TW, TH>;
-  float* sJ = reinterpret_cast<float*>(smem) + L::oJ;
+  using L = DetectLayout<TW, TH, kFused>;
+  float* sBuf = reinterpret_cast<float*>(smem) + L::oJ;
+  float* sJ = sBuf + L::JOFF;  // R6 of J, row pitch L::JP
   float* sS = reinterpret_cast<float*>(smem) + L::oS;
   float* sCM = sS;  // column medians; dead before S is written
   float* sM3 = reinterpret_cast<float*>(smem) + L::oM3;
@@ -296,6 +318,7 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   uint32_t* mNeedM3 = bits + 6 * L::MW;
   uint32_t* mG1 = bits + 7 * L::MW;
   uint32_t* mG2 = bits + 8 * L::MW;
+  uint32_t* mFl = bits + 9 * L::MW;  // fused: M_{k-1} over R8 rows
   uint16_t* L0 = reinterpret_cast<uint16_t*>(smem + L::oL0);
   uint16_t* L1 = reinterpret_cast<uint16_t*>(smem + L::oL1);
   uint16_t* L2 = reinterpret_cast<uint16_t*>(smem + L::oL2);
@@ -313,14 +336,122 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   const int tid = threadIdx.x;
 
   // P0: clear bit maps and counters, S' = -inf, load J over R6 (replicate edge)
-  for (int i = tid; i < L::kMaps * L::MW / 4; i += kThreads)
+  for (int i = tid; i < (L::kMaps * L::MW + L::MWF) / 4; i += kThreads)
     reinterpret_cast<uint4*>(bits)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (tid < 4) cnt[tid] = 0;
   for (int i = tid; i < L::W2 * L::H2; i += kThreads) sSp[i] = -INFINITY;
-  for (int i = tid; i < L::JW * L::JH; i += kThreads) {
-    const int iy = i / L::JW, ix = i - iy * L::JW;
-    const int gx = clampi(x0 - 6 + ix, 0, w - 1), gy = clampi(y0 - 6 + iy, 0, h - 1);
-    sJ[i] = __ldg(J + size_t(gy) * w + gx);
+  if (!kFused) {
+    for (int i = tid; i < L::JW * L::JH; i += kThreads) {
+      const int iy = i / L::JW, ix = i - iy * L::JW;
+      const int gx = clampi(x0 - 6 + ix, 0, w - 1), gy = clampi(y0 - 6 + iy, 0, h - 1);
+      sJ[iy * L::JP + ix] = __ldg(J + size_t(gy) * w + gx);
+    }
+  } else {
+    // Iteration k-1's replacement on R6, fused in front of iteration k's
+    // detection: I_{k-2} and M_{k-1} over R8, flagged R6 pixels replaced in
+    // place; the tile's I_{k-1} goes to the destination of iteration k-1.
+    const int kr = k - 1;
+    const float* __restrict__ Iprev = iter_src(f, kr, niter);
+    const uint32_t* __restrict__ Mb = mask_bits(f, kr);
+    for (int i = tid; i < L::JP * L::JR; i += kThreads) {
+      const int iy = i / L::JP, ix = i - iy * L::JP;
+      const int gx = clampi(x0 - 8 + ix, 0, w - 1), gy = clampi(y0 - 8 + iy, 0, h - 1);
+      sBuf[i] = __ldg(Iprev + size_t(gy) * w + gx);
+    }
+    const bool inner = x0 - 8 >= 0 && x0 + TW + 8 <= w && y0 - 8 >= 0 && y0 + TH + 8 <= h;
+    __syncthreads();  // the maps are clear
+    if (inner) {  // whole words: the bits that matter are all in the frame
+      for (int t = tid; t < L::MWF; t += kThreads) {
+        const int row = t / L::NW, j = t - row * L::NW;
+        mFl[t] = __ldg(Mb + size_t(y0 - 8 + row) * f.wpr + (x0 >> 5) - 1 + j);
+      }
+    }
+    __syncthreads();
+    if (!inner) {  // clamped flag of every R8 position (replicate edge)
+      for (int i = tid; i < L::JP * L::JR; i += kThreads) {
+        const int iy = i / L::JP, ix = i - iy * L::JP;
+        const int gx = clampi(x0 - 8 + ix, 0, w - 1), gy = clampi(y0 - 8 + iy, 0, h - 1);
+        if ((__ldg(Mb + size_t(gy) * f.wpr + (gx >> 5)) >> (gx & 31)) & 1u)
+          atomicOr(&mFl[iy * L::NW + ((ix + 24) >> 5)], 1u << ((ix + 24) & 31));
+      }
+      __syncthreads();
+    }
+    // flagged in-frame R6 positions -> list (entries: R6 row << 8 | bit column)
+    for (int t = tid; t < L::MW; t += kThreads) {
+      const int row = t / L::NW, j = t - row * L::NW;
+      mTmp[t] = mFl[(row + 2) * L::NW + j] & region_word<TW, TH>(6, row, j, x0, y0, w, h);
+    }
+    __syncthreads();
+    const int nR = bits_to_list<L::NW, L::MW>(mTmp, L0, cnt + 4);
+    __syncthreads();
+    float* val = sS;  // scratch for the replacement values (the S / med3 area is free here)
+    unsigned int none_left = 0;
+    for (int j = tid; j < nR; j += kThreads) {
+      const int e = L0[j];
+      const int r6 = e >> 8, xb = e & 255;
+      const int cy = r6 + 2, cx = xb - 24;  // R8 coordinates
+      uint32_t win = 0;                     // 25 window flags, row-major
+#pragma unroll
+      for (int dy = 0; dy < 5; ++dy) {
+        const int wj = (xb - 2) >> 5, sh = (xb - 2) & 31;
+        const uint32_t* rowp = mFl + (cy - 2 + dy) * L::NW;
+        const uint32_t lo = rowp[wj], hi = (wj + 1 < L::NW) ? rowp[wj + 1] : 0u;
+        win |= (__funnelshift_r(lo, hi, sh) & 31u) << (5 * dy);
+      }
+      const int n = 25 - __popc(win);
+      float v[25];
+      float out;
+      if (n > 0) {
+        const int a = 13 - (n + 1) / 2;  // flagged entries sent to -inf
+        int seen = 0;
+#pragma unroll
+        for (int q = 0; q < 25; ++q) {
+          float x = sBuf[(cy - 2 + q / 5) * L::JP + cx - 2 + q % 5];
+          if ((win >> q) & 1u) {
+            x = (seen < a) ? -INFINITY : INFINITY;
+            ++seen;
+          }
+          v[q] = x;
+        }
+        out = sel_med25(v);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 25; ++q) v[q] = sBuf[(cy - 2 + q / 5) * L::JP + cx - 2 + q % 5];
+        out = floor_m5(sel_med25(v));
+        if (r6 >= 6 && r6 < 6 + TH && xb >= 32 && xb < 32 + TW) ++none_left;
+      }
+      val[j] = out;
+    }
+    for (int off = 16; off; off >>= 1) none_left += __shfl_xor_sync(0xffffffffu, none_left, off);
+    if ((tid & 31) == 0 && none_left) atomicAdd(f.counters + 2 * (kr - 1) + 1, (unsigned long long)none_left);
+    __syncthreads();
+    float* __restrict__ Dprev = iter_dst(f, kr, niter);
+    for (int j = tid; j < nR; j += kThreads) {
+      const int e = L0[j];
+      const int r6 = e >> 8, xb = e & 255;
+      sBuf[(r6 + 2) * L::JP + xb - 24] = val[j];
+      if (r6 >= 6 && r6 < 6 + TH && xb >= 32 && xb < 32 + TW)
+        Dprev[size_t(y0 - 6 + r6) * w + (x0 - 32 + xb)] = val[j];
+    }
+    if (kr <= 2) {  // the destination of iterations 1 and 2 is written densely
+      for (int i = tid; i < TW * TH; i += kThreads) {
+        const int ly = i / TW, lx = i - ly * TW;
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= w || gy >= h) continue;
+        if ((mFl[(ly + 8) * L::NW + ((lx + 32) >> 5)] >> (lx & 31)) & 1u) continue;
+        Dprev[size_t(gy) * w + gx] = sBuf[(ly + 8) * L::JP + lx + 8];
+      }
+    }
+    __syncthreads();
+    if (edge) {  // replicate the replaced frame edge into the out-of-frame part of R6
+      for (int i = tid; i < L::JW * L::JH; i += kThreads) {
+        const int iy = i / L::JW, ix = i - iy * L::JW;
+        const int gx = x0 - 6 + ix, gy = y0 - 6 + iy;
+        if (gx >= 0 && gx < w && gy >= 0 && gy < h) continue;
+        const int sx = clampi(gx, 0, w - 1) - (x0 - 6), sy = clampi(gy, 0, h - 1) - (y0 - 6);
+        sJ[iy * L::JP + ix] = sJ[sy * L::JP + sx];
+      }
+    }
   }
   __syncthreads();
 
@@ -335,7 +466,7 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
       const int iy = i / L::W4, ix = i - iy * L::W4;
       float v[5];
 #pragma unroll
-      for (int d = 0; d < 5; ++d) v[d] = sJ[(iy + 2 + d) * L::JW + ix + 2];
+      for (int d = 0; d < 5; ++d) v[d] = sJ[(iy + 2 + d) * L::JP + ix + 2];
       sCM[i] = sel_med5(v);
     }
     __syncthreads();
@@ -345,8 +476,8 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
       const int iy = i / L::W2, ix = i - iy * L::W2;
       const int gx = x0 - 2 + ix, gy = y0 - 2 + iy;
       if (gx < 0 || gx >= w || gy < 0 || gy >= h) continue;
-      const float* c = sJ + (iy + 4) * L::JW + ix + 4;
-      const float lp = lplus(c[0], c[-L::JW], c[L::JW], c[-1], c[1]);
+      const float* c = sJ + (iy + 4) * L::JP + ix + 4;
+      const float lp = lplus(c[0], c[-L::JP], c[L::JP], c[-1], c[1]);
       const float* cm = sCM + iy * L::W4 + ix;
       const float mlow = min3f(min3f(cm[0], cm[1], cm[2]), cm[3], cm[4]);
       const float den = gain * (mlow > 0.f ? mlow : 0.f) + rn2;
@@ -369,6 +500,13 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   const int nS = bits_to_list<L::NW, L::MW>(mNeedS, L0, cnt + 4);
   const int nSp = bits_to_list<L::NW, L::MW>(mNeedSp, L2, cnt + 4);
   __syncthreads();
+  if (tid == 0 && f.work) {
+    unsigned long long* wk = f.work + 5 * (k - 1);
+    const long long dense = (long long)(min(x0 + TW + 2, w) - imax(x0 - 2, 0)) * (min(y0 + TH + 2, h) - imax(y0 - 2, 0));
+    atomicAdd(wk + 0, (unsigned long long)nS);
+    atomicAdd(wk + 1, (unsigned long long)nSp);
+    atomicAdd(wk + 4, (unsigned long long)dense);
+  }
 
   // P6: (a)+(b) at the listed positions: m5, N, L+, S
   for (int j = tid; j < nS; j += kThreads) {
@@ -380,11 +518,11 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
 #pragma unroll
     for (int dy = 0; dy < 5; ++dy)
 #pragma unroll
-      for (int dx = 0; dx < 5; ++dx) v[dy * 5 + dx] = sJ[(cy - 2 + dy) * L::JW + cx - 2 + dx];
+      for (int dx = 0; dx < 5; ++dx) v[dy * 5 + dx] = sJ[(cy - 2 + dy) * L::JP + cx - 2 + dx];
     const float m5f = floor_m5(sel_med25(v));
     const float n = noise_of(m5f, gain, rn2);
-    const float* c = sJ + cy * L::JW + cx;
-    const float lp = lplus(c[0], c[-L::JW], c[L::JW], c[-1], c[1]);
+    const float* c = sJ + cy * L::JP + cx;
+    const float lp = lplus(c[0], c[-L::JP], c[L::JP], c[-1], c[1]);
     const float s = __fdiv_rn(lp, __fmul_rn(2.f, n));
     sS[i] = s;
     if (ix >= 2 && ix < L::W4 - 2 && iy >= 2 && iy < L::H4 - 2) sN[(iy - 2) * L::W2 + ix - 2] = n;
@@ -446,6 +584,10 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   }
   const int nM3 = bits_to_list<L::NW, L::MW>(mNeedM3, L0, cnt + 4);
   __syncthreads();
+  if (tid == 0 && f.work) {
+    atomicAdd(f.work + 5 * (k - 1) + 2, (unsigned long long)nM3);
+    atomicAdd(f.work + 5 * (k - 1) + 3, (unsigned long long)cnt[0]);
+  }
 
   // P9: med3 at the listed positions
   for (int j = tid; j < nM3; j += kThreads) {
@@ -456,7 +598,7 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-      for (int dx = 0; dx < 3; ++dx) v[dy * 3 + dx] = sJ[(cy - 1 + dy) * L::JW + cx - 1 + dx];
+      for (int dx = 0; dx < 3; ++dx) v[dy * 3 + dx] = sJ[(cy - 1 + dy) * L::JP + cx - 1 + dx];
     const float m3 = sel_med9(v);
     sM3[iy * L::W5 + ix] = m3;
     if (kMaps && ix >= 5 && ix < 5 + TW && iy >= 5 && iy < 5 + TH)
@@ -528,9 +670,9 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
     const int gy = y0 + r;
     if (gy >= h || (x0 >> 5) + wc >= f.wpr) continue;
     const uint32_t g2w = mG2[(r + 6) * L::NW + 1 + wc];  // x0 + 32 wc is word 1 + wc of the row
-    uint32_t* wp = f.bits + size_t(gy) * f.wpr + (x0 >> 5) + wc;
-    const uint32_t prev = *wp;
-    if (g2w) *wp = prev | g2w;
+    const size_t wo = size_t(gy) * f.wpr + (x0 >> 5) + wc;
+    const uint32_t prev = mask_bits(f, k - 1)[wo];
+    mask_bits(f, k)[wo] = prev | g2w;
     new_flags += __popc(g2w & ~prev);
     if (kMaps) {
       const uint32_t g1w = mG1[(r + 6) * L::NW + 1 + wc];
@@ -547,14 +689,14 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   if ((tid & 31) == 0 && new_flags) atomicAdd(f.counters + 2 * (k - 1), (unsigned long long)new_flags);
 }
 
-template <int TW, int TH, bool kMaps>
+template <int TW, int TH, bool kMaps, bool kFused = false>
 __global__ void __launch_bounds__(kThreads) detect_kernel(const Frame* __restrict__ frames, int nframes,
                                                           long long ntiles, Params p, int k, int niter) {
   extern __shared__ __align__(16) char smem[];
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int fi = frame_of<false>(frames, nframes, t);
     const Frame f = frames[fi];
-    detect_tile<TW, TH, kMaps>(f, p, k, niter, t - f.tile0, smem);
+    detect_tile<TW, TH, kMaps, kFused>(f, p, k, niter, t - f.tile0, smem);
     __syncthreads();
   }
 }
@@ -578,8 +720,9 @@ struct ReplaceLayout {
   static constexpr size_t bytes = size_t(oCnt + 16);
 };
 
-__device__ __forceinline__ bool flag_at(const Frame& f, int x, int y) {
-  return (f.bits[size_t(y) * f.wpr + (x >> 5)] >> (x & 31)) & 1u;
+// flag of (x, y) in M_k (k = the replacement's iteration; see replace_tile)
+__device__ __forceinline__ bool flag_at(const uint32_t* __restrict__ M, const Frame& f, int x, int y) {
+  return (M[size_t(y) * f.wpr + (x >> 5)] >> (x & 31)) & 1u;
 }
 
 template <int RW, int RH>
@@ -597,6 +740,7 @@ __device__ void replace_tile(const Frame& f, int k, int niter, int dense, long l
   float* __restrict__ D = iter_dst(f, k, niter);
   const bool last = (k == niter);
   const int tid = threadIdx.x;
+  const uint32_t* __restrict__ M = mask_bits(f, k);
 
   // any flagged pixel in the tile?
   constexpr int kWords = RW / 32;
@@ -604,7 +748,7 @@ __device__ void replace_tile(const Frame& f, int k, int niter, int dense, long l
   for (int wi = tid; wi < kWords * RH; wi += kThreads) {
     const int r = wi / kWords, wc = wi - r * kWords;
     const int gy = y0 + r, wx = (x0 >> 5) + wc;
-    if (gy < h && wx < f.wpr) any |= f.bits[size_t(gy) * f.wpr + wx] != 0u;
+    if (gy < h && wx < f.wpr) any |= M[size_t(gy) * f.wpr + wx] != 0u;
   }
   if (tid == 0) cnt[0] = 0;
   any = __syncthreads_or(any);
@@ -626,7 +770,7 @@ __device__ void replace_tile(const Frame& f, int k, int niter, int dense, long l
     const int iy = i / L::W, ix = i - iy * L::W;
     const int gx = clampi(x0 - 2 + ix, 0, w - 1), gy = clampi(y0 - 2 + iy, 0, h - 1);
     sJ[i] = __ldg(J + size_t(gy) * w + gx);
-    sF[i] = flag_at(f, gx, gy) ? 1 : 0;
+    sF[i] = flag_at(M, f, gx, gy) ? 1 : 0;
   }
   __syncthreads();
 

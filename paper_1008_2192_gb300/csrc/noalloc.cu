@@ -142,7 +142,8 @@ extern "C" int crb_clean_noalloc(float gain, float readnoise, float sigclip, flo
   f.img = img;
   f.out_clean = out_clean;
   f.ws = reinterpret_cast<float*>(s->scratch + kOffImg);
-  f.bits = reinterpret_cast<uint32_t*>(s->scratch + kOffBits);
+  f.bits_a = reinterpret_cast<uint32_t*>(s->scratch + kOffBits);  // one buffer: flags updated in place
+  f.bits_b = f.bits_a;
   f.out_mask = out_mask;
   f.maps = nullptr;
   f.counters = reinterpret_cast<unsigned long long*>(s->scratch + kOffCount);
@@ -161,7 +162,7 @@ extern "C" int crb_clean_noalloc(float gain, float readnoise, float sigclip, flo
   const crb::Params p{sigclip, sigfrac, objlim, 0};
 
   noalloc_prepare<<<1, 128, 0, stream>>>(f, desc, f.counters, 2 * niter);
-  if ((e = cudaMemsetAsync(f.bits, 0, sizeof(uint32_t) * size_t(f.wpr) * size_t(h), stream)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(f.bits_a, 0, sizeof(uint32_t) * size_t(f.wpr) * size_t(h), stream)) != cudaSuccess)
     return cuda_err(e, "crb_clean_noalloc: clearing flag bits");
   const int dgrid = int(std::min<long long>(tiles, (long long)s->sms * s->occ_detect));
   const int rgrid = int(std::min<long long>(rtiles, (long long)s->sms * s->occ_replace));

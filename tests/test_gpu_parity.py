@@ -98,11 +98,12 @@ def test_end_to_end_800(cl):
     print(f"800x800: mask flips vs FP64 {flips}, fragile pixels {nfragile}, flagged {int(mask.sum())}")
 
 
+@pytest.mark.parametrize("fusion", [True, False], ids=["fused", "two-launch"])
 @pytest.mark.parametrize("w,h", SIZES)
 @pytest.mark.parametrize("niter", [1, 2, 3, 4])
-def test_clean_sizes(w, h, niter):
+def test_clean_sizes(w, h, niter, fusion):
     img = scene(w, h, seed=7 * w + h)
-    c = Cleaner(niter=niter)
+    c = Cleaner(niter=niter, fusion=fusion)
     out, mask = gpu_clean(c, img)
     r32 = oracle.clean(img, params_of({}), niter, precision="f32")
     assert np.array_equal(mask, r32.mask) and np.array_equal(out, r32.clean)
@@ -126,11 +127,12 @@ def test_parameters_and_objlim_forms(form, pset):
     assert np.array_equal(mask, r32.mask) and np.array_equal(out, r32.clean)
 
 
+@pytest.mark.parametrize("fusion", [True, False], ids=["fused", "two-launch"])
 @pytest.mark.parametrize("shape", [0, 1, 2, 3, 4])
-def test_tile_shapes_agree(shape):
+def test_tile_shapes_agree(shape, fusion):
     img = scene(300, 230, seed=11)
     ref = oracle.clean(img, params_of({}), 4, precision="f32")
-    c = Cleaner(niter=4, tile_shape=shape)
+    c = Cleaner(niter=4, tile_shape=shape, fusion=fusion)
     out, mask = gpu_clean(c, img)
     assert np.array_equal(mask, ref.mask) and np.array_equal(out, ref.clean)
 
