@@ -158,6 +158,14 @@ __device__ __forceinline__ int block_excl_scan(int v, int* ws, int& total) {
   return r;
 }
 
+// 4-byte asynchronous global -> shared copy (completion: cp_async_wait_all + barrier)
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // --------------------------------------------------------------------------------------------
 // detect: stages (a)-(d) for one output tile of TW x TH pixels, computed only
 // where they can change a flag.
@@ -177,69 +185,54 @@ __device__ __forceinline__ int block_excl_scan(int v, int* ws, int& total) {
 // 1e-4 margin exceeds the few float roundings of either side, so the test
 // never rejects a position whose exact float32 S exceeds t.
 // The sets are bit-row maps; dilations are word shifts and ORs, and the work
-// lists are read off the set bits with one block-wide prefix sum.
+// lists are read off the set bits with block-wide prefix sums.
+//
+// The fused variant first performs the replacement of iteration k-1 (stage
+// e) on R6 from I_{k-2} and M_{k-1} over R8, writes the tile's I_{k-1}, and
+// then detects on the result.
+//
+// A persistent CTA walks its tiles; the image region (and, fused, the flag
+// words) of the next tile is prefetched with cp.async into the second of two
+// buffers while the current tile is processed.
 //
 // Shared memory, regions centred on the tile ("Rk" = tile grown by k px):
-//   sJ (R6) J, clamped at load; sCM (R2 rows x R4 columns) column medians,
-//   aliased by sS (R4) S; sM3 (R5) med3; sN, sSp (R2) N and S' (-inf unless
-//   computed); 9 bit maps; three position lists and small counters.
+//   two image buffers (R6 of J, or fused R8 of I_{k-2}); sCM (R2 rows x R4
+//   columns) column medians, aliased by sS (R4) S; sM3 (R5) med3; sN, sSp
+//   (R2) N and S' (-inf unless computed); fused: two flag buffers (R8 rows);
+//   9 bit maps; three position lists and small counters.
 template <int TW, int TH, bool kFused = false>
 struct DetectLayout {
   static constexpr int JW = TW + 12, JH = TH + 12;  // R6
-  // image buffer: R6 of J, or (fused) R8 of I_{k-2}, replaced in place on R6
   static constexpr int JP = kFused ? TW + 16 : TW + 12, JR = kFused ? TH + 16 : TH + 12;
-  static constexpr int JOFF = kFused ? 2 * JP + 2 : 0;  // R6 origin inside the buffer
+  static constexpr int JOFF = kFused ? 2 * JP + 2 : 0;  // R6 origin inside an image buffer
+  static constexpr int HALO = kFused ? 8 : 6;          // halo of the loaded image region
   static constexpr int W5 = TW + 10, H5 = TH + 10;
   static constexpr int W4 = TW + 8, H4 = TH + 8;
   static constexpr int W2 = TW + 4, H2 = TH + 4;
   static constexpr int W1 = TW + 2, H1 = TH + 2;
-  static constexpr int NW = TW / 32 + 2;  // words per bit-map row
-  static constexpr int MW = NW * JH;      // words per bit map
+  static constexpr int NW = TW / 32 + 2;           // words per bit-map row
+  static constexpr int MW = NW * JH;               // words per bit map (R6 rows)
+  static constexpr int MWF = kFused ? NW * (TH + 16) : 0;  // flag words of M_{k-1} (R8 rows)
   static_assert(TW % 32 == 0 && 32 * NW <= 256 && JH <= 255, "list entries pack (row << 8 | bit column)");
   static_assert(MW % 4 == 0, "bit maps are cleared as 16-byte vectors");
-  static constexpr int oJ = 0;  // floats
-  static constexpr int oS = oJ + JP * JR;
+  static constexpr int oB0 = 0;  // floats
+  static constexpr int oB1 = oB0 + JP * JR;
+  static constexpr int oS = oB1 + JP * JR;
   static constexpr int oM3 = oS + imax(W4 * H4, H2 * W4);
   static constexpr int oN = oM3 + W5 * H5;
   static constexpr int oSp = oN + W2 * H2;
   static constexpr int nF = oSp + W2 * H2;
-  static constexpr int kMaps = 9;  // hot, act, tmp, needS', needS, test, needM3, g1, g2
-  static constexpr int MWF = kFused ? NW * (TH + 16) : 0;  // flags of M_{k-1} over R8 rows
-  static_assert(MWF % 4 == 0, "bit maps are cleared as 16-byte vectors");
   static_assert(imax(W4 * H4, H2 * W4) + W5 * H5 >= JW * JH, "replacement values fit in the S/med3 area");
-  static constexpr int oBits = round16(nF * 4);  // bytes
-  static constexpr int oL0 = round16(oBits + (kMaps * MW + MWF) * 4);
+  static constexpr int kMaps = 9;  // hot, act, tmp, needS', needS, test, needM3, g1, g2
+  static constexpr int oF0 = round16(nF * 4);  // bytes
+  static constexpr int oF1 = oF0 + round16(MWF * 4);
+  static constexpr int oBits = oF1 + round16(MWF * 4);
+  static constexpr int oL0 = round16(oBits + kMaps * MW * 4);
   static constexpr int oL1 = oL0 + round16(imax(W5 * H5, JW * JH) * 2);
   static constexpr int oL2 = oL1 + round16(W2 * H2 * 2);
   static constexpr int oCnt = oL2 + round16(W2 * H2 * 2);  // 16 ints: counters + scan scratch
   static constexpr size_t bytes = size_t(oCnt + 16 * 4);
 };
-
-// positions with a set bit in `map` -> list entries (row << 8 | bit column); returns the count
-template <int NW, int MW>
-__device__ __forceinline__ int bits_to_list(const uint32_t* map, uint16_t* list, int* ws) {
-  constexpr int kPer = (MW + kThreads - 1) / kThreads;
-  const int t0 = threadIdx.x * kPer;
-  int c = 0;
-#pragma unroll
-  for (int q = 0; q < kPer; ++q)
-    if (t0 + q < MW) c += __popc(map[t0 + q]);
-  int total = 0;
-  int off = block_excl_scan(c, ws, total);
-#pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    const int t = t0 + q;
-    if (t >= MW) break;
-    uint32_t v = map[t];
-    const int row = t / NW, j = t - row * NW;
-    while (v) {
-      const int b = __ffs(v) - 1;
-      v &= v - 1u;
-      list[off++] = uint16_t((row << 8) | (32 * j + b));
-    }
-  }
-  return total;
-}
 
 // bits of word j of bit-map row `row` (an R6 row) that lie in Rk and in the frame
 template <int TW, int TH>
@@ -250,37 +243,28 @@ __device__ __forceinline__ uint32_t region_word(int kreg, int row, int j, int x0
   return bits_between(imax(0, x0 - kreg) - xw, min(w, x0 + TW + kreg) - xw);
 }
 
-// out = in dilated horizontally by r (each thread a word), then (after a
-// barrier) vertically by r, ANDed with region & frame of Rk (+ an optional
-// extra map). `tmp` is scratch.
+// out = in dilated by a (2R+1)^2 box, within Rk and the frame (and and_map if
+// given); one pass, one barrier.
 template <int TW, int TH, int R>
-__device__ __forceinline__ void dilate_map(const uint32_t* in, uint32_t* tmp, uint32_t* out, const uint32_t* and_map,
-                                           int kreg, int x0, int y0, int w, int h) {
+__device__ __forceinline__ void dilate_map(const uint32_t* in, uint32_t* out, const uint32_t* and_map, int kreg,
+                                           int x0, int y0, int w, int h) {
   using L = DetectLayout<TW, TH>;
   for (int t = threadIdx.x; t < L::MW; t += kThreads) {
     const int row = t / L::NW, j = t - row * L::NW;
-    const uint32_t v = in[t];
-    const uint32_t l = j > 0 ? in[t - 1] : 0u;
-    const uint32_t r = j < L::NW - 1 ? in[t + 1] : 0u;
-    uint32_t o = v;
-#pragma unroll
-    for (int d = 1; d <= R; ++d) o |= (v << d) | (l >> (32 - d)) | (v >> d) | (r << (32 - d));
-    tmp[t] = o;
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < L::MW; t += kThreads) {
-    const int row = t / L::NW, j = t - row * L::NW;
-    uint32_t o = 0;
+    uint32_t a = 0, l = 0, r = 0;  // vertical ORs of words j, j-1, j+1
 #pragma unroll
     for (int d = -R; d <= R; ++d) {
       const int rr = row + d;
-      if (rr >= 0 && rr < L::JH) o |= tmp[rr * L::NW + j];
+      if (rr < 0 || rr >= L::JH) continue;
+      const uint32_t* p = in + rr * L::NW + j;
+      a |= p[0];
+      if (j > 0) l |= p[-1];
+      if (j < L::NW - 1) r |= p[1];
     }
-    const int y = y0 - 6 + row;
-    const bool rowok = y >= imax(0, y0 - kreg) && y < min(h, y0 + TH + kreg);
-    const int xw = x0 - 32 + 32 * j;
-    const uint32_t m = rowok ? bits_between(imax(0, x0 - kreg) - xw, min(w, x0 + TW + kreg) - xw) : 0u;
-    out[t] = o & m & (and_map ? and_map[t] : 0xffffffffu);
+    uint32_t o = a;
+#pragma unroll
+    for (int d = 1; d <= R; ++d) o |= (a << d) | (l >> (32 - d)) | (a >> d) | (r << (32 - d));
+    out[t] = o & region_word<TW, TH>(kreg, row, j, x0, y0, w, h) & (and_map ? and_map[t] : 0xffffffffu);
   }
   __syncthreads();
 }
@@ -291,34 +275,98 @@ __device__ __forceinline__ void region_map(uint32_t* out, int kreg, int x0, int 
   using L = DetectLayout<TW, TH>;
   for (int t = threadIdx.x; t < L::MW; t += kThreads) {
     const int row = t / L::NW, j = t - row * L::NW;
-    const int y = y0 - 6 + row;
-    const bool rowok = y >= imax(0, y0 - kreg) && y < min(h, y0 + TH + kreg);
-    const int xw = x0 - 32 + 32 * j;
-    out[t] = rowok ? bits_between(imax(0, x0 - kreg) - xw, min(w, x0 + TW + kreg) - xw) : 0u;
+    out[t] = region_word<TW, TH>(kreg, row, j, x0, y0, w, h);
   }
 }
 
-template <int TW, int TH, bool kMaps, bool kFused>
-__device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, long long tile, char* smem) {
+// Positions of the set bits of up to two bit maps (words given by wordA(t),
+// wordB(t)) -> list entries (row << 8 | bit column), with one block-wide scan.
+template <int NW, int MW, typename FA, typename FB>
+__device__ __forceinline__ void bits_to_lists(FA wordA, uint16_t* listA, int& nA, FB wordB, uint16_t* listB,
+                                              int& nB, int* ws) {
+  constexpr int kPer = (MW + kThreads - 1) / kThreads;
+  const int t0 = threadIdx.x * kPer;
+  uint32_t va[kPer], vb[kPer];
+  int c = 0;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    va[q] = (t0 + q < MW) ? wordA(t0 + q) : 0u;
+    vb[q] = (t0 + q < MW) ? wordB(t0 + q) : 0u;
+    c += __popc(va[q]) | (__popc(vb[q]) << 16);
+  }
+  int total = 0;
+  const int off = block_excl_scan(c, ws, total);
+  nA = total & 0xffff;
+  nB = total >> 16;
+  int oa = off & 0xffff, ob = off >> 16;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int t = t0 + q;
+    const int row = t / NW, j = t - row * NW;
+    uint32_t v = va[q];
+    while (v) {
+      const int b = __ffs(v) - 1;
+      v &= v - 1u;
+      listA[oa++] = uint16_t((row << 8) | (32 * j + b));
+    }
+    v = vb[q];
+    while (v) {
+      const int b = __ffs(v) - 1;
+      v &= v - 1u;
+      listB[ob++] = uint16_t((row << 8) | (32 * j + b));
+    }
+  }
+}
+
+// Issues the asynchronous load of tile t's image region (and, fused, the flag
+// words of an inner tile) into buffer b.
+template <int TW, int TH, bool kFused>
+__device__ __forceinline__ void issue_tile_load(const Frame* __restrict__ frames, int nframes, long long t, int k,
+                                                int niter, char* smem, int b) {
   using L = DetectLayout<TW, TH, kFused>;
-  float* sBuf = reinterpret_cast<float*>(smem) + L::oJ;
+  const int fi = frame_of<false>(frames, nframes, t);
+  const Frame& f = frames[fi];
+  const long long tile = t - f.tile0;
+  const int ty = int(tile / f.tiles_x), tx = int(tile - (long long)ty * f.tiles_x);
+  const int x0 = tx * TW, y0 = ty * TH, w = f.w, h = f.h;
+  const float* src = iter_src(f, kFused ? k - 1 : k, niter);
+  float* buf = reinterpret_cast<float*>(smem) + (b ? L::oB1 : L::oB0);
+  for (int i = threadIdx.x; i < L::JP * L::JR; i += kThreads) {
+    const int iy = i / L::JP, ix = i - iy * L::JP;
+    const int gx = clampi(x0 - L::HALO + ix, 0, w - 1), gy = clampi(y0 - L::HALO + iy, 0, h - 1);
+    cp_async4(buf + i, src + size_t(gy) * w + gx);
+  }
+  if (kFused && x0 - 8 >= 0 && x0 + TW + 8 <= w && y0 - 8 >= 0 && y0 + TH + 8 <= h) {
+    const uint32_t* Mb = mask_bits(f, k - 1);
+    uint32_t* fl = reinterpret_cast<uint32_t*>(smem + (b ? L::oF1 : L::oF0));
+    for (int i = threadIdx.x; i < L::MWF; i += kThreads) {
+      const int row = i / L::NW, j = i - row * L::NW;
+      cp_async4(fl + i, Mb + size_t(y0 - 8 + row) * f.wpr + (x0 >> 5) - 1 + j);
+    }
+  }
+  cp_async_commit();
+}
+
+template <int TW, int TH, bool kMaps, bool kFused>
+__device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, long long tile, char* smem, int b) {
+  using L = DetectLayout<TW, TH, kFused>;
+  float* sBuf = reinterpret_cast<float*>(smem) + (b ? L::oB1 : L::oB0);
   float* sJ = sBuf + L::JOFF;  // R6 of J, row pitch L::JP
   float* sS = reinterpret_cast<float*>(smem) + L::oS;
   float* sCM = sS;  // column medians; dead before S is written
   float* sM3 = reinterpret_cast<float*>(smem) + L::oM3;
   float* sN = reinterpret_cast<float*>(smem) + L::oN;
   float* sSp = reinterpret_cast<float*>(smem) + L::oSp;
+  uint32_t* mFl = reinterpret_cast<uint32_t*>(smem + (b ? L::oF1 : L::oF0));  // fused: M_{k-1} over R8 rows
   uint32_t* bits = reinterpret_cast<uint32_t*>(smem + L::oBits);
   uint32_t* mHot = bits + 0 * L::MW;
   uint32_t* mAct = bits + 1 * L::MW;
-  uint32_t* mTmp = bits + 2 * L::MW;
   uint32_t* mNeedSp = bits + 3 * L::MW;
   uint32_t* mNeedS = bits + 4 * L::MW;
   uint32_t* mTest = bits + 5 * L::MW;
   uint32_t* mNeedM3 = bits + 6 * L::MW;
   uint32_t* mG1 = bits + 7 * L::MW;
   uint32_t* mG2 = bits + 8 * L::MW;
-  uint32_t* mFl = bits + 9 * L::MW;  // fused: M_{k-1} over R8 rows
   uint16_t* L0 = reinterpret_cast<uint16_t*>(smem + L::oL0);
   uint16_t* L1 = reinterpret_cast<uint16_t*>(smem + L::oL1);
   uint16_t* L2 = reinterpret_cast<uint16_t*>(smem + L::oL2);
@@ -327,47 +375,28 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   const int w = f.w, h = f.h;
   const int ty = int(tile / f.tiles_x), tx = int(tile - (long long)ty * f.tiles_x);
   const int x0 = tx * TW, y0 = ty * TH;
-  const float* __restrict__ J = iter_src(f, k, niter);
   const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
   const float sigclip = p.sigclip, siglow = __fmul_rn(p.sigfrac, p.sigclip), objlim = p.objlim;
   const float chot = 4.f * sigclip * sigclip * 0.9999f, clow = 4.f * siglow * siglow * 0.9999f;
   const bool edge = (x0 - 6 < 0) || (y0 - 6 < 0) || (x0 + TW + 6 > w) || (y0 + TH + 6 > h);
+  const bool inner = x0 - 8 >= 0 && x0 + TW + 8 <= w && y0 - 8 >= 0 && y0 + TH + 8 <= h;
   const size_t npix = size_t(w) * size_t(h);
   const int tid = threadIdx.x;
 
-  // P0: clear bit maps and counters, S' = -inf, load J over R6 (replicate edge)
-  for (int i = tid; i < (L::kMaps * L::MW + L::MWF) / 4; i += kThreads)
+  // P0: clear bit maps and counters, S' = -inf (the image region is already in sBuf)
+  for (int i = tid; i < L::kMaps * L::MW / 4; i += kThreads)
     reinterpret_cast<uint4*>(bits)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (tid < 4) cnt[tid] = 0;
   for (int i = tid; i < L::W2 * L::H2; i += kThreads) sSp[i] = -INFINITY;
-  if (!kFused) {
-    for (int i = tid; i < L::JW * L::JH; i += kThreads) {
-      const int iy = i / L::JW, ix = i - iy * L::JW;
-      const int gx = clampi(x0 - 6 + ix, 0, w - 1), gy = clampi(y0 - 6 + iy, 0, h - 1);
-      sJ[iy * L::JP + ix] = __ldg(J + size_t(gy) * w + gx);
-    }
-  } else {
-    // Iteration k-1's replacement on R6, fused in front of iteration k's
-    // detection: I_{k-2} and M_{k-1} over R8, flagged R6 pixels replaced in
-    // place; the tile's I_{k-1} goes to the destination of iteration k-1.
+  if (kFused && !inner)
+    for (int i = tid; i < L::MWF; i += kThreads) mFl[i] = 0u;
+  __syncthreads();
+
+  if (kFused) {
+    // Iteration k-1's replacement on R6 from I_{k-2} (sBuf, R8) and M_{k-1} (mFl, R8 rows).
     const int kr = k - 1;
-    const float* __restrict__ Iprev = iter_src(f, kr, niter);
-    const uint32_t* __restrict__ Mb = mask_bits(f, kr);
-    for (int i = tid; i < L::JP * L::JR; i += kThreads) {
-      const int iy = i / L::JP, ix = i - iy * L::JP;
-      const int gx = clampi(x0 - 8 + ix, 0, w - 1), gy = clampi(y0 - 8 + iy, 0, h - 1);
-      sBuf[i] = __ldg(Iprev + size_t(gy) * w + gx);
-    }
-    const bool inner = x0 - 8 >= 0 && x0 + TW + 8 <= w && y0 - 8 >= 0 && y0 + TH + 8 <= h;
-    __syncthreads();  // the maps are clear
-    if (inner) {  // whole words: the bits that matter are all in the frame
-      for (int t = tid; t < L::MWF; t += kThreads) {
-        const int row = t / L::NW, j = t - row * L::NW;
-        mFl[t] = __ldg(Mb + size_t(y0 - 8 + row) * f.wpr + (x0 >> 5) - 1 + j);
-      }
-    }
-    __syncthreads();
     if (!inner) {  // clamped flag of every R8 position (replicate edge)
+      const uint32_t* __restrict__ Mb = mask_bits(f, kr);
       for (int i = tid; i < L::JP * L::JR; i += kThreads) {
         const int iy = i / L::JP, ix = i - iy * L::JP;
         const int gx = clampi(x0 - 8 + ix, 0, w - 1), gy = clampi(y0 - 8 + iy, 0, h - 1);
@@ -376,13 +405,13 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
       }
       __syncthreads();
     }
-    // flagged in-frame R6 positions -> list (entries: R6 row << 8 | bit column)
-    for (int t = tid; t < L::MW; t += kThreads) {
-      const int row = t / L::NW, j = t - row * L::NW;
-      mTmp[t] = mFl[(row + 2) * L::NW + j] & region_word<TW, TH>(6, row, j, x0, y0, w, h);
-    }
-    __syncthreads();
-    const int nR = bits_to_list<L::NW, L::MW>(mTmp, L0, cnt + 4);
+    int nR = 0, nDummy = 0;
+    bits_to_lists<L::NW, L::MW>(
+        [&](int t) {  // flagged in-frame R6 positions
+          const int row = t / L::NW, j = t - row * L::NW;
+          return mFl[(row + 2) * L::NW + j] & region_word<TW, TH>(6, row, j, x0, y0, w, h);
+        },
+        L0, nR, [](int) { return 0u; }, L1, nDummy, cnt + 4);
     __syncthreads();
     float* val = sS;  // scratch for the replacement values (the S / med3 area is free here)
     unsigned int none_left = 0;
@@ -451,9 +480,9 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
         const int sx = clampi(gx, 0, w - 1) - (x0 - 6), sy = clampi(gy, 0, h - 1) - (y0 - 6);
         sJ[iy * L::JP + ix] = sJ[sy * L::JP + sx];
       }
+      __syncthreads();
     }
   }
-  __syncthreads();
 
   if (kMaps) {
     region_map<TW, TH>(mAct, 2, x0, y0, w, h);
@@ -492,13 +521,14 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
     __syncthreads();
 
     // needS' = dilate5(hot) & act;  needS = dilate5(needS') within R4 and the frame
-    dilate_map<TW, TH, 2>(mHot, mTmp, mNeedSp, mAct, 2, x0, y0, w, h);
-    dilate_map<TW, TH, 2>(mNeedSp, mTmp, mNeedS, nullptr, 4, x0, y0, w, h);
+    dilate_map<TW, TH, 2>(mHot, mNeedSp, mAct, 2, x0, y0, w, h);
+    dilate_map<TW, TH, 2>(mNeedSp, mNeedS, nullptr, 4, x0, y0, w, h);
   }
 
   // lists: L0 <- needS (R4), L2 <- needS' (R2)
-  const int nS = bits_to_list<L::NW, L::MW>(mNeedS, L0, cnt + 4);
-  const int nSp = bits_to_list<L::NW, L::MW>(mNeedSp, L2, cnt + 4);
+  int nS = 0, nSp = 0;
+  bits_to_lists<L::NW, L::MW>([&](int t) { return mNeedS[t]; }, L0, nS, [&](int t) { return mNeedSp[t]; }, L2,
+                              nSp, cnt + 4);
   __syncthreads();
   if (tid == 0 && f.work) {
     unsigned long long* wk = f.work + 5 * (k - 1);
@@ -580,9 +610,11 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
     region_map<TW, TH>(mNeedM3, 5, x0, y0, w, h);
     __syncthreads();
   } else {
-    dilate_map<TW, TH, 3>(mTest, mTmp, mNeedM3, nullptr, 5, x0, y0, w, h);
+    dilate_map<TW, TH, 3>(mTest, mNeedM3, nullptr, 5, x0, y0, w, h);
   }
-  const int nM3 = bits_to_list<L::NW, L::MW>(mNeedM3, L0, cnt + 4);
+  int nM3 = 0, nDummy = 0;
+  bits_to_lists<L::NW, L::MW>([&](int t) { return mNeedM3[t]; }, L0, nM3, [](int) { return 0u; }, L2, nDummy,
+                              cnt + 4);
   __syncthreads();
   if (tid == 0 && f.work) {
     atomicAdd(f.work + 5 * (k - 1) + 2, (unsigned long long)nM3);
@@ -662,7 +694,7 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   }
   __syncthreads();
 
-  // P11: the tile's flag words
+  // P11: the tile's flag words, M_k = M_{k-1} | g2
   constexpr int kWordsPerRow = TW / 32;
   unsigned int new_flags = 0;
   for (int wi = tid; wi < kWordsPerRow * TH; wi += kThreads) {
@@ -676,12 +708,12 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
     new_flags += __popc(g2w & ~prev);
     if (kMaps) {
       const uint32_t g1w = mG1[(r + 6) * L::NW + 1 + wc];
-      for (int b = 0; b < 32; ++b) {
-        const int gx = x0 + 32 * wc + b;
+      for (int bb = 0; bb < 32; ++bb) {
+        const int gx = x0 + 32 * wc + bb;
         if (gx >= w) break;
         const size_t o = size_t(gy) * w + gx;
-        f.maps[9 * npix + o] = ((g1w >> b) & 1u) ? 1.f : 0.f;
-        f.maps[10 * npix + o] = ((g2w >> b) & 1u) ? 1.f : 0.f;
+        f.maps[9 * npix + o] = ((g1w >> bb) & 1u) ? 1.f : 0.f;
+        f.maps[10 * npix + o] = ((g2w >> bb) & 1u) ? 1.f : 0.f;
       }
     }
   }
@@ -693,10 +725,16 @@ template <int TW, int TH, bool kMaps, bool kFused = false>
 __global__ void __launch_bounds__(kThreads) detect_kernel(const Frame* __restrict__ frames, int nframes,
                                                           long long ntiles, Params p, int k, int niter) {
   extern __shared__ __align__(16) char smem[];
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  long long t = blockIdx.x;
+  if (t < ntiles) issue_tile_load<TW, TH, kFused>(frames, nframes, t, k, niter, smem, 0);
+  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+    cp_async_wait_all();
+    __syncthreads();  // tile t's image region has landed in buffer it & 1
+    const long long tn = t + gridDim.x;
+    if (tn < ntiles) issue_tile_load<TW, TH, kFused>(frames, nframes, tn, k, niter, smem, (it + 1) & 1);
     const int fi = frame_of<false>(frames, nframes, t);
     const Frame f = frames[fi];
-    detect_tile<TW, TH, kMaps, kFused>(f, p, k, niter, t - f.tile0, smem);
+    detect_tile<TW, TH, kMaps, kFused>(f, p, k, niter, t - f.tile0, smem, it & 1);
     __syncthreads();
   }
 }
