@@ -382,9 +382,6 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   const bool inner = x0 - 8 >= 0 && x0 + TW + 8 <= w && y0 - 8 >= 0 && y0 + TH + 8 <= h;
   const size_t npix = size_t(w) * size_t(h);
   const int tid = threadIdx.x;
-  // List entries are spread over all warps (entry lane * kWarps + warp), so a
-  // short list costs one network latency per phase instead of several.
-  const int jperm = (tid & 31) * (kThreads / 32) + (tid >> 5);
 
   // P0: clear bit maps and counters, S' = -inf (the image region is already in sBuf)
   for (int i = tid; i < L::kMaps * L::MW / 4; i += kThreads)
@@ -418,7 +415,7 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
     __syncthreads();
     float* val = sS;  // scratch for the replacement values (the S / med3 area is free here)
     unsigned int none_left = 0;
-    for (int j = jperm; j < nR; j += kThreads) {
+    for (int j = tid; j < nR; j += kThreads) {
       const int e = L0[j];
       const int r6 = e >> 8, xb = e & 255;
       const int cy = r6 + 2, cx = xb - 24;  // R8 coordinates
@@ -542,7 +539,7 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   }
 
   // P6: (a)+(b) at the listed positions: m5, N, L+, S
-  for (int j = jperm; j < nS; j += kThreads) {
+  for (int j = tid; j < nS; j += kThreads) {
     const int e = L0[j];
     const int iy = (e >> 8) - 2, ix = (e & 255) - 28;  // R4 coordinates
     const int i = iy * L::W4 + ix;
@@ -581,7 +578,7 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
 
   // P7: S' = S - med5(S) at the listed R2 positions; list the candidate tests (S' > sigclip)
   for (int j0 = 0; j0 < nSp; j0 += kThreads) {
-    const int j = j0 + jperm;
+    const int j = j0 + tid;
     bool test = false;
     int i = 0;
     if (j < nSp) {
@@ -625,7 +622,7 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   }
 
   // P9: med3 at the listed positions
-  for (int j = jperm; j < nM3; j += kThreads) {
+  for (int j = tid; j < nM3; j += kThreads) {
     const int e = L0[j];
     const int iy = (e >> 8) - 1, ix = (e & 255) - 27;  // R5 coordinates
     const int cx = ix + 1, cy = iy + 1;                 // centre in sJ
@@ -654,7 +651,7 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   // P10: (c)+(d) at the candidate tests: F, the objlim statistic, and for each
   // candidate the two growths it causes inside the tile (bits of g2)
   const int nT = cnt[0];
-  for (int j = jperm; j < nT; j += kThreads) {
+  for (int j = tid; j < nT; j += kThreads) {
     const int i = L1[j];
     const int iy = i / L::W2, ix = i - iy * L::W2;
     const int mx = ix + 3, my = iy + 3;  // centre in sM3
