@@ -69,7 +69,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="crb", choices=["crb", "reference"])
     ap.add_argument("--workload", default="batch64",
-                    choices=["batch64", "single4096", "single800", "mosaic16384", "triple4096"])
+                    choices=["batch64", "single4096", "single800", "mosaic16384", "triple4096", "serving"])
+    ap.add_argument("--rates", default="50,200,500,1000,2000", help="serving: arrival rates, frames/s")
+    ap.add_argument("--serve-frames", type=int, default=0, help="serving: frames per rate (0: ~4 s of arrivals)")
     ap.add_argument("--tile-shape", type=int, default=0)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / per-frame / cpu legs")
     return ap.parse_args()
@@ -179,6 +181,91 @@ def cpu_baseline(recipes, budget_s=12.0):
                       f"{oracle.max_threads()} threads, {t_tot:.1f} s"}
 
 
+def serve_run(torch, rate, nframes, seed=0, budget=64 << 30, max_inflight=2, max_batch=64):
+    """Poisson arrivals at `rate` frames/s, sizes uniform over the batch sizes, through crb_server.
+
+    A pool of 2 resident frames per size stands in for arriving data (their content does not change the
+    work per pixel much); outputs are recycled as frames finish. Latency = completion - scheduled arrival.
+    """
+    from paper_1008_2192_gb300 import Server
+    from synth import workloads as wl
+    t_arr, recipes = wl.serving_stream(nframes, rate, seed=seed)
+    pool = {}
+    for r in recipes:
+        key = (r["w"], r["h"])
+        if key not in pool:
+            imgs = []
+            for j in range(2):
+                rr = dict(r, index=900000 + len(pool) * 2 + j)
+                imgs.append(torch.from_numpy(wl.make(rr)).cuda())
+            pool[key] = {"imgs": imgs, "free": [], "n_alloc": 0}
+    srv = Server(niter=4, budget_bytes=budget, max_inflight=max_inflight, max_batch=max_batch)
+    lat = [None] * nframes
+    pix = 0
+    busy = {}
+    i = 0
+    t0 = time.perf_counter()
+    pending = None
+    done_n = 0
+    t_last = t0
+    while done_n < nframes:
+        for tag, l_srv, st in srv.poll(block_ms=0):
+            if st != 0:
+                raise RuntimeError(f"served frame {tag} failed with status {st}")
+            key, bufs, t_sub = busy.pop(tag)
+            pool[key]["free"].append(bufs)
+            lat[tag] = (t_sub - (t0 + t_arr[tag])) + l_srv
+            done_n += 1
+            t_last = time.perf_counter()
+        now = time.perf_counter() - t0
+        if pending is None and i < nframes and now >= t_arr[i]:
+            pending = i
+            i += 1
+        if pending is not None:
+            r = recipes[pending]
+            key = (r["w"], r["h"])
+            p = pool[key]
+            if not p["free"] and p["n_alloc"] < 16:
+                img0 = p["imgs"][0]
+                p["free"].append((torch.empty_like(img0), torch.empty(img0.shape, dtype=torch.uint8, device="cuda")))
+                p["n_alloc"] += 1
+            if p["free"]:
+                bufs = p["free"].pop()
+                img = p["imgs"][pending % 2]
+                if srv.submit(img, bufs[0], bufs[1], tag=pending, gain=r["gain"], readnoise=r["readnoise"]):
+                    busy[pending] = (key, bufs, time.perf_counter())
+                    pix += img.numel()
+                    pending = None
+                    continue
+                p["free"].append(bufs)
+        time.sleep(0.0002)
+    stats = srv.stats()
+    srv.close()
+    span = t_last - t0
+    lat = np.array(lat)
+    return {"rate_hz": rate, "frames": nframes, "mpix_per_s": pix / span / 1e6,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "waves": stats["waves"], "max_wave": stats["max_wave"], "peak_resident_gb": stats["peak_resident_bytes"] / 1e9}
+
+
+def run_serving(args):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rates = [float(x) for x in args.rates.split(",")]
+    res = []
+    for rate in rates:
+        n = args.serve_frames or int(min(4000, max(200, rate * 4)))
+        res.append(serve_run(torch, rate, n))
+    best = max(res, key=lambda r: r["mpix_per_s"])
+    line = {"metric": "Mpix/s served at niter=4 (continuous batching, 1 GB300); p50/p99 latency",
+            "value": best["mpix_per_s"], "unit": "Mpix/s", "n_gpus": 1, "steps": len(rates), "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Poisson arrivals, sizes uniform over 800x800, 1024x1024, 2048x4096, 4096x4096; "
+                                   "64 GB budget, 2 wave slots, waves of up to 64 frames"},
+            "serving": res}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle, timed on this host's cores, on 800x800 frames of the workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -216,6 +303,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "serving":
+        run_serving(args)
         return
     import torch
     import torch.distributed as dist
@@ -328,6 +418,10 @@ def main():
         pf_ms = a.elapsed_time(b) / k2
         extras["per_frame"] = {"value": world * npix / (pf_ms * 1e-3) / 1e6, "unit": "Mpix/s",
                                "ms_per_step": pf_ms}
+        # serving summary: continuous batching of Poisson arrivals (p50/p99 latency)
+        del plain, cl_plain
+        torch.cuda.empty_cache()
+        extras["serving"] = serve_run(torch, 1000.0, 2000)
 
     peaks = measured_peaks()
     det_avg_ms = det_ms / max(det_n, 1)

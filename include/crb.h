@@ -171,6 +171,43 @@ int crb_alu_peak(double* ops2_per_s, double* ops3_per_s, cudaStream_t stream);
 int crb_num_tile_shapes(void);
 int crb_tile_shape(int index, int* tile_w, int* tile_h);
 
+/* ---- Serving: continuous batching of frames that arrive over time ----------
+ * The paper's director collects each actor's result as soon as it is ready,
+ * without a barrier (Sec. 6.2, 6.3.3). The server does the same on one GPU:
+ * submitted frames are queued; a worker thread packs everything queued into
+ * the next wave (one crb_clean_batch call, at most max_batch frames) whenever
+ * one of max_inflight wave slots is free. Each slot has its own stream and
+ * context, so waves overlap on the GPU. Frames and outputs are device buffers
+ * owned by the caller, which keeps them resident until the frame is reported
+ * done. Results are bit-identical to crb_clean on the same frame. */
+typedef struct crb_server crb_server;
+
+/* Creates a server with the cleaning parameters of crb_create_ex (opts may be
+ * NULL). budget_bytes caps the device memory of the admitted, not yet done
+ * frames, counted as 13 bytes per pixel (input, output, mask, workspace) plus
+ * flag bits. 1 <= max_inflight <= 16, max_batch >= 1. NULL on error. */
+crb_server* crb_server_create(float gain, float readnoise, float sigclip, float sigfrac, float objlim, int niter,
+                              const crb_options* opts, size_t budget_bytes, int max_inflight, int max_batch);
+
+/* Queues one frame (device pointers, as crb_clean) with its own gain and read
+ * noise under an opaque tag. Returns CRB_OK, CRB_EINVAL, or CRB_EBUSY when
+ * admitting it would exceed the budget (poll, then submit again); an earlier
+ * device failure of the server is returned as its status. Thread-safe. */
+int crb_server_submit(crb_server* srv, const float* img, int w, int h, float gain, float readnoise,
+                      float* out_clean, uint8_t* out_mask, uint64_t tag);
+
+/* Moves up to max finished frames out of the server: their tags, and (if not
+ * NULL) the seconds from submission to completion and their status. Waits up
+ * to block_ms for at least one if none is finished. Returns the count, or -1. */
+int crb_server_poll(crb_server* srv, uint64_t* done_tags, double* latency_s, int* status, int max, int block_ms);
+
+/* Counters: submitted, done, waves launched, largest wave, rejected submissions,
+ * resident bytes, peak resident bytes, queued frames. Returns the count written. */
+int crb_server_stats(crb_server* srv, long long* out, int max);
+
+/* Stops the worker after the waves in flight complete and frees the server. */
+void crb_server_destroy(crb_server* srv);
+
 /* Message of the last error on this host thread ("" if none). */
 const char* crb_last_error(void);
 const char* crb_strerror(int status);

@@ -4,4 +4,4 @@
 CUDA library is loaded lazily on first use; nothing here runs on the CPU.
 """
 
-from .api import Cleaner  # noqa: F401
+from .api import Cleaner, Server  # noqa: F401

@@ -45,6 +45,13 @@ SIGNATURES = {
     "crb_profile_read": (_ci, [_vp, ctypes.POINTER(ctypes.c_double), _PI, ctypes.POINTER(ctypes.c_double), _PI,
                                _ci]),
     "crb_alu_peak": (_ci, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _vp]),
+    "crb_server_create": (_vp, [_cf, _cf, _cf, _cf, _cf, _ci, ctypes.POINTER(crb_options), ctypes.c_size_t, _ci,
+                                _ci]),
+    "crb_server_submit": (_ci, [_vp, _vp, _ci, _ci, _cf, _cf, _vp, _vp, ctypes.c_uint64]),
+    "crb_server_poll": (_ci, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double), _PI, _ci,
+                              _ci]),
+    "crb_server_stats": (_ci, [_vp, ctypes.POINTER(ctypes.c_longlong), _ci]),
+    "crb_server_destroy": (None, [_vp]),
     "crb_num_tile_shapes": (_ci, []),
     "crb_tile_shape": (_ci, [_ci, _PI, _PI]),
     "crb_last_error": (ctypes.c_char_p, []),

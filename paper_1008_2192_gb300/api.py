@@ -143,3 +143,63 @@ def alu_peak(stream=None):
     a, b = ctypes.c_double(), ctypes.c_double()
     check(_lib.load().crb_alu_peak(ctypes.byref(a), ctypes.byref(b), _stream(stream)), "crb_alu_peak")
     return a.value, b.value
+
+
+class Server:
+    """Continuous-batching server (crb_server_*): submit device frames, poll finished tags."""
+
+    def __init__(self, gain=7.0, readnoise=5.0, sigclip=4.5, sigfrac=0.5, objlim=1.0, niter=4, *,
+                 budget_bytes=64 << 30, max_inflight=2, max_batch=64, objlim_form=0, tile_shape=0):
+        lib = _lib.load()
+        opt = _lib.crb_options(int(objlim_form), 0, int(tile_shape), 0, 0, 0)
+        h = lib.crb_server_create(gain, readnoise, sigclip, sigfrac, objlim, int(niter), ctypes.byref(opt),
+                                  int(budget_bytes), int(max_inflight), int(max_batch))
+        if not h:
+            raise ValueError("crb_server_create: " + lib.crb_last_error().decode())
+        self._h = ctypes.c_void_p(h)
+        self._keep = {}  # tag -> tensors kept alive until done
+
+    def submit(self, img, out, mask, tag, gain, readnoise):
+        """Queues a frame; returns False when the memory budget refuses it (CRB_EBUSY)."""
+        _check_img(img)
+        h, w = img.shape
+        rc = _lib.load().crb_server_submit(self._h, _ptr(img), w, h, float(gain), float(readnoise), _ptr(out),
+                                           _ptr(mask), int(tag))
+        if rc == _lib.CRB_EBUSY:
+            return False
+        check(rc, "crb_server_submit")
+        self._keep[int(tag)] = (img, out, mask)
+        return True
+
+    def poll(self, max_n=256, block_ms=0):
+        """[(tag, latency seconds, status)] of frames finished since the last poll."""
+        tags = (ctypes.c_uint64 * max_n)()
+        lat = (ctypes.c_double * max_n)()
+        st = (ctypes.c_int * max_n)()
+        n = _lib.load().crb_server_poll(self._h, tags, lat, st, max_n, int(block_ms))
+        if n < 0:
+            raise RuntimeError("crb_server_poll failed")
+        out = []
+        for i in range(n):
+            self._keep.pop(int(tags[i]), None)
+            out.append((int(tags[i]), float(lat[i]), int(st[i])))
+        return out
+
+    def stats(self):
+        buf = (ctypes.c_longlong * 8)()
+        _lib.load().crb_server_stats(self._h, buf, 8)
+        keys = ("submitted", "done", "waves", "max_wave", "rejected", "resident_bytes", "peak_resident_bytes",
+                "queued")
+        return dict(zip(keys, (int(v) for v in buf)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().crb_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

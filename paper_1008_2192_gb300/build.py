@@ -50,7 +50,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
                "-I", os.path.join(ROOT, "include"), "-I", GEN,
-               os.path.join(CSRC, "crb.cu"), os.path.join(CSRC, "noalloc.cu"), "-o", tmp]
+               os.path.join(CSRC, "crb.cu"), os.path.join(CSRC, "noalloc.cu"), os.path.join(CSRC, "serve.cu"),
+               "-o", tmp]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -68,3 +68,13 @@ def test_networks_exhaustive_zero_one():
     for (_, n, rank) in g.SPECS:
         c, d, order, out = g.best_network(n, rank)
         g.verify(n, rank, d, order, out, exhaustive=True)
+
+
+def test_server_rejects_invalid_arguments():
+    lib = L.load()
+    opt = L.crb_options(0, 0, 0, 0, 0, 0)
+    assert not lib.crb_server_create(7.0, 5.0, 4.5, 0.5, 1.0, 4, ctypes.byref(opt), 1 << 30, 0, 8)
+    assert not lib.crb_server_create(7.0, 5.0, 4.5, 0.5, 1.0, 4, ctypes.byref(opt), 1 << 30, 2, 0)
+    assert not lib.crb_server_create(7.0, 5.0, 4.5, 0.5, 1.0, 4, None, 0, 2, 8)
+    assert lib.crb_server_submit(None, None, 1, 1, 7.0, 5.0, None, None, 0) == L.CRB_EINVAL
+    assert lib.crb_server_poll(None, None, None, None, 0, 0) == -1

@@ -1,0 +1,84 @@
+"""Serving: continuous batching gives each frame the same result as cleaning it alone."""
+
+import time
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1008_2192_gb300 import Cleaner, Server  # noqa: E402
+
+
+def _frames(n, seed=0):
+    rng = np.random.default_rng(seed)
+    sizes = [(256, 256), (512, 384), (800, 800), (1024, 200), (97, 311), (640, 480)]
+    out = []
+    for i in range(n):
+        w, h = sizes[i % len(sizes)]
+        g = float(np.float32(rng.uniform(1, 7)))
+        r = float(np.float32(rng.uniform(3, 10)))
+        img = synth.frame(w, h, seed=seed, index=i, sky=100.0, gain=g, readnoise=r)
+        out.append((torch.from_numpy(img).cuda(), g, r))
+    return out
+
+
+def test_served_results_equal_solo():
+    frames = _frames(24)
+    srv = Server(niter=4, budget_bytes=2 << 30, max_inflight=2, max_batch=5)
+    outs = {}
+    rng = np.random.default_rng(3)
+    for i, (img, g, r) in enumerate(frames):
+        o = torch.empty_like(img)
+        m = torch.empty(img.shape, dtype=torch.uint8, device="cuda")
+        assert srv.submit(img, o, m, tag=i, gain=g, readnoise=r)
+        outs[i] = (o, m)
+        time.sleep(float(rng.uniform(0, 0.004)))  # arrivals while earlier waves run
+    done = {}
+    t0 = time.time()
+    while len(done) < len(frames) and time.time() - t0 < 60:
+        for tag, lat, st in srv.poll(block_ms=100):
+            assert st == 0 and lat >= 0
+            done[tag] = lat
+    assert len(done) == len(frames)
+    st = srv.stats()
+    assert st["done"] == len(frames) and st["resident_bytes"] == 0 and st["queued"] == 0
+    assert st["waves"] >= 2 and st["max_wave"] >= 2, st  # batches formed and overlapped
+    for i, (img, g, r) in enumerate(frames):
+        c = Cleaner(gain=g, readnoise=r, niter=4)
+        ro, rm = c.clean(img)
+        c.sync()
+        o, m = outs[i]
+        assert torch.equal(o, ro) and torch.equal(m, rm), i
+    srv.close()
+
+
+def test_budget_admission():
+    img = torch.from_numpy(synth.frame(512, 512, seed=1)).cuda()
+    o = torch.empty_like(img)
+    m = torch.empty(img.shape, dtype=torch.uint8, device="cuda")
+    per_frame = 512 * 512 * 13 + 2 * 16 * 512 * 4
+    small = Server(niter=2, budget_bytes=per_frame - 1, max_inflight=1, max_batch=4)
+    assert not small.submit(img, o, m, tag=1, gain=7.0, readnoise=5.0)  # would exceed the budget
+    assert small.stats()["rejected"] == 1
+    small.close()
+    one = Server(niter=2, budget_bytes=per_frame, max_inflight=1, max_batch=4)
+    assert one.submit(img, o, m, tag=7, gain=7.0, readnoise=5.0)
+    got = []
+    t0 = time.time()
+    while not got and time.time() - t0 < 30:
+        got = one.poll(block_ms=100)
+    assert got and got[0][0] == 7 and got[0][2] == 0
+    assert one.stats()["resident_bytes"] == 0
+    assert one.submit(img, o, m, tag=8, gain=7.0, readnoise=5.0)  # budget released
+    t0 = time.time()
+    got = []
+    while not got and time.time() - t0 < 30:
+        got = one.poll(block_ms=100)
+    one.close()
