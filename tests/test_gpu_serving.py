@@ -18,7 +18,7 @@ from paper_1008_2192_gb300 import Cleaner, Server  # noqa: E402
 
 def _frames(n, seed=0):
     rng = np.random.default_rng(seed)
-    sizes = [(256, 256), (512, 384), (800, 800), (1024, 200), (97, 311), (640, 480)]
+    sizes = [(256, 256), (512, 384), (800, 800), (1024, 200), (97, 311), (2048, 1024)]
     out = []
     for i in range(n):
         w, h = sizes[i % len(sizes)]
@@ -39,7 +39,8 @@ def test_served_results_equal_solo():
         m = torch.empty(img.shape, dtype=torch.uint8, device="cuda")
         assert srv.submit(img, o, m, tag=i, gain=g, readnoise=r)
         outs[i] = (o, m)
-        time.sleep(float(rng.uniform(0, 0.004)))  # arrivals while earlier waves run
+        if i % 6 == 5:  # bursts of six arrivals while earlier waves run
+            time.sleep(float(rng.uniform(0, 0.002)))
     done = {}
     t0 = time.time()
     while len(done) < len(frames) and time.time() - t0 < 60:
