@@ -63,9 +63,16 @@ typedef struct {
    * without an unflagged neighbour; the result is then a fixed point, so the
    * output is identical to running all niter iterations. Default 0.            */
   int early_exit;
-  /* Tile shape index (crb_tile_shape); -1 = autotune per frame shape (default 0 = fixed). */
+  /* Tile shape of the detection kernel (index of crb_tile_shape; default 0).
+   * -1 = autotune: the first call with a new signature (the list of frame
+   * sizes and niter) runs the clean once per compiled shape, timing each on
+   * the stream (that call synchronises the stream), and keeps the fastest for
+   * later calls with the same signature. */
   int tile_shape;
-  /* 1: capture the niter loop of crb_clean in a CUDA graph per frame shape and replay it. */
+  /* 1: capture the work of a call (the memsets and the niter loop of launches)
+   * in a CUDA graph once per launch signature and replay it afterwards; the
+   * per-frame descriptors are uploaded before each replay. Ignored while
+   * profiling. */
   int use_graphs;
   /* 1: bracket every kernel launch with CUDA events on the launching stream;
    * read the accumulated device times with crb_profile_read. Default 0.       */

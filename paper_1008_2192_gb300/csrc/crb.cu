@@ -64,6 +64,22 @@ constexpr size_t kReplaceSmem = crb::ReplaceLayout<kRW, kRH>::bytes;
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
+struct GraphKey {
+  int n, niter, shape;
+  bool fuse;
+  long long tiles, rtiles;
+  size_t bits_total;
+  int ncounters, dgrid, fgrid, rgrid;
+  void* ws;
+  void* counters;
+  void* frames;
+  bool operator==(const GraphKey& o) const {
+    return n == o.n && niter == o.niter && shape == o.shape && fuse == o.fuse && tiles == o.tiles &&
+           rtiles == o.rtiles && bits_total == o.bits_total && ncounters == o.ncounters && dgrid == o.dgrid &&
+           fgrid == o.fgrid && rgrid == o.rgrid && ws == o.ws && counters == o.counters && frames == o.frames;
+  }
+};
+
 struct FrameSpec {
   const float* img;
   float* out_clean;
@@ -100,6 +116,11 @@ struct crb_ctx {
   cudaEvent_t upload_ev = nullptr, done_ev = nullptr;
   bool any_call = false;
   int latched = CRB_OK;
+
+  // graphs of the work of a call, by launch signature; autotuned tile shape by frame sizes
+  std::vector<std::pair<GraphKey, cudaGraphExec_t>> graphs;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<std::pair<std::vector<long long>, int>> tuned;
 
   // profiling: event pairs around launches, by kernel kind (0 detect, 1 replace)
   std::vector<cudaEvent_t> ev_pool;
@@ -201,14 +222,63 @@ int ensure_ws(crb_ctx* c, size_t bytes, int ncounters) {
   return CRB_OK;
 }
 
-// Enqueues the whole clean of `specs` (niter iterations) on `stream`.
-int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, cudaStream_t stream) {
-  const int n = int(specs.size());
-  const int shape = (c->opt.tile_shape >= 0 && c->opt.tile_shape < int(detect_shapes().size()))
-                        ? c->opt.tile_shape : 0;
-  const DetectShape& ds = detect_shapes()[size_t(shape)];
+// Work of one call after the descriptors are in device memory: the memsets
+// and kernel launches. Issued on `stream` directly, or into a CUDA graph.
+struct Plan {
+  int n = 0, niter = 0, shape = 0;
+  bool maps = false, fuse = false;
+  long long tiles = 0, rtiles = 0;
+  size_t bits_total = 0;
+  int ncounters = 0;
+  int dgrid = 0, fgrid = 0, rgrid = 0;
+};
 
-  // workspace: per frame, flag bits then (niter >= 2) one image
+int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs, cudaStream_t stream) {
+  const DetectShape& ds = detect_shapes()[size_t(P.shape)];
+  CRB_CUDA(cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * size_t(P.ncounters), stream));
+  if (P.niter == 0) {
+    for (const auto& s : specs) {
+      CRB_CUDA(cudaMemcpyAsync(s.out_clean, s.img, size_t(s.w) * s.h * 4, cudaMemcpyDeviceToDevice, stream));
+      CRB_CUDA(cudaMemsetAsync(s.out_mask, 0, size_t(s.w) * s.h, stream));
+    }
+    return CRB_OK;
+  }
+  CRB_CUDA(cudaMemsetAsync(c->ws, 0, P.bits_total, stream));
+  for (int i = 0; i < P.n; ++i) {
+    const auto& s = specs[size_t(i)];
+    if (s.mprev) {
+      const crb::Frame& f = c->h_frames[i];
+      const long long nwords = (long long)f.wpr * f.h;
+      const int blocks = int((nwords * 32 + 255) / 256 < 65535 ? (nwords * 32 + 255) / 256 : 65535);
+      crb::bytes_to_bits_kernel<<<blocks, 256, 0, stream>>>(s.mprev, f.bits_b, f.w, f.h, f.wpr);  // M_0
+    }
+  }
+  for (int k = 1; k <= P.niter; ++k) {
+    if (P.fuse && k >= 2) {  // replacement of iteration k-1 fused in front of detection k
+      timed(c, 0, stream, [&] {
+        ds.fn_fused<<<P.fgrid, crb::kThreads, ds.smem_fused, stream>>>(c->d_frames, P.n, P.tiles, c->p, k, P.niter);
+      });
+    } else {
+      timed(c, 0, stream, [&] {
+        (P.maps ? ds.fn_maps : ds.fn)<<<P.dgrid, crb::kThreads, ds.smem, stream>>>(c->d_frames, P.n, P.tiles, c->p, k,
+                                                                                     P.niter);
+      });
+    }
+    if (!P.fuse || k == P.niter) {
+      timed(c, 1, stream, [&] {
+        kReplace<<<P.rgrid, crb::kThreads, kReplaceSmem, stream>>>(c->d_frames, P.n, P.rtiles, k, P.niter,
+                                                                   k <= 2 ? 1 : 0);
+      });
+    }
+  }
+  CRB_CUDA(cudaGetLastError());
+  return CRB_OK;
+}
+
+// Lays out the workspace and writes the descriptors (host), for tile shape `shape`.
+int prepare(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, int shape, Plan& P) {
+  const int n = int(specs.size());
+  const DetectShape& ds = detect_shapes()[size_t(shape)];
   std::vector<size_t> off_bits(static_cast<size_t>(n)), off_img(static_cast<size_t>(n));
   size_t total = 0;
   for (int i = 0; i < n; ++i) {
@@ -229,8 +299,6 @@ int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, c
   if (rc) return rc;
   rc = ensure_ws(c, total > 0 ? total : 256, ncounters);
   if (rc) return rc;
-
-  if (c->any_call) CRB_CUDA(cudaStreamWaitEvent(stream, c->done_ev, 0));
   CRB_CUDA(cudaEventSynchronize(c->upload_ev));  // the staging buffer is free again
 
   long long tiles = 0, rtiles = 0;
@@ -259,54 +327,125 @@ int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, c
     tiles += (long long)f.tiles_x * ((s.h + ds.th - 1) / ds.th);
     rtiles += (long long)f.rtiles_x * ((s.h + kRH - 1) / kRH);
   }
-  CRB_CUDA(cudaMemcpyAsync(c->d_frames, c->h_frames, sizeof(crb::Frame) * size_t(n), cudaMemcpyHostToDevice,
+  P.n = n;
+  P.niter = niter;
+  P.shape = shape;
+  P.maps = maps;
+  P.fuse = !maps && !c->opt.no_fusion;
+  P.tiles = tiles;
+  P.rtiles = rtiles;
+  P.bits_total = bits_total;
+  P.ncounters = ncounters;
+  P.dgrid = int(std::min<long long>(tiles, (long long)c->num_sms *
+                                               (maps ? c->occ_detect_maps : c->occ_detect)[size_t(shape)]));
+  P.fgrid = int(std::min<long long>(tiles, (long long)c->num_sms * c->occ_fused[size_t(shape)]));
+  P.rgrid = int(std::min<long long>(rtiles, (long long)c->num_sms * c->occ_replace));
+  return CRB_OK;
+}
+
+int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
+  CRB_CUDA(cudaMemcpyAsync(c->d_frames, c->h_frames, sizeof(crb::Frame) * size_t(P.n), cudaMemcpyHostToDevice,
                            stream));
   CRB_CUDA(cudaEventRecord(c->upload_ev, stream));
-  CRB_CUDA(cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * size_t(ncounters), stream));
-  c->last_niter = niter;
-  c->last_nframes = n;
+  c->last_niter = P.niter;
+  c->last_nframes = P.n;
+  return CRB_OK;
+}
 
-  if (niter == 0) {
-    for (const auto& s : specs) {
-      CRB_CUDA(cudaMemcpyAsync(s.out_clean, s.img, size_t(s.w) * s.h * 4, cudaMemcpyDeviceToDevice, stream));
-      CRB_CUDA(cudaMemsetAsync(s.out_mask, 0, size_t(s.w) * s.h, stream));
+// Replays (or captures once) the work of plan P as a CUDA graph on `stream`.
+int launch_graph(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs, cudaStream_t stream) {
+  GraphKey key{P.n, P.niter, P.shape, P.fuse, P.tiles, P.rtiles, P.bits_total, P.ncounters, P.dgrid, P.fgrid,
+               P.rgrid, c->ws, c->d_counters, c->d_frames};
+  for (auto& g : c->graphs)
+    if (g.first == key) {
+      CRB_CUDA(cudaGraphLaunch(g.second, stream));
+      return CRB_OK;
     }
-  } else {
-    CRB_CUDA(cudaMemsetAsync(c->ws, 0, bits_total, stream));
-    for (int i = 0; i < n; ++i) {
-      const auto& s = specs[size_t(i)];
-      if (s.mprev) {
-        const crb::Frame& f = c->h_frames[i];
-        const long long nwords = (long long)f.wpr * f.h;
-        const int blocks = int((nwords * 32 + 255) / 256 < 65535 ? (nwords * 32 + 255) / 256 : 65535);
-        crb::bytes_to_bits_kernel<<<blocks, 256, 0, stream>>>(s.mprev, f.bits_b, f.w, f.h, f.wpr);  // M_0
-      }
-    }
-    const int dgrid = int(std::min<long long>(tiles, (long long)c->num_sms *
-                                                         (maps ? c->occ_detect_maps : c->occ_detect)[size_t(shape)]));
-    const int rgrid = int(std::min<long long>(rtiles, (long long)c->num_sms * c->occ_replace));
-    const bool fuse = !maps && !c->opt.no_fusion;
-    const int fgrid = int(std::min<long long>(tiles, (long long)c->num_sms * c->occ_fused[size_t(shape)]));
-    for (int k = 1; k <= niter; ++k) {
-      if (fuse && k >= 2) {  // replacement of iteration k-1 fused in front of detection k
-        timed(c, 0, stream, [&] {
-          ds.fn_fused<<<fgrid, crb::kThreads, ds.smem_fused, stream>>>(c->d_frames, n, tiles, c->p, k, niter);
-        });
-      } else {
-        timed(c, 0, stream, [&] {
-          (maps ? ds.fn_maps : ds.fn)<<<dgrid, crb::kThreads, ds.smem, stream>>>(c->d_frames, n, tiles, c->p, k,
-                                                                                   niter);
-        });
-      }
-      if (!fuse || k == niter) {
-        timed(c, 1, stream, [&] {
-          kReplace<<<rgrid, crb::kThreads, kReplaceSmem, stream>>>(c->d_frames, n, rtiles, k, niter,
-                                                                   k <= 2 ? 1 : 0);
-        });
-      }
-    }
-    CRB_CUDA(cudaGetLastError());
+  if (!c->cap_stream) CRB_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  CRB_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const int rc = enqueue_work(c, P, specs, c->cap_stream);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+  if (rc != CRB_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
   }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate");
+  if (c->graphs.size() >= 16) {  // keep the cache small
+    cudaGraphExecDestroy(c->graphs.front().second);
+    c->graphs.erase(c->graphs.begin());
+  }
+  c->graphs.emplace_back(key, exec);
+  CRB_CUDA(cudaGraphLaunch(exec, stream));
+  return CRB_OK;
+}
+
+// Enqueues the whole clean of `specs` (niter iterations) on `stream`.
+int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, cudaStream_t stream) {
+  const int nshapes = int(detect_shapes().size());
+  if (c->any_call) CRB_CUDA(cudaStreamWaitEvent(stream, c->done_ev, 0));
+  int shape = c->opt.tile_shape;
+  if (shape >= nshapes) shape = 0;
+  if (shape < 0 && !maps) {
+    // autotuning: the first call of a signature (frame sizes, niter) times every tile shape
+    std::vector<long long> sig{niter};
+    for (const auto& s : specs) {
+      sig.push_back(s.w);
+      sig.push_back(s.h);
+    }
+    shape = -1;
+    for (const auto& t : c->tuned)
+      if (t.first == sig) shape = t.second;
+    if (shape < 0) {
+      float best = 0.f;
+      int best_shape = 0;
+      cudaEvent_t a = nullptr, b = nullptr;
+      CRB_CUDA(cudaEventCreate(&a));
+      CRB_CUDA(cudaEventCreate(&b));
+      for (int sh = 0; sh < nshapes; ++sh) {
+        Plan P;
+        int rc = prepare(c, specs, niter, maps, sh, P);
+        if (rc == CRB_OK) rc = upload(c, P, stream);
+        if (rc == CRB_OK && cudaEventRecord(a, stream) != cudaSuccess) rc = CRB_ECUDA;
+        if (rc == CRB_OK) rc = enqueue_work(c, P, specs, stream);
+        float ms = 0.f;
+        if (rc == CRB_OK && (cudaEventRecord(b, stream) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, a, b) != cudaSuccess))
+          rc = CRB_ECUDA;
+        if (rc != CRB_OK) {
+          cudaEventDestroy(a);
+          cudaEventDestroy(b);
+          return rc;
+        }
+        if (sh == 0 || ms < best) {
+          best = ms;
+          best_shape = sh;
+        }
+      }
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      c->tuned.emplace_back(sig, best_shape);
+      // every trial produced the same outputs; the last one stays
+      CRB_CUDA(cudaEventRecord(c->done_ev, stream));
+      c->any_call = true;
+      return CRB_OK;
+    }
+  }
+  if (shape < 0) shape = 0;
+  Plan P;
+  int rc = prepare(c, specs, niter, maps, shape, P);
+  if (rc) return rc;
+  rc = upload(c, P, stream);
+  if (rc) return rc;
+  if (c->opt.use_graphs && !maps && !c->opt.profile)
+    rc = launch_graph(c, P, specs, stream);
+  else
+    rc = enqueue_work(c, P, specs, stream);
+  if (rc) return rc;
   CRB_CUDA(cudaEventRecord(c->done_ev, stream));
   c->any_call = true;
   return CRB_OK;
@@ -369,6 +508,8 @@ void crb_destroy(crb_ctx* c) {
       cudaEventDestroy(pr.second);
     }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaFree(c->ws);
   cudaFree(c->d_frames);
   cudaFree(c->d_counters);

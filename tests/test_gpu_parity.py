@@ -209,3 +209,22 @@ def test_mosaic_16384_sampled_crops():
     rng = np.random.default_rng(4)
     crops += [(int(rng.integers(0, S - n)), int(rng.integers(0, S - n))) for _ in range(8)]
     _check_crops(img, out, mask, 4, [(y, x, n, n) for (y, x) in crops], params_of(rec))
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+@pytest.mark.parametrize("shape", [0, -1])
+def test_graphs_and_autotune(graphs, shape):
+    """Graph replay and autotuned tile shapes give the plain path's results, call after call."""
+    c = Cleaner(niter=4, use_graphs=graphs, tile_shape=shape)
+    for seed in range(3):
+        img = scene(333, 251, seed=40 + seed)
+        out, mask = gpu_clean(c, img)
+        r32 = oracle.clean(img, params_of({}), 4, precision="f32")
+        assert np.array_equal(mask, r32.mask) and np.array_equal(out, r32.clean), seed
+    imgs = [scene(200, 150, seed=50 + i) for i in range(3)] + [scene(97, 400, seed=60)]
+    for rep in range(2):
+        outs, masks = c.clean_batch([dev(a) for a in imgs])
+        c.sync()
+        for a, o, m in zip(imgs, outs, masks):
+            r32 = oracle.clean(a, params_of({}), 4, precision="f32")
+            assert np.array_equal(host(m), r32.mask) and np.array_equal(host(o), r32.clean)
