@@ -81,6 +81,13 @@ typedef struct {
    * fusing the replacement of iteration k-1 into the detection of iteration k
    * (niter + 1 launches). Same results; for comparison. Default 0.            */
   int no_fusion;
+  /* Detection pipeline. 0 (default): queue pipeline -- a dense bound pass
+   * writes bit planes, and the medians run in separate kernels over global
+   * work queues of the positions that can change a flag. 1: tile pipeline --
+   * one kernel per iteration does all stages of a tile in shared memory (the
+   * form used by crb_iterate's map export and by crb_clean_noalloc). Both
+   * give identical results. */
+  int pipeline;
 } crb_options;
 
 /* Creates a context with the cleaning parameters (Sec. 5 lists gain, readn,
@@ -191,8 +198,8 @@ typedef struct crb_server crb_server;
 
 /* Creates a server with the cleaning parameters of crb_create_ex (opts may be
  * NULL). budget_bytes caps the device memory of the admitted, not yet done
- * frames, counted as 13 bytes per pixel (input, output, mask, workspace) plus
- * flag bits. 1 <= max_inflight <= 16, max_batch >= 1. NULL on error. */
+ * frames, each counted as crb_server_frame_bytes(w, h) (input, output, mask
+ * and workspace). 1 <= max_inflight <= 16, max_batch >= 1. NULL on error. */
 crb_server* crb_server_create(float gain, float readnoise, float sigclip, float sigfrac, float objlim, int niter,
                               const crb_options* opts, size_t budget_bytes, int max_inflight, int max_batch);
 
@@ -207,6 +214,11 @@ int crb_server_submit(crb_server* srv, const float* img, int w, int h, float gai
  * NULL) the seconds from submission to completion and their status. Waits up
  * to block_ms for at least one if none is finished. Returns the count, or -1. */
 int crb_server_poll(crb_server* srv, uint64_t* done_tags, double* latency_s, int* status, int max, int block_ms);
+
+/* Device bytes a w x h frame counts against the server budget: 9 per pixel of
+ * the caller's buffers, 32 per pixel of workspace, and 5 bit planes (0 for
+ * invalid sizes). */
+size_t crb_server_frame_bytes(int w, int h);
 
 /* Counters: submitted, done, waves launched, largest wave, rejected submissions,
  * resident bytes, peak resident bytes, queued frames. Returns the count written. */

@@ -34,10 +34,10 @@ class Cleaner:
 
     def __init__(self, gain=7.0, readnoise=5.0, sigclip=4.5, sigfrac=0.5, objlim=1.0, niter=4, *,
                  objlim_form=0, early_exit=False, tile_shape=0, use_graphs=False, profile=False,
-                 fusion=True):
+                 fusion=True, pipeline="queue"):
         lib = _lib.load()
         opt = _lib.crb_options(int(objlim_form), int(bool(early_exit)), int(tile_shape), int(bool(use_graphs)),
-                               int(bool(profile)), int(not fusion))
+                               int(bool(profile)), int(not fusion), 0 if pipeline == "queue" else 1)
         h = lib.crb_create_ex(gain, readnoise, sigclip, sigfrac, objlim, int(niter), ctypes.byref(opt))
         if not h:
             raise ValueError("crb_create_ex: " + lib.crb_last_error().decode())
@@ -151,7 +151,7 @@ class Server:
     def __init__(self, gain=7.0, readnoise=5.0, sigclip=4.5, sigfrac=0.5, objlim=1.0, niter=4, *,
                  budget_bytes=64 << 30, max_inflight=2, max_batch=64, objlim_form=0, tile_shape=0):
         lib = _lib.load()
-        opt = _lib.crb_options(int(objlim_form), 0, int(tile_shape), 0, 0, 0)
+        opt = _lib.crb_options(int(objlim_form), 0, int(tile_shape), 0, 0, 0, 0)
         h = lib.crb_server_create(gain, readnoise, sigclip, sigfrac, objlim, int(niter), ctypes.byref(opt),
                                   int(budget_bytes), int(max_inflight), int(max_batch))
         if not h:

@@ -6,6 +6,7 @@
 // context are ordered (each waits for the previous one's completion event),
 // so descriptors and workspace can be reused.
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -14,6 +15,7 @@
 #include "alu_peak.cuh"
 #include "crb.h"
 #include "kernels.cuh"
+#include "pipeline.cuh"
 
 namespace {
 
@@ -66,7 +68,7 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 struct GraphKey {
   int n, niter, shape;
-  bool fuse;
+  bool fuse, queue;
   long long tiles, rtiles;
   size_t bits_total;
   int ncounters, dgrid, fgrid, rgrid;
@@ -74,7 +76,8 @@ struct GraphKey {
   void* counters;
   void* frames;
   bool operator==(const GraphKey& o) const {
-    return n == o.n && niter == o.niter && shape == o.shape && fuse == o.fuse && tiles == o.tiles &&
+    return n == o.n && niter == o.niter && shape == o.shape && fuse == o.fuse && queue == o.queue &&
+           tiles == o.tiles &&
            rtiles == o.rtiles && bits_total == o.bits_total && ncounters == o.ncounters && dgrid == o.dgrid &&
            fgrid == o.fgrid && rgrid == o.rgrid && ws == o.ws && counters == o.counters && frames == o.frames;
   }
@@ -102,6 +105,7 @@ struct crb_ctx {
   crb_options opt{};
   int device = 0, num_sms = 0;
   std::vector<int> occ_detect, occ_detect_maps, occ_fused;
+  int occ_q[7] = {1, 1, 1, 1, 1, 1, 1};  // queue pipeline kernels
   int occ_replace = 0;
 
   void* ws = nullptr;
@@ -145,6 +149,23 @@ int init_ctx(crb_ctx* c) {
     c->occ_detect.push_back(occ > 0 ? occ : 1);
     c->occ_detect_maps.push_back(occm > 0 ? occm : 1);
     c->occ_fused.push_back(occf > 0 ? occf : 1);
+  }
+  {
+    int o = 0;
+    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, crb::bound_kernel, 256, 0));
+    c->occ_q[0] = o > 0 ? o : 1;
+    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, crb::need_kernel, 256, 0));
+    c->occ_q[1] = o > 0 ? o : 1;
+    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, crb::s_kernel, 256, 0));
+    c->occ_q[2] = o > 0 ? o : 1;
+    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, crb::sp_kernel, 256, 0));
+    c->occ_q[3] = o > 0 ? o : 1;
+    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, crb::m3need_kernel, 256, 0));
+    c->occ_q[4] = o > 0 ? o : 1;
+    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, crb::m3_kernel, 256, 0));
+    c->occ_q[5] = o > 0 ? o : 1;
+    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, crb::cand_kernel, 256, 0));
+    c->occ_q[6] = o > 0 ? o : 1;
   }
   CRB_CUDA(cudaFuncSetAttribute(kReplace, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kReplaceSmem)));
   CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_replace, kReplace, crb::kThreads, kReplaceSmem));
@@ -226,11 +247,13 @@ int ensure_ws(crb_ctx* c, size_t bytes, int ncounters) {
 // and kernel launches. Issued on `stream` directly, or into a CUDA graph.
 struct Plan {
   int n = 0, niter = 0, shape = 0;
-  bool maps = false, fuse = false;
+  bool maps = false, fuse = false, queue = false;
   long long tiles = 0, rtiles = 0;
-  size_t bits_total = 0;
+  size_t bits_total = 0;  // bytes from the start of the workspace that start at zero
   int ncounters = 0;
   int dgrid = 0, fgrid = 0, rgrid = 0;
+  long long nblocks = 0, npix = 0;  // queue pipeline: word blocks, pixels
+  crb::Queues Q{};
 };
 
 int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs, cudaStream_t stream) {
@@ -244,6 +267,29 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
     return CRB_OK;
   }
   CRB_CUDA(cudaMemsetAsync(c->ws, 0, P.bits_total, stream));
+  if (P.queue) {
+    const int g0 = int(std::min<long long>(P.nblocks, (long long)c->num_sms * c->occ_q[0]));
+    const int g1 = int(std::min<long long>(P.nblocks, (long long)c->num_sms * c->occ_q[1]));
+    const int g4 = int(std::min<long long>(P.nblocks, (long long)c->num_sms * c->occ_q[4]));
+    for (int k = 1; k <= P.niter; ++k) {
+      timed(c, 0, stream, [&] {
+        crb::bound_kernel<<<g0, 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, c->p, k, P.niter);
+        crb::need_kernel<<<g1, 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q);
+        crb::s_kernel<<<c->num_sms * c->occ_q[2], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k, P.niter);
+        crb::sp_kernel<<<c->num_sms * c->occ_q[3], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
+        crb::m3need_kernel<<<g4, 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q);
+        crb::m3_kernel<<<c->num_sms * c->occ_q[5], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k, P.niter);
+        crb::cand_kernel<<<c->num_sms * c->occ_q[6], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
+        crb::queue_work_kernel<<<1, 32, 0, stream>>>(c->d_frames, P.Q, k, P.npix);
+      });
+      timed(c, 1, stream, [&] {
+        kReplace<<<P.rgrid, crb::kThreads, kReplaceSmem, stream>>>(c->d_frames, P.n, P.rtiles, k, P.niter,
+                                                                   k <= 2 ? 1 : 0);
+      });
+    }
+    CRB_CUDA(cudaGetLastError());
+    return CRB_OK;
+  }
   for (int i = 0; i < P.n; ++i) {
     const auto& s = specs[size_t(i)];
     if (s.mprev) {
@@ -272,6 +318,94 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
     }
   }
   CRB_CUDA(cudaGetLastError());
+  return CRB_OK;
+}
+
+// Queue pipeline: workspace = [queue counters | per frame: 5 bit planes (M, hot,
+// act, nsp, test)] (zeroed) then [per frame: maps S, N, S', M3, the second image]
+// then [three queues of one entry per pixel of the call].
+int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Plan& P) {
+  const int n = int(specs.size());
+  long long npix = 0, nblocks = 0;
+  for (const auto& s : specs) npix += (long long)s.w * s.h;
+  size_t total = 256;  // queue counters
+  std::vector<size_t> off_bits(static_cast<size_t>(n)), off_maps(static_cast<size_t>(n));
+  for (int i = 0; i < n; ++i) {
+    const auto& s = specs[size_t(i)];
+    off_bits[size_t(i)] = total;
+    total += 5 * align256(size_t(s.w + 31) / 32 * size_t(s.h) * 4);
+  }
+  const size_t zero_bytes = total;
+  for (int i = 0; i < n; ++i) {
+    const auto& s = specs[size_t(i)];
+    off_maps[size_t(i)] = total;
+    total += (niter >= 2 ? 5 : 4) * align256(size_t(s.w) * size_t(s.h) * 4);
+  }
+  const size_t off_q = total;
+  total += 3 * align256(size_t(npix) * 4);
+  const int nit = niter > 0 ? niter : 1;
+  const int ncounters = 7 * nit * n;
+  int rc = ensure_frames(c, n);
+  if (rc) return rc;
+  rc = ensure_ws(c, total, ncounters);
+  if (rc) return rc;
+  CRB_CUDA(cudaEventSynchronize(c->upload_ev));
+  char* ws = static_cast<char*>(c->ws);
+  long long pix0 = 0, rtiles = 0;
+  for (int i = 0; i < n; ++i) {
+    const auto& s = specs[size_t(i)];
+    crb::Frame& f = c->h_frames[i];
+    f = crb::Frame{};
+    const size_t plane = align256(size_t(s.w + 31) / 32 * size_t(s.h) * 4);
+    const size_t fmap = align256(size_t(s.w) * size_t(s.h) * 4);
+    char* pb = ws + off_bits[size_t(i)];
+    char* pm = ws + off_maps[size_t(i)];
+    f.img = s.img;
+    f.out_clean = s.out_clean;
+    f.bits_a = f.bits_b = reinterpret_cast<uint32_t*>(pb);  // one plane, updated in place
+    f.hot = reinterpret_cast<uint32_t*>(pb + plane);
+    f.act = reinterpret_cast<uint32_t*>(pb + 2 * plane);
+    f.nsp = reinterpret_cast<uint32_t*>(pb + 3 * plane);
+    f.test = reinterpret_cast<uint32_t*>(pb + 4 * plane);
+    f.mapS = reinterpret_cast<float*>(pm);
+    f.mapN = reinterpret_cast<float*>(pm + fmap);
+    f.mapSp = reinterpret_cast<float*>(pm + 2 * fmap);
+    f.mapM3 = reinterpret_cast<float*>(pm + 3 * fmap);
+    f.ws = (niter >= 2) ? reinterpret_cast<float*>(pm + 4 * fmap) : nullptr;
+    f.out_mask = s.out_mask;
+    f.maps = nullptr;
+    f.counters = c->d_counters + size_t(7) * nit * i;
+    f.work = f.counters + size_t(2) * nit;
+    f.w = s.w;
+    f.h = s.h;
+    f.wpr = (s.w + 31) / 32;
+    f.gain = s.gain;
+    f.rn = s.rn;
+    f.rtiles_x = (s.w + kRW - 1) / kRW;
+    f.rtile0 = rtiles;
+    rtiles += (long long)f.rtiles_x * ((s.h + kRH - 1) / kRH);
+    f.pix0 = pix0;
+    pix0 += (long long)s.w * s.h;
+    f.bx = (f.wpr + crb::kBW - 1) / crb::kBW;
+    f.blk0 = nblocks;
+    nblocks += (long long)f.bx * ((s.h + crb::kBH - 1) / crb::kBH);
+  }
+  P.n = n;
+  P.niter = niter;
+  P.shape = 0;
+  P.maps = false;
+  P.fuse = false;
+  P.queue = true;
+  P.rtiles = rtiles;
+  P.bits_total = zero_bytes;
+  P.ncounters = ncounters;
+  P.rgrid = int(std::min<long long>(rtiles, (long long)c->num_sms * c->occ_replace));
+  P.nblocks = nblocks;
+  P.npix = npix;
+  P.Q.n = reinterpret_cast<unsigned int*>(ws);
+  P.Q.q0 = reinterpret_cast<uint32_t*>(ws + off_q);
+  P.Q.q1 = reinterpret_cast<uint32_t*>(ws + off_q + align256(size_t(npix) * 4));
+  P.Q.q2 = reinterpret_cast<uint32_t*>(ws + off_q + 2 * align256(size_t(npix) * 4));
   return CRB_OK;
 }
 
@@ -354,8 +488,8 @@ int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
 
 // Replays (or captures once) the work of plan P as a CUDA graph on `stream`.
 int launch_graph(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs, cudaStream_t stream) {
-  GraphKey key{P.n, P.niter, P.shape, P.fuse, P.tiles, P.rtiles, P.bits_total, P.ncounters, P.dgrid, P.fgrid,
-               P.rgrid, c->ws, c->d_counters, c->d_frames};
+  GraphKey key{P.n, P.niter, P.shape, P.fuse, P.queue, P.tiles + P.nblocks * 1000003LL, P.rtiles, P.bits_total,
+               P.ncounters, P.dgrid, P.fgrid, P.rgrid, c->ws, c->d_counters, c->d_frames};
   for (auto& g : c->graphs)
     if (g.first == key) {
       CRB_CUDA(cudaGraphLaunch(g.second, stream));
@@ -390,7 +524,7 @@ int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, c
   if (c->any_call) CRB_CUDA(cudaStreamWaitEvent(stream, c->done_ev, 0));
   int shape = c->opt.tile_shape;
   if (shape >= nshapes) shape = 0;
-  if (shape < 0 && !maps) {
+  if (shape < 0 && !maps && c->opt.pipeline != 0) {
     // autotuning: the first call of a signature (frame sizes, niter) times every tile shape
     std::vector<long long> sig{niter};
     for (const auto& s : specs) {
@@ -437,7 +571,11 @@ int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, c
   }
   if (shape < 0) shape = 0;
   Plan P;
-  int rc = prepare(c, specs, niter, maps, shape, P);
+  long long npix = 0;
+  for (const auto& s : specs) npix += (long long)s.w * s.h;
+  const bool queue = c->opt.pipeline == 0 && !maps && niter > 0 && npix < (1LL << 32) &&
+                     std::all_of(specs.begin(), specs.end(), [](const FrameSpec& s) { return s.mprev == nullptr; });
+  int rc = queue ? prepare_queue(c, specs, niter, P) : prepare(c, specs, niter, maps, shape, P);
   if (rc) return rc;
   rc = upload(c, P, stream);
   if (rc) return rc;

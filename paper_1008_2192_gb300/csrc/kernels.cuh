@@ -47,6 +47,12 @@ struct Frame {
   float gain, rn;
   int tiles_x, rtiles_x;  // detect / replace tiles per row of tiles
   long long tile0, rtile0;  // first tile index of this frame in the launch
+  // queue pipeline (pipeline.cuh): bit planes (flag-word layout) and float maps
+  uint32_t *hot, *act, *nsp, *test;
+  float *mapS, *mapN, *mapSp, *mapM3;
+  long long pix0;  // first global pixel index of this frame
+  long long blk0;  // first word block (kBW words x kBH rows) of this frame
+  int bx;          // word blocks per row of blocks
 };
 
 struct Params {
@@ -752,9 +758,11 @@ __global__ void __launch_bounds__(kThreads) detect_kernel(const Frame* __restric
 template <int RW, int RH>
 struct ReplaceLayout {
   static constexpr int W = RW + 4, H = RH + 4;
+  static constexpr int FW = RW / 32 + 2;  // flag words per row: (x0 >> 5) - 1 ... (x0 >> 5) + RW / 32
   static constexpr int oF = round16(W * H * 4);
   static constexpr int oL = oF + round16(W * H);
-  static constexpr int oCnt = oL + round16(RW * RH * 2);
+  static constexpr int oWd = oL + round16(RW * RH * 2);
+  static constexpr int oCnt = oWd + round16(H * FW * 4);
   static constexpr size_t bytes = size_t(oCnt + 16);
 };
 
@@ -804,11 +812,22 @@ __device__ void replace_tile(const Frame& f, int k, int niter, int dense, long l
     return;
   }
 
+  uint32_t* sWd = reinterpret_cast<uint32_t*>(smem + L::oWd);  // flag words of the rows (clamped)
+  for (int i = tid; i < L::H * L::FW; i += kThreads) {
+    const int iy = i / L::FW, j = i - iy * L::FW;
+    const int gy = clampi(y0 - 2 + iy, 0, h - 1), wx = (x0 >> 5) - 1 + j;
+    sWd[i] = (wx >= 0 && wx < f.wpr) ? __ldg(M + size_t(gy) * f.wpr + wx) : 0u;
+  }
   for (int i = tid; i < L::W * L::H; i += kThreads) {
     const int iy = i / L::W, ix = i - iy * L::W;
     const int gx = clampi(x0 - 2 + ix, 0, w - 1), gy = clampi(y0 - 2 + iy, 0, h - 1);
     sJ[i] = __ldg(J + size_t(gy) * w + gx);
-    sF[i] = flag_at(M, f, gx, gy) ? 1 : 0;
+  }
+  __syncthreads();
+  for (int i = tid; i < L::W * L::H; i += kThreads) {
+    const int iy = i / L::W, ix = i - iy * L::W;
+    const int bit = clampi(x0 - 2 + ix, 0, w - 1) - (x0 - 32);  // bit index in the row's words
+    sF[i] = uint8_t((sWd[iy * L::FW + (bit >> 5)] >> (bit & 31)) & 1u);
   }
   __syncthreads();
 

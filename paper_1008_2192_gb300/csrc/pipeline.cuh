@@ -1,0 +1,445 @@
+// Queue pipeline of one detection (stages a-d): small kernels connected by
+// global work queues, so that every sparse step runs with full warps and no
+// block barriers.
+//
+//   bound_kernel   dense: L+ and the upper bound S+ of every pixel -> bit
+//                  planes hot (S+ > sigclip) and act (S+ > sigfrac*sigclip);
+//   need_kernel    needS' = dilate5(hot) & act and needS = dilate5(needS')
+//                  -> queues QS (needS) and QSP (needS'), bit plane nsp;
+//   s_kernel       at QS: m5, N, L+, S -> maps N, S;
+//   sp_kernel      at QSP: S' = S - med5(S) -> map S'; S' > sigclip -> queue QT
+//                  and bit plane test;
+//   m3need_kernel  needM3 = dilate7(test) -> queue QM3;
+//   m3_kernel      at QM3: med3 -> map M3;
+//   cand_kernel    at QT: F = m3 - med7(m3), the objlim statistic, and for each
+//                  candidate the two growths, ORed into the flag bits.
+//
+// The sets, and the argument that the flags equal those of the full
+// computation, are those of detect_tile (kernels.cuh). Positions in queues are
+// global pixel indices over all frames of the call (frame base + y*w + x).
+// Every window read clamps its coordinates into the frame, which equals the
+// per-map replicate-edge rule.
+
+#pragma once
+
+#include "kernels.cuh"
+
+namespace crb {
+
+struct Queues {
+  uint32_t* q0;   // QS, then QM3
+  uint32_t* q1;   // QSP
+  uint32_t* q2;   // QT
+  unsigned int* n;  // [0] QS, [1] QSP, [2] QM3, [3] QT
+};
+
+// frame of global pixel index g (frames sorted by first pixel)
+__device__ __forceinline__ int frame_of_pixel(const Frame* frames, int nframes, long long g) {
+  int lo = 0, hi = nframes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (frames[mid].pix0 <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// frame of word block b (frames sorted by first block)
+__device__ __forceinline__ int frame_of_block(const Frame* frames, int nframes, long long b) {
+  int lo = 0, hi = nframes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (frames[mid].blk0 <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+constexpr int kBW = 8;   // words (32 px each) per block row: one warp per word column
+constexpr int kBH = 32;  // rows per block
+
+// ---------------------------------------------------------------------------------------------
+// bound_kernel: per pixel L+ and the lower bound of m5 (smallest of the five
+// column medians) -> bits of S+ > sigclip and S+ > sigfrac*sigclip (see
+// detect_tile for the bound and its margin). One warp walks down one 32-pixel
+// word column of kBH rows keeping the 5-row window of its column (and of the
+// two halo columns on each side, held by lanes 0-3) in registers.
+__global__ void __launch_bounds__(256) bound_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
+                                                    Params p, int k, int niter) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float sigclip = p.sigclip, siglow = __fmul_rn(p.sigfrac, p.sigclip);
+  const float chot = 4.f * sigclip * sigclip * 0.9999f, clow = 4.f * siglow * siglow * 0.9999f;
+  for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
+    const int fi = frame_of_block(frames, nframes, b);
+    const Frame& f = frames[fi];
+    const long long lb = b - f.blk0;
+    const int bys = int(lb / f.bx), bxs = int(lb - (long long)bys * f.bx);
+    const int wc = bxs * kBW + warp;
+    if (wc >= f.wpr) continue;  // whole warp
+    const int w = f.w, h = f.h;
+    const float* __restrict__ J = iter_src(f, k, niter);
+    const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
+    const int x0 = wc * 32, x = x0 + lane;
+    const int col = min(x, w - 1);
+    const int hx = lane < 2 ? x0 - 2 + lane : x0 + 30 + lane;  // halo columns (lanes 0-3)
+    const int hcol = clampi(hx, 0, w - 1);
+    const int y0 = bys * kBH, y1 = min(y0 + kBH, h);
+    float r[5], hr[5];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int yy = clampi(y0 - 2 + i, 0, h - 1);
+      r[i + 1] = __ldg(J + size_t(yy) * w + col);
+      hr[i + 1] = (lane < 4) ? __ldg(J + size_t(yy) * w + hcol) : 0.f;
+    }
+    for (int y = y0; y < y1; ++y) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        r[i] = r[i + 1];
+        hr[i] = hr[i + 1];
+      }
+      const int yn = min(y + 2, h - 1);
+      r[4] = __ldg(J + size_t(yn) * w + col);
+      hr[4] = (lane < 4) ? __ldg(J + size_t(yn) * w + hcol) : 0.f;
+      float v[5];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) v[i] = r[i];
+      const float cm = sel_med5(v);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) v[i] = hr[i];
+      const float hcm = sel_med5(v);
+      // column medians of x-2 .. x+2 (halo lanes: 0 -> x0-2, 1 -> x0-1, 2 -> x0+32, 3 -> x0+33)
+      const float h0 = __shfl_sync(0xffffffffu, hcm, 0), h1 = __shfl_sync(0xffffffffu, hcm, 1);
+      const float h2 = __shfl_sync(0xffffffffu, hcm, 2), h3 = __shfl_sync(0xffffffffu, hcm, 3);
+      float m2 = __shfl_up_sync(0xffffffffu, cm, 2), m1 = __shfl_up_sync(0xffffffffu, cm, 1);
+      float p1 = __shfl_down_sync(0xffffffffu, cm, 1), p2 = __shfl_down_sync(0xffffffffu, cm, 2);
+      if (lane == 0) { m2 = h0; m1 = h1; }
+      if (lane == 1) m2 = h1;
+      if (lane == 31) { p1 = h2; p2 = h3; }
+      if (lane == 30) p2 = h2;
+      const float mlow = min3f(min3f(m2, m1, cm), p1, p2);
+      // L+ from the pixel, its column neighbours (window) and its row neighbours (lanes)
+      const float c = r[2];
+      const float hc1 = __shfl_sync(0xffffffffu, hr[2], 1), hc2 = __shfl_sync(0xffffffffu, hr[2], 2);
+      float left = __shfl_up_sync(0xffffffffu, c, 1), right = __shfl_down_sync(0xffffffffu, c, 1);
+      if (lane == 0) left = hc1;
+      if (lane == 31) right = hc2;
+      const float lp = lplus(c, r[1], r[3], left, right);
+      const float den = gain * (mlow > 0.f ? mlow : 0.f) + rn2;
+      const float lhs = lp * lp * g2;
+      const bool ok = x < w;
+      const unsigned act = __ballot_sync(0xffffffffu, ok && lhs > clow * den);
+      const unsigned hot = __ballot_sync(0xffffffffu, ok && lhs > chot * den);
+      if (lane == 0) {
+        const size_t o = size_t(y) * f.wpr + wc;
+        f.act[o] = act;
+        f.hot[o] = hot;
+        f.test[o] = 0u;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Block-level helpers for the bit-plane kernels: a block covers kBW words x kBH
+// rows of one frame; 256 threads = one thread per word.
+
+// horizontal dilation by R of word v with its neighbours l (left), r (right)
+template <int R>
+__device__ __forceinline__ uint32_t hdil(uint32_t l, uint32_t v, uint32_t r) {
+  uint32_t o = v;
+#pragma unroll
+  for (int d = 1; d <= R; ++d) o |= (v << d) | (l >> (32 - d)) | (v >> d) | (r << (32 - d));
+  return o;
+}
+
+// in-frame bits of word wc (bits beyond the frame width are 0)
+__device__ __forceinline__ uint32_t frame_word(int wc, int w) {
+  const int lim = w - 32 * wc;
+  return lim >= 32 ? 0xffffffffu : (lim <= 0 ? 0u : ((1u << lim) - 1u));
+}
+
+// Appends, for each thread's word `v` at (wc, y) of frame f, the set bits as
+// global pixel indices to queue q (counter *n); one atomic per block.
+__device__ __forceinline__ void emit_word(uint32_t v, const Frame& f, int wc, int y, uint32_t* q, unsigned int* n,
+                                          int* ws) {
+  int total = 0;
+  const int off = block_excl_scan(__popc(v), ws, total);
+  __shared__ unsigned int base;
+  if (threadIdx.x == 0) base = total ? atomicAdd(n, (unsigned int)total) : 0u;
+  __syncthreads();
+  unsigned int o = base + off;
+  const uint32_t row = uint32_t(f.pix0 + (long long)y * f.w + 32 * wc);
+  while (v) {
+    const int bb = __ffs(v) - 1;
+    v &= v - 1u;
+    q[o++] = row + bb;
+  }
+  __syncthreads();
+}
+
+// need_kernel: needS' = dilate5(hot) & act, needS = dilate5(needS') within the
+// frame -> queues QS, QSP and the bit plane nsp.
+__global__ void __launch_bounds__(256) need_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
+                                                   Queues Q) {
+  // rows y0-4 .. y0+kBH+3 (kBH + 8), words wc0-1 .. wc0+kBW (kBW + 2)
+  constexpr int RW = kBW + 2, RR = kBH + 8;
+  __shared__ uint32_t sHot[RR][RW], sAct[RR][RW], sNsp[RR][RW];
+  __shared__ int ws[kThreads / 32 + 1];
+  const int t = threadIdx.x;
+  for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
+    const int fi = frame_of_block(frames, nframes, b);
+    const Frame& f = frames[fi];
+    const long long lb = b - f.blk0;
+    const int bys = int(lb / f.bx), bxs = int(lb - (long long)bys * f.bx);
+    const int wc0 = bxs * kBW, y0 = bys * kBH;
+    for (int i = t; i < RR * RW; i += kThreads) {
+      const int rr = i / RW, cc = i - rr * RW;
+      const int y = y0 - 4 + rr, wc = wc0 - 1 + cc;
+      const bool in = y >= 0 && y < f.h && wc >= 0 && wc < f.wpr;
+      sHot[rr][cc] = in ? f.hot[size_t(y) * f.wpr + wc] : 0u;
+      sAct[rr][cc] = in ? f.act[size_t(y) * f.wpr + wc] : 0u;
+    }
+    __syncthreads();
+    // needS' on rows y0-2 .. y0+kBH+1 (kBH + 4), all RW words
+    for (int i = t; i < (kBH + 4) * RW; i += kThreads) {
+      const int rr = i / RW + 2, cc = i - (i / RW) * RW;
+      uint32_t a = 0, l = 0, r = 0;
+#pragma unroll
+      for (int d = -2; d <= 2; ++d) {
+        a |= sHot[rr + d][cc];
+        if (cc > 0) l |= sHot[rr + d][cc - 1];
+        if (cc < RW - 1) r |= sHot[rr + d][cc + 1];
+      }
+      sNsp[rr][cc] = hdil<2>(l, a, r) & sAct[rr][cc];
+    }
+    __syncthreads();
+    // the block's own words: needS = dilate5(needS') in the frame; emit both queues
+    const int rr = t / kBW + 4, cc = t % kBW + 1;
+    const int y = y0 + t / kBW, wc = wc0 + t % kBW;
+    const bool mine = y < f.h && wc < f.wpr;
+    uint32_t a = 0, l = 0, r = 0;
+#pragma unroll
+    for (int d = -2; d <= 2; ++d) {
+      a |= sNsp[rr + d][cc];
+      l |= sNsp[rr + d][cc - 1];
+      r |= sNsp[rr + d][cc + 1];
+    }
+    const uint32_t needS = mine ? (hdil<2>(l, a, r) & frame_word(wc, f.w)) : 0u;
+    const uint32_t needSp = mine ? sNsp[rr][cc] : 0u;
+    if (mine) f.nsp[size_t(y) * f.wpr + wc] = needSp;
+    emit_word(needS, f, wc, y, Q.q0, Q.n + 0, ws);
+    emit_word(needSp, f, wc, y, Q.q1, Q.n + 1, ws);
+  }
+}
+
+// m3need_kernel: needM3 = dilate7(test) within the frame -> queue QM3.
+__global__ void __launch_bounds__(256) m3need_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
+                                                     Queues Q) {
+  constexpr int RW = kBW + 2, RR = kBH + 6;
+  __shared__ uint32_t sT[RR][RW];
+  __shared__ int ws[kThreads / 32 + 1];
+  const int t = threadIdx.x;
+  for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
+    const int fi = frame_of_block(frames, nframes, b);
+    const Frame& f = frames[fi];
+    const long long lb = b - f.blk0;
+    const int bys = int(lb / f.bx), bxs = int(lb - (long long)bys * f.bx);
+    const int wc0 = bxs * kBW, y0 = bys * kBH;
+    for (int i = t; i < RR * RW; i += kThreads) {
+      const int rr = i / RW, cc = i - rr * RW;
+      const int y = y0 - 3 + rr, wc = wc0 - 1 + cc;
+      sT[rr][cc] = (y >= 0 && y < f.h && wc >= 0 && wc < f.wpr) ? f.test[size_t(y) * f.wpr + wc] : 0u;
+    }
+    __syncthreads();
+    const int rr = t / kBW + 3, cc = t % kBW + 1;
+    const int y = y0 + t / kBW, wc = wc0 + t % kBW;
+    uint32_t a = 0, l = 0, r = 0;
+#pragma unroll
+    for (int d = -3; d <= 3; ++d) {
+      a |= sT[rr + d][cc];
+      l |= sT[rr + d][cc - 1];
+      r |= sT[rr + d][cc + 1];
+    }
+    const uint32_t need = (y < f.h && wc < f.wpr) ? (hdil<3>(l, a, r) & frame_word(wc, f.w)) : 0u;
+    emit_word(need, f, wc, y, Q.q0, Q.n + 2, ws);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Queue kernels: one thread per entry, grid-stride over the queue length.
+
+struct Pix {
+  int fi, x, y;
+};
+
+__device__ __forceinline__ Pix decode(const Frame* frames, int nframes, uint32_t g) {
+  Pix p;
+  p.fi = frame_of_pixel(frames, nframes, (long long)g);
+  const uint32_t o = g - uint32_t(frames[p.fi].pix0);
+  const int w = frames[p.fi].w;
+  p.y = int(o / uint32_t(w));
+  p.x = int(o - uint32_t(p.y) * uint32_t(w));
+  return p;
+}
+
+// s_kernel: at QS, m5 (floored), N, L+ and S of J.
+__global__ void __launch_bounds__(256) s_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k,
+                                                int niter) {
+  const unsigned int n = Q.n[0];
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t g = Q.q0[i];
+    const Pix P = decode(frames, nframes, g);
+    const Frame& f = frames[P.fi];
+    const float* __restrict__ J = iter_src(f, k, niter);
+    int xs[5];
+    size_t ro[5];
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+      xs[d] = clampi(P.x - 2 + d, 0, f.w - 1);
+      ro[d] = size_t(clampi(P.y - 2 + d, 0, f.h - 1)) * f.w;
+    }
+    float v[25];
+#pragma unroll
+    for (int dy = 0; dy < 5; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 5; ++dx) v[dy * 5 + dx] = __ldg(J + ro[dy] + xs[dx]);
+    const float lp = lplus(v[12], v[7], v[17], v[11], v[13]);
+    const float m5f = floor_m5(sel_med25(v));
+    const float nn = noise_of(m5f, f.gain, __fmul_rn(f.rn, f.rn));
+    const size_t o = size_t(g - uint32_t(f.pix0));
+    f.mapS[o] = __fdiv_rn(lp, __fmul_rn(2.f, nn));
+    f.mapN[o] = nn;
+  }
+}
+
+// sp_kernel: at QSP, S' = S - med5(S); S' > sigclip -> test bit and queue QT.
+__global__ void __launch_bounds__(256) sp_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p) {
+  const unsigned int n = Q.n[1];
+  const unsigned int stride = gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // whole warps iterate together
+    const unsigned int i = i0 + threadIdx.x;
+    bool test = false;
+    uint32_t g = 0;
+    if (i < n) {
+      g = Q.q1[i];
+      const Pix P = decode(frames, nframes, g);
+      const Frame& f = frames[P.fi];
+      int xs[5];
+      size_t ro[5];
+#pragma unroll
+      for (int d = 0; d < 5; ++d) {
+        xs[d] = clampi(P.x - 2 + d, 0, f.w - 1);
+        ro[d] = size_t(clampi(P.y - 2 + d, 0, f.h - 1)) * f.w;
+      }
+      float v[25];
+#pragma unroll
+      for (int dy = 0; dy < 5; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 5; ++dx) v[dy * 5 + dx] = f.mapS[ro[dy] + xs[dx]];
+      const float sp = __fsub_rn(v[12], sel_med25(v));
+      const size_t o = size_t(g - uint32_t(f.pix0));
+      f.mapSp[o] = sp;
+      test = sp > p.sigclip;
+      if (test) atomicOr(&f.test[size_t(P.y) * f.wpr + (P.x >> 5)], 1u << (P.x & 31));
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, test);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned int base = 0;
+      if (lane == leader) base = atomicAdd(Q.n + 3, (unsigned int)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (test) Q.q2[base + __popc(m & ((1u << lane) - 1u))] = g;
+    }
+  }
+}
+
+// m3_kernel: at QM3, med3 of J.
+__global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k,
+                                                 int niter) {
+  const unsigned int n = Q.n[2];
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t g = Q.q0[i];
+    const Pix P = decode(frames, nframes, g);
+    const Frame& f = frames[P.fi];
+    const float* __restrict__ J = iter_src(f, k, niter);
+    int xs[3];
+    size_t ro[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      xs[d] = clampi(P.x - 1 + d, 0, f.w - 1);
+      ro[d] = size_t(clampi(P.y - 1 + d, 0, f.h - 1)) * f.w;
+    }
+    float v[9];
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) v[dy * 3 + dx] = __ldg(J + ro[dy] + xs[dx]);
+    f.mapM3[size_t(g - uint32_t(f.pix0))] = sel_med9(v);
+  }
+}
+
+// cand_kernel: at QT, F = m3 - med7(m3), the objlim statistic, and for each
+// candidate the first growth (S' > sigclip) and the second (S' > sigfrac*sigclip)
+// ORed into the flag bits of M_k; counts the new flags of each frame.
+// S' is read only where the bit plane nsp says it was computed; elsewhere it
+// cannot pass a threshold.
+__global__ void __launch_bounds__(256) cand_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p,
+                                                   int k) {
+  const unsigned int n = Q.n[3];
+  const float sigclip = p.sigclip, siglow = __fmul_rn(p.sigfrac, p.sigclip);
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t g = Q.q2[i];
+    const Pix P = decode(frames, nframes, g);
+    const Frame& f = frames[P.fi];
+    const int w = f.w, h = f.h;
+    int xs[7];
+    size_t ro[7];
+#pragma unroll
+    for (int d = 0; d < 7; ++d) {
+      xs[d] = clampi(P.x - 3 + d, 0, w - 1);
+      ro[d] = size_t(clampi(P.y - 3 + d, 0, h - 1)) * w;
+    }
+    float u[49];
+#pragma unroll
+    for (int dy = 0; dy < 7; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 7; ++dx) u[dy * 7 + dx] = f.mapM3[ro[dy] + xs[dx]];
+    const size_t o = size_t(g - uint32_t(f.pix0));
+    const float fval = __fsub_rn(u[24], sel_med49(u));
+    const float fn = fmaxf(__fdiv_rn(fval, f.mapN[o]), 0.01f);
+    const float rval = (p.objlim_form == 1) ? __fdiv_rn(__fmul_rn(2.f, f.mapS[o]), fn) : __fdiv_rn(f.mapSp[o], fn);
+    if (!(rval > p.objlim)) continue;
+    unsigned int fresh = 0;
+    for (int qy = max(P.y - 1, 0); qy <= min(P.y + 1, h - 1); ++qy)
+      for (int qx = max(P.x - 1, 0); qx <= min(P.x + 1, w - 1); ++qx) {
+        if (!((f.nsp[size_t(qy) * f.wpr + (qx >> 5)] >> (qx & 31)) & 1u)) continue;
+        if (!(f.mapSp[size_t(qy) * w + qx] > sigclip)) continue;  // first growth
+        for (int ry = max(qy - 1, 0); ry <= min(qy + 1, h - 1); ++ry)
+          for (int rx = max(qx - 1, 0); rx <= min(qx + 1, w - 1); ++rx) {
+            const size_t wo = size_t(ry) * f.wpr + (rx >> 5);
+            const uint32_t bit = 1u << (rx & 31);
+            if (!(f.nsp[wo] & bit)) continue;
+            if (!(f.mapSp[size_t(ry) * w + rx] > siglow)) continue;  // second growth
+            if (f.bits_a[wo] & bit) continue;                        // already flagged
+            const uint32_t old = atomicOr(&f.bits_a[wo], bit);
+            fresh += (old & bit) ? 0u : 1u;
+          }
+      }
+    if (fresh) atomicAdd(f.counters + 2 * (k - 1), (unsigned long long)fresh);
+  }
+}
+
+// Adds the queue lengths of this iteration to the work counters of frame 0
+// (the totals of the call) and clears them for the next iteration.
+__global__ void queue_work_kernel(const Frame* __restrict__ frames, Queues Q, int k, long long dense) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    unsigned long long* wk = frames[0].work + 5 * (k - 1);
+    wk[0] += Q.n[0];
+    wk[1] += Q.n[1];
+    wk[2] += Q.n[2];
+    wk[3] += Q.n[3];
+    wk[4] += (unsigned long long)dense;
+    for (int i = 0; i < 4; ++i) Q.n[i] = 0u;
+  }
+}
+
+}  // namespace crb

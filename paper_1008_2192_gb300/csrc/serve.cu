@@ -85,10 +85,12 @@ struct crb_server {
 namespace {
 
 size_t frame_bytes(int w, int h) {
-  // input + cleaned output + mask (the caller's, resident while queued) + workspace (image + 2 flag planes)
+  // the caller's input, cleaned output and mask (resident while queued), and the
+  // workspace of the queue pipeline: 4 float maps, the second image, 3 queue
+  // entries per pixel and 5 bit planes
   const size_t n = size_t(w) * size_t(h);
-  const size_t bits = size_t(w + 31) / 32 * size_t(h) * 4;
-  return n * 4 + n * 4 + n + n * 4 + 2 * bits;
+  const size_t plane = size_t(w + 31) / 32 * size_t(h) * 4;
+  return n * (4 + 4 + 1) + n * 4 * 4 + n * 4 + n * 3 * 4 + 5 * plane;
 }
 
 void launch_wave(crb_server* s, int slot, std::vector<Request>&& reqs) {
@@ -272,6 +274,8 @@ int crb_server_poll(crb_server* s, uint64_t* done_tags, double* latency_s, int* 
   }
   return n;
 }
+
+size_t crb_server_frame_bytes(int w, int h) { return (w < 1 || h < 1) ? 0 : frame_bytes(w, h); }
 
 int crb_server_stats(crb_server* s, long long* out, int max) {
   if (!s || !out || max < 0) return -1;

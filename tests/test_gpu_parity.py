@@ -98,12 +98,16 @@ def test_end_to_end_800(cl):
     print(f"800x800: mask flips vs FP64 {flips}, fragile pixels {nfragile}, flagged {int(mask.sum())}")
 
 
-@pytest.mark.parametrize("fusion", [True, False], ids=["fused", "two-launch"])
+PATHS = [dict(pipeline="queue"), dict(pipeline="tile", fusion=True), dict(pipeline="tile", fusion=False)]
+PATH_IDS = ["queue", "tile-fused", "tile-two-launch"]
+
+
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
 @pytest.mark.parametrize("w,h", SIZES)
 @pytest.mark.parametrize("niter", [1, 2, 3, 4])
-def test_clean_sizes(w, h, niter, fusion):
+def test_clean_sizes(w, h, niter, path):
     img = scene(w, h, seed=7 * w + h)
-    c = Cleaner(niter=niter, fusion=fusion)
+    c = Cleaner(niter=niter, **path)
     out, mask = gpu_clean(c, img)
     r32 = oracle.clean(img, params_of({}), niter, precision="f32")
     assert np.array_equal(mask, r32.mask) and np.array_equal(out, r32.clean)
@@ -116,12 +120,13 @@ def test_niter_zero_copies():
     assert np.array_equal(out, img) and not mask.any()
 
 
+@pytest.mark.parametrize("pipeline", ["queue", "tile"])
 @pytest.mark.parametrize("form", [0, 1])
 @pytest.mark.parametrize("pset", [dict(), dict(gain=1.5, readnoise=9.0, sigclip=5.0, sigfrac=0.3, objlim=4.0)])
-def test_parameters_and_objlim_forms(form, pset):
+def test_parameters_and_objlim_forms(form, pset, pipeline):
     img = scene(160, 120, seed=3)
     kw = dict(pset, objlim_form=form)
-    c = Cleaner(niter=4, **kw)
+    c = Cleaner(niter=4, pipeline=pipeline, **kw)
     out, mask = gpu_clean(c, img)
     r32 = oracle.clean(img, params_of(kw), 4, precision="f32")
     assert np.array_equal(mask, r32.mask) and np.array_equal(out, r32.clean)
@@ -132,7 +137,7 @@ def test_parameters_and_objlim_forms(form, pset):
 def test_tile_shapes_agree(shape, fusion):
     img = scene(300, 230, seed=11)
     ref = oracle.clean(img, params_of({}), 4, precision="f32")
-    c = Cleaner(niter=4, tile_shape=shape, fusion=fusion)
+    c = Cleaner(niter=4, tile_shape=shape, fusion=fusion, pipeline="tile")
     out, mask = gpu_clean(c, img)
     assert np.array_equal(mask, ref.mask) and np.array_equal(out, ref.clean)
 
@@ -211,11 +216,12 @@ def test_mosaic_16384_sampled_crops():
     _check_crops(img, out, mask, 4, [(y, x, n, n) for (y, x) in crops], params_of(rec))
 
 
+@pytest.mark.parametrize("pipeline", ["queue", "tile"])
 @pytest.mark.parametrize("graphs", [True, False])
 @pytest.mark.parametrize("shape", [0, -1])
-def test_graphs_and_autotune(graphs, shape):
+def test_graphs_and_autotune(graphs, shape, pipeline):
     """Graph replay and autotuned tile shapes give the plain path's results, call after call."""
-    c = Cleaner(niter=4, use_graphs=graphs, tile_shape=shape)
+    c = Cleaner(niter=4, use_graphs=graphs, tile_shape=shape, pipeline=pipeline)
     for seed in range(3):
         img = scene(333, 251, seed=40 + seed)
         out, mask = gpu_clean(c, img)

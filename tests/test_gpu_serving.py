@@ -64,7 +64,9 @@ def test_budget_admission():
     img = torch.from_numpy(synth.frame(512, 512, seed=1)).cuda()
     o = torch.empty_like(img)
     m = torch.empty(img.shape, dtype=torch.uint8, device="cuda")
-    per_frame = 512 * 512 * 13 + 2 * 16 * 512 * 4
+    import paper_1008_2192_gb300._lib as L
+    per_frame = L.load().crb_server_frame_bytes(512, 512)
+    assert per_frame >= 512 * 512 * (9 + 32)
     small = Server(niter=2, budget_bytes=per_frame - 1, max_inflight=1, max_batch=4)
     assert not small.submit(img, o, m, tag=1, gain=7.0, readnoise=5.0)  # would exceed the budget
     assert small.stats()["rejected"] == 1
