@@ -105,7 +105,7 @@ struct crb_ctx {
   crb_options opt{};
   int device = 0, num_sms = 0;
   std::vector<int> occ_detect, occ_detect_maps, occ_fused;
-  int occ_q[7] = {1, 1, 1, 1, 1, 1, 1};  // queue pipeline kernels
+  int occ_q[8] = {1, 1, 1, 1, 1, 1, 1, 1};  // queue pipeline kernels
   int occ_replace = 0;
 
   void* ws = nullptr;
@@ -166,6 +166,8 @@ int init_ctx(crb_ctx* c) {
     c->occ_q[5] = o > 0 ? o : 1;
     CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, crb::cand_kernel, 256, 0));
     c->occ_q[6] = o > 0 ? o : 1;
+    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, crb::rep_kernel, 256, 0));
+    c->occ_q[7] = o > 0 ? o : 1;
   }
   CRB_CUDA(cudaFuncSetAttribute(kReplace, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kReplaceSmem)));
   CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_replace, kReplace, crb::kThreads, kReplaceSmem));
@@ -268,6 +270,13 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
   }
   CRB_CUDA(cudaMemsetAsync(c->ws, 0, P.bits_total, stream));
   if (P.queue) {
+    // both image buffers start as I0: every replacement then writes only its flagged pixels
+    for (int i = 0; i < P.n; ++i) {
+      const auto& s = specs[size_t(i)];
+      const crb::Frame& f = c->h_frames[i];
+      CRB_CUDA(cudaMemcpyAsync(s.out_clean, s.img, size_t(s.w) * s.h * 4, cudaMemcpyDeviceToDevice, stream));
+      if (f.ws) CRB_CUDA(cudaMemcpyAsync(f.ws, s.img, size_t(s.w) * s.h * 4, cudaMemcpyDeviceToDevice, stream));
+    }
     const int g0 = int(std::min<long long>(P.nblocks, (long long)c->num_sms * c->occ_q[0]));
     const int g1 = int(std::min<long long>(P.nblocks, (long long)c->num_sms * c->occ_q[1]));
     const int g4 = int(std::min<long long>(P.nblocks, (long long)c->num_sms * c->occ_q[4]));
@@ -280,12 +289,13 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
         crb::m3need_kernel<<<g4, 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q);
         crb::m3_kernel<<<c->num_sms * c->occ_q[5], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k, P.niter);
         crb::cand_kernel<<<c->num_sms * c->occ_q[6], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
-        crb::queue_work_kernel<<<1, 32, 0, stream>>>(c->d_frames, P.Q, k, P.npix);
       });
       timed(c, 1, stream, [&] {
-        kReplace<<<P.rgrid, crb::kThreads, kReplaceSmem, stream>>>(c->d_frames, P.n, P.rtiles, k, P.niter,
-                                                                   k <= 2 ? 1 : 0);
+        crb::flagq_kernel<<<g1, 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q);
+        crb::rep_kernel<<<c->num_sms * c->occ_q[7], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k, P.niter);
+        if (k == P.niter) crb::mask_kernel<<<g1, 256, 0, stream>>>(c->d_frames, P.n, P.nblocks);
       });
+      crb::queue_work_kernel<<<1, 32, 0, stream>>>(c->d_frames, P.Q, k, P.npix);
     }
     CRB_CUDA(cudaGetLastError());
     return CRB_OK;

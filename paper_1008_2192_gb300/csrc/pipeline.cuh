@@ -30,7 +30,7 @@ struct Queues {
   uint32_t* q0;   // QS, then QM3
   uint32_t* q1;   // QSP
   uint32_t* q2;   // QT
-  unsigned int* n;  // [0] QS, [1] QSP, [2] QM3, [3] QT
+  unsigned int* n;  // [0] QS, [1] QSP, [2] QM3, [3] QT, [4] flagged pixels
 };
 
 // frame of global pixel index g (frames sorted by first pixel)
@@ -428,6 +428,91 @@ __global__ void __launch_bounds__(256) cand_kernel(const Frame* __restrict__ fra
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Replacement (stage e) over a queue of the flagged pixels. Both image buffers
+// start as copies of I0, so unflagged pixels are never written and every
+// iteration only writes its flagged pixels (see replace_tile for the
+// +/-inf form of the lower median).
+
+// flagq_kernel: the flagged pixels of M_k -> queue q1 (counter n[4]).
+__global__ void __launch_bounds__(256) flagq_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
+                                                    Queues Q) {
+  __shared__ int ws[kThreads / 32 + 1];
+  const int t = threadIdx.x;
+  for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
+    const int fi = frame_of_block(frames, nframes, b);
+    const Frame& f = frames[fi];
+    const long long lb = b - f.blk0;
+    const int bys = int(lb / f.bx), bxs = int(lb - (long long)bys * f.bx);
+    const int y = bys * kBH + t / kBW, wc = bxs * kBW + t % kBW;
+    const uint32_t v = (y < f.h && wc < f.wpr) ? (f.bits_a[size_t(y) * f.wpr + wc] & frame_word(wc, f.w)) : 0u;
+    emit_word(v, f, wc, y, Q.q1, Q.n + 4, ws);
+  }
+}
+
+// rep_kernel: I_k at the queued flagged pixels, from J = I_{k-1} and M_k.
+__global__ void __launch_bounds__(256) rep_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k,
+                                                  int niter) {
+  const unsigned int n = Q.n[4];
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t g = Q.q1[i];
+    const Pix P = decode(frames, nframes, g);
+    const Frame& f = frames[P.fi];
+    const float* __restrict__ J = iter_src(f, k, niter);
+    const uint32_t* __restrict__ M = f.bits_a;
+    int xs[5], ys[5];
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+      xs[d] = clampi(P.x - 2 + d, 0, f.w - 1);
+      ys[d] = clampi(P.y - 2 + d, 0, f.h - 1);
+    }
+    uint32_t win = 0;  // 25 window flags, row-major
+    float v[25];
+#pragma unroll
+    for (int dy = 0; dy < 5; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 5; ++dx) {
+        const int q = dy * 5 + dx;
+        v[q] = __ldg(J + size_t(ys[dy]) * f.w + xs[dx]);
+        win |= ((__ldg(M + size_t(ys[dy]) * f.wpr + (xs[dx] >> 5)) >> (xs[dx] & 31)) & 1u) << q;
+      }
+    const int nu = 25 - __popc(win);
+    float out;
+    if (nu > 0) {
+      const int a = 13 - (nu + 1) / 2;  // flagged entries sent to -inf
+      int seen = 0;
+#pragma unroll
+      for (int q = 0; q < 25; ++q)
+        if ((win >> q) & 1u) {
+          v[q] = (seen < a) ? -INFINITY : INFINITY;
+          ++seen;
+        }
+      out = sel_med25(v);
+    } else {
+      out = floor_m5(sel_med25(v));
+      atomicAdd(f.counters + 2 * (k - 1) + 1, 1ull);
+    }
+    iter_dst(f, k, niter)[size_t(g - uint32_t(f.pix0))] = out;
+  }
+}
+
+// mask_kernel: the u8 mask of every frame from its flag bits (one word per thread).
+__global__ void __launch_bounds__(256) mask_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks) {
+  const int t = threadIdx.x;
+  for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
+    const int fi = frame_of_block(frames, nframes, b);
+    const Frame& f = frames[fi];
+    const long long lb = b - f.blk0;
+    const int bys = int(lb / f.bx), bxs = int(lb - (long long)bys * f.bx);
+    const int y = bys * kBH + t / kBW, wc = bxs * kBW + t % kBW;
+    if (y >= f.h || wc >= f.wpr || !f.out_mask) continue;
+    const uint32_t v = f.bits_a[size_t(y) * f.wpr + wc];
+    uint8_t* o = f.out_mask + size_t(y) * f.w + 32 * wc;
+    const int nb = min(32, f.w - 32 * wc);
+    for (int bb = 0; bb < nb; ++bb) o[bb] = uint8_t((v >> bb) & 1u);
+  }
+}
+
 // Adds the queue lengths of this iteration to the work counters of frame 0
 // (the totals of the call) and clears them for the next iteration.
 __global__ void queue_work_kernel(const Frame* __restrict__ frames, Queues Q, int k, long long dense) {
@@ -438,7 +523,7 @@ __global__ void queue_work_kernel(const Frame* __restrict__ frames, Queues Q, in
     wk[2] += Q.n[2];
     wk[3] += Q.n[3];
     wk[4] += (unsigned long long)dense;
-    for (int i = 0; i < 4; ++i) Q.n[i] = 0u;
+    for (int i = 0; i < 5; ++i) Q.n[i] = 0u;
   }
 }
 
