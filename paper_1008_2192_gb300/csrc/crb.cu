@@ -271,12 +271,7 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
   CRB_CUDA(cudaMemsetAsync(c->ws, 0, P.bits_total, stream));
   if (P.queue) {
     // both image buffers start as I0: every replacement then writes only its flagged pixels
-    for (int i = 0; i < P.n; ++i) {
-      const auto& s = specs[size_t(i)];
-      const crb::Frame& f = c->h_frames[i];
-      CRB_CUDA(cudaMemcpyAsync(s.out_clean, s.img, size_t(s.w) * s.h * 4, cudaMemcpyDeviceToDevice, stream));
-      if (f.ws) CRB_CUDA(cudaMemcpyAsync(f.ws, s.img, size_t(s.w) * s.h * 4, cudaMemcpyDeviceToDevice, stream));
-    }
+    crb::init_images_kernel<<<c->num_sms * 8, 256, 0, stream>>>(c->d_frames, P.n);
     const int g0 = int(std::min<long long>(P.nblocks, (long long)c->num_sms * c->occ_q[0]));
     const int g1 = int(std::min<long long>(P.nblocks, (long long)c->num_sms * c->occ_q[1]));
     const int g4 = int(std::min<long long>(P.nblocks, (long long)c->num_sms * c->occ_q[4]));
@@ -589,7 +584,10 @@ int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, c
   if (rc) return rc;
   rc = upload(c, P, stream);
   if (rc) return rc;
-  if (c->opt.use_graphs && !maps && !c->opt.profile)
+  // graphs replay only work whose pointers all come from the descriptors
+  const bool graphable = niter > 0 && !maps && !c->opt.profile &&
+                         std::all_of(specs.begin(), specs.end(), [](const FrameSpec& s) { return !s.mprev; });
+  if (c->opt.use_graphs && graphable)
     rc = launch_graph(c, P, specs, stream);
   else
     rc = enqueue_work(c, P, specs, stream);

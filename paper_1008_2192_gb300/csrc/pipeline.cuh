@@ -434,6 +434,36 @@ __global__ void __launch_bounds__(256) cand_kernel(const Frame* __restrict__ fra
 // iteration only writes its flagged pixels (see replace_tile for the
 // +/-inf form of the lower median).
 
+// init_images_kernel: I0 into both image buffers of every frame (out_clean and,
+// for niter >= 2, ws). Pointers come from the descriptors, so a captured graph
+// replays correctly for new frames.
+__global__ void __launch_bounds__(256) init_images_kernel(const Frame* __restrict__ frames, int nframes) {
+  const size_t t0 = size_t(blockIdx.x) * blockDim.x + threadIdx.x, stride = size_t(gridDim.x) * blockDim.x;
+  for (int fi = 0; fi < nframes; ++fi) {
+    const float* __restrict__ src = frames[fi].img;
+    float* __restrict__ a = frames[fi].out_clean;
+    float* __restrict__ b = frames[fi].ws;
+    const size_t n = size_t(frames[fi].w) * size_t(frames[fi].h);
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(a) |
+                       reinterpret_cast<uintptr_t>(b)) & 15u) == 0;
+    size_t done = 0;
+    if (vec) {
+      const size_t n4 = n / 4;
+      for (size_t i = t0; i < n4; i += stride) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(src) + i);
+        reinterpret_cast<float4*>(a)[i] = v;
+        if (b) reinterpret_cast<float4*>(b)[i] = v;
+      }
+      done = n4 * 4;
+    }
+    for (size_t i = done + t0; i < n; i += stride) {
+      const float v = __ldg(src + i);
+      a[i] = v;
+      if (b) b[i] = v;
+    }
+  }
+}
+
 // flagq_kernel: the flagged pixels of M_k -> queue q1 (counter n[4]).
 __global__ void __launch_bounds__(256) flagq_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
                                                     Queues Q) {
