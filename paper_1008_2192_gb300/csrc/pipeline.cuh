@@ -60,13 +60,27 @@ constexpr int kBH = 32;  // rows per block
 // bound_kernel: per pixel L+ and the lower bound of m5 (smallest of the five
 // column medians) -> bits of S+ > sigclip and S+ > sigfrac*sigclip (see
 // detect_tile for the bound and its margin). One warp walks down one 32-pixel
-// word column of kBH rows keeping the 5-row window of its column (and of the
-// two halo columns on each side, held by lanes 0-3) in registers.
+// word column of kBH rows, two rows per step, keeping the rows of its column
+// (and of the two halo columns on each side, held by lanes 0-3) in registers.
+//
+// Sliding column medians: the windows of rows y and y+1 share the four values
+// of rows y-1..y+2. With c1 <= c2 the two middle values of those four, the
+// median of the four and one more value e is min(max(e, c1), c2); the pair
+// (min, max) of rows y+1, y+2 is shared with the next step.
+struct ColPair {  // running state of one column
+  float lo, hi;   // min / max of the last row pair
+};
+
+__device__ __forceinline__ float clamp_med(float e, float c1, float c2) { return fminf(fmaxf(e, c1), c2); }
+
 __global__ void __launch_bounds__(256) bound_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
                                                     Params p, int k, int niter) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float sigclip = p.sigclip, siglow = __fmul_rn(p.sigfrac, p.sigclip);
   const float chot = 4.f * sigclip * sigclip * 0.9999f, clow = 4.f * siglow * siglow * 0.9999f;
+  // halo routing: src lane of the column median at x-2 (lanes 0,1) or x+2 (30,31); at x-1 (0) or x+1 (31)
+  const int srcA = lane == 0 ? 0 : lane == 1 ? 1 : lane == 30 ? 2 : 3;
+  const int srcB = lane == 0 ? 1 : 2;
   for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
     const int fi = frame_of_block(frames, nframes, b);
     const Frame& f = frames[fi];
@@ -82,57 +96,67 @@ __global__ void __launch_bounds__(256) bound_kernel(const Frame* __restrict__ fr
     const int hx = lane < 2 ? x0 - 2 + lane : x0 + 30 + lane;  // halo columns (lanes 0-3)
     const int hcol = clampi(hx, 0, w - 1);
     const int y0 = bys * kBH, y1 = min(y0 + kBH, h);
-    float r[5], hr[5];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int yy = clampi(y0 - 2 + i, 0, h - 1);
-      r[i + 1] = __ldg(J + size_t(yy) * w + col);
-      hr[i + 1] = (lane < 4) ? __ldg(J + size_t(yy) * w + hcol) : 0.f;
-    }
-    for (int y = y0; y < y1; ++y) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        r[i] = r[i + 1];
-        hr[i] = hr[i + 1];
+    const float* __restrict__ Jc = J + col;
+    const float* __restrict__ Jh = J + hcol;
+    auto rowp = [&](int yy) { return size_t(clampi(yy, 0, h - 1)) * size_t(w); };
+    // rows y0-2 .. y0+1 of the column (a..d) and of the halo column
+    float a = __ldg(Jc + rowp(y0 - 2)), bq = __ldg(Jc + rowp(y0 - 1));
+    float cq = __ldg(Jc + rowp(y0)), d = __ldg(Jc + rowp(y0 + 1));
+    float ha = __ldg(Jh + rowp(y0 - 2)), hb = __ldg(Jh + rowp(y0 - 1));
+    float hc = __ldg(Jh + rowp(y0)), hd = __ldg(Jh + rowp(y0 + 1));
+    for (int y = y0; y < y1; y += 2) {
+      // next two rows y+2, y+3
+      const float e = __ldg(Jc + rowp(y + 2)), g = __ldg(Jc + rowp(y + 3));
+      const float he = __ldg(Jh + rowp(y + 2)), hg = __ldg(Jh + rowp(y + 3));
+      // core rows y-1..y+2 = (bq, cq) and (d, e): middle two values
+      float cm0, cm1, hcm0, hcm1;
+      {
+        const float l1 = fminf(bq, cq), h1 = fmaxf(bq, cq), l2 = fminf(d, e), h2 = fmaxf(d, e);
+        const float u = fmaxf(l1, l2), v = fminf(h1, h2);
+        const float c1 = fminf(u, v), c2 = fmaxf(u, v);
+        cm0 = clamp_med(a, c1, c2);   // rows y-2..y+2
+        cm1 = clamp_med(g, c1, c2);   // rows y-1..y+3
+        const float hl1 = fminf(hb, hc), hh1 = fmaxf(hb, hc), hl2 = fminf(hd, he), hh2 = fmaxf(hd, he);
+        const float hu = fmaxf(hl1, hl2), hv = fminf(hh1, hh2);
+        const float hc1 = fminf(hu, hv), hc2 = fmaxf(hu, hv);
+        hcm0 = clamp_med(ha, hc1, hc2);
+        hcm1 = clamp_med(hg, hc1, hc2);
       }
-      const int yn = min(y + 2, h - 1);
-      r[4] = __ldg(J + size_t(yn) * w + col);
-      hr[4] = (lane < 4) ? __ldg(J + size_t(yn) * w + hcol) : 0.f;
-      float v[5];
 #pragma unroll
-      for (int i = 0; i < 5; ++i) v[i] = r[i];
-      const float cm = sel_med5(v);
-#pragma unroll
-      for (int i = 0; i < 5; ++i) v[i] = hr[i];
-      const float hcm = sel_med5(v);
-      // column medians of x-2 .. x+2 (halo lanes: 0 -> x0-2, 1 -> x0-1, 2 -> x0+32, 3 -> x0+33)
-      const float h0 = __shfl_sync(0xffffffffu, hcm, 0), h1 = __shfl_sync(0xffffffffu, hcm, 1);
-      const float h2 = __shfl_sync(0xffffffffu, hcm, 2), h3 = __shfl_sync(0xffffffffu, hcm, 3);
-      float m2 = __shfl_up_sync(0xffffffffu, cm, 2), m1 = __shfl_up_sync(0xffffffffu, cm, 1);
-      float p1 = __shfl_down_sync(0xffffffffu, cm, 1), p2 = __shfl_down_sync(0xffffffffu, cm, 2);
-      if (lane == 0) { m2 = h0; m1 = h1; }
-      if (lane == 1) m2 = h1;
-      if (lane == 31) { p1 = h2; p2 = h3; }
-      if (lane == 30) p2 = h2;
-      const float mlow = min3f(min3f(m2, m1, cm), p1, p2);
-      // L+ from the pixel, its column neighbours (window) and its row neighbours (lanes)
-      const float c = r[2];
-      const float hc1 = __shfl_sync(0xffffffffu, hr[2], 1), hc2 = __shfl_sync(0xffffffffu, hr[2], 2);
-      float left = __shfl_up_sync(0xffffffffu, c, 1), right = __shfl_down_sync(0xffffffffu, c, 1);
-      if (lane == 0) left = hc1;
-      if (lane == 31) right = hc2;
-      const float lp = lplus(c, r[1], r[3], left, right);
-      const float den = gain * (mlow > 0.f ? mlow : 0.f) + rn2;
-      const float lhs = lp * lp * g2;
-      const bool ok = x < w;
-      const unsigned act = __ballot_sync(0xffffffffu, ok && lhs > clow * den);
-      const unsigned hot = __ballot_sync(0xffffffffu, ok && lhs > chot * den);
-      if (lane == 0) {
-        const size_t o = size_t(y) * f.wpr + wc;
-        f.act[o] = act;
-        f.hot[o] = hot;
-        f.test[o] = 0u;
+      for (int s = 0; s < 2; ++s) {
+        const int yy = y + s;
+        if (yy >= y1) break;
+        const float cm = s ? cm1 : cm0, hcm = s ? hcm1 : hcm0;
+        float m2 = __shfl_up_sync(0xffffffffu, cm, 2), m1 = __shfl_up_sync(0xffffffffu, cm, 1);
+        float p1 = __shfl_down_sync(0xffffffffu, cm, 1), p2 = __shfl_down_sync(0xffffffffu, cm, 2);
+        const float hA = __shfl_sync(0xffffffffu, hcm, srcA), hB = __shfl_sync(0xffffffffu, hcm, srcB);
+        if (lane < 2) m2 = hA;
+        if (lane == 0) m1 = hB;
+        if (lane >= 30) p2 = hA;
+        if (lane == 31) p1 = hB;
+        const float mlow = min3f(min3f(m2, m1, cm), p1, p2);
+        // L+: the pixel, its column neighbours and its row neighbours (lanes, halo at the ends)
+        const float cc = s ? d : cq, up = s ? cq : bq, dn = s ? e : d;
+        const float hcc = s ? hd : hc;
+        const float hL = __shfl_sync(0xffffffffu, hcc, lane == 0 ? 1 : 2);
+        float left = __shfl_up_sync(0xffffffffu, cc, 1), right = __shfl_down_sync(0xffffffffu, cc, 1);
+        if (lane == 0) left = hL;
+        if (lane == 31) right = hL;
+        const float lp = lplus(cc, up, dn, left, right);
+        const float den = gain * (mlow > 0.f ? mlow : 0.f) + rn2;
+        const float lhs = lp * lp * g2;
+        const bool ok = x < w;
+        const unsigned act = __ballot_sync(0xffffffffu, ok && lhs > clow * den);
+        const unsigned hot = __ballot_sync(0xffffffffu, ok && lhs > chot * den);
+        if (lane == 0) {
+          const size_t o = size_t(yy) * f.wpr + wc;
+          f.act[o] = act;
+          f.hot[o] = hot;
+          f.test[o] = 0u;
+        }
       }
+      a = cq; bq = d; cq = e; d = g;
+      ha = hc; hb = hd; hc = he; hd = hg;
     }
   }
 }
@@ -526,7 +550,10 @@ __global__ void __launch_bounds__(256) rep_kernel(const Frame* __restrict__ fram
   }
 }
 
-// mask_kernel: the u8 mask of every frame from its flag bits (one word per thread).
+// mask_kernel: the u8 mask of every frame from its flag bits (one word per
+// thread; two 16-byte stores when the 32 bytes are aligned).
+__device__ __forceinline__ uint32_t nibble_bytes(uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; }
+
 __global__ void __launch_bounds__(256) mask_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks) {
   const int t = threadIdx.x;
   for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
@@ -539,7 +566,21 @@ __global__ void __launch_bounds__(256) mask_kernel(const Frame* __restrict__ fra
     const uint32_t v = f.bits_a[size_t(y) * f.wpr + wc];
     uint8_t* o = f.out_mask + size_t(y) * f.w + 32 * wc;
     const int nb = min(32, f.w - 32 * wc);
-    for (int bb = 0; bb < nb; ++bb) o[bb] = uint8_t((v >> bb) & 1u);
+    if (nb == 32 && (reinterpret_cast<uintptr_t>(o) & 15u) == 0) {
+      uint4 q0, q1;
+      q0.x = nibble_bytes(v & 15u);
+      q0.y = nibble_bytes((v >> 4) & 15u);
+      q0.z = nibble_bytes((v >> 8) & 15u);
+      q0.w = nibble_bytes((v >> 12) & 15u);
+      q1.x = nibble_bytes((v >> 16) & 15u);
+      q1.y = nibble_bytes((v >> 20) & 15u);
+      q1.z = nibble_bytes((v >> 24) & 15u);
+      q1.w = nibble_bytes(v >> 28);
+      reinterpret_cast<uint4*>(o)[0] = q0;
+      reinterpret_cast<uint4*>(o)[1] = q1;
+    } else {
+      for (int bb = 0; bb < nb; ++bb) o[bb] = uint8_t((v >> bb) & 1u);
+    }
   }
 }
 
