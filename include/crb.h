@@ -83,7 +83,9 @@ typedef struct {
   int no_fusion;
   /* Detection pipeline. 0 (default): queue pipeline -- a dense bound pass
    * writes bit planes, and the medians run in separate kernels over global
-   * work queues of the positions that can change a flag. 1: tile pipeline --
+   * work queues of the positions that can change a flag; iterations after the
+   * first recompute only near the pixels the previous replacement changed,
+   * and the replacement runs in place in out_clean. 1: tile pipeline --
    * one kernel per iteration does all stages of a tile in shared memory (the
    * form used by crb_iterate's map export and by crb_clean_noalloc). Both
    * give identical results. */
@@ -103,7 +105,8 @@ void crb_destroy(crb_ctx* ctx);
 /* Cleans one frame: img (device, w*h floats) -> out_clean (device, w*h floats,
  * must not overlap img: CRB_EALIAS) and out_mask (device, w*h bytes, 0/1, the
  * cumulative flags of all iterations). Enqueued on `stream`. The context's
- * workspace grows on demand (one image plus a bit mask). */
+ * workspace grows on demand (about 37 bytes per pixel with the default queue
+ * pipeline). */
 int crb_clean(crb_ctx* ctx, const float* img, int w, int h, float* out_clean, uint8_t* out_mask,
               cudaStream_t stream);
 
@@ -216,8 +219,8 @@ int crb_server_submit(crb_server* srv, const float* img, int w, int h, float gai
 int crb_server_poll(crb_server* srv, uint64_t* done_tags, double* latency_s, int* status, int max, int block_ms);
 
 /* Device bytes a w x h frame counts against the server budget: 9 per pixel of
- * the caller's buffers, 32 per pixel of workspace, and 5 bit planes (0 for
- * invalid sizes). */
+ * the caller's buffers, 36 per pixel of workspace, 9 bit planes and 20 bytes
+ * per cell of 32 x 8 pixels (0 for invalid sizes). */
 size_t crb_server_frame_bytes(int w, int h);
 
 /* Counters: submitted, done, waves launched, largest wave, rejected submissions,

@@ -66,10 +66,16 @@ constexpr size_t kReplaceSmem = crb::ReplaceLayout<kRW, kRH>::bytes;
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
+// queue pipeline kernels, for the occupancy table
+enum QK {
+  kQBound, kQNeed, kQS, kQSp, kQM3need, kQM3, kQCand, kQRepCompute, kQBoundList, kQNeedList, kQM3needList, kQRq,
+  kQRepWrite, kQCellList, kQKernels
+};
+
 struct GraphKey {
   int n, niter, shape;
   bool fuse, queue;
-  long long tiles, rtiles;
+  long long tiles, rtiles, nblocks, ncells, npix;
   size_t bits_total;
   int ncounters, dgrid, fgrid, rgrid;
   void* ws;
@@ -77,7 +83,7 @@ struct GraphKey {
   void* frames;
   bool operator==(const GraphKey& o) const {
     return n == o.n && niter == o.niter && shape == o.shape && fuse == o.fuse && queue == o.queue &&
-           tiles == o.tiles &&
+           tiles == o.tiles && nblocks == o.nblocks && ncells == o.ncells && npix == o.npix &&
            rtiles == o.rtiles && bits_total == o.bits_total && ncounters == o.ncounters && dgrid == o.dgrid &&
            fgrid == o.fgrid && rgrid == o.rgrid && ws == o.ws && counters == o.counters && frames == o.frames;
   }
@@ -105,7 +111,7 @@ struct crb_ctx {
   crb_options opt{};
   int device = 0, num_sms = 0;
   std::vector<int> occ_detect, occ_detect_maps, occ_fused;
-  int occ_q[8] = {1, 1, 1, 1, 1, 1, 1, 1};  // queue pipeline kernels
+  int occ_q[kQKernels] = {};  // queue pipeline kernels (QK order)
   int occ_replace = 0;
 
   void* ws = nullptr;
@@ -151,23 +157,19 @@ int init_ctx(crb_ctx* c) {
     c->occ_fused.push_back(occf > 0 ? occf : 1);
   }
   {
-    int o = 0;
-    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, crb::bound_kernel, 256, 0));
-    c->occ_q[0] = o > 0 ? o : 1;
-    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, crb::need_kernel, 256, 0));
-    c->occ_q[1] = o > 0 ? o : 1;
-    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, crb::s_kernel, 256, 0));
-    c->occ_q[2] = o > 0 ? o : 1;
-    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, crb::sp_kernel, 256, 0));
-    c->occ_q[3] = o > 0 ? o : 1;
-    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, crb::m3need_kernel, 256, 0));
-    c->occ_q[4] = o > 0 ? o : 1;
-    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, crb::m3_kernel, 256, 0));
-    c->occ_q[5] = o > 0 ? o : 1;
-    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, crb::cand_kernel, 256, 0));
-    c->occ_q[6] = o > 0 ? o : 1;
-    CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, crb::rep_kernel, 256, 0));
-    c->occ_q[7] = o > 0 ? o : 1;
+    const void* fns[kQKernels] = {
+        reinterpret_cast<const void*>(crb::bound_kernel),       reinterpret_cast<const void*>(crb::need_kernel),
+        reinterpret_cast<const void*>(crb::s_kernel),           reinterpret_cast<const void*>(crb::sp_kernel),
+        reinterpret_cast<const void*>(crb::m3need_kernel),      reinterpret_cast<const void*>(crb::m3_kernel),
+        reinterpret_cast<const void*>(crb::cand_kernel<true>),        reinterpret_cast<const void*>(crb::rep_compute_kernel),
+        reinterpret_cast<const void*>(crb::bound_list_kernel),  reinterpret_cast<const void*>(crb::need_list_kernel),
+        reinterpret_cast<const void*>(crb::m3need_list_kernel), reinterpret_cast<const void*>(crb::rq_kernel),
+        reinterpret_cast<const void*>(crb::rep_write_kernel),   reinterpret_cast<const void*>(crb::cell_list_kernel)};
+    for (int i = 0; i < kQKernels; ++i) {
+      int o = 0;
+      CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[i], 256, 0));
+      c->occ_q[i] = o > 0 ? o : 1;
+    }
   }
   CRB_CUDA(cudaFuncSetAttribute(kReplace, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kReplaceSmem)));
   CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_replace, kReplace, crb::kThreads, kReplaceSmem));
@@ -255,6 +257,8 @@ struct Plan {
   int ncounters = 0;
   int dgrid = 0, fgrid = 0, rgrid = 0;
   long long nblocks = 0, npix = 0;  // queue pipeline: word blocks, pixels
+  long long ncells = 0;             // queue pipeline: cells (one word x kCH rows)
+  uint32_t* cells[2] = {nullptr, nullptr};  // cell classes for even / odd iterations
   crb::Queues Q{};
 };
 
@@ -270,25 +274,55 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
   }
   CRB_CUDA(cudaMemsetAsync(c->ws, 0, P.bits_total, stream));
   if (P.queue) {
-    // both image buffers start as I0: every replacement then writes only its flagged pixels
+    // the image buffer starts as I0: every replacement then writes only its flagged pixels
     crb::init_images_kernel<<<c->num_sms * 8, 256, 0, stream>>>(c->d_frames, P.n);
-    const int g0 = int(std::min<long long>(P.nblocks, (long long)c->num_sms * c->occ_q[0]));
-    const int g1 = int(std::min<long long>(P.nblocks, (long long)c->num_sms * c->occ_q[1]));
-    const int g4 = int(std::min<long long>(P.nblocks, (long long)c->num_sms * c->occ_q[4]));
+    auto grid = [&](int kind, long long units) {
+      return int(std::max<long long>(1, std::min<long long>(units, (long long)c->num_sms * c->occ_q[kind])));
+    };
+    const int gq = c->num_sms;  // queue and list kernels: grid-stride over lengths known on the device
+    const size_t cells_bytes = size_t(P.ncells) * 4;
     for (int k = 1; k <= P.niter; ++k) {
+      uint32_t* cls = P.cells[k & 1];
+      uint32_t* cls_next = (k < P.niter) ? P.cells[(k + 1) & 1] : nullptr;
       timed(c, 0, stream, [&] {
-        crb::bound_kernel<<<g0, 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, c->p, k, P.niter);
-        crb::need_kernel<<<g1, 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q);
-        crb::s_kernel<<<c->num_sms * c->occ_q[2], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k, P.niter);
-        crb::sp_kernel<<<c->num_sms * c->occ_q[3], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
-        crb::m3need_kernel<<<g4, 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q);
-        crb::m3_kernel<<<c->num_sms * c->occ_q[5], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k, P.niter);
-        crb::cand_kernel<<<c->num_sms * c->occ_q[6], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
+        const unsigned int dense_from = unsigned(std::min<long long>(P.ncells / 4 + 1, 0xffffffffLL));
+        const uint32_t* kcls = (k == 1) ? nullptr : cls;
+        if (k == 1) {
+          crb::bound_kernel<<<grid(kQBound, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, c->p, k);
+        } else {
+          crb::cell_list_kernel<<<grid(kQCellList, (P.ncells + 255) / 256), 256, 0, stream>>>(c->d_frames, P.n,
+                                                                                              P.ncells, cls, P.Q);
+          crb::bound_list_kernel<<<gq * c->occ_q[kQBoundList], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
+        }
+        crb::need_kernel<<<grid(kQNeed, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q, kcls,
+                                                                       dense_from);
+        if (k >= 2)
+          crb::need_list_kernel<<<gq * c->occ_q[kQNeedList], 256, 0, stream>>>(c->d_frames, P.n, P.Q, cls,
+                                                                               dense_from);
+        crb::s_kernel<<<gq * c->occ_q[kQS], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k);
+        crb::sp_kernel<<<gq * c->occ_q[kQSp], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
+        crb::m3need_kernel<<<grid(kQM3need, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q, kcls,
+                                                                           dense_from);
+        if (k >= 2)
+          crb::m3need_list_kernel<<<gq * c->occ_q[kQM3needList], 256, 0, stream>>>(c->d_frames, P.n, P.Q, cls,
+                                                                                   dense_from);
+        crb::m3_kernel<<<gq * c->occ_q[kQM3], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k);
+        if (k == 1)
+          crb::cand_kernel<false><<<gq * c->occ_q[kQCand], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
+        else
+          crb::cand_kernel<true><<<gq * c->occ_q[kQCand], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
       });
+      // the classes of iteration k+1 start at zero (those of iteration k-1 were read by now)
+      if (k >= 3 && cls_next) CRB_CUDA(cudaMemsetAsync(cls_next, 0, cells_bytes, stream));
       timed(c, 1, stream, [&] {
-        crb::flagq_kernel<<<g1, 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q);
-        crb::rep_kernel<<<c->num_sms * c->occ_q[7], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k, P.niter);
-        if (k == P.niter) crb::mask_kernel<<<g1, 256, 0, stream>>>(c->d_frames, P.n, P.nblocks);
+        if (k == 1)
+          crb::flagq_kernel<<<grid(kQNeed, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q);
+        else
+          crb::rq_kernel<<<gq * c->occ_q[kQRq], 256, 0, stream>>>(c->d_frames, P.n, P.Q);
+        crb::rep_compute_kernel<<<gq * c->occ_q[kQRepCompute], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k);
+        crb::rep_write_kernel<<<gq * c->occ_q[kQRepWrite], 256, 0, stream>>>(c->d_frames, P.n, P.Q, cls_next,
+                                                                            k >= 2 ? 1 : 0);
+        if (k == P.niter) crb::mask_kernel<<<grid(kQNeed, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks);
       });
       crb::queue_work_kernel<<<1, 32, 0, stream>>>(c->d_frames, P.Q, k, P.npix);
     }
@@ -326,28 +360,38 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
   return CRB_OK;
 }
 
-// Queue pipeline: workspace = [queue counters | per frame: 5 bit planes (M, hot,
-// act, nsp, test)] (zeroed) then [per frame: maps S, N, S', M3, the second image]
-// then [three queues of one entry per pixel of the call].
+// Queue pipeline: workspace = [queue counters | per frame: bit planes M, rq, fb |
+// cell classes x 2] (zeroed at the start of a call) then [per frame: bit planes
+// hot, act, nsp, test, sval, m3val; maps S, N, S', M3] then [queues q0, q1, q2,
+// fresh, fbl of one entry per pixel of the call | cell lists l2, l6, l9].
 int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Plan& P) {
   const int n = int(specs.size());
-  long long npix = 0, nblocks = 0;
-  for (const auto& s : specs) npix += (long long)s.w * s.h;
+  long long npix = 0, nblocks = 0, ncells = 0;
+  for (const auto& s : specs) {
+    npix += (long long)s.w * s.h;
+    ncells += (long long)((s.w + 31) / 32) * ((s.h + crb::kCH - 1) / crb::kCH);
+  }
   size_t total = 256;  // queue counters
-  std::vector<size_t> off_bits(static_cast<size_t>(n)), off_maps(static_cast<size_t>(n));
+  std::vector<size_t> off_zero(static_cast<size_t>(n)), off_bits(static_cast<size_t>(n)),
+      off_maps(static_cast<size_t>(n));
   for (int i = 0; i < n; ++i) {
     const auto& s = specs[size_t(i)];
-    off_bits[size_t(i)] = total;
-    total += 5 * align256(size_t(s.w + 31) / 32 * size_t(s.h) * 4);
+    off_zero[size_t(i)] = total;
+    total += 3 * align256(size_t(s.w + 31) / 32 * size_t(s.h) * 4);
   }
+  const size_t off_cells = total;
+  total += 2 * align256(size_t(ncells) * 4);
   const size_t zero_bytes = total;
   for (int i = 0; i < n; ++i) {
     const auto& s = specs[size_t(i)];
+    off_bits[size_t(i)] = total;
+    total += 6 * align256(size_t(s.w + 31) / 32 * size_t(s.h) * 4);
     off_maps[size_t(i)] = total;
-    total += (niter >= 2 ? 5 : 4) * align256(size_t(s.w) * size_t(s.h) * 4);
+    total += 4 * align256(size_t(s.w) * size_t(s.h) * 4);
   }
+  const size_t qbytes = align256(size_t(npix) * 4), lbytes = align256(size_t(ncells) * 4);
   const size_t off_q = total;
-  total += 3 * align256(size_t(npix) * 4);
+  total += 5 * qbytes + 3 * lbytes;
   const int nit = niter > 0 ? niter : 1;
   const int ncounters = 7 * nit * n;
   int rc = ensure_frames(c, n);
@@ -356,27 +400,32 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
   if (rc) return rc;
   CRB_CUDA(cudaEventSynchronize(c->upload_ev));
   char* ws = static_cast<char*>(c->ws);
-  long long pix0 = 0, rtiles = 0;
+  long long pix0 = 0, rtiles = 0, cell0 = 0;
   for (int i = 0; i < n; ++i) {
     const auto& s = specs[size_t(i)];
     crb::Frame& f = c->h_frames[i];
     f = crb::Frame{};
     const size_t plane = align256(size_t(s.w + 31) / 32 * size_t(s.h) * 4);
     const size_t fmap = align256(size_t(s.w) * size_t(s.h) * 4);
+    char* pz = ws + off_zero[size_t(i)];
     char* pb = ws + off_bits[size_t(i)];
     char* pm = ws + off_maps[size_t(i)];
     f.img = s.img;
     f.out_clean = s.out_clean;
-    f.bits_a = f.bits_b = reinterpret_cast<uint32_t*>(pb);  // one plane, updated in place
-    f.hot = reinterpret_cast<uint32_t*>(pb + plane);
-    f.act = reinterpret_cast<uint32_t*>(pb + 2 * plane);
-    f.nsp = reinterpret_cast<uint32_t*>(pb + 3 * plane);
-    f.test = reinterpret_cast<uint32_t*>(pb + 4 * plane);
+    f.ws = nullptr;  // replacement is in place
+    f.bits_a = f.bits_b = reinterpret_cast<uint32_t*>(pz);  // one plane, updated in place
+    f.rq = reinterpret_cast<uint32_t*>(pz + plane);
+    f.fb = reinterpret_cast<uint32_t*>(pz + 2 * plane);
+    f.hot = reinterpret_cast<uint32_t*>(pb);
+    f.act = reinterpret_cast<uint32_t*>(pb + plane);
+    f.nsp = reinterpret_cast<uint32_t*>(pb + 2 * plane);
+    f.test = reinterpret_cast<uint32_t*>(pb + 3 * plane);
+    f.sval = reinterpret_cast<uint32_t*>(pb + 4 * plane);
+    f.m3val = reinterpret_cast<uint32_t*>(pb + 5 * plane);
     f.mapS = reinterpret_cast<float*>(pm);
     f.mapN = reinterpret_cast<float*>(pm + fmap);
     f.mapSp = reinterpret_cast<float*>(pm + 2 * fmap);
     f.mapM3 = reinterpret_cast<float*>(pm + 3 * fmap);
-    f.ws = (niter >= 2) ? reinterpret_cast<float*>(pm + 4 * fmap) : nullptr;
     f.out_mask = s.out_mask;
     f.maps = nullptr;
     f.counters = c->d_counters + size_t(7) * nit * i;
@@ -394,6 +443,9 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
     f.bx = (f.wpr + crb::kBW - 1) / crb::kBW;
     f.blk0 = nblocks;
     nblocks += (long long)f.bx * ((s.h + crb::kBH - 1) / crb::kBH);
+    f.ncy = (s.h + crb::kCH - 1) / crb::kCH;
+    f.cell0 = cell0;
+    cell0 += (long long)f.wpr * f.ncy;
   }
   P.n = n;
   P.niter = niter;
@@ -407,10 +459,18 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
   P.rgrid = int(std::min<long long>(rtiles, (long long)c->num_sms * c->occ_replace));
   P.nblocks = nblocks;
   P.npix = npix;
+  P.ncells = ncells;
+  P.cells[0] = reinterpret_cast<uint32_t*>(ws + off_cells);
+  P.cells[1] = reinterpret_cast<uint32_t*>(ws + off_cells + align256(size_t(ncells) * 4));
   P.Q.n = reinterpret_cast<unsigned int*>(ws);
   P.Q.q0 = reinterpret_cast<uint32_t*>(ws + off_q);
-  P.Q.q1 = reinterpret_cast<uint32_t*>(ws + off_q + align256(size_t(npix) * 4));
-  P.Q.q2 = reinterpret_cast<uint32_t*>(ws + off_q + 2 * align256(size_t(npix) * 4));
+  P.Q.q1 = reinterpret_cast<uint32_t*>(ws + off_q + qbytes);
+  P.Q.q2 = reinterpret_cast<uint32_t*>(ws + off_q + 2 * qbytes);
+  P.Q.fresh = reinterpret_cast<uint32_t*>(ws + off_q + 3 * qbytes);
+  P.Q.fbl = reinterpret_cast<uint32_t*>(ws + off_q + 4 * qbytes);
+  P.Q.l2 = reinterpret_cast<uint32_t*>(ws + off_q + 5 * qbytes);
+  P.Q.l6 = reinterpret_cast<uint32_t*>(ws + off_q + 5 * qbytes + lbytes);
+  P.Q.l9 = reinterpret_cast<uint32_t*>(ws + off_q + 5 * qbytes + 2 * lbytes);
   return CRB_OK;
 }
 
@@ -493,8 +553,9 @@ int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
 
 // Replays (or captures once) the work of plan P as a CUDA graph on `stream`.
 int launch_graph(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs, cudaStream_t stream) {
-  GraphKey key{P.n, P.niter, P.shape, P.fuse, P.queue, P.tiles + P.nblocks * 1000003LL, P.rtiles, P.bits_total,
-               P.ncounters, P.dgrid, P.fgrid, P.rgrid, c->ws, c->d_counters, c->d_frames};
+  GraphKey key{P.n,      P.niter,      P.shape,      P.fuse,  P.queue, P.tiles,          P.rtiles,
+               P.nblocks, P.ncells,     P.npix,       P.bits_total, P.ncounters, P.dgrid, P.fgrid,
+               P.rgrid,   c->ws,        c->d_counters, c->d_frames};
   for (auto& g : c->graphs)
     if (g.first == key) {
       CRB_CUDA(cudaGraphLaunch(g.second, stream));

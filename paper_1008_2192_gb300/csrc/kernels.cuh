@@ -28,9 +28,10 @@ namespace crb {
 constexpr int kThreads = 256;
 constexpr int kNumMaps = 11;  // m5, L+, N, S, S', m3, F, R, cand, g1, g2
 
-// One frame of a launch. The image buffers alternate between iterations so
-// that iteration niter writes out_clean: I_k goes to out_clean when
-// (niter - k) is even and to ws otherwise; iteration 1 reads img.
+// One frame of a launch. In the tile pipeline the image buffers alternate
+// between iterations so that iteration niter writes out_clean: I_k goes to
+// out_clean when (niter - k) is even and to ws otherwise; iteration 1 reads
+// img. The queue pipeline (pipeline.cuh) replaces in place in out_clean.
 struct Frame {
   const float* img;       // I_0 (input, read-only)
   float* out_clean;       // caller's output
@@ -49,10 +50,14 @@ struct Frame {
   long long tile0, rtile0;  // first tile index of this frame in the launch
   // queue pipeline (pipeline.cuh): bit planes (flag-word layout) and float maps
   uint32_t *hot, *act, *nsp, *test;
+  uint32_t *sval, *m3val;  // positions whose mapS/mapN, mapM3 hold the current iteration's values
+  uint32_t *rq, *fb;       // queued for replacement; known to have a fully flagged window
   float *mapS, *mapN, *mapSp, *mapM3;
   long long pix0;  // first global pixel index of this frame
   long long blk0;  // first word block (kBW words x kBH rows) of this frame
+  long long cell0; // first cell (one word x kCH rows) of this frame
   int bx;          // word blocks per row of blocks
+  int ncy;         // rows of cells
 };
 
 struct Params {
@@ -178,9 +183,10 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 //
 // Exact pruning. S >= 0 and med5(S) >= 0, so S' <= S (also after float
 // rounding). A flag needs a candidate within 2 px, a candidate needs
-// S' > sigclip, and a second-growth flag needs S' > sigfrac*sigclip. With an
-// upper bound S+ >= S, the only positions whose S' can matter are
-//   needS' = dilate5({S+ > sigclip}) and S+ > sigfrac*sigclip,
+// S' > sigclip, and a growth flag needs S' > sigclip (first growth) or
+// S' > sigfrac*sigclip (second). With an upper bound S+ >= S and
+// tlow = min(sigclip, sigfrac*sigclip), the only positions whose S' can matter are
+//   needS' = dilate5({S+ > sigclip}) and S+ > tlow,
 // the exact S is needed on dilate5(needS'), and med3 on the 7x7
 // neighbourhoods of the positions with S' > sigclip. S' elsewhere is replaced
 // by -inf, which passes no threshold: the flags are unchanged.
@@ -383,7 +389,8 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   const int x0 = tx * TW, y0 = ty * TH;
   const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
   const float sigclip = p.sigclip, siglow = __fmul_rn(p.sigfrac, p.sigclip), objlim = p.objlim;
-  const float chot = 4.f * sigclip * sigclip * 0.9999f, clow = 4.f * siglow * siglow * 0.9999f;
+  const float tlow = fminf(siglow, sigclip);
+  const float chot = 4.f * sigclip * sigclip * 0.9999f, clow = 4.f * tlow * tlow * 0.9999f;
   const bool edge = (x0 - 6 < 0) || (y0 - 6 < 0) || (x0 + TW + 6 > w) || (y0 + TH + 6 > h);
   const bool inner = x0 - 8 >= 0 && x0 + TW + 8 <= w && y0 - 8 >= 0 && y0 + TH + 8 <= h;
   const size_t npix = size_t(w) * size_t(h);
@@ -506,7 +513,7 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
     }
     __syncthreads();
 
-    // P2: L+ and the bound S+ on R2 -> bits of S+ > sigclip (hot) and S+ > sigfrac*sigclip (act)
+    // P2: L+ and the bound S+ on R2 -> bits of S+ > sigclip (hot) and S+ > tlow (act)
     for (int i = tid; i < L::W2 * L::H2; i += kThreads) {
       const int iy = i / L::W2, ix = i - iy * L::W2;
       const int gx = x0 - 2 + ix, gy = y0 - 2 + iy;

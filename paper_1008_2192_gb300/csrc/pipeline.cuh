@@ -1,37 +1,87 @@
-// Queue pipeline of one detection (stages a-d): small kernels connected by
-// global work queues, so that every sparse step runs with full warps and no
-// block barriers.
+// Queue pipeline: small kernels connected by global work queues, so that every
+// sparse step runs with full warps and no block barriers.
 //
-//   bound_kernel   dense: L+ and the upper bound S+ of every pixel -> bit
-//                  planes hot (S+ > sigclip) and act (S+ > sigfrac*sigclip);
-//   need_kernel    needS' = dilate5(hot) & act and needS = dilate5(needS')
-//                  -> queues QS (needS) and QSP (needS'), bit plane nsp;
-//   s_kernel       at QS: m5, N, L+, S -> maps N, S;
-//   sp_kernel      at QSP: S' = S - med5(S) -> map S'; S' > sigclip -> queue QT
-//                  and bit plane test;
-//   m3need_kernel  needM3 = dilate7(test) -> queue QM3;
-//   m3_kernel      at QM3: med3 -> map M3;
-//   cand_kernel    at QT: F = m3 - med7(m3), the objlim statistic, and for each
-//                  candidate the two growths, ORed into the flag bits.
+// Detection (stages a-d) of iteration k:
+//   bound          L+ and the upper bound S+ of every pixel -> bit planes hot
+//                  (S+ > sigclip) and act (S+ > min(sigclip, sigfrac*sigclip));
+//   need           nsp = needS' = dilate5(hot) & act, needS = dilate5(nsp)
+//                  -> queues QS (S to compute) and QSP (S' to compute);
+//   s              at QS: m5, N, L+, S -> maps N, S;
+//   sp             at QSP: S' = S - med5(S) -> map S'; S' > sigclip -> bit
+//                  plane test and queue QT;
+//   m3need         needM3 = dilate3(QT) -> queue QM3;
+//   m3             at QM3: med3 -> map M3;
+//   cand           at QT: F = m3 - med7(m3), the objlim statistic, and for each
+//                  candidate the two growths, ORed into the flag bits M.
+// Replacement (stage e): the flagged pixels whose value can change are queued,
+// their values computed into a side array (rep_compute) and then written in
+// place into the one image buffer (rep_write), which starts as a copy of I0.
 //
-// The sets, and the argument that the flags equal those of the full
-// computation, are those of detect_tile (kernels.cuh). Positions in queues are
-// global pixel indices over all frames of the call (frame base + y*w + x).
-// Every window read clamps its coordinates into the frame, which equals the
-// per-map replicate-edge rule.
+// Incremental iterations. Every stage value at a pixel depends on J only within
+// a fixed radius (hot/act 2, S 2, nsp 4, S' 4, M3 1, F and the candidate test 4,
+// a candidate's growth 6). Iteration k >= 2 therefore recomputes each map only
+// where J changed within its radius since iteration k-1, and tests only the
+// candidates within 6 px of a change: a candidate farther away grows exactly
+// what it grew before, which M already holds. The changed pixels are those that
+// rep_write gave a new value; it marks, per cell of one word x kCH rows, the
+// smallest radius class (2, 4 or 6 px) that reaches into the cell. Validity
+// planes sval and m3val record where mapS/mapN and mapM3 hold current values;
+// S' is current on all of nsp (nsp and S' change only within 4 px). Iteration 1
+// treats every cell as changed.
+//
+// Replacement is exact in place: a flagged pixel with an unflagged window pixel
+// takes the lower median of its unflagged window pixels, which are I0 values
+// that are never written; only pixels whose whole window is flagged read
+// replaced values, and all values are computed before any is written. Its value
+// changes only when its window gains a flag, or, for a fully flagged window,
+// when J changes in it; iteration k >= 2 queues the flagged pixels within 2 px
+// of a new flag, and every pixel known to have a fully flagged window.
+//
+// The sets, and the argument that pruning leaves the flags unchanged, are those
+// of detect_tile (kernels.cuh). Positions in queues are global pixel indices
+// over all frames of the call (frame base + y*w + x); cells are global cell
+// indices. Every window read clamps its coordinates into the frame, which
+// equals the per-map replicate-edge rule.
 
 #pragma once
+
+#include <cooperative_groups.h>
 
 #include "kernels.cuh"
 
 namespace crb {
 
-struct Queues {
-  uint32_t* q0;   // QS, then QM3
-  uint32_t* q1;   // QSP
-  uint32_t* q2;   // QT
-  unsigned int* n;  // [0] QS, [1] QSP, [2] QM3, [3] QT, [4] flagged pixels
+namespace cg = cooperative_groups;
+
+constexpr int kCH = 8;  // rows per cell
+
+// queue counters (Queues::n)
+enum : int {
+  kNS = 0,      // QS
+  kNSP = 1,     // QSP
+  kNM3 = 2,     // QM3
+  kNT = 3,      // QT
+  kNRep = 4,    // replacement queue
+  kNFresh = 5,  // new flags of this iteration
+  kNFb = 6,     // pixels with a fully flagged window (kept over the iterations)
+  kNL2 = 7,     // cells within 2 px of a change
+  kNL6 = 8,     // cells within 6 px of a change
+  kNL9 = 9,     // cells next to a kNL6 cell (or one)
+  kNCount = 10
 };
+
+struct Queues {
+  uint32_t* q0;     // QS, then QM3, then the replacement values (as float)
+  uint32_t* q1;     // QSP, then the replacement queue
+  uint32_t* q2;     // QT
+  uint32_t* fresh;  // new flags
+  uint32_t* fbl;    // fully flagged windows
+  uint32_t *l2, *l6, *l9;  // cell lists
+  unsigned int* n;  // kNCount counters
+};
+
+// the image J of iteration k (I0, then the in-place buffer)
+__device__ __forceinline__ const float* qsrc(const Frame& f, int k) { return k == 1 ? f.img : f.out_clean; }
 
 // frame of global pixel index g (frames sorted by first pixel)
 __device__ __forceinline__ int frame_of_pixel(const Frame* frames, int nframes, long long g) {
@@ -53,34 +103,158 @@ __device__ __forceinline__ int frame_of_block(const Frame* frames, int nframes, 
   return lo;
 }
 
+// frame of global cell c (frames sorted by first cell)
+__device__ __forceinline__ int frame_of_cell(const Frame* frames, int nframes, long long c) {
+  int lo = 0, hi = nframes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (frames[mid].cell0 <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 constexpr int kBW = 8;   // words (32 px each) per block row: one warp per word column
 constexpr int kBH = 32;  // rows per block
 
+// Appends, for each lane's word `v` at (wc, y) of frame f, the set bits as
+// global pixel indices to queue q (counter *n); one atomic per warp. All 32
+// lanes call it.
+__device__ __forceinline__ void warp_emit(uint32_t v, const Frame& f, int wc, int y, uint32_t* q,
+                                          unsigned int* n) {
+  const int lane = threadIdx.x & 31;
+  const int c = __popc(v);
+  int x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
+  }
+  const int total = __shfl_sync(0xffffffffu, x, 31);
+  if (total == 0) return;
+  unsigned int base = 0;
+  if (lane == 0) base = atomicAdd(n, (unsigned int)total);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  unsigned int o = base + unsigned(x - c);
+  const uint32_t row = uint32_t(f.pix0 + (long long)y * f.w + 32 * wc);
+  while (v) {
+    const int bb = __ffs(v) - 1;
+    v &= v - 1u;
+    q[o++] = row + bb;
+  }
+}
+
+// Appends g to queue q from divergent code: one atomic per group of lanes that
+// arrive together.
+__device__ __forceinline__ void group_append(uint32_t g, uint32_t* q, unsigned int* n) {
+  cg::coalesced_group grp = cg::coalesced_threads();
+  unsigned int base = 0;
+  if (grp.thread_rank() == 0) base = atomicAdd(n, grp.size());
+  base = grp.shfl(base, 0);
+  q[base + grp.thread_rank()] = g;
+}
+
 // ---------------------------------------------------------------------------------------------
-// bound_kernel: per pixel L+ and the lower bound of m5 (smallest of the five
-// column medians) -> bits of S+ > sigclip and S+ > sigfrac*sigclip (see
-// detect_tile for the bound and its margin). One warp walks down one 32-pixel
-// word column of kBH rows, two rows per step, keeping the rows of its column
-// (and of the two halo columns on each side, held by lanes 0-3) in registers.
+// bound: per pixel L+ and the lower bound of m5 (smallest of the five column
+// medians) -> bits of S+ > sigclip and S+ > min(sigclip, sigfrac*sigclip) (see detect_tile
+// for the bound and its margin). One warp walks down one 32-pixel word column,
+// two rows per step, keeping the rows of its column (and of the two halo
+// columns on each side, held by lanes 0-3) in registers.
 //
 // Sliding column medians: the windows of rows y and y+1 share the four values
 // of rows y-1..y+2. With c1 <= c2 the two middle values of those four, the
-// median of the four and one more value e is min(max(e, c1), c2); the pair
-// (min, max) of rows y+1, y+2 is shared with the next step.
-struct ColPair {  // running state of one column
-  float lo, hi;   // min / max of the last row pair
-};
+// median of the four and one more value e is min(max(e, c1), c2).
 
 __device__ __forceinline__ float clamp_med(float e, float c1, float c2) { return fminf(fmaxf(e, c1), c2); }
 
-__global__ void __launch_bounds__(256) bound_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
-                                                    Params p, int k, int niter) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float sigclip = p.sigclip, siglow = __fmul_rn(p.sigfrac, p.sigclip);
-  const float chot = 4.f * sigclip * sigclip * 0.9999f, clow = 4.f * siglow * siglow * 0.9999f;
+// hot/act bits of word column wc, rows [y0, y1), of frame f (whole warp)
+__device__ __forceinline__ void bound_span(const Frame& f, const float* __restrict__ J, int wc, int y0, int y1,
+                                           float chot, float clow) {
+  const int lane = threadIdx.x & 31;
   // halo routing: src lane of the column median at x-2 (lanes 0,1) or x+2 (30,31); at x-1 (0) or x+1 (31)
   const int srcA = lane == 0 ? 0 : lane == 1 ? 1 : lane == 30 ? 2 : 3;
   const int srcB = lane == 0 ? 1 : 2;
+  const int w = f.w, h = f.h;
+  const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
+  const int x0 = wc * 32, x = x0 + lane;
+  const int col = min(x, w - 1);
+  const int hx = lane < 2 ? x0 - 2 + lane : x0 + 30 + lane;  // halo columns (lanes 0-3)
+  const int hcol = clampi(hx, 0, w - 1);
+  const float* __restrict__ Jc = J + col;
+  const float* __restrict__ Jh = J + hcol;
+  auto rowp = [&](int yy) { return size_t(clampi(yy, 0, h - 1)) * size_t(w); };
+  // rows y0-2 .. y0+1 of the column (a..d) and of the halo column
+  float a = __ldg(Jc + rowp(y0 - 2)), bq = __ldg(Jc + rowp(y0 - 1));
+  float cq = __ldg(Jc + rowp(y0)), d = __ldg(Jc + rowp(y0 + 1));
+  float ha = __ldg(Jh + rowp(y0 - 2)), hb = __ldg(Jh + rowp(y0 - 1));
+  float hc = __ldg(Jh + rowp(y0)), hd = __ldg(Jh + rowp(y0 + 1));
+  for (int y = y0; y < y1; y += 2) {
+    // next two rows y+2, y+3
+    const float e = __ldg(Jc + rowp(y + 2)), g = __ldg(Jc + rowp(y + 3));
+    const float he = __ldg(Jh + rowp(y + 2)), hg = __ldg(Jh + rowp(y + 3));
+    // core rows y-1..y+2 = (bq, cq) and (d, e): middle two values
+    float cm0, cm1, hcm0, hcm1;
+    {
+      const float l1 = fminf(bq, cq), h1 = fmaxf(bq, cq), l2 = fminf(d, e), h2 = fmaxf(d, e);
+      const float u = fmaxf(l1, l2), v = fminf(h1, h2);
+      const float c1 = fminf(u, v), c2 = fmaxf(u, v);
+      cm0 = clamp_med(a, c1, c2);  // rows y-2..y+2
+      cm1 = clamp_med(g, c1, c2);  // rows y-1..y+3
+      const float hl1 = fminf(hb, hc), hh1 = fmaxf(hb, hc), hl2 = fminf(hd, he), hh2 = fmaxf(hd, he);
+      const float hu = fmaxf(hl1, hl2), hv = fminf(hh1, hh2);
+      const float hc1 = fminf(hu, hv), hc2 = fmaxf(hu, hv);
+      hcm0 = clamp_med(ha, hc1, hc2);
+      hcm1 = clamp_med(hg, hc1, hc2);
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int yy = y + s;
+      if (yy >= y1) break;
+      const float cm = s ? cm1 : cm0, hcm = s ? hcm1 : hcm0;
+      float m2 = __shfl_up_sync(0xffffffffu, cm, 2), m1 = __shfl_up_sync(0xffffffffu, cm, 1);
+      float p1 = __shfl_down_sync(0xffffffffu, cm, 1), p2 = __shfl_down_sync(0xffffffffu, cm, 2);
+      const float hA = __shfl_sync(0xffffffffu, hcm, srcA), hB = __shfl_sync(0xffffffffu, hcm, srcB);
+      if (lane < 2) m2 = hA;
+      if (lane == 0) m1 = hB;
+      if (lane >= 30) p2 = hA;
+      if (lane == 31) p1 = hB;
+      const float mlow = min3f(min3f(m2, m1, cm), p1, p2);
+      // L+: the pixel, its column neighbours and its row neighbours (lanes, halo at the ends)
+      const float cc = s ? d : cq, up = s ? cq : bq, dn = s ? e : d;
+      const float hcc = s ? hd : hc;
+      const float hL = __shfl_sync(0xffffffffu, hcc, lane == 0 ? 1 : 2);
+      float left = __shfl_up_sync(0xffffffffu, cc, 1), right = __shfl_down_sync(0xffffffffu, cc, 1);
+      if (lane == 0) left = hL;
+      if (lane == 31) right = hL;
+      const float lp = lplus(cc, up, dn, left, right);
+      const float den = gain * (mlow > 0.f ? mlow : 0.f) + rn2;
+      const float lhs = lp * lp * g2;
+      const bool ok = x < w;
+      const unsigned act = __ballot_sync(0xffffffffu, ok && lhs > clow * den);
+      const unsigned hot = __ballot_sync(0xffffffffu, ok && lhs > chot * den);
+      if (lane == 0) {
+        const size_t o = size_t(yy) * f.wpr + wc;
+        f.act[o] = act;
+        f.hot[o] = hot;
+      }
+    }
+    a = cq; bq = d; cq = e; d = g;
+    ha = hc; hb = hd; hc = he; hd = hg;
+  }
+}
+
+// thresholds of the bound test: S+ > sigclip (hot), S+ > min(sigclip, sigfrac*sigclip) (act)
+__device__ __forceinline__ void bound_consts(const Params& p, float& chot, float& clow) {
+  const float sigclip = p.sigclip, tlow = fminf(__fmul_rn(p.sigfrac, p.sigclip), sigclip);
+  chot = 4.f * sigclip * sigclip * 0.9999f;
+  clow = 4.f * tlow * tlow * 0.9999f;
+}
+
+// every word column of every frame (iteration 1): blocks of kBW words x kBH rows
+__global__ void __launch_bounds__(256) bound_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
+                                                    Params p, int k) {
+  const int warp = threadIdx.x >> 5;
+  float chot, clow;
+  bound_consts(p, chot, clow);
   for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
     const int fi = frame_of_block(frames, nframes, b);
     const Frame& f = frames[fi];
@@ -88,76 +262,24 @@ __global__ void __launch_bounds__(256) bound_kernel(const Frame* __restrict__ fr
     const int bys = int(lb / f.bx), bxs = int(lb - (long long)bys * f.bx);
     const int wc = bxs * kBW + warp;
     if (wc >= f.wpr) continue;  // whole warp
-    const int w = f.w, h = f.h;
-    const float* __restrict__ J = iter_src(f, k, niter);
-    const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
-    const int x0 = wc * 32, x = x0 + lane;
-    const int col = min(x, w - 1);
-    const int hx = lane < 2 ? x0 - 2 + lane : x0 + 30 + lane;  // halo columns (lanes 0-3)
-    const int hcol = clampi(hx, 0, w - 1);
-    const int y0 = bys * kBH, y1 = min(y0 + kBH, h);
-    const float* __restrict__ Jc = J + col;
-    const float* __restrict__ Jh = J + hcol;
-    auto rowp = [&](int yy) { return size_t(clampi(yy, 0, h - 1)) * size_t(w); };
-    // rows y0-2 .. y0+1 of the column (a..d) and of the halo column
-    float a = __ldg(Jc + rowp(y0 - 2)), bq = __ldg(Jc + rowp(y0 - 1));
-    float cq = __ldg(Jc + rowp(y0)), d = __ldg(Jc + rowp(y0 + 1));
-    float ha = __ldg(Jh + rowp(y0 - 2)), hb = __ldg(Jh + rowp(y0 - 1));
-    float hc = __ldg(Jh + rowp(y0)), hd = __ldg(Jh + rowp(y0 + 1));
-    for (int y = y0; y < y1; y += 2) {
-      // next two rows y+2, y+3
-      const float e = __ldg(Jc + rowp(y + 2)), g = __ldg(Jc + rowp(y + 3));
-      const float he = __ldg(Jh + rowp(y + 2)), hg = __ldg(Jh + rowp(y + 3));
-      // core rows y-1..y+2 = (bq, cq) and (d, e): middle two values
-      float cm0, cm1, hcm0, hcm1;
-      {
-        const float l1 = fminf(bq, cq), h1 = fmaxf(bq, cq), l2 = fminf(d, e), h2 = fmaxf(d, e);
-        const float u = fmaxf(l1, l2), v = fminf(h1, h2);
-        const float c1 = fminf(u, v), c2 = fmaxf(u, v);
-        cm0 = clamp_med(a, c1, c2);   // rows y-2..y+2
-        cm1 = clamp_med(g, c1, c2);   // rows y-1..y+3
-        const float hl1 = fminf(hb, hc), hh1 = fmaxf(hb, hc), hl2 = fminf(hd, he), hh2 = fmaxf(hd, he);
-        const float hu = fmaxf(hl1, hl2), hv = fminf(hh1, hh2);
-        const float hc1 = fminf(hu, hv), hc2 = fmaxf(hu, hv);
-        hcm0 = clamp_med(ha, hc1, hc2);
-        hcm1 = clamp_med(hg, hc1, hc2);
-      }
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const int yy = y + s;
-        if (yy >= y1) break;
-        const float cm = s ? cm1 : cm0, hcm = s ? hcm1 : hcm0;
-        float m2 = __shfl_up_sync(0xffffffffu, cm, 2), m1 = __shfl_up_sync(0xffffffffu, cm, 1);
-        float p1 = __shfl_down_sync(0xffffffffu, cm, 1), p2 = __shfl_down_sync(0xffffffffu, cm, 2);
-        const float hA = __shfl_sync(0xffffffffu, hcm, srcA), hB = __shfl_sync(0xffffffffu, hcm, srcB);
-        if (lane < 2) m2 = hA;
-        if (lane == 0) m1 = hB;
-        if (lane >= 30) p2 = hA;
-        if (lane == 31) p1 = hB;
-        const float mlow = min3f(min3f(m2, m1, cm), p1, p2);
-        // L+: the pixel, its column neighbours and its row neighbours (lanes, halo at the ends)
-        const float cc = s ? d : cq, up = s ? cq : bq, dn = s ? e : d;
-        const float hcc = s ? hd : hc;
-        const float hL = __shfl_sync(0xffffffffu, hcc, lane == 0 ? 1 : 2);
-        float left = __shfl_up_sync(0xffffffffu, cc, 1), right = __shfl_down_sync(0xffffffffu, cc, 1);
-        if (lane == 0) left = hL;
-        if (lane == 31) right = hL;
-        const float lp = lplus(cc, up, dn, left, right);
-        const float den = gain * (mlow > 0.f ? mlow : 0.f) + rn2;
-        const float lhs = lp * lp * g2;
-        const bool ok = x < w;
-        const unsigned act = __ballot_sync(0xffffffffu, ok && lhs > clow * den);
-        const unsigned hot = __ballot_sync(0xffffffffu, ok && lhs > chot * den);
-        if (lane == 0) {
-          const size_t o = size_t(yy) * f.wpr + wc;
-          f.act[o] = act;
-          f.hot[o] = hot;
-          f.test[o] = 0u;
-        }
-      }
-      a = cq; bq = d; cq = e; d = g;
-      ha = hc; hb = hd; hc = he; hd = hg;
-    }
+    const int y0 = bys * kBH;
+    bound_span(f, qsrc(f, k), wc, y0, min(y0 + kBH, f.h), chot, clow);
+  }
+}
+
+// the cells of list l2 (iteration >= 2): one warp per cell
+__global__ void __launch_bounds__(256) bound_list_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
+                                                         Params p) {
+  const int warp = threadIdx.x >> 5;
+  float chot, clow;
+  bound_consts(p, chot, clow);
+  const unsigned int n = Q.n[kNL2];
+  for (unsigned int i = blockIdx.x * 8u + warp; i < n; i += gridDim.x * 8u) {
+    const uint32_t c = Q.l2[i];
+    const Frame& f = frames[frame_of_cell(frames, nframes, c)];
+    const uint32_t lc = c - uint32_t(f.cell0);
+    const int cy = int(lc / uint32_t(f.wpr)), wc = int(lc - uint32_t(cy) * uint32_t(f.wpr));
+    bound_span(f, f.out_clean, wc, cy * kCH, min(cy * kCH + kCH, f.h), chot, clow);
   }
 }
 
@@ -199,14 +321,30 @@ __device__ __forceinline__ void emit_word(uint32_t v, const Frame& f, int wc, in
   __syncthreads();
 }
 
-// need_kernel: needS' = dilate5(hot) & act, needS = dilate5(needS') within the
-// frame -> queues QS, QSP and the bit plane nsp.
+// The incremental kernels come in two forms: over all words in blocks (as in
+// iteration 1, with the cell classes deciding what each word does) and over
+// the listed cells (one warp per cell). Both are launched; the block form runs
+// when at least a quarter of the cells are listed (`dense_from`), the list
+// form otherwise.
+
+// cell class of word (wc, y) of frame f; 4 (everything changed) without classes
+__device__ __forceinline__ uint32_t cell_class(const uint32_t* __restrict__ cls, const Frame& f, int wc, int y) {
+  return cls ? cls[f.cell0 + (long long)(y / kCH) * f.wpr + wc] : 4u;
+}
+
+// need_kernel: nsp = dilate5(hot) & act, needS = dilate5(nsp) within the frame.
+// Per word by cell class (iteration 1: class 4 everywhere): within 4 px of a
+// change (class >= 3) nsp is written, test cleared and all of nsp queued for
+// S'; within 6 px only (class 2) the test bits join QT; within 6 px, S is
+// queued where needS holds and S is not current (sval; cleared within 2 px).
 __global__ void __launch_bounds__(256) need_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
-                                                   Queues Q) {
+                                                   Queues Q, const uint32_t* __restrict__ cls,
+                                                   unsigned int dense_from) {
   // rows y0-4 .. y0+kBH+3 (kBH + 8), words wc0-1 .. wc0+kBW (kBW + 2)
   constexpr int RW = kBW + 2, RR = kBH + 8;
   __shared__ uint32_t sHot[RR][RW], sAct[RR][RW], sNsp[RR][RW];
   __shared__ int ws[kThreads / 32 + 1];
+  if (cls && Q.n[kNL6] < dense_from) return;  // the list form runs
   const int t = threadIdx.x;
   for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
     const int fi = frame_of_block(frames, nframes, b);
@@ -222,7 +360,7 @@ __global__ void __launch_bounds__(256) need_kernel(const Frame* __restrict__ fra
       sAct[rr][cc] = in ? f.act[size_t(y) * f.wpr + wc] : 0u;
     }
     __syncthreads();
-    // needS' on rows y0-2 .. y0+kBH+1 (kBH + 4), all RW words
+    // nsp on rows y0-2 .. y0+kBH+1 (kBH + 4), all RW words
     for (int i = t; i < (kBH + 4) * RW; i += kThreads) {
       const int rr = i / RW + 2, cc = i - (i / RW) * RW;
       uint32_t a = 0, l = 0, r = 0;
@@ -235,31 +373,120 @@ __global__ void __launch_bounds__(256) need_kernel(const Frame* __restrict__ fra
       sNsp[rr][cc] = hdil<2>(l, a, r) & sAct[rr][cc];
     }
     __syncthreads();
-    // the block's own words: needS = dilate5(needS') in the frame; emit both queues
+    // the block's own words
     const int rr = t / kBW + 4, cc = t % kBW + 1;
     const int y = y0 + t / kBW, wc = wc0 + t % kBW;
     const bool mine = y < f.h && wc < f.wpr;
-    uint32_t a = 0, l = 0, r = 0;
+    uint32_t qs = 0, qsp = 0, qt = 0;
+    const uint32_t cl = mine ? cell_class(cls, f, wc, y) : 0u;
+    if (cl >= 2u) {
+      uint32_t a = 0, l = 0, r = 0;
 #pragma unroll
-    for (int d = -2; d <= 2; ++d) {
-      a |= sNsp[rr + d][cc];
-      l |= sNsp[rr + d][cc - 1];
-      r |= sNsp[rr + d][cc + 1];
+      for (int d = -2; d <= 2; ++d) {
+        a |= sNsp[rr + d][cc];
+        l |= sNsp[rr + d][cc - 1];
+        r |= sNsp[rr + d][cc + 1];
+      }
+      const uint32_t needS = hdil<2>(l, a, r) & frame_word(wc, f.w);
+      const size_t o = size_t(y) * f.wpr + wc;
+      if (cl >= 3u) {
+        qsp = sNsp[rr][cc];
+        f.nsp[o] = qsp;
+        f.test[o] = 0u;
+      } else {
+        qt = f.test[o];
+      }
+      const uint32_t sv = (cl >= 4u) ? 0u : f.sval[o];
+      qs = needS & ~sv;
+      f.sval[o] = sv | needS;
     }
-    const uint32_t needS = mine ? (hdil<2>(l, a, r) & frame_word(wc, f.w)) : 0u;
-    const uint32_t needSp = mine ? sNsp[rr][cc] : 0u;
-    if (mine) f.nsp[size_t(y) * f.wpr + wc] = needSp;
-    emit_word(needS, f, wc, y, Q.q0, Q.n + 0, ws);
-    emit_word(needSp, f, wc, y, Q.q1, Q.n + 1, ws);
+    emit_word(qs, f, wc, y, Q.q0, Q.n + kNS, ws);
+    emit_word(qsp, f, wc, y, Q.q1, Q.n + kNSP, ws);
+    if (cls) emit_word(qt, f, wc, y, Q.q2, Q.n + kNT, ws);
   }
 }
 
-// m3need_kernel: needM3 = dilate7(test) within the frame -> queue QM3.
+// Vertical OR over rows lane-R .. lane+R of the warp (lanes hold consecutive rows).
+template <int R>
+__device__ __forceinline__ uint32_t vor(uint32_t v) {
+  uint32_t o = v;
+#pragma unroll
+  for (int d = 1; d <= R; ++d) o |= __shfl_up_sync(0xffffffffu, v, d) | __shfl_down_sync(0xffffffffu, v, d);
+  return o;
+}
+
+// need_list_kernel (iteration >= 2), one warp per cell of list l6. Lanes 0-15
+// hold rows y0-4 .. y0+11 of the cell's word column and its neighbours; nsp is
+// recomputed on rows y0-2 .. y0+9, needS on the cell's rows (lanes 4-11).
+// Cells within 4 px of a change: nsp written, S' requeued on all of nsp, test
+// cleared (sp sets it again). Cells within 6 px only: their (current) test bits
+// join QT. S is requeued where needed and not current (all of needS in cells
+// within 2 px of a change).
+__global__ void __launch_bounds__(256) need_list_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
+                                                        const uint32_t* __restrict__ cls, unsigned int dense_from) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned int n = Q.n[kNL6];
+  if (n >= dense_from) return;  // the block form runs
+  for (unsigned int i = blockIdx.x * 8u + warp; i < n; i += gridDim.x * 8u) {
+    const uint32_t c = Q.l6[i];
+    const Frame& f = frames[frame_of_cell(frames, nframes, c)];
+    const uint32_t lc = c - uint32_t(f.cell0);
+    const int cy = int(lc / uint32_t(f.wpr)), wc = int(lc - uint32_t(cy) * uint32_t(f.wpr));
+    const uint32_t cl = cls[c];
+    const int y = cy * kCH - 4 + (lane & 15);
+    const bool rowin = lane < 16 && y >= 0 && y < f.h;
+    const size_t ro = size_t(rowin ? y : 0) * f.wpr;
+    uint32_t hv[5], aw[3];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      const int wj = wc - 2 + j;
+      hv[j] = vor<2>((rowin && wj >= 0 && wj < f.wpr) ? f.hot[ro + wj] : 0u);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int wj = wc - 1 + j;
+      aw[j] = (rowin && wj >= 0 && wj < f.wpr) ? f.act[ro + wj] : 0u;
+    }
+    uint32_t nv[3];
+    uint32_t nsp_c = 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const uint32_t ns = hdil<2>(hv[j], hv[j + 1], hv[j + 2]) & aw[j];
+      if (j == 1) nsp_c = ns;
+      nv[j] = vor<2>(ns);
+    }
+    const bool mine = lane >= 4 && lane < 4 + kCH && y < f.h;
+    uint32_t qs = 0, qsp = 0, qt = 0;
+    if (mine) {
+      const uint32_t needS = hdil<2>(nv[0], nv[1], nv[2]) & frame_word(wc, f.w);
+      const size_t o = ro + wc;
+      if (cl >= 3) {
+        f.nsp[o] = nsp_c;
+        f.test[o] = 0u;
+        qsp = nsp_c;
+      } else {
+        qt = f.test[o];
+      }
+      const uint32_t sv = (cl >= 4) ? 0u : f.sval[o];
+      qs = needS & ~sv;
+      f.sval[o] = sv | needS;
+    }
+    warp_emit(qs, f, wc, y, Q.q0, Q.n + kNS);
+    warp_emit(qsp, f, wc, y, Q.q1, Q.n + kNSP);
+    warp_emit(qt, f, wc, y, Q.q2, Q.n + kNT);
+  }
+}
+
+// m3need_kernel: needM3 = dilate3(QT) within the frame, QT = the test bits of
+// cells of class >= 2 (iteration 1: all) -> queue QM3 where M3 is not current
+// (m3val; cleared in cells of class 4), bit plane m3val.
 __global__ void __launch_bounds__(256) m3need_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
-                                                     Queues Q) {
+                                                     Queues Q, const uint32_t* __restrict__ cls,
+                                                     unsigned int dense_from) {
   constexpr int RW = kBW + 2, RR = kBH + 6;
   __shared__ uint32_t sT[RR][RW];
   __shared__ int ws[kThreads / 32 + 1];
+  if (cls && Q.n[kNL9] < dense_from) return;  // the list form runs
   const int t = threadIdx.x;
   for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
     const int fi = frame_of_block(frames, nframes, b);
@@ -270,7 +497,8 @@ __global__ void __launch_bounds__(256) m3need_kernel(const Frame* __restrict__ f
     for (int i = t; i < RR * RW; i += kThreads) {
       const int rr = i / RW, cc = i - rr * RW;
       const int y = y0 - 3 + rr, wc = wc0 - 1 + cc;
-      sT[rr][cc] = (y >= 0 && y < f.h && wc >= 0 && wc < f.wpr) ? f.test[size_t(y) * f.wpr + wc] : 0u;
+      const bool in = y >= 0 && y < f.h && wc >= 0 && wc < f.wpr;
+      sT[rr][cc] = (in && cell_class(cls, f, wc, y) >= 2u) ? f.test[size_t(y) * f.wpr + wc] : 0u;
     }
     __syncthreads();
     const int rr = t / kBW + 3, cc = t % kBW + 1;
@@ -282,8 +510,100 @@ __global__ void __launch_bounds__(256) m3need_kernel(const Frame* __restrict__ f
       l |= sT[rr + d][cc - 1];
       r |= sT[rr + d][cc + 1];
     }
-    const uint32_t need = (y < f.h && wc < f.wpr) ? (hdil<3>(l, a, r) & frame_word(wc, f.w)) : 0u;
-    emit_word(need, f, wc, y, Q.q0, Q.n + 2, ws);
+    const bool mine = y < f.h && wc < f.wpr;
+    uint32_t qm = 0;
+    if (mine) {
+      const uint32_t need = hdil<3>(l, a, r) & frame_word(wc, f.w);
+      const size_t o = size_t(y) * f.wpr + wc;
+      const uint32_t old = f.m3val[o];
+      const uint32_t mv = (cell_class(cls, f, wc, y) >= 4u) ? 0u : old;
+      qm = need & ~mv;
+      if ((mv | need) != old) f.m3val[o] = mv | need;
+    }
+    emit_word(qm, f, wc, y, Q.q0, Q.n + kNM3, ws);  // ends with a barrier: sT may be refilled
+  }
+}
+
+// m3need_list_kernel (iteration >= 2), one warp per cell of list l9: needM3 =
+// dilate3(QT), where QT = test bits in cells of class >= 2 (within 6 px of a
+// change); lanes 0-13 hold rows y0-3 .. y0+10. M3 is requeued where needed and
+// not current (all of needM3 in cells within 2 px of a change).
+__global__ void __launch_bounds__(256) m3need_list_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
+                                                          const uint32_t* __restrict__ cls, unsigned int dense_from) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned int n = Q.n[kNL9];
+  if (n >= dense_from) return;  // the block form runs
+  for (unsigned int i = blockIdx.x * 8u + warp; i < n; i += gridDim.x * 8u) {
+    const uint32_t c = Q.l9[i];
+    const Frame& f = frames[frame_of_cell(frames, nframes, c)];
+    const uint32_t lc = c - uint32_t(f.cell0);
+    const int cy = int(lc / uint32_t(f.wpr)), wc = int(lc - uint32_t(cy) * uint32_t(f.wpr));
+    const int y0 = cy * kCH;
+    const int y = y0 - 3 + lane;
+    const bool rowin = lane < kCH + 6 && y >= 0 && y < f.h;
+    const int ry = rowin ? y : 0;
+    const long long crow = f.cell0 + (long long)(ry / kCH) * f.wpr;  // first cell of this row's cell row
+    uint32_t tv[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int wj = wc - 1 + j;
+      uint32_t t = 0;
+      if (rowin && wj >= 0 && wj < f.wpr && cls[crow + wj] >= 2u) t = f.test[size_t(ry) * f.wpr + wj];
+      tv[j] = vor<3>(t);
+    }
+    const bool mine = lane >= 3 && lane < 3 + kCH && y < f.h;
+    uint32_t qm = 0;
+    if (mine) {
+      const uint32_t need = hdil<3>(tv[0], tv[1], tv[2]) & frame_word(wc, f.w);
+      const size_t o = size_t(y) * f.wpr + wc;
+      const uint32_t mv = (cls[c] >= 4u) ? 0u : f.m3val[o];
+      qm = need & ~mv;
+      f.m3val[o] = mv | need;
+    }
+    warp_emit(qm, f, wc, y, Q.q0, Q.n + kNM3);
+  }
+}
+
+// cell_list_kernel (iteration >= 2): the cells of class 4 (within 2 px of a
+// change) -> l2, class >= 2 (within 6 px) -> l6, class >= 2 or next to such a
+// cell -> l9 (needM3 reaches 3 px beyond the cells whose candidates are tested).
+__global__ void __launch_bounds__(256) cell_list_kernel(const Frame* __restrict__ frames, int nframes,
+                                                        long long ncells, const uint32_t* __restrict__ cls, Queues Q) {
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long c0 = (long long)blockIdx.x * blockDim.x; c0 < ncells; c0 += stride) {  // whole warps
+    const long long c = c0 + threadIdx.x;
+    uint32_t cl = 0;
+    bool in9 = false;
+    if (c < ncells) {
+      cl = cls[c];
+      in9 = cl >= 2u;
+      if (!in9) {
+        const Frame& f = frames[frame_of_cell(frames, nframes, c)];
+        const long long lc = c - f.cell0;
+        const int cy = int(lc / f.wpr), wc = int(lc - (long long)cy * f.wpr);
+        for (int dy = -1; dy <= 1 && !in9; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int yy = cy + dy, xx = wc + dx;
+            if (yy < 0 || yy >= f.ncy || xx < 0 || xx >= f.wpr) continue;
+            if (cls[f.cell0 + (long long)yy * f.wpr + xx] >= 2u) {
+              in9 = true;
+              break;
+            }
+          }
+      }
+    }
+    const bool put[3] = {cl >= 4u, cl >= 2u, in9};
+    uint32_t* lists[3] = {Q.l2, Q.l6, Q.l9};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const unsigned m = __ballot_sync(0xffffffffu, put[j]);
+      if (!m) continue;
+      unsigned int base = 0;
+      if (lane == 0) base = atomicAdd(Q.n + kNL2 + j, (unsigned int)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (put[j]) lists[j][base + __popc(m & ((1u << lane) - 1u))] = uint32_t(c);
+    }
   }
 }
 
@@ -305,14 +625,13 @@ __device__ __forceinline__ Pix decode(const Frame* frames, int nframes, uint32_t
 }
 
 // s_kernel: at QS, m5 (floored), N, L+ and S of J.
-__global__ void __launch_bounds__(256) s_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k,
-                                                int niter) {
-  const unsigned int n = Q.n[0];
+__global__ void __launch_bounds__(256) s_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k) {
+  const unsigned int n = Q.n[kNS];
   for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t g = Q.q0[i];
     const Pix P = decode(frames, nframes, g);
     const Frame& f = frames[P.fi];
-    const float* __restrict__ J = iter_src(f, k, niter);
+    const float* __restrict__ J = qsrc(f, k);
     int xs[5];
     size_t ro[5];
 #pragma unroll
@@ -336,7 +655,7 @@ __global__ void __launch_bounds__(256) s_kernel(const Frame* __restrict__ frames
 
 // sp_kernel: at QSP, S' = S - med5(S); S' > sigclip -> test bit and queue QT.
 __global__ void __launch_bounds__(256) sp_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p) {
-  const unsigned int n = Q.n[1];
+  const unsigned int n = Q.n[kNSP];
   const unsigned int stride = gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
   for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // whole warps iterate together
@@ -369,7 +688,7 @@ __global__ void __launch_bounds__(256) sp_kernel(const Frame* __restrict__ frame
     if (m) {
       const int leader = __ffs(m) - 1;
       unsigned int base = 0;
-      if (lane == leader) base = atomicAdd(Q.n + 3, (unsigned int)__popc(m));
+      if (lane == leader) base = atomicAdd(Q.n + kNT, (unsigned int)__popc(m));
       base = __shfl_sync(0xffffffffu, base, leader);
       if (test) Q.q2[base + __popc(m & ((1u << lane) - 1u))] = g;
     }
@@ -377,14 +696,13 @@ __global__ void __launch_bounds__(256) sp_kernel(const Frame* __restrict__ frame
 }
 
 // m3_kernel: at QM3, med3 of J.
-__global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k,
-                                                 int niter) {
-  const unsigned int n = Q.n[2];
+__global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k) {
+  const unsigned int n = Q.n[kNM3];
   for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t g = Q.q0[i];
     const Pix P = decode(frames, nframes, g);
     const Frame& f = frames[P.fi];
-    const float* __restrict__ J = iter_src(f, k, niter);
+    const float* __restrict__ J = qsrc(f, k);
     int xs[3];
     size_t ro[3];
 #pragma unroll
@@ -402,93 +720,128 @@ __global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frame
 }
 
 // cand_kernel: at QT, F = m3 - med7(m3), the objlim statistic, and for each
-// candidate the first growth (S' > sigclip) and the second (S' > sigfrac*sigclip)
-// ORed into the flag bits of M_k; counts the new flags of each frame.
-// S' is read only where the bit plane nsp says it was computed; elsewhere it
-// cannot pass a threshold.
+// candidate c the first growth g1 (S' > sigclip in the 3x3 around c) and the
+// second (S' > sigfrac*sigclip in the 3x3 around g1), as bit masks over the 5x5
+// around c, ORed into the flag bits of M_k; counts the new flags of each frame
+// and, for kFresh, lists them. S' is read only where the bit plane nsp says it
+// is current; elsewhere it cannot pass either threshold.
+template <bool kFresh>
 __global__ void __launch_bounds__(256) cand_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p,
                                                    int k) {
-  const unsigned int n = Q.n[3];
+  const unsigned int n = Q.n[kNT];
   const float sigclip = p.sigclip, siglow = __fmul_rn(p.sigfrac, p.sigclip);
-  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t g = Q.q2[i];
-    const Pix P = decode(frames, nframes, g);
-    const Frame& f = frames[P.fi];
-    const int w = f.w, h = f.h;
-    int xs[7];
-    size_t ro[7];
+  const unsigned int stride = gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // whole warps iterate together
+    const unsigned int i = i0 + threadIdx.x;
+    uint32_t fm = 0;  // new flags, bit (dy+2)*5 + (dx+2)
+    uint32_t g = 0;
+    int w = 1;
+    if (i < n) {
+      g = Q.q2[i];
+      const Pix P = decode(frames, nframes, g);
+      const Frame& f = frames[P.fi];
+      w = f.w;
+      const int h = f.h;
+      int xs[7];
+      size_t ro[7];
 #pragma unroll
-    for (int d = 0; d < 7; ++d) {
-      xs[d] = clampi(P.x - 3 + d, 0, w - 1);
-      ro[d] = size_t(clampi(P.y - 3 + d, 0, h - 1)) * w;
-    }
-    float u[49];
-#pragma unroll
-    for (int dy = 0; dy < 7; ++dy)
-#pragma unroll
-      for (int dx = 0; dx < 7; ++dx) u[dy * 7 + dx] = f.mapM3[ro[dy] + xs[dx]];
-    const size_t o = size_t(g - uint32_t(f.pix0));
-    const float fval = __fsub_rn(u[24], sel_med49(u));
-    const float fn = fmaxf(__fdiv_rn(fval, f.mapN[o]), 0.01f);
-    const float rval = (p.objlim_form == 1) ? __fdiv_rn(__fmul_rn(2.f, f.mapS[o]), fn) : __fdiv_rn(f.mapSp[o], fn);
-    if (!(rval > p.objlim)) continue;
-    unsigned int fresh = 0;
-    for (int qy = max(P.y - 1, 0); qy <= min(P.y + 1, h - 1); ++qy)
-      for (int qx = max(P.x - 1, 0); qx <= min(P.x + 1, w - 1); ++qx) {
-        if (!((f.nsp[size_t(qy) * f.wpr + (qx >> 5)] >> (qx & 31)) & 1u)) continue;
-        if (!(f.mapSp[size_t(qy) * w + qx] > sigclip)) continue;  // first growth
-        for (int ry = max(qy - 1, 0); ry <= min(qy + 1, h - 1); ++ry)
-          for (int rx = max(qx - 1, 0); rx <= min(qx + 1, w - 1); ++rx) {
-            const size_t wo = size_t(ry) * f.wpr + (rx >> 5);
-            const uint32_t bit = 1u << (rx & 31);
-            if (!(f.nsp[wo] & bit)) continue;
-            if (!(f.mapSp[size_t(ry) * w + rx] > siglow)) continue;  // second growth
-            if (f.bits_a[wo] & bit) continue;                        // already flagged
-            const uint32_t old = atomicOr(&f.bits_a[wo], bit);
-            fresh += (old & bit) ? 0u : 1u;
-          }
+      for (int d = 0; d < 7; ++d) {
+        xs[d] = clampi(P.x - 3 + d, 0, w - 1);
+        ro[d] = size_t(clampi(P.y - 3 + d, 0, h - 1)) * w;
       }
-    if (fresh) atomicAdd(f.counters + 2 * (k - 1), (unsigned long long)fresh);
+      float u[49];
+#pragma unroll
+      for (int dy = 0; dy < 7; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 7; ++dx) u[dy * 7 + dx] = f.mapM3[ro[dy] + xs[dx]];
+      const size_t o = size_t(g - uint32_t(f.pix0));
+      const float fval = __fsub_rn(u[24], sel_med49(u));
+      const float fn = fmaxf(__fdiv_rn(fval, f.mapN[o]), 0.01f);
+      const float rval =
+          (p.objlim_form == 1) ? __fdiv_rn(__fmul_rn(2.f, f.mapS[o]), fn) : __fdiv_rn(f.mapSp[o], fn);
+      if (rval > p.objlim) {
+        uint32_t A = 0, B = 0;  // S' > sigclip (3x3), S' > sigfrac*sigclip (5x5)
+#pragma unroll
+        for (int dy = -2; dy <= 2; ++dy) {
+          const int qy = P.y + dy;
+          if (qy < 0 || qy >= h) continue;
+          const uint32_t* __restrict__ nrow = f.nsp + size_t(qy) * f.wpr;
+          const float* __restrict__ srow = f.mapSp + size_t(qy) * w;
+#pragma unroll
+          for (int dx = -2; dx <= 2; ++dx) {
+            const int qx = P.x + dx;
+            if (qx < 0 || qx >= w || !((nrow[qx >> 5] >> (qx & 31)) & 1u)) continue;
+            const float s = srow[qx];
+            const int bb = (dy + 2) * 5 + dx + 2;
+            if (s > siglow) B |= 1u << bb;
+            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && s > sigclip) A |= 1u << bb;
+          }
+        }
+        // 3x3 dilation of A (inside the inner 3x3, so no shift leaves the 5x5)
+        const uint32_t dA = A | (A << 1) | (A >> 1) | (A << 5) | (A >> 5) | (A << 4) | (A >> 4) | (A << 6) | (A >> 6);
+        uint32_t g2 = dA & B;
+        while (g2) {
+          const int bb = __ffs(g2) - 1;
+          g2 &= g2 - 1u;
+          const int qy = P.y + bb / 5 - 2, qx = P.x + bb % 5 - 2;
+          const size_t wo = size_t(qy) * f.wpr + (qx >> 5);
+          const uint32_t bit = 1u << (qx & 31);
+          if (f.bits_a[wo] & bit) continue;  // already flagged
+          if (!(atomicOr(&f.bits_a[wo], bit) & bit)) fm |= 1u << bb;
+        }
+        if (fm) atomicAdd(f.counters + 2 * (k - 1), (unsigned long long)__popc(fm));
+      }
+    }
+    if (kFresh) {  // list the new flags: one atomic per warp
+      const int c = __popc(fm);
+      int x = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+      }
+      const int total = __shfl_sync(0xffffffffu, x, 31);
+      if (total) {
+        unsigned int base = 0;
+        if (lane == 0) base = atomicAdd(Q.n + kNFresh, (unsigned int)total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        unsigned int out = base + unsigned(x - c);
+        while (fm) {
+          const int bb = __ffs(fm) - 1;
+          fm &= fm - 1u;
+          // g + (dy * w + dx), with the new flag inside the frame
+          Q.fresh[out++] = uint32_t(int64_t(g) + (long long)(bb / 5 - 2) * w + (bb % 5 - 2));
+        }
+      }
+    }
   }
 }
 
 // ---------------------------------------------------------------------------------------------
-// Replacement (stage e) over a queue of the flagged pixels. Both image buffers
-// start as copies of I0, so unflagged pixels are never written and every
-// iteration only writes its flagged pixels (see replace_tile for the
-// +/-inf form of the lower median).
+// Replacement (stage e).
 
-// init_images_kernel: I0 into both image buffers of every frame (out_clean and,
-// for niter >= 2, ws). Pointers come from the descriptors, so a captured graph
-// replays correctly for new frames.
+// init_images_kernel: I0 into the image buffer (out_clean) of every frame.
+// Pointers come from the descriptors, so a captured graph replays correctly for
+// new frames.
 __global__ void __launch_bounds__(256) init_images_kernel(const Frame* __restrict__ frames, int nframes) {
   const size_t t0 = size_t(blockIdx.x) * blockDim.x + threadIdx.x, stride = size_t(gridDim.x) * blockDim.x;
   for (int fi = 0; fi < nframes; ++fi) {
     const float* __restrict__ src = frames[fi].img;
     float* __restrict__ a = frames[fi].out_clean;
-    float* __restrict__ b = frames[fi].ws;
     const size_t n = size_t(frames[fi].w) * size_t(frames[fi].h);
-    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(a) |
-                       reinterpret_cast<uintptr_t>(b)) & 15u) == 0;
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(a)) & 15u) == 0;
     size_t done = 0;
     if (vec) {
       const size_t n4 = n / 4;
-      for (size_t i = t0; i < n4; i += stride) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(src) + i);
-        reinterpret_cast<float4*>(a)[i] = v;
-        if (b) reinterpret_cast<float4*>(b)[i] = v;
-      }
+      for (size_t i = t0; i < n4; i += stride) reinterpret_cast<float4*>(a)[i] = __ldg(reinterpret_cast<const float4*>(src) + i);
       done = n4 * 4;
     }
-    for (size_t i = done + t0; i < n; i += stride) {
-      const float v = __ldg(src + i);
-      a[i] = v;
-      if (b) b[i] = v;
-    }
+    for (size_t i = done + t0; i < n; i += stride) a[i] = __ldg(src + i);
   }
 }
 
-// flagq_kernel: the flagged pixels of M_k -> queue q1 (counter n[4]).
+// flagq_kernel (iteration 1): every flagged pixel -> the replacement queue.
 __global__ void __launch_bounds__(256) flagq_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
                                                     Queues Q) {
   __shared__ int ws[kThreads / 32 + 1];
@@ -500,19 +853,51 @@ __global__ void __launch_bounds__(256) flagq_kernel(const Frame* __restrict__ fr
     const int bys = int(lb / f.bx), bxs = int(lb - (long long)bys * f.bx);
     const int y = bys * kBH + t / kBW, wc = bxs * kBW + t % kBW;
     const uint32_t v = (y < f.h && wc < f.wpr) ? (f.bits_a[size_t(y) * f.wpr + wc] & frame_word(wc, f.w)) : 0u;
-    emit_word(v, f, wc, y, Q.q1, Q.n + 4, ws);
+    emit_word(v, f, wc, y, Q.q1, Q.n + kNRep, ws);
   }
 }
 
-// rep_kernel: I_k at the queued flagged pixels, from J = I_{k-1} and M_k.
-__global__ void __launch_bounds__(256) rep_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k,
-                                                  int niter) {
-  const unsigned int n = Q.n[4];
+// Queues pixel (x, y) of frame f for replacement once (bit plane rq).
+__device__ __forceinline__ void queue_once(const Frame& f, int x, int y, Queues& Q) {
+  const size_t wo = size_t(y) * f.wpr + (x >> 5);
+  const uint32_t bit = 1u << (x & 31);
+  if (f.rq[wo] & bit) return;
+  const uint32_t old = atomicOr(&f.rq[wo], bit);
+  if (!(old & bit)) group_append(uint32_t(f.pix0 + (long long)y * f.w + x), Q.q1, Q.n + kNRep);
+}
+
+// rq_kernel (iteration >= 2): the flagged pixels within 2 px of a new flag
+// (their windows gained a flag) and every pixel with a fully flagged window (J
+// may have changed in it) -> the replacement queue.
+__global__ void __launch_bounds__(256) rq_kernel(const Frame* __restrict__ frames, int nframes, Queues Q) {
+  const unsigned int nf = Q.n[kNFresh], n = nf + Q.n[kNFb];
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const bool is_fresh = i < nf;
+    const uint32_t g = is_fresh ? Q.fresh[i] : Q.fbl[i - nf];
+    const Pix P = decode(frames, nframes, g);
+    const Frame& f = frames[P.fi];
+    if (!is_fresh) {
+      queue_once(f, P.x, P.y, Q);
+      continue;
+    }
+    for (int y = max(P.y - 2, 0); y <= min(P.y + 2, f.h - 1); ++y)
+      for (int x = max(P.x - 2, 0); x <= min(P.x + 2, f.w - 1); ++x)
+        if ((f.bits_a[size_t(y) * f.wpr + (x >> 5)] >> (x & 31)) & 1u) queue_once(f, x, y, Q);
+  }
+}
+
+// rep_compute_kernel: I_k at the queued pixels, from J = I_{k-1} and M_k, into
+// the side array q0 (nothing is written to the image yet). A pixel whose
+// window is fully flagged is counted and, the first time, listed.
+__global__ void __launch_bounds__(256) rep_compute_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
+                                                          int k) {
+  const unsigned int n = Q.n[kNRep];
+  float* __restrict__ vals = reinterpret_cast<float*>(Q.q0);
   for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t g = Q.q1[i];
     const Pix P = decode(frames, nframes, g);
     const Frame& f = frames[P.fi];
-    const float* __restrict__ J = iter_src(f, k, niter);
+    const float* __restrict__ J = qsrc(f, k);
     const uint32_t* __restrict__ M = f.bits_a;
     int xs[5], ys[5];
 #pragma unroll
@@ -527,8 +912,8 @@ __global__ void __launch_bounds__(256) rep_kernel(const Frame* __restrict__ fram
 #pragma unroll
       for (int dx = 0; dx < 5; ++dx) {
         const int q = dy * 5 + dx;
-        v[q] = __ldg(J + size_t(ys[dy]) * f.w + xs[dx]);
-        win |= ((__ldg(M + size_t(ys[dy]) * f.wpr + (xs[dx] >> 5)) >> (xs[dx] & 31)) & 1u) << q;
+        v[q] = J[size_t(ys[dy]) * f.w + xs[dx]];
+        win |= ((M[size_t(ys[dy]) * f.wpr + (xs[dx] >> 5)] >> (xs[dx] & 31)) & 1u) << q;
       }
     const int nu = 25 - __popc(win);
     float out;
@@ -545,8 +930,50 @@ __global__ void __launch_bounds__(256) rep_kernel(const Frame* __restrict__ fram
     } else {
       out = floor_m5(sel_med25(v));
       atomicAdd(f.counters + 2 * (k - 1) + 1, 1ull);
+      const size_t wo = size_t(P.y) * f.wpr + (P.x >> 5);
+      const uint32_t bit = 1u << (P.x & 31);
+      if (!(f.fb[wo] & bit) && !(atomicOr(&f.fb[wo], bit) & bit)) group_append(g, Q.fbl, Q.n + kNFb);
     }
-    iter_dst(f, k, niter)[size_t(g - uint32_t(f.pix0))] = out;
+    vals[i] = out;
+  }
+}
+
+// Marks, in the cell classes `cls`, the cells reached by a change at (x, y):
+// class 4 within 2 px, 3 within 4 px, 2 within 6 px (distance to the cell's
+// rectangle, Chebyshev).
+__device__ __forceinline__ void mark_change(const Frame& f, int x, int y, uint32_t* cls) {
+  const int cx0 = max(x - 6, 0) >> 5, cx1 = min(x + 6, f.w - 1) >> 5;
+  const int cy0 = max(y - 6, 0) / kCH, cy1 = min(y + 6, f.h - 1) / kCH;
+  for (int cy = cy0; cy <= cy1; ++cy)
+    for (int cx = cx0; cx <= cx1; ++cx) {
+      const int dx = max(0, max(32 * cx - x, x - (32 * cx + 31)));
+      const int dy = max(0, max(kCH * cy - y, y - (kCH * cy + kCH - 1)));
+      const int d = max(dx, dy);
+      const uint32_t cl = d <= 2 ? 4u : d <= 4 ? 3u : d <= 6 ? 2u : 0u;
+      if (!cl) continue;
+      uint32_t* p = cls + f.cell0 + (long long)cy * f.wpr + cx;
+      if (*p < cl) atomicMax(p, cl);
+    }
+}
+
+// rep_write_kernel: writes the computed values in place; a changed value marks
+// the cells of the next iteration (cls_next, or nothing after the last one).
+// Clears the queued bits.
+__global__ void __launch_bounds__(256) rep_write_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
+                                                        uint32_t* cls_next, int clear_rq) {
+  const unsigned int n = Q.n[kNRep];
+  const float* __restrict__ vals = reinterpret_cast<const float*>(Q.q0);
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t g = Q.q1[i];
+    const Pix P = decode(frames, nframes, g);
+    const Frame& f = frames[P.fi];
+    const size_t o = size_t(g - uint32_t(f.pix0));
+    const float v = vals[i];
+    if (__float_as_uint(f.out_clean[o]) != __float_as_uint(v)) {
+      f.out_clean[o] = v;
+      if (cls_next) mark_change(f, P.x, P.y, cls_next);
+    }
+    if (clear_rq) atomicAnd(&f.rq[size_t(P.y) * f.wpr + (P.x >> 5)], ~(1u << (P.x & 31)));
   }
 }
 
@@ -584,17 +1011,19 @@ __global__ void __launch_bounds__(256) mask_kernel(const Frame* __restrict__ fra
   }
 }
 
-// Adds the queue lengths of this iteration to the work counters of frame 0
-// (the totals of the call) and clears them for the next iteration.
+// Adds the queue lengths of iteration k to the work counters of frame 0 (the
+// totals of the call) and clears the per-iteration counters. Bound tests:
+// `dense` positions in iteration 1, kCH*32 per listed cell after it.
 __global__ void queue_work_kernel(const Frame* __restrict__ frames, Queues Q, int k, long long dense) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     unsigned long long* wk = frames[0].work + 5 * (k - 1);
-    wk[0] += Q.n[0];
-    wk[1] += Q.n[1];
-    wk[2] += Q.n[2];
-    wk[3] += Q.n[3];
-    wk[4] += (unsigned long long)dense;
-    for (int i = 0; i < 5; ++i) Q.n[i] = 0u;
+    wk[0] += Q.n[kNS];
+    wk[1] += Q.n[kNSP];
+    wk[2] += Q.n[kNM3];
+    wk[3] += Q.n[kNT];
+    wk[4] += (k == 1) ? (unsigned long long)dense : (unsigned long long)Q.n[kNL2] * (kCH * 32);
+    for (int i = 0; i < kNCount; ++i)
+      if (i != kNFb) Q.n[i] = 0u;
   }
 }
 

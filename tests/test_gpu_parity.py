@@ -122,7 +122,8 @@ def test_niter_zero_copies():
 
 @pytest.mark.parametrize("pipeline", ["queue", "tile"])
 @pytest.mark.parametrize("form", [0, 1])
-@pytest.mark.parametrize("pset", [dict(), dict(gain=1.5, readnoise=9.0, sigclip=5.0, sigfrac=0.3, objlim=4.0)])
+@pytest.mark.parametrize("pset", [dict(), dict(gain=1.5, readnoise=9.0, sigclip=5.0, sigfrac=0.3, objlim=4.0),
+                                  dict(sigclip=3.0, sigfrac=1.6, objlim=0.5)])
 def test_parameters_and_objlim_forms(form, pset, pipeline):
     img = scene(160, 120, seed=3)
     kw = dict(pset, objlim_form=form)
