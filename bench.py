@@ -44,9 +44,10 @@ DENSE_OPS_PER_PIX_ITER = 425.0
 # Algorithmic HBM bytes per pixel and iteration: read J (4 B), write I_k (4 B),
 # flag bits in and out (0.25 B).
 ALG_BYTES_PER_PIX_ITER = 8.25
-# min/max operations per dense bound-test position: median of 5 (column), two
-# three-input minima, four clips in L+.
-BOUND_TEST_MINMAX = 12 + 2 + 4
+# min/max operations per bound-test position: the sliding column median (12
+# per two rows: the middle pair of four shared values, then one clamp per
+# row), two three-input minima over the five column medians, four clips in L+.
+BOUND_TEST_MINMAX = 6 + 2 + 4
 
 
 def network_minmax():
@@ -429,8 +430,9 @@ def main():
     # work of the last step (every step cleans the same batch), averaged per detection launch
     work = cl.last_work()
     net = network_minmax()
-    minmax = sum(w[0] * net[25] + w[1] * net[25] + w[2] * net[9] + w[3] * net[49] + w[4] * BOUND_TEST_MINMAX
-                 for w in work) / max(len(work), 1)
+    # candidate test: 7 column medians of 7 and their min and max (12), the full 49-median where still open
+    minmax = sum(w[0] * net[25] + w[1] * net[25] + w[2] * net[9] + w[3] * (7 * net[7] + 12) + w[4] * net[49]
+                 + w[5] * BOUND_TEST_MINMAX for w in work) / max(len(work), 1)
     achieved = minmax / (det_avg_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": "detect (stages a-d)", "achieved": achieved, "peak": ops2 / 1e12,
                 "unit": "Tops/s", "frac": achieved / (ops2 / 1e12), "traffic": None,
@@ -438,8 +440,8 @@ def main():
                                f"{ops3 / 1e12:.2f})",
                 "achieved_is": "min/max operations of the selection networks the method evaluated (counted live "
                                "per launch) / average detect launch time",
-                "work_per_launch": {"S": work[-1][0], "Sprime": work[-1][1], "med3": work[-1][2],
-                                    "cand_tests": work[-1][3], "bound_tests": work[-1][4]} if work else None,
+                "work_per_iteration": [{"S": w[0], "Sprime": w[1], "med3": w[2], "cand_tests": w[3],
+                                        "cand_full_median": w[4], "bound_tests": w[5]} for w in work],
                 "dense_equivalent_tops": DENSE_OPS_PER_PIX_ITER * npix / (det_avg_ms * 1e-3) / 1e12,
                 "detect_ms_avg": det_avg_ms, "replace_ms_avg": rep_avg_ms,
                 "detect_share": det_ms / max(det_ms + rep_ms, 1e-9),

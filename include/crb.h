@@ -152,12 +152,14 @@ int crb_sync_status(crb_ctx* ctx, cudaStream_t stream);
  * neighbour. Returns the number of iterations written (<= max_iter), or -1. */
 int crb_last_counts(crb_ctx* ctx, long long* out, int max_iter);
 
-/* After crb_sync_status: the work the detection kernel did in each iteration
- * of the last call, summed over its frames: out[5k..5k+4] = positions at which
- * it evaluated S (5x5 median of J), S' (5x5 median of S), med3, the candidate
- * test (7x7 median of med3), and the dense upper-bound test. The stages are
- * evaluated only where they can change a flag, so these counts are the
- * method's work on this input. Returns the number of iterations, or -1. */
+/* After crb_sync_status: the work the detection kernels did in each iteration
+ * of the last call, summed over its frames: out[6k..6k+5] = positions at which
+ * they evaluated S (5x5 median of J), S' (5x5 median of S), med3, the
+ * candidate test, the full 7x7 median of med3 for that test (the tests that
+ * bounds of the median leave open; every test in the tile pipeline), and the
+ * upper-bound test. The stages are evaluated only where they can change a
+ * flag, so these counts are the method's work on this input. Returns the
+ * number of iterations, or -1. */
 int crb_last_work(crb_ctx* ctx, long long* out, int max_iter);
 
 /* One iteration from an explicit state, for stage-by-stage checks:

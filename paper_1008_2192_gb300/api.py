@@ -122,12 +122,13 @@ class Cleaner:
         return [(int(buf[2 * i]), int(buf[2 * i + 1])) for i in range(k)]
 
     def last_work(self):
-        """Per iteration of the last call: positions given (S, S', med3, candidate test, bound test)."""
-        buf = (ctypes.c_longlong * (5 * max(self.niter, 1)))()
+        """Per iteration of the last call: positions given (S, S', med3, candidate test, full 7x7 median of
+        the test, bound test)."""
+        buf = (ctypes.c_longlong * (6 * max(self.niter, 1)))()
         k = _lib.load().crb_last_work(self._h, buf, max(self.niter, 1))
         if k < 0:
             raise RuntimeError("crb_last_work failed")
-        return [tuple(int(buf[5 * i + j]) for j in range(5)) for i in range(k)]
+        return [tuple(int(buf[6 * i + j]) for j in range(6)) for i in range(k)]
 
     def profile_read(self, reset=True):
         """(detect ms, detect launches, replace ms, replace launches) since the last reset."""

@@ -69,7 +69,7 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 // queue pipeline kernels, for the occupancy table
 enum QK {
   kQBound, kQNeed, kQS, kQSp, kQM3need, kQM3, kQCand, kQRepCompute, kQBoundList, kQNeedList, kQM3needList, kQRq,
-  kQRepWrite, kQCellList, kQKernels
+  kQRepWrite, kQCellList, kQCandFull, kQGrow, kQKernels
 };
 
 struct GraphKey {
@@ -161,10 +161,11 @@ int init_ctx(crb_ctx* c) {
         reinterpret_cast<const void*>(crb::bound_kernel),       reinterpret_cast<const void*>(crb::need_kernel),
         reinterpret_cast<const void*>(crb::s_kernel),           reinterpret_cast<const void*>(crb::sp_kernel),
         reinterpret_cast<const void*>(crb::m3need_kernel),      reinterpret_cast<const void*>(crb::m3_kernel),
-        reinterpret_cast<const void*>(crb::cand_kernel<true>),        reinterpret_cast<const void*>(crb::rep_compute_kernel),
+        reinterpret_cast<const void*>(crb::cand_test_kernel),        reinterpret_cast<const void*>(crb::rep_compute_kernel),
         reinterpret_cast<const void*>(crb::bound_list_kernel),  reinterpret_cast<const void*>(crb::need_list_kernel),
         reinterpret_cast<const void*>(crb::m3need_list_kernel), reinterpret_cast<const void*>(crb::rq_kernel),
-        reinterpret_cast<const void*>(crb::rep_write_kernel),   reinterpret_cast<const void*>(crb::cell_list_kernel)};
+        reinterpret_cast<const void*>(crb::rep_write_kernel),   reinterpret_cast<const void*>(crb::cell_list_kernel),
+        reinterpret_cast<const void*>(crb::cand_full_kernel),   reinterpret_cast<const void*>(crb::grow_kernel<true>)};
     for (int i = 0; i < kQKernels; ++i) {
       int o = 0;
       CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[i], 256, 0));
@@ -274,8 +275,8 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
   }
   CRB_CUDA(cudaMemsetAsync(c->ws, 0, P.bits_total, stream));
   if (P.queue) {
-    // the image buffer starts as I0: every replacement then writes only its flagged pixels
-    crb::init_images_kernel<<<c->num_sms * 8, 256, 0, stream>>>(c->d_frames, P.n);
+    // the image buffer starts as I0 (copied by the first bound pass): every
+    // replacement then writes only its flagged pixels
     auto grid = [&](int kind, long long units) {
       return int(std::max<long long>(1, std::min<long long>(units, (long long)c->num_sms * c->occ_q[kind])));
     };
@@ -307,10 +308,12 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
           crb::m3need_list_kernel<<<gq * c->occ_q[kQM3needList], 256, 0, stream>>>(c->d_frames, P.n, P.Q, cls,
                                                                                    dense_from);
         crb::m3_kernel<<<gq * c->occ_q[kQM3], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k);
+        crb::cand_test_kernel<<<gq * c->occ_q[kQCand], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
+        crb::cand_full_kernel<<<gq * c->occ_q[kQCandFull], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
         if (k == 1)
-          crb::cand_kernel<false><<<gq * c->occ_q[kQCand], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
+          crb::grow_kernel<false><<<gq * c->occ_q[kQGrow], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
         else
-          crb::cand_kernel<true><<<gq * c->occ_q[kQCand], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
+          crb::grow_kernel<true><<<gq * c->occ_q[kQGrow], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
       });
       // the classes of iteration k+1 start at zero (those of iteration k-1 were read by now)
       if (k >= 3 && cls_next) CRB_CUDA(cudaMemsetAsync(cls_next, 0, cells_bytes, stream));
@@ -319,9 +322,10 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
           crb::flagq_kernel<<<grid(kQNeed, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q);
         else
           crb::rq_kernel<<<gq * c->occ_q[kQRq], 256, 0, stream>>>(c->d_frames, P.n, P.Q);
-        crb::rep_compute_kernel<<<gq * c->occ_q[kQRepCompute], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k);
-        crb::rep_write_kernel<<<gq * c->occ_q[kQRepWrite], 256, 0, stream>>>(c->d_frames, P.n, P.Q, cls_next,
-                                                                            k >= 2 ? 1 : 0);
+        crb::rep_compute_kernel<<<gq * c->occ_q[kQRepCompute], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k,
+                                                                                cls_next);
+        if (k >= 2)
+          crb::rep_write_kernel<<<gq * c->occ_q[kQRepWrite], 256, 0, stream>>>(c->d_frames, P.n, P.Q, cls_next, 1);
         if (k == P.niter) crb::mask_kernel<<<grid(kQNeed, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks);
       });
       crb::queue_work_kernel<<<1, 32, 0, stream>>>(c->d_frames, P.Q, k, P.npix);
@@ -393,7 +397,7 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
   const size_t off_q = total;
   total += 5 * qbytes + 3 * lbytes;
   const int nit = niter > 0 ? niter : 1;
-  const int ncounters = 7 * nit * n;
+  const int ncounters = (2 + crb::kWork) * nit * n;
   int rc = ensure_frames(c, n);
   if (rc) return rc;
   rc = ensure_ws(c, total, ncounters);
@@ -428,7 +432,7 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
     f.mapM3 = reinterpret_cast<float*>(pm + 3 * fmap);
     f.out_mask = s.out_mask;
     f.maps = nullptr;
-    f.counters = c->d_counters + size_t(7) * nit * i;
+    f.counters = c->d_counters + size_t(2 + crb::kWork) * nit * i;
     f.work = f.counters + size_t(2) * nit;
     f.w = s.w;
     f.h = s.h;
@@ -493,7 +497,7 @@ int prepare(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool map
     if (niter >= 2) total += align256(size_t(s.w) * size_t(s.h) * 4);
   }
   const int nit = niter > 0 ? niter : 1;
-  const int ncounters = 7 * nit * n;  // per frame: 2 per iteration, then 5 per iteration of work
+  const int ncounters = (2 + crb::kWork) * nit * n;  // per frame: 2 per iteration, then kWork per iteration
   int rc = ensure_frames(c, n);
   if (rc) return rc;
   rc = ensure_ws(c, total > 0 ? total : 256, ncounters);
@@ -512,7 +516,7 @@ int prepare(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool map
                                            align256(size_t(s.w + 31) / 32 * size_t(s.h) * 4));
     f.out_mask = s.out_mask;
     f.maps = s.maps;
-    f.counters = c->d_counters + size_t(7) * nit * i;
+    f.counters = c->d_counters + size_t(2 + crb::kWork) * nit * i;
     f.work = f.counters + size_t(2) * nit;
     f.w = s.w;
     f.h = s.h;
@@ -785,7 +789,7 @@ int read_counters(crb_ctx* c, long long* out, int max_iter, int base, int width)
   const int k = std::min(c->last_niter, max_iter);
   if (k == 0 || c->last_nframes == 0) return 0;
   const int nit = c->last_niter;
-  std::vector<unsigned long long> tmp(size_t(7) * nit * c->last_nframes);
+  std::vector<unsigned long long> tmp(size_t(2 + crb::kWork) * nit * c->last_nframes);
   if (cudaMemcpy(tmp.data(), c->d_counters, sizeof(unsigned long long) * tmp.size(), cudaMemcpyDeviceToHost) !=
       cudaSuccess)
     return -1;
@@ -793,7 +797,7 @@ int read_counters(crb_ctx* c, long long* out, int max_iter, int base, int width)
     for (int j = 0; j < width; ++j) {
       long long s = 0;
       for (int fr = 0; fr < c->last_nframes; ++fr)
-        s += (long long)tmp[size_t(7) * nit * fr + size_t(base) * nit + size_t(width) * it + j];
+        s += (long long)tmp[size_t(2 + crb::kWork) * nit * fr + size_t(base) * nit + size_t(width) * it + j];
       out[width * it + j] = s;
     }
   return k;
@@ -802,7 +806,9 @@ int read_counters(crb_ctx* c, long long* out, int max_iter, int base, int width)
 
 int crb_last_counts(crb_ctx* c, long long* out, int max_iter) { return read_counters(c, out, max_iter, 0, 2); }
 
-int crb_last_work(crb_ctx* c, long long* out, int max_iter) { return read_counters(c, out, max_iter, 2, 5); }
+int crb_last_work(crb_ctx* c, long long* out, int max_iter) {
+  return read_counters(c, out, max_iter, 2, crb::kWork);
+}
 
 int crb_profile_read(crb_ctx* c, double* detect_ms, int* detect_launches, double* replace_ms,
                      int* replace_launches, int reset) {

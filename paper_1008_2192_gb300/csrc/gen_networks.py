@@ -219,7 +219,8 @@ def emit(name, n, rank, d, order, out):
     return "\n".join(lines)
 
 
-SPECS = [("sel_med5", 5, 2), ("sel_med9", 9, 4), ("sel_med25", 25, 12), ("sel_med49", 49, 24)]
+SPECS = [("sel_med5", 5, 2), ("sel_med7", 7, 3), ("sel_med9", 9, 4), ("sel_med25", 25, 12),
+         ("sel_med49", 49, 24)]
 
 PRELUDE = """// Three-input min/max (PTX min.f32 / max.f32 with three sources, sm_100+).
 __device__ __forceinline__ float min3f(float a, float b, float c) {

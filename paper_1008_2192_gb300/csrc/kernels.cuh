@@ -27,6 +27,9 @@ namespace crb {
 
 constexpr int kThreads = 256;
 constexpr int kNumMaps = 11;  // m5, L+, N, S, S', m3, F, R, cand, g1, g2
+// work counters per iteration: positions given S, S', med3, a candidate test,
+// the full 7x7 median of that test, and the bound test
+constexpr int kWork = 6;
 
 // One frame of a launch. In the tile pipeline the image buffers alternate
 // between iterations so that iteration niter writes out_clean: I_k goes to
@@ -42,8 +45,7 @@ struct Frame {
   uint8_t* out_mask;      // caller's 0/1 mask, written by the last replacement
   float* maps;            // kNumMaps debug maps (crb_iterate) or nullptr
   unsigned long long* counters;  // 2 per iteration: new flags, no-unflagged-neighbour pixels
-  unsigned long long* work;      // nullable; 5 per iteration: positions given S, S', med3, a
-                                 // candidate test, and the dense bound test
+  unsigned long long* work;      // nullable; kWork per iteration (see kWork)
   int w, h, wpr;
   float gain, rn;
   int tiles_x, rtiles_x;  // detect / replace tiles per row of tiles
@@ -544,11 +546,11 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
                               nSp, cnt + 4);
   __syncthreads();
   if (tid == 0 && f.work) {
-    unsigned long long* wk = f.work + 5 * (k - 1);
+    unsigned long long* wk = f.work + kWork * (k - 1);
     const long long dense = (long long)(min(x0 + TW + 2, w) - imax(x0 - 2, 0)) * (min(y0 + TH + 2, h) - imax(y0 - 2, 0));
     atomicAdd(wk + 0, (unsigned long long)nS);
     atomicAdd(wk + 1, (unsigned long long)nSp);
-    atomicAdd(wk + 4, (unsigned long long)dense);
+    atomicAdd(wk + 5, (unsigned long long)dense);
   }
 
   // P6: (a)+(b) at the listed positions: m5, N, L+, S
@@ -630,8 +632,9 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
                               cnt + 4);
   __syncthreads();
   if (tid == 0 && f.work) {
-    atomicAdd(f.work + 5 * (k - 1) + 2, (unsigned long long)nM3);
-    atomicAdd(f.work + 5 * (k - 1) + 3, (unsigned long long)cnt[0]);
+    atomicAdd(f.work + kWork * (k - 1) + 2, (unsigned long long)nM3);
+    atomicAdd(f.work + kWork * (k - 1) + 3, (unsigned long long)cnt[0]);  // every test takes the full median
+    atomicAdd(f.work + kWork * (k - 1) + 4, (unsigned long long)cnt[0]);
   }
 
   // P9: med3 at the listed positions

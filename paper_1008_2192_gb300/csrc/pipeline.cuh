@@ -11,11 +11,16 @@
 //                  plane test and queue QT;
 //   m3need         needM3 = dilate3(QT) -> queue QM3;
 //   m3             at QM3: med3 -> map M3;
-//   cand           at QT: F = m3 - med7(m3), the objlim statistic, and for each
-//                  candidate the two growths, ORed into the flag bits M.
+//   cand_test      at QT: the objlim test from bounds of med7(m3) (smallest
+//                  and largest column median), decided exactly where they
+//                  suffice -> candidates; otherwise -> open tests;
+//   cand_full      at the open tests: F = m3 - med7(m3) and the test ->
+//                  candidates;
+//   grow           at the candidates: the two growths, ORed into the flags M.
 // Replacement (stage e): the flagged pixels whose value can change are queued,
 // their values computed into a side array (rep_compute) and then written in
-// place into the one image buffer (rep_write), which starts as a copy of I0.
+// place into the one image buffer (rep_write), which the first bound pass
+// starts as a copy of I0.
 //
 // Incremental iterations. Every stage value at a pixel depends on J only within
 // a fixed radius (hot/act 2, S 2, nsp 4, S' 4, M3 1, F and the candidate test 4,
@@ -67,12 +72,14 @@ enum : int {
   kNL2 = 7,     // cells within 2 px of a change
   kNL6 = 8,     // cells within 6 px of a change
   kNL9 = 9,     // cells next to a kNL6 cell (or one)
-  kNCount = 10
+  kNPass = 10,  // candidates (passed the objlim test)
+  kNAmb = 11,   // tests the column-median bounds leave open
+  kNCount = 12
 };
 
 struct Queues {
-  uint32_t* q0;     // QS, then QM3, then the replacement values (as float)
-  uint32_t* q1;     // QSP, then the replacement queue
+  uint32_t* q0;     // QS, then QM3, then the candidates, then the replacement values (as float)
+  uint32_t* q1;     // QSP, then the open tests, then the replacement queue
   uint32_t* q2;     // QT
   uint32_t* fresh;  // new flags
   uint32_t* fbl;    // fully flagged windows
@@ -166,9 +173,11 @@ __device__ __forceinline__ void group_append(uint32_t g, uint32_t* q, unsigned i
 
 __device__ __forceinline__ float clamp_med(float e, float c1, float c2) { return fminf(fmaxf(e, c1), c2); }
 
-// hot/act bits of word column wc, rows [y0, y1), of frame f (whole warp)
+// hot/act bits of word column wc, rows [y0, y1), of frame f (whole warp);
+// copy != nullptr also copies those pixels of J there (iteration 1: I0 into the
+// image buffer).
 __device__ __forceinline__ void bound_span(const Frame& f, const float* __restrict__ J, int wc, int y0, int y1,
-                                           float chot, float clow) {
+                                           float chot, float clow, float* __restrict__ copy) {
   const int lane = threadIdx.x & 31;
   // halo routing: src lane of the column median at x-2 (lanes 0,1) or x+2 (30,31); at x-1 (0) or x+1 (31)
   const int srcA = lane == 0 ? 0 : lane == 1 ? 1 : lane == 30 ? 2 : 3;
@@ -226,6 +235,7 @@ __device__ __forceinline__ void bound_span(const Frame& f, const float* __restri
       if (lane == 0) left = hL;
       if (lane == 31) right = hL;
       const float lp = lplus(cc, up, dn, left, right);
+      if (copy && x < w) copy[size_t(yy) * w + x] = cc;
       const float den = gain * (mlow > 0.f ? mlow : 0.f) + rn2;
       const float lhs = lp * lp * g2;
       const bool ok = x < w;
@@ -249,7 +259,8 @@ __device__ __forceinline__ void bound_consts(const Params& p, float& chot, float
   clow = 4.f * tlow * tlow * 0.9999f;
 }
 
-// every word column of every frame (iteration 1): blocks of kBW words x kBH rows
+// every word column of every frame (iteration 1; it also starts the image
+// buffer as a copy of I0): blocks of kBW words x kBH rows
 __global__ void __launch_bounds__(256) bound_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
                                                     Params p, int k) {
   const int warp = threadIdx.x >> 5;
@@ -263,7 +274,7 @@ __global__ void __launch_bounds__(256) bound_kernel(const Frame* __restrict__ fr
     const int wc = bxs * kBW + warp;
     if (wc >= f.wpr) continue;  // whole warp
     const int y0 = bys * kBH;
-    bound_span(f, qsrc(f, k), wc, y0, min(y0 + kBH, f.h), chot, clow);
+    bound_span(f, qsrc(f, k), wc, y0, min(y0 + kBH, f.h), chot, clow, k == 1 ? f.out_clean : nullptr);
   }
 }
 
@@ -279,7 +290,7 @@ __global__ void __launch_bounds__(256) bound_list_kernel(const Frame* __restrict
     const Frame& f = frames[frame_of_cell(frames, nframes, c)];
     const uint32_t lc = c - uint32_t(f.cell0);
     const int cy = int(lc / uint32_t(f.wpr)), wc = int(lc - uint32_t(cy) * uint32_t(f.wpr));
-    bound_span(f, f.out_clean, wc, cy * kCH, min(cy * kCH + kCH, f.h), chot, clow);
+    bound_span(f, f.out_clean, wc, cy * kCH, min(cy * kCH + kCH, f.h), chot, clow, nullptr);
   }
 }
 
@@ -719,16 +730,116 @@ __global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frame
   }
 }
 
-// cand_kernel: at QT, F = m3 - med7(m3), the objlim statistic, and for each
-// candidate c the first growth g1 (S' > sigclip in the 3x3 around c) and the
-// second (S' > sigfrac*sigclip in the 3x3 around g1), as bit masks over the 5x5
-// around c, ORed into the flag bits of M_k; counts the new flags of each frame
-// and, for kFresh, lists them. S' is read only where the bit plane nsp says it
-// is current; elsewhere it cannot pass either threshold.
-template <bool kFresh>
-__global__ void __launch_bounds__(256) cand_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p,
-                                                   int k) {
+// The objlim test of candidate c: S'(c) / max(F/N, 0.01) > objlim (article
+// form: 2S(c) / max(F/N, 0.01)), F = m3(c) - med7(m3)(c). Every operation is
+// monotone (IEEE rounding is monotone; N > 0, and S, S' > 0 at a test
+// position), so a lower bound of med7 gives an upper bound of F and a lower
+// bound of the statistic, and vice versa.
+__device__ __forceinline__ float objlim_stat(const Params& p, float fval, float nn, float s, float sp) {
+  const float fn = fmaxf(__fdiv_rn(fval, nn), 0.01f);
+  return (p.objlim_form == 1) ? __fdiv_rn(__fmul_rn(2.f, s), fn) : __fdiv_rn(sp, fn);
+}
+
+// Appends g to queue q when pred holds (warp-aggregated; every lane calls it).
+__device__ __forceinline__ void warp_append_if(bool pred, uint32_t g, uint32_t* q, unsigned int* n) {
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (!m) return;
+  const int leader = __ffs(m) - 1;
+  unsigned int base = 0;
+  if (lane == leader) base = atomicAdd(n, (unsigned int)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (pred) q[base + __popc(m & ((1u << lane) - 1u))] = g;
+}
+
+// cand_test_kernel: at QT, the 7 column medians of the 7x7 window of m3; at
+// most 3 values of a column lie below (above) its median, so at most 21 of 49
+// lie below the smallest (above the largest) column median, which bound
+// med7(m3) from below (above). Tests the bounds decide go to the candidates
+// (pass) or are dropped; the rest to the open tests.
+__global__ void __launch_bounds__(256) cand_test_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
+                                                        Params p) {
   const unsigned int n = Q.n[kNT];
+  const unsigned int stride = gridDim.x * blockDim.x;
+  for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // whole warps iterate together
+    const unsigned int i = i0 + threadIdx.x;
+    bool pass = false, open = false;
+    uint32_t g = 0;
+    if (i < n) {
+      g = Q.q2[i];
+      const Pix P = decode(frames, nframes, g);
+      const Frame& f = frames[P.fi];
+      size_t ro[7];
+#pragma unroll
+      for (int d = 0; d < 7; ++d) ro[d] = size_t(clampi(P.y - 3 + d, 0, f.h - 1)) * f.w;
+      float lo = INFINITY, hi = -INFINITY, mc = 0.f;
+#pragma unroll
+      for (int dx = 0; dx < 7; ++dx) {
+        const int xx = clampi(P.x - 3 + dx, 0, f.w - 1);
+        float col[7];
+#pragma unroll
+        for (int dy = 0; dy < 7; ++dy) col[dy] = f.mapM3[ro[dy] + xx];
+        if (dx == 3) mc = col[3];
+        const float cm = sel_med7(col);
+        lo = fminf(lo, cm);
+        hi = fmaxf(hi, cm);
+      }
+      const size_t o = size_t(g - uint32_t(f.pix0));
+      const float nn = f.mapN[o], sv = f.mapS[o], spv = f.mapSp[o];
+      const float rlow = objlim_stat(p, __fsub_rn(mc, lo), nn, sv, spv);   // F at its largest
+      const float rhigh = objlim_stat(p, __fsub_rn(mc, hi), nn, sv, spv);  // F at its smallest
+      pass = rlow > p.objlim;
+      open = !pass && rhigh > p.objlim;
+    }
+    warp_append_if(pass, g, Q.q0, Q.n + kNPass);
+    warp_append_if(open, g, Q.q1, Q.n + kNAmb);
+  }
+}
+
+// cand_full_kernel: at the open tests, the exact F = m3 - med7(m3) and the
+// objlim test -> candidates.
+__global__ void __launch_bounds__(256) cand_full_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
+                                                        Params p) {
+  const unsigned int n = Q.n[kNAmb];
+  const unsigned int stride = gridDim.x * blockDim.x;
+  for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // whole warps iterate together
+    const unsigned int i = i0 + threadIdx.x;
+    bool pass = false;
+    uint32_t g = 0;
+    if (i < n) {
+      g = Q.q1[i];
+      const Pix P = decode(frames, nframes, g);
+      const Frame& f = frames[P.fi];
+      int xs[7];
+      size_t ro[7];
+#pragma unroll
+      for (int d = 0; d < 7; ++d) {
+        xs[d] = clampi(P.x - 3 + d, 0, f.w - 1);
+        ro[d] = size_t(clampi(P.y - 3 + d, 0, f.h - 1)) * f.w;
+      }
+      float u[49];
+#pragma unroll
+      for (int dy = 0; dy < 7; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 7; ++dx) u[dy * 7 + dx] = f.mapM3[ro[dy] + xs[dx]];
+      const size_t o = size_t(g - uint32_t(f.pix0));
+      const float fval = __fsub_rn(u[24], sel_med49(u));
+      pass = objlim_stat(p, fval, f.mapN[o], f.mapS[o], f.mapSp[o]) > p.objlim;
+    }
+    warp_append_if(pass, g, Q.q0, Q.n + kNPass);
+  }
+}
+
+// grow_kernel: for each candidate c, the first growth g1 (S' > sigclip in the
+// 3x3 around c) and the second (S' > sigfrac*sigclip in the 3x3 around g1), as
+// bit masks over the 5x5 around c, ORed into the flag bits of M_k; counts the
+// new flags of each frame and, for kFresh, lists them. S' is read only where
+// the bit plane nsp says it is current; elsewhere it cannot pass either
+// threshold.
+template <bool kFresh>
+__global__ void __launch_bounds__(256) grow_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p,
+                                                   int k) {
+  const unsigned int n = Q.n[kNPass];
   const float sigclip = p.sigclip, siglow = __fmul_rn(p.sigfrac, p.sigclip);
   const unsigned int stride = gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
@@ -738,60 +849,41 @@ __global__ void __launch_bounds__(256) cand_kernel(const Frame* __restrict__ fra
     uint32_t g = 0;
     int w = 1;
     if (i < n) {
-      g = Q.q2[i];
+      g = Q.q0[i];
       const Pix P = decode(frames, nframes, g);
       const Frame& f = frames[P.fi];
       w = f.w;
       const int h = f.h;
-      int xs[7];
-      size_t ro[7];
+      uint32_t A = 0, B = 0;  // S' > sigclip (3x3), S' > sigfrac*sigclip (5x5)
 #pragma unroll
-      for (int d = 0; d < 7; ++d) {
-        xs[d] = clampi(P.x - 3 + d, 0, w - 1);
-        ro[d] = size_t(clampi(P.y - 3 + d, 0, h - 1)) * w;
-      }
-      float u[49];
+      for (int dy = -2; dy <= 2; ++dy) {
+        const int qy = P.y + dy;
+        if (qy < 0 || qy >= h) continue;
+        const uint32_t* __restrict__ nrow = f.nsp + size_t(qy) * f.wpr;
+        const float* __restrict__ srow = f.mapSp + size_t(qy) * w;
 #pragma unroll
-      for (int dy = 0; dy < 7; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 7; ++dx) u[dy * 7 + dx] = f.mapM3[ro[dy] + xs[dx]];
-      const size_t o = size_t(g - uint32_t(f.pix0));
-      const float fval = __fsub_rn(u[24], sel_med49(u));
-      const float fn = fmaxf(__fdiv_rn(fval, f.mapN[o]), 0.01f);
-      const float rval =
-          (p.objlim_form == 1) ? __fdiv_rn(__fmul_rn(2.f, f.mapS[o]), fn) : __fdiv_rn(f.mapSp[o], fn);
-      if (rval > p.objlim) {
-        uint32_t A = 0, B = 0;  // S' > sigclip (3x3), S' > sigfrac*sigclip (5x5)
-#pragma unroll
-        for (int dy = -2; dy <= 2; ++dy) {
-          const int qy = P.y + dy;
-          if (qy < 0 || qy >= h) continue;
-          const uint32_t* __restrict__ nrow = f.nsp + size_t(qy) * f.wpr;
-          const float* __restrict__ srow = f.mapSp + size_t(qy) * w;
-#pragma unroll
-          for (int dx = -2; dx <= 2; ++dx) {
-            const int qx = P.x + dx;
-            if (qx < 0 || qx >= w || !((nrow[qx >> 5] >> (qx & 31)) & 1u)) continue;
-            const float s = srow[qx];
-            const int bb = (dy + 2) * 5 + dx + 2;
-            if (s > siglow) B |= 1u << bb;
-            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && s > sigclip) A |= 1u << bb;
-          }
+        for (int dx = -2; dx <= 2; ++dx) {
+          const int qx = P.x + dx;
+          if (qx < 0 || qx >= w || !((nrow[qx >> 5] >> (qx & 31)) & 1u)) continue;
+          const float sv = srow[qx];
+          const int bb = (dy + 2) * 5 + dx + 2;
+          if (sv > siglow) B |= 1u << bb;
+          if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && sv > sigclip) A |= 1u << bb;
         }
-        // 3x3 dilation of A (inside the inner 3x3, so no shift leaves the 5x5)
-        const uint32_t dA = A | (A << 1) | (A >> 1) | (A << 5) | (A >> 5) | (A << 4) | (A >> 4) | (A << 6) | (A >> 6);
-        uint32_t g2 = dA & B;
-        while (g2) {
-          const int bb = __ffs(g2) - 1;
-          g2 &= g2 - 1u;
-          const int qy = P.y + bb / 5 - 2, qx = P.x + bb % 5 - 2;
-          const size_t wo = size_t(qy) * f.wpr + (qx >> 5);
-          const uint32_t bit = 1u << (qx & 31);
-          if (f.bits_a[wo] & bit) continue;  // already flagged
-          if (!(atomicOr(&f.bits_a[wo], bit) & bit)) fm |= 1u << bb;
-        }
-        if (fm) atomicAdd(f.counters + 2 * (k - 1), (unsigned long long)__popc(fm));
       }
+      // 3x3 dilation of A (inside the inner 3x3, so no shift leaves the 5x5)
+      const uint32_t dA = A | (A << 1) | (A >> 1) | (A << 5) | (A >> 5) | (A << 4) | (A >> 4) | (A << 6) | (A >> 6);
+      uint32_t g2 = dA & B;
+      while (g2) {
+        const int bb = __ffs(g2) - 1;
+        g2 &= g2 - 1u;
+        const int qy = P.y + bb / 5 - 2, qx = P.x + bb % 5 - 2;
+        const size_t wo = size_t(qy) * f.wpr + (qx >> 5);
+        const uint32_t bit = 1u << (qx & 31);
+        if (f.bits_a[wo] & bit) continue;  // already flagged
+        if (!(atomicOr(&f.bits_a[wo], bit) & bit)) fm |= 1u << bb;
+      }
+      if (fm) atomicAdd(f.counters + 2 * (k - 1), (unsigned long long)__popc(fm));
     }
     if (kFresh) {  // list the new flags: one atomic per warp
       const int c = __popc(fm);
@@ -820,26 +912,6 @@ __global__ void __launch_bounds__(256) cand_kernel(const Frame* __restrict__ fra
 
 // ---------------------------------------------------------------------------------------------
 // Replacement (stage e).
-
-// init_images_kernel: I0 into the image buffer (out_clean) of every frame.
-// Pointers come from the descriptors, so a captured graph replays correctly for
-// new frames.
-__global__ void __launch_bounds__(256) init_images_kernel(const Frame* __restrict__ frames, int nframes) {
-  const size_t t0 = size_t(blockIdx.x) * blockDim.x + threadIdx.x, stride = size_t(gridDim.x) * blockDim.x;
-  for (int fi = 0; fi < nframes; ++fi) {
-    const float* __restrict__ src = frames[fi].img;
-    float* __restrict__ a = frames[fi].out_clean;
-    const size_t n = size_t(frames[fi].w) * size_t(frames[fi].h);
-    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(a)) & 15u) == 0;
-    size_t done = 0;
-    if (vec) {
-      const size_t n4 = n / 4;
-      for (size_t i = t0; i < n4; i += stride) reinterpret_cast<float4*>(a)[i] = __ldg(reinterpret_cast<const float4*>(src) + i);
-      done = n4 * 4;
-    }
-    for (size_t i = done + t0; i < n; i += stride) a[i] = __ldg(src + i);
-  }
-}
 
 // flagq_kernel (iteration 1): every flagged pixel -> the replacement queue.
 __global__ void __launch_bounds__(256) flagq_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
@@ -886,11 +958,31 @@ __global__ void __launch_bounds__(256) rq_kernel(const Frame* __restrict__ frame
   }
 }
 
+// Marks, in the cell classes `cls`, the cells reached by a change at (x, y):
+// class 4 within 2 px, 3 within 4 px, 2 within 6 px (distance to the cell's
+// rectangle, Chebyshev).
+__device__ __forceinline__ void mark_change(const Frame& f, int x, int y, uint32_t* cls) {
+  const int cx0 = max(x - 6, 0) >> 5, cx1 = min(x + 6, f.w - 1) >> 5;
+  const int cy0 = max(y - 6, 0) / kCH, cy1 = min(y + 6, f.h - 1) / kCH;
+  for (int cy = cy0; cy <= cy1; ++cy)
+    for (int cx = cx0; cx <= cx1; ++cx) {
+      const int dx = max(0, max(32 * cx - x, x - (32 * cx + 31)));
+      const int dy = max(0, max(kCH * cy - y, y - (kCH * cy + kCH - 1)));
+      const int d = max(dx, dy);
+      const uint32_t cl = d <= 2 ? 4u : d <= 4 ? 3u : d <= 6 ? 2u : 0u;
+      if (!cl) continue;
+      uint32_t* p = cls + f.cell0 + (long long)cy * f.wpr + cx;
+      if (*p < cl) atomicMax(p, cl);
+    }
+}
+
 // rep_compute_kernel: I_k at the queued pixels, from J = I_{k-1} and M_k, into
 // the side array q0 (nothing is written to the image yet). A pixel whose
-// window is fully flagged is counted and, the first time, listed.
+// window is fully flagged is counted and, the first time, listed. In
+// iteration 1, J = I0 is not the image buffer, so the values go to the buffer
+// directly (`cls_next`: cell classes to mark, or nullptr).
 __global__ void __launch_bounds__(256) rep_compute_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
-                                                          int k) {
+                                                          int k, uint32_t* cls_next) {
   const unsigned int n = Q.n[kNRep];
   float* __restrict__ vals = reinterpret_cast<float*>(Q.q0);
   for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -934,26 +1026,14 @@ __global__ void __launch_bounds__(256) rep_compute_kernel(const Frame* __restric
       const uint32_t bit = 1u << (P.x & 31);
       if (!(f.fb[wo] & bit) && !(atomicOr(&f.fb[wo], bit) & bit)) group_append(g, Q.fbl, Q.n + kNFb);
     }
-    vals[i] = out;
-  }
-}
-
-// Marks, in the cell classes `cls`, the cells reached by a change at (x, y):
-// class 4 within 2 px, 3 within 4 px, 2 within 6 px (distance to the cell's
-// rectangle, Chebyshev).
-__device__ __forceinline__ void mark_change(const Frame& f, int x, int y, uint32_t* cls) {
-  const int cx0 = max(x - 6, 0) >> 5, cx1 = min(x + 6, f.w - 1) >> 5;
-  const int cy0 = max(y - 6, 0) / kCH, cy1 = min(y + 6, f.h - 1) / kCH;
-  for (int cy = cy0; cy <= cy1; ++cy)
-    for (int cx = cx0; cx <= cx1; ++cx) {
-      const int dx = max(0, max(32 * cx - x, x - (32 * cx + 31)));
-      const int dy = max(0, max(kCH * cy - y, y - (kCH * cy + kCH - 1)));
-      const int d = max(dx, dy);
-      const uint32_t cl = d <= 2 ? 4u : d <= 4 ? 3u : d <= 6 ? 2u : 0u;
-      if (!cl) continue;
-      uint32_t* p = cls + f.cell0 + (long long)cy * f.wpr + cx;
-      if (*p < cl) atomicMax(p, cl);
+    if (k == 1) {
+      const size_t o = size_t(g - uint32_t(f.pix0));
+      f.out_clean[o] = out;
+      if (cls_next && __float_as_uint(out) != __float_as_uint(J[o])) mark_change(f, P.x, P.y, cls_next);
+    } else {
+      vals[i] = out;
     }
+  }
 }
 
 // rep_write_kernel: writes the computed values in place; a changed value marks
@@ -1016,12 +1096,13 @@ __global__ void __launch_bounds__(256) mask_kernel(const Frame* __restrict__ fra
 // `dense` positions in iteration 1, kCH*32 per listed cell after it.
 __global__ void queue_work_kernel(const Frame* __restrict__ frames, Queues Q, int k, long long dense) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
-    unsigned long long* wk = frames[0].work + 5 * (k - 1);
+    unsigned long long* wk = frames[0].work + kWork * (k - 1);
     wk[0] += Q.n[kNS];
     wk[1] += Q.n[kNSP];
     wk[2] += Q.n[kNM3];
     wk[3] += Q.n[kNT];
-    wk[4] += (k == 1) ? (unsigned long long)dense : (unsigned long long)Q.n[kNL2] * (kCH * 32);
+    wk[4] += Q.n[kNAmb];
+    wk[5] += (k == 1) ? (unsigned long long)dense : (unsigned long long)Q.n[kNL2] * (kCH * 32);
     for (int i = 0; i < kNCount; ++i)
       if (i != kNFb) Q.n[i] = 0u;
   }
