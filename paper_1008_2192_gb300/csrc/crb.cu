@@ -81,11 +81,13 @@ struct GraphKey {
   void* ws;
   void* counters;
   void* frames;
+  void* tab;
   bool operator==(const GraphKey& o) const {
     return n == o.n && niter == o.niter && shape == o.shape && fuse == o.fuse && queue == o.queue &&
            tiles == o.tiles && nblocks == o.nblocks && ncells == o.ncells && npix == o.npix &&
            rtiles == o.rtiles && bits_total == o.bits_total && ncounters == o.ncounters && dgrid == o.dgrid &&
-           fgrid == o.fgrid && rgrid == o.rgrid && ws == o.ws && counters == o.counters && frames == o.frames;
+           fgrid == o.fgrid && rgrid == o.rgrid && ws == o.ws && counters == o.counters && frames == o.frames &&
+           tab == o.tab;
   }
 };
 
@@ -119,6 +121,9 @@ struct crb_ctx {
   crb::Frame* d_frames = nullptr;
   int frames_cap = 0;
   crb::Frame* h_frames = nullptr;  // pinned staging
+  uint32_t* d_tab = nullptr;       // queue pipeline: frame of each 2^kTabShift pixels
+  uint32_t* h_tab = nullptr;       // pinned staging
+  size_t tab_cap = 0, tab_n = 0;   // entries
   unsigned long long* d_counters = nullptr;
   int counters_cap = 0;  // in unsigned long longs
   int last_niter = 0;
@@ -222,6 +227,20 @@ int ensure_frames(crb_ctx* c, int n) {
   CRB_CUDA(cudaMalloc(&c->d_frames, sizeof(crb::Frame) * size_t(n)));
   CRB_CUDA(cudaMallocHost(&c->h_frames, sizeof(crb::Frame) * size_t(n)));
   c->frames_cap = n;
+  return CRB_OK;
+}
+
+int ensure_tab(crb_ctx* c, size_t entries) {
+  if (entries <= c->tab_cap) return CRB_OK;
+  CRB_CUDA(cudaDeviceSynchronize());
+  cudaFree(c->d_tab);
+  cudaFreeHost(c->h_tab);
+  c->d_tab = nullptr;
+  c->h_tab = nullptr;
+  c->tab_cap = 0;
+  CRB_CUDA(cudaMalloc(&c->d_tab, sizeof(uint32_t) * entries));
+  CRB_CUDA(cudaMallocHost(&c->h_tab, sizeof(uint32_t) * entries));
+  c->tab_cap = entries;
   return CRB_OK;
 }
 
@@ -451,6 +470,16 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
     f.cell0 = cell0;
     cell0 += (long long)f.wpr * f.ncy;
   }
+  // frame of the first pixel of each 2^kTabShift pixels (frames are consecutive ranges)
+  const size_t tab_n = size_t(npix >> crb::kTabShift) + 1;
+  rc = ensure_tab(c, tab_n);
+  if (rc) return rc;
+  c->tab_n = tab_n;
+  for (size_t t = 0, fi = 0; t < tab_n; ++t) {
+    const long long g = (long long)t << crb::kTabShift;
+    while (fi + 1 < size_t(n) && c->h_frames[fi + 1].pix0 <= g) ++fi;
+    c->h_tab[t] = uint32_t(fi);
+  }
   P.n = n;
   P.niter = niter;
   P.shape = 0;
@@ -467,6 +496,7 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
   P.cells[0] = reinterpret_cast<uint32_t*>(ws + off_cells);
   P.cells[1] = reinterpret_cast<uint32_t*>(ws + off_cells + align256(size_t(ncells) * 4));
   P.Q.n = reinterpret_cast<unsigned int*>(ws);
+  P.Q.ftab = c->d_tab;
   P.Q.q0 = reinterpret_cast<uint32_t*>(ws + off_q);
   P.Q.q1 = reinterpret_cast<uint32_t*>(ws + off_q + qbytes);
   P.Q.q2 = reinterpret_cast<uint32_t*>(ws + off_q + 2 * qbytes);
@@ -549,6 +579,8 @@ int prepare(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool map
 int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
   CRB_CUDA(cudaMemcpyAsync(c->d_frames, c->h_frames, sizeof(crb::Frame) * size_t(P.n), cudaMemcpyHostToDevice,
                            stream));
+  if (P.queue)
+    CRB_CUDA(cudaMemcpyAsync(c->d_tab, c->h_tab, sizeof(uint32_t) * c->tab_n, cudaMemcpyHostToDevice, stream));
   CRB_CUDA(cudaEventRecord(c->upload_ev, stream));
   c->last_niter = P.niter;
   c->last_nframes = P.n;
@@ -559,7 +591,7 @@ int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
 int launch_graph(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs, cudaStream_t stream) {
   GraphKey key{P.n,      P.niter,      P.shape,      P.fuse,  P.queue, P.tiles,          P.rtiles,
                P.nblocks, P.ncells,     P.npix,       P.bits_total, P.ncounters, P.dgrid, P.fgrid,
-               P.rgrid,   c->ws,        c->d_counters, c->d_frames};
+               P.rgrid,   c->ws,        c->d_counters, c->d_frames, P.queue ? c->d_tab : nullptr};
   for (auto& g : c->graphs)
     if (g.first == key) {
       CRB_CUDA(cudaGraphLaunch(g.second, stream));
@@ -723,8 +755,10 @@ void crb_destroy(crb_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaFree(c->ws);
   cudaFree(c->d_frames);
+  cudaFree(c->d_tab);
   cudaFree(c->d_counters);
   if (c->h_frames) cudaFreeHost(c->h_frames);
+  if (c->h_tab) cudaFreeHost(c->h_tab);
   if (c->upload_ev) cudaEventDestroy(c->upload_ev);
   if (c->done_ev) cudaEventDestroy(c->done_ev);
   delete c;

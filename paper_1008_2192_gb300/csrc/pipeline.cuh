@@ -58,7 +58,8 @@ namespace crb {
 
 namespace cg = cooperative_groups;
 
-constexpr int kCH = 8;  // rows per cell
+constexpr int kCH = 8;         // rows per cell
+constexpr int kTabShift = 16;  // pixels per entry of the frame table: 2^kTabShift
 
 // queue counters (Queues::n)
 enum : int {
@@ -85,20 +86,11 @@ struct Queues {
   uint32_t* fbl;    // fully flagged windows
   uint32_t *l2, *l6, *l9;  // cell lists
   unsigned int* n;  // kNCount counters
+  const uint32_t* ftab;  // frame of global pixel t << kTabShift
 };
 
 // the image J of iteration k (I0, then the in-place buffer)
 __device__ __forceinline__ const float* qsrc(const Frame& f, int k) { return k == 1 ? f.img : f.out_clean; }
-
-// frame of global pixel index g (frames sorted by first pixel)
-__device__ __forceinline__ int frame_of_pixel(const Frame* frames, int nframes, long long g) {
-  int lo = 0, hi = nframes - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (frames[mid].pix0 <= g) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
 
 // frame of word block b (frames sorted by first block)
 __device__ __forceinline__ int frame_of_block(const Frame* frames, int nframes, long long b) {
@@ -625,11 +617,15 @@ struct Pix {
   int fi, x, y;
 };
 
-__device__ __forceinline__ Pix decode(const Frame* frames, int nframes, uint32_t g) {
+// Frame and coordinates of global pixel index g: the table gives the frame of
+// the first pixel of g's 2^kTabShift block, later frames in the block follow.
+__device__ __forceinline__ Pix decode(const Frame* frames, int nframes, const Queues& Q, uint32_t g) {
   Pix p;
-  p.fi = frame_of_pixel(frames, nframes, (long long)g);
-  const uint32_t o = g - uint32_t(frames[p.fi].pix0);
-  const int w = frames[p.fi].w;
+  int fi = int(__ldg(Q.ftab + (g >> kTabShift)));
+  while (fi + 1 < nframes && frames[fi + 1].pix0 <= (long long)g) ++fi;
+  p.fi = fi;
+  const uint32_t o = g - uint32_t(frames[fi].pix0);
+  const int w = frames[fi].w;
   p.y = int(o / uint32_t(w));
   p.x = int(o - uint32_t(p.y) * uint32_t(w));
   return p;
@@ -640,7 +636,7 @@ __global__ void __launch_bounds__(256) s_kernel(const Frame* __restrict__ frames
   const unsigned int n = Q.n[kNS];
   for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t g = Q.q0[i];
-    const Pix P = decode(frames, nframes, g);
+    const Pix P = decode(frames, nframes, Q, g);
     const Frame& f = frames[P.fi];
     const float* __restrict__ J = qsrc(f, k);
     int xs[5];
@@ -675,7 +671,7 @@ __global__ void __launch_bounds__(256) sp_kernel(const Frame* __restrict__ frame
     uint32_t g = 0;
     if (i < n) {
       g = Q.q1[i];
-      const Pix P = decode(frames, nframes, g);
+      const Pix P = decode(frames, nframes, Q, g);
       const Frame& f = frames[P.fi];
       int xs[5];
       size_t ro[5];
@@ -711,7 +707,7 @@ __global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frame
   const unsigned int n = Q.n[kNM3];
   for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t g = Q.q0[i];
-    const Pix P = decode(frames, nframes, g);
+    const Pix P = decode(frames, nframes, Q, g);
     const Frame& f = frames[P.fi];
     const float* __restrict__ J = qsrc(f, k);
     int xs[3];
@@ -767,7 +763,7 @@ __global__ void __launch_bounds__(256) cand_test_kernel(const Frame* __restrict_
     uint32_t g = 0;
     if (i < n) {
       g = Q.q2[i];
-      const Pix P = decode(frames, nframes, g);
+      const Pix P = decode(frames, nframes, Q, g);
       const Frame& f = frames[P.fi];
       size_t ro[7];
 #pragma unroll
@@ -808,7 +804,7 @@ __global__ void __launch_bounds__(256) cand_full_kernel(const Frame* __restrict_
     uint32_t g = 0;
     if (i < n) {
       g = Q.q1[i];
-      const Pix P = decode(frames, nframes, g);
+      const Pix P = decode(frames, nframes, Q, g);
       const Frame& f = frames[P.fi];
       int xs[7];
       size_t ro[7];
@@ -850,38 +846,67 @@ __global__ void __launch_bounds__(256) grow_kernel(const Frame* __restrict__ fra
     int w = 1;
     if (i < n) {
       g = Q.q0[i];
-      const Pix P = decode(frames, nframes, g);
+      const Pix P = decode(frames, nframes, Q, g);
       const Frame& f = frames[P.fi];
       w = f.w;
       const int h = f.h;
+      // the 5x5 around c: nsp bits and S' values, loaded without dependencies
+      // (clamped; out-of-frame positions are masked)
+      const int xs = P.x - 2;                      // first column of the 5x5
+      const int wl = max(xs, 0) >> 5, wr = min(P.x + 2, w - 1) >> 5;
+      int cx[5];
+#pragma unroll
+      for (int dx = 0; dx < 5; ++dx) cx[dx] = clampi(xs + dx, 0, w - 1);
+      uint32_t nb[5];
+      float sv[5][5];
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        const size_t qy = size_t(clampi(P.y + r - 2, 0, h - 1));
+        const uint64_t pair = uint64_t(f.nsp[qy * f.wpr + wl]) | (uint64_t(f.nsp[qy * f.wpr + wr]) << 32);
+        // bit dx = nsp at column xs + dx (columns left of the frame read as 0 below)
+        const int sh = xs - 32 * wl;  // in [-2, 31]
+        nb[r] = uint32_t(sh >= 0 ? (pair >> sh) : (pair << -sh)) & 31u;
+#pragma unroll
+        for (int dx = 0; dx < 5; ++dx) sv[r][dx] = f.mapSp[qy * w + cx[dx]];
+      }
+      uint32_t inx = 0;  // columns inside the frame
+#pragma unroll
+      for (int dx = 0; dx < 5; ++dx) inx |= (xs + dx >= 0 && xs + dx < w) ? (1u << dx) : 0u;
       uint32_t A = 0, B = 0;  // S' > sigclip (3x3), S' > sigfrac*sigclip (5x5)
 #pragma unroll
-      for (int dy = -2; dy <= 2; ++dy) {
-        const int qy = P.y + dy;
-        if (qy < 0 || qy >= h) continue;
-        const uint32_t* __restrict__ nrow = f.nsp + size_t(qy) * f.wpr;
-        const float* __restrict__ srow = f.mapSp + size_t(qy) * w;
+      for (int r = 0; r < 5; ++r) {
+        const bool rowin = P.y + r - 2 >= 0 && P.y + r - 2 < h;
+        const uint32_t ok = rowin ? (nb[r] & inx) : 0u;
 #pragma unroll
-        for (int dx = -2; dx <= 2; ++dx) {
-          const int qx = P.x + dx;
-          if (qx < 0 || qx >= w || !((nrow[qx >> 5] >> (qx & 31)) & 1u)) continue;
-          const float sv = srow[qx];
-          const int bb = (dy + 2) * 5 + dx + 2;
-          if (sv > siglow) B |= 1u << bb;
-          if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && sv > sigclip) A |= 1u << bb;
+        for (int dx = 0; dx < 5; ++dx) {
+          const bool valid = (ok >> dx) & 1u;
+          const int bb = r * 5 + dx;
+          if (valid && sv[r][dx] > siglow) B |= 1u << bb;
+          if (valid && r >= 1 && r <= 3 && dx >= 1 && dx <= 3 && sv[r][dx] > sigclip) A |= 1u << bb;
         }
       }
       // 3x3 dilation of A (inside the inner 3x3, so no shift leaves the 5x5)
       const uint32_t dA = A | (A << 1) | (A >> 1) | (A << 5) | (A >> 5) | (A << 4) | (A >> 4) | (A << 6) | (A >> 6);
-      uint32_t g2 = dA & B;
-      while (g2) {
-        const int bb = __ffs(g2) - 1;
-        g2 &= g2 - 1u;
-        const int qy = P.y + bb / 5 - 2, qx = P.x + bb % 5 - 2;
-        const size_t wo = size_t(qy) * f.wpr + (qx >> 5);
-        const uint32_t bit = 1u << (qx & 31);
-        if (f.bits_a[wo] & bit) continue;  // already flagged
-        if (!(atomicOr(&f.bits_a[wo], bit) & bit)) fm |= 1u << bb;
+      const uint32_t g2 = dA & B;
+      // OR each row's flags into its (at most two) flag words
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        const uint32_t m = (g2 >> (5 * r)) & 31u;
+        if (!m) continue;
+        const int qy = P.y + r - 2;
+        const int w0 = (xs + __ffs(m) - 1) >> 5;  // word of the lowest flag
+        const int sh = xs - 32 * w0;              // in [-4, 31]
+        const uint64_t mm = sh >= 0 ? (uint64_t(m) << sh) : (uint64_t(m) >> -sh);
+        uint64_t fresh = 0;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const uint32_t part = uint32_t(mm >> (32 * j));
+          if (!part) continue;
+          uint32_t* wp = f.bits_a + size_t(qy) * f.wpr + w0 + j;
+          if ((*wp & part) == part) continue;  // already flagged
+          fresh |= uint64_t(part & ~atomicOr(wp, part)) << (32 * j);
+        }
+        fm |= (uint32_t(sh >= 0 ? (fresh >> sh) : (fresh << -sh)) & 31u) << (5 * r);
       }
       if (fm) atomicAdd(f.counters + 2 * (k - 1), (unsigned long long)__popc(fm));
     }
@@ -946,7 +971,7 @@ __global__ void __launch_bounds__(256) rq_kernel(const Frame* __restrict__ frame
   for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const bool is_fresh = i < nf;
     const uint32_t g = is_fresh ? Q.fresh[i] : Q.fbl[i - nf];
-    const Pix P = decode(frames, nframes, g);
+    const Pix P = decode(frames, nframes, Q, g);
     const Frame& f = frames[P.fi];
     if (!is_fresh) {
       queue_once(f, P.x, P.y, Q);
@@ -987,7 +1012,7 @@ __global__ void __launch_bounds__(256) rep_compute_kernel(const Frame* __restric
   float* __restrict__ vals = reinterpret_cast<float*>(Q.q0);
   for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t g = Q.q1[i];
-    const Pix P = decode(frames, nframes, g);
+    const Pix P = decode(frames, nframes, Q, g);
     const Frame& f = frames[P.fi];
     const float* __restrict__ J = qsrc(f, k);
     const uint32_t* __restrict__ M = f.bits_a;
@@ -1045,7 +1070,7 @@ __global__ void __launch_bounds__(256) rep_write_kernel(const Frame* __restrict_
   const float* __restrict__ vals = reinterpret_cast<const float*>(Q.q0);
   for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t g = Q.q1[i];
-    const Pix P = decode(frames, nframes, g);
+    const Pix P = decode(frames, nframes, Q, g);
     const Frame& f = frames[P.fi];
     const size_t o = size_t(g - uint32_t(f.pix0));
     const float v = vals[i];
