@@ -324,6 +324,31 @@ __device__ __forceinline__ void emit_word(uint32_t v, const Frame& f, int wc, in
   __syncthreads();
 }
 
+// Appends g to each list j with put[j] (NL <= 3 lists, counters n[0..NL-1]),
+// in thread order; one atomic per block and list. Every thread of the block
+// calls it; ws holds kThreads/32 + 1 ints, sbase NL.
+template <int NL>
+__device__ __forceinline__ void block_append(const bool (&put)[NL], uint32_t g, uint32_t* const (&q)[NL],
+                                             unsigned int* n, int* ws, unsigned int* sbase) {
+  int packed = 0;  // 10 bits per list (at most kThreads entries each)
+#pragma unroll
+  for (int j = 0; j < NL; ++j) packed |= (put[j] ? 1 : 0) << (10 * j);
+  int total = 0;
+  const int off = block_excl_scan(packed, ws, total);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const unsigned int t = unsigned(total >> (10 * j)) & 1023u;
+      sbase[j] = t ? atomicAdd(n + j, t) : 0u;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NL; ++j)
+    if (put[j]) q[j][sbase[j] + (unsigned(off >> (10 * j)) & 1023u)] = g;
+  __syncthreads();
+}
+
 // The incremental kernels come in two forms: over all words in blocks (as in
 // iteration 1, with the cell classes deciding what each word does) and over
 // the listed cells (one warp per cell). Both are launched; the block form runs
@@ -405,7 +430,7 @@ __global__ void __launch_bounds__(256) need_kernel(const Frame* __restrict__ fra
     }
     emit_word(qs, f, wc, y, Q.q0, Q.n + kNS, ws);
     emit_word(qsp, f, wc, y, Q.q1, Q.n + kNSP, ws);
-    if (cls) emit_word(qt, f, wc, y, Q.q2, Q.n + kNT, ws);
+    if (cls) emit_word(qt, f, wc, y, Q.q2, Q.n + kNT, ws);  // emit_word ends with a barrier
   }
 }
 
@@ -572,9 +597,10 @@ __global__ void __launch_bounds__(256) m3need_list_kernel(const Frame* __restric
 // cell -> l9 (needM3 reaches 3 px beyond the cells whose candidates are tested).
 __global__ void __launch_bounds__(256) cell_list_kernel(const Frame* __restrict__ frames, int nframes,
                                                         long long ncells, const uint32_t* __restrict__ cls, Queues Q) {
-  const int lane = threadIdx.x & 31;
+  __shared__ int ws[kThreads / 32 + 1];
+  __shared__ unsigned int sbase[3];
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long c0 = (long long)blockIdx.x * blockDim.x; c0 < ncells; c0 += stride) {  // whole warps
+  for (long long c0 = (long long)blockIdx.x * blockDim.x; c0 < ncells; c0 += stride) {  // whole blocks
     const long long c = c0 + threadIdx.x;
     uint32_t cl = 0;
     bool in9 = false;
@@ -597,16 +623,8 @@ __global__ void __launch_bounds__(256) cell_list_kernel(const Frame* __restrict_
       }
     }
     const bool put[3] = {cl >= 4u, cl >= 2u, in9};
-    uint32_t* lists[3] = {Q.l2, Q.l6, Q.l9};
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const unsigned m = __ballot_sync(0xffffffffu, put[j]);
-      if (!m) continue;
-      unsigned int base = 0;
-      if (lane == 0) base = atomicAdd(Q.n + kNL2 + j, (unsigned int)__popc(m));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (put[j]) lists[j][base + __popc(m & ((1u << lane) - 1u))] = uint32_t(c);
-    }
+    uint32_t* const lists[3] = {Q.l2, Q.l6, Q.l9};
+    block_append<3>(put, uint32_t(c), lists, Q.n + kNL2, ws, sbase);
   }
 }
 
@@ -631,6 +649,34 @@ __device__ __forceinline__ Pix decode(const Frame* frames, int nframes, const Qu
   return p;
 }
 
+// The (2R+1)^2 window of map a around (x, y), row-major, coordinates clamped
+// into the w x h frame; away from the frame edge the loads take immediate
+// offsets from one row pointer.
+template <int R>
+__device__ __forceinline__ void load_window(const float* __restrict__ a, int x, int y, int w, int h,
+                                            float (&v)[(2 * R + 1) * (2 * R + 1)]) {
+  constexpr int D = 2 * R + 1;
+  if (x >= R && x < w - R && y >= R && y < h - R) {
+    const float* __restrict__ p = a + size_t(y - R) * w + (x - R);
+#pragma unroll
+    for (int dy = 0; dy < D; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < D; ++dx) v[dy * D + dx] = __ldg(p + size_t(dy) * w + dx);
+  } else {
+    int xs[D];
+    size_t ro[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      xs[d] = clampi(x - R + d, 0, w - 1);
+      ro[d] = size_t(clampi(y - R + d, 0, h - 1)) * w;
+    }
+#pragma unroll
+    for (int dy = 0; dy < D; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < D; ++dx) v[dy * D + dx] = __ldg(a + ro[dy] + xs[dx]);
+  }
+}
+
 // s_kernel: at QS, m5 (floored), N, L+ and S of J.
 __global__ void __launch_bounds__(256) s_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k) {
   const unsigned int n = Q.n[kNS];
@@ -638,19 +684,8 @@ __global__ void __launch_bounds__(256) s_kernel(const Frame* __restrict__ frames
     const uint32_t g = Q.q0[i];
     const Pix P = decode(frames, nframes, Q, g);
     const Frame& f = frames[P.fi];
-    const float* __restrict__ J = qsrc(f, k);
-    int xs[5];
-    size_t ro[5];
-#pragma unroll
-    for (int d = 0; d < 5; ++d) {
-      xs[d] = clampi(P.x - 2 + d, 0, f.w - 1);
-      ro[d] = size_t(clampi(P.y - 2 + d, 0, f.h - 1)) * f.w;
-    }
     float v[25];
-#pragma unroll
-    for (int dy = 0; dy < 5; ++dy)
-#pragma unroll
-      for (int dx = 0; dx < 5; ++dx) v[dy * 5 + dx] = __ldg(J + ro[dy] + xs[dx]);
+    load_window<2>(qsrc(f, k), P.x, P.y, f.w, f.h, v);
     const float lp = lplus(v[12], v[7], v[17], v[11], v[13]);
     const float m5f = floor_m5(sel_med25(v));
     const float nn = noise_of(m5f, f.gain, __fmul_rn(f.rn, f.rn));
@@ -662,10 +697,11 @@ __global__ void __launch_bounds__(256) s_kernel(const Frame* __restrict__ frames
 
 // sp_kernel: at QSP, S' = S - med5(S); S' > sigclip -> test bit and queue QT.
 __global__ void __launch_bounds__(256) sp_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p) {
+  __shared__ int ws[kThreads / 32 + 1];
+  __shared__ unsigned int sbase[1];
   const unsigned int n = Q.n[kNSP];
   const unsigned int stride = gridDim.x * blockDim.x;
-  const int lane = threadIdx.x & 31;
-  for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // whole warps iterate together
+  for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // whole blocks iterate together
     const unsigned int i = i0 + threadIdx.x;
     bool test = false;
     uint32_t g = 0;
@@ -673,32 +709,17 @@ __global__ void __launch_bounds__(256) sp_kernel(const Frame* __restrict__ frame
       g = Q.q1[i];
       const Pix P = decode(frames, nframes, Q, g);
       const Frame& f = frames[P.fi];
-      int xs[5];
-      size_t ro[5];
-#pragma unroll
-      for (int d = 0; d < 5; ++d) {
-        xs[d] = clampi(P.x - 2 + d, 0, f.w - 1);
-        ro[d] = size_t(clampi(P.y - 2 + d, 0, f.h - 1)) * f.w;
-      }
       float v[25];
-#pragma unroll
-      for (int dy = 0; dy < 5; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 5; ++dx) v[dy * 5 + dx] = f.mapS[ro[dy] + xs[dx]];
+      load_window<2>(f.mapS, P.x, P.y, f.w, f.h, v);
       const float sp = __fsub_rn(v[12], sel_med25(v));
       const size_t o = size_t(g - uint32_t(f.pix0));
       f.mapSp[o] = sp;
       test = sp > p.sigclip;
       if (test) atomicOr(&f.test[size_t(P.y) * f.wpr + (P.x >> 5)], 1u << (P.x & 31));
     }
-    const unsigned m = __ballot_sync(0xffffffffu, test);
-    if (m) {
-      const int leader = __ffs(m) - 1;
-      unsigned int base = 0;
-      if (lane == leader) base = atomicAdd(Q.n + kNT, (unsigned int)__popc(m));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (test) Q.q2[base + __popc(m & ((1u << lane) - 1u))] = g;
-    }
+    const bool put[1] = {test};
+    uint32_t* const lists[1] = {Q.q2};
+    block_append<1>(put, g, lists, Q.n + kNT, ws, sbase);
   }
 }
 
@@ -709,19 +730,8 @@ __global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frame
     const uint32_t g = Q.q0[i];
     const Pix P = decode(frames, nframes, Q, g);
     const Frame& f = frames[P.fi];
-    const float* __restrict__ J = qsrc(f, k);
-    int xs[3];
-    size_t ro[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      xs[d] = clampi(P.x - 1 + d, 0, f.w - 1);
-      ro[d] = size_t(clampi(P.y - 1 + d, 0, f.h - 1)) * f.w;
-    }
     float v[9];
-#pragma unroll
-    for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-      for (int dx = 0; dx < 3; ++dx) v[dy * 3 + dx] = __ldg(J + ro[dy] + xs[dx]);
+    load_window<1>(qsrc(f, k), P.x, P.y, f.w, f.h, v);
     f.mapM3[size_t(g - uint32_t(f.pix0))] = sel_med9(v);
   }
 }
@@ -753,11 +763,13 @@ __device__ __forceinline__ void warp_append_if(bool pred, uint32_t g, uint32_t* 
 // lie below the smallest (above the largest) column median, which bound
 // med7(m3) from below (above). Tests the bounds decide go to the candidates
 // (pass) or are dropped; the rest to the open tests.
-__global__ void __launch_bounds__(256) cand_test_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
+__global__ void __launch_bounds__(256, 3) cand_test_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
                                                         Params p) {
+  __shared__ int ws[kThreads / 32 + 1];
+  __shared__ unsigned int sbase[2];
   const unsigned int n = Q.n[kNT];
   const unsigned int stride = gridDim.x * blockDim.x;
-  for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // whole warps iterate together
+  for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // whole blocks iterate together
     const unsigned int i = i0 + threadIdx.x;
     bool pass = false, open = false;
     uint32_t g = 0;
@@ -765,30 +777,29 @@ __global__ void __launch_bounds__(256) cand_test_kernel(const Frame* __restrict_
       g = Q.q2[i];
       const Pix P = decode(frames, nframes, Q, g);
       const Frame& f = frames[P.fi];
-      size_t ro[7];
-#pragma unroll
-      for (int d = 0; d < 7; ++d) ro[d] = size_t(clampi(P.y - 3 + d, 0, f.h - 1)) * f.w;
-      float lo = INFINITY, hi = -INFINITY, mc = 0.f;
+      const size_t o = size_t(g - uint32_t(f.pix0));
+      const float nn = f.mapN[o], sv = f.mapS[o], spv = f.mapSp[o];
+      float u[49];
+      load_window<3>(f.mapM3, P.x, P.y, f.w, f.h, u);
+      float lo = INFINITY, hi = -INFINITY;
+      const float mc = u[24];
 #pragma unroll
       for (int dx = 0; dx < 7; ++dx) {
-        const int xx = clampi(P.x - 3 + dx, 0, f.w - 1);
         float col[7];
 #pragma unroll
-        for (int dy = 0; dy < 7; ++dy) col[dy] = f.mapM3[ro[dy] + xx];
-        if (dx == 3) mc = col[3];
+        for (int dy = 0; dy < 7; ++dy) col[dy] = u[dy * 7 + dx];
         const float cm = sel_med7(col);
         lo = fminf(lo, cm);
         hi = fmaxf(hi, cm);
       }
-      const size_t o = size_t(g - uint32_t(f.pix0));
-      const float nn = f.mapN[o], sv = f.mapS[o], spv = f.mapSp[o];
       const float rlow = objlim_stat(p, __fsub_rn(mc, lo), nn, sv, spv);   // F at its largest
       const float rhigh = objlim_stat(p, __fsub_rn(mc, hi), nn, sv, spv);  // F at its smallest
       pass = rlow > p.objlim;
       open = !pass && rhigh > p.objlim;
     }
-    warp_append_if(pass, g, Q.q0, Q.n + kNPass);
-    warp_append_if(open, g, Q.q1, Q.n + kNAmb);
+    const bool put[2] = {pass, open};
+    uint32_t* const lists[2] = {Q.q0, Q.q1};
+    block_append<2>(put, g, lists, Q.n + kNPass, ws, sbase);
   }
 }
 
@@ -806,18 +817,8 @@ __global__ void __launch_bounds__(256) cand_full_kernel(const Frame* __restrict_
       g = Q.q1[i];
       const Pix P = decode(frames, nframes, Q, g);
       const Frame& f = frames[P.fi];
-      int xs[7];
-      size_t ro[7];
-#pragma unroll
-      for (int d = 0; d < 7; ++d) {
-        xs[d] = clampi(P.x - 3 + d, 0, f.w - 1);
-        ro[d] = size_t(clampi(P.y - 3 + d, 0, f.h - 1)) * f.w;
-      }
       float u[49];
-#pragma unroll
-      for (int dy = 0; dy < 7; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 7; ++dx) u[dy * 7 + dx] = f.mapM3[ro[dy] + xs[dx]];
+      load_window<3>(f.mapM3, P.x, P.y, f.w, f.h, u);
       const size_t o = size_t(g - uint32_t(f.pix0));
       const float fval = __fsub_rn(u[24], sel_med49(u));
       pass = objlim_stat(p, fval, f.mapN[o], f.mapS[o], f.mapSp[o]) > p.objlim;
@@ -888,27 +889,45 @@ __global__ void __launch_bounds__(256) grow_kernel(const Frame* __restrict__ fra
       // 3x3 dilation of A (inside the inner 3x3, so no shift leaves the 5x5)
       const uint32_t dA = A | (A << 1) | (A >> 1) | (A << 5) | (A >> 5) | (A << 4) | (A >> 4) | (A << 6) | (A >> 6);
       const uint32_t g2 = dA & B;
-      // OR each row's flags into its (at most two) flag words
+      // OR each row's flags into its (at most two) flag words: the row's 5 bits
+      // shifted to the word of its lowest flag (sh in [-4, 31])
+      uint32_t* wp[5];
+      uint64_t mm[5];
+      int sh[5];
 #pragma unroll
       for (int r = 0; r < 5; ++r) {
         const uint32_t m = (g2 >> (5 * r)) & 31u;
-        if (!m) continue;
-        const int qy = P.y + r - 2;
-        const int w0 = (xs + __ffs(m) - 1) >> 5;  // word of the lowest flag
-        const int sh = xs - 32 * w0;              // in [-4, 31]
-        const uint64_t mm = sh >= 0 ? (uint64_t(m) << sh) : (uint64_t(m) >> -sh);
-        uint64_t fresh = 0;
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const uint32_t part = uint32_t(mm >> (32 * j));
-          if (!part) continue;
-          uint32_t* wp = f.bits_a + size_t(qy) * f.wpr + w0 + j;
-          if ((*wp & part) == part) continue;  // already flagged
-          fresh |= uint64_t(part & ~atomicOr(wp, part)) << (32 * j);
-        }
-        fm |= (uint32_t(sh >= 0 ? (fresh >> sh) : (fresh << -sh)) & 31u) << (5 * r);
+        const int w0 = m ? (xs + __ffs(m) - 1) >> 5 : 0;
+        sh[r] = xs - 32 * w0;
+        mm[r] = sh[r] >= 0 ? (uint64_t(m) << sh[r]) : (uint64_t(m) >> -sh[r]);
+        wp[r] = f.bits_a + size_t(clampi(P.y + r - 2, 0, h - 1)) * f.wpr + w0;
       }
-      if (fm) atomicAdd(f.counters + 2 * (k - 1), (unsigned long long)__popc(fm));
+      if (!kFresh) {
+        // iteration 1: no flag exists before, so the new flags are counted from
+        // M_1 afterwards (flagq) and the ORs need no reply
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const uint32_t part = uint32_t(mm[r] >> (32 * j));
+            if (part) atomicOr(wp[r] + j, part);
+          }
+      } else {
+        uint32_t old[5][2];
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const uint32_t part = uint32_t(mm[r] >> (32 * j));
+            old[r][j] = part ? atomicOr(wp[r] + j, part) : 0u;
+          }
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+          const uint64_t fresh = mm[r] & ~(uint64_t(old[r][0]) | (uint64_t(old[r][1]) << 32));
+          fm |= (uint32_t(sh[r] >= 0 ? (fresh >> sh[r]) : (fresh << -sh[r])) & 31u) << (5 * r);
+        }
+        if (fm) atomicAdd(f.counters + 2 * (k - 1), (unsigned long long)__popc(fm));
+      }
     }
     if (kFresh) {  // list the new flags: one atomic per warp
       const int c = __popc(fm);
@@ -938,10 +957,12 @@ __global__ void __launch_bounds__(256) grow_kernel(const Frame* __restrict__ fra
 // ---------------------------------------------------------------------------------------------
 // Replacement (stage e).
 
-// flagq_kernel (iteration 1): every flagged pixel -> the replacement queue.
+// flagq_kernel (iteration 1): every flagged pixel -> the replacement queue; all
+// of them are new flags of iteration 1, counted per frame (one atomic per block).
 __global__ void __launch_bounds__(256) flagq_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
                                                     Queues Q) {
   __shared__ int ws[kThreads / 32 + 1];
+  __shared__ unsigned int bcount;
   const int t = threadIdx.x;
   for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
     const int fi = frame_of_block(frames, nframes, b);
@@ -950,7 +971,12 @@ __global__ void __launch_bounds__(256) flagq_kernel(const Frame* __restrict__ fr
     const int bys = int(lb / f.bx), bxs = int(lb - (long long)bys * f.bx);
     const int y = bys * kBH + t / kBW, wc = bxs * kBW + t % kBW;
     const uint32_t v = (y < f.h && wc < f.wpr) ? (f.bits_a[size_t(y) * f.wpr + wc] & frame_word(wc, f.w)) : 0u;
-    emit_word(v, f, wc, y, Q.q1, Q.n + kNRep, ws);
+    if (t == 0) bcount = 0u;
+    __syncthreads();
+    const unsigned int wsum = __reduce_add_sync(0xffffffffu, unsigned(__popc(v)));
+    if ((t & 31) == 0 && wsum) atomicAdd(&bcount, wsum);
+    emit_word(v, f, wc, y, Q.q1, Q.n + kNRep, ws);  // ends with a barrier
+    if (t == 0 && bcount) atomicAdd(f.counters + 0, (unsigned long long)bcount);
   }
 }
 
