@@ -457,7 +457,7 @@ def main():
                            "params": "sigclip 4.5, sigfrac 0.5, objlim 1.0", "l2": "inputs 1.7 GB > L2, no flush"
                            if args.workload == "batch64" else "see workload",
                            "parallelism": f"replicas x{world}", "tile_shape": args.tile_shape},
-                "gpu_launches": args.steps * 2 * niter, "clocks": clk, "roofline": roofline}
+                "gpu_launches": args.steps * cl.last_launches(), "clocks": clk, "roofline": roofline}
         line.update(extras)
         if not args.no_extras:
             line["cpu_baseline"] = cpu_baseline(recipes)

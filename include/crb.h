@@ -162,6 +162,13 @@ int crb_last_counts(crb_ctx* ctx, long long* out, int max_iter);
  * number of iterations, or -1. */
 int crb_last_work(crb_ctx* ctx, long long* out, int max_iter);
 
+/* Kernel launches the last crb_clean / crb_clean_batch / crb_iterate enqueued
+ * (memsets and copies not counted; a graph replay counts its kernels). The
+ * queue pipeline launches 12 kernels in iteration 1, 16 in each later one
+ * (including the form of need/m3need that the device-side size test skips) and
+ * the mask kernel. -1 for a NULL context. */
+int crb_last_launches(const crb_ctx* ctx);
+
 /* One iteration from an explicit state, for stage-by-stage checks:
  * J (device, w*h floats) = I_{k-1}, Mprev (device, w*h bytes, may be NULL for
  * no flags) -> out_J = I_k, out_M = M_k (device). If maps is not NULL it

@@ -41,6 +41,7 @@ SIGNATURES = {
     "crb_sync_status": (_ci, [_vp, _vp]),
     "crb_last_counts": (_ci, [_vp, ctypes.POINTER(ctypes.c_longlong), _ci]),
     "crb_last_work": (_ci, [_vp, ctypes.POINTER(ctypes.c_longlong), _ci]),
+    "crb_last_launches": (_ci, [_vp]),
     "crb_iterate": (_ci, [_vp, _vp, _vp, _ci, _ci, _vp, _vp, _vp, _vp]),
     "crb_profile_read": (_ci, [_vp, ctypes.POINTER(ctypes.c_double), _PI, ctypes.POINTER(ctypes.c_double), _PI,
                                _ci]),

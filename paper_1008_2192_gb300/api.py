@@ -130,6 +130,10 @@ class Cleaner:
             raise RuntimeError("crb_last_work failed")
         return [tuple(int(buf[6 * i + j]) for j in range(6)) for i in range(k)]
 
+    def last_launches(self):
+        """Kernel launches the last call enqueued."""
+        return int(_lib.load().crb_last_launches(self._h))
+
     def profile_read(self, reset=True):
         """(detect ms, detect launches, replace ms, replace launches) since the last reset."""
         dm, rm = ctypes.c_double(), ctypes.c_double()

@@ -127,6 +127,8 @@ struct crb_ctx {
   unsigned long long* d_counters = nullptr;
   int counters_cap = 0;  // in unsigned long longs
   int last_niter = 0;
+  int last_launches = 0;  // kernels the work of the last call launches
+  int mprev_frames = 0;   // crb_iterate: frames given an explicit M_{k-1}
   int last_nframes = 0;
   cudaEvent_t upload_ev = nullptr, done_ev = nullptr;
   bool any_call = false;
@@ -584,6 +586,13 @@ int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
   CRB_CUDA(cudaEventRecord(c->upload_ev, stream));
   c->last_niter = P.niter;
   c->last_nframes = P.n;
+  // the launches enqueue_work makes for this plan (memsets and copies not counted)
+  if (P.niter == 0)
+    c->last_launches = 0;
+  else if (P.queue)  // iteration 1: 12 kernels, later ones 16, plus the mask
+    c->last_launches = 12 + 16 * (P.niter - 1) + 1;
+  else
+    c->last_launches = (P.fuse ? P.niter + 1 : 2 * P.niter) + c->mprev_frames;
   return CRB_OK;
 }
 
@@ -679,6 +688,7 @@ int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, c
                      std::all_of(specs.begin(), specs.end(), [](const FrameSpec& s) { return s.mprev == nullptr; });
   int rc = queue ? prepare_queue(c, specs, niter, P) : prepare(c, specs, niter, maps, shape, P);
   if (rc) return rc;
+  c->mprev_frames = int(std::count_if(specs.begin(), specs.end(), [](const FrameSpec& s) { return s.mprev; }));
   rc = upload(c, P, stream);
   if (rc) return rc;
   // graphs replay only work whose pointers all come from the descriptors
@@ -839,6 +849,8 @@ int read_counters(crb_ctx* c, long long* out, int max_iter, int base, int width)
 }  // namespace
 
 int crb_last_counts(crb_ctx* c, long long* out, int max_iter) { return read_counters(c, out, max_iter, 0, 2); }
+
+int crb_last_launches(const crb_ctx* c) { return c ? c->last_launches : -1; }
 
 int crb_last_work(crb_ctx* c, long long* out, int max_iter) {
   return read_counters(c, out, max_iter, 2, crb::kWork);

@@ -980,32 +980,93 @@ __global__ void __launch_bounds__(256) flagq_kernel(const Frame* __restrict__ fr
   }
 }
 
-// Queues pixel (x, y) of frame f for replacement once (bit plane rq).
-__device__ __forceinline__ void queue_once(const Frame& f, int x, int y, Queues& Q) {
-  const size_t wo = size_t(y) * f.wpr + (x >> 5);
-  const uint32_t bit = 1u << (x & 31);
-  if (f.rq[wo] & bit) return;
-  const uint32_t old = atomicOr(&f.rq[wo], bit);
-  if (!(old & bit)) group_append(uint32_t(f.pix0 + (long long)y * f.w + x), Q.q1, Q.n + kNRep);
+// Bits of columns xs .. xs+4 of row qy of a bit plane (bit dx = column
+// xs + dx); columns outside [0, w) read as 0.
+__device__ __forceinline__ uint32_t plane_bits5(const uint32_t* __restrict__ plane, int wpr, int w, int xs, int qy) {
+  const int wl = max(xs, 0) >> 5, wr = min(xs + 4, w - 1) >> 5;
+  const uint64_t pair = uint64_t(plane[size_t(qy) * wpr + wl]) | (uint64_t(plane[size_t(qy) * wpr + wr]) << 32);
+  const int sh = xs - 32 * wl;  // in [-2, 31]
+  uint32_t b = uint32_t(sh >= 0 ? (pair >> sh) : (pair << -sh)) & 31u;
+#pragma unroll
+  for (int dx = 0; dx < 5; ++dx)
+    if (xs + dx < 0 || xs + dx >= w) b &= ~(1u << dx);
+  return b;
+}
+
+// ORs a 5x5 mask (bit r*5 + dx = column xs + dx of row y0 + r; only in-frame
+// positions set) into a bit plane, one atomic per row and word, and returns the
+// bits that were clear before.
+__device__ __forceinline__ uint32_t or_window(uint32_t* plane, int wpr, int h, int xs, int y0, uint32_t m25) {
+  uint32_t* wp[5];
+  uint64_t mm[5];
+  int sh[5];
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const uint32_t m = (m25 >> (5 * r)) & 31u;
+    const int w0 = m ? (xs + __ffs(m) - 1) >> 5 : 0;  // word of the row's first bit
+    sh[r] = xs - 32 * w0;                            // in [-4, 31]
+    mm[r] = sh[r] >= 0 ? (uint64_t(m) << sh[r]) : (uint64_t(m) >> -sh[r]);
+    wp[r] = plane + size_t(clampi(y0 + r, 0, h - 1)) * wpr + w0;
+  }
+  uint32_t old[5][2];
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const uint32_t part = uint32_t(mm[r] >> (32 * j));
+      old[r][j] = part ? atomicOr(wp[r] + j, part) : 0u;
+    }
+  uint32_t res = 0;
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const uint64_t fresh = mm[r] & ~(uint64_t(old[r][0]) | (uint64_t(old[r][1]) << 32));
+    res |= (uint32_t(sh[r] >= 0 ? (fresh >> sh[r]) : (fresh << -sh[r])) & 31u) << (5 * r);
+  }
+  return res;
 }
 
 // rq_kernel (iteration >= 2): the flagged pixels within 2 px of a new flag
 // (their windows gained a flag) and every pixel with a fully flagged window (J
-// may have changed in it) -> the replacement queue.
+// may have changed in it) -> the replacement queue, each once (bit plane rq;
+// one append atomic per block).
 __global__ void __launch_bounds__(256) rq_kernel(const Frame* __restrict__ frames, int nframes, Queues Q) {
+  __shared__ int ws[kThreads / 32 + 1];
+  __shared__ unsigned int sbase;
   const unsigned int nf = Q.n[kNFresh], n = nf + Q.n[kNFb];
-  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const bool is_fresh = i < nf;
-    const uint32_t g = is_fresh ? Q.fresh[i] : Q.fbl[i - nf];
-    const Pix P = decode(frames, nframes, Q, g);
-    const Frame& f = frames[P.fi];
-    if (!is_fresh) {
-      queue_once(f, P.x, P.y, Q);
-      continue;
+  const unsigned int stride = gridDim.x * blockDim.x;
+  for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // whole blocks iterate together
+    const unsigned int i = i0 + threadIdx.x;
+    uint32_t nq = 0;  // newly queued, bit (dy+2)*5 + (dx+2) around the entry
+    uint32_t g = 0;
+    int w = 1;
+    if (i < n) {
+      const bool is_fresh = i < nf;
+      g = is_fresh ? Q.fresh[i] : Q.fbl[i - nf];
+      const Pix P = decode(frames, nframes, Q, g);
+      const Frame& f = frames[P.fi];
+      w = f.w;
+      uint32_t want = 1u << 12;  // the pixel itself (fully flagged window)
+      if (is_fresh) {           // the flagged pixels of the 5x5
+        want = 0;
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+          const int qy = P.y + r - 2;
+          if (qy >= 0 && qy < f.h) want |= plane_bits5(f.bits_a, f.wpr, f.w, P.x - 2, qy) << (5 * r);
+        }
+      }
+      nq = or_window(f.rq, f.wpr, f.h, P.x - 2, P.y - 2, want);
     }
-    for (int y = max(P.y - 2, 0); y <= min(P.y + 2, f.h - 1); ++y)
-      for (int x = max(P.x - 2, 0); x <= min(P.x + 2, f.w - 1); ++x)
-        if ((f.bits_a[size_t(y) * f.wpr + (x >> 5)] >> (x & 31)) & 1u) queue_once(f, x, y, Q);
+    int total = 0;
+    const int off = block_excl_scan(__popc(nq), ws, total);
+    if (threadIdx.x == 0) sbase = total ? atomicAdd(Q.n + kNRep, (unsigned int)total) : 0u;
+    __syncthreads();
+    unsigned int out = sbase + unsigned(off);
+    while (nq) {
+      const int bb = __ffs(nq) - 1;
+      nq &= nq - 1u;
+      Q.q1[out++] = uint32_t(int64_t(g) + (long long)(bb / 5 - 2) * w + (bb % 5 - 2));
+    }
+    __syncthreads();
   }
 }
 

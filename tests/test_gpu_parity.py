@@ -235,3 +235,16 @@ def test_graphs_and_autotune(graphs, shape, pipeline):
         for a, o, m in zip(imgs, outs, masks):
             r32 = oracle.clean(a, params_of({}), 4, precision="f32")
             assert np.array_equal(host(m), r32.mask) and np.array_equal(host(o), r32.clean)
+
+
+@pytest.mark.parametrize("niter", [1, 2, 4])
+def test_launch_counts(niter):
+    """crb_last_launches reports the kernels a call enqueues: 12 + 16 (niter - 1) + 1 on the queue
+    pipeline, niter + 1 on the fused tile pipeline."""
+    img = scene(120, 90, seed=9)
+    cq = Cleaner(niter=niter)
+    gpu_clean(cq, img)
+    assert cq.last_launches() == 12 + 16 * (niter - 1) + 1
+    ct = Cleaner(niter=niter, pipeline="tile")
+    gpu_clean(ct, img)
+    assert ct.last_launches() == niter + 1
