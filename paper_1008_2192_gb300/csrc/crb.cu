@@ -175,7 +175,7 @@ int init_ctx(crb_ctx* c) {
         reinterpret_cast<const void*>(crb::cand_full_kernel),   reinterpret_cast<const void*>(crb::grow_kernel<true>)};
     for (int i = 0; i < kQKernels; ++i) {
       int o = 0;
-      CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[i], 256, 0));
+      CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[i], i == kQBound ? 128 : 256, 0));
       c->occ_q[i] = o > 0 ? o : 1;
     }
   }
@@ -309,13 +309,14 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
       timed(c, 0, stream, [&] {
         const unsigned int dense_from = unsigned(std::min<long long>(P.ncells / 4 + 1, 0xffffffffLL));
         const uint32_t* kcls = (k == 1) ? nullptr : cls;
-        if (k == 1) {
-          crb::bound_kernel<<<grid(kQBound, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, c->p, k);
-        } else {
+        if (k >= 2)
           crb::cell_list_kernel<<<grid(kQCellList, (P.ncells + 255) / 256), 256, 0, stream>>>(c->d_frames, P.n,
                                                                                               P.ncells, cls, P.Q);
-          crb::bound_list_kernel<<<gq * c->occ_q[kQBoundList], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
-        }
+        crb::bound_kernel<<<grid(kQBound, P.nblocks), 128, 0, stream>>>(c->d_frames, P.n, P.nblocks, c->p, k, P.Q,
+                                                                        kcls, dense_from);
+        if (k >= 2)
+          crb::bound_list_kernel<<<gq * c->occ_q[kQBoundList], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p,
+                                                                                dense_from);
         crb::need_kernel<<<grid(kQNeed, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q, kcls,
                                                                        dense_from);
         if (k >= 2)
@@ -589,8 +590,8 @@ int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
   // the launches enqueue_work makes for this plan (memsets and copies not counted)
   if (P.niter == 0)
     c->last_launches = 0;
-  else if (P.queue)  // iteration 1: 12 kernels, later ones 16, plus the mask
-    c->last_launches = 12 + 16 * (P.niter - 1) + 1;
+  else if (P.queue)  // iteration 1: 12 kernels, later ones 17, plus the mask
+    c->last_launches = 12 + 17 * (P.niter - 1) + 1;
   else
     c->last_launches = (P.fuse ? P.niter + 1 : 2 * P.niter) + c->mprev_frames;
   return CRB_OK;

@@ -251,10 +251,139 @@ __device__ __forceinline__ void bound_consts(const Params& p, float& chot, float
   clow = 4.f * tlow * tlow * 0.9999f;
 }
 
-// every word column of every frame (iteration 1; it also starts the image
-// buffer as a copy of I0): blocks of kBW words x kBH rows
-__global__ void __launch_bounds__(256) bound_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
-                                                    Params p, int k) {
+// 16 bits spread to the even bits of a word (bit i -> bit 2i)
+__device__ __forceinline__ uint32_t spread16(uint32_t x) {
+  x &= 0xffffu;
+  x = (x | (x << 8)) & 0x00ff00ffu;
+  x = (x | (x << 4)) & 0x0f0f0f0fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}
+
+// Sliding column-median state of one column: rows r-2 .. r+1 of the current step.
+struct Col4 {
+  float a, b, c, d;
+};
+
+// Advances a column by the two rows (e, g) below it: the medians of the five
+// rows around the first and the second row of the step.
+__device__ __forceinline__ void col_step(Col4& s, float e, float g, float& m0, float& m1) {
+  const float l1 = fminf(s.b, s.c), h1 = fmaxf(s.b, s.c), l2 = fminf(s.d, e), h2 = fmaxf(s.d, e);
+  const float u = fmaxf(l1, l2), v = fminf(h1, h2);
+  const float c1 = fminf(u, v), c2 = fmaxf(u, v);
+  m0 = clamp_med(s.a, c1, c2);
+  m1 = clamp_med(g, c1, c2);
+}
+
+// hot/act bits of the two word columns wc, wc+1 (wc even), rows [y0, y1), of
+// frame f (whole warp). Lane l holds the pixel pair x0+2l, x0+2l+1, so one
+// shuffle brings two neighbours; lanes 0-3 also hold the halo columns x0-2,
+// x0-1, x0+64, x0+65. copy != nullptr also copies the pixels of J there.
+__device__ __forceinline__ void bound_span2(const Frame& f, const float* __restrict__ J, int wc, int y0, int y1,
+                                            float chot, float clow, float* __restrict__ copy) {
+  const int lane = threadIdx.x & 31;
+  const int w = f.w, h = f.h;
+  const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
+  const int x0 = wc * 32, xa = x0 + 2 * lane, xb = xa + 1;
+  const int ca = min(xa, w - 1), cb = min(xb, w - 1);
+  const int hx = lane < 2 ? x0 - 2 + lane : x0 + 62 + lane;  // halo columns (lanes 0-3)
+  const int hc = clampi(hx, 0, w - 1);
+  // one 8-byte load for the pair when the row pitch and the base keep it aligned
+  const bool vec = ((reinterpret_cast<uintptr_t>(J) & 7u) == 0) && ((w & 1) == 0) && (xb < w);
+  const int src_h0 = lane == 0 ? 0 : 2, src_h1 = lane == 0 ? 1 : 3, src_hl = lane == 0 ? 1 : 2;
+  auto row = [&](int yy) { return J + size_t(clampi(yy, 0, h - 1)) * size_t(w); };
+  auto ld = [&](int yy, float& va, float& vb, float& vh) {
+    const float* r = row(yy);
+    if (vec) {
+      const float2 t = __ldg(reinterpret_cast<const float2*>(r + xa));
+      va = t.x;
+      vb = t.y;
+    } else {
+      va = __ldg(r + ca);
+      vb = __ldg(r + cb);
+    }
+    vh = __ldg(r + hc);
+  };
+  Col4 A, B, H;
+  ld(y0 - 2, A.a, B.a, H.a);
+  ld(y0 - 1, A.b, B.b, H.b);
+  ld(y0, A.c, B.c, H.c);
+  ld(y0 + 1, A.d, B.d, H.d);
+  for (int y = y0; y < y1; y += 2) {
+    float ea, eb, eh, ga, gb, gh;
+    ld(y + 2, ea, eb, eh);
+    ld(y + 3, ga, gb, gh);
+    float ma[2], mb[2], mh[2];
+    col_step(A, ea, ga, ma[0], ma[1]);
+    col_step(B, eb, gb, mb[0], mb[1]);
+    col_step(H, eh, gh, mh[0], mh[1]);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int yy = y + s;
+      if (yy >= y1) break;
+      const float cmA = ma[s], cmB = mb[s];
+      // column medians of the neighbouring pairs (lane-1: pA pB, lane+1: nA nB); halo at the ends
+      float pA = __shfl_up_sync(0xffffffffu, cmA, 1), pB = __shfl_up_sync(0xffffffffu, cmB, 1);
+      float nA = __shfl_down_sync(0xffffffffu, cmA, 1), nB = __shfl_down_sync(0xffffffffu, cmB, 1);
+      const float hX = __shfl_sync(0xffffffffu, mh[s], src_h0), hY = __shfl_sync(0xffffffffu, mh[s], src_h1);
+      if (lane == 0) {
+        pA = hX;
+        pB = hY;
+      }
+      if (lane == 31) {
+        nA = hX;
+        nB = hY;
+      }
+      const float mlowA = min3f(min3f(pA, pB, cmA), cmB, nA);
+      const float mlowB = min3f(min3f(pB, cmA, cmB), nA, nB);
+      // L+ of both pixels: rows of the step, row neighbours within the pair or one lane away
+      const float ccA = s ? A.d : A.c, upA = s ? A.c : A.b, dnA = s ? ea : A.d;
+      const float ccB = s ? B.d : B.c, upB = s ? B.c : B.b, dnB = s ? eb : B.d;
+      const float hcc = s ? H.d : H.c;
+      const float hL = __shfl_sync(0xffffffffu, hcc, src_hl);
+      float lB = __shfl_up_sync(0xffffffffu, ccB, 1), rA = __shfl_down_sync(0xffffffffu, ccA, 1);
+      if (lane == 0) lB = hL;
+      if (lane == 31) rA = hL;
+      const float lpA = lplus(ccA, upA, dnA, lB, ccB);
+      const float lpB = lplus(ccB, upB, dnB, ccA, rA);
+      if (copy) {
+        float* o = copy + size_t(yy) * w;
+        if (xa < w) o[xa] = ccA;
+        if (xb < w) o[xb] = ccB;
+      }
+      const float denA = gain * (mlowA > 0.f ? mlowA : 0.f) + rn2;
+      const float denB = gain * (mlowB > 0.f ? mlowB : 0.f) + rn2;
+      const float lhsA = lpA * lpA * g2, lhsB = lpB * lpB * g2;
+      const unsigned actA = __ballot_sync(0xffffffffu, xa < w && lhsA > clow * denA);
+      const unsigned actB = __ballot_sync(0xffffffffu, xb < w && lhsB > clow * denB);
+      const unsigned hotA = __ballot_sync(0xffffffffu, xa < w && lhsA > chot * denA);
+      const unsigned hotB = __ballot_sync(0xffffffffu, xb < w && lhsB > chot * denB);
+      // word wc holds lanes 0-15 (bits 2l, 2l+1), word wc+1 lanes 16-31; lane j < 2 stores word wc+j
+      const int sh = lane ? 16 : 0;
+      const uint32_t act = spread16(actA >> sh) | (spread16(actB >> sh) << 1);
+      const uint32_t hot = spread16(hotA >> sh) | (spread16(hotB >> sh) << 1);
+      if (lane < 2 && wc + lane < f.wpr) {
+        const size_t o = size_t(yy) * f.wpr + wc + lane;
+        f.act[o] = act;
+        f.hot[o] = hot;
+      }
+    }
+    A = Col4{A.c, A.d, ea, ga};
+    B = Col4{B.c, B.d, eb, gb};
+    H = Col4{H.c, H.d, eh, gh};
+  }
+}
+
+// bound_kernel: pairs of word columns of every frame, blocks of kBW words x
+// kBH rows, 4 warps of 2 words. Iteration 1 (cls == nullptr): every row, and
+// the image buffer starts as a copy of I0. Iteration >= 2: the runs of cell
+// rows in which either word's cell has class 4; runs only when at least
+// `dense_from` cells are listed (bound_list_kernel runs otherwise).
+__global__ void __launch_bounds__(128) bound_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
+                                                    Params p, int k, Queues Q, const uint32_t* __restrict__ cls,
+                                                    unsigned int dense_from) {
+  if (cls && Q.n[kNL2] < dense_from) return;  // the list form runs
   const int warp = threadIdx.x >> 5;
   float chot, clow;
   bound_consts(p, chot, clow);
@@ -263,20 +392,40 @@ __global__ void __launch_bounds__(256) bound_kernel(const Frame* __restrict__ fr
     const Frame& f = frames[fi];
     const long long lb = b - f.blk0;
     const int bys = int(lb / f.bx), bxs = int(lb - (long long)bys * f.bx);
-    const int wc = bxs * kBW + warp;
+    const int wc = bxs * kBW + 2 * warp;
     if (wc >= f.wpr) continue;  // whole warp
-    const int y0 = bys * kBH;
-    bound_span(f, qsrc(f, k), wc, y0, min(y0 + kBH, f.h), chot, clow, k == 1 ? f.out_clean : nullptr);
+    const int y0 = bys * kBH, y1 = min(y0 + kBH, f.h);
+    const float* J = qsrc(f, k);
+    if (!cls) {
+      bound_span2(f, J, wc, y0, y1, chot, clow, k == 1 ? f.out_clean : nullptr);
+      continue;
+    }
+    auto dirty = [&](int cy) {
+      const uint32_t* c = cls + f.cell0 + (long long)cy * f.wpr + wc;
+      return c[0] >= 4u || (wc + 1 < f.wpr && c[1] >= 4u);
+    };
+    const int cy1 = (y1 + kCH - 1) / kCH;
+    for (int cy = y0 / kCH; cy < cy1;) {
+      if (!dirty(cy)) {
+        ++cy;
+        continue;
+      }
+      int ce = cy + 1;
+      while (ce < cy1 && dirty(ce)) ++ce;
+      bound_span2(f, J, wc, cy * kCH, min(ce * kCH, f.h), chot, clow, nullptr);
+      cy = ce;
+    }
   }
 }
 
 // the cells of list l2 (iteration >= 2): one warp per cell
 __global__ void __launch_bounds__(256) bound_list_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
-                                                         Params p) {
+                                                         Params p, unsigned int dense_from) {
   const int warp = threadIdx.x >> 5;
   float chot, clow;
   bound_consts(p, chot, clow);
   const unsigned int n = Q.n[kNL2];
+  if (n >= dense_from) return;  // the block form runs
   for (unsigned int i = blockIdx.x * 8u + warp; i < n; i += gridDim.x * 8u) {
     const uint32_t c = Q.l2[i];
     const Frame& f = frames[frame_of_cell(frames, nframes, c)];
