@@ -164,9 +164,9 @@ int crb_last_work(crb_ctx* ctx, long long* out, int max_iter);
 
 /* Kernel launches the last crb_clean / crb_clean_batch / crb_iterate enqueued
  * (memsets and copies not counted; a graph replay counts its kernels). The
- * queue pipeline launches 12 kernels in iteration 1, 17 in each later one
- * (including the form of bound/need/m3need that the device-side size test
- * skips) and the mask kernel. -1 for a NULL context. */
+ * queue pipeline launches 12 kernels in iteration 1, 15 in each later one
+ * (including the form of the bound pass that the device-side size test skips)
+ * and the mask kernel. -1 for a NULL context. */
 int crb_last_launches(const crb_ctx* ctx);
 
 /* One iteration from an explicit state, for stage-by-stage checks:

@@ -68,8 +68,8 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 // queue pipeline kernels, for the occupancy table
 enum QK {
-  kQBound, kQNeed, kQS, kQSp, kQM3need, kQM3, kQCand, kQRepCompute, kQBoundList, kQNeedList, kQM3needList, kQRq,
-  kQRepWrite, kQCellList, kQCandFull, kQGrow, kQKernels
+  kQBound, kQNeed, kQS, kQSp, kQM3need, kQM3, kQCand, kQRepCompute, kQBoundList, kQRq, kQRepWrite, kQCellList,
+  kQCandFull, kQGrow, kQFlagq, kQKernels
 };
 
 struct GraphKey {
@@ -168,14 +168,15 @@ int init_ctx(crb_ctx* c) {
         reinterpret_cast<const void*>(crb::bound_kernel),       reinterpret_cast<const void*>(crb::need_kernel),
         reinterpret_cast<const void*>(crb::s_kernel),           reinterpret_cast<const void*>(crb::sp_kernel),
         reinterpret_cast<const void*>(crb::m3need_kernel),      reinterpret_cast<const void*>(crb::m3_kernel),
-        reinterpret_cast<const void*>(crb::cand_test_kernel),        reinterpret_cast<const void*>(crb::rep_compute_kernel),
-        reinterpret_cast<const void*>(crb::bound_list_kernel),  reinterpret_cast<const void*>(crb::need_list_kernel),
-        reinterpret_cast<const void*>(crb::m3need_list_kernel), reinterpret_cast<const void*>(crb::rq_kernel),
+        reinterpret_cast<const void*>(crb::cand_test_kernel),   reinterpret_cast<const void*>(crb::rep_compute_kernel),
+        reinterpret_cast<const void*>(crb::bound_list_kernel),  reinterpret_cast<const void*>(crb::rq_kernel),
         reinterpret_cast<const void*>(crb::rep_write_kernel),   reinterpret_cast<const void*>(crb::cell_list_kernel),
-        reinterpret_cast<const void*>(crb::cand_full_kernel),   reinterpret_cast<const void*>(crb::grow_kernel<true>)};
+        reinterpret_cast<const void*>(crb::cand_full_kernel),   reinterpret_cast<const void*>(crb::grow_kernel<true>),
+        reinterpret_cast<const void*>(crb::flagq_kernel)};
     for (int i = 0; i < kQKernels; ++i) {
       int o = 0;
-      CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[i], i == kQBound ? 128 : 256, 0));
+      const int threads = i == kQBound ? 128 : (i == kQNeed || i == kQM3need) ? crb::kColWarps * 32 : 256;
+      CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[i], threads, 0));
       c->occ_q[i] = o > 0 ? o : 1;
     }
   }
@@ -280,6 +281,7 @@ struct Plan {
   int dgrid = 0, fgrid = 0, rgrid = 0;
   long long nblocks = 0, npix = 0;  // queue pipeline: word blocks, pixels
   long long ncells = 0;             // queue pipeline: cells (one word x kCH rows)
+  long long nunits = 0;             // queue pipeline: strips of 32 words x kSH rows
   uint32_t* cells[2] = {nullptr, nullptr};  // cell classes for even / odd iterations
   crb::Queues Q{};
 };
@@ -309,26 +311,18 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
       timed(c, 0, stream, [&] {
         const unsigned int dense_from = unsigned(std::min<long long>(P.ncells / 4 + 1, 0xffffffffLL));
         const uint32_t* kcls = (k == 1) ? nullptr : cls;
+        const int gcol = grid(kQNeed, (P.nunits + crb::kColWarps - 1) / crb::kColWarps);
         if (k >= 2)
-          crb::cell_list_kernel<<<grid(kQCellList, (P.ncells + 255) / 256), 256, 0, stream>>>(c->d_frames, P.n,
-                                                                                              P.ncells, cls, P.Q);
+          crb::cell_list_kernel<<<grid(kQCellList, (P.ncells + 255) / 256), 256, 0, stream>>>(P.ncells, cls, P.Q);
         crb::bound_kernel<<<grid(kQBound, P.nblocks), 128, 0, stream>>>(c->d_frames, P.n, P.nblocks, c->p, k, P.Q,
                                                                         kcls, dense_from);
         if (k >= 2)
           crb::bound_list_kernel<<<gq * c->occ_q[kQBoundList], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p,
                                                                                 dense_from);
-        crb::need_kernel<<<grid(kQNeed, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q, kcls,
-                                                                       dense_from);
-        if (k >= 2)
-          crb::need_list_kernel<<<gq * c->occ_q[kQNeedList], 256, 0, stream>>>(c->d_frames, P.n, P.Q, cls,
-                                                                               dense_from);
+        crb::need_kernel<<<gcol, crb::kColWarps * 32, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, kcls);
         crb::s_kernel<<<gq * c->occ_q[kQS], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k);
         crb::sp_kernel<<<gq * c->occ_q[kQSp], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
-        crb::m3need_kernel<<<grid(kQM3need, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q, kcls,
-                                                                           dense_from);
-        if (k >= 2)
-          crb::m3need_list_kernel<<<gq * c->occ_q[kQM3needList], 256, 0, stream>>>(c->d_frames, P.n, P.Q, cls,
-                                                                                   dense_from);
+        crb::m3need_kernel<<<gcol, crb::kColWarps * 32, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, kcls);
         crb::m3_kernel<<<gq * c->occ_q[kQM3], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k);
         crb::cand_test_kernel<<<gq * c->occ_q[kQCand], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
         crb::cand_full_kernel<<<gq * c->occ_q[kQCandFull], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
@@ -341,14 +335,14 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
       if (k >= 3 && cls_next) CRB_CUDA(cudaMemsetAsync(cls_next, 0, cells_bytes, stream));
       timed(c, 1, stream, [&] {
         if (k == 1)
-          crb::flagq_kernel<<<grid(kQNeed, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q);
+          crb::flagq_kernel<<<grid(kQFlagq, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q);
         else
           crb::rq_kernel<<<gq * c->occ_q[kQRq], 256, 0, stream>>>(c->d_frames, P.n, P.Q);
         crb::rep_compute_kernel<<<gq * c->occ_q[kQRepCompute], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k,
                                                                                 cls_next);
         if (k >= 2)
           crb::rep_write_kernel<<<gq * c->occ_q[kQRepWrite], 256, 0, stream>>>(c->d_frames, P.n, P.Q, cls_next, 1);
-        if (k == P.niter) crb::mask_kernel<<<grid(kQNeed, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks);
+        if (k == P.niter) crb::mask_kernel<<<grid(kQFlagq, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks);
       });
       crb::queue_work_kernel<<<1, 32, 0, stream>>>(c->d_frames, P.Q, k, P.npix);
     }
@@ -388,13 +382,15 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
 
 // Queue pipeline: workspace = [queue counters | per frame: bit planes M, rq, fb |
 // cell classes x 2] (zeroed at the start of a call) then [per frame: bit planes
-// hot, act, nsp, test, sval, m3val; maps S, N, S', M3] then [queues q0, q1, q2,
-// fresh, fbl of one entry per pixel of the call | cell lists l2, l6, l9].
+// hot, act, nsp, test, sval, m3val; maps S, N, S', M3] then [queues q0, q1, q2
+// (a pixel index per pixel or a word entry per word), fresh, fbl (a pixel index
+// per pixel) | the list of class-4 cells].
 int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Plan& P) {
   const int n = int(specs.size());
-  long long npix = 0, nblocks = 0, ncells = 0;
+  long long npix = 0, nblocks = 0, ncells = 0, nwords = 0;
   for (const auto& s : specs) {
     npix += (long long)s.w * s.h;
+    nwords += (long long)((s.w + 31) / 32) * s.h;
     ncells += (long long)((s.w + 31) / 32) * ((s.h + crb::kCH - 1) / crb::kCH);
   }
   size_t total = 256;  // queue counters
@@ -415,9 +411,11 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
     off_maps[size_t(i)] = total;
     total += 4 * align256(size_t(s.w) * size_t(s.h) * 4);
   }
-  const size_t qbytes = align256(size_t(npix) * 4), lbytes = align256(size_t(ncells) * 4);
+  // q0..q2 hold a pixel index per pixel or a word entry (8 bytes) per word
+  const size_t qbytes = align256(std::max(size_t(npix) * 4, size_t(nwords) * 8));
+  const size_t fbytes = align256(size_t(npix) * 4), lbytes = align256(size_t(ncells) * 4);
   const size_t off_q = total;
-  total += 5 * qbytes + 3 * lbytes;
+  total += 3 * qbytes + 2 * fbytes + lbytes;
   const int nit = niter > 0 ? niter : 1;
   const int ncounters = (2 + crb::kWork) * nit * n;
   int rc = ensure_frames(c, n);
@@ -426,7 +424,7 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
   if (rc) return rc;
   CRB_CUDA(cudaEventSynchronize(c->upload_ev));
   char* ws = static_cast<char*>(c->ws);
-  long long pix0 = 0, rtiles = 0, cell0 = 0;
+  long long pix0 = 0, rtiles = 0, cell0 = 0, nunits = 0, word0 = 0;
   for (int i = 0; i < n; ++i) {
     const auto& s = specs[size_t(i)];
     crb::Frame& f = c->h_frames[i];
@@ -472,6 +470,11 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
     f.ncy = (s.h + crb::kCH - 1) / crb::kCH;
     f.cell0 = cell0;
     cell0 += (long long)f.wpr * f.ncy;
+    f.word0 = word0;
+    word0 += (long long)f.wpr * s.h;
+    f.ugx = (f.wpr + 31) / 32;
+    f.u0 = nunits;
+    nunits += (long long)f.ugx * ((s.h + crb::kSH - 1) / crb::kSH);
   }
   // frame of the first pixel of each 2^kTabShift pixels (frames are consecutive ranges)
   const size_t tab_n = size_t(npix >> crb::kTabShift) + 1;
@@ -496,6 +499,7 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
   P.nblocks = nblocks;
   P.npix = npix;
   P.ncells = ncells;
+  P.nunits = nunits;
   P.cells[0] = reinterpret_cast<uint32_t*>(ws + off_cells);
   P.cells[1] = reinterpret_cast<uint32_t*>(ws + off_cells + align256(size_t(ncells) * 4));
   P.Q.n = reinterpret_cast<unsigned int*>(ws);
@@ -504,10 +508,8 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
   P.Q.q1 = reinterpret_cast<uint32_t*>(ws + off_q + qbytes);
   P.Q.q2 = reinterpret_cast<uint32_t*>(ws + off_q + 2 * qbytes);
   P.Q.fresh = reinterpret_cast<uint32_t*>(ws + off_q + 3 * qbytes);
-  P.Q.fbl = reinterpret_cast<uint32_t*>(ws + off_q + 4 * qbytes);
-  P.Q.l2 = reinterpret_cast<uint32_t*>(ws + off_q + 5 * qbytes);
-  P.Q.l6 = reinterpret_cast<uint32_t*>(ws + off_q + 5 * qbytes + lbytes);
-  P.Q.l9 = reinterpret_cast<uint32_t*>(ws + off_q + 5 * qbytes + 2 * lbytes);
+  P.Q.fbl = reinterpret_cast<uint32_t*>(ws + off_q + 3 * qbytes + fbytes);
+  P.Q.l2 = reinterpret_cast<uint32_t*>(ws + off_q + 3 * qbytes + 2 * fbytes);
   return CRB_OK;
 }
 
@@ -590,8 +592,8 @@ int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
   // the launches enqueue_work makes for this plan (memsets and copies not counted)
   if (P.niter == 0)
     c->last_launches = 0;
-  else if (P.queue)  // iteration 1: 12 kernels, later ones 17, plus the mask
-    c->last_launches = 12 + 17 * (P.niter - 1) + 1;
+  else if (P.queue)  // iteration 1: 12 kernels, later ones 15, plus the mask
+    c->last_launches = 12 + 15 * (P.niter - 1) + 1;
   else
     c->last_launches = (P.fuse ? P.niter + 1 : 2 * P.niter) + c->mprev_frames;
   return CRB_OK;

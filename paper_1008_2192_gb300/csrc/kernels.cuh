@@ -60,6 +60,9 @@ struct Frame {
   long long cell0; // first cell (one word x kCH rows) of this frame
   int bx;          // word blocks per row of blocks
   int ncy;         // rows of cells
+  long long u0;    // first strip (32 words x 32 rows) of this frame
+  long long word0; // first word (32 px of a row) of this frame
+  int ugx;         // strips per row of strips
 };
 
 struct Params {
@@ -95,14 +98,19 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v,
 // Stage formulas, float32, no contraction.
 
 // (a) L+ from the pixel c and its four edge neighbours.
+// The clip max(0, t) is taken as t + |t| = 2 max(0, t), exact for finite t
+// below FLT_MAX/2 (an add with an operand modifier instead of a min/max
+// instruction); the doubled partial sums round exactly as the plain ones, so
+// 1/8 of their sum equals 1/4 of the sum of the clips in every bit.
 __device__ __forceinline__ float lplus(float c, float up, float down, float left, float right) {
   const float dn = __fsub_rn(c, up), ds = __fsub_rn(c, down);
   const float dw = __fsub_rn(c, left), de = __fsub_rn(c, right);
-  float acc = fmaxf(0.f, __fadd_rn(dn, dw));
-  acc = __fadd_rn(acc, fmaxf(0.f, __fadd_rn(dn, de)));
-  acc = __fadd_rn(acc, fmaxf(0.f, __fadd_rn(ds, dw)));
-  acc = __fadd_rn(acc, fmaxf(0.f, __fadd_rn(ds, de)));
-  return __fmul_rn(0.25f, acc);
+  const float t0 = __fadd_rn(dn, dw), t1 = __fadd_rn(dn, de), t2 = __fadd_rn(ds, dw), t3 = __fadd_rn(ds, de);
+  float acc = __fadd_rn(t0, fabsf(t0));
+  acc = __fadd_rn(acc, __fadd_rn(t1, fabsf(t1)));
+  acc = __fadd_rn(acc, __fadd_rn(t2, fabsf(t2)));
+  acc = __fadd_rn(acc, __fadd_rn(t3, fabsf(t3)));
+  return __fmul_rn(0.125f, acc);
 }
 
 // (b) floored 5x5 median -> noise N.

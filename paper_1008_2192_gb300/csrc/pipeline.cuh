@@ -8,8 +8,9 @@
 //                  -> queues QS (S to compute) and QSP (S' to compute);
 //   s              at QS: m5, N, L+, S -> maps N, S;
 //   sp             at QSP: S' = S - med5(S) -> map S'; S' > sigclip -> bit
-//                  plane test and queue QT;
-//   m3need         needM3 = dilate3(QT) -> queue QM3;
+//                  plane test;
+//   m3need         QT = the test bits to (re)test, needM3 = dilate3(QT) ->
+//                  queues QT and QM3;
 //   m3             at QM3: med3 -> map M3;
 //   cand_test      at QT: the objlim test from bounds of med7(m3) (smallest
 //                  and largest column median), decided exactly where they
@@ -59,32 +60,39 @@ namespace crb {
 namespace cg = cooperative_groups;
 
 constexpr int kCH = 8;         // rows per cell
+constexpr int kSH = 32;        // rows per strip of the column-sliding kernels (32 words wide)
 constexpr int kTabShift = 16;  // pixels per entry of the frame table: 2^kTabShift
 
 // queue counters (Queues::n)
 enum : int {
-  kNS = 0,      // QS
-  kNSP = 1,     // QSP
-  kNM3 = 2,     // QM3
-  kNT = 3,      // QT
+  kNS = 0,      // QS (word entries)
+  kNSP = 1,     // QSP (word entries)
+  kNM3 = 2,     // QM3 (word entries)
+  kNT = 3,      // QT (word entries)
   kNRep = 4,    // replacement queue
   kNFresh = 5,  // new flags of this iteration
   kNFb = 6,     // pixels with a fully flagged window (kept over the iterations)
   kNL2 = 7,     // cells within 2 px of a change
-  kNL6 = 8,     // cells within 6 px of a change
-  kNL9 = 9,     // cells next to a kNL6 cell (or one)
-  kNPass = 10,  // candidates (passed the objlim test)
-  kNAmb = 11,   // tests the column-median bounds leave open
-  kNCount = 12
+  kNPass = 8,   // candidates (passed the objlim test)
+  kNAmb = 9,    // tests the column-median bounds leave open
+  kNSpx = 10,   // positions in QS, QSP, QM3, QT (work counters)
+  kNSPpx = 11,
+  kNM3px = 12,
+  kNTpx = 13,
+  kNCount = 14
 };
 
+// QS, QSP, QM3 and QT hold word entries: (global word index, mask of the
+// word's pixels), one per word with a set bit, so that the bit-plane kernels
+// write one entry per word; the kernels that use them expand the masks into
+// one pixel per thread (expand_words).
 struct Queues {
   uint32_t* q0;     // QS, then QM3, then the candidates, then the replacement values (as float)
   uint32_t* q1;     // QSP, then the open tests, then the replacement queue
   uint32_t* q2;     // QT
   uint32_t* fresh;  // new flags
   uint32_t* fbl;    // fully flagged windows
-  uint32_t *l2, *l6, *l9;  // cell lists
+  uint32_t* l2;     // cells of class 4
   unsigned int* n;  // kNCount counters
   const uint32_t* ftab;  // frame of global pixel t << kTabShift
 };
@@ -108,6 +116,16 @@ __device__ __forceinline__ int frame_of_cell(const Frame* frames, int nframes, l
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (frames[mid].cell0 <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// frame of strip u (frames sorted by first strip)
+__device__ __forceinline__ int frame_of_unit(const Frame* frames, int nframes, long long u) {
+  int lo = 0, hi = nframes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (frames[mid].u0 <= u) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
@@ -498,282 +516,217 @@ __device__ __forceinline__ void block_append(const bool (&put)[NL], uint32_t g, 
   __syncthreads();
 }
 
-// The incremental kernels come in two forms: over all words in blocks (as in
-// iteration 1, with the cell classes deciding what each word does) and over
-// the listed cells (one warp per cell). Both are launched; the block form runs
-// when at least a quarter of the cells are listed (`dense_from`), the list
-// form otherwise.
-
 // cell class of word (wc, y) of frame f; 4 (everything changed) without classes
 __device__ __forceinline__ uint32_t cell_class(const uint32_t* __restrict__ cls, const Frame& f, int wc, int y) {
   return cls ? cls[f.cell0 + (long long)(y / kCH) * f.wpr + wc] : 4u;
 }
 
-// need_kernel: nsp = dilate5(hot) & act, needS = dilate5(nsp) within the frame.
-// Per word by cell class (iteration 1: class 4 everywhere): within 4 px of a
-// change (class >= 3) nsp is written, test cleared and all of nsp queued for
-// S'; within 6 px only (class 2) the test bits join QT; within 6 px, S is
-// queued where needS holds and S is not current (sval; cleared within 2 px).
-__global__ void __launch_bounds__(256) need_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
-                                                   Queues Q, const uint32_t* __restrict__ cls,
-                                                   unsigned int dense_from) {
-  // rows y0-4 .. y0+kBH+3 (kBH + 8), words wc0-1 .. wc0+kBW (kBW + 2)
-  constexpr int RW = kBW + 2, RR = kBH + 8;
-  __shared__ uint32_t sHot[RR][RW], sAct[RR][RW], sNsp[RR][RW];
-  __shared__ int ws[kThreads / 32 + 1];
-  if (cls && Q.n[kNL6] < dense_from) return;  // the list form runs
-  const int t = threadIdx.x;
-  for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
-    const int fi = frame_of_block(frames, nframes, b);
-    const Frame& f = frames[fi];
-    const long long lb = b - f.blk0;
-    const int bys = int(lb / f.bx), bxs = int(lb - (long long)bys * f.bx);
-    const int wc0 = bxs * kBW, y0 = bys * kBH;
-    for (int i = t; i < RR * RW; i += kThreads) {
-      const int rr = i / RW, cc = i - rr * RW;
-      const int y = y0 - 4 + rr, wc = wc0 - 1 + cc;
-      const bool in = y >= 0 && y < f.h && wc >= 0 && wc < f.wpr;
-      sHot[rr][cc] = in ? f.hot[size_t(y) * f.wpr + wc] : 0u;
-      sAct[rr][cc] = in ? f.act[size_t(y) * f.wpr + wc] : 0u;
+// The column kernels (need, m3need): one warp per strip of 32 words x kSH rows,
+// lane = word. The lane walks down the strip keeping the last rows of its word
+// in registers, so a vertical dilation is an OR of registers and a horizontal
+// one an OR across lanes; lanes 0 and 31 also carry the words left and right of
+// the strip, of which only the bits next to the strip are used. The strip's
+// queue words wait in shared memory until the warp has counted them: one
+// atomic per warp and queue, then one coalesced entry per nonzero word.
+constexpr int kColWarps = 4;
+
+struct ColWords {
+  uint32_t w[kColWarps][kSH][2][32];  // per warp, row, queue: the word of each lane
+};
+
+// Counts a row's words of queue j (entries: words with a bit; positions: bits).
+__device__ __forceinline__ void col_count(uint32_t v, unsigned int& ents, unsigned int& pix) {
+  ents += __popc(__ballot_sync(0xffffffffu, v != 0u));
+  pix += __reduce_add_sync(0xffffffffu, unsigned(__popc(v)));
+}
+
+// Writes the strip's entries of queue j (rows y0 .. y0+kSH-1, lane = word wc0+lane).
+__device__ __forceinline__ void col_write(const ColWords& sw, int warp, int j, const Frame& f, int wc0, int y0,
+                                          unsigned int base, uint2* q) {
+  const int lane = threadIdx.x & 31;
+  for (int rr = 0; rr < kSH; ++rr) {
+    const uint32_t v = sw.w[warp][rr][j][lane];
+    const unsigned bal = __ballot_sync(0xffffffffu, v != 0u);
+    if (v) {
+      const uint32_t gw = uint32_t(f.word0 + (long long)(y0 + rr) * f.wpr + wc0 + lane);
+      q[base + __popc(bal & ((1u << lane) - 1u))] = make_uint2(gw, v);
     }
-    __syncthreads();
-    // nsp on rows y0-2 .. y0+kBH+1 (kBH + 4), all RW words
-    for (int i = t; i < (kBH + 4) * RW; i += kThreads) {
-      const int rr = i / RW + 2, cc = i - (i / RW) * RW;
-      uint32_t a = 0, l = 0, r = 0;
-#pragma unroll
-      for (int d = -2; d <= 2; ++d) {
-        a |= sHot[rr + d][cc];
-        if (cc > 0) l |= sHot[rr + d][cc - 1];
-        if (cc < RW - 1) r |= sHot[rr + d][cc + 1];
-      }
-      sNsp[rr][cc] = hdil<2>(l, a, r) & sAct[rr][cc];
-    }
-    __syncthreads();
-    // the block's own words
-    const int rr = t / kBW + 4, cc = t % kBW + 1;
-    const int y = y0 + t / kBW, wc = wc0 + t % kBW;
-    const bool mine = y < f.h && wc < f.wpr;
-    uint32_t qs = 0, qsp = 0, qt = 0;
-    const uint32_t cl = mine ? cell_class(cls, f, wc, y) : 0u;
-    if (cl >= 2u) {
-      uint32_t a = 0, l = 0, r = 0;
-#pragma unroll
-      for (int d = -2; d <= 2; ++d) {
-        a |= sNsp[rr + d][cc];
-        l |= sNsp[rr + d][cc - 1];
-        r |= sNsp[rr + d][cc + 1];
-      }
-      const uint32_t needS = hdil<2>(l, a, r) & frame_word(wc, f.w);
-      const size_t o = size_t(y) * f.wpr + wc;
-      if (cl >= 3u) {
-        qsp = sNsp[rr][cc];
-        f.nsp[o] = qsp;
-        f.test[o] = 0u;
-      } else {
-        qt = f.test[o];
-      }
-      const uint32_t sv = (cl >= 4u) ? 0u : f.sval[o];
-      qs = needS & ~sv;
-      f.sval[o] = sv | needS;
-    }
-    emit_word(qs, f, wc, y, Q.q0, Q.n + kNS, ws);
-    emit_word(qsp, f, wc, y, Q.q1, Q.n + kNSP, ws);
-    if (cls) emit_word(qt, f, wc, y, Q.q2, Q.n + kNT, ws);  // emit_word ends with a barrier
+    base += __popc(bal);
   }
 }
 
-// Vertical OR over rows lane-R .. lane+R of the warp (lanes hold consecutive rows).
-template <int R>
-__device__ __forceinline__ uint32_t vor(uint32_t v) {
-  uint32_t o = v;
-#pragma unroll
-  for (int d = 1; d <= R; ++d) o |= __shfl_up_sync(0xffffffffu, v, d) | __shfl_down_sync(0xffffffffu, v, d);
-  return o;
+// Reserves the strip's entries and positions of two queues (counters ne[0..1],
+// np[0..1]); returns the entry bases to every lane.
+__device__ __forceinline__ void col_reserve(const unsigned int (&ents)[2], const unsigned int (&pix)[2],
+                                            unsigned int* ne0, unsigned int* ne1, unsigned int* np0,
+                                            unsigned int* np1, unsigned int (&base)[2]) {
+  const int lane = threadIdx.x & 31;
+  unsigned int b0 = 0, b1 = 0;
+  if (lane == 0) {
+    if (ents[0]) b0 = atomicAdd(ne0, ents[0]);
+    if (ents[1]) b1 = atomicAdd(ne1, ents[1]);
+    if (pix[0]) atomicAdd(np0, pix[0]);
+    if (pix[1]) atomicAdd(np1, pix[1]);
+  }
+  base[0] = __shfl_sync(0xffffffffu, b0, 0);
+  base[1] = __shfl_sync(0xffffffffu, b1, 0);
 }
 
-// need_list_kernel (iteration >= 2), one warp per cell of list l6. Lanes 0-15
-// hold rows y0-4 .. y0+11 of the cell's word column and its neighbours; nsp is
-// recomputed on rows y0-2 .. y0+9, needS on the cell's rows (lanes 4-11).
-// Cells within 4 px of a change: nsp written, S' requeued on all of nsp, test
-// cleared (sp sets it again). Cells within 6 px only: their (current) test bits
-// join QT. S is requeued where needed and not current (all of needS in cells
-// within 2 px of a change).
-__global__ void __launch_bounds__(256) need_list_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
-                                                        const uint32_t* __restrict__ cls, unsigned int dense_from) {
+// need_kernel: nsp = dilate5(hot) & act, needS = dilate5(nsp) within the frame,
+// per word by cell class (iteration 1: class 4 everywhere): within 4 px of a
+// change (class >= 3) nsp is written, test cleared (sp sets it again) and all of
+// nsp queued for S'; within 6 px (class >= 2), S is queued where needS holds
+// and S is not current (sval; cleared within 2 px). Column kernel: rows
+// y0-4 .. y0+kSH+3 feed the five-row windows of hot and nsp.
+__global__ void __launch_bounds__(kColWarps * 32) need_kernel(const Frame* __restrict__ frames, int nframes,
+                                                              long long nunits, Queues Q,
+                                                              const uint32_t* __restrict__ cls) {
+  __shared__ ColWords sw;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned int n = Q.n[kNL6];
-  if (n >= dense_from) return;  // the block form runs
-  for (unsigned int i = blockIdx.x * 8u + warp; i < n; i += gridDim.x * 8u) {
-    const uint32_t c = Q.l6[i];
-    const Frame& f = frames[frame_of_cell(frames, nframes, c)];
-    const uint32_t lc = c - uint32_t(f.cell0);
-    const int cy = int(lc / uint32_t(f.wpr)), wc = int(lc - uint32_t(cy) * uint32_t(f.wpr));
-    const uint32_t cl = cls[c];
-    const int y = cy * kCH - 4 + (lane & 15);
-    const bool rowin = lane < 16 && y >= 0 && y < f.h;
-    const size_t ro = size_t(rowin ? y : 0) * f.wpr;
-    uint32_t hv[5], aw[3];
-#pragma unroll
-    for (int j = 0; j < 5; ++j) {
-      const int wj = wc - 2 + j;
-      hv[j] = vor<2>((rowin && wj >= 0 && wj < f.wpr) ? f.hot[ro + wj] : 0u);
-    }
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const int wj = wc - 1 + j;
-      aw[j] = (rowin && wj >= 0 && wj < f.wpr) ? f.act[ro + wj] : 0u;
-    }
-    uint32_t nv[3];
-    uint32_t nsp_c = 0;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const uint32_t ns = hdil<2>(hv[j], hv[j + 1], hv[j + 2]) & aw[j];
-      if (j == 1) nsp_c = ns;
-      nv[j] = vor<2>(ns);
-    }
-    const bool mine = lane >= 4 && lane < 4 + kCH && y < f.h;
-    uint32_t qs = 0, qsp = 0, qt = 0;
-    if (mine) {
-      const uint32_t needS = hdil<2>(nv[0], nv[1], nv[2]) & frame_word(wc, f.w);
-      const size_t o = ro + wc;
-      if (cl >= 3) {
-        f.nsp[o] = nsp_c;
-        f.test[o] = 0u;
-        qsp = nsp_c;
-      } else {
-        qt = f.test[o];
+  for (long long u = (long long)blockIdx.x * kColWarps + warp; u < nunits; u += (long long)gridDim.x * kColWarps) {
+    const Frame& f = frames[frame_of_unit(frames, nframes, u)];
+    const long long lu = u - f.u0;
+    const int uy = int(lu / f.ugx), ux = int(lu - (long long)uy * f.ugx);
+    const int wc0 = ux * 32, y0 = uy * kSH, wc = wc0 + lane;
+    const bool inw = wc < f.wpr;
+    const int hw = lane == 0 ? wc0 - 1 : wc0 + 32;  // halo word (lanes 0 and 31)
+    const bool hin = (lane == 0 || lane == 31) && hw >= 0 && hw < f.wpr;
+    const uint32_t fmask = inw ? frame_word(wc, f.w) : 0u;
+    uint32_t h0 = 0, h1 = 0, h2 = 0, h3 = 0, h4 = 0;  // own hot, rows r-4 .. r
+    uint32_t g0 = 0, g1 = 0, g2 = 0, g3 = 0, g4 = 0;  // halo hot
+    uint32_t a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;  // act, rows r-2 .. r (own, halo)
+    uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0, n4 = 0;  // own nsp, rows r-6 .. r-2
+    uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0, m4 = 0;  // halo nsp
+    unsigned int ents[2] = {0u, 0u}, pix[2] = {0u, 0u};
+    for (int r = y0 - 4; r < y0 + kSH + 4; ++r) {
+      const bool rin = r >= 0 && r < f.h;
+      const size_t ro = size_t(rin ? r : 0) * f.wpr;
+      const uint32_t hot = (rin && inw) ? f.hot[ro + wc] : 0u, act = (rin && inw) ? f.act[ro + wc] : 0u;
+      const uint32_t ghot = (rin && hin) ? f.hot[ro + hw] : 0u, gact = (rin && hin) ? f.act[ro + hw] : 0u;
+      h0 = h1; h1 = h2; h2 = h3; h3 = h4; h4 = hot;
+      g0 = g1; g1 = g2; g2 = g3; g3 = g4; g4 = ghot;
+      a0 = a1; a1 = a2; a2 = act;
+      b0 = b1; b1 = b2; b2 = gact;
+      // nsp of row r-2
+      const uint32_t vh = h0 | h1 | h2 | h3 | h4, gvh = g0 | g1 | g2 | g3 | g4;
+      uint32_t left = __shfl_up_sync(0xffffffffu, vh, 1), right = __shfl_down_sync(0xffffffffu, vh, 1);
+      const uint32_t gl = __shfl_sync(0xffffffffu, gvh, 0), gr = __shfl_sync(0xffffffffu, gvh, 31);
+      if (lane == 0) left = gl;
+      if (lane == 31) right = gr;
+      const uint32_t nsp = hdil<2>(left, vh, right) & a0;
+      const uint32_t gn = (lane == 0 ? hdil<2>(0u, gvh, vh) : hdil<2>(vh, gvh, 0u)) & b0;
+      n0 = n1; n1 = n2; n2 = n3; n3 = n4; n4 = nsp;
+      m0 = m1; m1 = m2; m2 = m3; m3 = m4; m4 = gn;
+      // needS of row r-4
+      const int yo = r - 4;
+      if (yo < y0) continue;  // whole warp
+      const uint32_t vn = n0 | n1 | n2 | n3 | n4, gvn = m0 | m1 | m2 | m3 | m4;
+      uint32_t nl = __shfl_up_sync(0xffffffffu, vn, 1), nr = __shfl_down_sync(0xffffffffu, vn, 1);
+      const uint32_t gnl = __shfl_sync(0xffffffffu, gvn, 0), gnr = __shfl_sync(0xffffffffu, gvn, 31);
+      if (lane == 0) nl = gnl;
+      if (lane == 31) nr = gnr;
+      uint32_t qs = 0, qsp = 0;
+      if (yo < f.h && inw) {
+        const uint32_t cl = cell_class(cls, f, wc, yo);
+        if (cl >= 2u) {
+          const uint32_t needS = hdil<2>(nl, vn, nr) & fmask;
+          const size_t o = size_t(yo) * f.wpr + wc;
+          if (cl >= 3u) {
+            qsp = n2;  // nsp of row yo
+            f.nsp[o] = qsp;
+            f.test[o] = 0u;
+          }
+          const uint32_t sv = (cl >= 4u) ? 0u : f.sval[o];
+          qs = needS & ~sv;
+          if ((sv | needS) != sv || cl >= 4u) f.sval[o] = sv | needS;
+        }
       }
-      const uint32_t sv = (cl >= 4) ? 0u : f.sval[o];
-      qs = needS & ~sv;
-      f.sval[o] = sv | needS;
+      sw.w[warp][yo - y0][0][lane] = qs;
+      sw.w[warp][yo - y0][1][lane] = qsp;
+      col_count(qs, ents[0], pix[0]);
+      col_count(qsp, ents[1], pix[1]);
     }
-    warp_emit(qs, f, wc, y, Q.q0, Q.n + kNS);
-    warp_emit(qsp, f, wc, y, Q.q1, Q.n + kNSP);
-    warp_emit(qt, f, wc, y, Q.q2, Q.n + kNT);
+    unsigned int base[2];
+    col_reserve(ents, pix, Q.n + kNS, Q.n + kNSP, Q.n + kNSpx, Q.n + kNSPpx, base);
+    __syncwarp();
+    col_write(sw, warp, 0, f, wc0, y0, base[0], reinterpret_cast<uint2*>(Q.q0));
+    col_write(sw, warp, 1, f, wc0, y0, base[1], reinterpret_cast<uint2*>(Q.q1));
+    __syncwarp();  // the shared words are refilled for the next strip
   }
 }
 
-// m3need_kernel: needM3 = dilate3(QT) within the frame, QT = the test bits of
-// cells of class >= 2 (iteration 1: all) -> queue QM3 where M3 is not current
-// (m3val; cleared in cells of class 4), bit plane m3val.
-__global__ void __launch_bounds__(256) m3need_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
-                                                     Queues Q, const uint32_t* __restrict__ cls,
-                                                     unsigned int dense_from) {
-  constexpr int RW = kBW + 2, RR = kBH + 6;
-  __shared__ uint32_t sT[RR][RW];
-  __shared__ int ws[kThreads / 32 + 1];
-  if (cls && Q.n[kNL9] < dense_from) return;  // the list form runs
-  const int t = threadIdx.x;
-  for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
-    const int fi = frame_of_block(frames, nframes, b);
-    const Frame& f = frames[fi];
-    const long long lb = b - f.blk0;
-    const int bys = int(lb / f.bx), bxs = int(lb - (long long)bys * f.bx);
-    const int wc0 = bxs * kBW, y0 = bys * kBH;
-    for (int i = t; i < RR * RW; i += kThreads) {
-      const int rr = i / RW, cc = i - rr * RW;
-      const int y = y0 - 3 + rr, wc = wc0 - 1 + cc;
-      const bool in = y >= 0 && y < f.h && wc >= 0 && wc < f.wpr;
-      sT[rr][cc] = (in && cell_class(cls, f, wc, y) >= 2u) ? f.test[size_t(y) * f.wpr + wc] : 0u;
-    }
-    __syncthreads();
-    const int rr = t / kBW + 3, cc = t % kBW + 1;
-    const int y = y0 + t / kBW, wc = wc0 + t % kBW;
-    uint32_t a = 0, l = 0, r = 0;
-#pragma unroll
-    for (int d = -3; d <= 3; ++d) {
-      a |= sT[rr + d][cc];
-      l |= sT[rr + d][cc - 1];
-      r |= sT[rr + d][cc + 1];
-    }
-    const bool mine = y < f.h && wc < f.wpr;
-    uint32_t qm = 0;
-    if (mine) {
-      const uint32_t need = hdil<3>(l, a, r) & frame_word(wc, f.w);
-      const size_t o = size_t(y) * f.wpr + wc;
-      const uint32_t old = f.m3val[o];
-      const uint32_t mv = (cell_class(cls, f, wc, y) >= 4u) ? 0u : old;
-      qm = need & ~mv;
-      if ((mv | need) != old) f.m3val[o] = mv | need;
-    }
-    emit_word(qm, f, wc, y, Q.q0, Q.n + kNM3, ws);  // ends with a barrier: sT may be refilled
-  }
-}
-
-// m3need_list_kernel (iteration >= 2), one warp per cell of list l9: needM3 =
-// dilate3(QT), where QT = test bits in cells of class >= 2 (within 6 px of a
-// change); lanes 0-13 hold rows y0-3 .. y0+10. M3 is requeued where needed and
-// not current (all of needM3 in cells within 2 px of a change).
-__global__ void __launch_bounds__(256) m3need_list_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
-                                                          const uint32_t* __restrict__ cls, unsigned int dense_from) {
+// m3need_kernel: QT = the test bits of cells of class >= 2 (iteration 1: all),
+// needM3 = dilate3(QT) within the frame -> queue QT, and queue QM3 where M3 is
+// not current (m3val; cleared in cells of class 4); bit plane m3val. Column
+// kernel: rows y0-3 .. y0+kSH+2 feed the seven-row window of QT.
+__global__ void __launch_bounds__(kColWarps * 32) m3need_kernel(const Frame* __restrict__ frames, int nframes,
+                                                                long long nunits, Queues Q,
+                                                                const uint32_t* __restrict__ cls) {
+  __shared__ ColWords sw;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned int n = Q.n[kNL9];
-  if (n >= dense_from) return;  // the block form runs
-  for (unsigned int i = blockIdx.x * 8u + warp; i < n; i += gridDim.x * 8u) {
-    const uint32_t c = Q.l9[i];
-    const Frame& f = frames[frame_of_cell(frames, nframes, c)];
-    const uint32_t lc = c - uint32_t(f.cell0);
-    const int cy = int(lc / uint32_t(f.wpr)), wc = int(lc - uint32_t(cy) * uint32_t(f.wpr));
-    const int y0 = cy * kCH;
-    const int y = y0 - 3 + lane;
-    const bool rowin = lane < kCH + 6 && y >= 0 && y < f.h;
-    const int ry = rowin ? y : 0;
-    const long long crow = f.cell0 + (long long)(ry / kCH) * f.wpr;  // first cell of this row's cell row
-    uint32_t tv[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const int wj = wc - 1 + j;
-      uint32_t t = 0;
-      if (rowin && wj >= 0 && wj < f.wpr && cls[crow + wj] >= 2u) t = f.test[size_t(ry) * f.wpr + wj];
-      tv[j] = vor<3>(t);
+  for (long long u = (long long)blockIdx.x * kColWarps + warp; u < nunits; u += (long long)gridDim.x * kColWarps) {
+    const Frame& f = frames[frame_of_unit(frames, nframes, u)];
+    const long long lu = u - f.u0;
+    const int uy = int(lu / f.ugx), ux = int(lu - (long long)uy * f.ugx);
+    const int wc0 = ux * 32, y0 = uy * kSH, wc = wc0 + lane;
+    const bool inw = wc < f.wpr;
+    const int hw = lane == 0 ? wc0 - 1 : wc0 + 32;
+    const bool hin = (lane == 0 || lane == 31) && hw >= 0 && hw < f.wpr;
+    const uint32_t fmask = inw ? frame_word(wc, f.w) : 0u;
+    uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0;  // own QT words, rows r-6 .. r
+    uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0, s6 = 0;  // halo QT words
+    unsigned int ents[2] = {0u, 0u}, pix[2] = {0u, 0u};
+    for (int r = y0 - 3; r < y0 + kSH + 3; ++r) {
+      const bool rin = r >= 0 && r < f.h;
+      const size_t ro = size_t(rin ? r : 0) * f.wpr;
+      const uint32_t qt = (rin && inw && cell_class(cls, f, wc, r) >= 2u) ? f.test[ro + wc] : 0u;
+      const uint32_t gqt = (rin && hin && cell_class(cls, f, hw, r) >= 2u) ? f.test[ro + hw] : 0u;
+      t0 = t1; t1 = t2; t2 = t3; t3 = t4; t4 = t5; t5 = t6; t6 = qt;
+      s0 = s1; s1 = s2; s2 = s3; s3 = s4; s4 = s5; s5 = s6; s6 = gqt;
+      const int yo = r - 3;
+      if (yo < y0) continue;  // whole warp
+      const uint32_t v = t0 | t1 | t2 | t3 | t4 | t5 | t6, gv = s0 | s1 | s2 | s3 | s4 | s5 | s6;
+      uint32_t left = __shfl_up_sync(0xffffffffu, v, 1), right = __shfl_down_sync(0xffffffffu, v, 1);
+      const uint32_t gl = __shfl_sync(0xffffffffu, gv, 0), gr = __shfl_sync(0xffffffffu, gv, 31);
+      if (lane == 0) left = gl;
+      if (lane == 31) right = gr;
+      uint32_t qm = 0, qto = 0;
+      if (yo < f.h && inw) {
+        const uint32_t need = hdil<3>(left, v, right) & fmask;
+        const size_t o = size_t(yo) * f.wpr + wc;
+        const bool c4 = cell_class(cls, f, wc, yo) >= 4u;
+        if (need || c4) {
+          const uint32_t old = c4 ? 0u : f.m3val[o];
+          qm = need & ~old;
+          if (c4 || qm) f.m3val[o] = old | need;
+        }
+        qto = t3;  // QT word of row yo
+      }
+      sw.w[warp][yo - y0][0][lane] = qm;
+      sw.w[warp][yo - y0][1][lane] = qto;
+      col_count(qm, ents[0], pix[0]);
+      col_count(qto, ents[1], pix[1]);
     }
-    const bool mine = lane >= 3 && lane < 3 + kCH && y < f.h;
-    uint32_t qm = 0;
-    if (mine) {
-      const uint32_t need = hdil<3>(tv[0], tv[1], tv[2]) & frame_word(wc, f.w);
-      const size_t o = size_t(y) * f.wpr + wc;
-      const uint32_t mv = (cls[c] >= 4u) ? 0u : f.m3val[o];
-      qm = need & ~mv;
-      f.m3val[o] = mv | need;
-    }
-    warp_emit(qm, f, wc, y, Q.q0, Q.n + kNM3);
+    unsigned int base[2];
+    col_reserve(ents, pix, Q.n + kNM3, Q.n + kNT, Q.n + kNM3px, Q.n + kNTpx, base);
+    __syncwarp();
+    col_write(sw, warp, 0, f, wc0, y0, base[0], reinterpret_cast<uint2*>(Q.q0));
+    col_write(sw, warp, 1, f, wc0, y0, base[1], reinterpret_cast<uint2*>(Q.q2));
+    __syncwarp();
   }
 }
 
 // cell_list_kernel (iteration >= 2): the cells of class 4 (within 2 px of a
-// change) -> l2, class >= 2 (within 6 px) -> l6, class >= 2 or next to such a
-// cell -> l9 (needM3 reaches 3 px beyond the cells whose candidates are tested).
-__global__ void __launch_bounds__(256) cell_list_kernel(const Frame* __restrict__ frames, int nframes,
-                                                        long long ncells, const uint32_t* __restrict__ cls, Queues Q) {
+// change) -> l2, for the bound pass.
+__global__ void __launch_bounds__(256) cell_list_kernel(long long ncells, const uint32_t* __restrict__ cls, Queues Q) {
   __shared__ int ws[kThreads / 32 + 1];
-  __shared__ unsigned int sbase[3];
+  __shared__ unsigned int sbase[1];
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long c0 = (long long)blockIdx.x * blockDim.x; c0 < ncells; c0 += stride) {  // whole blocks
     const long long c = c0 + threadIdx.x;
-    uint32_t cl = 0;
-    bool in9 = false;
-    if (c < ncells) {
-      cl = cls[c];
-      in9 = cl >= 2u;
-      if (!in9) {
-        const Frame& f = frames[frame_of_cell(frames, nframes, c)];
-        const long long lc = c - f.cell0;
-        const int cy = int(lc / f.wpr), wc = int(lc - (long long)cy * f.wpr);
-        for (int dy = -1; dy <= 1 && !in9; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int yy = cy + dy, xx = wc + dx;
-            if (yy < 0 || yy >= f.ncy || xx < 0 || xx >= f.wpr) continue;
-            if (cls[f.cell0 + (long long)yy * f.wpr + xx] >= 2u) {
-              in9 = true;
-              break;
-            }
-          }
-      }
-    }
-    const bool put[3] = {cl >= 4u, cl >= 2u, in9};
-    uint32_t* const lists[3] = {Q.l2, Q.l6, Q.l9};
-    block_append<3>(put, uint32_t(c), lists, Q.n + kNL2, ws, sbase);
+    const bool put[1] = {c < ncells && cls[c] >= 4u};
+    uint32_t* const lists[1] = {Q.l2};
+    block_append<1>(put, uint32_t(c), lists, Q.n + kNL2, ws, sbase);
   }
 }
 
@@ -826,63 +779,126 @@ __device__ __forceinline__ void load_window(const float* __restrict__ a, int x, 
   }
 }
 
-// s_kernel: at QS, m5 (floored), N, L+ and S of J.
-__global__ void __launch_bounds__(256) s_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k) {
-  const unsigned int n = Q.n[kNS];
-  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t g = Q.q0[i];
-    const Pix P = decode(frames, nframes, Q, g);
-    const Frame& f = frames[P.fi];
-    float v[25];
-    load_window<2>(qsrc(f, k), P.x, P.y, f.w, f.h, v);
-    const float lp = lplus(v[12], v[7], v[17], v[11], v[13]);
-    const float m5f = floor_m5(sel_med25(v));
-    const float nn = noise_of(m5f, f.gain, __fmul_rn(f.rn, f.rn));
-    const size_t o = size_t(g - uint32_t(f.pix0));
-    f.mapS[o] = __fdiv_rn(lp, __fmul_rn(2.f, nn));
-    f.mapN[o] = nn;
+// Position of the r-th (0-based) set bit of w (r < popc(w)).
+__device__ __forceinline__ int select_bit(uint32_t w, int r) {
+  int p = 0;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const int c = __popc(w & ((1u << s) - 1u));
+    if (r >= c) {
+      r -= c;
+      w >>= s;
+      p += s;
+    }
+  }
+  return p;
+}
+
+// Frame, row and first column of global word gw (frames sorted by first word).
+__device__ __forceinline__ void decode_word(const Frame* frames, int nframes, uint32_t gw, int& fi, int& y, int& x0) {
+  int lo = 0, hi = nframes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (frames[mid].word0 <= (long long)gw) lo = mid; else hi = mid - 1;
+  }
+  fi = lo;
+  const uint32_t lw = gw - uint32_t(frames[lo].word0), wpr = uint32_t(frames[lo].wpr);
+  y = int(lw / wpr);
+  x0 = 32 * int(lw - uint32_t(y) * wpr);
+}
+
+// Shared state of expand_words.
+struct ExpandSmem {
+  uint32_t mask[kThreads];
+  int incl[kThreads];  // inclusive prefix of the masks' bit counts
+  int fi[kThreads], y[kThreads], x0[kThreads];
+  int ws[kThreads / 32 + 1];
+};
+
+// Expands a queue of n word entries into pixels: per chunk of kThreads
+// entries, a block scan of the bit counts, then one pixel per thread per round,
+// found by binary search in the prefix and a bit select in the mask. Every
+// thread of the block runs every round and calls body(valid, frame, x, y), so
+// body may hold block-wide steps.
+template <typename F>
+__device__ __forceinline__ void expand_words(const Frame* __restrict__ frames, int nframes, const uint2* __restrict__ q,
+                                             unsigned int n, ExpandSmem& sm, F&& body) {
+  const int t = threadIdx.x;
+  for (unsigned int c0 = blockIdx.x * kThreads; c0 < n; c0 += gridDim.x * kThreads) {  // whole blocks
+    uint32_t m = 0;
+    int fi = 0, y = 0, x0 = 0;
+    if (c0 + t < n) {
+      const uint2 e = q[c0 + t];
+      m = e.y;
+      decode_word(frames, nframes, e.x, fi, y, x0);
+    }
+    int total = 0;
+    const int ex = block_excl_scan(__popc(m), sm.ws, total);
+    sm.mask[t] = m;
+    sm.incl[t] = ex + __popc(m);
+    sm.fi[t] = fi;
+    sm.y[t] = y;
+    sm.x0[t] = x0;
+    __syncthreads();
+    for (int r0 = 0; r0 < total; r0 += kThreads) {
+      const int j = r0 + t;
+      int k = 0;  // first entry whose inclusive prefix exceeds j
+#pragma unroll
+      for (int s = kThreads / 2; s >= 1; s >>= 1)
+        if (sm.incl[k + s - 1] <= j) k += s;
+      const bool valid = j < total;
+      const uint32_t mk = sm.mask[k];
+      const int bit = valid ? select_bit(mk, j - (sm.incl[k] - __popc(mk))) : 0;
+      body(valid, sm.fi[k], sm.x0[k] + bit, sm.y[k]);
+    }
+    __syncthreads();  // the shared state is refilled by the next chunk
   }
 }
 
-// sp_kernel: at QSP, S' = S - med5(S); S' > sigclip -> test bit and queue QT.
+// s_kernel: at QS, m5 (floored), N, L+ and S of J.
+__global__ void __launch_bounds__(256) s_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k) {
+  __shared__ ExpandSmem sm;
+  expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNS], sm,
+               [&](bool valid, int fi, int x, int y) {
+                 if (!valid) return;
+                 const Frame& f = frames[fi];
+                 float v[25];
+                 load_window<2>(qsrc(f, k), x, y, f.w, f.h, v);
+                 const float lp = lplus(v[12], v[7], v[17], v[11], v[13]);
+                 const float m5f = floor_m5(sel_med25(v));
+                 const float nn = noise_of(m5f, f.gain, __fmul_rn(f.rn, f.rn));
+                 const size_t o = size_t(y) * f.w + x;
+                 f.mapS[o] = __fdiv_rn(lp, __fmul_rn(2.f, nn));
+                 f.mapN[o] = nn;
+               });
+}
+
+// sp_kernel: at QSP, S' = S - med5(S); S' > sigclip -> test bit.
 __global__ void __launch_bounds__(256) sp_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p) {
-  __shared__ int ws[kThreads / 32 + 1];
-  __shared__ unsigned int sbase[1];
-  const unsigned int n = Q.n[kNSP];
-  const unsigned int stride = gridDim.x * blockDim.x;
-  for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // whole blocks iterate together
-    const unsigned int i = i0 + threadIdx.x;
-    bool test = false;
-    uint32_t g = 0;
-    if (i < n) {
-      g = Q.q1[i];
-      const Pix P = decode(frames, nframes, Q, g);
-      const Frame& f = frames[P.fi];
-      float v[25];
-      load_window<2>(f.mapS, P.x, P.y, f.w, f.h, v);
-      const float sp = __fsub_rn(v[12], sel_med25(v));
-      const size_t o = size_t(g - uint32_t(f.pix0));
-      f.mapSp[o] = sp;
-      test = sp > p.sigclip;
-      if (test) atomicOr(&f.test[size_t(P.y) * f.wpr + (P.x >> 5)], 1u << (P.x & 31));
-    }
-    const bool put[1] = {test};
-    uint32_t* const lists[1] = {Q.q2};
-    block_append<1>(put, g, lists, Q.n + kNT, ws, sbase);
-  }
+  __shared__ ExpandSmem sm;
+  expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q1), Q.n[kNSP], sm,
+               [&](bool valid, int fi, int x, int y) {
+                 if (!valid) return;
+                 const Frame& f = frames[fi];
+                 float v[25];
+                 load_window<2>(f.mapS, x, y, f.w, f.h, v);
+                 const float sp = __fsub_rn(v[12], sel_med25(v));
+                 f.mapSp[size_t(y) * f.w + x] = sp;
+                 if (sp > p.sigclip) atomicOr(&f.test[size_t(y) * f.wpr + (x >> 5)], 1u << (x & 31));
+               });
 }
 
 // m3_kernel: at QM3, med3 of J.
 __global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k) {
-  const unsigned int n = Q.n[kNM3];
-  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t g = Q.q0[i];
-    const Pix P = decode(frames, nframes, Q, g);
-    const Frame& f = frames[P.fi];
-    float v[9];
-    load_window<1>(qsrc(f, k), P.x, P.y, f.w, f.h, v);
-    f.mapM3[size_t(g - uint32_t(f.pix0))] = sel_med9(v);
-  }
+  __shared__ ExpandSmem sm;
+  expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNM3], sm,
+               [&](bool valid, int fi, int x, int y) {
+                 if (!valid) return;
+                 const Frame& f = frames[fi];
+                 float v[9];
+                 load_window<1>(qsrc(f, k), x, y, f.w, f.h, v);
+                 f.mapM3[size_t(y) * f.w + x] = sel_med9(v);
+               });
 }
 
 // The objlim test of candidate c: S'(c) / max(F/N, 0.01) > objlim (article
@@ -895,67 +911,54 @@ __device__ __forceinline__ float objlim_stat(const Params& p, float fval, float 
   return (p.objlim_form == 1) ? __fdiv_rn(__fmul_rn(2.f, s), fn) : __fdiv_rn(sp, fn);
 }
 
-// Appends g to queue q when pred holds (warp-aggregated; every lane calls it).
-__device__ __forceinline__ void warp_append_if(bool pred, uint32_t g, uint32_t* q, unsigned int* n) {
-  const int lane = threadIdx.x & 31;
-  const unsigned m = __ballot_sync(0xffffffffu, pred);
-  if (!m) return;
-  const int leader = __ffs(m) - 1;
-  unsigned int base = 0;
-  if (lane == leader) base = atomicAdd(n, (unsigned int)__popc(m));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (pred) q[base + __popc(m & ((1u << lane) - 1u))] = g;
-}
-
 // cand_test_kernel: at QT, the 7 column medians of the 7x7 window of m3; at
 // most 3 values of a column lie below (above) its median, so at most 21 of 49
 // lie below the smallest (above the largest) column median, which bound
 // med7(m3) from below (above). Tests the bounds decide go to the candidates
 // (pass) or are dropped; the rest to the open tests.
 __global__ void __launch_bounds__(256, 3) cand_test_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
-                                                        Params p) {
-  __shared__ int ws[kThreads / 32 + 1];
+                                                           Params p) {
+  __shared__ ExpandSmem sm;
   __shared__ unsigned int sbase[2];
-  const unsigned int n = Q.n[kNT];
-  const unsigned int stride = gridDim.x * blockDim.x;
-  for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // whole blocks iterate together
-    const unsigned int i = i0 + threadIdx.x;
-    bool pass = false, open = false;
-    uint32_t g = 0;
-    if (i < n) {
-      g = Q.q2[i];
-      const Pix P = decode(frames, nframes, Q, g);
-      const Frame& f = frames[P.fi];
-      const size_t o = size_t(g - uint32_t(f.pix0));
-      const float nn = f.mapN[o], sv = f.mapS[o], spv = f.mapSp[o];
-      float u[49];
-      load_window<3>(f.mapM3, P.x, P.y, f.w, f.h, u);
-      float lo = INFINITY, hi = -INFINITY;
-      const float mc = u[24];
+  expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q2), Q.n[kNT], sm,
+               [&](bool valid, int fi, int x, int y) {
+                 bool pass = false, open = false;
+                 uint32_t g = 0;
+                 if (valid) {
+                   const Frame& f = frames[fi];
+                   const size_t o = size_t(y) * f.w + x;
+                   g = uint32_t(f.pix0 + (long long)o);
+                   const float nn = f.mapN[o], sv = f.mapS[o], spv = f.mapSp[o];
+                   float u[49];
+                   load_window<3>(f.mapM3, x, y, f.w, f.h, u);
+                   float lo = INFINITY, hi = -INFINITY;
+                   const float mc = u[24];
 #pragma unroll
-      for (int dx = 0; dx < 7; ++dx) {
-        float col[7];
+                   for (int dx = 0; dx < 7; ++dx) {
+                     float col[7];
 #pragma unroll
-        for (int dy = 0; dy < 7; ++dy) col[dy] = u[dy * 7 + dx];
-        const float cm = sel_med7(col);
-        lo = fminf(lo, cm);
-        hi = fmaxf(hi, cm);
-      }
-      const float rlow = objlim_stat(p, __fsub_rn(mc, lo), nn, sv, spv);   // F at its largest
-      const float rhigh = objlim_stat(p, __fsub_rn(mc, hi), nn, sv, spv);  // F at its smallest
-      pass = rlow > p.objlim;
-      open = !pass && rhigh > p.objlim;
-    }
-    const bool put[2] = {pass, open};
-    uint32_t* const lists[2] = {Q.q0, Q.q1};
-    block_append<2>(put, g, lists, Q.n + kNPass, ws, sbase);
-  }
+                     for (int dy = 0; dy < 7; ++dy) col[dy] = u[dy * 7 + dx];
+                     const float cm = sel_med7(col);
+                     lo = fminf(lo, cm);
+                     hi = fmaxf(hi, cm);
+                   }
+                   const float rlow = objlim_stat(p, __fsub_rn(mc, lo), nn, sv, spv);   // F at its largest
+                   const float rhigh = objlim_stat(p, __fsub_rn(mc, hi), nn, sv, spv);  // F at its smallest
+                   pass = rlow > p.objlim;
+                   open = !pass && rhigh > p.objlim;
+                 }
+                 const bool put[2] = {pass, open};
+                 uint32_t* const lists[2] = {Q.q0, Q.q1};
+                 block_append<2>(put, g, lists, Q.n + kNPass, sm.ws, sbase);
+               });
 }
 
 // cand_full_kernel: at the open tests, the exact F = m3 - med7(m3) and the
 // objlim test -> candidates.
 __global__ void __launch_bounds__(256) cand_full_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
                                                         Params p) {
+  __shared__ int ws[kThreads / 32 + 1];
+  __shared__ unsigned int sbase[1];
   const unsigned int n = Q.n[kNAmb];
   const unsigned int stride = gridDim.x * blockDim.x;
   for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // whole warps iterate together
@@ -972,7 +975,9 @@ __global__ void __launch_bounds__(256) cand_full_kernel(const Frame* __restrict_
       const float fval = __fsub_rn(u[24], sel_med49(u));
       pass = objlim_stat(p, fval, f.mapN[o], f.mapS[o], f.mapSp[o]) > p.objlim;
     }
-    warp_append_if(pass, g, Q.q0, Q.n + kNPass);
+    const bool put[1] = {pass};
+    uint32_t* const lists[1] = {Q.q0};
+    block_append<1>(put, g, lists, Q.n + kNPass, ws, sbase);
   }
 }
 
@@ -1251,23 +1256,24 @@ __global__ void __launch_bounds__(256) rep_compute_kernel(const Frame* __restric
     const Pix P = decode(frames, nframes, Q, g);
     const Frame& f = frames[P.fi];
     const float* __restrict__ J = qsrc(f, k);
-    const uint32_t* __restrict__ M = f.bits_a;
-    int xs[5], ys[5];
-#pragma unroll
-    for (int d = 0; d < 5; ++d) {
-      xs[d] = clampi(P.x - 2 + d, 0, f.w - 1);
-      ys[d] = clampi(P.y - 2 + d, 0, f.h - 1);
-    }
-    uint32_t win = 0;  // 25 window flags, row-major
     float v[25];
+    load_window<2>(J, P.x, P.y, f.w, f.h, v);
+    uint32_t win = 0;  // 25 window flags, row-major, of the clamped window
+    if (P.x >= 2 && P.x < f.w - 2) {
 #pragma unroll
-    for (int dy = 0; dy < 5; ++dy)
+      for (int dy = 0; dy < 5; ++dy)
+        win |= plane_bits5(f.bits_a, f.wpr, f.w, P.x - 2, clampi(P.y - 2 + dy, 0, f.h - 1)) << (5 * dy);
+    } else {
 #pragma unroll
-      for (int dx = 0; dx < 5; ++dx) {
-        const int q = dy * 5 + dx;
-        v[q] = J[size_t(ys[dy]) * f.w + xs[dx]];
-        win |= ((M[size_t(ys[dy]) * f.wpr + (xs[dx] >> 5)] >> (xs[dx] & 31)) & 1u) << q;
+      for (int dy = 0; dy < 5; ++dy) {
+        const size_t ro = size_t(clampi(P.y - 2 + dy, 0, f.h - 1)) * f.wpr;
+#pragma unroll
+        for (int dx = 0; dx < 5; ++dx) {
+          const int xx = clampi(P.x - 2 + dx, 0, f.w - 1);
+          win |= ((f.bits_a[ro + (xx >> 5)] >> (xx & 31)) & 1u) << (dy * 5 + dx);
+        }
       }
+    }
     const int nu = 25 - __popc(win);
     float out;
     if (nu > 0) {
@@ -1358,10 +1364,10 @@ __global__ void __launch_bounds__(256) mask_kernel(const Frame* __restrict__ fra
 __global__ void queue_work_kernel(const Frame* __restrict__ frames, Queues Q, int k, long long dense) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     unsigned long long* wk = frames[0].work + kWork * (k - 1);
-    wk[0] += Q.n[kNS];
-    wk[1] += Q.n[kNSP];
-    wk[2] += Q.n[kNM3];
-    wk[3] += Q.n[kNT];
+    wk[0] += Q.n[kNSpx];
+    wk[1] += Q.n[kNSPpx];
+    wk[2] += Q.n[kNM3px];
+    wk[3] += Q.n[kNTpx];
     wk[4] += Q.n[kNAmb];
     wk[5] += (k == 1) ? (unsigned long long)dense : (unsigned long long)Q.n[kNL2] * (kCH * 32);
     for (int i = 0; i < kNCount; ++i)
