@@ -269,16 +269,6 @@ __device__ __forceinline__ void bound_consts(const Params& p, float& chot, float
   clow = 4.f * tlow * tlow * 0.9999f;
 }
 
-// 16 bits spread to the even bits of a word (bit i -> bit 2i)
-__device__ __forceinline__ uint32_t spread16(uint32_t x) {
-  x &= 0xffffu;
-  x = (x | (x << 8)) & 0x00ff00ffu;
-  x = (x | (x << 4)) & 0x0f0f0f0fu;
-  x = (x | (x << 2)) & 0x33333333u;
-  x = (x | (x << 1)) & 0x55555555u;
-  return x;
-}
-
 // Sliding column-median state of one column: rows r-2 .. r+1 of the current step.
 struct Col4 {
   float a, b, c, d;
@@ -373,16 +363,23 @@ __device__ __forceinline__ void bound_span2(const Frame& f, const float* __restr
       const float denA = gain * (mlowA > 0.f ? mlowA : 0.f) + rn2;
       const float denB = gain * (mlowB > 0.f ? mlowB : 0.f) + rn2;
       const float lhsA = lpA * lpA * g2, lhsB = lpB * lpB * g2;
-      const unsigned actA = __ballot_sync(0xffffffffu, xa < w && lhsA > clow * denA);
-      const unsigned actB = __ballot_sync(0xffffffffu, xb < w && lhsB > clow * denB);
-      const unsigned hotA = __ballot_sync(0xffffffffu, xa < w && lhsA > chot * denA);
-      const unsigned hotB = __ballot_sync(0xffffffffu, xb < w && lhsB > chot * denB);
-      // word wc holds lanes 0-15 (bits 2l, 2l+1), word wc+1 lanes 16-31; lane j < 2 stores word wc+j
-      const int sh = lane ? 16 : 0;
-      const uint32_t act = spread16(actA >> sh) | (spread16(actB >> sh) << 1);
-      const uint32_t hot = spread16(hotA >> sh) | (spread16(hotB >> sh) << 1);
-      if (lane < 2 && wc + lane < f.wpr) {
-        const size_t o = size_t(yy) * f.wpr + wc + lane;
+      // word wc holds lanes 0-15 (bits 2l, 2l+1), word wc+1 lanes 16-31: each half
+      // ORs its lanes' bit pairs, shifted into place
+      const int sh = 2 * (lane & 15);
+      const uint32_t va = (uint32_t(xa < w && lhsA > clow * denA) | (uint32_t(xb < w && lhsB > clow * denB) << 1))
+                          << sh;
+      const uint32_t vh = (uint32_t(xa < w && lhsA > chot * denA) | (uint32_t(xb < w && lhsB > chot * denB) << 1))
+                          << sh;
+      uint32_t act, hot;
+      if (lane < 16) {
+        act = __reduce_or_sync(0x0000ffffu, va);
+        hot = __reduce_or_sync(0x0000ffffu, vh);
+      } else {
+        act = __reduce_or_sync(0xffff0000u, va);
+        hot = __reduce_or_sync(0xffff0000u, vh);
+      }
+      if ((lane & 15) == 0 && wc + (lane >> 4) < f.wpr) {
+        const size_t o = size_t(yy) * f.wpr + wc + (lane >> 4);
         f.act[o] = act;
         f.hot[o] = hot;
       }
@@ -572,6 +569,20 @@ __device__ __forceinline__ void col_reserve(const unsigned int (&ents)[2], const
   base[1] = __shfl_sync(0xffffffffu, b1, 0);
 }
 
+// Whether this lane's word (and halo word) has a cell of class >= 2 among the
+// strip's cell rows, widened by `margin` cell rows: a strip where no lane has
+// one has nothing to compute (iterations >= 2).
+__device__ __forceinline__ bool strip_has_class2(const uint32_t* __restrict__ cls, const Frame& f, int wc, bool inw,
+                                                 int hw, bool hin, int y0, int margin) {
+  const int cy0 = y0 / kCH - margin, cy1 = min((y0 + kSH) / kCH + margin, f.ncy);
+  bool any = false;
+  for (int cy = max(cy0, 0); cy < cy1; ++cy) {
+    const uint32_t* row = cls + f.cell0 + (long long)cy * f.wpr;
+    if ((inw && row[wc] >= 2u) || (hin && row[hw] >= 2u)) any = true;
+  }
+  return any;
+}
+
 // need_kernel: nsp = dilate5(hot) & act, needS = dilate5(nsp) within the frame,
 // per word by cell class (iteration 1: class 4 everywhere): within 4 px of a
 // change (class >= 3) nsp is written, test cleared (sp sets it again) and all of
@@ -592,42 +603,56 @@ __global__ void __launch_bounds__(kColWarps * 32) need_kernel(const Frame* __res
     const int hw = lane == 0 ? wc0 - 1 : wc0 + 32;  // halo word (lanes 0 and 31)
     const bool hin = (lane == 0 || lane == 31) && hw >= 0 && hw < f.wpr;
     const uint32_t fmask = inw ? frame_word(wc, f.w) : 0u;
+    if (cls && !__any_sync(0xffffffffu, strip_has_class2(cls, f, wc, inw, -1, false, y0, 0))) continue;
     uint32_t h0 = 0, h1 = 0, h2 = 0, h3 = 0, h4 = 0;  // own hot, rows r-4 .. r
     uint32_t g0 = 0, g1 = 0, g2 = 0, g3 = 0, g4 = 0;  // halo hot
     uint32_t a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;  // act, rows r-2 .. r (own, halo)
     uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0, n4 = 0;  // own nsp, rows r-6 .. r-2
     uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0, m4 = 0;  // halo nsp
     unsigned int ents[2] = {0u, 0u}, pix[2] = {0u, 0u};
-    for (int r = y0 - 4; r < y0 + kSH + 4; ++r) {
-      const bool rin = r >= 0 && r < f.h;
-      const size_t ro = size_t(rin ? r : 0) * f.wpr;
-      const uint32_t hot = (rin && inw) ? f.hot[ro + wc] : 0u, act = (rin && inw) ? f.act[ro + wc] : 0u;
-      const uint32_t ghot = (rin && hin) ? f.hot[ro + hw] : 0u, gact = (rin && hin) ? f.act[ro + hw] : 0u;
-      h0 = h1; h1 = h2; h2 = h3; h3 = h4; h4 = hot;
-      g0 = g1; g1 = g2; g2 = g3; g3 = g4; g4 = ghot;
-      a0 = a1; a1 = a2; a2 = act;
-      b0 = b1; b1 = b2; b2 = gact;
-      // nsp of row r-2
-      const uint32_t vh = h0 | h1 | h2 | h3 | h4, gvh = g0 | g1 | g2 | g3 | g4;
-      uint32_t left = __shfl_up_sync(0xffffffffu, vh, 1), right = __shfl_down_sync(0xffffffffu, vh, 1);
-      const uint32_t gl = __shfl_sync(0xffffffffu, gvh, 0), gr = __shfl_sync(0xffffffffu, gvh, 31);
-      if (lane == 0) left = gl;
-      if (lane == 31) right = gr;
-      const uint32_t nsp = hdil<2>(left, vh, right) & a0;
-      const uint32_t gn = (lane == 0 ? hdil<2>(0u, gvh, vh) : hdil<2>(vh, gvh, 0u)) & b0;
-      n0 = n1; n1 = n2; n2 = n3; n3 = n4; n4 = nsp;
-      m0 = m1; m1 = m2; m2 = m3; m3 = m4; m4 = gn;
-      // needS of row r-4
-      const int yo = r - 4;
-      if (yo < y0) continue;  // whole warp
-      const uint32_t vn = n0 | n1 | n2 | n3 | n4, gvn = m0 | m1 | m2 | m3 | m4;
-      uint32_t nl = __shfl_up_sync(0xffffffffu, vn, 1), nr = __shfl_down_sync(0xffffffffu, vn, 1);
-      const uint32_t gnl = __shfl_sync(0xffffffffu, gvn, 0), gnr = __shfl_sync(0xffffffffu, gvn, 31);
-      if (lane == 0) nl = gnl;
-      if (lane == 31) nr = gnr;
-      uint32_t qs = 0, qsp = 0;
-      if (yo < f.h && inw) {
-        const uint32_t cl = cell_class(cls, f, wc, yo);
+    // rows y0-4 .. y0+kSH+3 in chunks of 8: the chunk's loads are issued together
+    static_assert((kSH + 8) % 8 == 0, "whole chunks");
+    for (int rc = y0 - 4; rc < y0 + kSH + 4; rc += 8) {
+      uint32_t Lh[8], La[8], Lgh[8], Lga[8], Lc[8], Ls[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = rc + i, yo = r - 4;
+        const bool rin = r >= 0 && r < f.h;
+        const size_t ro = size_t(rin ? r : 0) * f.wpr;
+        Lh[i] = (rin && inw) ? f.hot[ro + wc] : 0u;
+        La[i] = (rin && inw) ? f.act[ro + wc] : 0u;
+        Lgh[i] = (rin && hin) ? f.hot[ro + hw] : 0u;
+        Lga[i] = (rin && hin) ? f.act[ro + hw] : 0u;
+        const bool out = yo >= y0 && yo < f.h && inw;
+        Lc[i] = out ? cell_class(cls, f, wc, yo) : 0u;
+        Ls[i] = (out && Lc[i] >= 2u && Lc[i] < 4u) ? f.sval[size_t(yo) * f.wpr + wc] : 0u;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        h0 = h1; h1 = h2; h2 = h3; h3 = h4; h4 = Lh[i];
+        g0 = g1; g1 = g2; g2 = g3; g3 = g4; g4 = Lgh[i];
+        a0 = a1; a1 = a2; a2 = La[i];
+        b0 = b1; b1 = b2; b2 = Lga[i];
+        // nsp of row r-2
+        const uint32_t vh = h0 | h1 | h2 | h3 | h4, gvh = g0 | g1 | g2 | g3 | g4;
+        uint32_t left = __shfl_up_sync(0xffffffffu, vh, 1), right = __shfl_down_sync(0xffffffffu, vh, 1);
+        const uint32_t gl = __shfl_sync(0xffffffffu, gvh, 0), gr = __shfl_sync(0xffffffffu, gvh, 31);
+        if (lane == 0) left = gl;
+        if (lane == 31) right = gr;
+        const uint32_t nsp = hdil<2>(left, vh, right) & a0;
+        const uint32_t gn = (lane == 0 ? hdil<2>(0u, gvh, vh) : hdil<2>(vh, gvh, 0u)) & b0;
+        n0 = n1; n1 = n2; n2 = n3; n3 = n4; n4 = nsp;
+        m0 = m1; m1 = m2; m2 = m3; m3 = m4; m4 = gn;
+        // needS of row r-4
+        const int yo = rc + i - 4;
+        if (yo < y0) continue;  // whole warp
+        const uint32_t vn = n0 | n1 | n2 | n3 | n4, gvn = m0 | m1 | m2 | m3 | m4;
+        uint32_t nl = __shfl_up_sync(0xffffffffu, vn, 1), nr = __shfl_down_sync(0xffffffffu, vn, 1);
+        const uint32_t gnl = __shfl_sync(0xffffffffu, gvn, 0), gnr = __shfl_sync(0xffffffffu, gvn, 31);
+        if (lane == 0) nl = gnl;
+        if (lane == 31) nr = gnr;
+        uint32_t qs = 0, qsp = 0;
+        const uint32_t cl = Lc[i];  // 0 outside the frame
         if (cl >= 2u) {
           const uint32_t needS = hdil<2>(nl, vn, nr) & fmask;
           const size_t o = size_t(yo) * f.wpr + wc;
@@ -636,15 +661,15 @@ __global__ void __launch_bounds__(kColWarps * 32) need_kernel(const Frame* __res
             f.nsp[o] = qsp;
             f.test[o] = 0u;
           }
-          const uint32_t sv = (cl >= 4u) ? 0u : f.sval[o];
+          const uint32_t sv = Ls[i];  // 0 in cells of class 4
           qs = needS & ~sv;
           if ((sv | needS) != sv || cl >= 4u) f.sval[o] = sv | needS;
         }
+        sw.w[warp][yo - y0][0][lane] = qs;
+        sw.w[warp][yo - y0][1][lane] = qsp;
+        col_count(qs, ents[0], pix[0]);
+        col_count(qsp, ents[1], pix[1]);
       }
-      sw.w[warp][yo - y0][0][lane] = qs;
-      sw.w[warp][yo - y0][1][lane] = qsp;
-      col_count(qs, ents[0], pix[0]);
-      col_count(qsp, ents[1], pix[1]);
     }
     unsigned int base[2];
     col_reserve(ents, pix, Q.n + kNS, Q.n + kNSP, Q.n + kNSpx, Q.n + kNSPpx, base);
@@ -673,39 +698,51 @@ __global__ void __launch_bounds__(kColWarps * 32) m3need_kernel(const Frame* __r
     const int hw = lane == 0 ? wc0 - 1 : wc0 + 32;
     const bool hin = (lane == 0 || lane == 31) && hw >= 0 && hw < f.wpr;
     const uint32_t fmask = inw ? frame_word(wc, f.w) : 0u;
+    if (cls && !__any_sync(0xffffffffu, strip_has_class2(cls, f, wc, inw, hw, hin, y0, 1))) continue;
     uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0;  // own QT words, rows r-6 .. r
     uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0, s6 = 0;  // halo QT words
     unsigned int ents[2] = {0u, 0u}, pix[2] = {0u, 0u};
-    for (int r = y0 - 3; r < y0 + kSH + 3; ++r) {
-      const bool rin = r >= 0 && r < f.h;
-      const size_t ro = size_t(rin ? r : 0) * f.wpr;
-      const uint32_t qt = (rin && inw && cell_class(cls, f, wc, r) >= 2u) ? f.test[ro + wc] : 0u;
-      const uint32_t gqt = (rin && hin && cell_class(cls, f, hw, r) >= 2u) ? f.test[ro + hw] : 0u;
-      t0 = t1; t1 = t2; t2 = t3; t3 = t4; t4 = t5; t5 = t6; t6 = qt;
-      s0 = s1; s1 = s2; s2 = s3; s3 = s4; s4 = s5; s5 = s6; s6 = gqt;
-      const int yo = r - 3;
-      if (yo < y0) continue;  // whole warp
-      const uint32_t v = t0 | t1 | t2 | t3 | t4 | t5 | t6, gv = s0 | s1 | s2 | s3 | s4 | s5 | s6;
-      uint32_t left = __shfl_up_sync(0xffffffffu, v, 1), right = __shfl_down_sync(0xffffffffu, v, 1);
-      const uint32_t gl = __shfl_sync(0xffffffffu, gv, 0), gr = __shfl_sync(0xffffffffu, gv, 31);
-      if (lane == 0) left = gl;
-      if (lane == 31) right = gr;
-      uint32_t qm = 0, qto = 0;
-      if (yo < f.h && inw) {
-        const uint32_t need = hdil<3>(left, v, right) & fmask;
-        const size_t o = size_t(yo) * f.wpr + wc;
-        const bool c4 = cell_class(cls, f, wc, yo) >= 4u;
-        if (need || c4) {
-          const uint32_t old = c4 ? 0u : f.m3val[o];
-          qm = need & ~old;
-          if (c4 || qm) f.m3val[o] = old | need;
-        }
-        qto = t3;  // QT word of row yo
+    // rows y0-3 .. y0+kSH+2 in chunks of 8 (the last chunk runs 2 rows past the end)
+    for (int rc = y0 - 3; rc < y0 + kSH + 3; rc += 8) {
+      uint32_t Lq[8], Lg[8], Lm[8], Lc4[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = rc + i, yo = r - 3;
+        const bool rin = r >= 0 && r < f.h && r < y0 + kSH + 3;
+        const size_t ro = size_t(rin ? r : 0) * f.wpr;
+        Lq[i] = (rin && inw && cell_class(cls, f, wc, r) >= 2u) ? f.test[ro + wc] : 0u;
+        Lg[i] = (rin && hin && cell_class(cls, f, hw, r) >= 2u) ? f.test[ro + hw] : 0u;
+        const bool out = yo >= y0 && yo < y0 + kSH && yo < f.h && inw;
+        Lc4[i] = out ? uint32_t(cell_class(cls, f, wc, yo) >= 4u) : 0u;
+        Lm[i] = (out && !Lc4[i]) ? f.m3val[size_t(yo) * f.wpr + wc] : 0u;
       }
-      sw.w[warp][yo - y0][0][lane] = qm;
-      sw.w[warp][yo - y0][1][lane] = qto;
-      col_count(qm, ents[0], pix[0]);
-      col_count(qto, ents[1], pix[1]);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        t0 = t1; t1 = t2; t2 = t3; t3 = t4; t4 = t5; t5 = t6; t6 = Lq[i];
+        s0 = s1; s1 = s2; s2 = s3; s3 = s4; s4 = s5; s5 = s6; s6 = Lg[i];
+        const int yo = rc + i - 3;
+        if (yo < y0 || yo >= y0 + kSH) continue;  // whole warp
+        const uint32_t v = t0 | t1 | t2 | t3 | t4 | t5 | t6, gv = s0 | s1 | s2 | s3 | s4 | s5 | s6;
+        uint32_t left = __shfl_up_sync(0xffffffffu, v, 1), right = __shfl_down_sync(0xffffffffu, v, 1);
+        const uint32_t gl = __shfl_sync(0xffffffffu, gv, 0), gr = __shfl_sync(0xffffffffu, gv, 31);
+        if (lane == 0) left = gl;
+        if (lane == 31) right = gr;
+        uint32_t qm = 0, qto = 0;
+        if (yo < f.h && inw) {
+          const uint32_t need = hdil<3>(left, v, right) & fmask;
+          const bool c4 = Lc4[i] != 0u;
+          if (need || c4) {
+            const uint32_t old = Lm[i];  // 0 in cells of class 4
+            qm = need & ~old;
+            if (c4 || qm) f.m3val[size_t(yo) * f.wpr + wc] = old | need;
+          }
+          qto = t3;  // QT word of row yo
+        }
+        sw.w[warp][yo - y0][0][lane] = qm;
+        sw.w[warp][yo - y0][1][lane] = qto;
+        col_count(qm, ents[0], pix[0]);
+        col_count(qto, ents[1], pix[1]);
+      }
     }
     unsigned int base[2];
     col_reserve(ents, pix, Q.n + kNM3, Q.n + kNT, Q.n + kNM3px, Q.n + kNTpx, base);
