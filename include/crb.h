@@ -119,6 +119,24 @@ int crb_clean_batch(crb_ctx* ctx, int n, const float* const* imgs, const int* ws
                     const float* gains, const float* readnoises, float* const* out_cleans,
                     uint8_t* const* out_masks, cudaStream_t stream);
 
+/* crb_clean_batch for frames in HOST memory: imgs[i] (ws[i]*hs[i] floats) in,
+ * out_cleans[i] and out_masks[i] out, all host pointers (page-locked memory,
+ * e.g. cudaHostAlloc, lets the copies overlap the work). The frames are cut
+ * into chunks of consecutive frames of about 1/8 of the pixels each; chunk k+1
+ * is copied to the device while chunk k is cleaned and chunk k-1 is copied
+ * back, on the context's own streams with four device staging slots, and
+ * consecutive chunks are cleaned by the context and a second one it creates
+ * (own workspace and stream), so that their kernels overlap (all allocated on
+ * the first call and reused). Starts after the work already enqueued
+ * on `stream`; `stream` waits for the last copy-out, so a synchronisation of
+ * `stream` makes the host outputs valid. The results equal crb_clean_batch's on
+ * the same frames; crb_last_counts / crb_last_work of this context then
+ * describe its last chunk. CRB_ENOMEM when the staging buffers or the second
+ * context cannot be created. */
+int crb_clean_batch_host(crb_ctx* ctx, int n, const float* const* imgs, const int* ws, const int* hs,
+                         const float* gains, const float* readnoises, float* const* out_cleans,
+                         uint8_t* const* out_masks, cudaStream_t stream);
+
 /* Allocation-free clean of one frame. The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory while they
  * run -- onboard or embedded pipelines that fix their memory plan at start-up,
@@ -164,9 +182,10 @@ int crb_last_work(crb_ctx* ctx, long long* out, int max_iter);
 
 /* Kernel launches the last crb_clean / crb_clean_batch / crb_iterate enqueued
  * (memsets and copies not counted; a graph replay counts its kernels). The
- * queue pipeline launches 12 kernels in iteration 1, 15 in each later one
- * (including the form of the bound pass that the device-side size test skips)
- * and the mask kernel. -1 for a NULL context. */
+ * queue pipeline launches 2 descriptor uploads, 12 kernels in iteration 1, 15
+ * in each later one (including the form of the bound pass that the device-side
+ * size test skips) and the mask kernel; the fused tile pipeline 1 upload and
+ * niter + 1 kernels. -1 for a NULL context. */
 int crb_last_launches(const crb_ctx* ctx);
 
 /* One iteration from an explicit state, for stage-by-stage checks:

@@ -37,6 +37,7 @@ SIGNATURES = {
     "crb_destroy": (None, [_vp]),
     "crb_clean": (_ci, [_vp, _vp, _ci, _ci, _vp, _vp, _vp]),
     "crb_clean_batch": (_ci, [_vp, _ci, _PP, _PI, _PI, _PF, _PF, _PP, _PP, _vp]),
+    "crb_clean_batch_host": (_ci, [_vp, _ci, _PP, _PI, _PI, _PF, _PF, _PP, _PP, _vp]),
     "crb_clean_noalloc": (_ci, [_cf, _cf, _cf, _cf, _cf, _ci, _vp, _ci, _ci, _vp, _vp, _vp]),
     "crb_sync_status": (_ci, [_vp, _vp]),
     "crb_last_counts": (_ci, [_vp, ctypes.POINTER(ctypes.c_longlong), _ci]),

@@ -91,6 +91,31 @@ class Cleaner:
         rc = _lib.load().crb_clean_batch(self._h, n, a_img, a_w, a_h, a_g, a_r, a_out, a_msk, _stream(stream))
         check(rc, "crb_clean_batch")
 
+    def clean_batch_host_into(self, imgs, outs, masks, gains=None, readnoises=None, stream=None):
+        """crb_clean_batch_host: frames, outputs and masks are CPU tensors (pinned memory lets the copies
+        overlap the work); the outputs are valid once `stream` (default: the current stream) is synchronised."""
+        n = len(imgs)
+        for t, o, m in zip(imgs, outs, masks):
+            if t.device.type != "cpu" or o.device.type != "cpu" or m.device.type != "cpu":
+                raise ValueError("clean_batch_host_into takes CPU tensors")
+            if t.dtype != torch.float32 or o.dtype != torch.float32 or m.dtype != torch.uint8:
+                raise ValueError("frames and outputs float32, masks uint8")
+            if t.dim() != 2 or not t.is_contiguous() or o.shape != t.shape or m.shape != t.shape:
+                raise ValueError("contiguous 2-D frames with outputs of the same shape")
+        P = ctypes.c_void_p * n
+        I = ctypes.c_int * n
+        F = ctypes.c_float * n
+        a_img = P(*[t.data_ptr() for t in imgs])
+        a_out = P(*[t.data_ptr() for t in outs])
+        a_msk = P(*[t.data_ptr() for t in masks])
+        a_w = I(*[t.shape[1] for t in imgs])
+        a_h = I(*[t.shape[0] for t in imgs])
+        a_g = F(*gains) if gains is not None else None
+        a_r = F(*readnoises) if readnoises is not None else None
+        rc = _lib.load().crb_clean_batch_host(self._h, n, a_img, a_w, a_h, a_g, a_r, a_out, a_msk,
+                                              _stream(stream))
+        check(rc, "crb_clean_batch_host")
+
     def clean_batch(self, imgs, gains=None, readnoises=None, stream=None):
         outs = [torch.empty_like(t) for t in imgs]
         masks = [torch.empty(t.shape, dtype=torch.uint8, device=t.device) for t in imgs]

@@ -66,6 +66,11 @@ constexpr size_t kReplaceSmem = crb::ReplaceLayout<kRW, kRH>::bytes;
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
+// crb_clean_batch_host: staging slots and chunks per call
+constexpr int kStageSlots = 4, kStageChunks = 8;
+// descriptor buffers per context
+constexpr int kDescSlots = 4;
+
 // queue pipeline kernels, for the occupancy table
 enum QK {
   kQBound, kQNeed, kQS, kQSp, kQM3need, kQM3, kQCand, kQRepCompute, kQBoundList, kQRq, kQRepWrite, kQCellList,
@@ -118,25 +123,46 @@ struct crb_ctx {
 
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  // Descriptors (and the queue pipeline's frame table: frame of each
+  // 2^kTabShift pixels) go through a ring of kDescSlots staging and device
+  // buffers, so that a call waits only for the upload of the call kDescSlots
+  // back before refilling a staging buffer. The fields below view the slot of
+  // the current call.
+  struct DescSlot {
+    crb::Frame *d_frames = nullptr, *h_frames = nullptr;
+    uint32_t *d_tab = nullptr, *h_tab = nullptr;
+    int frames_cap = 0;
+    size_t tab_cap = 0;
+    cudaEvent_t upload_ev = nullptr;
+  } slot[kDescSlots];
+  int cur = 0;
   crb::Frame* d_frames = nullptr;
-  int frames_cap = 0;
   crb::Frame* h_frames = nullptr;  // pinned staging
-  uint32_t* d_tab = nullptr;       // queue pipeline: frame of each 2^kTabShift pixels
-  uint32_t* h_tab = nullptr;       // pinned staging
-  size_t tab_cap = 0, tab_n = 0;   // entries
+  uint32_t* d_tab = nullptr;
+  uint32_t* h_tab = nullptr;
+  size_t tab_n = 0;  // entries
   unsigned long long* d_counters = nullptr;
   int counters_cap = 0;  // in unsigned long longs
   int last_niter = 0;
   int last_launches = 0;  // kernels the work of the last call launches
   int mprev_frames = 0;   // crb_iterate: frames given an explicit M_{k-1}
   int last_nframes = 0;
-  cudaEvent_t upload_ev = nullptr, done_ev = nullptr;
+  cudaEvent_t upload_ev = nullptr, done_ev = nullptr;  // upload_ev: the current slot's
   bool any_call = false;
   int latched = CRB_OK;
 
   // graphs of the work of a call, by launch signature; autotuned tile shape by frame sizes
   std::vector<std::pair<GraphKey, cudaGraphExec_t>> graphs;
   cudaStream_t cap_stream = nullptr;
+
+  // crb_clean_batch_host: copy-in, clean and copy-out streams, kStageSlots device
+  // staging slots; chunks alternate between this context and a twin (own
+  // workspace, own clean stream), so that consecutive chunks' cleans overlap
+  crb_ctx* twin = nullptr;
+  cudaStream_t hs_in = nullptr, hs_cmp = nullptr, hs_cmp2 = nullptr, hs_out = nullptr;
+  cudaEvent_t h_entry = nullptr, h_in[kStageSlots] = {}, h_cmp[kStageSlots] = {}, h_free[kStageSlots] = {};
+  char* d_stage[kStageSlots] = {};
+  size_t stage_cap = 0;
   std::vector<std::pair<std::vector<long long>, int>> tuned;
 
   // profiling: event pairs around launches, by kernel kind (0 detect, 1 replace)
@@ -183,7 +209,8 @@ int init_ctx(crb_ctx* c) {
   CRB_CUDA(cudaFuncSetAttribute(kReplace, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kReplaceSmem)));
   CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_replace, kReplace, crb::kThreads, kReplaceSmem));
   if (c->occ_replace < 1) c->occ_replace = 1;
-  CRB_CUDA(cudaEventCreateWithFlags(&c->upload_ev, cudaEventDisableTiming));
+  for (auto& sl : c->slot) CRB_CUDA(cudaEventCreateWithFlags(&sl.upload_ev, cudaEventDisableTiming));
+  c->upload_ev = c->slot[0].upload_ev;
   CRB_CUDA(cudaEventCreateWithFlags(&c->done_ev, cudaEventDisableTiming));
   return CRB_OK;
 }
@@ -219,31 +246,41 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   return pa < pb + nb && pb < pa + na;
 }
 
-int ensure_frames(crb_ctx* c, int n) {
-  if (n <= c->frames_cap) return CRB_OK;
-  CRB_CUDA(cudaDeviceSynchronize());
-  cudaFree(c->d_frames);
-  cudaFreeHost(c->h_frames);
-  c->d_frames = nullptr;
-  c->h_frames = nullptr;
-  c->frames_cap = 0;
-  CRB_CUDA(cudaMalloc(&c->d_frames, sizeof(crb::Frame) * size_t(n)));
-  CRB_CUDA(cudaMallocHost(&c->h_frames, sizeof(crb::Frame) * size_t(n)));
-  c->frames_cap = n;
-  return CRB_OK;
-}
-
-int ensure_tab(crb_ctx* c, size_t entries) {
-  if (entries <= c->tab_cap) return CRB_OK;
-  CRB_CUDA(cudaDeviceSynchronize());
-  cudaFree(c->d_tab);
-  cudaFreeHost(c->h_tab);
-  c->d_tab = nullptr;
-  c->h_tab = nullptr;
-  c->tab_cap = 0;
-  CRB_CUDA(cudaMalloc(&c->d_tab, sizeof(uint32_t) * entries));
-  CRB_CUDA(cudaMallocHost(&c->h_tab, sizeof(uint32_t) * entries));
-  c->tab_cap = entries;
+// Moves to the next descriptor slot, with room for n frames and tab_entries
+// table entries, once the slot's previous upload has run; sets the views.
+int next_desc_slot(crb_ctx* c, int n, size_t tab_entries) {
+  c->cur = (c->cur + 1) % kDescSlots;
+  crb_ctx::DescSlot& S = c->slot[c->cur];
+  // generous first capacities, so that growing (which synchronises the device) is rare
+  n = std::max(n, 64);
+  tab_entries = std::max<size_t>(tab_entries, 8192);
+  if (n > S.frames_cap || tab_entries > S.tab_cap) {
+    CRB_CUDA(cudaDeviceSynchronize());
+    if (n > S.frames_cap) {
+      cudaFree(S.d_frames);
+      cudaFreeHost(S.h_frames);
+      S.d_frames = S.h_frames = nullptr;
+      S.frames_cap = 0;
+      CRB_CUDA(cudaMalloc(&S.d_frames, sizeof(crb::Frame) * size_t(n)));
+      CRB_CUDA(cudaMallocHost(&S.h_frames, sizeof(crb::Frame) * size_t(n)));
+      S.frames_cap = n;
+    }
+    if (tab_entries > S.tab_cap) {
+      cudaFree(S.d_tab);
+      cudaFreeHost(S.h_tab);
+      S.d_tab = S.h_tab = nullptr;
+      S.tab_cap = 0;
+      CRB_CUDA(cudaMalloc(&S.d_tab, sizeof(uint32_t) * tab_entries));
+      CRB_CUDA(cudaMallocHost(&S.h_tab, sizeof(uint32_t) * tab_entries));
+      S.tab_cap = tab_entries;
+    }
+  }
+  CRB_CUDA(cudaEventSynchronize(S.upload_ev));  // the staging buffers are free again
+  c->d_frames = S.d_frames;
+  c->h_frames = S.h_frames;
+  c->d_tab = S.d_tab;
+  c->h_tab = S.h_tab;
+  c->upload_ev = S.upload_ev;
   return CRB_OK;
 }
 
@@ -418,11 +455,11 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
   total += 3 * qbytes + 2 * fbytes + lbytes;
   const int nit = niter > 0 ? niter : 1;
   const int ncounters = (2 + crb::kWork) * nit * n;
-  int rc = ensure_frames(c, n);
+  const size_t tab_n = size_t(npix >> crb::kTabShift) + 1;
+  int rc = ensure_ws(c, total, ncounters);
   if (rc) return rc;
-  rc = ensure_ws(c, total, ncounters);
+  rc = next_desc_slot(c, n, tab_n);
   if (rc) return rc;
-  CRB_CUDA(cudaEventSynchronize(c->upload_ev));
   char* ws = static_cast<char*>(c->ws);
   long long pix0 = 0, rtiles = 0, cell0 = 0, nunits = 0, word0 = 0;
   for (int i = 0; i < n; ++i) {
@@ -477,9 +514,6 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
     nunits += (long long)f.ugx * ((s.h + crb::kSH - 1) / crb::kSH);
   }
   // frame of the first pixel of each 2^kTabShift pixels (frames are consecutive ranges)
-  const size_t tab_n = size_t(npix >> crb::kTabShift) + 1;
-  rc = ensure_tab(c, tab_n);
-  if (rc) return rc;
   c->tab_n = tab_n;
   for (size_t t = 0, fi = 0; t < tab_n; ++t) {
     const long long g = (long long)t << crb::kTabShift;
@@ -533,11 +567,10 @@ int prepare(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool map
   }
   const int nit = niter > 0 ? niter : 1;
   const int ncounters = (2 + crb::kWork) * nit * n;  // per frame: 2 per iteration, then kWork per iteration
-  int rc = ensure_frames(c, n);
+  int rc = ensure_ws(c, total > 0 ? total : 256, ncounters);
   if (rc) return rc;
-  rc = ensure_ws(c, total > 0 ? total : 256, ncounters);
+  rc = next_desc_slot(c, n, 0);
   if (rc) return rc;
-  CRB_CUDA(cudaEventSynchronize(c->upload_ev));  // the staging buffer is free again
 
   long long tiles = 0, rtiles = 0;
   for (int i = 0; i < n; ++i) {
@@ -581,21 +614,33 @@ int prepare(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool map
   return CRB_OK;
 }
 
+// Copies n 4-byte words from page-locked host memory, read directly by the
+// kernel: the descriptors reach the device without a copy engine, so they do
+// not queue behind large transfers of other streams (crb_clean_batch_host).
+__global__ void upload_kernel(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src, size_t n) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    dst[i] = src[i];
+}
+
 int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
-  CRB_CUDA(cudaMemcpyAsync(c->d_frames, c->h_frames, sizeof(crb::Frame) * size_t(P.n), cudaMemcpyHostToDevice,
-                           stream));
+  static_assert(sizeof(crb::Frame) % 4 == 0, "whole words");
+  const size_t nf = sizeof(crb::Frame) * size_t(P.n) / 4;
+  upload_kernel<<<int(std::min<size_t>((nf + 255) / 256, 64)), 256, 0, stream>>>(
+      reinterpret_cast<uint32_t*>(c->d_frames), reinterpret_cast<const uint32_t*>(c->h_frames), nf);
   if (P.queue)
-    CRB_CUDA(cudaMemcpyAsync(c->d_tab, c->h_tab, sizeof(uint32_t) * c->tab_n, cudaMemcpyHostToDevice, stream));
+    upload_kernel<<<int(std::min<size_t>((c->tab_n + 255) / 256, 64)), 256, 0, stream>>>(c->d_tab, c->h_tab,
+                                                                                          c->tab_n);
+  CRB_CUDA(cudaGetLastError());
   CRB_CUDA(cudaEventRecord(c->upload_ev, stream));
   c->last_niter = P.niter;
   c->last_nframes = P.n;
-  // the launches enqueue_work makes for this plan (memsets and copies not counted)
+  // the launches of this upload and of enqueue_work for this plan (memsets and copies not counted)
   if (P.niter == 0)
-    c->last_launches = 0;
-  else if (P.queue)  // iteration 1: 12 kernels, later ones 15, plus the mask
-    c->last_launches = 12 + 15 * (P.niter - 1) + 1;
+    c->last_launches = 1;
+  else if (P.queue)  // 2 uploads; iteration 1: 12 kernels, later ones 15, plus the mask
+    c->last_launches = 2 + 12 + 15 * (P.niter - 1) + 1;
   else
-    c->last_launches = (P.fuse ? P.niter + 1 : 2 * P.niter) + c->mprev_frames;
+    c->last_launches = 1 + (P.fuse ? P.niter + 1 : 2 * P.niter) + c->mprev_frames;
   return CRB_OK;
 }
 
@@ -766,13 +811,25 @@ void crb_destroy(crb_ctx* c) {
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->hs_out) cudaStreamSynchronize(c->hs_out);
+  if (c->twin) crb_destroy(c->twin);
+  for (cudaStream_t st : {c->hs_in, c->hs_cmp, c->hs_cmp2, c->hs_out})
+    if (st) cudaStreamDestroy(st);
+  if (c->h_entry) cudaEventDestroy(c->h_entry);
+  for (int i = 0; i < kStageSlots; ++i) {
+    for (cudaEvent_t e : {c->h_in[i], c->h_cmp[i], c->h_free[i]})
+      if (e) cudaEventDestroy(e);
+    cudaFree(c->d_stage[i]);
+  }
   cudaFree(c->ws);
-  cudaFree(c->d_frames);
-  cudaFree(c->d_tab);
+  for (auto& sl : c->slot) {
+    cudaFree(sl.d_frames);
+    cudaFree(sl.d_tab);
+    if (sl.h_frames) cudaFreeHost(sl.h_frames);
+    if (sl.h_tab) cudaFreeHost(sl.h_tab);
+    if (sl.upload_ev) cudaEventDestroy(sl.upload_ev);
+  }
   cudaFree(c->d_counters);
-  if (c->h_frames) cudaFreeHost(c->h_frames);
-  if (c->h_tab) cudaFreeHost(c->h_tab);
-  if (c->upload_ev) cudaEventDestroy(c->upload_ev);
   if (c->done_ev) cudaEventDestroy(c->done_ev);
   delete c;
 }
@@ -804,6 +861,119 @@ int crb_clean_batch(crb_ctx* c, int n, const float* const* imgs, const int* ws, 
     specs.push_back(FrameSpec{imgs[i], out_cleans[i], out_masks[i], nullptr, nullptr, ws[i], hs[i], g, r});
   }
   return run(c, specs, c->niter, false, stream);
+}
+
+int crb_clean_batch_host(crb_ctx* c, int n, const float* const* imgs, const int* ws, const int* hs,
+                         const float* gains, const float* readnoises, float* const* out_cleans,
+                         uint8_t* const* out_masks, cudaStream_t stream) {
+  if (!c) return fail(CRB_EINVAL, "null context");
+  if (n < 0 || (n > 0 && (!imgs || !ws || !hs || !out_cleans || !out_masks)))
+    return fail(CRB_EINVAL, "invalid batch arrays");
+  if (n == 0) return CRB_OK;
+  long long total = 0, largest = 0;
+  for (int i = 0; i < n; ++i) {
+    if (ws[i] < 1 || hs[i] < 1 || (long long)ws[i] * hs[i] >= (1LL << 31))
+      return fail(CRB_EINVAL, "frame " + std::to_string(i) + ": sizes");
+    if (!imgs[i] || !out_cleans[i] || !out_masks[i]) return fail(CRB_EINVAL, "frame " + std::to_string(i) + ": null");
+    const long long px = (long long)ws[i] * hs[i];
+    total += px;
+    largest = std::max(largest, px);
+  }
+  // chunks of consecutive frames of about total/kStageChunks pixels (at least the largest frame)
+  const long long target = std::max(largest, (total + kStageChunks - 1) / kStageChunks);
+  std::vector<int> first{0};
+  for (long long acc = 0, i = 0; i < n; ++i) {
+    const long long px = (long long)ws[i] * hs[i];
+    if (acc > 0 && acc + px > target) {
+      first.push_back(int(i));
+      acc = 0;
+    }
+    acc += px;
+  }
+  first.push_back(n);
+  auto frame_bytes = [&](int i) { return align256(size_t(ws[i]) * hs[i] * 4) * 2 + align256(size_t(ws[i]) * hs[i]); };
+  size_t need = 0;
+  for (size_t k = 0; k + 1 < first.size(); ++k) {
+    size_t b = 0;
+    for (int i = first[k]; i < first[k + 1]; ++i) b += frame_bytes(i);
+    need = std::max(need, b);
+  }
+  if (!c->twin) {
+    crb_options o = c->opt;
+    o.profile = 0;
+    c->twin = crb_create_ex(c->gain, c->rn, c->p.sigclip, c->p.sigfrac, c->p.objlim,
+                            c->niter, &o);
+    if (!c->twin) return fail(CRB_ENOMEM, "crb_clean_batch_host: second context: " + g_err);
+    c->twin->p = c->p;
+  }
+  if (!c->hs_in) {
+    for (cudaStream_t* st : {&c->hs_in, &c->hs_cmp, &c->hs_cmp2, &c->hs_out})
+      CRB_CUDA(cudaStreamCreateWithFlags(st, cudaStreamNonBlocking));
+    CRB_CUDA(cudaEventCreateWithFlags(&c->h_entry, cudaEventDisableTiming));
+    for (int i = 0; i < kStageSlots; ++i)
+      for (cudaEvent_t* e : {&c->h_in[i], &c->h_cmp[i], &c->h_free[i]})
+        CRB_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  }
+  if (need > c->stage_cap) {
+    CRB_CUDA(cudaDeviceSynchronize());
+    for (int s = 0; s < kStageSlots; ++s) {
+      cudaFree(c->d_stage[s]);
+      c->d_stage[s] = nullptr;
+    }
+    c->stage_cap = 0;
+    for (int s = 0; s < kStageSlots; ++s) {
+      const cudaError_t e = cudaMalloc(&c->d_stage[s], need);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CRB_ENOMEM, "staging buffers of " + std::to_string(kStageSlots) + " x " + std::to_string(need) +
+                                    " bytes could not be allocated");
+      }
+    }
+    c->stage_cap = need;
+  }
+  // the pipeline starts after the work already on `stream`
+  CRB_CUDA(cudaEventRecord(c->h_entry, stream));
+  CRB_CUDA(cudaStreamWaitEvent(c->hs_in, c->h_entry, 0));
+  for (size_t k = 0; k + 1 < first.size(); ++k) {
+    const int slot = int(k % kStageSlots), a = first[k], b = first[k + 1], m = b - a;
+    std::vector<const float*> d_img(static_cast<size_t>(m));
+    std::vector<float*> d_out(static_cast<size_t>(m));
+    std::vector<uint8_t*> d_msk(static_cast<size_t>(m));
+    char* p = c->d_stage[slot];
+    for (int i = a; i < b; ++i) {
+      const size_t px = size_t(ws[i]) * hs[i];
+      d_img[size_t(i - a)] = reinterpret_cast<const float*>(p);
+      d_out[size_t(i - a)] = reinterpret_cast<float*>(p + align256(px * 4));
+      d_msk[size_t(i - a)] = reinterpret_cast<uint8_t*>(p + 2 * align256(px * 4));
+      p += frame_bytes(i);
+    }
+    // copy in once the slot's previous copy-out is done
+    CRB_CUDA(cudaStreamWaitEvent(c->hs_in, c->h_free[slot], 0));
+    for (int i = a; i < b; ++i)
+      CRB_CUDA(cudaMemcpyAsync(const_cast<float*>(d_img[size_t(i - a)]), imgs[i], size_t(ws[i]) * hs[i] * 4,
+                               cudaMemcpyHostToDevice, c->hs_in));
+    CRB_CUDA(cudaEventRecord(c->h_in[slot], c->hs_in));
+    // clean, on this context or its twin
+    crb_ctx* cc = (k & 1) ? c->twin : c;
+    cudaStream_t cs = (k & 1) ? c->hs_cmp2 : c->hs_cmp;
+    CRB_CUDA(cudaStreamWaitEvent(cs, c->h_in[slot], 0));
+    const int rc = crb_clean_batch(cc, m, d_img.data(), ws + a, hs + a, gains ? gains + a : nullptr,
+                                   readnoises ? readnoises + a : nullptr, d_out.data(), d_msk.data(), cs);
+    if (rc != CRB_OK) return rc;
+    CRB_CUDA(cudaEventRecord(c->h_cmp[slot], cs));
+    // copy out
+    CRB_CUDA(cudaStreamWaitEvent(c->hs_out, c->h_cmp[slot], 0));
+    for (int i = a; i < b; ++i) {
+      const size_t px = size_t(ws[i]) * hs[i];
+      CRB_CUDA(cudaMemcpyAsync(out_cleans[i], d_out[size_t(i - a)], px * 4, cudaMemcpyDeviceToHost, c->hs_out));
+      CRB_CUDA(cudaMemcpyAsync(out_masks[i], d_msk[size_t(i - a)], px, cudaMemcpyDeviceToHost, c->hs_out));
+    }
+    CRB_CUDA(cudaEventRecord(c->h_free[slot], c->hs_out));
+  }
+  // `stream` continues after the last copy-out
+  CRB_CUDA(cudaEventRecord(c->h_entry, c->hs_out));
+  CRB_CUDA(cudaStreamWaitEvent(stream, c->h_entry, 0));
+  return CRB_OK;
 }
 
 int crb_iterate(crb_ctx* c, const float* J, const uint8_t* Mprev, int w, int h, float* out_J, uint8_t* out_M,

@@ -239,12 +239,40 @@ def test_graphs_and_autotune(graphs, shape, pipeline):
 
 @pytest.mark.parametrize("niter", [1, 2, 4])
 def test_launch_counts(niter):
-    """crb_last_launches reports the kernels a call enqueues: 12 + 15 (niter - 1) + 1 on the queue
-    pipeline, niter + 1 on the fused tile pipeline."""
+    """crb_last_launches reports the kernels a call enqueues: 2 descriptor uploads + 12 + 15 (niter - 1) + 1
+    on the queue pipeline, 1 upload + niter + 1 on the fused tile pipeline."""
     img = scene(120, 90, seed=9)
     cq = Cleaner(niter=niter)
     gpu_clean(cq, img)
-    assert cq.last_launches() == 12 + 15 * (niter - 1) + 1
+    assert cq.last_launches() == 2 + 12 + 15 * (niter - 1) + 1
     ct = Cleaner(niter=niter, pipeline="tile")
     gpu_clean(ct, img)
-    assert ct.last_launches() == niter + 1
+    assert ct.last_launches() == 1 + niter + 1
+
+
+@pytest.mark.parametrize("pinned", [True, False], ids=["pinned", "pageable"])
+def test_batch_host_equals_device_batch(pinned):
+    """crb_clean_batch_host (host buffers, chunked copies overlapping the cleans) gives crb_clean_batch's
+    results, call after call (the staging slots are reused)."""
+    rng = np.random.default_rng(3)
+    sizes = [(300, 200), (64, 1), (517, 333), (1, 40), (256, 256), (800, 600), (33, 97), (1024, 512), (90, 90)]
+    c_dev = Cleaner(niter=4)
+    c_host = Cleaner(niter=4)
+    for rep in range(2):
+        imgs = [synth.frame(w, h, seed=20 + rep, index=i) for i, (w, h) in enumerate(sizes)]
+        gains = [float(np.float32(rng.uniform(1, 7))) for _ in sizes]
+        rns = [float(np.float32(rng.uniform(3, 10))) for _ in sizes]
+        outs, masks = c_dev.clean_batch([dev(a) for a in imgs], gains, rns)
+        c_dev.sync()
+        h_imgs = [torch.from_numpy(a) for a in imgs]
+        h_outs = [torch.empty(a.shape, dtype=torch.float32) for a in imgs]
+        h_masks = [torch.empty(a.shape, dtype=torch.uint8) for a in imgs]
+        if pinned:
+            h_imgs = [t.pin_memory() for t in h_imgs]
+            h_outs = [t.pin_memory() for t in h_outs]
+            h_masks = [t.pin_memory() for t in h_masks]
+        c_host.clean_batch_host_into(h_imgs, h_outs, h_masks, gains, rns)
+        torch.cuda.synchronize()
+        for i in range(len(sizes)):
+            assert np.array_equal(h_outs[i].numpy(), host(outs[i])), (rep, i)
+            assert np.array_equal(h_masks[i].numpy(), host(masks[i])), (rep, i)
