@@ -44,10 +44,24 @@ DENSE_OPS_PER_PIX_ITER = 425.0
 # Algorithmic HBM bytes per pixel and iteration: read J (4 B), write I_k (4 B),
 # flag bits in and out (0.25 B).
 ALG_BYTES_PER_PIX_ITER = 8.25
-# min/max operations per bound-test position: the sliding column median (12
-# per two rows: the middle pair of four shared values, then one clamp per
-# row), two three-input minima over the five column medians, four clips in L+.
-BOUND_TEST_MINMAX = 6 + 2 + 4
+# Per tested pixel of the bound pass: min/max operations -- the sliding column
+# median (12 per two rows: the middle pair of four shared values, then one
+# clamp per row), the minimum of the five column medians (4), the clamp of that
+# minimum at 0 (1) -- and other FP32 operations: L+ (4 differences, 4 quadrant
+# sums, 4 clips taken as t+|t|, 3 sums, 1 scale = 16) and the two threshold
+# tests (gain*m, +rn^2, L+^2, *gain^2, two scaled thresholds, two compares = 8).
+BOUND_TEST_MINMAX = 6 + 4 + 1
+# DRAM bytes per bound-pass launch (read + write) on the 64-frame batch, from the
+# ncu capture of the current bound kernel on three 4096x4096 frames, scaled by
+# the tested pixels (see profiles/bound_kernel_triple4096.md); None when stale.
+BOUND_TRAFFIC = None
+# Algorithmic FP32 operations per unit of each kernel kind: (min/max, other).
+KIND_OPS = {
+    "bound": (BOUND_TEST_MINMAX, 24),
+    "s": (192, 22),       # med25; L+ 16, N: mul, add, sqrt, div; S: mul, div
+    "sprime": (192, 1),   # med25 of S; the difference
+    "m3": (33, 0),        # med9
+}
 
 
 def network_minmax():
@@ -323,7 +337,7 @@ def main():
             dist.barrier()
 
     from paper_1008_2192_gb300 import Cleaner
-    from paper_1008_2192_gb300.api import alu_peak
+    from paper_1008_2192_gb300.api import alu_peak, fadd_peak
     from synth import workloads as wl
 
     recipes, desc = recipes_for(args.workload)
@@ -364,7 +378,10 @@ def main():
     barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    det_ms, det_n, rep_ms, rep_n = cl.profile_read(reset=True)
+    kinds = cl.profile_kernels(reset=True)
+    det_ms = sum(v[0] for k, v in kinds.items() if k in ("bound", "need", "s", "sprime", "m3need", "m3", "cand",
+                                                          "grow", "cell_list", "tile_detect"))
+    rep_ms = sum(v[0] for k, v in kinds.items() if k in ("replace", "mask", "tile_replace"))
     cl.sync()
 
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")
@@ -435,28 +452,44 @@ def main():
         extras["serving"] = serve_run(torch, 1000.0, 2000)
 
     peaks = measured_peaks()
-    det_avg_ms = det_ms / max(det_n, 1)
-    rep_avg_ms = rep_ms / max(rep_n, 1)
-    # work of the last step (every step cleans the same batch), averaged per detection launch
+    fadd = fadd_peak()
+    # work of the last step (every step cleans the same batch)
     work = cl.last_work()
     net = network_minmax()
-    # candidate test: 7 column medians of 7 and their min and max (12), the full 49-median where still open
+    units = {"bound": sum(w[5] for w in work), "s": sum(w[0] for w in work), "sprime": sum(w[1] for w in work),
+             "m3": sum(w[2] for w in work)}
+    per_step = {k: v[0] / args.steps for k, v in kinds.items()}
+    tot = sum(per_step.values())
+    kernels = {k: {"ms_per_step": round(v, 4), "share": round(v / max(tot, 1e-9), 4)}
+               for k, v in sorted(per_step.items(), key=lambda kv: -kv[1]) if v > 0}
+    dom = max(per_step, key=lambda k: per_step[k])
+    if dom in KIND_OPS:
+        mm, fp = KIND_OPS[dom]
+        ops = (mm + fp) * units[dom]  # per step
+        achieved = ops / (per_step[dom] * 1e-3) / 1e12
+        peak = (mm + fp) / (mm / ops2 + fp / fadd) / 1e12  # the kernel's op mix at the measured issue rates
+        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                    "frac": achieved / peak, "traffic": BOUND_TRAFFIC if dom == "bound" else None,
+                    "peak_source": f"measured: crb_alu_peak min/max {ops2 / 1e12:.2f} T/s and crb_fadd_peak "
+                                   f"{fadd / 1e12:.2f} T/s, weighted by the kernel's {mm} min/max + {fp} other FP32 "
+                                   "operations per unit",
+                    "achieved_is": f"({mm} + {fp}) FP32 operations x units the kernel processed (counted live) / "
+                                   "its device time (CUDA events around each launch, timed region)",
+                    "units_per_step": units[dom]}
+    else:
+        roofline = {"bound": "latency", "kernel": dom, "achieved": None, "peak": None, "unit": None, "frac": None,
+                    "traffic": None}
+    # context: the selection networks over all detection kernels
     minmax = sum(w[0] * net[25] + w[1] * net[25] + w[2] * net[9] + w[3] * (7 * net[7] + 12) + w[4] * net[49]
-                 + w[5] * BOUND_TEST_MINMAX for w in work) / max(len(work), 1)
-    achieved = minmax / (det_avg_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "detect (stages a-d)", "achieved": achieved, "peak": ops2 / 1e12,
-                "unit": "Tops/s", "frac": achieved / (ops2 / 1e12), "traffic": None,
-                "peak_source": "measured: crb_alu_peak FP32 min/max issue rate (2-input form; 3-input form "
-                               f"{ops3 / 1e12:.2f})",
-                "achieved_is": "min/max operations of the selection networks the method evaluated (counted live "
-                               "per launch) / average detect launch time",
-                "work_per_iteration": [{"S": w[0], "Sprime": w[1], "med3": w[2], "cand_tests": w[3],
-                                        "cand_full_median": w[4], "bound_tests": w[5]} for w in work],
-                "dense_equivalent_tops": DENSE_OPS_PER_PIX_ITER * npix / (det_avg_ms * 1e-3) / 1e12,
-                "detect_ms_avg": det_avg_ms, "replace_ms_avg": rep_avg_ms,
-                "detect_share": det_ms / max(det_ms + rep_ms, 1e-9),
-                "hbm_frac_alg": (ALG_BYTES_PER_PIX_ITER * npix / (det_avg_ms + rep_avg_ms) / 1e6)
-                / peaks.get("hbm_gbs", 6782.4)}
+                 + w[5] * BOUND_TEST_MINMAX for w in work)
+    roofline.update({
+        "kernels": kernels,
+        "work_per_iteration": [{"S": w[0], "Sprime": w[1], "med3": w[2], "cand_tests": w[3],
+                                "cand_full_median": w[4], "bound_tests": w[5]} for w in work],
+        "detect_minmax_tops": minmax / (det_ms / args.steps * 1e-3) / 1e12,
+        "detect_ms_per_step": det_ms / args.steps, "replace_ms_per_step": rep_ms / args.steps,
+        "hbm_frac_alg": (ALG_BYTES_PER_PIX_ITER * npix * niter / ((det_ms + rep_ms) / args.steps) / 1e6)
+        / peaks.get("hbm_gbs", 6782.4)})
 
     if rank == 0:
         line = {"metric": "Mpix/s cleaned at niter=4 (batched, 1 GB300)", "value": value, "unit": "Mpix/s",

@@ -197,10 +197,10 @@ int crb_iterate(crb_ctx* ctx, const float* J, const uint8_t* Mprev, int w, int h
                 uint8_t* out_M, float* maps, cudaStream_t stream);
 
 /* Profiling (crb_options.profile = 1): after the stream has been synchronised,
- * writes the total device time in milliseconds and the number of launches of
- * the detection kernel (stages a-d) and of the replacement kernel (stage e)
- * since the last reset, then resets if reset != 0. Returns CRB_OK or
- * CRB_EINVAL (profiling off / null pointers). */
+ * writes the total device time in milliseconds and the number of timed
+ * brackets of the detection kernels (stages a-d) and of the replacement kernels
+ * (stage e) since the last reset, then resets if reset != 0 (all kinds of
+ * crb_profile_kernels). Returns CRB_OK or CRB_EINVAL (profiling off). */
 int crb_profile_read(crb_ctx* ctx, double* detect_ms, int* detect_launches, double* replace_ms,
                      int* replace_launches, int reset);
 
@@ -211,6 +211,19 @@ int crb_profile_read(crb_ctx* ctx, double* detect_ms, int* detect_launches, doub
  * Returns CRB_OK or CRB_ECUDA. A measurement aid for the roofline, not a
  * step of the method. */
 int crb_alu_peak(double* ops2_per_s, double* ops3_per_s, cudaStream_t stream);
+
+/* Measures the FP32 add issue rate the same way (independent add chains).
+ * Writes adds per second. Returns CRB_OK or CRB_ECUDA. A measurement aid. */
+int crb_fadd_peak(double* ops_per_s, cudaStream_t stream);
+
+/* Profiling by kernel kind (crb_options.profile = 1): after the stream has been
+ * synchronised, writes for up to max kinds the total device time in ms and the
+ * number of timed brackets since the last reset (then resets if reset != 0).
+ * Kinds, in order: 0 bound pass (both forms), 1 need, 2 S, 3 S', 4 m3need,
+ * 5 med3, 6 candidate tests, 7 growth, 8 cell lists, 9 tile-pipeline detection,
+ * 10 replacement, 11 u8 mask, 12 tile-pipeline replacement, 13 work counters.
+ * Returns the number of kinds written, or CRB_EINVAL. */
+int crb_profile_kernels(crb_ctx* ctx, double* ms, int* brackets, int max, int reset);
 
 /* Number of compiled tile shapes and their sizes (output tile of the detection kernel). */
 int crb_num_tile_shapes(void);

@@ -47,6 +47,8 @@ SIGNATURES = {
     "crb_profile_read": (_ci, [_vp, ctypes.POINTER(ctypes.c_double), _PI, ctypes.POINTER(ctypes.c_double), _PI,
                                _ci]),
     "crb_alu_peak": (_ci, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _vp]),
+    "crb_fadd_peak": (_ci, [ctypes.POINTER(ctypes.c_double), _vp]),
+    "crb_profile_kernels": (_ci, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_ci), _ci, _ci]),
     "crb_server_create": (_vp, [_cf, _cf, _cf, _cf, _cf, _ci, ctypes.POINTER(crb_options), ctypes.c_size_t, _ci,
                                 _ci]),
     "crb_server_submit": (_ci, [_vp, _vp, _ci, _ci, _cf, _cf, _vp, _vp, ctypes.c_uint64]),

@@ -167,6 +167,26 @@ class Cleaner:
                                            ctypes.byref(rn), int(reset)), "crb_profile_read")
         return dm.value, dn.value, rm.value, rn.value
 
+    PROFILE_KINDS = ("bound", "need", "s", "sprime", "m3need", "m3", "cand", "grow", "cell_list", "tile_detect",
+                     "replace", "mask", "tile_replace", "work")
+
+    def profile_kernels(self, reset=True):
+        """{kind: (ms, timed brackets)} since the last reset (crb_profile_kernels)."""
+        n = len(self.PROFILE_KINDS)
+        ms = (ctypes.c_double * n)()
+        br = (ctypes.c_int * n)()
+        k = _lib.load().crb_profile_kernels(self._h, ms, br, n, int(reset))
+        if k < 0:
+            check(k, "crb_profile_kernels")
+        return {self.PROFILE_KINDS[i]: (ms[i], br[i]) for i in range(k)}
+
+
+def fadd_peak(stream=None):
+    """Measured FP32 adds per second."""
+    a = ctypes.c_double()
+    check(_lib.load().crb_fadd_peak(ctypes.byref(a), _stream(stream)), "crb_fadd_peak")
+    return a.value
+
 
 def alu_peak(stream=None):
     """Measured FP32 min/max operations per second: (2-input form, 3-input form)."""

@@ -66,6 +66,15 @@ constexpr size_t kReplaceSmem = crb::ReplaceLayout<kRW, kRH>::bytes;
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
+// profiling kinds (crb_profile_kernels order); kinds below kProfReplace0 are detection
+enum ProfKind {
+  kPBound, kPNeed, kPS, kPSp, kPM3need, kPM3, kPCand, kPGrow, kPCellList, kPTileDetect,  // detection
+  kPRep, kPMask, kPTileReplace,                                                      // replacement
+  kPWork,                                                                             // work counters
+  kProfKinds
+};
+constexpr int kProfReplace0 = kPRep;
+
 // crb_clean_batch_host: staging slots and chunks per call
 constexpr int kStageSlots = 4, kStageChunks = 8;
 // descriptor buffers per context
@@ -167,9 +176,9 @@ struct crb_ctx {
 
   // profiling: event pairs around launches, by kernel kind (0 detect, 1 replace)
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[2];
-  double prof_ms[2] = {0, 0};
-  int prof_n[2] = {0, 0};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[kProfKinds];
+  double prof_ms[kProfKinds] = {};
+  int prof_n[kProfKinds] = {};
 };
 
 namespace {
@@ -345,24 +354,35 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
     for (int k = 1; k <= P.niter; ++k) {
       uint32_t* cls = P.cells[k & 1];
       uint32_t* cls_next = (k < P.niter) ? P.cells[(k + 1) & 1] : nullptr;
-      timed(c, 0, stream, [&] {
-        const unsigned int dense_from = unsigned(std::min<long long>(P.ncells / 4 + 1, 0xffffffffLL));
-        const uint32_t* kcls = (k == 1) ? nullptr : cls;
-        const int gcol = grid(kQNeed, (P.nunits + crb::kColWarps - 1) / crb::kColWarps);
-        if (k >= 2)
+      const unsigned int dense_from = unsigned(std::min<long long>(P.ncells / 4 + 1, 0xffffffffLL));
+      const uint32_t* kcls = (k == 1) ? nullptr : cls;
+      const int gcol = grid(kQNeed, (P.nunits + crb::kColWarps - 1) / crb::kColWarps);
+      if (k >= 2)
+        timed(c, kPCellList, stream, [&] {
           crb::cell_list_kernel<<<grid(kQCellList, (P.ncells + 255) / 256), 256, 0, stream>>>(P.ncells, cls, P.Q);
+        });
+      timed(c, kPBound, stream, [&] {
         crb::bound_kernel<<<grid(kQBound, P.nblocks), 128, 0, stream>>>(c->d_frames, P.n, P.nblocks, c->p, k, P.Q,
                                                                         kcls, dense_from);
         if (k >= 2)
           crb::bound_list_kernel<<<gq * c->occ_q[kQBoundList], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p,
                                                                                 dense_from);
+      });
+      timed(c, kPNeed, stream, [&] {
         crb::need_kernel<<<gcol, crb::kColWarps * 32, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, kcls);
-        crb::s_kernel<<<gq * c->occ_q[kQS], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k);
-        crb::sp_kernel<<<gq * c->occ_q[kQSp], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
+      });
+      timed(c, kPS, stream, [&] { crb::s_kernel<<<gq * c->occ_q[kQS], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k); });
+      timed(c, kPSp, stream,
+            [&] { crb::sp_kernel<<<gq * c->occ_q[kQSp], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p); });
+      timed(c, kPM3need, stream, [&] {
         crb::m3need_kernel<<<gcol, crb::kColWarps * 32, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, kcls);
-        crb::m3_kernel<<<gq * c->occ_q[kQM3], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k);
+      });
+      timed(c, kPM3, stream, [&] { crb::m3_kernel<<<gq * c->occ_q[kQM3], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k); });
+      timed(c, kPCand, stream, [&] {
         crb::cand_test_kernel<<<gq * c->occ_q[kQCand], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
         crb::cand_full_kernel<<<gq * c->occ_q[kQCandFull], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
+      });
+      timed(c, kPGrow, stream, [&] {
         if (k == 1)
           crb::grow_kernel<false><<<gq * c->occ_q[kQGrow], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
         else
@@ -370,7 +390,7 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
       });
       // the classes of iteration k+1 start at zero (those of iteration k-1 were read by now)
       if (k >= 3 && cls_next) CRB_CUDA(cudaMemsetAsync(cls_next, 0, cells_bytes, stream));
-      timed(c, 1, stream, [&] {
+      timed(c, kPRep, stream, [&] {
         if (k == 1)
           crb::flagq_kernel<<<grid(kQFlagq, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q);
         else
@@ -379,9 +399,12 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
                                                                                 cls_next);
         if (k >= 2)
           crb::rep_write_kernel<<<gq * c->occ_q[kQRepWrite], 256, 0, stream>>>(c->d_frames, P.n, P.Q, cls_next, 1);
-        if (k == P.niter) crb::mask_kernel<<<grid(kQFlagq, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks);
       });
-      crb::queue_work_kernel<<<1, 32, 0, stream>>>(c->d_frames, P.Q, k, P.npix);
+      if (k == P.niter)
+        timed(c, kPMask, stream, [&] {
+          crb::mask_kernel<<<grid(kQFlagq, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks);
+        });
+      timed(c, kPWork, stream, [&] { crb::queue_work_kernel<<<1, 32, 0, stream>>>(c->d_frames, P.Q, k, P.npix); });
     }
     CRB_CUDA(cudaGetLastError());
     return CRB_OK;
@@ -397,17 +420,17 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
   }
   for (int k = 1; k <= P.niter; ++k) {
     if (P.fuse && k >= 2) {  // replacement of iteration k-1 fused in front of detection k
-      timed(c, 0, stream, [&] {
+      timed(c, kPTileDetect, stream, [&] {
         ds.fn_fused<<<P.fgrid, crb::kThreads, ds.smem_fused, stream>>>(c->d_frames, P.n, P.tiles, c->p, k, P.niter);
       });
     } else {
-      timed(c, 0, stream, [&] {
+      timed(c, kPTileDetect, stream, [&] {
         (P.maps ? ds.fn_maps : ds.fn)<<<P.dgrid, crb::kThreads, ds.smem, stream>>>(c->d_frames, P.n, P.tiles, c->p, k,
                                                                                      P.niter);
       });
     }
     if (!P.fuse || k == P.niter) {
-      timed(c, 1, stream, [&] {
+      timed(c, kPTileReplace, stream, [&] {
         kReplace<<<P.rgrid, crb::kThreads, kReplaceSmem, stream>>>(c->d_frames, P.n, P.rtiles, k, P.niter,
                                                                    k <= 2 ? 1 : 0);
       });
@@ -1029,10 +1052,10 @@ int crb_last_work(crb_ctx* c, long long* out, int max_iter) {
   return read_counters(c, out, max_iter, 2, crb::kWork);
 }
 
-int crb_profile_read(crb_ctx* c, double* detect_ms, int* detect_launches, double* replace_ms,
-                     int* replace_launches, int reset) {
-  if (!c || !c->opt.profile) return fail(CRB_EINVAL, "profiling is off for this context");
-  for (int kind = 0; kind < 2; ++kind) {
+namespace {
+// Folds the finished event pairs of every kind into the totals.
+int profile_collect(crb_ctx* c) {
+  for (int kind = 0; kind < kProfKinds; ++kind) {
     for (auto& pr : c->pending[kind]) {
       float ms = 0.f;
       CRB_CUDA(cudaEventSynchronize(pr.second));
@@ -1044,15 +1067,89 @@ int crb_profile_read(crb_ctx* c, double* detect_ms, int* detect_launches, double
     }
     c->pending[kind].clear();
   }
-  if (detect_ms) *detect_ms = c->prof_ms[0];
-  if (detect_launches) *detect_launches = c->prof_n[0];
-  if (replace_ms) *replace_ms = c->prof_ms[1];
-  if (replace_launches) *replace_launches = c->prof_n[1];
-  if (reset) {
-    c->prof_ms[0] = c->prof_ms[1] = 0;
-    c->prof_n[0] = c->prof_n[1] = 0;
-  }
   return CRB_OK;
+}
+}  // namespace
+
+int crb_profile_read(crb_ctx* c, double* detect_ms, int* detect_launches, double* replace_ms,
+                     int* replace_launches, int reset) {
+  if (!c || !c->opt.profile) return fail(CRB_EINVAL, "profiling is off for this context");
+  const int rc = profile_collect(c);
+  if (rc) return rc;
+  double dm = 0, rm = 0;
+  int dn = 0, rn = 0;
+  for (int kind = 0; kind < kPWork; ++kind) {
+    if (kind < kProfReplace0) {
+      dm += c->prof_ms[kind];
+      dn += c->prof_n[kind];
+    } else {
+      rm += c->prof_ms[kind];
+      rn += c->prof_n[kind];
+    }
+  }
+  if (detect_ms) *detect_ms = dm;
+  if (detect_launches) *detect_launches = dn;
+  if (replace_ms) *replace_ms = rm;
+  if (replace_launches) *replace_launches = rn;
+  if (reset)
+    for (int kind = 0; kind < kProfKinds; ++kind) {
+      c->prof_ms[kind] = 0;
+      c->prof_n[kind] = 0;
+    }
+  return CRB_OK;
+}
+
+int crb_profile_kernels(crb_ctx* c, double* ms, int* brackets, int max, int reset) {
+  if (!c || !c->opt.profile || max < 0 || (max > 0 && !ms)) return fail(CRB_EINVAL, "profiling off / bad arguments");
+  const int rc = profile_collect(c);
+  if (rc) return rc;
+  const int k = std::min(max, int(kProfKinds));
+  for (int i = 0; i < k; ++i) {
+    ms[i] = c->prof_ms[i];
+    if (brackets) brackets[i] = c->prof_n[i];
+  }
+  if (reset)
+    for (int kind = 0; kind < kProfKinds; ++kind) {
+      c->prof_ms[kind] = 0;
+      c->prof_n[kind] = 0;
+    }
+  return k;
+}
+
+int crb_fadd_peak(double* ops_per_s, cudaStream_t stream) {
+  int dev = 0, sms = 0;
+  CRB_CUDA(cudaGetDevice(&dev));
+  CRB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  float* buf = nullptr;
+  CRB_CUDA(cudaMalloc(&buf, sizeof(float) * (192 + size_t(sms) * 8 * 256)));
+  std::vector<float> init(192);
+  for (int i = 0; i < 192; ++i) init[size_t(i)] = 1e-3f * float(i + 1);
+  cudaEvent_t a = nullptr, b = nullptr;
+  int rc = CRB_OK;
+  const int blocks = sms * 8, iters = 4096;
+  double best = 0;
+  if (cudaMemcpy(buf, init.data(), sizeof(float) * 192, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+    rc = cuda_fail(cudaGetLastError(), "crb_fadd_peak setup");
+  for (int rep = 0; rep < 4 && rc == CRB_OK; ++rep) {
+    cudaEventRecord(a, stream);
+    crb::fadd_peak_kernel<<<blocks, 256, 0, stream>>>(buf, buf + 192, iters);
+    cudaEventRecord(b, stream);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "crb_fadd_peak");
+      break;
+    }
+    const double ops = double(blocks) * 256 * iters * crb::kPeakChains;
+    if (rep > 0) best = std::max(best, ops / (ms * 1e-3));
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(buf);
+  if (rc == CRB_OK && ops_per_s) *ops_per_s = best;
+  return rc;
 }
 
 int crb_alu_peak(double* ops2_per_s, double* ops3_per_s, cudaStream_t stream) {
