@@ -51,10 +51,11 @@ ALG_BYTES_PER_PIX_ITER = 8.25
 # sums, 4 clips taken as t+|t|, 3 sums, 1 scale = 16) and the two threshold
 # tests (gain*m, +rn^2, L+^2, *gain^2, two scaled thresholds, two compares = 8).
 BOUND_TEST_MINMAX = 6 + 4 + 1
-# DRAM bytes per bound-pass launch (read + write) on the 64-frame batch, from the
-# ncu capture of the current bound kernel on three 4096x4096 frames, scaled by
-# the tested pixels (see profiles/bound_kernel_triple4096.md); None when stale.
-BOUND_TRAFFIC = None
+# DRAM bytes (read + write) of the bound pass per step and per input pixel: the
+# ncu capture of all its launches of one step on three 4096x4096 frames of the
+# batch mix (690.4 MB for 50.3 Mpix; the summary is kept with the profiles),
+# applied to the workload's pixels; None once the kernel changes.
+BOUND_TRAFFIC_PER_PIXEL = 690445312 / 50331648
 # Algorithmic FP32 operations per unit of each kernel kind: (min/max, other).
 KIND_OPS = {
     "bound": (BOUND_TEST_MINMAX, 24),
@@ -469,7 +470,9 @@ def main():
         achieved = ops / (per_step[dom] * 1e-3) / 1e12
         peak = (mm + fp) / (mm / ops2 + fp / fadd) / 1e12  # the kernel's op mix at the measured issue rates
         roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                    "frac": achieved / peak, "traffic": BOUND_TRAFFIC if dom == "bound" else None,
+                    "frac": achieved / peak,
+                    "traffic": BOUND_TRAFFIC_PER_PIXEL * npix if dom == "bound" and BOUND_TRAFFIC_PER_PIXEL else None,
+                    "traffic_is": "DRAM bytes of the kernel's launches per step (ncu capture scaled by pixels)",
                     "peak_source": f"measured: crb_alu_peak min/max {ops2 / 1e12:.2f} T/s and crb_fadd_peak "
                                    f"{fadd / 1e12:.2f} T/s, weighted by the kernel's {mm} min/max + {fp} other FP32 "
                                    "operations per unit",
