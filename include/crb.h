@@ -182,9 +182,8 @@ int crb_last_work(crb_ctx* ctx, long long* out, int max_iter);
 
 /* Kernel launches the last crb_clean / crb_clean_batch / crb_iterate enqueued
  * (memsets and copies not counted; a graph replay counts its kernels). The
- * queue pipeline launches 2 descriptor uploads, 12 kernels in iteration 1, 15
- * in each later one (including the form of the bound pass that the device-side
- * size test skips) and the mask kernel; the fused tile pipeline 1 upload and
+ * queue pipeline launches 2 descriptor uploads, 12 kernels in iteration 1, 14
+ * in each later one and the mask kernel; the fused tile pipeline 1 upload and
  * niter + 1 kernels. -1 for a NULL context. */
 int crb_last_launches(const crb_ctx* ctx);
 

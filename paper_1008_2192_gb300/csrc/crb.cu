@@ -204,13 +204,14 @@ int init_ctx(crb_ctx* c) {
         reinterpret_cast<const void*>(crb::s_kernel),           reinterpret_cast<const void*>(crb::sp_kernel),
         reinterpret_cast<const void*>(crb::m3need_kernel),      reinterpret_cast<const void*>(crb::m3_kernel),
         reinterpret_cast<const void*>(crb::cand_test_kernel),   reinterpret_cast<const void*>(crb::rep_compute_kernel),
-        reinterpret_cast<const void*>(crb::bound_list_kernel),  reinterpret_cast<const void*>(crb::rq_kernel),
-        reinterpret_cast<const void*>(crb::rep_write_kernel),   reinterpret_cast<const void*>(crb::cell_list_kernel),
+        reinterpret_cast<const void*>(crb::bound_sparse_kernel),  reinterpret_cast<const void*>(crb::rq_kernel),
+        reinterpret_cast<const void*>(crb::rep_write_kernel),   reinterpret_cast<const void*>(crb::d2_kernel),
         reinterpret_cast<const void*>(crb::cand_full_kernel),   reinterpret_cast<const void*>(crb::grow_kernel<true>),
         reinterpret_cast<const void*>(crb::flagq_kernel)};
     for (int i = 0; i < kQKernels; ++i) {
       int o = 0;
-      const int threads = i == kQBound ? 128 : (i == kQNeed || i == kQM3need) ? crb::kColWarps * 32 : 256;
+      const int threads =
+          i == kQBound ? 128 : (i == kQNeed || i == kQM3need || i == kQCellList) ? crb::kColWarps * 32 : 256;
       CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[i], threads, 0));
       c->occ_q[i] = o > 0 ? o : 1;
     }
@@ -329,6 +330,8 @@ struct Plan {
   long long ncells = 0;             // queue pipeline: cells (one word x kCH rows)
   long long nunits = 0;             // queue pipeline: strips of 32 words x kSH rows
   uint32_t* cells[2] = {nullptr, nullptr};  // cell classes for even / odd iterations
+  char* chg[2] = {nullptr, nullptr};         // changed-pixel planes (all frames) for even / odd iterations
+  size_t chg_bytes = 0;
   crb::Queues Q{};
 };
 
@@ -354,19 +357,15 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
     for (int k = 1; k <= P.niter; ++k) {
       uint32_t* cls = P.cells[k & 1];
       uint32_t* cls_next = (k < P.niter) ? P.cells[(k + 1) & 1] : nullptr;
-      const unsigned int dense_from = unsigned(std::min<long long>(P.ncells / 4 + 1, 0xffffffffLL));
       const uint32_t* kcls = (k == 1) ? nullptr : cls;
       const int gcol = grid(kQNeed, (P.nunits + crb::kColWarps - 1) / crb::kColWarps);
-      if (k >= 2)
-        timed(c, kPCellList, stream, [&] {
-          crb::cell_list_kernel<<<grid(kQCellList, (P.ncells + 255) / 256), 256, 0, stream>>>(P.ncells, cls, P.Q);
-        });
       timed(c, kPBound, stream, [&] {
-        crb::bound_kernel<<<grid(kQBound, P.nblocks), 128, 0, stream>>>(c->d_frames, P.n, P.nblocks, c->p, k, P.Q,
-                                                                        kcls, dense_from);
-        if (k >= 2)
-          crb::bound_list_kernel<<<gq * c->occ_q[kQBoundList], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p,
-                                                                                dense_from);
+        if (k == 1) {
+          crb::bound_kernel<<<grid(kQBound, P.nblocks), 128, 0, stream>>>(c->d_frames, P.n, P.nblocks, c->p);
+        } else {  // the pixels within 2 px of a change, re-tested one by one
+          crb::d2_kernel<<<gcol, crb::kColWarps * 32, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, k);
+          crb::bound_sparse_kernel<<<gq * c->occ_q[kQBoundList], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
+        }
       });
       timed(c, kPNeed, stream, [&] {
         crb::need_kernel<<<gcol, crb::kColWarps * 32, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, kcls);
@@ -388,8 +387,11 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
         else
           crb::grow_kernel<true><<<gq * c->occ_q[kQGrow], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
       });
-      // the classes of iteration k+1 start at zero (those of iteration k-1 were read by now)
-      if (k >= 3 && cls_next) CRB_CUDA(cudaMemsetAsync(cls_next, 0, cells_bytes, stream));
+      // the classes and changed pixels of iteration k+1 start at zero (those of iteration k-1 were read by now)
+      if (k >= 3 && cls_next) {
+        CRB_CUDA(cudaMemsetAsync(cls_next, 0, cells_bytes, stream));
+        CRB_CUDA(cudaMemsetAsync(P.chg[(k + 1) & 1], 0, P.chg_bytes, stream));
+      }
       timed(c, kPRep, stream, [&] {
         if (k == 1)
           crb::flagq_kernel<<<grid(kQFlagq, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q);
@@ -398,7 +400,8 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
         crb::rep_compute_kernel<<<gq * c->occ_q[kQRepCompute], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k,
                                                                                 cls_next);
         if (k >= 2)
-          crb::rep_write_kernel<<<gq * c->occ_q[kQRepWrite], 256, 0, stream>>>(c->d_frames, P.n, P.Q, cls_next, 1);
+          crb::rep_write_kernel<<<gq * c->occ_q[kQRepWrite], 256, 0, stream>>>(c->d_frames, P.n, P.Q, cls_next,
+                                                                              k + 1, 1);
       });
       if (k == P.niter)
         timed(c, kPMask, stream, [&] {
@@ -441,10 +444,10 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
 }
 
 // Queue pipeline: workspace = [queue counters | per frame: bit planes M, rq, fb |
-// cell classes x 2] (zeroed at the start of a call) then [per frame: bit planes
-// hot, act, nsp, test, sval, m3val; maps S, N, S', M3] then [queues q0, q1, q2
-// (a pixel index per pixel or a word entry per word), fresh, fbl (a pixel index
-// per pixel) | the list of class-4 cells].
+// cell classes x 2 | changed-pixel planes x 2] (zeroed at the start of a call)
+// then [per frame: bit planes hot, act, nsp, test, sval, m3val; maps S, N, S',
+// M3] then [queues q0, q1, q2 (a pixel index per pixel or a word entry per
+// word), fresh, fbl (a pixel index per pixel)].
 int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Plan& P) {
   const int n = int(specs.size());
   long long npix = 0, nblocks = 0, ncells = 0, nwords = 0;
@@ -463,6 +466,15 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
   }
   const size_t off_cells = total;
   total += 2 * align256(size_t(ncells) * 4);
+  // changed-pixel planes, one region per parity (all frames), zeroed with one memset each
+  std::vector<size_t> off_chg(static_cast<size_t>(n));
+  size_t chg_bytes = 0;
+  for (int i = 0; i < n; ++i) {
+    off_chg[size_t(i)] = chg_bytes;
+    chg_bytes += align256(size_t(specs[size_t(i)].w + 31) / 32 * size_t(specs[size_t(i)].h) * 4);
+  }
+  const size_t off_chg0 = total;
+  total += 2 * chg_bytes;
   const size_t zero_bytes = total;
   for (int i = 0; i < n; ++i) {
     const auto& s = specs[size_t(i)];
@@ -473,9 +485,9 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
   }
   // q0..q2 hold a pixel index per pixel or a word entry (8 bytes) per word
   const size_t qbytes = align256(std::max(size_t(npix) * 4, size_t(nwords) * 8));
-  const size_t fbytes = align256(size_t(npix) * 4), lbytes = align256(size_t(ncells) * 4);
+  const size_t fbytes = align256(size_t(npix) * 4);
   const size_t off_q = total;
-  total += 3 * qbytes + 2 * fbytes + lbytes;
+  total += 3 * qbytes + 2 * fbytes;
   const int nit = niter > 0 ? niter : 1;
   const int ncounters = (2 + crb::kWork) * nit * n;
   const size_t tab_n = size_t(npix >> crb::kTabShift) + 1;
@@ -500,6 +512,8 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
     f.bits_a = f.bits_b = reinterpret_cast<uint32_t*>(pz);  // one plane, updated in place
     f.rq = reinterpret_cast<uint32_t*>(pz + plane);
     f.fb = reinterpret_cast<uint32_t*>(pz + 2 * plane);
+    f.chg[0] = reinterpret_cast<uint32_t*>(ws + off_chg0 + off_chg[size_t(i)]);
+    f.chg[1] = reinterpret_cast<uint32_t*>(ws + off_chg0 + chg_bytes + off_chg[size_t(i)]);
     f.hot = reinterpret_cast<uint32_t*>(pb);
     f.act = reinterpret_cast<uint32_t*>(pb + plane);
     f.nsp = reinterpret_cast<uint32_t*>(pb + 2 * plane);
@@ -566,7 +580,9 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
   P.Q.q2 = reinterpret_cast<uint32_t*>(ws + off_q + 2 * qbytes);
   P.Q.fresh = reinterpret_cast<uint32_t*>(ws + off_q + 3 * qbytes);
   P.Q.fbl = reinterpret_cast<uint32_t*>(ws + off_q + 3 * qbytes + fbytes);
-  P.Q.l2 = reinterpret_cast<uint32_t*>(ws + off_q + 3 * qbytes + 2 * fbytes);
+  P.chg[0] = ws + off_chg0;
+  P.chg[1] = ws + off_chg0 + chg_bytes;
+  P.chg_bytes = chg_bytes;
   return CRB_OK;
 }
 
@@ -660,8 +676,8 @@ int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
   // the launches of this upload and of enqueue_work for this plan (memsets and copies not counted)
   if (P.niter == 0)
     c->last_launches = 1;
-  else if (P.queue)  // 2 uploads; iteration 1: 12 kernels, later ones 15, plus the mask
-    c->last_launches = 2 + 12 + 15 * (P.niter - 1) + 1;
+  else if (P.queue)  // 2 uploads; iteration 1: 12 kernels, later ones 14, plus the mask
+    c->last_launches = 2 + 12 + 14 * (P.niter - 1) + 1;
   else
     c->last_launches = 1 + (P.fuse ? P.niter + 1 : 2 * P.niter) + c->mprev_frames;
   return CRB_OK;

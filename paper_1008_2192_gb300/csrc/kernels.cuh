@@ -54,6 +54,7 @@ struct Frame {
   uint32_t *hot, *act, *nsp, *test;
   uint32_t *sval, *m3val;  // positions whose mapS/mapN, mapM3 hold the current iteration's values
   uint32_t *rq, *fb;       // queued for replacement; known to have a fully flagged window
+  uint32_t* chg[2];        // pixels the replacement changed, for even / odd next iterations
   float *mapS, *mapN, *mapSp, *mapM3;
   long long pix0;  // first global pixel index of this frame
   long long blk0;  // first word block (kBW words x kBH rows) of this frame

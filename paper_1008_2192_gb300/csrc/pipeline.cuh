@@ -72,14 +72,16 @@ enum : int {
   kNRep = 4,    // replacement queue
   kNFresh = 5,  // new flags of this iteration
   kNFb = 6,     // pixels with a fully flagged window (kept over the iterations)
-  kNL2 = 7,     // cells within 2 px of a change
+  kNL2 = 7,     // (unused)
   kNPass = 8,   // candidates (passed the objlim test)
   kNAmb = 9,    // tests the column-median bounds leave open
   kNSpx = 10,   // positions in QS, QSP, QM3, QT (work counters)
   kNSPpx = 11,
   kNM3px = 12,
   kNTpx = 13,
-  kNCount = 14
+  kNB = 14,     // pixels to re-test in the bound pass (word entries)
+  kNBpx = 15,
+  kNCount = 16
 };
 
 // QS, QSP, QM3 and QT hold word entries: (global word index, mask of the
@@ -89,10 +91,9 @@ enum : int {
 struct Queues {
   uint32_t* q0;     // QS, then QM3, then the candidates, then the replacement values (as float)
   uint32_t* q1;     // QSP, then the open tests, then the replacement queue
-  uint32_t* q2;     // QT
+  uint32_t* q2;     // the bound pass's pixels (iterations >= 2), then QT
   uint32_t* fresh;  // new flags
   uint32_t* fbl;    // fully flagged windows
-  uint32_t* l2;     // cells of class 4
   unsigned int* n;  // kNCount counters
   const uint32_t* ftab;  // frame of global pixel t << kTabShift
 };
@@ -173,94 +174,15 @@ __device__ __forceinline__ void group_append(uint32_t g, uint32_t* q, unsigned i
 // ---------------------------------------------------------------------------------------------
 // bound: per pixel L+ and the lower bound of m5 (smallest of the five column
 // medians) -> bits of S+ > sigclip and S+ > min(sigclip, sigfrac*sigclip) (see detect_tile
-// for the bound and its margin). One warp walks down one 32-pixel word column,
-// two rows per step, keeping the rows of its column (and of the two halo
-// columns on each side, held by lanes 0-3) in registers.
+// for the bound and its margin). In iteration 1 a warp walks down a strip of
+// two word columns, two rows per step, keeping the rows of its columns (and of
+// the halo columns, held by lanes 0-3) in registers.
 //
 // Sliding column medians: the windows of rows y and y+1 share the four values
 // of rows y-1..y+2. With c1 <= c2 the two middle values of those four, the
 // median of the four and one more value e is min(max(e, c1), c2).
 
 __device__ __forceinline__ float clamp_med(float e, float c1, float c2) { return fminf(fmaxf(e, c1), c2); }
-
-// hot/act bits of word column wc, rows [y0, y1), of frame f (whole warp);
-// copy != nullptr also copies those pixels of J there (iteration 1: I0 into the
-// image buffer).
-__device__ __forceinline__ void bound_span(const Frame& f, const float* __restrict__ J, int wc, int y0, int y1,
-                                           float chot, float clow, float* __restrict__ copy) {
-  const int lane = threadIdx.x & 31;
-  // halo routing: src lane of the column median at x-2 (lanes 0,1) or x+2 (30,31); at x-1 (0) or x+1 (31)
-  const int srcA = lane == 0 ? 0 : lane == 1 ? 1 : lane == 30 ? 2 : 3;
-  const int srcB = lane == 0 ? 1 : 2;
-  const int w = f.w, h = f.h;
-  const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
-  const int x0 = wc * 32, x = x0 + lane;
-  const int col = min(x, w - 1);
-  const int hx = lane < 2 ? x0 - 2 + lane : x0 + 30 + lane;  // halo columns (lanes 0-3)
-  const int hcol = clampi(hx, 0, w - 1);
-  const float* __restrict__ Jc = J + col;
-  const float* __restrict__ Jh = J + hcol;
-  auto rowp = [&](int yy) { return size_t(clampi(yy, 0, h - 1)) * size_t(w); };
-  // rows y0-2 .. y0+1 of the column (a..d) and of the halo column
-  float a = __ldg(Jc + rowp(y0 - 2)), bq = __ldg(Jc + rowp(y0 - 1));
-  float cq = __ldg(Jc + rowp(y0)), d = __ldg(Jc + rowp(y0 + 1));
-  float ha = __ldg(Jh + rowp(y0 - 2)), hb = __ldg(Jh + rowp(y0 - 1));
-  float hc = __ldg(Jh + rowp(y0)), hd = __ldg(Jh + rowp(y0 + 1));
-  for (int y = y0; y < y1; y += 2) {
-    // next two rows y+2, y+3
-    const float e = __ldg(Jc + rowp(y + 2)), g = __ldg(Jc + rowp(y + 3));
-    const float he = __ldg(Jh + rowp(y + 2)), hg = __ldg(Jh + rowp(y + 3));
-    // core rows y-1..y+2 = (bq, cq) and (d, e): middle two values
-    float cm0, cm1, hcm0, hcm1;
-    {
-      const float l1 = fminf(bq, cq), h1 = fmaxf(bq, cq), l2 = fminf(d, e), h2 = fmaxf(d, e);
-      const float u = fmaxf(l1, l2), v = fminf(h1, h2);
-      const float c1 = fminf(u, v), c2 = fmaxf(u, v);
-      cm0 = clamp_med(a, c1, c2);  // rows y-2..y+2
-      cm1 = clamp_med(g, c1, c2);  // rows y-1..y+3
-      const float hl1 = fminf(hb, hc), hh1 = fmaxf(hb, hc), hl2 = fminf(hd, he), hh2 = fmaxf(hd, he);
-      const float hu = fmaxf(hl1, hl2), hv = fminf(hh1, hh2);
-      const float hc1 = fminf(hu, hv), hc2 = fmaxf(hu, hv);
-      hcm0 = clamp_med(ha, hc1, hc2);
-      hcm1 = clamp_med(hg, hc1, hc2);
-    }
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const int yy = y + s;
-      if (yy >= y1) break;
-      const float cm = s ? cm1 : cm0, hcm = s ? hcm1 : hcm0;
-      float m2 = __shfl_up_sync(0xffffffffu, cm, 2), m1 = __shfl_up_sync(0xffffffffu, cm, 1);
-      float p1 = __shfl_down_sync(0xffffffffu, cm, 1), p2 = __shfl_down_sync(0xffffffffu, cm, 2);
-      const float hA = __shfl_sync(0xffffffffu, hcm, srcA), hB = __shfl_sync(0xffffffffu, hcm, srcB);
-      if (lane < 2) m2 = hA;
-      if (lane == 0) m1 = hB;
-      if (lane >= 30) p2 = hA;
-      if (lane == 31) p1 = hB;
-      const float mlow = min3f(min3f(m2, m1, cm), p1, p2);
-      // L+: the pixel, its column neighbours and its row neighbours (lanes, halo at the ends)
-      const float cc = s ? d : cq, up = s ? cq : bq, dn = s ? e : d;
-      const float hcc = s ? hd : hc;
-      const float hL = __shfl_sync(0xffffffffu, hcc, lane == 0 ? 1 : 2);
-      float left = __shfl_up_sync(0xffffffffu, cc, 1), right = __shfl_down_sync(0xffffffffu, cc, 1);
-      if (lane == 0) left = hL;
-      if (lane == 31) right = hL;
-      const float lp = lplus(cc, up, dn, left, right);
-      if (copy && x < w) copy[size_t(yy) * w + x] = cc;
-      const float den = gain * (mlow > 0.f ? mlow : 0.f) + rn2;
-      const float lhs = lp * lp * g2;
-      const bool ok = x < w;
-      const unsigned act = __ballot_sync(0xffffffffu, ok && lhs > clow * den);
-      const unsigned hot = __ballot_sync(0xffffffffu, ok && lhs > chot * den);
-      if (lane == 0) {
-        const size_t o = size_t(yy) * f.wpr + wc;
-        f.act[o] = act;
-        f.hot[o] = hot;
-      }
-    }
-    a = cq; bq = d; cq = e; d = g;
-    ha = hc; hb = hd; hc = he; hd = hg;
-  }
-}
 
 // thresholds of the bound test: S+ > sigclip (hot), S+ > min(sigclip, sigfrac*sigclip) (act)
 __device__ __forceinline__ void bound_consts(const Params& p, float& chot, float& clow) {
@@ -390,15 +312,12 @@ __device__ __forceinline__ void bound_span2(const Frame& f, const float* __restr
   }
 }
 
-// bound_kernel: pairs of word columns of every frame, blocks of kBW words x
-// kBH rows, 4 warps of 2 words. Iteration 1 (cls == nullptr): every row, and
-// the image buffer starts as a copy of I0. Iteration >= 2: the runs of cell
-// rows in which either word's cell has class 4; runs only when at least
-// `dense_from` cells are listed (bound_list_kernel runs otherwise).
+// bound_kernel (iteration 1): pairs of word columns of every frame, blocks of
+// kBW words x kBH rows, 4 warps of 2 words; the image buffer starts as a copy of
+// I0. Later iterations re-test only the pixels within 2 px of a change
+// (d2_kernel, bound_sparse_kernel).
 __global__ void __launch_bounds__(128) bound_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
-                                                    Params p, int k, Queues Q, const uint32_t* __restrict__ cls,
-                                                    unsigned int dense_from) {
-  if (cls && Q.n[kNL2] < dense_from) return;  // the list form runs
+                                                    Params p) {
   const int warp = threadIdx.x >> 5;
   float chot, clow;
   bound_consts(p, chot, clow);
@@ -409,44 +328,8 @@ __global__ void __launch_bounds__(128) bound_kernel(const Frame* __restrict__ fr
     const int bys = int(lb / f.bx), bxs = int(lb - (long long)bys * f.bx);
     const int wc = bxs * kBW + 2 * warp;
     if (wc >= f.wpr) continue;  // whole warp
-    const int y0 = bys * kBH, y1 = min(y0 + kBH, f.h);
-    const float* J = qsrc(f, k);
-    if (!cls) {
-      bound_span2(f, J, wc, y0, y1, chot, clow, k == 1 ? f.out_clean : nullptr);
-      continue;
-    }
-    auto dirty = [&](int cy) {
-      const uint32_t* c = cls + f.cell0 + (long long)cy * f.wpr + wc;
-      return c[0] >= 4u || (wc + 1 < f.wpr && c[1] >= 4u);
-    };
-    const int cy1 = (y1 + kCH - 1) / kCH;
-    for (int cy = y0 / kCH; cy < cy1;) {
-      if (!dirty(cy)) {
-        ++cy;
-        continue;
-      }
-      int ce = cy + 1;
-      while (ce < cy1 && dirty(ce)) ++ce;
-      bound_span2(f, J, wc, cy * kCH, min(ce * kCH, f.h), chot, clow, nullptr);
-      cy = ce;
-    }
-  }
-}
-
-// the cells of list l2 (iteration >= 2): one warp per cell
-__global__ void __launch_bounds__(256) bound_list_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
-                                                         Params p, unsigned int dense_from) {
-  const int warp = threadIdx.x >> 5;
-  float chot, clow;
-  bound_consts(p, chot, clow);
-  const unsigned int n = Q.n[kNL2];
-  if (n >= dense_from) return;  // the block form runs
-  for (unsigned int i = blockIdx.x * 8u + warp; i < n; i += gridDim.x * 8u) {
-    const uint32_t c = Q.l2[i];
-    const Frame& f = frames[frame_of_cell(frames, nframes, c)];
-    const uint32_t lc = c - uint32_t(f.cell0);
-    const int cy = int(lc / uint32_t(f.wpr)), wc = int(lc - uint32_t(cy) * uint32_t(f.wpr));
-    bound_span(f, f.out_clean, wc, cy * kCH, min(cy * kCH + kCH, f.h), chot, clow, nullptr);
+    const int y0 = bys * kBH;
+    bound_span2(f, f.img, wc, y0, min(y0 + kBH, f.h), chot, clow, f.out_clean);
   }
 }
 
@@ -753,17 +636,57 @@ __global__ void __launch_bounds__(kColWarps * 32) m3need_kernel(const Frame* __r
   }
 }
 
-// cell_list_kernel (iteration >= 2): the cells of class 4 (within 2 px of a
-// change) -> l2, for the bound pass.
-__global__ void __launch_bounds__(256) cell_list_kernel(long long ncells, const uint32_t* __restrict__ cls, Queues Q) {
-  __shared__ int ws[kThreads / 32 + 1];
-  __shared__ unsigned int sbase[1];
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long c0 = (long long)blockIdx.x * blockDim.x; c0 < ncells; c0 += stride) {  // whole blocks
-    const long long c = c0 + threadIdx.x;
-    const bool put[1] = {c < ncells && cls[c] >= 4u};
-    uint32_t* const lists[1] = {Q.l2};
-    block_append<1>(put, uint32_t(c), lists, Q.n + kNL2, ws, sbase);
+// d2_kernel (iteration >= 2): the pixels within 2 px of a change (the
+// changed-pixel plane of this iteration, dilated by 5 x 5 within the frame) ->
+// word entries of the pixels the bound pass re-tests (q2). Column kernel: rows
+// y0-2 .. y0+kSH+1 feed the five-row window.
+__global__ void __launch_bounds__(kColWarps * 32) d2_kernel(const Frame* __restrict__ frames, int nframes,
+                                                            long long nunits, Queues Q, int k) {
+  __shared__ ColWords sw;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (long long u = (long long)blockIdx.x * kColWarps + warp; u < nunits; u += (long long)gridDim.x * kColWarps) {
+    const Frame& f = frames[frame_of_unit(frames, nframes, u)];
+    const uint32_t* __restrict__ chg = f.chg[k & 1];
+    const long long lu = u - f.u0;
+    const int uy = int(lu / f.ugx), ux = int(lu - (long long)uy * f.ugx);
+    const int wc0 = ux * 32, y0 = uy * kSH, wc = wc0 + lane;
+    const bool inw = wc < f.wpr;
+    const int hw = lane == 0 ? wc0 - 1 : wc0 + 32;
+    const bool hin = (lane == 0 || lane == 31) && hw >= 0 && hw < f.wpr;
+    const uint32_t fmask = inw ? frame_word(wc, f.w) : 0u;
+    uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, e0 = 0, e1 = 0, e2 = 0, e3 = 0, e4 = 0;
+    unsigned int ents[2] = {0u, 0u}, pix[2] = {0u, 0u};
+    for (int rc = y0 - 2; rc < y0 + kSH + 2; rc += 8) {  // 36 rows: chunks of 8, the last one partly past the end
+      uint32_t L[8], G[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = rc + i;
+        const bool rin = r >= 0 && r < f.h && r < y0 + kSH + 2;
+        const size_t ro = size_t(rin ? r : 0) * f.wpr;
+        L[i] = (rin && inw) ? chg[ro + wc] : 0u;
+        G[i] = (rin && hin) ? chg[ro + hw] : 0u;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        c0 = c1; c1 = c2; c2 = c3; c3 = c4; c4 = L[i];
+        e0 = e1; e1 = e2; e2 = e3; e3 = e4; e4 = G[i];
+        const int yo = rc + i - 2;
+        if (yo < y0 || yo >= y0 + kSH) continue;  // whole warp
+        const uint32_t v = c0 | c1 | c2 | c3 | c4, gv = e0 | e1 | e2 | e3 | e4;
+        uint32_t left = __shfl_up_sync(0xffffffffu, v, 1), right = __shfl_down_sync(0xffffffffu, v, 1);
+        const uint32_t gl = __shfl_sync(0xffffffffu, gv, 0), gr = __shfl_sync(0xffffffffu, gv, 31);
+        if (lane == 0) left = gl;
+        if (lane == 31) right = gr;
+        const uint32_t d2 = (yo < f.h) ? (hdil<2>(left, v, right) & fmask) : 0u;
+        sw.w[warp][yo - y0][0][lane] = d2;
+        col_count(d2, ents[0], pix[0]);
+      }
+    }
+    unsigned int base[2];
+    col_reserve(ents, pix, Q.n + kNB, Q.n + kNB, Q.n + kNBpx, Q.n + kNBpx, base);
+    __syncwarp();
+    col_write(sw, warp, 0, f, wc0, y0, base[0], reinterpret_cast<uint2*>(Q.q2));
+    __syncwarp();
   }
 }
 
@@ -935,6 +858,55 @@ __global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frame
                  float v[9];
                  load_window<1>(qsrc(f, k), x, y, f.w, f.h, v);
                  f.mapM3[size_t(y) * f.w + x] = sel_med9(v);
+               });
+}
+
+// bound_sparse_kernel (iteration >= 2): the bound test of each listed pixel
+// from its own 5x5 window of J (five column medians, their minimum, L+): the
+// same values as the sliding form. The warp merges its results per word and
+// writes them with one AND and one OR per plane and word (the words' other
+// bits are untouched, so warps sharing a word do not interfere).
+__global__ void __launch_bounds__(256) bound_sparse_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
+                                                           Params p) {
+  __shared__ ExpandSmem sm;
+  float chot, clow;
+  bound_consts(p, chot, clow);
+  const int lane = threadIdx.x & 31;
+  expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q2), Q.n[kNB], sm,
+               [&](bool valid, int fi, int x, int y) {
+                 bool hot = false, act = false;
+                 unsigned long long key = ~0ull;
+                 if (valid) {
+                   const Frame& f = frames[fi];
+                   float v[25];
+                   load_window<2>(f.out_clean, x, y, f.w, f.h, v);
+                   float mlow = INFINITY;
+#pragma unroll
+                   for (int dx = 0; dx < 5; ++dx) {
+                     const float col[5] = {v[dx], v[5 + dx], v[10 + dx], v[15 + dx], v[20 + dx]};
+                     mlow = fminf(mlow, sel_med5(col));
+                   }
+                   const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
+                   const float lp = lplus(v[12], v[7], v[17], v[11], v[13]);
+                   const float den = gain * (mlow > 0.f ? mlow : 0.f) + rn2;
+                   const float lhs = lp * lp * g2;
+                   act = lhs > clow * den;
+                   hot = lhs > chot * den;
+                   key = (static_cast<unsigned long long>(fi) << 40) | (size_t(y) * f.wpr + (x >> 5));
+                 }
+                 const unsigned grp = __match_any_sync(0xffffffffu, key);
+                 const uint32_t bit = valid ? 1u << (x & 31) : 0u;
+                 const uint32_t m = __reduce_or_sync(grp, bit);
+                 const uint32_t hb = __reduce_or_sync(grp, hot ? bit : 0u);
+                 const uint32_t ab = __reduce_or_sync(grp, act ? bit : 0u);
+                 if (valid && lane == __ffs(grp) - 1) {
+                   const Frame& f = frames[fi];
+                   const size_t wo = size_t(y) * f.wpr + (x >> 5);
+                   atomicAnd(f.hot + wo, ~(m & ~hb));
+                   atomicOr(f.hot + wo, hb);
+                   atomicAnd(f.act + wo, ~(m & ~ab));
+                   atomicOr(f.act + wo, ab);
+                 }
                });
 }
 
@@ -1261,10 +1233,12 @@ __global__ void __launch_bounds__(256) rq_kernel(const Frame* __restrict__ frame
   }
 }
 
-// Marks, in the cell classes `cls`, the cells reached by a change at (x, y):
-// class 4 within 2 px, 3 within 4 px, 2 within 6 px (distance to the cell's
-// rectangle, Chebyshev).
-__device__ __forceinline__ void mark_change(const Frame& f, int x, int y, uint32_t* cls) {
+// Marks a change at (x, y) for iteration knext: its bit in the changed-pixel
+// plane, and in the cell classes `cls` the cells it reaches: class 4 within
+// 2 px, 3 within 4 px, 2 within 6 px (distance to the cell's rectangle,
+// Chebyshev).
+__device__ __forceinline__ void mark_change(const Frame& f, int x, int y, uint32_t* cls, int knext) {
+  atomicOr(f.chg[knext & 1] + size_t(y) * f.wpr + (x >> 5), 1u << (x & 31));
   const int cx0 = max(x - 6, 0) >> 5, cx1 = min(x + 6, f.w - 1) >> 5;
   const int cy0 = max(y - 6, 0) / kCH, cy1 = min(y + 6, f.h - 1) / kCH;
   for (int cy = cy0; cy <= cy1; ++cy)
@@ -1333,7 +1307,7 @@ __global__ void __launch_bounds__(256) rep_compute_kernel(const Frame* __restric
     if (k == 1) {
       const size_t o = size_t(g - uint32_t(f.pix0));
       f.out_clean[o] = out;
-      if (cls_next && __float_as_uint(out) != __float_as_uint(J[o])) mark_change(f, P.x, P.y, cls_next);
+      if (cls_next && __float_as_uint(out) != __float_as_uint(J[o])) mark_change(f, P.x, P.y, cls_next, k + 1);
     } else {
       vals[i] = out;
     }
@@ -1344,7 +1318,7 @@ __global__ void __launch_bounds__(256) rep_compute_kernel(const Frame* __restric
 // the cells of the next iteration (cls_next, or nothing after the last one).
 // Clears the queued bits.
 __global__ void __launch_bounds__(256) rep_write_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
-                                                        uint32_t* cls_next, int clear_rq) {
+                                                        uint32_t* cls_next, int knext, int clear_rq) {
   const unsigned int n = Q.n[kNRep];
   const float* __restrict__ vals = reinterpret_cast<const float*>(Q.q0);
   for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1355,7 +1329,7 @@ __global__ void __launch_bounds__(256) rep_write_kernel(const Frame* __restrict_
     const float v = vals[i];
     if (__float_as_uint(f.out_clean[o]) != __float_as_uint(v)) {
       f.out_clean[o] = v;
-      if (cls_next) mark_change(f, P.x, P.y, cls_next);
+      if (cls_next) mark_change(f, P.x, P.y, cls_next, knext);
     }
     if (clear_rq) atomicAnd(&f.rq[size_t(P.y) * f.wpr + (P.x >> 5)], ~(1u << (P.x & 31)));
   }
@@ -1397,7 +1371,7 @@ __global__ void __launch_bounds__(256) mask_kernel(const Frame* __restrict__ fra
 
 // Adds the queue lengths of iteration k to the work counters of frame 0 (the
 // totals of the call) and clears the per-iteration counters. Bound tests:
-// `dense` positions in iteration 1, kCH*32 per listed cell after it.
+// `dense` positions in iteration 1, the re-tested pixels after it.
 __global__ void queue_work_kernel(const Frame* __restrict__ frames, Queues Q, int k, long long dense) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     unsigned long long* wk = frames[0].work + kWork * (k - 1);
@@ -1406,7 +1380,7 @@ __global__ void queue_work_kernel(const Frame* __restrict__ frames, Queues Q, in
     wk[2] += Q.n[kNM3px];
     wk[3] += Q.n[kNTpx];
     wk[4] += Q.n[kNAmb];
-    wk[5] += (k == 1) ? (unsigned long long)dense : (unsigned long long)Q.n[kNL2] * (kCH * 32);
+    wk[5] += (k == 1) ? (unsigned long long)dense : (unsigned long long)Q.n[kNBpx];
     for (int i = 0; i < kNCount; ++i)
       if (i != kNFb) Q.n[i] = 0u;
   }
