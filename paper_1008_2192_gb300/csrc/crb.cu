@@ -445,7 +445,7 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
 
 // Queue pipeline: workspace = [queue counters | per frame: bit planes M, rq, fb |
 // cell classes x 2 | changed-pixel planes x 2] (zeroed at the start of a call)
-// then [per frame: bit planes hot, act, nsp, test, sval, m3val; maps S, N, S',
+// then [per frame: bit planes hot, act, nsp, test, sval, m3val, lpz; maps S, N, S',
 // M3] then [queues q0, q1, q2 (a pixel index per pixel or a word entry per
 // word), fresh, fbl (a pixel index per pixel)].
 int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Plan& P) {
@@ -479,7 +479,7 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
   for (int i = 0; i < n; ++i) {
     const auto& s = specs[size_t(i)];
     off_bits[size_t(i)] = total;
-    total += 6 * align256(size_t(s.w + 31) / 32 * size_t(s.h) * 4);
+    total += 7 * align256(size_t(s.w + 31) / 32 * size_t(s.h) * 4);
     off_maps[size_t(i)] = total;
     total += 4 * align256(size_t(s.w) * size_t(s.h) * 4);
   }
@@ -520,6 +520,7 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
     f.test = reinterpret_cast<uint32_t*>(pb + 3 * plane);
     f.sval = reinterpret_cast<uint32_t*>(pb + 4 * plane);
     f.m3val = reinterpret_cast<uint32_t*>(pb + 5 * plane);
+    f.lpz = reinterpret_cast<uint32_t*>(pb + 6 * plane);
     f.mapS = reinterpret_cast<float*>(pm);
     f.mapN = reinterpret_cast<float*>(pm + fmap);
     f.mapSp = reinterpret_cast<float*>(pm + 2 * fmap);

@@ -292,18 +292,22 @@ __device__ __forceinline__ void bound_span2(const Frame& f, const float* __restr
                           << sh;
       const uint32_t vh = (uint32_t(xa < w && lhsA > chot * denA) | (uint32_t(xb < w && lhsB > chot * denB) << 1))
                           << sh;
-      uint32_t act, hot;
+      const uint32_t vz = (uint32_t(xa < w && lpA == 0.f) | (uint32_t(xb < w && lpB == 0.f) << 1)) << sh;
+      uint32_t act, hot, lz;
       if (lane < 16) {
         act = __reduce_or_sync(0x0000ffffu, va);
         hot = __reduce_or_sync(0x0000ffffu, vh);
+        lz = __reduce_or_sync(0x0000ffffu, vz);
       } else {
         act = __reduce_or_sync(0xffff0000u, va);
         hot = __reduce_or_sync(0xffff0000u, vh);
+        lz = __reduce_or_sync(0xffff0000u, vz);
       }
       if ((lane & 15) == 0 && wc + (lane >> 4) < f.wpr) {
         const size_t o = size_t(yy) * f.wpr + wc + (lane >> 4);
         f.act[o] = act;
         f.hot[o] = hot;
+        f.lpz[o] = lz;
       }
     }
     A = Col4{A.c, A.d, ea, ga};
@@ -496,7 +500,7 @@ __global__ void __launch_bounds__(kColWarps * 32) need_kernel(const Frame* __res
     // rows y0-4 .. y0+kSH+3 in chunks of 8: the chunk's loads are issued together
     static_assert((kSH + 8) % 8 == 0, "whole chunks");
     for (int rc = y0 - 4; rc < y0 + kSH + 4; rc += 8) {
-      uint32_t Lh[8], La[8], Lgh[8], Lga[8], Lc[8], Ls[8];
+      uint32_t Lh[8], La[8], Lgh[8], Lga[8], Lc[8], Ls[8], Lz[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int r = rc + i, yo = r - 4;
@@ -509,6 +513,7 @@ __global__ void __launch_bounds__(kColWarps * 32) need_kernel(const Frame* __res
         const bool out = yo >= y0 && yo < f.h && inw;
         Lc[i] = out ? cell_class(cls, f, wc, yo) : 0u;
         Ls[i] = (out && Lc[i] >= 2u && Lc[i] < 4u) ? f.sval[size_t(yo) * f.wpr + wc] : 0u;
+        Lz[i] = (out && Lc[i] >= 2u) ? f.lpz[size_t(yo) * f.wpr + wc] : 0u;
       }
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
@@ -545,7 +550,7 @@ __global__ void __launch_bounds__(kColWarps * 32) need_kernel(const Frame* __res
             f.test[o] = 0u;
           }
           const uint32_t sv = Ls[i];  // 0 in cells of class 4
-          qs = needS & ~sv;
+          qs = needS & ~sv & ~Lz[i];  // S = 0 exactly where L+ = 0: no median needed
           if ((sv | needS) != sv || cl >= 4u) f.sval[o] = sv | needS;
         }
         sw.w[warp][yo - y0][0][lane] = qs;
@@ -739,6 +744,19 @@ __device__ __forceinline__ void load_window(const float* __restrict__ a, int x, 
   }
 }
 
+// Bits of columns xs .. xs+4 of row qy of a bit plane (bit dx = column
+// xs + dx); columns outside [0, w) read as 0.
+__device__ __forceinline__ uint32_t plane_bits5(const uint32_t* __restrict__ plane, int wpr, int w, int xs, int qy) {
+  const int wl = max(xs, 0) >> 5, wr = min(xs + 4, w - 1) >> 5;
+  const uint64_t pair = uint64_t(plane[size_t(qy) * wpr + wl]) | (uint64_t(plane[size_t(qy) * wpr + wr]) << 32);
+  const int sh = xs - 32 * wl;  // in [-2, 31]
+  uint32_t b = uint32_t(sh >= 0 ? (pair >> sh) : (pair << -sh)) & 31u;
+#pragma unroll
+  for (int dx = 0; dx < 5; ++dx)
+    if (xs + dx < 0 || xs + dx >= w) b &= ~(1u << dx);
+  return b;
+}
+
 // Position of the r-th (0-based) set bit of w (r < popc(w)).
 __device__ __forceinline__ int select_bit(uint32_t w, int r) {
   int p = 0;
@@ -842,6 +860,26 @@ __global__ void __launch_bounds__(256) sp_kernel(const Frame* __restrict__ frame
                  const Frame& f = frames[fi];
                  float v[25];
                  load_window<2>(f.mapS, x, y, f.w, f.h, v);
+                 // S is exactly 0 where L+ = 0; mapS is not written there
+                 if (x >= 2 && x < f.w - 2) {
+#pragma unroll
+                   for (int dy = 0; dy < 5; ++dy) {
+                     const uint32_t z = plane_bits5(f.lpz, f.wpr, f.w, x - 2, clampi(y - 2 + dy, 0, f.h - 1));
+#pragma unroll
+                     for (int dx = 0; dx < 5; ++dx)
+                       if ((z >> dx) & 1u) v[dy * 5 + dx] = 0.f;
+                   }
+                 } else {
+#pragma unroll
+                   for (int dy = 0; dy < 5; ++dy) {
+                     const size_t ro = size_t(clampi(y - 2 + dy, 0, f.h - 1)) * f.wpr;
+#pragma unroll
+                     for (int dx = 0; dx < 5; ++dx) {
+                       const int xx = clampi(x - 2 + dx, 0, f.w - 1);
+                       if ((f.lpz[ro + (xx >> 5)] >> (xx & 31)) & 1u) v[dy * 5 + dx] = 0.f;
+                     }
+                   }
+                 }
                  const float sp = __fsub_rn(v[12], sel_med25(v));
                  f.mapSp[size_t(y) * f.w + x] = sp;
                  if (sp > p.sigclip) atomicOr(&f.test[size_t(y) * f.wpr + (x >> 5)], 1u << (x & 31));
@@ -874,7 +912,7 @@ __global__ void __launch_bounds__(256) bound_sparse_kernel(const Frame* __restri
   const int lane = threadIdx.x & 31;
   expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q2), Q.n[kNB], sm,
                [&](bool valid, int fi, int x, int y) {
-                 bool hot = false, act = false;
+                 bool hot = false, act = false, lz = false;
                  unsigned long long key = ~0ull;
                  if (valid) {
                    const Frame& f = frames[fi];
@@ -892,6 +930,7 @@ __global__ void __launch_bounds__(256) bound_sparse_kernel(const Frame* __restri
                    const float lhs = lp * lp * g2;
                    act = lhs > clow * den;
                    hot = lhs > chot * den;
+                   lz = lp == 0.f;
                    key = (static_cast<unsigned long long>(fi) << 40) | (size_t(y) * f.wpr + (x >> 5));
                  }
                  const unsigned grp = __match_any_sync(0xffffffffu, key);
@@ -899,6 +938,7 @@ __global__ void __launch_bounds__(256) bound_sparse_kernel(const Frame* __restri
                  const uint32_t m = __reduce_or_sync(grp, bit);
                  const uint32_t hb = __reduce_or_sync(grp, hot ? bit : 0u);
                  const uint32_t ab = __reduce_or_sync(grp, act ? bit : 0u);
+                 const uint32_t zb = __reduce_or_sync(grp, lz ? bit : 0u);
                  if (valid && lane == __ffs(grp) - 1) {
                    const Frame& f = frames[fi];
                    const size_t wo = size_t(y) * f.wpr + (x >> 5);
@@ -906,6 +946,8 @@ __global__ void __launch_bounds__(256) bound_sparse_kernel(const Frame* __restri
                    atomicOr(f.hot + wo, hb);
                    atomicAnd(f.act + wo, ~(m & ~ab));
                    atomicOr(f.act + wo, ab);
+                   atomicAnd(f.lpz + wo, ~(m & ~zb));
+                   atomicOr(f.lpz + wo, zb);
                  }
                });
 }
@@ -1141,19 +1183,6 @@ __global__ void __launch_bounds__(256) flagq_kernel(const Frame* __restrict__ fr
     emit_word(v, f, wc, y, Q.q1, Q.n + kNRep, ws);  // ends with a barrier
     if (t == 0 && bcount) atomicAdd(f.counters + 0, (unsigned long long)bcount);
   }
-}
-
-// Bits of columns xs .. xs+4 of row qy of a bit plane (bit dx = column
-// xs + dx); columns outside [0, w) read as 0.
-__device__ __forceinline__ uint32_t plane_bits5(const uint32_t* __restrict__ plane, int wpr, int w, int xs, int qy) {
-  const int wl = max(xs, 0) >> 5, wr = min(xs + 4, w - 1) >> 5;
-  const uint64_t pair = uint64_t(plane[size_t(qy) * wpr + wl]) | (uint64_t(plane[size_t(qy) * wpr + wr]) << 32);
-  const int sh = xs - 32 * wl;  // in [-2, 31]
-  uint32_t b = uint32_t(sh >= 0 ? (pair >> sh) : (pair << -sh)) & 31u;
-#pragma unroll
-  for (int dx = 0; dx < 5; ++dx)
-    if (xs + dx < 0 || xs + dx >= w) b &= ~(1u << dx);
-  return b;
 }
 
 // ORs a 5x5 mask (bit r*5 + dx = column xs + dx of row y0 + r; only in-frame

@@ -87,13 +87,13 @@ namespace {
 size_t frame_bytes(int w, int h) {
   // the caller's input, cleaned output and mask (resident while queued), and the
   // workspace of the queue pipeline: 4 float maps, 5 queue entries per pixel,
-  // 9 bit planes, and 5 words per cell of one word x 8 rows (2 class arrays,
-  // 3 cell lists)
+  // 12 bit planes (2 of them changed-pixel planes), and 2 words per cell of one
+  // word x 8 rows (the class arrays)
   const size_t n = size_t(w) * size_t(h);
   const size_t wpr = size_t(w + 31) / 32;
   const size_t plane = wpr * size_t(h) * 4;
   const size_t cells = wpr * ((size_t(h) + 7) / 8);
-  return n * (4 + 4 + 1) + n * 4 * 4 + n * 5 * 4 + 9 * plane + 5 * 4 * cells;
+  return n * (4 + 4 + 1) + n * 4 * 4 + n * 5 * 4 + 12 * plane + 2 * 4 * cells;
 }
 
 void launch_wave(crb_server* s, int slot, std::vector<Request>&& reqs) {
