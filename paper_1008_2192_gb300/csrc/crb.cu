@@ -83,7 +83,7 @@ constexpr int kDescSlots = 4;
 // queue pipeline kernels, for the occupancy table
 enum QK {
   kQBound, kQNeed, kQS, kQSp, kQM3need, kQM3, kQCand, kQRepCompute, kQBoundList, kQRq, kQRepWrite, kQCellList,
-  kQCandFull, kQGrow, kQFlagq, kQKernels
+  kQCandFull, kQGrow, kQFlagq, kQSegList, kQD2Seg, kQNeedSeg, kQM3needSeg, kQKernels
 };
 
 struct GraphKey {
@@ -204,14 +204,17 @@ int init_ctx(crb_ctx* c) {
         reinterpret_cast<const void*>(crb::s_kernel),           reinterpret_cast<const void*>(crb::sp_kernel),
         reinterpret_cast<const void*>(crb::m3need_kernel),      reinterpret_cast<const void*>(crb::m3_kernel),
         reinterpret_cast<const void*>(crb::cand_test_kernel),   reinterpret_cast<const void*>(crb::rep_compute_kernel),
-        reinterpret_cast<const void*>(crb::bound_sparse_kernel),  reinterpret_cast<const void*>(crb::rq_kernel),
+        reinterpret_cast<const void*>(crb::bound_sparse_kernel),   reinterpret_cast<const void*>(crb::rq_kernel),
         reinterpret_cast<const void*>(crb::rep_write_kernel),   reinterpret_cast<const void*>(crb::d2_kernel),
         reinterpret_cast<const void*>(crb::cand_full_kernel),   reinterpret_cast<const void*>(crb::grow_kernel<true>),
-        reinterpret_cast<const void*>(crb::flagq_kernel)};
+        reinterpret_cast<const void*>(crb::flagq_kernel),       reinterpret_cast<const void*>(crb::seg_list_kernel),
+        reinterpret_cast<const void*>(crb::d2_seg_kernel),      reinterpret_cast<const void*>(crb::need_seg_kernel),
+        reinterpret_cast<const void*>(crb::m3need_seg_kernel)};
     for (int i = 0; i < kQKernels; ++i) {
       int o = 0;
-      const int threads =
-          i == kQBound ? 128 : (i == kQNeed || i == kQM3need || i == kQCellList) ? crb::kColWarps * 32 : 256;
+      const bool col = i == kQNeed || i == kQM3need || i == kQCellList || i == kQD2Seg || i == kQNeedSeg ||
+                       i == kQM3needSeg;
+      const int threads = i == kQBound ? 128 : col ? crb::kColWarps * 32 : 256;
       CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[i], threads, 0));
       c->occ_q[i] = o > 0 ? o : 1;
     }
@@ -359,22 +362,36 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
       uint32_t* cls_next = (k < P.niter) ? P.cells[(k + 1) & 1] : nullptr;
       const uint32_t* kcls = (k == 1) ? nullptr : cls;
       const int gcol = grid(kQNeed, (P.nunits + crb::kColWarps - 1) / crb::kColWarps);
+      const bool seg = k >= crb::kSegFrom;  // the column kernels walk the listed segments only
+      const int tcol = crb::kColWarps * 32;
       timed(c, kPBound, stream, [&] {
         if (k == 1) {
           crb::bound_kernel<<<grid(kQBound, P.nblocks), 128, 0, stream>>>(c->d_frames, P.n, P.nblocks, c->p);
         } else {  // the pixels within 2 px of a change, re-tested one by one
-          crb::d2_kernel<<<gcol, crb::kColWarps * 32, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, k);
+          if (seg) {
+            crb::seg_list_kernel<<<grid(kQSegList, (P.nunits + 7) / 8), crb::kThreads, 0, stream>>>(
+                c->d_frames, P.n, P.nunits, P.Q, cls);
+            crb::d2_seg_kernel<<<gq * c->occ_q[kQD2Seg], tcol, 0, stream>>>(c->d_frames, P.n, P.Q, k);
+          } else {
+            crb::d2_kernel<<<gcol, tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, k);
+          }
           crb::bound_sparse_kernel<<<gq * c->occ_q[kQBoundList], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
         }
       });
       timed(c, kPNeed, stream, [&] {
-        crb::need_kernel<<<gcol, crb::kColWarps * 32, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, kcls);
+        if (seg)
+          crb::need_seg_kernel<<<gq * c->occ_q[kQNeedSeg], tcol, 0, stream>>>(c->d_frames, P.n, P.Q, cls);
+        else
+          crb::need_kernel<<<gcol, tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, kcls);
       });
       timed(c, kPS, stream, [&] { crb::s_kernel<<<gq * c->occ_q[kQS], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k); });
       timed(c, kPSp, stream,
             [&] { crb::sp_kernel<<<gq * c->occ_q[kQSp], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p); });
       timed(c, kPM3need, stream, [&] {
-        crb::m3need_kernel<<<gcol, crb::kColWarps * 32, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, kcls);
+        if (seg)
+          crb::m3need_seg_kernel<<<gq * c->occ_q[kQM3needSeg], tcol, 0, stream>>>(c->d_frames, P.n, P.Q, cls);
+        else
+          crb::m3need_kernel<<<gcol, tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, kcls);
       });
       timed(c, kPM3, stream, [&] { crb::m3_kernel<<<gq * c->occ_q[kQM3], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k); });
       timed(c, kPCand, stream, [&] {
@@ -450,9 +467,10 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
 // word), fresh, fbl (a pixel index per pixel)].
 int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Plan& P) {
   const int n = int(specs.size());
-  long long npix = 0, nblocks = 0, ncells = 0, nwords = 0;
+  long long npix = 0, nblocks = 0, ncells = 0, nwords = 0, nsegs = 0;
   for (const auto& s : specs) {
     npix += (long long)s.w * s.h;
+    nsegs += 32LL * (((s.w + 31) / 32 + 31) / 32) * ((s.h + crb::kSH - 1) / crb::kSH);  // 32 per strip
     nwords += (long long)((s.w + 31) / 32) * s.h;
     ncells += (long long)((s.w + 31) / 32) * ((s.h + crb::kCH - 1) / crb::kCH);
   }
@@ -488,6 +506,9 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
   const size_t fbytes = align256(size_t(npix) * 4);
   const size_t off_q = total;
   total += 3 * qbytes + 2 * fbytes;
+  const size_t off_seg = total;  // three segment lists, one entry per segment at most
+  const size_t segbytes = align256(size_t(nsegs) * 4);
+  total += 3 * segbytes;
   const int nit = niter > 0 ? niter : 1;
   const int ncounters = (2 + crb::kWork) * nit * n;
   const size_t tab_n = size_t(npix >> crb::kTabShift) + 1;
@@ -581,6 +602,7 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
   P.Q.q2 = reinterpret_cast<uint32_t*>(ws + off_q + 2 * qbytes);
   P.Q.fresh = reinterpret_cast<uint32_t*>(ws + off_q + 3 * qbytes);
   P.Q.fbl = reinterpret_cast<uint32_t*>(ws + off_q + 3 * qbytes + fbytes);
+  for (int j = 0; j < 3; ++j) P.Q.seg[j] = reinterpret_cast<uint32_t*>(ws + off_seg + size_t(j) * segbytes);
   P.chg[0] = ws + off_chg0;
   P.chg[1] = ws + off_chg0 + chg_bytes;
   P.chg_bytes = chg_bytes;
@@ -677,8 +699,8 @@ int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
   // the launches of this upload and of enqueue_work for this plan (memsets and copies not counted)
   if (P.niter == 0)
     c->last_launches = 1;
-  else if (P.queue)  // 2 uploads; iteration 1: 12 kernels, later ones 14, plus the mask
-    c->last_launches = 2 + 12 + 14 * (P.niter - 1) + 1;
+  else if (P.queue)  // 2 uploads; iteration 1: 12 kernels, later ones 14 (15 with the segment list), plus the mask
+    c->last_launches = 2 + 12 + 14 * (P.niter - 1) + std::max(0, P.niter - (crb::kSegFrom - 1)) + 1;
   else
     c->last_launches = 1 + (P.fuse ? P.niter + 1 : 2 * P.niter) + c->mprev_frames;
   return CRB_OK;

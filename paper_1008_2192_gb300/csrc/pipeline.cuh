@@ -81,7 +81,10 @@ enum : int {
   kNTpx = 13,
   kNB = 14,     // pixels to re-test in the bound pass (word entries)
   kNBpx = 15,
-  kNCount = 16
+  kNSeg = 16,   // segments (1 word x kSH rows) listed for m3need_seg_kernel,
+  kNSegN = 17,  // for need_seg_kernel,
+  kNSegD = 18,  // for d2_seg_kernel (the three in Queues::seg order)
+  kNCount = 19
 };
 
 // QS, QSP, QM3 and QT hold word entries: (global word index, mask of the
@@ -96,6 +99,7 @@ struct Queues {
   uint32_t* fbl;    // fully flagged windows
   unsigned int* n;  // kNCount counters
   const uint32_t* ftab;  // frame of global pixel t << kTabShift
+  uint32_t* seg[3];      // segments listed for m3need, need, d2 (iterations >= kSegFrom): 32 * strip + word
 };
 
 // the image J of iteration k (I0, then the in-place buffer)
@@ -318,8 +322,8 @@ __device__ __forceinline__ void bound_span2(const Frame& f, const float* __restr
 
 // bound_kernel (iteration 1): pairs of word columns of every frame, blocks of
 // kBW words x kBH rows, 4 warps of 2 words; the image buffer starts as a copy of
-// I0. Later iterations re-test only the pixels within 2 px of a change
-// (d2_kernel, bound_sparse_kernel).
+// I0. Later iterations re-test only the words with a pixel within 2 px of a
+// change (d2_kernel or d2_seg_kernel, then bound_sparse_kernel).
 __global__ void __launch_bounds__(128) bound_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
                                                     Params p) {
   const int warp = threadIdx.x >> 5;
@@ -424,17 +428,16 @@ __device__ __forceinline__ void col_count(uint32_t v, unsigned int& ents, unsign
   pix += __reduce_add_sync(0xffffffffu, unsigned(__popc(v)));
 }
 
-// Writes the strip's entries of queue j (rows y0 .. y0+kSH-1, lane = word wc0+lane).
-__device__ __forceinline__ void col_write(const ColWords& sw, int warp, int j, const Frame& f, int wc0, int y0,
+// Writes the warp's entries of queue j: row rr of the lane's column is the
+// global word gw0 + rr * wpr (both per lane).
+__device__ __forceinline__ void col_write(const ColWords& sw, int warp, int j, uint32_t gw0, int wpr,
                                           unsigned int base, uint2* q) {
   const int lane = threadIdx.x & 31;
+#pragma unroll 1
   for (int rr = 0; rr < kSH; ++rr) {
     const uint32_t v = sw.w[warp][rr][j][lane];
     const unsigned bal = __ballot_sync(0xffffffffu, v != 0u);
-    if (v) {
-      const uint32_t gw = uint32_t(f.word0 + (long long)(y0 + rr) * f.wpr + wc0 + lane);
-      q[base + __popc(bal & ((1u << lane) - 1u))] = make_uint2(gw, v);
-    }
+    if (v) q[base + __popc(bal & ((1u << lane) - 1u))] = make_uint2(gw0 + uint32_t(rr) * uint32_t(wpr), v);
     base += __popc(bal);
   }
 }
@@ -562,8 +565,8 @@ __global__ void __launch_bounds__(kColWarps * 32) need_kernel(const Frame* __res
     unsigned int base[2];
     col_reserve(ents, pix, Q.n + kNS, Q.n + kNSP, Q.n + kNSpx, Q.n + kNSPpx, base);
     __syncwarp();
-    col_write(sw, warp, 0, f, wc0, y0, base[0], reinterpret_cast<uint2*>(Q.q0));
-    col_write(sw, warp, 1, f, wc0, y0, base[1], reinterpret_cast<uint2*>(Q.q1));
+    col_write(sw, warp, 0, uint32_t(f.word0 + (long long)y0 * f.wpr + wc), f.wpr, base[0], reinterpret_cast<uint2*>(Q.q0));
+    col_write(sw, warp, 1, uint32_t(f.word0 + (long long)y0 * f.wpr + wc), f.wpr, base[1], reinterpret_cast<uint2*>(Q.q1));
     __syncwarp();  // the shared words are refilled for the next strip
   }
 }
@@ -635,8 +638,8 @@ __global__ void __launch_bounds__(kColWarps * 32) m3need_kernel(const Frame* __r
     unsigned int base[2];
     col_reserve(ents, pix, Q.n + kNM3, Q.n + kNT, Q.n + kNM3px, Q.n + kNTpx, base);
     __syncwarp();
-    col_write(sw, warp, 0, f, wc0, y0, base[0], reinterpret_cast<uint2*>(Q.q0));
-    col_write(sw, warp, 1, f, wc0, y0, base[1], reinterpret_cast<uint2*>(Q.q2));
+    col_write(sw, warp, 0, uint32_t(f.word0 + (long long)y0 * f.wpr + wc), f.wpr, base[0], reinterpret_cast<uint2*>(Q.q0));
+    col_write(sw, warp, 1, uint32_t(f.word0 + (long long)y0 * f.wpr + wc), f.wpr, base[1], reinterpret_cast<uint2*>(Q.q2));
     __syncwarp();
   }
 }
@@ -690,7 +693,301 @@ __global__ void __launch_bounds__(kColWarps * 32) d2_kernel(const Frame* __restr
     unsigned int base[2];
     col_reserve(ents, pix, Q.n + kNB, Q.n + kNB, Q.n + kNBpx, Q.n + kNBpx, base);
     __syncwarp();
-    col_write(sw, warp, 0, f, wc0, y0, base[0], reinterpret_cast<uint2*>(Q.q2));
+    col_write(sw, warp, 0, uint32_t(f.word0 + (long long)y0 * f.wpr + wc), f.wpr, base[0], reinterpret_cast<uint2*>(Q.q2));
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Segment kernels (iterations >= kSegFrom). A segment is one word column of a
+// strip (32 px x kSH rows). From the third iteration on, the cells near a
+// change are a small part of each frame, though they still touch most strips;
+// so the segments with work are listed first, and the lanes of a warp each walk
+// one listed segment down its rows, loading the words left and right of it
+// themselves (the strip kernels above share them across lanes instead). The
+// outputs are those of the strip kernels: a segment left out of the list has
+// none, because every output of need, m3need and d2 lies within 3 px of a cell
+// of class >= 2.
+constexpr int kSegFrom = 3;
+
+// seg_list_kernel: lists the segments each segment kernel walks. d2: a cell
+// of class 4 among the segment's own cells (a pixel within 2 px of a change
+// lies in one); need: a cell of class >= 2 among them; m3need: a cell of class
+// >= 2 in the segment's word column or the ones left and right of it, among
+// the segment's cell rows widened by one each way (QT of those cells reaches 3
+// px into the segment). 8 strips per block (warp = strip, lane = word); one
+// atomic per block and list.
+__global__ void __launch_bounds__(kThreads) seg_list_kernel(const Frame* __restrict__ frames, int nframes,
+                                                            long long nunits, Queues Q,
+                                                            const uint32_t* __restrict__ cls) {
+  __shared__ int ws[kThreads / 32 + 1];
+  __shared__ unsigned int sbase[3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kWarps = kThreads / 32, kCells = kSH / kCH;
+  for (long long ub = (long long)blockIdx.x * kWarps; ub < nunits; ub += (long long)gridDim.x * kWarps) {
+    const long long u = ub + warp;
+    bool put[3] = {false, false, false};
+    if (u < nunits) {  // whole warp
+      const Frame& f = frames[frame_of_unit(frames, nframes, u)];
+      const long long lu = u - f.u0;
+      const int uy = int(lu / f.ugx), ux = int(lu - (long long)uy * f.ugx);
+      const int wc0 = ux * 32, wc = wc0 + lane;
+      const bool inw = wc < f.wpr;
+      const int hw = lane == 0 ? wc0 - 1 : wc0 + 32;
+      const bool hin = (lane == 0 || lane == 31) && hw >= 0 && hw < f.wpr;
+      bool own2 = false, own4 = false, near2 = false, halo2 = false;
+      for (int cy = max(uy * kCells - 1, 0); cy < min((uy + 1) * kCells + 1, f.ncy); ++cy) {
+        const uint32_t* row = cls + f.cell0 + (long long)cy * f.wpr;
+        const uint32_t c = inw ? row[wc] : 0u;
+        const bool mine = cy >= uy * kCells && cy < (uy + 1) * kCells;
+        near2 |= c >= 2u;
+        own2 |= mine && c >= 2u;
+        own4 |= mine && c >= 4u;
+        if (hin && row[hw] >= 2u) halo2 = true;
+      }
+      const bool l = __shfl_up_sync(0xffffffffu, near2, 1), r = __shfl_down_sync(0xffffffffu, near2, 1);
+      put[0] = inw && (near2 || (lane == 0 ? halo2 : l) || (lane == 31 ? halo2 : r));
+      put[1] = own2;
+      put[2] = own4;
+    }
+    uint32_t* const qq[3] = {Q.seg[0], Q.seg[1], Q.seg[2]};
+    block_append<3>(put, uint32_t(u * 32 + lane), qq, Q.n + kNSeg, ws, sbase);
+  }
+}
+
+// A lane's listed segment: frame, word column wc, first row y0; ok = false for
+// the lanes past the end of the list (their loads and outputs are masked off).
+struct SegLane {
+  const Frame* f;
+  int wc, y0, wpr, h;
+  bool ok, inl, inr;  // inl, inr: the words left and right of wc are in the frame
+  uint32_t fmask;     // in-frame bits of word wc
+  uint32_t gw0;       // global word of (wc, y0)
+};
+
+__device__ __forceinline__ SegLane seg_lane(const Frame* __restrict__ frames, int nframes, const uint32_t* seg,
+                                            unsigned int b, unsigned int nseg) {
+  const int lane = threadIdx.x & 31;
+  SegLane L;
+  L.ok = b + lane < nseg;
+  const uint32_t s = seg[L.ok ? b + lane : b];
+  const long long u = s >> 5;
+  L.f = frames + frame_of_unit(frames, nframes, u);
+  const Frame& f = *L.f;
+  const long long lu = u - f.u0;
+  const int uy = int(lu / f.ugx), ux = int(lu - (long long)uy * f.ugx);
+  L.wc = ux * 32 + int(s & 31u);
+  L.y0 = uy * kSH;
+  L.wpr = f.wpr;
+  L.h = f.h;
+  L.inl = L.ok && L.wc > 0;
+  L.inr = L.ok && L.wc + 1 < f.wpr;
+  L.fmask = L.ok ? frame_word(L.wc, f.w) : 0u;
+  L.gw0 = uint32_t(f.word0 + (long long)L.y0 * f.wpr + L.wc);
+  return L;
+}
+
+// d2_seg_kernel: d2_kernel over the listed segments.
+__global__ void __launch_bounds__(kColWarps * 32) d2_seg_kernel(const Frame* __restrict__ frames, int nframes,
+                                                                Queues Q, int k) {
+  __shared__ ColWords sw;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned int nseg = Q.n[kNSegD];
+  for (unsigned int b = (blockIdx.x * kColWarps + warp) * 32u; b < nseg; b += gridDim.x * kColWarps * 32u) {
+    const SegLane S = seg_lane(frames, nframes, Q.seg[2], b, nseg);
+    const Frame& f = *S.f;
+    const int wc = S.wc, y0 = S.y0, wpr = S.wpr, h = S.h;
+    const bool ok = S.ok, inl = S.inl, inr = S.inr;
+    const uint32_t* __restrict__ chg = f.chg[k & 1];
+    uint32_t cl0 = 0, cl1 = 0, cl2 = 0, cl3 = 0, cl4 = 0;  // rows r-4 .. r: left, own, right words
+    uint32_t cc0 = 0, cc1 = 0, cc2 = 0, cc3 = 0, cc4 = 0;
+    uint32_t cr0 = 0, cr1 = 0, cr2 = 0, cr3 = 0, cr4 = 0;
+    unsigned int ents[2] = {0u, 0u}, pix[2] = {0u, 0u};
+    for (int tc = -2; tc < kSH + 2; tc += 8) {  // rows y0-2 .. y0+kSH+1 (the last chunk runs past them)
+      uint32_t L[8], C[8], R[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = y0 + tc + i;
+        const bool rin = ok && r >= 0 && r < h && tc + i < kSH + 2;
+        const size_t ro = size_t(rin ? r : 0) * wpr + wc;
+        C[i] = rin ? chg[ro] : 0u;
+        L[i] = (rin && inl) ? chg[ro - 1] : 0u;
+        R[i] = (rin && inr) ? chg[ro + 1] : 0u;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        cl0 = cl1; cl1 = cl2; cl2 = cl3; cl3 = cl4; cl4 = L[i];
+        cc0 = cc1; cc1 = cc2; cc2 = cc3; cc3 = cc4; cc4 = C[i];
+        cr0 = cr1; cr1 = cr2; cr2 = cr3; cr3 = cr4; cr4 = R[i];
+        const int t = tc + i - 2;
+        if (t < 0 || t >= kSH) continue;  // whole warp
+        const uint32_t v = cc0 | cc1 | cc2 | cc3 | cc4;
+        const uint32_t d2 = (y0 + t < h) ? (hdil<2>(cl0 | cl1 | cl2 | cl3 | cl4, v, cr0 | cr1 | cr2 | cr3 | cr4) & S.fmask) : 0u;
+        sw.w[warp][t][0][lane] = d2;
+        col_count(d2, ents[0], pix[0]);
+      }
+    }
+    unsigned int base[2];
+    col_reserve(ents, pix, Q.n + kNB, Q.n + kNB, Q.n + kNBpx, Q.n + kNBpx, base);
+    __syncwarp();
+    col_write(sw, warp, 0, S.gw0, wpr, base[0], reinterpret_cast<uint2*>(Q.q2));
+    __syncwarp();
+  }
+}
+
+// need_seg_kernel: need_kernel over the listed segments.
+__global__ void __launch_bounds__(kColWarps * 32) need_seg_kernel(const Frame* __restrict__ frames, int nframes,
+                                                                  Queues Q, const uint32_t* __restrict__ cls) {
+  __shared__ ColWords sw;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned int nseg = Q.n[kNSegN];
+  for (unsigned int b = (blockIdx.x * kColWarps + warp) * 32u; b < nseg; b += gridDim.x * kColWarps * 32u) {
+    const SegLane S = seg_lane(frames, nframes, Q.seg[1], b, nseg);
+    const Frame& f = *S.f;
+    const int wc = S.wc, y0 = S.y0, wpr = S.wpr, h = S.h;
+    const bool ok = S.ok, inl = S.inl, inr = S.inr;
+    const uint32_t* __restrict__ hot = f.hot;
+    const uint32_t* __restrict__ act = f.act;
+    const long long cb = f.cell0 + wc;  // cell (wc, y / kCH) at cb + (y / kCH) * wpr
+    uint32_t hl[5] = {}, hc[5] = {}, hr[5] = {};  // hot, rows r-4 .. r: left, own, right words
+    uint32_t al[3] = {}, ac[3] = {}, ar[3] = {};  // act, rows r-2 .. r
+    uint32_t nl[5] = {}, nc[5] = {}, nr[5] = {};  // nsp, rows r-6 .. r-2
+    unsigned int ents[2] = {0u, 0u}, pix[2] = {0u, 0u};
+    constexpr int kC = 4;  // rows per chunk of loads
+    for (int tc = -4; tc < kSH + 4; tc += kC) {  // rows y0-4 .. y0+kSH+3
+      uint32_t Hl[kC], Hc[kC], Hr[kC], Al[kC], Ac[kC], Ar[kC], Cl[kC], Sv[kC], Lz[kC];
+#pragma unroll
+      for (int i = 0; i < kC; ++i) {
+        const int r = y0 + tc + i, yo = r - 4;
+        const bool rin = ok && r >= 0 && r < h;
+        const size_t ro = size_t(rin ? r : 0) * wpr + wc;
+        Hc[i] = rin ? hot[ro] : 0u;
+        Ac[i] = rin ? act[ro] : 0u;
+        Hl[i] = (rin && inl) ? hot[ro - 1] : 0u;
+        Al[i] = (rin && inl) ? act[ro - 1] : 0u;
+        Hr[i] = (rin && inr) ? hot[ro + 1] : 0u;
+        Ar[i] = (rin && inr) ? act[ro + 1] : 0u;
+        const bool out = ok && tc + i >= 4 && yo < h;
+        const size_t oo = size_t(out ? yo : 0) * wpr + wc;
+        // the loads do not wait for the class (the few listed segments make the extra bytes cheap)
+        Cl[i] = out ? cls[cb + (long long)(yo / kCH) * wpr] : 0u;
+        Sv[i] = out ? f.sval[oo] : 0u;
+        Lz[i] = out ? f.lpz[oo] : 0u;
+      }
+#pragma unroll
+      for (int i = 0; i < kC; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { hl[j] = hl[j + 1]; hc[j] = hc[j + 1]; hr[j] = hr[j + 1]; }
+        hl[4] = Hl[i]; hc[4] = Hc[i]; hr[4] = Hr[i];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) { al[j] = al[j + 1]; ac[j] = ac[j + 1]; ar[j] = ar[j + 1]; }
+        al[2] = Al[i]; ac[2] = Ac[i]; ar[2] = Ar[i];
+        // nsp of row r-2: exact in the own word, and in the two bits of each side word next to it
+        const uint32_t vl = hl[0] | hl[1] | hl[2] | hl[3] | hl[4];
+        const uint32_t vc = hc[0] | hc[1] | hc[2] | hc[3] | hc[4];
+        const uint32_t vr = hr[0] | hr[1] | hr[2] | hr[3] | hr[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { nl[j] = nl[j + 1]; nc[j] = nc[j + 1]; nr[j] = nr[j + 1]; }
+        nl[4] = hdil<2>(0u, vl, vc) & al[0];
+        nc[4] = hdil<2>(vl, vc, vr) & ac[0];
+        nr[4] = hdil<2>(vc, vr, 0u) & ar[0];
+        // needS of row r-4
+        const int t = tc + i - 4;
+        if (t < 0) continue;  // whole warp
+        uint32_t qs = 0, qsp = 0;
+        const uint32_t cl = Cl[i];  // 0 outside the frame
+        if (cl >= 2u) {
+          const uint32_t needS = hdil<2>(nl[0] | nl[1] | nl[2] | nl[3] | nl[4], nc[0] | nc[1] | nc[2] | nc[3] | nc[4],
+                                         nr[0] | nr[1] | nr[2] | nr[3] | nr[4]) &
+                                 S.fmask;
+          const size_t o = size_t(y0 + t) * wpr + wc;
+          if (cl >= 3u) {
+            qsp = nc[2];  // nsp of row y0+t
+            f.nsp[o] = qsp;
+            f.test[o] = 0u;
+          }
+          const uint32_t sv = cl < 4u ? Sv[i] : 0u;  // S is not current anywhere in cells of class 4
+          qs = needS & ~sv & ~Lz[i];
+          if ((sv | needS) != sv || cl >= 4u) f.sval[o] = sv | needS;
+        }
+        sw.w[warp][t][0][lane] = qs;
+        sw.w[warp][t][1][lane] = qsp;
+        col_count(qs, ents[0], pix[0]);
+        col_count(qsp, ents[1], pix[1]);
+      }
+    }
+    unsigned int base[2];
+    col_reserve(ents, pix, Q.n + kNS, Q.n + kNSP, Q.n + kNSpx, Q.n + kNSPpx, base);
+    __syncwarp();
+    col_write(sw, warp, 0, S.gw0, wpr, base[0], reinterpret_cast<uint2*>(Q.q0));
+    col_write(sw, warp, 1, S.gw0, wpr, base[1], reinterpret_cast<uint2*>(Q.q1));
+    __syncwarp();
+  }
+}
+
+// m3need_seg_kernel: m3need_kernel over the listed segments.
+__global__ void __launch_bounds__(kColWarps * 32) m3need_seg_kernel(const Frame* __restrict__ frames, int nframes,
+                                                                    Queues Q, const uint32_t* __restrict__ cls) {
+  __shared__ ColWords sw;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned int nseg = Q.n[kNSeg];
+  for (unsigned int b = (blockIdx.x * kColWarps + warp) * 32u; b < nseg; b += gridDim.x * kColWarps * 32u) {
+    const SegLane S = seg_lane(frames, nframes, Q.seg[0], b, nseg);
+    const Frame& f = *S.f;
+    const int wc = S.wc, y0 = S.y0, wpr = S.wpr, h = S.h;
+    const bool ok = S.ok, inl = S.inl, inr = S.inr;
+    const uint32_t* __restrict__ test = f.test;
+    const long long cb = f.cell0 + wc;
+    uint32_t ql[7] = {}, qc[7] = {}, qr[7] = {};  // QT, rows r-6 .. r: left, own, right words
+    unsigned int ents[2] = {0u, 0u}, pix[2] = {0u, 0u};
+    for (int tc = -3; tc < kSH + 3; tc += 8) {  // rows y0-3 .. y0+kSH+2 (the last chunk runs past them)
+      uint32_t Ql[8], Qc[8], Qr[8], Lm[8], Lc4[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = y0 + tc + i, t = tc + i - 3;
+        const bool rin = ok && r >= 0 && r < h && tc + i < kSH + 3;
+        const size_t ro = size_t(rin ? r : 0) * wpr + wc;
+        const long long cr = cb + (long long)((rin ? r : 0) / kCH) * wpr;
+        // the loads do not wait for the classes: test is masked by them afterwards
+        Qc[i] = rin ? test[ro] & (cls[cr] >= 2u ? ~0u : 0u) : 0u;
+        Ql[i] = (rin && inl) ? test[ro - 1] & (cls[cr - 1] >= 2u ? ~0u : 0u) : 0u;
+        Qr[i] = (rin && inr) ? test[ro + 1] & (cls[cr + 1] >= 2u ? ~0u : 0u) : 0u;
+        const bool out = ok && t >= 0 && t < kSH && y0 + t < h;
+        Lc4[i] = out ? uint32_t(cls[cb + (long long)((y0 + t) / kCH) * wpr] >= 4u) : 0u;
+        Lm[i] = out ? f.m3val[size_t(y0 + t) * wpr + wc] : 0u;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) { ql[j] = ql[j + 1]; qc[j] = qc[j + 1]; qr[j] = qr[j + 1]; }
+        ql[6] = Ql[i]; qc[6] = Qc[i]; qr[6] = Qr[i];
+        const int t = tc + i - 3;
+        if (t < 0 || t >= kSH) continue;  // whole warp
+        uint32_t qm = 0, qto = 0;
+        if (ok && y0 + t < h) {
+          const uint32_t need = hdil<3>(ql[0] | ql[1] | ql[2] | ql[3] | ql[4] | ql[5] | ql[6],
+                                        qc[0] | qc[1] | qc[2] | qc[3] | qc[4] | qc[5] | qc[6],
+                                        qr[0] | qr[1] | qr[2] | qr[3] | qr[4] | qr[5] | qr[6]) &
+                                S.fmask;
+          const bool c4 = Lc4[i] != 0u;
+          if (need || c4) {
+            const uint32_t old = c4 ? 0u : Lm[i];  // M3 is not current anywhere in cells of class 4
+            qm = need & ~old;
+            if (c4 || qm) f.m3val[size_t(y0 + t) * wpr + wc] = old | need;
+          }
+          qto = qc[3];  // QT word of row y0+t
+        }
+        sw.w[warp][t][0][lane] = qm;
+        sw.w[warp][t][1][lane] = qto;
+        col_count(qm, ents[0], pix[0]);
+        col_count(qto, ents[1], pix[1]);
+      }
+    }
+    unsigned int base[2];
+    col_reserve(ents, pix, Q.n + kNM3, Q.n + kNT, Q.n + kNM3px, Q.n + kNTpx, base);
+    __syncwarp();
+    col_write(sw, warp, 0, S.gw0, wpr, base[0], reinterpret_cast<uint2*>(Q.q0));
+    col_write(sw, warp, 1, S.gw0, wpr, base[1], reinterpret_cast<uint2*>(Q.q2));
     __syncwarp();
   }
 }
@@ -793,12 +1090,24 @@ struct ExpandSmem {
   int ws[kThreads / 32 + 1];
 };
 
-// Expands a queue of n word entries into pixels: per chunk of kThreads
-// entries, a block scan of the bit counts, then one pixel per thread per round,
-// found by binary search in the prefix and a bit select in the mask. Every
-// thread of the block runs every round and calls body(valid, frame, x, y), so
-// body may hold block-wide steps.
-template <typename F>
+// The mask of the kGran-pixel groups of word mask m that hold a set bit (bit i:
+// pixels kGran*i .. kGran*i + kGran-1).
+template <int kGran>
+__device__ __forceinline__ uint32_t group_mask(uint32_t m) {
+  if (kGran == 1) return m;
+  uint32_t g = 0;
+#pragma unroll
+  for (int i = 0; i < 32 / kGran; ++i) g |= uint32_t(((m >> (kGran * i)) & ((1u << kGran) - 1u)) != 0u) << i;
+  return g;
+}
+
+// Expands a queue of n word entries into items of kGran pixels (1: pixels; 4:
+// the groups of four with a listed pixel): per chunk of kThreads entries, a
+// block scan of the item counts, then one item per thread per round, found by
+// binary search in the prefix and a bit select in the item mask. Every thread
+// of the block runs every round and calls body(valid, frame, x, y) with x the
+// item's first pixel, so body may hold block-wide steps.
+template <int kGran = 1, typename F>
 __device__ __forceinline__ void expand_words(const Frame* __restrict__ frames, int nframes, const uint2* __restrict__ q,
                                              unsigned int n, ExpandSmem& sm, F&& body) {
   const int t = threadIdx.x;
@@ -807,7 +1116,7 @@ __device__ __forceinline__ void expand_words(const Frame* __restrict__ frames, i
     int fi = 0, y = 0, x0 = 0;
     if (c0 + t < n) {
       const uint2 e = q[c0 + t];
-      m = e.y;
+      m = group_mask<kGran>(e.y);
       decode_word(frames, nframes, e.x, fi, y, x0);
     }
     int total = 0;
@@ -827,7 +1136,7 @@ __device__ __forceinline__ void expand_words(const Frame* __restrict__ frames, i
       const bool valid = j < total;
       const uint32_t mk = sm.mask[k];
       const int bit = valid ? select_bit(mk, j - (sm.incl[k] - __popc(mk))) : 0;
-      body(valid, sm.fi[k], sm.x0[k] + bit, sm.y[k]);
+      body(valid, sm.fi[k], sm.x0[k] + kGran * bit, sm.y[k]);
     }
     __syncthreads();  // the shared state is refilled by the next chunk
   }
@@ -899,57 +1208,87 @@ __global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frame
                });
 }
 
-// bound_sparse_kernel (iteration >= 2): the bound test of each listed pixel
-// from its own 5x5 window of J (five column medians, their minimum, L+): the
-// same values as the sliding form. The warp merges its results per word and
-// writes them with one AND and one OR per plane and word (the words' other
-// bits are untouched, so warps sharing a word do not interfere).
+// bound_sparse_kernel (iteration >= 2): the bound test of the pixels listed in
+// q2 (within 2 px of a change), by groups of four pixels x .. x+3 that hold a
+// listed one: one thread forms the column medians of the eight columns x-2 ..
+// x+5 (rows and columns clamped at the frame's edges, as in the sliding pass),
+// then per pixel the minimum of five of them and L+: the sliding pass's
+// values. The whole group is rewritten (an unlisted pixel gets the value it
+// holds, its window being unchanged). The warp merges its groups per word and
+// writes them with one AND and one OR per plane and word, so warps sharing a
+// word touch disjoint bits.
 __global__ void __launch_bounds__(256) bound_sparse_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
                                                            Params p) {
   __shared__ ExpandSmem sm;
   float chot, clow;
   bound_consts(p, chot, clow);
   const int lane = threadIdx.x & 31;
-  expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q2), Q.n[kNB], sm,
-               [&](bool valid, int fi, int x, int y) {
-                 bool hot = false, act = false, lz = false;
-                 unsigned long long key = ~0ull;
-                 if (valid) {
-                   const Frame& f = frames[fi];
-                   float v[25];
-                   load_window<2>(f.out_clean, x, y, f.w, f.h, v);
-                   float mlow = INFINITY;
+  expand_words<4>(frames, nframes, reinterpret_cast<const uint2*>(Q.q2), Q.n[kNB], sm,
+                  [&](bool valid, int fi, int x0, int y) {
+                    uint32_t hb = 0, ab = 0, zb = 0, gm = 0;
+                    unsigned long long key = ~0ull;
+                    if (valid) {
+                      const Frame& f = frames[fi];
+                      const int w = f.w, h = f.h;
+                      const float* __restrict__ J = f.out_clean;
+                      float v[5][8];  // rows y-2 .. y+2, columns x0-2 .. x0+5
+                      const bool vec =
+                          x0 >= 4 && x0 + 8 <= w && (w & 3) == 0 && (reinterpret_cast<uintptr_t>(J) & 15u) == 0;
 #pragma unroll
-                   for (int dx = 0; dx < 5; ++dx) {
-                     const float col[5] = {v[dx], v[5 + dx], v[10 + dx], v[15 + dx], v[20 + dx]};
-                     mlow = fminf(mlow, sel_med5(col));
-                   }
-                   const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
-                   const float lp = lplus(v[12], v[7], v[17], v[11], v[13]);
-                   const float den = gain * (mlow > 0.f ? mlow : 0.f) + rn2;
-                   const float lhs = lp * lp * g2;
-                   act = lhs > clow * den;
-                   hot = lhs > chot * den;
-                   lz = lp == 0.f;
-                   key = (static_cast<unsigned long long>(fi) << 40) | (size_t(y) * f.wpr + (x >> 5));
-                 }
-                 const unsigned grp = __match_any_sync(0xffffffffu, key);
-                 const uint32_t bit = valid ? 1u << (x & 31) : 0u;
-                 const uint32_t m = __reduce_or_sync(grp, bit);
-                 const uint32_t hb = __reduce_or_sync(grp, hot ? bit : 0u);
-                 const uint32_t ab = __reduce_or_sync(grp, act ? bit : 0u);
-                 const uint32_t zb = __reduce_or_sync(grp, lz ? bit : 0u);
-                 if (valid && lane == __ffs(grp) - 1) {
-                   const Frame& f = frames[fi];
-                   const size_t wo = size_t(y) * f.wpr + (x >> 5);
-                   atomicAnd(f.hot + wo, ~(m & ~hb));
-                   atomicOr(f.hot + wo, hb);
-                   atomicAnd(f.act + wo, ~(m & ~ab));
-                   atomicOr(f.act + wo, ab);
-                   atomicAnd(f.lpz + wo, ~(m & ~zb));
-                   atomicOr(f.lpz + wo, zb);
-                 }
-               });
+                      for (int dy = 0; dy < 5; ++dy) {
+                        const float* __restrict__ r = J + size_t(clampi(y - 2 + dy, 0, h - 1)) * size_t(w);
+                        if (vec) {  // three aligned 16-byte loads: x0-4 .. x0+7
+                          const float4 a = __ldg(reinterpret_cast<const float4*>(r + x0 - 4));
+                          const float4 m = __ldg(reinterpret_cast<const float4*>(r + x0));
+                          const float4 c = __ldg(reinterpret_cast<const float4*>(r + x0 + 4));
+                          v[dy][0] = a.z; v[dy][1] = a.w;
+                          v[dy][2] = m.x; v[dy][3] = m.y; v[dy][4] = m.z; v[dy][5] = m.w;
+                          v[dy][6] = c.x; v[dy][7] = c.y;
+                        } else {
+#pragma unroll
+                          for (int c = 0; c < 8; ++c) v[dy][c] = __ldg(r + clampi(x0 - 2 + c, 0, w - 1));
+                        }
+                      }
+                      float cm[8];
+#pragma unroll
+                      for (int c = 0; c < 8; ++c) {
+                        const float col[5] = {v[0][c], v[1][c], v[2][c], v[3][c], v[4][c]};
+                        cm[c] = sel_med5(col);
+                      }
+                      const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
+#pragma unroll
+                      for (int i = 0; i < 4; ++i) {
+                        const float mlow = min3f(min3f(cm[i], cm[i + 1], cm[i + 2]), cm[i + 3], cm[i + 4]);
+                        const float lp = lplus(v[2][i + 2], v[1][i + 2], v[3][i + 2], v[2][i + 1], v[2][i + 3]);
+                        const float den = gain * (mlow > 0.f ? mlow : 0.f) + rn2;
+                        const float lhs = lp * lp * g2;
+                        ab |= uint32_t(lhs > clow * den) << i;
+                        hb |= uint32_t(lhs > chot * den) << i;
+                        zb |= uint32_t(lp == 0.f) << i;
+                      }
+                      const int sh = x0 & 31;
+                      gm = (15u << sh) & frame_word(x0 >> 5, w);
+                      ab = (ab << sh) & gm;
+                      hb = (hb << sh) & gm;
+                      zb = (zb << sh) & gm;
+                      key = (static_cast<unsigned long long>(fi) << 40) | (size_t(y) * f.wpr + (x0 >> 5));
+                    }
+                    const unsigned grp = __match_any_sync(0xffffffffu, key);
+                    const uint32_t m = __reduce_or_sync(grp, gm);
+                    const uint32_t hw = __reduce_or_sync(grp, hb);
+                    const uint32_t aw = __reduce_or_sync(grp, ab);
+                    const uint32_t zw = __reduce_or_sync(grp, zb);
+                    if (valid && lane == __ffs(grp) - 1) {
+                      const Frame& f = frames[fi];
+                      const size_t wo = size_t(y) * f.wpr + (x0 >> 5);
+                      atomicAnd(f.hot + wo, ~(m & ~hw));
+                      atomicOr(f.hot + wo, hw);
+                      atomicAnd(f.act + wo, ~(m & ~aw));
+                      atomicOr(f.act + wo, aw);
+                      atomicAnd(f.lpz + wo, ~(m & ~zw));
+                      atomicOr(f.lpz + wo, zw);
+                    }
+                  });
 }
 
 // The objlim test of candidate c: S'(c) / max(F/N, 0.01) > objlim (article
