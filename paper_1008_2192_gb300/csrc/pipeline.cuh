@@ -1085,10 +1085,36 @@ __device__ __forceinline__ void decode_word(const Frame* frames, int nframes, ui
 // Shared state of expand_words.
 struct ExpandSmem {
   uint32_t mask[kThreads];
+  uint32_t pm[kThreads];  // the entries' pixel masks (grouped expansion)
   int incl[kThreads];  // inclusive prefix of the masks' bit counts
   int fi[kThreads], y[kThreads], x0[kThreads];
   int ws[kThreads / 32 + 1];
 };
+
+// Rows y-R .. y+R and columns x0-R .. x0+3+R of a (clamped at the frame's
+// edges, as load_window) for a group of four pixels, x0 a multiple of 4: away
+// from the edges, three aligned 16-byte loads per row (x0-4 .. x0+7).
+template <int R>
+__device__ __forceinline__ void load_span(const float* __restrict__ a, int x0, int y, int w, int h,
+                                          float (&v)[2 * R + 1][4 + 2 * R]) {
+  static_assert(R >= 1 && R <= 4, "the 16-byte loads cover 4 columns either side");
+  const bool vec = x0 >= 4 && x0 + 8 <= w && (w & 3) == 0 && (reinterpret_cast<uintptr_t>(a) & 15u) == 0;
+#pragma unroll
+  for (int dy = 0; dy <= 2 * R; ++dy) {
+    const float* __restrict__ r = a + size_t(clampi(y - R + dy, 0, h - 1)) * size_t(w);
+    if (vec) {
+      const float4 A = __ldg(reinterpret_cast<const float4*>(r + x0 - 4));
+      const float4 M = __ldg(reinterpret_cast<const float4*>(r + x0));
+      const float4 C = __ldg(reinterpret_cast<const float4*>(r + x0 + 4));
+      const float s12[12] = {A.x, A.y, A.z, A.w, M.x, M.y, M.z, M.w, C.x, C.y, C.z, C.w};
+#pragma unroll
+      for (int c = 0; c < 4 + 2 * R; ++c) v[dy][c] = s12[4 - R + c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4 + 2 * R; ++c) v[dy][c] = __ldg(r + clampi(x0 - R + c, 0, w - 1));
+    }
+  }
+}
 
 // The mask of the kGran-pixel groups of word mask m that hold a set bit (bit i:
 // pixels kGran*i .. kGran*i + kGran-1).
@@ -1106,7 +1132,9 @@ __device__ __forceinline__ uint32_t group_mask(uint32_t m) {
 // block scan of the item counts, then one item per thread per round, found by
 // binary search in the prefix and a bit select in the item mask. Every thread
 // of the block runs every round and calls body(valid, frame, x, y) with x the
-// item's first pixel, so body may hold block-wide steps.
+// item's first pixel (grouped: body(valid, frame, x, y, bits), bits = the
+// listed pixels of the group, bit i for pixel x + i), so body may hold
+// block-wide steps.
 template <int kGran = 1, typename F>
 __device__ __forceinline__ void expand_words(const Frame* __restrict__ frames, int nframes, const uint2* __restrict__ q,
                                              unsigned int n, ExpandSmem& sm, F&& body) {
@@ -1117,6 +1145,7 @@ __device__ __forceinline__ void expand_words(const Frame* __restrict__ frames, i
     if (c0 + t < n) {
       const uint2 e = q[c0 + t];
       m = group_mask<kGran>(e.y);
+      if (kGran > 1) sm.pm[t] = e.y;
       decode_word(frames, nframes, e.x, fi, y, x0);
     }
     int total = 0;
@@ -1136,7 +1165,12 @@ __device__ __forceinline__ void expand_words(const Frame* __restrict__ frames, i
       const bool valid = j < total;
       const uint32_t mk = sm.mask[k];
       const int bit = valid ? select_bit(mk, j - (sm.incl[k] - __popc(mk))) : 0;
-      body(valid, sm.fi[k], sm.x0[k] + kGran * bit, sm.y[k]);
+      if constexpr (kGran == 1) {
+        body(valid, sm.fi[k], sm.x0[k] + bit, sm.y[k]);
+      } else {
+        const uint32_t bits = valid ? (sm.pm[k] >> (kGran * bit)) & ((1u << kGran) - 1u) : 0u;
+        body(valid, sm.fi[k], sm.x0[k] + kGran * bit, sm.y[k], bits);
+      }
     }
     __syncthreads();  // the shared state is refilled by the next chunk
   }
@@ -1195,17 +1229,38 @@ __global__ void __launch_bounds__(256) sp_kernel(const Frame* __restrict__ frame
                });
 }
 
-// m3_kernel: at QM3, med3 of J.
+// m3_kernel: at QM3, med3 of J, by groups of four pixels x0 .. x0+3 that hold
+// a listed one. The six columns x0-1 .. x0+4 of the rows y-1 .. y+1 are sorted
+// once; the median of a 3x3 window is then the median of three values: the
+// largest of its column minima, the median of its column medians and the
+// smallest of its column maxima (an exact selection of the fifth of nine).
 __global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k) {
   __shared__ ExpandSmem sm;
-  expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNM3], sm,
-               [&](bool valid, int fi, int x, int y) {
-                 if (!valid) return;
-                 const Frame& f = frames[fi];
-                 float v[9];
-                 load_window<1>(qsrc(f, k), x, y, f.w, f.h, v);
-                 f.mapM3[size_t(y) * f.w + x] = sel_med9(v);
-               });
+  expand_words<4>(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNM3], sm,
+                  [&](bool valid, int fi, int x0, int y, uint32_t bits) {
+                    if (!valid) return;
+                    const Frame& f = frames[fi];
+                    float v[3][6];
+                    load_span<1>(qsrc(f, k), x0, y, f.w, f.h, v);
+                    float lo[6], mi[6], hi[6];
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {  // sort the column: lo <= mi <= hi
+                      const float s0 = fminf(v[0][c], v[1][c]), s1 = fmaxf(v[0][c], v[1][c]);
+                      hi[c] = fmaxf(s1, v[2][c]);
+                      const float t = fminf(s1, v[2][c]);
+                      lo[c] = fminf(s0, t);
+                      mi[c] = fmaxf(s0, t);
+                    }
+                    float* __restrict__ out = f.mapM3 + size_t(y) * f.w + x0;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                      if (!((bits >> i) & 1u)) continue;
+                      const float a = max3f(lo[i], lo[i + 1], lo[i + 2]);
+                      const float b = fmaxf(fminf(mi[i], mi[i + 1]), fminf(fmaxf(mi[i], mi[i + 1]), mi[i + 2]));
+                      const float c = min3f(hi[i], hi[i + 1], hi[i + 2]);
+                      out[i] = fmaxf(fminf(a, b), fminf(fmaxf(a, b), c));
+                    }
+                  });
 }
 
 // bound_sparse_kernel (iteration >= 2): the bound test of the pixels listed in
@@ -1224,31 +1279,14 @@ __global__ void __launch_bounds__(256) bound_sparse_kernel(const Frame* __restri
   bound_consts(p, chot, clow);
   const int lane = threadIdx.x & 31;
   expand_words<4>(frames, nframes, reinterpret_cast<const uint2*>(Q.q2), Q.n[kNB], sm,
-                  [&](bool valid, int fi, int x0, int y) {
+                  [&](bool valid, int fi, int x0, int y, uint32_t) {
                     uint32_t hb = 0, ab = 0, zb = 0, gm = 0;
                     unsigned long long key = ~0ull;
                     if (valid) {
                       const Frame& f = frames[fi];
                       const int w = f.w, h = f.h;
-                      const float* __restrict__ J = f.out_clean;
                       float v[5][8];  // rows y-2 .. y+2, columns x0-2 .. x0+5
-                      const bool vec =
-                          x0 >= 4 && x0 + 8 <= w && (w & 3) == 0 && (reinterpret_cast<uintptr_t>(J) & 15u) == 0;
-#pragma unroll
-                      for (int dy = 0; dy < 5; ++dy) {
-                        const float* __restrict__ r = J + size_t(clampi(y - 2 + dy, 0, h - 1)) * size_t(w);
-                        if (vec) {  // three aligned 16-byte loads: x0-4 .. x0+7
-                          const float4 a = __ldg(reinterpret_cast<const float4*>(r + x0 - 4));
-                          const float4 m = __ldg(reinterpret_cast<const float4*>(r + x0));
-                          const float4 c = __ldg(reinterpret_cast<const float4*>(r + x0 + 4));
-                          v[dy][0] = a.z; v[dy][1] = a.w;
-                          v[dy][2] = m.x; v[dy][3] = m.y; v[dy][4] = m.z; v[dy][5] = m.w;
-                          v[dy][6] = c.x; v[dy][7] = c.y;
-                        } else {
-#pragma unroll
-                          for (int c = 0; c < 8; ++c) v[dy][c] = __ldg(r + clampi(x0 - 2 + c, 0, w - 1));
-                        }
-                      }
+                      load_span<2>(f.out_clean, x0, y, w, h, v);
                       float cm[8];
 #pragma unroll
                       for (int c = 0; c < 8; ++c) {
