@@ -3,7 +3,8 @@
 //
 // Detection (stages a-d) of iteration k:
 //   bound          L+ and the upper bound S+ of every pixel -> bit planes hot
-//                  (S+ > sigclip) and act (S+ > min(sigclip, sigfrac*sigclip));
+//                  (S+ > sigclip), act (S+ > min(sigclip, sigfrac*sigclip))
+//                  and lpz (L+ = 0, where S = 0 exactly);
 //   need           nsp = needS' = dilate5(hot) & act, needS = dilate5(nsp)
 //                  -> queues QS (S to compute) and QSP (S' to compute);
 //   s              at QS: m5, N, L+, S -> maps N, S;
@@ -29,11 +30,14 @@
 // where J changed within its radius since iteration k-1, and tests only the
 // candidates within 6 px of a change: a candidate farther away grows exactly
 // what it grew before, which M already holds. The changed pixels are those that
-// rep_write gave a new value; it marks, per cell of one word x kCH rows, the
-// smallest radius class (2, 4 or 6 px) that reaches into the cell. Validity
-// planes sval and m3val record where mapS/mapN and mapM3 hold current values;
-// S' is current on all of nsp (nsp and S' change only within 4 px). Iteration 1
-// treats every cell as changed.
+// the replacement gave a new value: it sets their bits in a changed-pixel plane
+// and marks, per cell of one word x kCH rows, the smallest radius class (2, 4
+// or 6 px) that reaches into the cell. The bound pass re-tests exactly the
+// pixels within 2 px of a changed one (d2, bound_sparse). Validity planes sval
+// and m3val record where mapS/mapN and mapM3 hold current values; S' is
+// current on all of nsp (nsp and S' change only within 4 px). Iteration 1
+// treats every cell as changed; from iteration kSegFrom on, the bit-plane
+// kernels walk only the listed segments that hold work.
 //
 // Replacement is exact in place: a flagged pixel with an unflagged window pixel
 // takes the lower median of its unflagged window pixels, which are I0 values
