@@ -932,26 +932,41 @@ int crb_clean_batch_host(crb_ctx* c, int n, const float* const* imgs, const int*
   if (n < 0 || (n > 0 && (!imgs || !ws || !hs || !out_cleans || !out_masks)))
     return fail(CRB_EINVAL, "invalid batch arrays");
   if (n == 0) return CRB_OK;
-  long long total = 0, largest = 0;
+  long long total = 0;
   for (int i = 0; i < n; ++i) {
     if (ws[i] < 1 || hs[i] < 1 || (long long)ws[i] * hs[i] >= (1LL << 31))
       return fail(CRB_EINVAL, "frame " + std::to_string(i) + ": sizes");
     if (!imgs[i] || !out_cleans[i] || !out_masks[i]) return fail(CRB_EINVAL, "frame " + std::to_string(i) + ": null");
     const long long px = (long long)ws[i] * hs[i];
     total += px;
-    largest = std::max(largest, px);
   }
-  // chunks of consecutive frames of about total/kStageChunks pixels (at least the largest frame)
-  const long long target = std::max(largest, (total + kStageChunks - 1) / kStageChunks);
+  // chunks of consecutive frames of about total/kStageChunks pixels, ramped at
+  // both ends (total/32, total/16): the first copy-in and the last copy-out
+  // overlap no other work, so they are kept short
+  const long long mid = (total + kStageChunks - 1) / kStageChunks;
+  auto px_of = [&](int i) { return (long long)ws[i] * hs[i]; };
+  // the tail: the last chunk up to total/32, the one before up to total/16 (a frame at least each)
+  std::vector<int> tail_first;  // first frames of the tail chunks, last chunk first
+  int end = n;
+  for (const long long t : {total / 32, total / 16}) {
+    int i = end - 1;
+    for (long long acc = px_of(i); i > 0 && acc + px_of(i - 1) <= t; --i) acc += px_of(i - 1);
+    if (i <= 0) break;
+    tail_first.push_back(i);
+    end = i;
+  }
   std::vector<int> first{0};
-  for (long long acc = 0, i = 0; i < n; ++i) {
-    const long long px = (long long)ws[i] * hs[i];
+  long long target = total / 32;  // then total/16, then total/kStageChunks
+  for (long long acc = 0, i = 0; i < end; ++i) {
+    const long long px = px_of(int(i));
     if (acc > 0 && acc + px > target) {
       first.push_back(int(i));
       acc = 0;
+      target = std::min(2 * target, mid);
     }
     acc += px;
   }
+  for (auto it = tail_first.rbegin(); it != tail_first.rend(); ++it) first.push_back(*it);
   first.push_back(n);
   auto frame_bytes = [&](int i) { return align256(size_t(ws[i]) * hs[i] * 4) * 2 + align256(size_t(ws[i]) * hs[i]); };
   size_t need = 0;
