@@ -85,7 +85,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="crb", choices=["crb", "reference"])
     ap.add_argument("--workload", default="batch64",
-                    choices=["batch64", "single4096", "single800", "mosaic16384", "triple4096", "serving"])
+                    choices=["batch64", "single4096", "single800", "mosaic16384", "triple4096", "serving",
+                             "poisson750", "poisson_batch64"])
     ap.add_argument("--rates", default="50,200,500,1000,2000", help="serving: arrival rates, frames/s")
     ap.add_argument("--serve-frames", type=int, default=0, help="serving: frames per rate (0: ~4 s of arrivals)")
     ap.add_argument("--tile-shape", type=int, default=0)
@@ -289,6 +290,9 @@ def run_reference(args):
         return
     import oracle
     from synth import workloads as wl
+    if args.workload.startswith("poisson"):
+        run_reference_poisson(args)
+        return
     recipes, desc = recipes_for(args.workload)
     threads = os.cpu_count() or 1
     oracle.set_threads(threads)
@@ -315,6 +319,129 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# FP64 multiplies of the POISSON work function: two per uniform drawn (its scaling by 2^-53 and the
+# product), and 13 in the Horner polynomial plus 3 in the reduction of e^-mu per pixel.
+POISSON_FP64_EXP = 16
+# Nominal dense FP64 rate of a GB300 (no measured figure): 1.25 TFLOP/s counting a multiply-add as two
+# operations, i.e. 0.625 T multiplies per second.
+POISSON_FP64_PEAK = 0.625e12
+
+
+def run_poisson(args):
+    """The POISSON work function (Sec. 6.3.2): the paper's 750x750 image of 24.3, or 64 frames of the batch
+    sizes at the same mean; device buffers, CUDA events; the oracle timed on the host cores beside it."""
+    import torch
+    import oracle
+    from paper_1008_2192_gb300 import poisson_batch_into
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    mu = 24.3
+    if args.workload == "poisson750":
+        sizes, desc = [(750, 750)], "the paper's POISSON test image: 750x750, every pixel 24.3"
+    else:
+        sizes = [(800, 800)] * 16 + [(1024, 1024)] * 16 + [(2048, 4096)] * 16 + [(4096, 4096)] * 16
+        desc = "64 frames of the batch sizes (16x800x800, 16x1024x1024, 16x2048x4096, 16x4096x4096), every pixel 24.3"
+    imgs = [torch.full((h, w), mu, dtype=torch.float32, device="cuda") for (w, h) in sizes]
+    outs = [torch.empty_like(a) for a in imgs]
+    seeds = list(range(len(imgs)))
+    npix = sum(w * h for (w, h) in sizes)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        poisson_batch_into(imgs, outs, seeds)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    draws = sum(float(o.double().sum().item()) + o.numel() for o in outs)  # k + 1 uniforms per pixel
+    fp64 = 2 * draws + POISSON_FP64_EXP * npix
+    # end to end: pinned host input, copies in and out inside the timed region
+    h_in = [a.cpu().pin_memory() for a in imgs]
+    h_out = [torch.empty(a.shape, dtype=torch.float32).pin_memory() for a in imgs]
+
+    def e2e_step():
+        for hi, di in zip(h_in, imgs):
+            di.copy_(hi, non_blocking=True)
+        step()
+        for ho, do in zip(h_out, outs):
+            ho.copy_(do, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k2 = max(2, min(args.steps, 20))
+    a.record(stream)
+    for _ in range(k2):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = a.elapsed_time(b) / k2
+    # the oracle on the host cores: the 750x750 image (the first frame)
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    h0 = np.full((750, 750), mu, np.float32)
+    oracle.poisson(h0, 0)
+    t0 = time.perf_counter()
+    reps = 0
+    while time.perf_counter() - t0 < 3.0:
+        oracle.poisson(h0, reps)
+        reps += 1
+    cpu = reps * h0.size / (time.perf_counter() - t0) / 1e6
+    achieved = fp64 / (ms * 1e-3)
+    line = {"metric": "Mpix/s of the POISSON work function (mean 24.3, 1 GB300)", "value": npix / (ms * 1e-3) / 1e6,
+            "unit": "Mpix/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "frames": len(sizes), "mpix_per_step": npix / 1e6,
+                       "l2": "inputs below L2" if npix * 8 < 120e6 else "inputs above L2, no flush"},
+            "gpu_launches": args.steps * ((len(sizes) + 255) // 256), "clocks": clk,
+            "roofline": {"bound": "alu", "kernel": "poisson_kernel", "achieved": achieved / 1e12,
+                         "peak": POISSON_FP64_PEAK / 1e12, "unit": "T FP64 multiplies/s",
+                         "frac": achieved / POISSON_FP64_PEAK, "traffic": None,
+                         "peak_source": "nominal FP64 rate (1.25 TFLOP/s counting a multiply-add as two)",
+                         "achieved_is": "2 FP64 multiplies per uniform drawn (counted from the deviates) + 16 per "
+                                        "pixel for e^-mu, / device time per step"},
+            "e2e": {"value": npix / (e2e_ms * 1e-3) / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": npix * 4,
+                    "d2h_bytes_per_step": npix * 4, "api": "crb_poisson_batch with pinned host copies around it"},
+            "cpu_baseline": {"value": cpu, "unit": "Mpix/s", "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"the 750x750 image of 24.3, {reps} calls in ~3 s"},
+            "paper_context": "CRBLASTER with POISSON on the 750x750 image: 79.738 s on one TILE64 tile "
+                             "(0.0071 Mpix/s), Sec. 6.3.2"}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_poisson(args):
+    """The reference arm of the POISSON workloads: the oracle on the 750x750 image of 24.3 per step."""
+    import oracle
+    oracle.set_threads(os.cpu_count() or 1)
+    img = np.full((750, 750), 24.3, np.float32)
+    for i in range(max(0, min(args.warmup, 1))):
+        oracle.poisson(img, i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle.poisson(img, i)
+    dt = time.perf_counter() - t0
+    value = args.steps * img.size / dt / 1e6
+    line = {"impl": "reference", "metric": "Mpix/s of the POISSON work function (mean 24.3, 1 GB300)",
+            "value": value, "unit": "Mpix/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "each step: the 750x750 image of 24.3 (the paper's POISSON test image)"},
+            "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": "the 750x750 image of 24.3 per step"},
+            "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -322,6 +449,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args)
+        return
+    if args.workload.startswith("poisson"):
+        run_poisson(args)
         return
     import torch
     import torch.distributed as dist

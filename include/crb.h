@@ -270,6 +270,36 @@ int crb_server_stats(crb_server* srv, long long* out, int max);
 /* Stops the worker after the waves in flight complete and frees the server. */
 void crb_server_destroy(crb_server* srv);
 
+/* ---- The POISSON work function (Sec. 6.3.2) ---------------------------------
+ * The paper measures the cost of its framework by swapping L.A.Cosmic for a
+ * work function with a known, nearly equal load per pixel and no overlap
+ * regions: each output pixel is a Poisson deviate whose mean is the input
+ * pixel, drawn with Knuth's multiplicative method (Algorithm Q): uniforms are
+ * multiplied until the product falls below e^-mu; the number of factors taken
+ * before that is the deviate, so the cost per pixel grows linearly with mu.
+ *
+ * img, out: device, w*h floats, row-major; out receives the deviates (integer
+ * values). out may equal img (each output depends only on its own input) but
+ * must not overlap it otherwise. The uniforms come from SplitMix64 (golden
+ * gamma 0x9e3779b97f4a7c15, Stafford's Mix13 finaliser) used as a
+ * counter-based generator, value(s, j) = mix(s + (j+1)*gamma): pixel p
+ * (row-major index in its frame) draws from the stream keyed by value(seed, p),
+ * its j-th uniform being the top 53 bits of value(key, j) times 2^-53. e^-mu is
+ * formed in double by fixed steps: -mu = n ln2 + r (ln2 rounded to double and
+ * split at its low 20 significand bits), the Taylor polynomial of e^r to degree
+ * 13 by Horner's rule with coefficients 1/i! by repeated division, times 2^n.
+ * mu <= 0 or NaN gives 0; mu above 700 is taken as 700; at most 4096 factors
+ * are drawn. Asynchronous on `stream`; no allocation. CRB_EINVAL for null
+ * pointers or sizes outside 1 <= w, h and w*h < 2^31, CRB_ECUDA if the launch
+ * fails. */
+int crb_poisson(const float* img, int w, int h, uint64_t seed, float* out, cudaStream_t stream);
+
+/* The POISSON work function on n frames in one launch per 256 frames: frame i
+ * (imgs[i], ws[i] x hs[i], device) with seed seeds[i] into outs[i]; arrays in
+ * host memory. Each frame's result equals crb_poisson's with the same seed. */
+int crb_poisson_batch(int n, const float* const* imgs, const int* ws, const int* hs, const uint64_t* seeds,
+                      float* const* outs, cudaStream_t stream);
+
 /* Message of the last error on this host thread ("" if none). */
 const char* crb_last_error(void);
 const char* crb_strerror(int status);

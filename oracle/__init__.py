@@ -1,6 +1,7 @@
 """ORACLE -- TEST INFRASTRUCTURE ONLY.
 
-Plain CPU L.A.Cosmic (``lacosmic.cpp``) used to check the CUDA library. Only
+Plain CPU L.A.Cosmic (``lacosmic.cpp``) and the POISSON work function
+(``poisson.cpp``) used to check the CUDA library. Only
 the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
 leg may import this package; the product path never does.
 
@@ -21,8 +22,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_POISSON_PATH = os.path.join(_HERE, "_build", "libpoisson.so")
 _lock = threading.Lock()
 _lib = None
+_plib = None
 
 MAP_NAMES = ("m5", "lplus", "noise", "s", "sprime", "m3", "f", "r", "cand", "g1", "g2")
 
@@ -249,3 +252,55 @@ def clean(I0, params: Params, niter: int = 4, *, precision: str = "f64",
         raise ValueError("oracle_clean rejected its arguments")
     return CleanResult(out, mask, [int(counts[2 * k]) for k in range(niter)],
                        [int(counts[2 * k + 1]) for k in range(niter)], fr)
+
+
+# --- POISSON work function (Sec. 6.3.2) -------------------------------------------------------
+
+
+def build_poisson(force: bool = False) -> str:
+    """Compile ``poisson.cpp`` into ``_build/libpoisson.so``."""
+    return build(force, src=os.path.join(_HERE, "poisson.cpp"), out=_POISSON_PATH)
+
+
+def _load_poisson():
+    global _plib
+    with _lock:
+        if _plib is None:
+            lib = ctypes.CDLL(build_poisson())
+            lib.oracle_exp_neg.restype = ctypes.c_double
+            lib.oracle_exp_neg.argtypes = [ctypes.c_double]
+            lib.oracle_stream_value.restype = ctypes.c_uint64
+            lib.oracle_stream_value.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+            lib.oracle_algorithm_q.restype = ctypes.c_int
+            lib.oracle_algorithm_q.argtypes = [ctypes.c_double, ctypes.c_void_p, ctypes.c_int]
+            lib.oracle_poisson.restype = ctypes.c_int
+            lib.oracle_poisson.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                           ctypes.c_void_p]
+            _plib = lib
+    return _plib
+
+
+def exp_neg(mu: float) -> float:
+    """e^-mu by the fixed double-precision steps the work function uses (0 <= mu <= 700)."""
+    return float(_load_poisson().oracle_exp_neg(float(mu)))
+
+
+def stream_value(s: int, j: int) -> int:
+    """The j-th value of the counter-based SplitMix64 stream with key s."""
+    return int(_load_poisson().oracle_stream_value(s & (2**64 - 1), j & (2**64 - 1)))
+
+
+def algorithm_q(mu: float, u) -> int:
+    """Algorithm Q on the given uniforms; -1 if it needs more of them."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    return int(_load_poisson().oracle_algorithm_q(float(mu), u.ctypes.data, int(u.size)))
+
+
+def poisson(img, seed: int) -> np.ndarray:
+    """The POISSON work function on one frame: a deviate of mean img[p] per pixel (float32)."""
+    a = _f32(img)
+    h, w = a.shape
+    out = np.empty_like(a)
+    if _load_poisson().oracle_poisson(a.ctypes.data, w, h, seed & (2**64 - 1), out.ctypes.data) != 0:
+        raise ValueError("oracle_poisson rejected its arguments")
+    return out

@@ -59,6 +59,8 @@ SIGNATURES = {
     "crb_server_destroy": (None, [_vp]),
     "crb_num_tile_shapes": (_ci, []),
     "crb_tile_shape": (_ci, [_ci, _PI, _PI]),
+    "crb_poisson": (_ci, [_vp, _ci, _ci, ctypes.c_uint64, _vp, _vp]),
+    "crb_poisson_batch": (_ci, [_ci, _PP, _PI, _PI, ctypes.POINTER(ctypes.c_uint64), _PP, _vp]),
     "crb_last_error": (ctypes.c_char_p, []),
     "crb_strerror": (ctypes.c_char_p, [_ci]),
 }

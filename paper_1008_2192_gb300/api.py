@@ -195,6 +195,42 @@ def alu_peak(stream=None):
     return a.value, b.value
 
 
+def poisson_into(img, out, seed, stream=None):
+    """The POISSON work function (crb_poisson): out[p] = a Poisson deviate of mean img[p]."""
+    _check_img(img)
+    _check_img(out, "out")
+    if out.shape != img.shape:
+        raise ValueError("out must have the shape of img")
+    h, w = img.shape
+    check(_lib.load().crb_poisson(_ptr(img), w, h, ctypes.c_uint64(seed & (2**64 - 1)), _ptr(out),
+                                  _stream(stream)), "crb_poisson")
+    return out
+
+
+def poisson(img, seed, stream=None):
+    """The POISSON work function into a new tensor."""
+    return poisson_into(img, torch.empty_like(img), seed, stream)
+
+
+def poisson_batch_into(imgs, outs, seeds, stream=None):
+    """crb_poisson_batch: frame i with seed seeds[i] into outs[i]."""
+    n = len(imgs)
+    if len(outs) != n or len(seeds) != n:
+        raise ValueError("imgs, outs and seeds must have the same length")
+    for a, o in zip(imgs, outs):
+        _check_img(a)
+        _check_img(o, "out")
+        if o.shape != a.shape:
+            raise ValueError("each out must have the shape of its img")
+    P = ctypes.c_void_p * n
+    I = ctypes.c_int * n
+    rc = _lib.load().crb_poisson_batch(
+        n, P(*[a.data_ptr() for a in imgs]), I(*[a.shape[1] for a in imgs]), I(*[a.shape[0] for a in imgs]),
+        (ctypes.c_uint64 * n)(*[s & (2**64 - 1) for s in seeds]), P(*[o.data_ptr() for o in outs]), _stream(stream))
+    check(rc, "crb_poisson_batch")
+    return outs
+
+
 class Server:
     """Continuous-batching server (crb_server_*): submit device frames, poll finished tags."""
 

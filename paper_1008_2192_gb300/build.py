@@ -1,6 +1,6 @@
 """Build of the CUDA library (in-tree, sm_103a only).
 
-Generates the selection-network header and compiles ``csrc/crb.cu`` into
+Generates the selection-network header and compiles ``csrc/*.cu`` into
 ``_build/libcrb.so`` with nvcc. No torch extension machinery is involved.
 """
 
@@ -51,6 +51,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
                "-I", os.path.join(ROOT, "include"), "-I", GEN,
                os.path.join(CSRC, "crb.cu"), os.path.join(CSRC, "noalloc.cu"), os.path.join(CSRC, "serve.cu"),
+               os.path.join(CSRC, "poisson.cu"),
                "-o", tmp]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
