@@ -62,7 +62,15 @@ __device__ __forceinline__ uint64_t mix13(uint64_t z) {
 
 __device__ __forceinline__ uint64_t stream_value(uint64_t s, uint64_t j) { return mix13(s + (j + 1) * kGamma); }
 
-__device__ __forceinline__ double uniform53(uint64_t v) { return __dmul_rn(__ull2double_rn(v >> 11), 0x1.0p-53); }
+// (v >> 11) * 2^-53, built from its bits with integer operations (the value
+// is exact either way): the FP64 pipe is left to the product.
+__device__ __forceinline__ double uniform53(uint64_t v) {
+  const uint64_t m = v >> 11;
+  if (m == 0) return 0.0;
+  const int e = 63 - __clzll((long long)m);  // top bit of m, 0 .. 52
+  const uint64_t frac = (m << (52 - e)) & ((uint64_t(1) << 52) - 1);
+  return __longlong_as_double((long long)((uint64_t(e - 53 + 1023) << 52) | frac));
+}
 
 __device__ __forceinline__ double exp_neg(double mu, const PLaunch& P) {
   const double x = -mu;
@@ -88,12 +96,15 @@ __global__ void __launch_bounds__(256) poisson_kernel(const __grid_constant__ PL
     int k = 0;
     if (mu > 0.0) {
       mu = fmin(mu, kMuMax);
-      const double L = exp_neg(mu, P);
+      // q and e^-mu are non-negative doubles, which order as their bit patterns
+      const long long L = __double_as_longlong(exp_neg(mu, P));
       const uint64_t key = stream_value(f.seed, uint64_t(p));
-      double q = uniform53(stream_value(key, 0));
-      while (q >= L && k < kQMax) {
+      uint64_t ctr = key + kGamma;  // key + (j + 1) * gamma for draw j
+      double q = uniform53(mix13(ctr));
+      while (__double_as_longlong(q) >= L && k < kQMax) {
         ++k;
-        q = __dmul_rn(q, uniform53(stream_value(key, uint64_t(k))));
+        ctr += kGamma;
+        q = __dmul_rn(q, uniform53(mix13(ctr)));
       }
     }
     f.out[p] = float(k);
