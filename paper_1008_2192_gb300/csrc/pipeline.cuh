@@ -119,16 +119,6 @@ __device__ __forceinline__ int frame_of_block(const Frame* frames, int nframes, 
   return lo;
 }
 
-// frame of global cell c (frames sorted by first cell)
-__device__ __forceinline__ int frame_of_cell(const Frame* frames, int nframes, long long c) {
-  int lo = 0, hi = nframes - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (frames[mid].cell0 <= c) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
 // frame of strip u (frames sorted by first strip)
 __device__ __forceinline__ int frame_of_unit(const Frame* frames, int nframes, long long u) {
   int lo = 0, hi = nframes - 1;
@@ -141,33 +131,6 @@ __device__ __forceinline__ int frame_of_unit(const Frame* frames, int nframes, l
 
 constexpr int kBW = 8;   // words (32 px each) per block row: one warp per word column
 constexpr int kBH = 32;  // rows per block
-
-// Appends, for each lane's word `v` at (wc, y) of frame f, the set bits as
-// global pixel indices to queue q (counter *n); one atomic per warp. All 32
-// lanes call it.
-__device__ __forceinline__ void warp_emit(uint32_t v, const Frame& f, int wc, int y, uint32_t* q,
-                                          unsigned int* n) {
-  const int lane = threadIdx.x & 31;
-  const int c = __popc(v);
-  int x = c;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += t;
-  }
-  const int total = __shfl_sync(0xffffffffu, x, 31);
-  if (total == 0) return;
-  unsigned int base = 0;
-  if (lane == 0) base = atomicAdd(n, (unsigned int)total);
-  base = __shfl_sync(0xffffffffu, base, 0);
-  unsigned int o = base + unsigned(x - c);
-  const uint32_t row = uint32_t(f.pix0 + (long long)y * f.w + 32 * wc);
-  while (v) {
-    const int bb = __ffs(v) - 1;
-    v &= v - 1u;
-    q[o++] = row + bb;
-  }
-}
 
 // Appends g to queue q from divergent code: one atomic per group of lanes that
 // arrive together.
