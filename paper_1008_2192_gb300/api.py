@@ -29,15 +29,19 @@ def _check_img(t, name="img"):
         raise ValueError(f"{name} must be a contiguous 2-D float32 CUDA tensor")
 
 
+# crb_options.pipeline: "auto" picks by the pixels of each call (queue from 6 Mpix on)
+PIPELINES = {"auto": 0, "tile": 1, "queue": 2}
+
+
 class Cleaner:
     """One cleaning context (crb_create_ex). Not thread-safe; use one per thread."""
 
     def __init__(self, gain=7.0, readnoise=5.0, sigclip=4.5, sigfrac=0.5, objlim=1.0, niter=4, *,
                  objlim_form=0, early_exit=False, tile_shape=0, use_graphs=False, profile=False,
-                 fusion=True, pipeline="queue"):
+                 fusion=True, pipeline="auto"):
         lib = _lib.load()
         opt = _lib.crb_options(int(objlim_form), int(bool(early_exit)), int(tile_shape), int(bool(use_graphs)),
-                               int(bool(profile)), int(not fusion), 0 if pipeline == "queue" else 1)
+                               int(bool(profile)), int(not fusion), PIPELINES[pipeline])
         h = lib.crb_create_ex(gain, readnoise, sigclip, sigfrac, objlim, int(niter), ctypes.byref(opt))
         if not h:
             raise ValueError("crb_create_ex: " + lib.crb_last_error().decode())

@@ -30,9 +30,10 @@ def scene(w, h, seed=0):
                        ncr=max(1, int(n * synth.CR_DENSITY * 3)))
 
 
-@pytest.fixture(scope="module")
-def cl():
-    c = Cleaner(niter=4)
+@pytest.fixture(scope="module", params=["queue", "auto"])
+def cl(request):
+    """The queue pipeline, and the default choice by call size (the tile pipeline below 6 Mpix)."""
+    c = Cleaner(niter=4, pipeline=request.param)
     yield c
     c.close()
 
@@ -153,7 +154,7 @@ def test_batch_equals_single(cl):
     outs, masks = cl.clean_batch([dev(a) for a in imgs], gains, rns)
     cl.sync()
     for i, a in enumerate(imgs):
-        ci = Cleaner(gain=gains[i], readnoise=rns[i], niter=4)
+        ci = Cleaner(gain=gains[i], readnoise=rns[i], niter=4, pipeline="queue")
         o, m = gpu_clean(ci, a)
         assert np.array_equal(host(outs[i]), o) and np.array_equal(host(masks[i]), m), i
         if a.size <= 400_000:
@@ -243,22 +244,37 @@ def test_launch_counts(niter):
     on the queue pipeline, plus the segment list of each iteration from the third on, and 1 upload +
     niter + 1 on the fused tile pipeline."""
     img = scene(120, 90, seed=9)
-    cq = Cleaner(niter=niter)
+    cq = Cleaner(niter=niter, pipeline="queue")
     gpu_clean(cq, img)
     assert cq.last_launches() == 2 + 12 + 14 * (niter - 1) + max(0, niter - 2) + 1
     ct = Cleaner(niter=niter, pipeline="tile")
     gpu_clean(ct, img)
     assert ct.last_launches() == 1 + niter + 1
+    ca = Cleaner(niter=niter)  # automatic: tiles for a frame this small
+    gpu_clean(ca, img)
+    assert ca.last_launches() == 1 + niter + 1
 
 
+def test_auto_takes_the_queue_pipeline_for_large_calls():
+    """From 6,000,000 pixels per call the automatic choice is the queue pipeline (59 launches at niter 4)."""
+    img = synth.frame(2048, 3072, seed=3)
+    ca = Cleaner(niter=4)
+    out, mask = gpu_clean(ca, img)
+    assert ca.last_launches() == 2 + 12 + 14 * 3 + 2 + 1
+    ct = Cleaner(niter=4, pipeline="tile")
+    o2, m2 = gpu_clean(ct, img)
+    assert np.array_equal(out, o2) and np.array_equal(mask, m2)
+
+
+@pytest.mark.parametrize("pipeline", ["queue", "auto"])
 @pytest.mark.parametrize("pinned", [True, False], ids=["pinned", "pageable"])
-def test_batch_host_equals_device_batch(pinned):
+def test_batch_host_equals_device_batch(pinned, pipeline):
     """crb_clean_batch_host (host buffers, chunked copies overlapping the cleans) gives crb_clean_batch's
     results, call after call (the staging slots are reused)."""
     rng = np.random.default_rng(3)
     sizes = [(300, 200), (64, 1), (517, 333), (1, 40), (256, 256), (800, 600), (33, 97), (1024, 512), (90, 90)]
-    c_dev = Cleaner(niter=4)
-    c_host = Cleaner(niter=4)
+    c_dev = Cleaner(niter=4, pipeline=pipeline)
+    c_host = Cleaner(niter=4, pipeline=pipeline)
     for rep in range(2):
         imgs = [synth.frame(w, h, seed=20 + rep, index=i) for i, (w, h) in enumerate(sizes)]
         gains = [float(np.float32(rng.uniform(1, 7))) for _ in sizes]
