@@ -186,8 +186,9 @@ int crb_last_work(crb_ctx* ctx, long long* out, int max_iter);
 /* Kernel launches the last crb_clean / crb_clean_batch / crb_iterate enqueued
  * (memsets and copies not counted; a graph replay counts its kernels). The
  * queue pipeline launches 2 descriptor uploads, 12 kernels in iteration 1, 14
- * in each later one and the mask kernel; the fused tile pipeline 1 upload and
- * niter + 1 kernels. -1 for a NULL context. */
+ * in each later one (15 from the third on, with the segment list) and the
+ * mask kernel; the fused tile pipeline 1 upload and niter + 1 kernels.
+ * -1 for a NULL context. */
 int crb_last_launches(const crb_ctx* ctx);
 
 /* One iteration from an explicit state, for stage-by-stage checks:
@@ -262,8 +263,9 @@ int crb_server_submit(crb_server* srv, const float* img, int w, int h, float gai
 int crb_server_poll(crb_server* srv, uint64_t* done_tags, double* latency_s, int* status, int max, int block_ms);
 
 /* Device bytes a w x h frame counts against the server budget: 9 per pixel of
- * the caller's buffers, 36 per pixel of workspace, 9 bit planes and 20 bytes
- * per cell of 32 x 8 pixels (0 for invalid sizes). */
+ * the caller's buffers, 36 per pixel of workspace (4 float maps, 5 queue
+ * entries), 12 bit planes, 8 bytes per cell of 32 x 8 pixels and 12 per
+ * segment of 32 x 32 pixels (0 for invalid sizes). */
 size_t crb_server_frame_bytes(int w, int h);
 
 /* Counters: submitted, done, waves launched, largest wave, rejected submissions,
