@@ -1143,8 +1143,9 @@ __device__ __forceinline__ void expand_words(const Frame* __restrict__ frames, i
   }
 }
 
-// s_kernel: at QS, m5 (floored), N, L+ and S of J.
-__global__ void __launch_bounds__(256) s_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k) {
+// s_kernel: at QS, m5 (floored), N, L+ and S of J. Five blocks per SM (48
+// registers) hide more of the window loads' latency than four.
+__global__ void __launch_bounds__(256, 5) s_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k) {
   __shared__ ExpandSmem sm;
   expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNS], sm,
                [&](bool valid, int fi, int x, int y) {
