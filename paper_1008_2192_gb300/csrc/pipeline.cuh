@@ -94,7 +94,7 @@ enum : int {
 // QS, QSP, QM3 and QT hold word entries: (global word index, mask of the
 // word's pixels), one per word with a set bit, so that the bit-plane kernels
 // write one entry per word; the kernels that use them expand the masks into
-// one pixel per thread (expand_words).
+// one pixel (or group of pixels) per thread (expand_words).
 struct Queues {
   uint32_t* q0;     // QS, then QM3, then the candidates, then the replacement values (as float)
   uint32_t* q1;     // QSP, then the open tests, then the replacement queue
@@ -1049,15 +1049,6 @@ __device__ __forceinline__ void decode_word(const Frame* frames, int nframes, ui
   x0 = 32 * int(lw - uint32_t(y) * wpr);
 }
 
-// Shared state of expand_words.
-struct ExpandSmem {
-  uint32_t mask[kThreads];
-  uint32_t pm[kThreads];  // the entries' pixel masks (grouped expansion)
-  int incl[kThreads];  // inclusive prefix of the masks' bit counts
-  int fi[kThreads], y[kThreads], x0[kThreads];
-  int ws[kThreads / 32 + 1];
-};
-
 // Rows y-R .. y+R and columns x0-R .. x0+3+R of a (clamped at the frame's
 // edges, as load_window) for a group of four pixels, x0 a multiple of 4: away
 // from the edges, three aligned 16-byte loads per row (x0-4 .. x0+7).
@@ -1095,59 +1086,108 @@ __device__ __forceinline__ uint32_t group_mask(uint32_t m) {
 }
 
 // Expands a queue of n word entries into items of kGran pixels (1: pixels; 4:
-// the groups of four with a listed pixel): per chunk of kThreads entries, a
-// block scan of the item counts, then one item per thread per round, found by
-// binary search in the prefix and a bit select in the item mask. Every thread
-// of the block runs every round and calls body(valid, frame, x, y) with x the
-// item's first pixel (grouped: body(valid, frame, x, y, bits), bits = the
-// listed pixels of the group, bit i for pixel x + i), so body may hold
-// block-wide steps.
+// the groups of four with a listed pixel), one warp at a time: the warp takes
+// 32 entries, scans their item counts across its lanes, then hands one item
+// per lane per round, found by a binary search over the lanes' prefixes and a
+// bit select in the entry's item mask. There is no block barrier, so a warp
+// waiting on its loads holds back no other. Every lane of the warp runs every
+// round and calls body(valid, frame, x, y) with x the item's first pixel
+// (grouped: body(valid, frame, x, y, bits), bits = the listed pixels of the
+// group, bit i for pixel x + i), so body may hold warp-wide steps.
 template <int kGran = 1, typename F>
 __device__ __forceinline__ void expand_words(const Frame* __restrict__ frames, int nframes, const uint2* __restrict__ q,
-                                             unsigned int n, ExpandSmem& sm, F&& body) {
-  const int t = threadIdx.x;
-  for (unsigned int c0 = blockIdx.x * kThreads; c0 < n; c0 += gridDim.x * kThreads) {  // whole blocks
-    uint32_t m = 0;
+                                             unsigned int n, F&& body) {
+  const int lane = threadIdx.x & 31;
+  const unsigned int wpb = blockDim.x >> 5;
+  for (unsigned int c0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * 32u; c0 < n; c0 += gridDim.x * wpb * 32u) {
+    uint32_t m = 0, pm = 0;
     int fi = 0, y = 0, x0 = 0;
-    if (c0 + t < n) {
-      const uint2 e = q[c0 + t];
+    if (c0 + lane < n) {
+      const uint2 e = q[c0 + lane];
+      pm = e.y;
       m = group_mask<kGran>(e.y);
-      if (kGran > 1) sm.pm[t] = e.y;
       decode_word(frames, nframes, e.x, fi, y, x0);
     }
-    int total = 0;
-    const int ex = block_excl_scan(__popc(m), sm.ws, total);
-    sm.mask[t] = m;
-    sm.incl[t] = ex + __popc(m);
-    sm.fi[t] = fi;
-    sm.y[t] = y;
-    sm.x0[t] = x0;
-    __syncthreads();
-    for (int r0 = 0; r0 < total; r0 += kThreads) {
-      const int j = r0 + t;
+    int incl = __popc(m);  // inclusive prefix of the item counts over the lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int r0 = 0; r0 < total; r0 += 32) {
+      const int j = r0 + lane;
       int k = 0;  // first entry whose inclusive prefix exceeds j
 #pragma unroll
-      for (int s = kThreads / 2; s >= 1; s >>= 1)
-        if (sm.incl[k + s - 1] <= j) k += s;
+      for (int s = 16; s >= 1; s >>= 1)
+        if (__shfl_sync(0xffffffffu, incl, k + s - 1) <= j) k += s;
       const bool valid = j < total;
-      const uint32_t mk = sm.mask[k];
-      const int bit = valid ? select_bit(mk, j - (sm.incl[k] - __popc(mk))) : 0;
+      const uint32_t mk = __shfl_sync(0xffffffffu, m, k);
+      const int ik = __shfl_sync(0xffffffffu, incl, k);
+      const int fk = __shfl_sync(0xffffffffu, fi, k), yk = __shfl_sync(0xffffffffu, y, k);
+      const int xk = __shfl_sync(0xffffffffu, x0, k);
+      const int bit = valid ? select_bit(mk, j - (ik - __popc(mk))) : 0;
       if constexpr (kGran == 1) {
-        body(valid, sm.fi[k], sm.x0[k] + bit, sm.y[k]);
+        body(valid, fk, xk + bit, yk);
       } else {
-        const uint32_t bits = valid ? (sm.pm[k] >> (kGran * bit)) & ((1u << kGran) - 1u) : 0u;
-        body(valid, sm.fi[k], sm.x0[k] + kGran * bit, sm.y[k], bits);
+        const uint32_t pk = __shfl_sync(0xffffffffu, pm, k);
+        const uint32_t bits = valid ? (pk >> (kGran * bit)) & ((1u << kGran) - 1u) : 0u;
+        body(valid, fk, xk + kGran * bit, yk, bits);
       }
     }
-    __syncthreads();  // the shared state is refilled by the next chunk
   }
 }
 
-// s_kernel: at QS, m5 (floored), N, L+ and S of J. Five blocks per SM (48
-// registers) hide more of the window loads' latency than four.
-__global__ void __launch_bounds__(256, 5) s_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k) {
-  __shared__ ExpandSmem sm;
-  expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNS], sm,
+// Per-warp staging of NL lists in shared memory: a warp adds its lanes' entries
+// without an atomic, and moves a list to global memory with one atomic when it
+// would overflow and at the end (flush). Warp-wide calls; no block barrier.
+template <int NL, int CAP>
+struct WarpLists {
+  uint32_t v[kThreads / 32][NL][CAP];
+  unsigned int n[kThreads / 32][NL];
+
+  __device__ __forceinline__ void init() {
+    if ((threadIdx.x & 31) < NL) n[threadIdx.x >> 5][threadIdx.x & 31] = 0u;
+    __syncwarp();
+  }
+
+  __device__ __forceinline__ void flush_list(int j, uint32_t* q, unsigned int* cnt) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned int m = n[warp][j];
+    unsigned int base = 0;
+    if (lane == 0 && m) base = atomicAdd(cnt, m);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (unsigned int i = lane; i < m; i += 32) q[base + i] = v[warp][j][i];
+    __syncwarp();
+    if (lane == 0) n[warp][j] = 0u;
+    __syncwarp();
+  }
+
+  // adds g to list j (global list q[j], counter cnt[j]) on the lanes with put[j]
+  __device__ __forceinline__ void put(const bool (&p)[NL], uint32_t g, uint32_t* const (&q)[NL], unsigned int* cnt) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const unsigned bal = __ballot_sync(0xffffffffu, p[j]);
+      if (!bal) continue;
+      if (n[warp][j] + unsigned(__popc(bal)) > unsigned(CAP)) flush_list(j, q[j], cnt + j);
+      const unsigned int n0 = n[warp][j];
+      if (p[j]) v[warp][j][n0 + __popc(bal & ((1u << lane) - 1u))] = g;
+      __syncwarp();
+      if (lane == 0) n[warp][j] = n0 + unsigned(__popc(bal));
+      __syncwarp();
+    }
+  }
+
+  __device__ __forceinline__ void flush(uint32_t* const (&q)[NL], unsigned int* cnt) {
+#pragma unroll
+    for (int j = 0; j < NL; ++j) flush_list(j, q[j], cnt + j);
+  }
+};
+
+// s_kernel: at QS, m5 (floored), N, L+ and S of J.
+__global__ void __launch_bounds__(256, 4) s_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k) {
+  expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNS],
                [&](bool valid, int fi, int x, int y) {
                  if (!valid) return;
                  const Frame& f = frames[fi];
@@ -1164,8 +1204,7 @@ __global__ void __launch_bounds__(256, 5) s_kernel(const Frame* __restrict__ fra
 
 // sp_kernel: at QSP, S' = S - med5(S); S' > sigclip -> test bit.
 __global__ void __launch_bounds__(256) sp_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p) {
-  __shared__ ExpandSmem sm;
-  expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q1), Q.n[kNSP], sm,
+  expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q1), Q.n[kNSP],
                [&](bool valid, int fi, int x, int y) {
                  if (!valid) return;
                  const Frame& f = frames[fi];
@@ -1203,8 +1242,7 @@ __global__ void __launch_bounds__(256) sp_kernel(const Frame* __restrict__ frame
 // largest of its column minima, the median of its column medians and the
 // smallest of its column maxima (an exact selection of the fifth of nine).
 __global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k) {
-  __shared__ ExpandSmem sm;
-  expand_words<4>(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNM3], sm,
+  expand_words<4>(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNM3],
                   [&](bool valid, int fi, int x0, int y, uint32_t bits) {
                     if (!valid) return;
                     const Frame& f = frames[fi];
@@ -1242,11 +1280,10 @@ __global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frame
 // word touch disjoint bits.
 __global__ void __launch_bounds__(256) bound_sparse_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
                                                            Params p) {
-  __shared__ ExpandSmem sm;
   float chot, clow;
   bound_consts(p, chot, clow);
   const int lane = threadIdx.x & 31;
-  expand_words<4>(frames, nframes, reinterpret_cast<const uint2*>(Q.q2), Q.n[kNB], sm,
+  expand_words<4>(frames, nframes, reinterpret_cast<const uint2*>(Q.q2), Q.n[kNB],
                   [&](bool valid, int fi, int x0, int y, uint32_t) {
                     uint32_t hb = 0, ab = 0, zb = 0, gm = 0;
                     unsigned long long key = ~0ull;
@@ -1312,11 +1349,12 @@ __device__ __forceinline__ float objlim_stat(const Params& p, float fval, float 
 // lie below the smallest (above the largest) column median, which bound
 // med7(m3) from below (above). Tests the bounds decide go to the candidates
 // (pass) or are dropped; the rest to the open tests.
-__global__ void __launch_bounds__(256, 3) cand_test_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
+__global__ void __launch_bounds__(256) cand_test_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
                                                            Params p) {
-  __shared__ ExpandSmem sm;
-  __shared__ unsigned int sbase[2];
-  expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q2), Q.n[kNT], sm,
+  __shared__ WarpLists<2, 128> wl;
+  wl.init();
+  uint32_t* const lists[2] = {Q.q0, Q.q1};
+  expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q2), Q.n[kNT],
                [&](bool valid, int fi, int x, int y) {
                  bool pass = false, open = false;
                  uint32_t g = 0;
@@ -1344,17 +1382,18 @@ __global__ void __launch_bounds__(256, 3) cand_test_kernel(const Frame* __restri
                    open = !pass && rhigh > p.objlim;
                  }
                  const bool put[2] = {pass, open};
-                 uint32_t* const lists[2] = {Q.q0, Q.q1};
-                 block_append<2>(put, g, lists, Q.n + kNPass, sm.ws, sbase);
+                 wl.put(put, g, lists, Q.n + kNPass);
                });
+  wl.flush(lists, Q.n + kNPass);
 }
 
 // cand_full_kernel: at the open tests, the exact F = m3 - med7(m3) and the
 // objlim test -> candidates.
 __global__ void __launch_bounds__(256) cand_full_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
                                                         Params p) {
-  __shared__ int ws[kThreads / 32 + 1];
-  __shared__ unsigned int sbase[1];
+  __shared__ WarpLists<1, 128> wl;
+  wl.init();
+  uint32_t* const lists[1] = {Q.q0};
   const unsigned int n = Q.n[kNAmb];
   const unsigned int stride = gridDim.x * blockDim.x;
   for (unsigned int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // whole warps iterate together
@@ -1372,9 +1411,9 @@ __global__ void __launch_bounds__(256) cand_full_kernel(const Frame* __restrict_
       pass = objlim_stat(p, fval, f.mapN[o], f.mapS[o], f.mapSp[o]) > p.objlim;
     }
     const bool put[1] = {pass};
-    uint32_t* const lists[1] = {Q.q0};
-    block_append<1>(put, g, lists, Q.n + kNPass, ws, sbase);
+    wl.put(put, g, lists, Q.n + kNPass);
   }
+  wl.flush(lists, Q.n + kNPass);
 }
 
 // grow_kernel: for each candidate c, the first growth g1 (S' > sigclip in the
