@@ -83,7 +83,7 @@ constexpr int kDescSlots = 4;
 // queue pipeline kernels, for the occupancy table
 enum QK {
   kQBound, kQNeed, kQS, kQSp, kQM3need, kQM3, kQCand, kQRepCompute, kQBoundList, kQRq, kQRepWrite, kQCellList,
-  kQCandFull, kQGrow, kQFlagq, kQSegList, kQD2Seg, kQNeedSeg, kQM3needSeg, kQKernels
+  kQCandFull, kQGrow, kQFlagq, kQSegList, kQD2Seg, kQNeedSeg, kQM3needSeg, kQM3needAll, kQKernels
 };
 
 struct GraphKey {
@@ -202,18 +202,18 @@ int init_ctx(crb_ctx* c) {
     const void* fns[kQKernels] = {
         reinterpret_cast<const void*>(crb::bound_kernel),       reinterpret_cast<const void*>(crb::need_kernel),
         reinterpret_cast<const void*>(crb::s_kernel),           reinterpret_cast<const void*>(crb::sp_kernel),
-        reinterpret_cast<const void*>(crb::m3need_kernel),      reinterpret_cast<const void*>(crb::m3_kernel),
+        reinterpret_cast<const void*>(crb::m3need_kernel<false>), reinterpret_cast<const void*>(crb::m3_kernel),
         reinterpret_cast<const void*>(crb::cand_test_kernel),   reinterpret_cast<const void*>(crb::rep_compute_kernel),
         reinterpret_cast<const void*>(crb::bound_sparse_kernel),   reinterpret_cast<const void*>(crb::rq_kernel),
         reinterpret_cast<const void*>(crb::rep_write_kernel),   reinterpret_cast<const void*>(crb::d2_kernel),
         reinterpret_cast<const void*>(crb::cand_full_kernel),   reinterpret_cast<const void*>(crb::grow_kernel<true>),
         reinterpret_cast<const void*>(crb::flagq_kernel),       reinterpret_cast<const void*>(crb::seg_list_kernel),
         reinterpret_cast<const void*>(crb::d2_seg_kernel),      reinterpret_cast<const void*>(crb::need_seg_kernel),
-        reinterpret_cast<const void*>(crb::m3need_seg_kernel)};
+        reinterpret_cast<const void*>(crb::m3need_seg_kernel),  reinterpret_cast<const void*>(crb::m3need_kernel<true>)};
     for (int i = 0; i < kQKernels; ++i) {
       int o = 0;
       const bool col = i == kQNeed || i == kQM3need || i == kQCellList || i == kQD2Seg || i == kQNeedSeg ||
-                       i == kQM3needSeg;
+                       i == kQM3needSeg || i == kQM3needAll;
       const int threads = i == kQBound ? 128 : col ? crb::kColWarps * 32 : 256;
       CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[i], threads, 0));
       c->occ_q[i] = o > 0 ? o : 1;
@@ -361,7 +361,9 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
       uint32_t* cls = P.cells[k & 1];
       uint32_t* cls_next = (k < P.niter) ? P.cells[(k + 1) & 1] : nullptr;
       const uint32_t* kcls = (k == 1) ? nullptr : cls;
-      const int gcol = grid(kQNeed, (P.nunits + crb::kColWarps - 1) / crb::kColWarps);
+      const long long ucol = (P.nunits + crb::kColWarps - 1) / crb::kColWarps;
+      const int gcol = grid(kQNeed, ucol);
+      const int gcolm = grid(kQM3need, ucol), gcol1m = grid(kQM3needAll, ucol);
       const bool seg = k >= crb::kSegFrom;  // the column kernels walk the listed segments only
       const int tcol = crb::kColWarps * 32;
       timed(c, kPBound, stream, [&] {
@@ -373,7 +375,7 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
                 c->d_frames, P.n, P.nunits, P.Q, cls);
             crb::d2_seg_kernel<<<gq * c->occ_q[kQD2Seg], tcol, 0, stream>>>(c->d_frames, P.n, P.Q, k);
           } else {
-            crb::d2_kernel<<<gcol, tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, k);
+            crb::d2_kernel<<<grid(kQCellList, ucol), tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, k);
           }
           crb::bound_sparse_kernel<<<gq * c->occ_q[kQBoundList], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
         }
@@ -390,8 +392,10 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
       timed(c, kPM3need, stream, [&] {
         if (seg)
           crb::m3need_seg_kernel<<<gq * c->occ_q[kQM3needSeg], tcol, 0, stream>>>(c->d_frames, P.n, P.Q, cls);
+        else if (k == 1)
+          crb::m3need_kernel<true><<<gcol1m, tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, nullptr);
         else
-          crb::m3need_kernel<<<gcol, tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, kcls);
+          crb::m3need_kernel<false><<<gcolm, tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, kcls);
       });
       timed(c, kPM3, stream, [&] { crb::m3_kernel<<<gq * c->occ_q[kQM3], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k); });
       timed(c, kPCand, stream, [&] {

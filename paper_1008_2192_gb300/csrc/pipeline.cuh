@@ -542,9 +542,12 @@ __global__ void __launch_bounds__(kColWarps * 32) need_kernel(const Frame* __res
 // needM3 = dilate3(QT) within the frame -> queue QT, and queue QM3 where M3 is
 // not current (m3val; cleared in cells of class 4); bit plane m3val. Column
 // kernel: rows y0-3 .. y0+kSH+2 feed the seven-row window of QT.
+// kAll (iteration 1): every cell counts as changed and cls is not read.
+template <bool kAll>
 __global__ void __launch_bounds__(kColWarps * 32) m3need_kernel(const Frame* __restrict__ frames, int nframes,
                                                                 long long nunits, Queues Q,
-                                                                const uint32_t* __restrict__ cls) {
+                                                                const uint32_t* __restrict__ cls_in) {
+  const uint32_t* __restrict__ cls = kAll ? nullptr : cls_in;
   __shared__ ColWords sw;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (long long u = (long long)blockIdx.x * kColWarps + warp; u < nunits; u += (long long)gridDim.x * kColWarps) {
