@@ -78,6 +78,23 @@ def network_minmax():
     return counts
 
 
+def max_over_ranks(ms, world, device="cpu"):
+    """The slowest rank's time (every rank gets it); the time itself with one rank."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(npix_per_rank, steps, ms_max, world):
+    """Mpix/s of the whole job: every rank cleans its own copy of the workload (replicas), timed by the
+    slowest rank."""
+    return world * npix_per_rank * steps / (ms_max * 1e-3) / 1e6
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -517,11 +534,8 @@ def main():
     rep_ms = sum(v[0] for k, v in kinds.items() if k in ("replace", "mask", "tile_replace"))
     cl.sync()
 
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * npix * args.steps / (ms_max * 1e-3) / 1e6
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = whole_job_value(npix, args.steps, ms_max, world)
 
     extras = {}
     if not args.no_extras:
