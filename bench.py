@@ -530,7 +530,7 @@ def main():
     clk = clocks.stop()
     kinds = cl.profile_kernels(reset=True)
     det_ms = sum(v[0] for k, v in kinds.items() if k in ("bound", "need", "s", "sprime", "m3need", "m3", "cand",
-                                                          "grow", "cell_list", "tile_detect"))
+                                                          "grow", "tile_detect"))
     rep_ms = sum(v[0] for k, v in kinds.items() if k in ("replace", "mask", "tile_replace"))
     cl.sync()
 

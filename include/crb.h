@@ -222,9 +222,11 @@ int crb_fadd_peak(double* ops_per_s, cudaStream_t stream);
 /* Profiling by kernel kind (crb_options.profile = 1): after the stream has been
  * synchronised, writes for up to max kinds the total device time in ms and the
  * number of timed brackets since the last reset (then resets if reset != 0).
- * Kinds, in order: 0 bound pass (both forms), 1 need, 2 S, 3 S', 4 m3need,
- * 5 med3, 6 candidate tests, 7 growth, 8 cell lists, 9 tile-pipeline detection,
- * 10 replacement, 11 u8 mask, 12 tile-pipeline replacement, 13 work counters.
+ * Kinds, in order: 0 bound pass (iteration 1: the dense pass; later: the
+ * segment list, the dilation of the changed pixels and the re-test), 1 need,
+ * 2 S, 3 S', 4 m3need, 5 med3, 6 candidate tests, 7 growth, 8 reserved (no
+ * kernel is timed under it), 9 tile-pipeline detection, 10 replacement,
+ * 11 u8 mask, 12 tile-pipeline replacement, 13 work counters.
  * Returns the number of kinds written, or CRB_EINVAL. */
 int crb_profile_kernels(crb_ctx* ctx, double* ms, int* brackets, int max, int reset);
 

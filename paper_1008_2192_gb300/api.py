@@ -171,7 +171,7 @@ class Cleaner:
                                            ctypes.byref(rn), int(reset)), "crb_profile_read")
         return dm.value, dn.value, rm.value, rn.value
 
-    PROFILE_KINDS = ("bound", "need", "s", "sprime", "m3need", "m3", "cand", "grow", "cell_list", "tile_detect",
+    PROFILE_KINDS = ("bound", "need", "s", "sprime", "m3need", "m3", "cand", "grow", "reserved", "tile_detect",
                      "replace", "mask", "tile_replace", "work")
 
     def profile_kernels(self, reset=True):

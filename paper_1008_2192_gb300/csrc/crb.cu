@@ -68,7 +68,7 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 // profiling kinds (crb_profile_kernels order); kinds below kProfReplace0 are detection
 enum ProfKind {
-  kPBound, kPNeed, kPS, kPSp, kPM3need, kPM3, kPCand, kPGrow, kPCellList, kPTileDetect,  // detection
+  kPBound, kPNeed, kPS, kPSp, kPM3need, kPM3, kPCand, kPGrow, kPReserved, kPTileDetect,  // detection
   kPRep, kPMask, kPTileReplace,                                                      // replacement
   kPWork,                                                                             // work counters
   kProfKinds
@@ -82,7 +82,7 @@ constexpr int kDescSlots = 4;
 
 // queue pipeline kernels, for the occupancy table
 enum QK {
-  kQBound, kQNeed, kQS, kQSp, kQM3need, kQM3, kQCand, kQRepCompute, kQBoundList, kQRq, kQRepWrite, kQCellList,
+  kQBound, kQNeed, kQS, kQSp, kQM3need, kQM3, kQCand, kQRepCompute, kQBoundSparse, kQRq, kQRepWrite, kQD2,
   kQCandFull, kQGrow, kQFlagq, kQSegList, kQD2Seg, kQNeedSeg, kQM3needSeg, kQM3needAll, kQKernels
 };
 
@@ -212,7 +212,7 @@ int init_ctx(crb_ctx* c) {
         reinterpret_cast<const void*>(crb::m3need_seg_kernel),  reinterpret_cast<const void*>(crb::m3need_kernel<true>)};
     for (int i = 0; i < kQKernels; ++i) {
       int o = 0;
-      const bool col = i == kQNeed || i == kQM3need || i == kQCellList || i == kQD2Seg || i == kQNeedSeg ||
+      const bool col = i == kQNeed || i == kQM3need || i == kQD2 || i == kQD2Seg || i == kQNeedSeg ||
                        i == kQM3needSeg || i == kQM3needAll;
       const int threads = i == kQBound ? 128 : col ? crb::kColWarps * 32 : 256;
       CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[i], threads, 0));
@@ -375,9 +375,9 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
                 c->d_frames, P.n, P.nunits, P.Q, cls);
             crb::d2_seg_kernel<<<gq * c->occ_q[kQD2Seg], tcol, 0, stream>>>(c->d_frames, P.n, P.Q, k);
           } else {
-            crb::d2_kernel<<<grid(kQCellList, ucol), tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, k);
+            crb::d2_kernel<<<grid(kQD2, ucol), tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, k);
           }
-          crb::bound_sparse_kernel<<<gq * c->occ_q[kQBoundList], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
+          crb::bound_sparse_kernel<<<gq * c->occ_q[kQBoundSparse], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
         }
       });
       timed(c, kPNeed, stream, [&] {

@@ -76,7 +76,7 @@ enum : int {
   kNRep = 4,    // replacement queue
   kNFresh = 5,  // new flags of this iteration
   kNFb = 6,     // pixels with a fully flagged window (kept over the iterations)
-  kNL2 = 7,     // (unused)
+  kNReserved = 7,  // (not used)
   kNPass = 8,   // candidates (passed the objlim test)
   kNAmb = 9,    // tests the column-median bounds leave open
   kNSpx = 10,   // positions in QS, QSP, QM3, QT (work counters)
