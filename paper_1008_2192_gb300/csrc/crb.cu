@@ -181,6 +181,11 @@ struct crb_ctx {
   int prof_n[kProfKinds] = {};
 };
 
+// Lets the server turn graph replay on for the calls whose signature repeats (single-frame waves).
+void crb_detail_set_graphs(crb_ctx* c, int on) {
+  if (c) c->opt.use_graphs = on;
+}
+
 namespace {
 
 int init_ctx(crb_ctx* c) {

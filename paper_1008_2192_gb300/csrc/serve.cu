@@ -24,6 +24,7 @@
 #include "crb.h"
 
 void crb_detail_set_error(const char* msg);  // crb.cu
+void crb_detail_set_graphs(crb_ctx* c, int on);  // crb.cu
 
 namespace {
 
@@ -119,6 +120,9 @@ void launch_wave(crb_server* s, int slot, std::vector<Request>&& reqs) {
     gs[size_t(i)] = r.gain;
     rs[size_t(i)] = r.rn;
   }
+  // a single frame's launch signature repeats across waves (a handful of frame sizes), so its
+  // work is captured once per size and replayed; a mixed wave's signature rarely repeats
+  crb_detail_set_graphs(s->ctx[size_t(slot)], n == 1);
   int rc = crb_clean_batch(s->ctx[size_t(slot)], n, imgs.data(), ws.data(), hs.data(), gs.data(), rs.data(),
                            outs.data(), masks.data(), s->stream[size_t(slot)]);
   if (rc == CRB_OK && cudaEventCreateWithFlags(&wv.done, cudaEventDisableTiming) != cudaSuccess) rc = CRB_ECUDA;
