@@ -162,6 +162,18 @@ __device__ __forceinline__ void bound_consts(const Params& p, float& chot, float
   clow = 4.f * tlow * tlow * 0.9999f;
 }
 
+// The two bound tests of one pixel from its L+ and the smallest of its five
+// column medians, with every rounding spelled out: the dense pass and the
+// re-test share it, so a pixel re-tested with an unchanged window keeps its
+// bits exactly.
+__device__ __forceinline__ void bound_test(float lp, float mlow, float gain, float rn2, float g2, float clow,
+                                           float chot, bool& act, bool& hot) {
+  const float den = __fmaf_rn(gain, mlow > 0.f ? mlow : 0.f, rn2);
+  const float lhs = __fmul_rn(__fmul_rn(lp, lp), g2);
+  act = lhs > __fmul_rn(clow, den);
+  hot = lhs > __fmul_rn(chot, den);
+}
+
 // Sliding column-median state of one column: rows r-2 .. r+1 of the current step.
 struct Col4 {
   float a, b, c, d;
@@ -253,16 +265,14 @@ __device__ __forceinline__ void bound_span2(const Frame& f, const float* __restr
         if (xa < w) o[xa] = ccA;
         if (xb < w) o[xb] = ccB;
       }
-      const float denA = gain * (mlowA > 0.f ? mlowA : 0.f) + rn2;
-      const float denB = gain * (mlowB > 0.f ? mlowB : 0.f) + rn2;
-      const float lhsA = lpA * lpA * g2, lhsB = lpB * lpB * g2;
+      bool actA, hotA, actB, hotB;
+      bound_test(lpA, mlowA, gain, rn2, g2, clow, chot, actA, hotA);
+      bound_test(lpB, mlowB, gain, rn2, g2, clow, chot, actB, hotB);
       // word wc holds lanes 0-15 (bits 2l, 2l+1), word wc+1 lanes 16-31: each half
       // ORs its lanes' bit pairs, shifted into place
       const int sh = 2 * (lane & 15);
-      const uint32_t va = (uint32_t(xa < w && lhsA > clow * denA) | (uint32_t(xb < w && lhsB > clow * denB) << 1))
-                          << sh;
-      const uint32_t vh = (uint32_t(xa < w && lhsA > chot * denA) | (uint32_t(xb < w && lhsB > chot * denB) << 1))
-                          << sh;
+      const uint32_t va = (uint32_t(xa < w && actA) | (uint32_t(xb < w && actB) << 1)) << sh;
+      const uint32_t vh = (uint32_t(xa < w && hotA) | (uint32_t(xb < w && hotB) << 1)) << sh;
       const uint32_t vz = (uint32_t(xa < w && lpA == 0.f) | (uint32_t(xb < w && lpB == 0.f) << 1)) << sh;
       uint32_t act, hot, lz;
       if (lane < 16) {
@@ -1306,10 +1316,10 @@ __global__ void __launch_bounds__(256) bound_sparse_kernel(const Frame* __restri
                       for (int i = 0; i < 4; ++i) {
                         const float mlow = min3f(min3f(cm[i], cm[i + 1], cm[i + 2]), cm[i + 3], cm[i + 4]);
                         const float lp = lplus(v[2][i + 2], v[1][i + 2], v[3][i + 2], v[2][i + 1], v[2][i + 3]);
-                        const float den = gain * (mlow > 0.f ? mlow : 0.f) + rn2;
-                        const float lhs = lp * lp * g2;
-                        ab |= uint32_t(lhs > clow * den) << i;
-                        hb |= uint32_t(lhs > chot * den) << i;
+                        bool act, hot;
+                        bound_test(lp, mlow, gain, rn2, g2, clow, chot, act, hot);
+                        ab |= uint32_t(act) << i;
+                        hb |= uint32_t(hot) << i;
                         zb |= uint32_t(lp == 0.f) << i;
                       }
                       const int sh = x0 & 31;
