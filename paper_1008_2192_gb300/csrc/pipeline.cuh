@@ -1436,7 +1436,7 @@ __global__ void __launch_bounds__(256) cand_full_kernel(const Frame* __restrict_
 // the bit plane nsp says it is current; elsewhere it cannot pass either
 // threshold.
 template <bool kFresh>
-__global__ void __launch_bounds__(256) grow_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p,
+__global__ void __launch_bounds__(256, 4) grow_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p,
                                                    int k) {
   const unsigned int n = Q.n[kNPass];
   const float sigclip = p.sigclip, siglow = __fmul_rn(p.sigfrac, p.sigclip);
