@@ -53,9 +53,9 @@ ALG_BYTES_PER_PIX_ITER = 8.25
 BOUND_TEST_MINMAX = 6 + 4 + 1
 # DRAM bytes (read + write) of the bound pass per step and per input pixel: the
 # ncu capture of all its launches of one step on three 4096x4096 frames of the
-# batch mix (636.7 MB for 50.3 Mpix; the summary is kept with the profiles),
+# batch mix (637.2 MB for 50.3 Mpix; the summary is kept with the profiles),
 # applied to the workload's pixels; None once the kernel changes.
-BOUND_TRAFFIC_PER_PIXEL = 636707328 / 50331648
+BOUND_TRAFFIC_PER_PIXEL = 637184512 / 50331648
 # Algorithmic FP32 operations per unit of each kernel kind: (min/max, other).
 KIND_OPS = {
     "bound": (BOUND_TEST_MINMAX, 24),
