@@ -36,7 +36,7 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-# Survey's dense estimate of the detection work per pixel and iteration (two
+# A dense estimate of the detection work per pixel and iteration (two
 # 25-input median selections of ~200 min/max each plus ~25 arithmetic
 # operations); reported for context only, since the kernel evaluates the
 # medians only where they can change a flag.
