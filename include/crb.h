@@ -16,7 +16,9 @@
  *       their 5x5 window (the 5x5 median of the frame when none is unflagged).
  * Flags accumulate over iterations. Every filter clamps its coordinates into
  * the frame (replicate edge); the paper leaves the outer pixels undefined
- * (Sec. 6.1). The arithmetic is IEEE float32 with no contraction.
+ * (Sec. 6.1). The method's arithmetic is IEEE float32 with no contraction.
+ * The library also provides the paper's POISSON work function (Sec. 6.3.2;
+ * crb_poisson), the probe the paper uses to measure its framework's overhead.
  *
  * Conventions for every call:
  *   - Images are float32 DN, row-major, contiguous (row pitch = w), DEVICE
