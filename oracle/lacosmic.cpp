@@ -20,11 +20,11 @@
 // Inputs J are float; every median is an exact selection, so maps that are
 // medians of J are exact in either type.
 //
-// Parity status: medians, L+, the replacement rule and the dependency radius
-// are pinned by the tests (brute force, closed forms, invariants). The objlim
-// statistic form, the cumulative-mask rule and the tie and edge rules are
-// readings of a paper that does not restate the algorithm: parity unpinned
-// against the paper for those readings.
+// Parity status: medians, L+, the replacement rule, the dependency radius and
+// the fragile map are pinned by the tests (brute force, closed forms,
+// invariants). The objlim statistic form, the cumulative-mask rule and the tie
+// and edge rules are readings of a paper that does not restate the algorithm:
+// parity unpinned against the paper for those readings.
 
 #include <algorithm>
 #include <cmath>

@@ -16,7 +16,10 @@ What pins what:
                        star); invariants (monotone mask, untouched unflagged
                        pixels, transpose/flip equivariance, fixed point);
                        the dependency radius (mask <= 6 = the paper's BORDER,
-                       image <= 8 per iteration) and crops with 8*niter context.
+                       image <= 8 per iteration) and crops with 8*niter context;
+  * fragile map     -- the closed form of a hot pixel whose statistic sits at a
+                       stated relative distance from each threshold (inside and
+                       outside the 1e-4 tolerance; interior and corner cone).
 """
 
 from __future__ import annotations
@@ -418,6 +421,51 @@ def pin_crop_context(orc):
         sl = (slice(y0 - ya, y0 - ya + hh), slice(x0 - xa, x0 - xa + ww))
         assert np.array_equal(c.mask[sl], full.mask[y0:y0 + hh, x0:x0 + ww])
         assert np.array_equal(c.clean[sl], full.clean[y0:y0 + hh, x0:x0 + ww])
+
+
+# ----------------------------------------------------------------------------- fragile map
+def _cone(shape, py, px):
+    """The clamped 5x5 box around (py, px): the pixels whose growth can reach from p."""
+    h, w = shape
+    c = np.zeros(shape, np.uint8)
+    c[max(py - 2, 0):min(py + 3, h), max(px - 2, 0):min(px + 3, w)] = 1
+    return c
+
+
+def pin_fragile_closed_form(orc):
+    """The fragile map of a hot pixel on a flat sky, no noise, in closed form.
+
+    From the closed form of pin_hot_pixel_closed_form, S'(p) = kA/N and R(p) = S'(p)/0.01 at the
+    hot pixel p, and S' = 0 everywhere else; k = 1 in the interior, where all four differences
+    are A, and k = 1/2 at a frame corner, where the two clamped differences vanish (L+ = A;
+    med5(S) stays 0, p filling 9 of the 25 clamped window places). Choosing A puts one statistic
+    at a stated relative
+    distance d from its threshold: S' = sigclip (1 + d), S' = sigfrac sigclip (1 + d), or, with
+    S' = 9 > sigclip, R = objlim (1 + d) by setting objlim = 900 (1 + d). A statistic within 1e-4
+    (relative) of its threshold marks the clamped 5x5 box around it, so the fragile map is
+    exactly that box for |d| = 5e-5 (either side) and empty for |d| = 1.5e-4. The corner position
+    of p checks the clamp of the box.
+    """
+    b = 20.0
+    N = math.sqrt(7.0 * b + 25.0) / 7.0
+    shape = (15, 17)
+    for (py, px), kappa in (((7, 8), 1.0), ((0, 0), 0.5)):
+        for d, inside in ((5e-5, True), (-5e-5, True), (1.5e-4, False), (-1.5e-4, False)):
+            cases = (("sigclip", Params(), 4.5 * (1 + d)),
+                     ("sigfrac", Params(), 0.5 * 4.5 * (1 + d)),
+                     ("objlim", Params(objlim=900.0 * (1 + d)), 9.0))
+            for name, P, s_target in cases:
+                J = np.full(shape, b, np.float32)
+                J[py, px] = np.float32(b + s_target * N / kappa)
+                r = orc.iterate(J, None, P, maps=True, fragile=True)
+                got_sp = r.maps["sprime"][py, px]
+                assert abs(got_sp / s_target - 1) < 1e-6, (name, got_sp, s_target)
+                exp = _cone(shape, py, px) if inside else np.zeros(shape, np.uint8)
+                assert np.array_equal(r.fragile, exp), (name, d, (py, px), int(r.fragile.sum()))
+    # the end-to-end fragile map is the union over the iterations
+    J = np.full(shape, b, np.float32)
+    J[7, 8] = np.float32(b + 4.5 * (1 + 5e-5) * N)
+    assert np.array_equal(orc.clean(J, Params(), 2, fragile=True).fragile, _cone(shape, 7, 8))
 
 
 def pin_precisions_agree(orc):

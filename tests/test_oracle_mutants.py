@@ -48,6 +48,17 @@ MUTANTS = {
     "replace_window3": ("for (int dy = -2; dy <= 2; ++dy)\n        for (int dx = -2; dx <= 2; ++dx)\n          if (!Mk",
                         "for (int dy = -1; dy <= 1; ++dy)\n        for (int dx = -1; dx <= 1; ++dx)\n          if (!Mk"),
     "m5_floor_missing": ("if (v <= T(0)) v = T(0.0001);\n  Map<T> noise", "if (v < T(-1e30)) v = T(0.0001);\n  Map<T> noise"),
+    # the fragile map: its tolerance, its cone, and each of its three threshold conditions
+    "fragile_tol": ("const double tol = 1e-4;", "const double tol = 10;"),
+    "fragile_tol_loose": ("const double tol = 1e-4;", "const double tol = 2e-4;"),
+    "fragile_cone_1x1": ("for (int dy = -2; dy <= 2; ++dy)\n          for (int dx = -2; dx <= 2; ++dx) any |= near",
+                         "for (int dy = 0; dy <= 0; ++dy)\n          for (int dx = 0; dx <= 0; ++dx) any |= near"),
+    "fragile_cone_3x3": ("for (int dy = -2; dy <= 2; ++dy)\n          for (int dx = -2; dx <= 2; ++dx) any |= near",
+                         "for (int dy = -1; dy <= 1; ++dy)\n          for (int dx = -1; dx <= 1; ++dx) any |= near"),
+    "fragile_no_sigclip": ("const bool a = std::fabs(spv - c) <= tol * c;", "const bool a = false;"),
+    "fragile_no_sigfrac": ("const bool b = std::fabs(spv - c2) <= tol * c2;", "const bool b = false;"),
+    "fragile_no_objlim": ("const bool d = spv > c * (1.0 - tol) && std::fabs(rv - ol) <= tol * ol;",
+                          "const bool d = false;"),
 }
 
 
