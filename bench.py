@@ -2,21 +2,28 @@
 """Throughput benchmark: Mpix/s cleaned at niter=4 on synthetic CCD frames.
 
 Default workload: 64 uneven frames (16 each of 800^2, 1024^2, 2048x4096,
-4096^2; per-frame gain and read noise), one crb_clean_batch call per step.
-A step is the whole hot path (niter iterations of detection + replacement)
-over that batch. Inputs (1.72 GB) exceed the 126 MB L2, so no flush is needed.
+4096^2; per-frame gain and read noise), one crb_clean_batch call per step with
+the niter loop replayed from a CUDA graph. A step is the whole hot path (niter
+iterations of detection + replacement) over that batch. Inputs (1.72 GB)
+exceed the 126 MB L2, so no flush is needed.
 
 Printed (one JSON line from rank 0):
-  value       device-timed batched throughput, inputs resident in HBM;
-  e2e         the same through the public API with host buffers (pinned H2D
-              of the inputs, D2H of cleaned frames and masks inside the timed
-              region);
-  per_frame   the plain path: one crb_clean call per frame, no batching;
-  roofline    the detection kernel (stages a-d, the dominant kernel) against
-              the measured FP32 min/max rate of the device;
-  cpu_baseline the CPU oracle on a bounded sample of the same workload.
+  value        device-timed batched throughput, inputs resident in HBM, graph
+               replay, no per-kernel events in the timed region;
+  e2e          the same through the public API with host buffers (pinned H2D
+               of the inputs, D2H of cleaned frames and masks inside the timed
+               region);
+  per_frame    the plain path: one crb_clean call per frame, no batching;
+  roofline     the dominant kernel kind, timed with CUDA events around every
+               launch in a separate profiled pass of the same steps, against
+               the measured issue rates of its operation mix;
+  serving      Poisson arrivals of 10,000 frames at 1000 and 2000 frames/s;
+  cpu_baseline the CPU oracle on a bounded sample of the workload, all host
+               cores and one core;
+  parity_sample the same sample cleaned on the GPU against the FP64 oracle:
+               mask flips and fragile pixels.
 With --impl reference the CPU oracle itself is the timed arm (this method has
-no runnable reference implementation).
+no runnable reference implementation), on the same sample.
 Multi-GPU (torchrun): independent replicas, one per GPU, weak scaling.
 """
 
@@ -51,11 +58,11 @@ ALG_BYTES_PER_PIX_ITER = 8.25
 # sums, 4 clips taken as t+|t|, 3 sums, 1 scale = 16) and the two threshold
 # tests (gain*m, +rn^2, L+^2, *gain^2, two scaled thresholds, two compares = 8).
 BOUND_TEST_MINMAX = 6 + 4 + 1
-# DRAM bytes (read + write) of the bound pass per step and per input pixel: the
-# ncu capture of all its launches of one step on three 4096x4096 frames of the
-# batch mix (637.2 MB for 50.3 Mpix; the summary is kept with the profiles),
-# applied to the workload's pixels; None once the kernel changes.
-BOUND_TRAFFIC_PER_PIXEL = 637184512 / 50331648
+# DRAM bytes (read + write) per step and per input pixel of each kernel kind's
+# launches, from an ncu capture of one step on three 4096x4096 frames of the
+# batch mix (the summaries are kept with the profiles), applied to the
+# workload's pixels; a kind whose kernels changed since their capture has none.
+TRAFFIC_PER_PIXEL = {}
 # Algorithmic FP32 operations per unit of each kernel kind: (min/max, other).
 KIND_OPS = {
     "bound": (BOUND_TEST_MINMAX, 24),
@@ -63,6 +70,126 @@ KIND_OPS = {
     "sprime": (192, 1),   # med25 of S; the difference
     "m3": (33, 0),        # med9
 }
+
+
+# The headline metric, printed alike by both arms.
+METRIC = "Mpix/s cleaned at niter=4, batched vs per-frame on 1 GB300; p50/p99 latency"
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_sample(recipes, max_frames=4):
+    """The bounded sample the CPU legs time: one 800x800 frame per size class of the workload (at most
+    max_frames), generated from that class's recipe (sky, gain, read noise, star and cosmic-ray
+    densities scaled to the smaller area)."""
+    seen, out = set(), []
+    for r in recipes:
+        if (r["w"], r["h"]) in seen:
+            continue
+        seen.add((r["w"], r["h"]))
+        rr = dict(r)
+        rr.update(w=min(r["w"], 800), h=min(r["h"], 800))
+        scale = rr["w"] * rr["h"] / (r["w"] * r["h"])
+        rr.update(nstars=max(1, int(round(r["nstars"] * scale))), ncr=max(1, int(round(r["ncr"] * scale))))
+        out.append(rr)
+        if len(out) >= max_frames:
+            break
+    return out
+
+
+def sample_desc(sample):
+    sizes = ", ".join(f"{r['w']}x{r['h']} (gain {r['gain']:.2f}, read noise {r['readnoise']:.2f})" for r in sample)
+    return f"{len(sample)} frames, one per size class of the workload, from that class's recipe: {sizes}"
+
+
+def time_oracle(frames, threads, min_s):
+    """The FP64 oracle over the frames, taken in turn, until min_s seconds have passed (at least one
+    frame); returns (Mpix/s, frames timed, seconds)."""
+    import oracle
+    oracle.set_threads(threads)
+    pix, t_tot, n = 0, 0.0, 0
+    while t_tot < min_s or n == 0:
+        img, P = frames[n % len(frames)]
+        t0 = time.perf_counter()
+        oracle.clean(img, P, 4)
+        t_tot += time.perf_counter() - t0
+        pix += img.size
+        n += 1
+    return pix / t_tot / 1e6, n, t_tot
+
+
+def cpu_baseline(sample, all_s=4.0, one_s=10.0):
+    """The oracle (FP64) timed on this host: all cores, then one core, on the bounded sample."""
+    import oracle
+    from synth import workloads as wl
+    frames = [(wl.make(r), oracle.Params(gain=r["gain"], readnoise=r["readnoise"])) for r in sample]
+    nproc = os.cpu_count() or 1
+    v_all, n_all, t_all = time_oracle(frames, nproc, all_s)
+    cores = oracle.max_threads()
+    v_one, n_one, t_one = time_oracle(frames, 1, one_s)
+    oracle.set_threads(nproc)
+    return {"value": v_all, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+            "sample": f"{sample_desc(sample)}; niter=4, FP64; {n_all} frames in {t_all:.1f} s on {cores} threads",
+            "single_thread": {"value": v_one, "unit": "Mpix/s", "cores": 1,
+                              "sample": f"the same frames, {n_one} in {t_one:.1f} s on 1 thread"},
+            "nproc": nproc, "cpu_model": cpu_model()}
+
+
+def parity_sample(torch, sample, pipeline="queue"):
+    """The sample cleaned on the GPU in one batched call (the headline's kernels) against the oracle:
+    bit-identical to its FP32 run; against FP64, mask flips (all on fragile pixels) and fragile pixels."""
+    import oracle
+    from paper_1008_2192_gb300 import Cleaner
+    from synth import workloads as wl
+    imgs = [wl.make(r) for r in sample]
+    gains = [r["gain"] for r in sample]
+    rns = [r["readnoise"] for r in sample]
+    cl = Cleaner(niter=4, pipeline=pipeline)
+    outs, masks = cl.clean_batch([torch.from_numpy(a).cuda() for a in imgs], gains, rns)
+    cl.sync()
+    flips = off = fragile = 0
+    exact = True
+    for a, o, m, g, r in zip(imgs, outs, masks, gains, rns):
+        o, m = o.cpu().numpy(), m.cpu().numpy()
+        P = oracle.Params(gain=g, readnoise=r)
+        r32 = oracle.clean(a, P, 4, precision="f32")
+        exact &= bool(np.array_equal(m, r32.mask) and np.array_equal(o, r32.clean))
+        r64 = oracle.clean(a, P, 4, fragile=True)
+        fl = m != r64.mask
+        flips += int(fl.sum())
+        off += int((fl & (r64.fragile == 0)).sum())
+        fragile += int(r64.fragile.sum())
+    cl.close()
+    return {"frames": len(imgs), "pixels": int(sum(a.size for a in imgs)), "pipeline": pipeline,
+            "bit_exact_vs_fp32_oracle": exact, "flips_vs_fp64": flips, "flips_off_fragile": off,
+            "fragile": fragile}
+
+
+def arm_config(args, desc, recipes):
+    """The config object both arms print for a workload."""
+    npix = sum(r["w"] * r["h"] for r in recipes)
+    return {"workload": desc, "frames": len(recipes), "mpix_per_step": npix / 1e6, "niter": 4,
+            "params": "sigclip 4.5, sigfrac 0.5, objlim 1.0",
+            "l2": "inputs 1.7 GB > L2, no flush" if args.workload == "batch64" else "see workload",
+            "parallelism": "replicas"}
 
 
 def network_minmax():
@@ -105,7 +232,7 @@ def parse():
                     choices=["batch64", "single4096", "single800", "mosaic16384", "triple4096", "serving",
                              "poisson750", "poisson_batch64"])
     ap.add_argument("--rates", default="50,200,500,1000,2000", help="serving: arrival rates, frames/s")
-    ap.add_argument("--serve-frames", type=int, default=0, help="serving: frames per rate (0: ~4 s of arrivals)")
+    ap.add_argument("--serve-frames", type=int, default=0, help="serving: frames per rate (0: 10,000)")
     ap.add_argument("--tile-shape", type=int, default=0)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / per-frame / cpu legs")
     return ap.parse_args()
@@ -188,33 +315,6 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(recipes, budget_s=12.0):
-    """The oracle (FP64, all host cores) on a bounded sample: 800x800 crops of the workload's frames."""
-    import oracle
-    from synth import workloads as wl
-    threads = os.cpu_count() or 1
-    oracle.set_threads(threads)
-    P = oracle.Params()
-    pix, t_tot, n = 0, 0.0, 0
-    i = 0
-    while t_tot < budget_s and i < len(recipes):
-        r = dict(recipes[i])
-        r.update(w=min(r["w"], 800), h=min(r["h"], 800))
-        scale = r["w"] * r["h"] / (recipes[i]["w"] * recipes[i]["h"])
-        r.update(nstars=max(1, int(r["nstars"] * scale)), ncr=max(1, int(r["ncr"] * scale)))
-        img = wl.make(r)
-        P = oracle.Params(gain=r["gain"], readnoise=r["readnoise"])
-        t0 = time.perf_counter()
-        oracle.clean(img, P, 4)
-        t_tot += time.perf_counter() - t0
-        pix += img.size
-        n += 1
-        i += 1
-    return {"value": pix / t_tot / 1e6, "unit": "Mpix/s", "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"{n} frames of up to 800x800 from the workload's recipes, niter=4, FP64, "
-                      f"{oracle.max_threads()} threads, {t_tot:.1f} s"}
-
-
 def serve_run(torch, rate, nframes, seed=0, budget=64 << 30, max_inflight=2, max_batch=64):
     """Poisson arrivals at `rate` frames/s, sizes uniform over the batch sizes, through crb_server.
 
@@ -288,7 +388,7 @@ def run_serving(args):
     rates = [float(x) for x in args.rates.split(",")]
     res = []
     for rate in rates:
-        n = args.serve_frames or int(min(4000, max(200, rate * 4)))
+        n = args.serve_frames or 10000
         res.append(serve_run(torch, rate, n))
     best = max(res, key=lambda r: r["mpix_per_s"])
     line = {"metric": "Mpix/s served at niter=4 (continuous batching, 1 GB300); p50/p99 latency",
@@ -301,7 +401,8 @@ def run_serving(args):
 
 
 def run_reference(args):
-    """The reference arm: the CPU oracle, timed on this host's cores, on 800x800 frames of the workload."""
+    """The reference arm: the FP64 CPU oracle, timed on this host's cores, each step one pass over the
+    bounded sample of the workload that the CPU baseline uses."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -311,27 +412,32 @@ def run_reference(args):
         run_reference_poisson(args)
         return
     recipes, desc = recipes_for(args.workload)
+    sample = cpu_sample(recipes)
+    frames = [(wl.make(r), oracle.Params(gain=r["gain"], readnoise=r["readnoise"])) for r in sample]
     threads = os.cpu_count() or 1
     oracle.set_threads(threads)
-    r0 = dict(recipes[0])
-    r0.update(w=800, h=800, nstars=200, ncr=1500)
-    img = wl.make(r0)
-    P = oracle.Params(gain=r0["gain"], readnoise=r0["readnoise"])
+
+    def step():
+        for img, P in frames:
+            oracle.clean(img, P, 4)
+
     for _ in range(max(0, min(args.warmup, 1))):
-        oracle.clean(img, P, 4)
+        step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.clean(img, P, 4)
+        step()
     dt = time.perf_counter() - t0
-    value = args.steps * img.size / dt / 1e6
-    sample = (f"each step: one 800x800 frame of the workload's generative model, niter=4, FP64 oracle, "
-              f"{oracle.max_threads()} threads")
-    line = {"impl": "reference", "metric": "Mpix/s cleaned at niter=4", "value": value, "unit": "Mpix/s",
+    pix = sum(img.size for img, _ in frames)
+    value = args.steps * pix / dt / 1e6
+    sample_txt = f"each step: {sample_desc(sample)}; niter=4, FP64 oracle, {oracle.max_threads()} threads"
+    config = arm_config(args, desc, recipes)
+    config["sample"] = sample_txt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "niter": 4},
+            "config": config,
             "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": oracle.max_threads(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample_txt, "nproc": threads, "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -504,15 +610,15 @@ def main():
     stream = torch.cuda.current_stream()
 
     ops2, ops3 = alu_peak()
-    cl = Cleaner(gain=7.0, readnoise=5.0, niter=niter, tile_shape=args.tile_shape, profile=True)
+    # the headline: one batched call per step, its work replayed from a CUDA graph
+    cl = Cleaner(gain=7.0, readnoise=5.0, niter=niter, tile_shape=args.tile_shape, use_graphs=True)
 
-    def step():
-        cl.clean_batch_into(d_imgs, d_outs, d_masks, gains, rns)
+    def step(c=cl):
+        c.clean_batch_into(d_imgs, d_outs, d_masks, gains, rns)
 
     for _ in range(max(args.warmup, 0)):
         step()
     cl.sync()
-    cl.profile_read(reset=True)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -528,11 +634,28 @@ def main():
     barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    kinds = cl.profile_kernels(reset=True)
+    cl.sync()
+    launches = cl.last_launches()
+
+    # the profiled pass: the same steps with CUDA events around every launch (no graph), for the
+    # per-kernel breakdown and the roofline of the dominant kernel kind
+    clp = Cleaner(gain=7.0, readnoise=5.0, niter=niter, tile_shape=args.tile_shape, profile=True)
+    step(clp)
+    clp.sync()
+    clp.profile_read(reset=True)
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    for _ in range(args.steps):
+        step(clp)
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    prof_ms = pe0.elapsed_time(pe1)
+    kinds = clp.profile_kernels(reset=True)
+    work = clp.last_work()  # every step cleans the same batch
+    clp.close()
     det_ms = sum(v[0] for k, v in kinds.items() if k in ("bound", "need", "s", "sprime", "m3need", "m3", "cand",
                                                           "grow", "tile_detect"))
     rep_ms = sum(v[0] for k, v in kinds.items() if k in ("replace", "mask", "tile_replace"))
-    cl.sync()
 
     ms_max = max_over_ranks(ms, world, "cuda")
     value = whole_job_value(npix, args.steps, ms_max, world)
@@ -593,15 +716,13 @@ def main():
         pf_ms = timed_steps(plain_step, k2)
         extras["per_frame"] = {"value": world * npix / (pf_ms * 1e-3) / 1e6, "unit": "Mpix/s",
                                "ms_per_step": pf_ms}
-        # serving summary: continuous batching of Poisson arrivals (p50/p99 latency)
+        # serving: continuous batching of Poisson arrivals, 10,000 frames per rate (p50/p99 latency)
         del plain, cl_plain
         torch.cuda.empty_cache()
-        extras["serving"] = serve_run(torch, 1000.0, 2000)
+        extras["serving"] = [serve_run(torch, rate, 10000) for rate in (1000.0, 2000.0)]
 
     peaks = measured_peaks()
     fadd = fadd_peak()
-    # work of the last step (every step cleans the same batch)
-    work = cl.last_work()
     net = network_minmax()
     units = {"bound": sum(w[5] for w in work), "s": sum(w[0] for w in work), "sprime": sum(w[1] for w in work),
              "m3": sum(w[2] for w in work)}
@@ -615,15 +736,16 @@ def main():
         ops = (mm + fp) * units[dom]  # per step
         achieved = ops / (per_step[dom] * 1e-3) / 1e12
         peak = (mm + fp) / (mm / ops2 + fp / fadd) / 1e12  # the kernel's op mix at the measured issue rates
+        traffic = TRAFFIC_PER_PIXEL.get(dom)
         roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Tops/s",
                     "frac": achieved / peak,
-                    "traffic": BOUND_TRAFFIC_PER_PIXEL * npix if dom == "bound" and BOUND_TRAFFIC_PER_PIXEL else None,
-                    "traffic_is": "DRAM bytes of the kernel's launches per step (ncu capture scaled by pixels)",
+                    "traffic": traffic * npix if traffic else None,
+                    "traffic_is": "DRAM bytes of the kernel kind's launches per step (ncu capture scaled by pixels)",
                     "peak_source": f"measured: crb_alu_peak min/max {ops2 / 1e12:.2f} T/s and crb_fadd_peak "
                                    f"{fadd / 1e12:.2f} T/s, weighted by the kernel's {mm} min/max + {fp} other FP32 "
                                    "operations per unit",
                     "achieved_is": f"({mm} + {fp}) FP32 operations x units the kernel processed (counted live) / "
-                                   "its device time (CUDA events around each launch, timed region)",
+                                   "its device time (CUDA events around each launch in the profiled pass)",
                     "units_per_step": units[dom]}
     else:
         roofline = {"bound": "latency", "kernel": dom, "achieved": None, "peak": None, "unit": None, "frac": None,
@@ -633,6 +755,8 @@ def main():
                  + w[5] * BOUND_TEST_MINMAX for w in work)
     roofline.update({
         "kernels": kernels,
+        "profiled_pass": {"steps": args.steps, "ms_per_step": prof_ms / args.steps,
+                          "how": "the timed steps again, no graph, CUDA events around every launch"},
         "work_per_iteration": [{"S": w[0], "Sprime": w[1], "med3": w[2], "cand_tests": w[3],
                                 "cand_full_median": w[4], "bound_tests": w[5]} for w in work],
         "detect_minmax_tops": minmax / (det_ms / args.steps * 1e-3) / 1e12,
@@ -641,18 +765,22 @@ def main():
         / peaks.get("hbm_gbs", 6782.4)})
 
     if rank == 0:
-        line = {"metric": "Mpix/s cleaned at niter=4 (batched, 1 GB300)", "value": value, "unit": "Mpix/s",
+        config = arm_config(args, desc, recipes)
+        config.update({"parallelism": f"replicas x{world}", "tile_shape": args.tile_shape,
+                       "graph": "the work of the call captured once and replayed"})
+        line = {"metric": METRIC, "value": value, "unit": "Mpix/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic",
-                "config": {"workload": desc, "frames": len(frames), "mpix_per_step": npix / 1e6, "niter": niter,
-                           "params": "sigclip 4.5, sigfrac 0.5, objlim 1.0", "l2": "inputs 1.7 GB > L2, no flush"
-                           if args.workload == "batch64" else "see workload",
-                           "parallelism": f"replicas x{world}", "tile_shape": args.tile_shape},
-                "gpu_launches": args.steps * cl.last_launches(), "clocks": clk, "roofline": roofline}
+                "data": "synthetic", "config": config,
+                "gpu_launches": args.steps * launches, "clocks": clk, "roofline": roofline}
         line.update(extras)
         if not args.no_extras:
-            line["cpu_baseline"] = cpu_baseline(recipes)
+            sample = cpu_sample(recipes)
+            ps = parity_sample(torch, sample)
+            line["parity_sample"] = ps
+            line["flips_vs_fp64"] = ps["flips_vs_fp64"]
+            line["fragile"] = ps["fragile"]
+            line["cpu_baseline"] = cpu_baseline(sample)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -105,6 +105,9 @@ typedef struct {
 crb_ctx* crb_create(float gain, float readnoise, float sigclip, float sigfrac, float objlim, int niter);
 crb_ctx* crb_create_ex(float gain, float readnoise, float sigclip, float sigfrac, float objlim, int niter,
                        const crb_options* opts);
+/* Waits for the context's last call, then frees its workspace, graphs, streams
+ * and events. No counterpart in the paper (its actors hold no state between
+ * images). NULL is ignored. */
 void crb_destroy(crb_ctx* ctx);
 
 /* Cleans one frame: img (device, w*h floats) -> out_clean (device, w*h floats,
@@ -116,7 +119,10 @@ int crb_clean(crb_ctx* ctx, const float* img, int w, int h, float* out_clean, ui
               cudaStream_t stream);
 
 /* Cleans n frames of different sizes in one launch per stage and iteration
- * (a persistent tile loop over all frames). Arrays of length n in HOST memory:
+ * (a persistent tile loop over all frames). The paper's director hands every
+ * actor a sub-image and gathers the results with no barrier between them
+ * (Sec. 6.2); here the frames of one call are that set of work items, each
+ * cleaned as by crb_clean. Arrays of length n in HOST memory:
  * imgs[i] (device, ws[i]*hs[i] floats), out_cleans[i], out_masks[i] (device).
  * gains / readnoises may be NULL (use the context's values) or give per-frame
  * values (> 0 and >= 0). The result of each frame equals crb_clean's. */
@@ -155,18 +161,25 @@ int crb_clean_batch_host(crb_ctx* ctx, int n, const float* const* imgs, const in
  * the library until the process exits.
  * Limits: w, h <= 16384, w*h <= 4194304 (4 Mpix, e.g. 2048x2048), niter <= 64;
  * larger frames return CRB_EINVAL with a message (use crb_clean).
- * The first call on a device, with that device current, looks up the device
- * address of the scratch array and sets the kernels' launch attributes; make
- * that first call before any stream capture. Every call on a device uses the
- * same scratch, which keeps the previous call's contents (each call clears
- * what must start at zero): calls that overlap on the GPU -- on unordered
- * streams or from several host threads -- race and corrupt each other's
- * results; order them on one stream or with events. */
+ * The first call on a device, with that device current, loads the library's
+ * device code there if that has not happened yet (CUDA loads modules lazily by
+ * default), which commits the scratch array's memory on that device, looks up
+ * the array's device address and sets the kernels' launch attributes. That
+ * first call can therefore fail with CRB_ECUDA when the device has no room for
+ * the scratch, and it may synchronise the device: make it once at start-up,
+ * before any stream capture (a call with niter = 0 on a 1x1 frame does the
+ * set-up and nothing else of note). Every call on a device uses the same
+ * scratch, which keeps the previous call's contents (each call clears what
+ * must start at zero): calls that overlap on the GPU -- on unordered streams
+ * or from several host threads -- race and corrupt each other's results;
+ * order them on one stream or with events. Calls on different devices are
+ * independent. */
 int crb_clean_noalloc(float gain, float readnoise, float sigclip, float sigfrac, float objlim, int niter,
                       const float* img, int w, int h, float* out_clean, uint8_t* out_mask, cudaStream_t stream);
 
 /* Synchronises `stream` and returns the latched device status of the context
- * (CRB_OK, CRB_ETIMEOUT, CRB_EDEVICE or CRB_ECUDA), then clears it. */
+ * (CRB_OK, CRB_ETIMEOUT, CRB_EDEVICE or CRB_ECUDA), then clears it. No
+ * counterpart in the paper (its MPI calls block until they complete). */
 int crb_sync_status(crb_ctx* ctx, cudaStream_t stream);
 
 /* After crb_sync_status: per-iteration counters of the last crb_clean /
@@ -273,7 +286,10 @@ int crb_server_poll(crb_server* srv, uint64_t* done_tags, double* latency_s, int
 size_t crb_server_frame_bytes(int w, int h);
 
 /* Counters: submitted, done, waves launched, largest wave, rejected submissions,
- * resident bytes, peak resident bytes, queued frames. Returns the count written. */
+ * resident bytes, peak resident bytes, queued frames, the longest host time
+ * spent enqueueing one wave (microseconds; the worker does not hold the
+ * server's lock meanwhile) and the longest time a crb_server_submit waited for
+ * that lock (microseconds). Returns the count written (at most 10). */
 int crb_server_stats(crb_server* srv, long long* out, int max);
 
 /* Stops the worker after the waves in flight complete and frees the server. */

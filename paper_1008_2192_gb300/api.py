@@ -276,10 +276,10 @@ class Server:
         return out
 
     def stats(self):
-        buf = (ctypes.c_longlong * 8)()
-        _lib.load().crb_server_stats(self._h, buf, 8)
+        buf = (ctypes.c_longlong * 10)()
+        _lib.load().crb_server_stats(self._h, buf, 10)
         keys = ("submitted", "done", "waves", "max_wave", "rejected", "resident_bytes", "peak_resident_bytes",
-                "queued")
+                "queued", "max_enqueue_us", "max_submit_wait_us")
         return dict(zip(keys, (int(v) for v in buf)))
 
     def close(self):

@@ -47,19 +47,33 @@ def build(force: bool = False, verbose: bool = False) -> str:
         subprocess.run([sys.executable, gen, net + ".tmp", "--quick"], check=True)
         os.replace(net + ".tmp", net)
     if force or _stale(LIB, _sources() + [net]):
+        units = ["crb.cu", "noalloc.cu", "serve.cu", "poisson.cu"]
+        common = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                  "-I", os.path.join(ROOT, "include"), "-I", GEN]
+        if verbose:
+            common.insert(1, "-Xptxas=-v")
+        # the translation units compile in parallel, then link into one shared library
+        procs = []
+        for u in units:
+            obj = os.path.join(OUT, u + f".{os.getpid()}.o")
+            procs.append((obj, subprocess.Popen(common + ["-c", os.path.join(CSRC, u), "-o", obj],
+                                                stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
+        log, failed = "", False
+        for obj, pr in procs:
+            out, _ = pr.communicate()
+            log += out
+            failed |= pr.returncode != 0
+        if failed:
+            raise RuntimeError("nvcc failed:\n" + log)
+        if verbose:
+            print(log)
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-               "-I", os.path.join(ROOT, "include"), "-I", GEN,
-               os.path.join(CSRC, "crb.cu"), os.path.join(CSRC, "noalloc.cu"), os.path.join(CSRC, "serve.cu"),
-               os.path.join(CSRC, "poisson.cu"),
-               "-o", tmp]
-        if verbose:
-            cmd.insert(1, "-Xptxas=-v")
-        r = subprocess.run(cmd, capture_output=True, text=True)
+        r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp] + [o for o, _ in procs], capture_output=True,
+                           text=True)
+        for o, _ in procs:
+            os.remove(o)
         if r.returncode != 0:
-            raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
-        if verbose:
-            print(r.stdout + r.stderr)
+            raise RuntimeError("nvcc link failed:\n" + r.stdout + r.stderr)
         os.replace(tmp, LIB)
     return LIB
 

@@ -133,22 +133,28 @@ struct crb_ctx {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   // Descriptors (and the queue pipeline's frame table: frame of each
-  // 2^kTabShift pixels) go through a ring of kDescSlots staging and device
+  // 2^kTabShift pixels) are staged in a ring of kDescSlots page-locked host
   // buffers, so that a call waits only for the upload of the call kDescSlots
-  // back before refilling a staging buffer. The fields below view the slot of
-  // the current call.
+  // back before refilling one, and uploaded into one device buffer of the
+  // context: calls on a context are ordered (each starts after the previous
+  // one's completion event), so no kernel still reads the device copy when the
+  // next upload overwrites it, and a captured graph always finds its
+  // descriptors at the same address. The fields below view the slot of the
+  // current call.
   struct DescSlot {
-    crb::Frame *d_frames = nullptr, *h_frames = nullptr;
-    uint32_t *d_tab = nullptr, *h_tab = nullptr;
+    crb::Frame* h_frames = nullptr;
+    uint32_t* h_tab = nullptr;
     int frames_cap = 0;
     size_t tab_cap = 0;
     cudaEvent_t upload_ev = nullptr;
   } slot[kDescSlots];
   int cur = 0;
-  crb::Frame* d_frames = nullptr;
-  crb::Frame* h_frames = nullptr;  // pinned staging
-  uint32_t* d_tab = nullptr;
+  crb::Frame* d_frames = nullptr;  // device descriptors (capacity d_frames_cap)
+  crb::Frame* h_frames = nullptr;  // pinned staging of the current slot
+  uint32_t* d_tab = nullptr;       // device frame table (capacity d_tab_cap)
   uint32_t* h_tab = nullptr;
+  int d_frames_cap = 0;
+  size_t d_tab_cap = 0;
   size_t tab_n = 0;  // entries
   unsigned long long* d_counters = nullptr;
   int counters_cap = 0;  // in unsigned long longs
@@ -265,38 +271,47 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
 }
 
 // Moves to the next descriptor slot, with room for n frames and tab_entries
-// table entries, once the slot's previous upload has run; sets the views.
+// table entries, once the slot's previous upload has run; sets the views and
+// grows the device copies if needed.
 int next_desc_slot(crb_ctx* c, int n, size_t tab_entries) {
   c->cur = (c->cur + 1) % kDescSlots;
   crb_ctx::DescSlot& S = c->slot[c->cur];
   // generous first capacities, so that growing (which synchronises the device) is rare
   n = std::max(n, 64);
   tab_entries = std::max<size_t>(tab_entries, 8192);
-  if (n > S.frames_cap || tab_entries > S.tab_cap) {
+  if (n > S.frames_cap || tab_entries > S.tab_cap || n > c->d_frames_cap || tab_entries > c->d_tab_cap) {
     CRB_CUDA(cudaDeviceSynchronize());
     if (n > S.frames_cap) {
-      cudaFree(S.d_frames);
       cudaFreeHost(S.h_frames);
-      S.d_frames = S.h_frames = nullptr;
+      S.h_frames = nullptr;
       S.frames_cap = 0;
-      CRB_CUDA(cudaMalloc(&S.d_frames, sizeof(crb::Frame) * size_t(n)));
       CRB_CUDA(cudaMallocHost(&S.h_frames, sizeof(crb::Frame) * size_t(n)));
       S.frames_cap = n;
     }
     if (tab_entries > S.tab_cap) {
-      cudaFree(S.d_tab);
       cudaFreeHost(S.h_tab);
-      S.d_tab = S.h_tab = nullptr;
+      S.h_tab = nullptr;
       S.tab_cap = 0;
-      CRB_CUDA(cudaMalloc(&S.d_tab, sizeof(uint32_t) * tab_entries));
       CRB_CUDA(cudaMallocHost(&S.h_tab, sizeof(uint32_t) * tab_entries));
       S.tab_cap = tab_entries;
     }
+    if (n > c->d_frames_cap) {
+      cudaFree(c->d_frames);
+      c->d_frames = nullptr;
+      c->d_frames_cap = 0;
+      CRB_CUDA(cudaMalloc(&c->d_frames, sizeof(crb::Frame) * size_t(n)));
+      c->d_frames_cap = n;
+    }
+    if (tab_entries > c->d_tab_cap) {
+      cudaFree(c->d_tab);
+      c->d_tab = nullptr;
+      c->d_tab_cap = 0;
+      CRB_CUDA(cudaMalloc(&c->d_tab, sizeof(uint32_t) * tab_entries));
+      c->d_tab_cap = tab_entries;
+    }
   }
   CRB_CUDA(cudaEventSynchronize(S.upload_ev));  // the staging buffers are free again
-  c->d_frames = S.d_frames;
   c->h_frames = S.h_frames;
-  c->d_tab = S.d_tab;
   c->h_tab = S.h_tab;
   c->upload_ev = S.upload_ev;
   return CRB_OK;
@@ -904,9 +919,9 @@ void crb_destroy(crb_ctx* c) {
     cudaFree(c->d_stage[i]);
   }
   cudaFree(c->ws);
+  cudaFree(c->d_frames);
+  cudaFree(c->d_tab);
   for (auto& sl : c->slot) {
-    cudaFree(sl.d_frames);
-    cudaFree(sl.d_tab);
     if (sl.h_frames) cudaFreeHost(sl.h_frames);
     if (sl.h_tab) cudaFreeHost(sl.h_tab);
     if (sl.upload_ev) cudaEventDestroy(sl.upload_ev);

@@ -46,7 +46,7 @@ struct DeviceSetup {
 };
 
 std::mutex g_mu;
-std::vector<DeviceSetup> g_setup;
+std::vector<DeviceSetup> g_setup;  // by device; read and written under g_mu only
 
 using Detect = void (*)(const crb::Frame*, int, long long, crb::Params, int, int);
 using Replace = void (*)(const crb::Frame*, int, long long, int, int, int);
@@ -71,8 +71,10 @@ int cuda_err(cudaError_t e, const char* what) {
 }
 
 // Once per device, with that device current: the device address of the
-// scratch array and the kernels' launch attributes.
-int setup_current_device(DeviceSetup** out) {
+// scratch array and the kernels' launch attributes. The caller gets a copy, so
+// a first call on another device (which may grow g_setup) from another host
+// thread cannot move the entry under it.
+int setup_current_device(DeviceSetup* out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_err(e, "cudaGetDevice");
@@ -98,7 +100,7 @@ int setup_current_device(DeviceSetup** out) {
     s.scratch = static_cast<unsigned char*>(p);
     s.done = true;
   }
-  *out = &s;
+  *out = s;
   return CRB_OK;
 }
 
@@ -126,9 +128,10 @@ extern "C" int crb_clean_noalloc(float gain, float readnoise, float sigclip, flo
   if (overlap(img, n * 4, out_clean, n * 4) || overlap(img, n * 4, out_mask, n) || overlap(out_clean, n * 4, out_mask, n))
     return err(CRB_EALIAS, "crb_clean_noalloc: outputs must not overlap the input or each other");
 
-  DeviceSetup* s = nullptr;
-  int rc = setup_current_device(&s);
+  DeviceSetup setup;
+  int rc = setup_current_device(&setup);
   if (rc != CRB_OK) return rc;
+  const DeviceSetup* s = &setup;
 
   cudaError_t e;
   if (niter == 0) {
@@ -162,6 +165,7 @@ extern "C" int crb_clean_noalloc(float gain, float readnoise, float sigclip, flo
   const crb::Params p{sigclip, sigfrac, objlim, 0};
 
   noalloc_prepare<<<1, 128, 0, stream>>>(f, desc, f.counters, 2 * niter);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e, "crb_clean_noalloc: descriptor upload");
   if ((e = cudaMemsetAsync(f.bits_a, 0, sizeof(uint32_t) * size_t(f.wpr) * size_t(h), stream)) != cudaSuccess)
     return cuda_err(e, "crb_clean_noalloc: clearing flag bits");
   const int dgrid = int(std::min<long long>(tiles, (long long)s->sms * s->occ_detect));

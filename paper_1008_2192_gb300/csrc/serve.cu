@@ -81,6 +81,8 @@ struct crb_server {
   // statistics
   long long n_submitted = 0, n_done = 0, n_waves = 0, n_rejected = 0, max_wave = 0;
   size_t peak_resident = 0;
+  double max_enqueue_s = 0;      // longest enqueue of a wave (host time in crb_clean_batch and its event)
+  double max_submit_wait_s = 0;  // longest time a submission waited for the server lock
 };
 
 namespace {
@@ -99,10 +101,17 @@ size_t frame_bytes(int w, int h) {
   return n * (4 + 4 + 1) + n * 4 * 4 + n * 5 * 4 + 12 * plane + 2 * 4 * cells + 3 * 4 * segs;
 }
 
-void launch_wave(crb_server* s, int slot, std::vector<Request>&& reqs) {
+// Enqueues one wave on slot `slot`. Called by the worker with the server lock
+// held in `lk`; the lock is released while the wave is enqueued (which can take
+// milliseconds: a first call of a signature grows the slot's workspace or
+// captures a graph), so that submissions and polls are not held up, and taken
+// again to publish the wave. Only the worker uses the slot's context and stream.
+void launch_wave(crb_server* s, int slot, std::vector<Request>&& reqs, std::unique_lock<std::mutex>& lk) {
   Wave wv;
   wv.reqs = std::move(reqs);
   wv.slot = slot;
+  s->busy[size_t(slot)] = true;
+  lk.unlock();
   wv.t_launch = now_s();
   const int n = int(wv.reqs.size());
   std::vector<const float*> imgs(size_t(n), nullptr);
@@ -127,17 +136,20 @@ void launch_wave(crb_server* s, int slot, std::vector<Request>&& reqs) {
                            outs.data(), masks.data(), s->stream[size_t(slot)]);
   if (rc == CRB_OK && cudaEventCreateWithFlags(&wv.done, cudaEventDisableTiming) != cudaSuccess) rc = CRB_ECUDA;
   if (rc == CRB_OK && cudaEventRecord(wv.done, s->stream[size_t(slot)]) != cudaSuccess) rc = CRB_ECUDA;
+  const double t_enq = now_s() - wv.t_launch;
+  lk.lock();
+  s->max_enqueue_s = std::max(s->max_enqueue_s, t_enq);
   if (rc != CRB_OK) {  // report every frame of the wave as failed
     for (const Request& r : wv.reqs) {
       s->done.push_back(Done{r.tag, r.t_submit, now_s(), rc});
       s->resident -= r.bytes;
     }
     if (wv.done) cudaEventDestroy(wv.done);
+    s->busy[size_t(slot)] = false;
     s->error = rc;
     s->cv_done.notify_all();
     return;
   }
-  s->busy[size_t(slot)] = true;
   s->n_waves += 1;
   s->max_wave = std::max<long long>(s->max_wave, n);
   s->inflight.push_back(std::move(wv));
@@ -184,7 +196,7 @@ void worker_main(crb_server* s) {
           reqs.push_back(s->pending.front());
           s->pending.pop_front();
         }
-        launch_wave(s, slot, std::move(reqs));
+        launch_wave(s, slot, std::move(reqs), lk);
         continue;
       }
     }
@@ -252,7 +264,9 @@ int crb_server_submit(crb_server* s, const float* img, int w, int h, float gain,
     return CRB_EINVAL;
   }
   const size_t need = frame_bytes(w, h);
+  const double t0 = now_s();
   std::lock_guard<std::mutex> lk(s->mu);
+  s->max_submit_wait_s = std::max(s->max_submit_wait_s, now_s() - t0);
   if (s->error != CRB_OK) return s->error;
   if (need > s->budget - std::min(s->budget, s->resident)) {
     s->n_rejected += 1;
@@ -289,9 +303,12 @@ size_t crb_server_frame_bytes(int w, int h) { return (w < 1 || h < 1) ? 0 : fram
 int crb_server_stats(crb_server* s, long long* out, int max) {
   if (!s || !out || max < 0) return -1;
   std::lock_guard<std::mutex> lk(s->mu);
-  const long long v[8] = {s->n_submitted, s->n_done, s->n_waves, s->max_wave, s->n_rejected,
-                          (long long)s->resident, (long long)s->peak_resident, (long long)s->pending.size()};
-  const int k = std::min(max, 8);
+  const long long v[10] = {s->n_submitted,       s->n_done,
+                           s->n_waves,           s->max_wave,
+                           s->n_rejected,        (long long)s->resident,
+                           (long long)s->peak_resident, (long long)s->pending.size(),
+                           (long long)(s->max_enqueue_s * 1e6), (long long)(s->max_submit_wait_s * 1e6)};
+  const int k = std::min(max, 10);
   for (int i = 0; i < k; ++i) out[i] = v[i];
   return k;
 }

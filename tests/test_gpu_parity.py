@@ -8,8 +8,8 @@ import pytest
 import oracle
 import synth
 from synth import workloads
-from gpu_util import (assert_clean_matches_f64, assert_map_close, crop_with_context, dev, gpu_clean, host,
-                      params_of)
+from gpu_util import (assert_clean_matches_f64, assert_map_close, compare_f64, crop_with_context, dev,
+                      gpu_clean, host, map_floors, params_of)
 
 pytestmark = pytest.mark.gpu
 
@@ -60,11 +60,12 @@ def test_stage_maps_match_oracle(w, h):
         else:
             assert np.array_equal(g, o.astype(np.float32)), name
     assert np.array_equal(M, r32.Mk) and np.array_equal(J, r32.Ik)
+    floors = map_floors(img, r64.maps)
     for name in ("m5", "lplus", "noise", "s", "sprime", "m3"):
-        assert_map_close(gm[name], r64.maps[name], name)
+        assert_map_close(gm[name], r64.maps[name], name, floors[name])
     both64 = (gm["sprime"] > 4.5) & (r64.maps["sprime"] > 4.5)
     for name in lazy:
-        assert_map_close(gm[name][both64], r64.maps[name][both64], name)
+        assert_map_close(gm[name][both64], r64.maps[name][both64], name, floors[name][both64])
     ok = r64.fragile == 0
     assert np.array_equal(M[ok], r64.Mk[ok])
 
@@ -177,19 +178,34 @@ def test_alias_and_invalid_sizes_rejected(cl):
     assert e.value.status == L.CRB_EALIAS
     lib = L.load()
     import ctypes
-    rc = lib.crb_clean(cl.handle, ctypes.c_void_p(t.data_ptr()), 0, 30, ctypes.c_void_p(t.data_ptr() + 4),
-                       ctypes.c_void_p(t.data_ptr()), None)
+    o = torch.empty_like(t)
+    m = torch.empty(t.shape, dtype=torch.uint8, device="cuda")
+    for (w, h) in ((0, 30), (40, 0), (-1, 30)):
+        rc = lib.crb_clean(cl.handle, ctypes.c_void_p(t.data_ptr()), w, h, ctypes.c_void_p(o.data_ptr()),
+                           ctypes.c_void_p(m.data_ptr()), None)
+        assert rc == L.CRB_EINVAL
+    rc = lib.crb_clean(cl.handle, ctypes.c_void_p(t.data_ptr()), 40, 30, None, ctypes.c_void_p(m.data_ptr()), None)
     assert rc == L.CRB_EINVAL
 
 
-def _check_crops(img, out, mask, niter, crops, P):
-    """Oracle on crops with 8*niter context (exact by the dependency radius) vs the GPU full frame."""
+def _check_crops(img, out, mask, niter, crops, P, what=""):
+    """Oracle on crops with 8*niter context (exact by the dependency radius) vs the GPU full frame:
+    bit-identical to the FP32 oracle; against FP64, mask flips only on fragile pixels and cleaned
+    values within tolerance. Returns (flips, fragile pixels) summed over the crops."""
     ctx = 8 * niter
+    flips = fragile = 0
     for (y0, x0, hh, ww) in crops:
         c, sl = crop_with_context(img, y0, x0, hh, ww, ctx)
+        go, gm = out[y0:y0 + hh, x0:x0 + ww], mask[y0:y0 + hh, x0:x0 + ww]
         r = oracle.clean(c, P, niter, precision="f32")
-        assert np.array_equal(r.mask[sl], mask[y0:y0 + hh, x0:x0 + ww]), (y0, x0)
-        assert np.array_equal(r.clean[sl], out[y0:y0 + hh, x0:x0 + ww]), (y0, x0)
+        assert np.array_equal(r.mask[sl], gm), (y0, x0)
+        assert np.array_equal(r.clean[sl], go), (y0, x0)
+        r64 = oracle.clean(c, P, niter, fragile=True)
+        a, b = compare_f64(go, gm, r64.clean[sl], r64.mask[sl], r64.fragile[sl], f"{what} crop {(y0, x0)}")
+        flips += a
+        fragile += b
+    print(f"{what}: {len(crops)} crops, mask flips vs FP64 {flips}, fragile pixels {fragile}")
+    return flips, fragile
 
 
 def test_4096_sampled_crops():
@@ -201,7 +217,7 @@ def test_4096_sampled_crops():
     rng = np.random.default_rng(0)
     crops = [(0, 0, 256, 256), (0, 3840, 256, 256), (3840, 0, 256, 256), (3840, 3840, 256, 256)]
     crops += [(int(rng.integers(0, 3840)), int(rng.integers(0, 3840)), 256, 256) for _ in range(6)]
-    _check_crops(img, out, mask, 4, crops, params_of(rec))
+    _check_crops(img, out, mask, 4, crops, params_of(rec), "4096x4096")
 
 
 def test_mosaic_16384_sampled_crops():
@@ -215,7 +231,25 @@ def test_mosaic_16384_sampled_crops():
              (S // 2, S - n)]
     rng = np.random.default_rng(4)
     crops += [(int(rng.integers(0, S - n)), int(rng.integers(0, S - n))) for _ in range(8)]
-    _check_crops(img, out, mask, 4, [(y, x, n, n) for (y, x) in crops], params_of(rec))
+    _check_crops(img, out, mask, 4, [(y, x, n, n) for (y, x) in crops], params_of(rec), "16384x16384")
+
+
+def test_batch_size_classes_f64():
+    """One frame of each size class of the 64-frame batch (800^2, 1024^2, 2048x4096, 4096^2), with its
+    per-frame gain and read noise, cleaned in one batched call: 256x256 crops (corners and random
+    ones) against the FP32 oracle (bit-identical) and the FP64 oracle (flips only on fragile pixels)."""
+    recs = [workloads.batch_64()[i] for i in (0, 16, 32, 48)]
+    imgs = [workloads.make(r) for r in recs]
+    c = Cleaner(niter=4)
+    outs, masks = c.clean_batch([dev(a) for a in imgs], [r["gain"] for r in recs], [r["readnoise"] for r in recs])
+    c.sync()
+    rng = np.random.default_rng(6)
+    for rec, img, o, m in zip(recs, imgs, outs, masks):
+        H, W = img.shape
+        n = 256
+        crops = [(0, 0, n, n), (H - n, W - n, n, n)]
+        crops += [(int(rng.integers(0, H - n)), int(rng.integers(0, W - n)), n, n) for _ in range(4)]
+        _check_crops(img, host(o), host(m), 4, crops, params_of(rec), f"{W}x{H} gain {rec['gain']:.2f}")
 
 
 @pytest.mark.parametrize("pipeline", ["queue", "tile"])

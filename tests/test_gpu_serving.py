@@ -85,3 +85,36 @@ def test_budget_admission():
     while not got and time.time() - t0 < 30:
         got = one.poll(block_ms=100)
     one.close()
+
+
+def test_submit_not_held_up_by_a_wave_enqueue():
+    """The worker enqueues a wave without holding the server's lock: while it enqueues the first wave of a
+    fresh slot (which grows the slot's workspace and staging buffers, milliseconds of host work), further
+    submissions return at once. The server records its longest wave enqueue and the longest time a
+    submission waited for the lock."""
+    big = torch.from_numpy(synth.frame(4096, 4096, seed=2)).cuda()
+    small = torch.from_numpy(synth.frame(64, 64, seed=3)).cuda()
+    srv = Server(niter=4, budget_bytes=8 << 30, max_inflight=1, max_batch=64)
+    bufs = [(torch.empty_like(big), torch.empty(big.shape, dtype=torch.uint8, device="cuda"))]
+    bufs += [(torch.empty_like(small), torch.empty(small.shape, dtype=torch.uint8, device="cuda"))
+             for _ in range(400)]
+    torch.cuda.synchronize()
+    assert srv.submit(big, *bufs[0], tag=0, gain=7.0, readnoise=5.0)
+    tag, t0 = 1, time.perf_counter()
+    while time.perf_counter() - t0 < 0.2 and tag < len(bufs):  # submissions while the first wave is enqueued
+        assert srv.submit(small, *bufs[tag], tag=tag, gain=7.0, readnoise=5.0)
+        tag += 1
+    done = set()
+    t0 = time.time()
+    while len(done) < tag and time.time() - t0 < 60:
+        for t, lat, st in srv.poll(block_ms=100):
+            assert st == 0
+            done.add(t)
+    assert len(done) == tag
+    st = srv.stats()
+    print(f"longest wave enqueue {st['max_enqueue_us']} us, longest submit wait {st['max_submit_wait_us']} us, "
+          f"{tag} submissions, {st['waves']} waves")
+    assert st["max_enqueue_us"] > 0
+    if st["max_enqueue_us"] > 2000:  # a window in which a held lock would have shown
+        assert st["max_submit_wait_us"] < st["max_enqueue_us"] / 4
+    srv.close()
