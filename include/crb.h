@@ -177,6 +177,45 @@ int crb_clean_batch_host(crb_ctx* ctx, int n, const float* const* imgs, const in
 int crb_clean_noalloc(float gain, float readnoise, float sigclip, float sigfrac, float objlim, int niter,
                       const float* img, int w, int h, float* out_clean, uint8_t* out_mask, cudaStream_t stream);
 
+/* ---- The paper's 2-D image segmentation (Sec. 6.2, Sec. 6.3.1) --------------
+ * CRBLASTER cuts a frame into N rectangular sub-images of nearly equal area and
+ * widens each by BORDER pixels beyond every edge it shares with another, so
+ * that its actors clean them with no communication. A rectangle here is its
+ * interior (x0, y0, w, h) and its context region (cx0, cy0, cw, ch): the
+ * interior widened by `context` pixels on each side, clipped to the frame. A
+ * context of 8 * niter pixels makes the cleaned interior identical to that of
+ * the whole-frame clean (every iteration's result depends on its input within
+ * 8 pixels: 6 for the flags, 2 more for the replacement). */
+typedef struct {
+  int x0, y0, w, h;      /* interior */
+  int cx0, cy0, cw, ch;  /* context region (contains the interior) */
+} crb_rect;
+
+/* The segmentation of a w x h frame into nparts = cols x rows rectangles, row
+ * by row (rects[r * cols + c]); the first w % cols columns (h % rows rows) are
+ * one pixel wider (taller). cols = 0 takes the factorisation whose sub-images
+ * are closest to square (|log(aspect)| smallest, ties to fewer columns), the
+ * paper's 2-D algorithm: a prime nparts gives 1 x nparts horizontal slices,
+ * its 1-D scheme, which cols = 1 forces. Writes *out_cols, *out_rows (if not
+ * NULL) and, when max_rects >= nparts, the rectangles; returns nparts, or
+ * -CRB_EINVAL (sizes < 1, context < 0, cols not dividing nparts, or no cut that
+ * fits the frame). Host only: needs no GPU. */
+int crb_partition(int w, int h, int nparts, int cols, int context, crb_rect* rects, int max_rects, int* out_cols,
+                  int* out_rows);
+
+/* Cleans n rectangles of one frame img (device, w*h floats) as independent
+ * frames, each its context region, and writes each rectangle's interior, only,
+ * into out_clean and out_mask (device, w*h): the work of the paper's actors
+ * and the director's assembly (Sec. 6.2) on one GPU. Rectangles whose
+ * interiors tile the frame fill the outputs; with context >= 8 * niter (as
+ * crb_partition gives) the result equals crb_clean's. The context region of
+ * every rectangle must contain its interior and lie in the frame
+ * (CRB_EINVAL); outputs must not overlap img (CRB_EALIAS). The crops go
+ * through the context's own staging buffers (grown on demand) and one
+ * crb_clean_batch. Asynchronous on `stream`. */
+int crb_clean_rects(crb_ctx* ctx, const float* img, int w, int h, int n, const crb_rect* rects, float* out_clean,
+                    uint8_t* out_mask, cudaStream_t stream);
+
 /* Synchronises `stream` and returns the latched device status of the context
  * (CRB_OK, CRB_ETIMEOUT, CRB_EDEVICE or CRB_ECUDA), then clears it. No
  * counterpart in the paper (its MPI calls block until they complete). */

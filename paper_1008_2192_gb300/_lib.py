@@ -26,6 +26,11 @@ class crb_options(ctypes.Structure):
                 ("no_fusion", ctypes.c_int), ("pipeline", ctypes.c_int)]
 
 
+class crb_rect(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_int), ("y0", ctypes.c_int), ("w", ctypes.c_int), ("h", ctypes.c_int),
+                ("cx0", ctypes.c_int), ("cy0", ctypes.c_int), ("cw", ctypes.c_int), ("ch", ctypes.c_int)]
+
+
 # (name, restype, argtypes)
 _vp, _ci, _cf = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
 _PP = ctypes.POINTER(ctypes.c_void_p)
@@ -59,6 +64,8 @@ SIGNATURES = {
     "crb_server_destroy": (None, [_vp]),
     "crb_num_tile_shapes": (_ci, []),
     "crb_tile_shape": (_ci, [_ci, _PI, _PI]),
+    "crb_partition": (_ci, [_ci, _ci, _ci, _ci, _ci, ctypes.POINTER(crb_rect), _ci, _PI, _PI]),
+    "crb_clean_rects": (_ci, [_vp, _vp, _ci, _ci, _ci, ctypes.POINTER(crb_rect), _vp, _vp, _vp]),
     "crb_poisson": (_ci, [_vp, _ci, _ci, ctypes.c_uint64, _vp, _vp]),
     "crb_poisson_batch": (_ci, [_ci, _PP, _PI, _PI, ctypes.POINTER(ctypes.c_uint64), _PP, _vp]),
     "crb_last_error": (ctypes.c_char_p, []),

@@ -120,6 +120,24 @@ class Cleaner:
                                               _stream(stream))
         check(rc, "crb_clean_batch_host")
 
+    def clean_rects_into(self, img, rects, out_clean, out_mask, stream=None):
+        """crb_clean_rects: each rectangle (partition.Rect) cleaned as its context region, its interior
+        written into out_clean / out_mask."""
+        from .partition import to_c
+        _check_img(img)
+        h, w = img.shape
+        arr = to_c(rects)
+        rc = _lib.load().crb_clean_rects(self._h, _ptr(img), w, h, len(rects), arr, _ptr(out_clean),
+                                         _ptr(out_mask), _stream(stream))
+        check(rc, "crb_clean_rects")
+
+    def clean_rects(self, img, rects, stream=None):
+        """crb_clean_rects into new tensors (pixels outside every interior are left unset)."""
+        out = torch.empty_like(img)
+        mask = torch.empty(img.shape, dtype=torch.uint8, device=img.device)
+        self.clean_rects_into(img, rects, out, mask, stream)
+        return out, mask
+
     def clean_batch(self, imgs, gains=None, readnoises=None, stream=None):
         outs = [torch.empty_like(t) for t in imgs]
         masks = [torch.empty(t.shape, dtype=torch.uint8, device=t.device) for t in imgs]

@@ -47,7 +47,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         subprocess.run([sys.executable, gen, net + ".tmp", "--quick"], check=True)
         os.replace(net + ".tmp", net)
     if force or _stale(LIB, _sources() + [net]):
-        units = ["crb.cu", "noalloc.cu", "serve.cu", "poisson.cu"]
+        units = ["crb.cu", "noalloc.cu", "serve.cu", "poisson.cu", "partition.cu"]
         common = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                   "-I", os.path.join(ROOT, "include"), "-I", GEN]
         if verbose:

@@ -178,6 +178,9 @@ struct crb_ctx {
   cudaEvent_t h_entry = nullptr, h_in[kStageSlots] = {}, h_cmp[kStageSlots] = {}, h_free[kStageSlots] = {};
   char* d_stage[kStageSlots] = {};
   size_t stage_cap = 0;
+  // crb_clean_rects: the crops (input, cleaned, mask) of the rectangles of a call
+  char* d_rects = nullptr;
+  size_t rects_cap = 0;
   std::vector<std::pair<std::vector<long long>, int>> tuned;
 
   // profiling: event pairs around launches, by kernel kind (0 detect, 1 replace)
@@ -919,6 +922,7 @@ void crb_destroy(crb_ctx* c) {
     cudaFree(c->d_stage[i]);
   }
   cudaFree(c->ws);
+  cudaFree(c->d_rects);
   cudaFree(c->d_frames);
   cudaFree(c->d_tab);
   for (auto& sl : c->slot) {
@@ -1085,6 +1089,74 @@ int crb_clean_batch_host(crb_ctx* c, int n, const float* const* imgs, const int*
   // `stream` continues after the last copy-out
   CRB_CUDA(cudaEventRecord(c->h_entry, c->hs_out));
   CRB_CUDA(cudaStreamWaitEvent(stream, c->h_entry, 0));
+  return CRB_OK;
+}
+
+int crb_clean_rects(crb_ctx* c, const float* img, int w, int h, int n, const crb_rect* rects, float* out_clean,
+                    uint8_t* out_mask, cudaStream_t stream) {
+  if (!c) return fail(CRB_EINVAL, "null context");
+  int rc = check_frame(img, w, h, out_clean, out_mask);
+  if (rc) return rc;
+  if (n < 0 || (n > 0 && !rects)) return fail(CRB_EINVAL, "crb_clean_rects: invalid rectangle array");
+  if (n == 0) return CRB_OK;
+  auto crop_bytes = [](const crb_rect& r) {
+    const size_t px = size_t(r.cw) * size_t(r.ch);
+    return 2 * align256(px * 4) + align256(px);
+  };
+  size_t need = 0;
+  for (int i = 0; i < n; ++i) {
+    const crb_rect& r = rects[i];
+    const bool ok = r.w >= 1 && r.h >= 1 && r.cx0 >= 0 && r.cy0 >= 0 && r.cx0 <= r.x0 && r.cy0 <= r.y0 &&
+                    r.x0 + r.w <= r.cx0 + r.cw && r.y0 + r.h <= r.cy0 + r.ch && r.cx0 + r.cw <= w &&
+                    r.cy0 + r.ch <= h;
+    if (!ok)
+      return fail(CRB_EINVAL, "crb_clean_rects: rectangle " + std::to_string(i) +
+                                  ": the context region must contain the interior and lie in the frame");
+    need += crop_bytes(r);
+  }
+  if (need > c->rects_cap) {
+    CRB_CUDA(cudaDeviceSynchronize());
+    cudaFree(c->d_rects);
+    c->d_rects = nullptr;
+    c->rects_cap = 0;
+    const cudaError_t e = cudaMalloc(&c->d_rects, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CRB_ENOMEM, "crb_clean_rects: crops of " + std::to_string(need) + " bytes could not be allocated");
+    }
+    c->rects_cap = need;
+  }
+  // the crops are reused: copy into them after the context's previous call is done
+  if (c->any_call) CRB_CUDA(cudaStreamWaitEvent(stream, c->done_ev, 0));
+  std::vector<const float*> in(static_cast<size_t>(n));
+  std::vector<float*> out(static_cast<size_t>(n));
+  std::vector<uint8_t*> msk(static_cast<size_t>(n));
+  std::vector<int> cws(static_cast<size_t>(n)), chs(static_cast<size_t>(n));
+  char* p = c->d_rects;
+  for (int i = 0; i < n; ++i) {
+    const crb_rect& r = rects[i];
+    const size_t px = size_t(r.cw) * size_t(r.ch);
+    float* ci = reinterpret_cast<float*>(p);
+    in[size_t(i)] = ci;
+    out[size_t(i)] = reinterpret_cast<float*>(p + align256(px * 4));
+    msk[size_t(i)] = reinterpret_cast<uint8_t*>(p + 2 * align256(px * 4));
+    cws[size_t(i)] = r.cw;
+    chs[size_t(i)] = r.ch;
+    p += crop_bytes(r);
+    CRB_CUDA(cudaMemcpy2DAsync(ci, size_t(r.cw) * 4, img + size_t(r.cy0) * w + r.cx0, size_t(w) * 4,
+                               size_t(r.cw) * 4, size_t(r.ch), cudaMemcpyDeviceToDevice, stream));
+  }
+  rc = crb_clean_batch(c, n, in.data(), cws.data(), chs.data(), nullptr, nullptr, out.data(), msk.data(), stream);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {  // the interiors into the frame (the director's assembly)
+    const crb_rect& r = rects[i];
+    const size_t o = size_t(r.y0 - r.cy0) * r.cw + size_t(r.x0 - r.cx0);
+    CRB_CUDA(cudaMemcpy2DAsync(out_clean + size_t(r.y0) * w + r.x0, size_t(w) * 4, out[size_t(i)] + o,
+                               size_t(r.cw) * 4, size_t(r.w) * 4, size_t(r.h), cudaMemcpyDeviceToDevice, stream));
+    CRB_CUDA(cudaMemcpy2DAsync(out_mask + size_t(r.y0) * w + r.x0, size_t(w), msk[size_t(i)] + o, size_t(r.cw),
+                               size_t(r.w), size_t(r.h), cudaMemcpyDeviceToDevice, stream));
+  }
+  CRB_CUDA(cudaEventRecord(c->done_ev, stream));  // the next call waits for these reads of the crops
   return CRB_OK;
 }
 
