@@ -24,10 +24,11 @@
 //     polynomial of e^r to degree 13 by Horner's rule, then scaling by 2^n.
 //     Any kernel that follows the same steps takes every decision q >= e^-mu
 //     identically.
-// Parity status: the generator's statistics (mean, variance, the distribution
-// against the Poisson pmf) and Algorithm Q on given uniforms are pinned by
-// the tests; that the paper's own generator drew the same uniforms is not
-// (parity unpinned against the paper for the choice of uniform generator).
+// Parity status: the uniform stream against published SplitMix64 outputs, the
+// generator's statistics (mean, variance, the distribution against the Poisson
+// pmf) and Algorithm Q on given uniforms are pinned by the tests; that the
+// paper's own generator drew the same uniforms is not (parity unpinned against
+// the paper for the choice of uniform generator).
 
 #include <cmath>
 #include <cstdint>

@@ -1,7 +1,8 @@
 """Pins of the POISSON work function oracle (Sec. 6.3.2), usable with any build of ``poisson.cpp``.
 
 Each pin takes a ``PoissonLib`` and raises on a mismatch with what mathematics fixes: e^-mu against
-the C library's exp; Algorithm Q on hand-worked uniform sequences (closed forms); the deviates' mean,
+the C library's exp; Algorithm Q on hand-worked uniform sequences (closed forms); the generator's
+stream against published SplitMix64 outputs; the deviates' mean,
 variance and histogram against the Poisson pmf on the paper's 750x750 test image of 24.3 and at other
 means; the seed, edge-value and cap rules.
 """
@@ -9,7 +10,9 @@ means; the seed, edge-value and cap rules.
 from __future__ import annotations
 
 import ctypes
+import json
 import math
+import os
 
 import numpy as np
 
@@ -47,6 +50,17 @@ class PoissonLib:
         if self.lib.oracle_poisson(a.ctypes.data, w, h, seed & (2**64 - 1), out.ctypes.data) != 0:
             raise ValueError("oracle_poisson rejected its arguments")
         return out
+
+
+def pin_stream_published_outputs(P):
+    """The counter-based stream is SplitMix64: value(s, j) is the (j+1)-th output of the sequential
+    generator started at state s, which the published reference outputs fix (tests/golden/splitmix64.json)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "splitmix64.json")
+    with open(path) as f:
+        seqs = json.load(f)["sequences"]
+    for seed, outs in seqs.items():
+        for j, v in enumerate(outs):
+            assert P.stream_value(int(seed), j) == int(v, 0), (seed, j)
 
 
 def pin_exp_neg(P):
@@ -114,4 +128,5 @@ def pin_seeds_and_edges(P):
     assert abs(out[0, 4] - 700) < 150 and abs(out[0, 5] - 700) < 150  # mu above 700 is taken as 700
 
 
-ALL_PINS = [pin_exp_neg, pin_algorithm_q_hand_cases, pin_poisson_law, pin_seeds_and_edges]
+ALL_PINS = [pin_stream_published_outputs, pin_exp_neg, pin_algorithm_q_hand_cases, pin_poisson_law,
+            pin_seeds_and_edges]

@@ -38,6 +38,10 @@ def test_seeds_and_edge_values(lib):
     pp.pin_seeds_and_edges(lib)
 
 
+def test_stream_published_outputs(lib):
+    pp.pin_stream_published_outputs(lib)
+
+
 def test_stream_value_arithmetic(lib):
     """The C stream's 64-bit arithmetic against Python integers (a cross-check of the build, not a pin)."""
     def mix13(z):
@@ -68,6 +72,10 @@ MUTANTS = {
     "seed_ignored": ("const uint64_t key = stream_value(seed, uint64_t(p));",
                      "const uint64_t key = stream_value(0, uint64_t(p));"),
     "first_factor_skipped": ("double q = u(0);", "double q = 1.0;"),
+    "mix_shift": ("z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;", "z = (z ^ (z >> 31)) * 0xbf58476d1ce4e5b9ULL;"),
+    "mix_constant": ("z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;", "z = (z ^ (z >> 27)) * 0x94d049bb133111ecULL;"),
+    "gamma": ("constexpr uint64_t kGamma = 0x9e3779b97f4a7c15ULL;", "constexpr uint64_t kGamma = 0x9e3779b97f4a7c17ULL;"),
+    "counter_offset": ("return mix13(s + (j + 1) * kGamma);", "return mix13(s + j * kGamma);"),
 }
 
 
