@@ -155,6 +155,9 @@ __device__ __forceinline__ void group_append(uint32_t g, uint32_t* q, unsigned i
 
 __device__ __forceinline__ float clamp_med(float e, float c1, float c2) { return fminf(fmaxf(e, c1), c2); }
 
+// The dense bound pass loads the rows of its next step one step ahead.
+constexpr bool kBoundPrefetch = true;
+
 // thresholds of the bound test: S+ > sigclip (hot), S+ > min(sigclip, sigfrac*sigclip) (act)
 __device__ __forceinline__ void bound_consts(const Params& p, float& chot, float& clow) {
   const float sigclip = p.sigclip, tlow = fminf(__fmul_rn(p.sigfrac, p.sigclip), sigclip);
@@ -223,10 +226,25 @@ __device__ __forceinline__ void bound_span2(const Frame& f, const float* __restr
   ld(y0 - 1, A.b, B.b, H.b);
   ld(y0, A.c, B.c, H.c);
   ld(y0 + 1, A.d, B.d, H.d);
+  // the two rows below the current step are loaded one step ahead, so their
+  // latency overlaps the current step's arithmetic
+  float na, nb, nh, pa, pb, ph;
+  if (kBoundPrefetch) {
+    ld(y0 + 2, na, nb, nh);
+    ld(y0 + 3, pa, pb, ph);
+  }
   for (int y = y0; y < y1; y += 2) {
     float ea, eb, eh, ga, gb, gh;
-    ld(y + 2, ea, eb, eh);
-    ld(y + 3, ga, gb, gh);
+    if (kBoundPrefetch) {
+      ea = na, eb = nb, eh = nh, ga = pa, gb = pb, gh = ph;
+      if (y + 2 < y1) {
+        ld(y + 4, na, nb, nh);
+        ld(y + 5, pa, pb, ph);
+      }
+    } else {
+      ld(y + 2, ea, eb, eh);
+      ld(y + 3, ga, gb, gh);
+    }
     float ma[2], mb[2], mh[2];
     col_step(A, ea, ga, ma[0], ma[1]);
     col_step(B, eb, gb, mb[0], mb[1]);
