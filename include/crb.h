@@ -95,6 +95,17 @@ typedef struct {
    * launches cost about 0.5 ms per call, the tile pipeline's cost is about 4.5
    * times more per pixel. All give identical results. */
   int pipeline;
+  /* 1: autotune the queue pipeline. The first call with a new signature (the
+   * list of frame sizes and niter) times trial cleans of its own frames on the
+   * stream (that call synchronises the stream; about 15 cleans): four
+   * occupancy levels (all, 3/4, 1/2 and 1/4 of each queue-pipeline kernel's
+   * largest blocks per SM), each kernel keeping the level at which its own
+   * launches took least device time; then the first iteration from which the
+   * bit-plane kernels walk listed segments (2, 3, 4 or none); then, for calls
+   * under 2^25 pixels with pipeline 0, the tile pipeline against the result.
+   * Later calls with the same signature reuse the choice (crb_tuned_config
+   * reports it). The launch configuration changes no result. Default 0. */
+  int autotune;
 } crb_options;
 
 /* Creates a context with the cleaning parameters (Sec. 5 lists gain, readn,
@@ -283,6 +294,17 @@ int crb_fadd_peak(double* ops_per_s, cudaStream_t stream);
  * 11 u8 mask, 12 tile-pipeline replacement, 13 work counters.
  * Returns the number of kinds written, or CRB_EINVAL. */
 int crb_profile_kernels(crb_ctx* ctx, double* ms, int* brackets, int max, int reset);
+
+/* The launch configuration of the context's last call: blocks per SM of the
+ * queue-pipeline kernels, in the order bound (dense), need, S, S', m3need,
+ * med3, candidate test, replacement, bound re-test, replacement queue,
+ * replacement write, changed-pixel dilation, full candidate test, growth,
+ * flag queue and u8 mask, segment list, segment-form dilation, need and
+ * m3need, m3need of iteration 1 (up to max of them); the first iteration of
+ * the segment-list forms; the pipeline (1 tile, 2 queue). Returns the number of
+ * kernels written, or CRB_EINVAL. A measurement aid, not a step of the method
+ * (the paper has no counterpart). */
+int crb_tuned_config(const crb_ctx* ctx, int* blocks_per_sm, int max, int* seg_from, int* pipeline);
 
 /* Number of compiled tile shapes and their sizes (output tile of the detection kernel). */
 int crb_num_tile_shapes(void);

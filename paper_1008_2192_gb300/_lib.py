@@ -23,7 +23,7 @@ MAP_NAMES = ("m5", "lplus", "noise", "s", "sprime", "m3", "f", "r", "cand", "g1"
 class crb_options(ctypes.Structure):
     _fields_ = [("objlim_form", ctypes.c_int), ("early_exit", ctypes.c_int),
                 ("tile_shape", ctypes.c_int), ("use_graphs", ctypes.c_int), ("profile", ctypes.c_int),
-                ("no_fusion", ctypes.c_int), ("pipeline", ctypes.c_int)]
+                ("no_fusion", ctypes.c_int), ("pipeline", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class crb_rect(ctypes.Structure):
@@ -62,6 +62,7 @@ SIGNATURES = {
     "crb_server_stats": (_ci, [_vp, ctypes.POINTER(ctypes.c_longlong), _ci]),
     "crb_server_frame_bytes": (ctypes.c_size_t, [_ci, _ci]),
     "crb_server_destroy": (None, [_vp]),
+    "crb_tuned_config": (_ci, [_vp, _PI, _ci, _PI, _PI]),
     "crb_num_tile_shapes": (_ci, []),
     "crb_tile_shape": (_ci, [_ci, _PI, _PI]),
     "crb_partition": (_ci, [_ci, _ci, _ci, _ci, _ci, ctypes.POINTER(crb_rect), _ci, _PI, _PI]),

@@ -38,10 +38,10 @@ class Cleaner:
 
     def __init__(self, gain=7.0, readnoise=5.0, sigclip=4.5, sigfrac=0.5, objlim=1.0, niter=4, *,
                  objlim_form=0, early_exit=False, tile_shape=0, use_graphs=False, profile=False,
-                 fusion=True, pipeline="auto"):
+                 fusion=True, pipeline="auto", autotune=False):
         lib = _lib.load()
         opt = _lib.crb_options(int(objlim_form), int(bool(early_exit)), int(tile_shape), int(bool(use_graphs)),
-                               int(bool(profile)), int(not fusion), PIPELINES[pipeline])
+                               int(bool(profile)), int(not fusion), PIPELINES[pipeline], int(bool(autotune)))
         h = lib.crb_create_ex(gain, readnoise, sigclip, sigfrac, objlim, int(niter), ctypes.byref(opt))
         if not h:
             raise ValueError("crb_create_ex: " + lib.crb_last_error().decode())
@@ -176,6 +176,21 @@ class Cleaner:
         if k < 0:
             raise RuntimeError("crb_last_work failed")
         return [tuple(int(buf[6 * i + j]) for j in range(6)) for i in range(k)]
+
+    QUEUE_KERNELS = ("bound", "need", "s", "sprime", "m3need", "m3", "cand_test", "rep_compute", "bound_sparse",
+                     "rq", "rep_write", "d2", "cand_full", "grow", "flagq_mask", "seg_list", "d2_seg", "need_seg",
+                     "m3need_seg", "m3need_first")
+
+    def tuned_config(self):
+        """Launch configuration of the last call: ({kernel: blocks per SM}, first segment-list iteration,
+        pipeline "tile" or "queue")."""
+        n = len(self.QUEUE_KERNELS)
+        occ = (ctypes.c_int * n)()
+        sf, pl = ctypes.c_int(), ctypes.c_int()
+        k = _lib.load().crb_tuned_config(self._h, occ, n, ctypes.byref(sf), ctypes.byref(pl))
+        if k < 0:
+            check(k, "crb_tuned_config")
+        return dict(zip(self.QUEUE_KERNELS, list(occ)[:k])), sf.value, {1: "tile", 2: "queue"}.get(pl.value)
 
     def last_launches(self):
         """Kernel launches the last call enqueued."""

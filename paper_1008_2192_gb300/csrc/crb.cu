@@ -89,6 +89,8 @@ enum QK {
 struct GraphKey {
   int n, niter, shape;
   bool fuse, queue;
+  int seg_from;
+  long long occ_sig;  // the queue kernels' blocks per SM, packed
   long long tiles, rtiles, nblocks, ncells, npix;
   size_t bits_total;
   int ncounters, dgrid, fgrid, rgrid;
@@ -98,6 +100,7 @@ struct GraphKey {
   void* tab;
   bool operator==(const GraphKey& o) const {
     return n == o.n && niter == o.niter && shape == o.shape && fuse == o.fuse && queue == o.queue &&
+           seg_from == o.seg_from && occ_sig == o.occ_sig &&
            tiles == o.tiles && nblocks == o.nblocks && ncells == o.ncells && npix == o.npix &&
            rtiles == o.rtiles && bits_total == o.bits_total && ncounters == o.ncounters && dgrid == o.dgrid &&
            fgrid == o.fgrid && rgrid == o.rgrid && ws == o.ws && counters == o.counters && frames == o.frames &&
@@ -183,6 +186,19 @@ struct crb_ctx {
   size_t rects_cap = 0;
   std::vector<std::pair<std::vector<long long>, int>> tuned;
 
+  // queue-pipeline autotuner (crb_options.autotune): the chosen launch
+  // configuration of each call signature, and the per-launch events of a trial
+  struct QTune {
+    std::vector<long long> sig;
+    int occ[kQKernels];
+    int seg_from;
+    bool tile;  // the tile pipeline measured faster for this signature
+  };
+  std::vector<QTune> qtuned;
+  bool tuning = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> tune_ev;
+  int last_occ[kQKernels] = {};
+  int last_seg_from = 0, last_pipeline = 0;
   // profiling: event pairs around launches, by kernel kind (0 detect, 1 replace)
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[kProfKinds];
@@ -359,6 +375,8 @@ struct Plan {
   char* chg[2] = {nullptr, nullptr};         // changed-pixel planes (all frames) for even / odd iterations
   size_t chg_bytes = 0;
   crb::Queues Q{};
+  int occ[kQKernels] = {};       // queue pipeline: blocks per SM of each kernel (QK order)
+  int seg_from = crb::kSegFrom;  // queue pipeline: first iteration of the segment-list forms
 };
 
 int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs, cudaStream_t stream) {
@@ -376,9 +394,21 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
     // the image buffer starts as I0 (copied by the first bound pass): every
     // replacement then writes only its flagged pixels
     auto grid = [&](int kind, long long units) {
-      return int(std::max<long long>(1, std::min<long long>(units, (long long)c->num_sms * c->occ_q[kind])));
+      return int(std::max<long long>(1, std::min<long long>(units, (long long)c->num_sms * P.occ[kind])));
     };
     const int gq = c->num_sms;  // queue and list kernels: grid-stride over lengths known on the device
+    // while tuning, every launch is bracketed by events keyed by its kernel (QK order)
+    auto tq = [&](int kernel, auto&& launch) {
+      if (!c->tuning) {
+        launch();
+        return;
+      }
+      cudaEvent_t a = take_event(c), b = take_event(c);
+      cudaEventRecord(a, stream);
+      launch();
+      cudaEventRecord(b, stream);
+      c->tune_ev.push_back({kernel, {a, b}});
+    };
     const size_t cells_bytes = size_t(P.ncells) * 4;
     for (int k = 1; k <= P.niter; ++k) {
       uint32_t* cls = P.cells[k & 1];
@@ -387,49 +417,80 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
       const long long ucol = (P.nunits + crb::kColWarps - 1) / crb::kColWarps;
       const int gcol = grid(kQNeed, ucol);
       const int gcolm = grid(kQM3need, ucol), gcol1m = grid(kQM3needAll, ucol);
-      const bool seg = k >= crb::kSegFrom;  // the column kernels walk the listed segments only
+      const bool seg = k >= P.seg_from;  // the column kernels walk the listed segments only
       const int tcol = crb::kColWarps * 32;
       timed(c, kPBound, stream, [&] {
         if (k == 1) {
-          crb::bound_kernel<<<grid(kQBound, P.nblocks), 128, 0, stream>>>(c->d_frames, P.n, P.nblocks, c->p);
+          tq(kQBound, [&] {
+            crb::bound_kernel<<<grid(kQBound, P.nblocks), 128, 0, stream>>>(c->d_frames, P.n, P.nblocks, c->p);
+          });
         } else {  // the pixels within 2 px of a change, re-tested one by one
           if (seg) {
-            crb::seg_list_kernel<<<grid(kQSegList, (P.nunits + 7) / 8), crb::kThreads, 0, stream>>>(
-                c->d_frames, P.n, P.nunits, P.Q, cls);
-            crb::d2_seg_kernel<<<gq * c->occ_q[kQD2Seg], tcol, 0, stream>>>(c->d_frames, P.n, P.Q, k);
+            tq(kQSegList, [&] {
+              crb::seg_list_kernel<<<grid(kQSegList, (P.nunits + 7) / 8), crb::kThreads, 0, stream>>>(
+                  c->d_frames, P.n, P.nunits, P.Q, cls);
+            });
+            tq(kQD2Seg, [&] {
+              crb::d2_seg_kernel<<<gq * P.occ[kQD2Seg], tcol, 0, stream>>>(c->d_frames, P.n, P.Q, k);
+            });
           } else {
-            crb::d2_kernel<<<grid(kQD2, ucol), tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, k);
+            tq(kQD2, [&] {
+              crb::d2_kernel<<<grid(kQD2, ucol), tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, k);
+            });
           }
-          crb::bound_sparse_kernel<<<gq * c->occ_q[kQBoundSparse], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
+          tq(kQBoundSparse, [&] {
+            crb::bound_sparse_kernel<<<gq * P.occ[kQBoundSparse], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
+          });
         }
       });
       timed(c, kPNeed, stream, [&] {
         if (seg)
-          crb::need_seg_kernel<<<gq * c->occ_q[kQNeedSeg], tcol, 0, stream>>>(c->d_frames, P.n, P.Q, cls);
+          tq(kQNeedSeg, [&] {
+            crb::need_seg_kernel<<<gq * P.occ[kQNeedSeg], tcol, 0, stream>>>(c->d_frames, P.n, P.Q, cls);
+          });
         else
-          crb::need_kernel<<<gcol, tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, kcls);
+          tq(kQNeed, [&] {
+            crb::need_kernel<<<gcol, tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, kcls);
+          });
       });
-      timed(c, kPS, stream, [&] { crb::s_kernel<<<gq * c->occ_q[kQS], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k); });
-      timed(c, kPSp, stream,
-            [&] { crb::sp_kernel<<<gq * c->occ_q[kQSp], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p); });
+      timed(c, kPS, stream, [&] {
+        tq(kQS, [&] { crb::s_kernel<<<gq * P.occ[kQS], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k); });
+      });
+      timed(c, kPSp, stream, [&] {
+        tq(kQSp, [&] { crb::sp_kernel<<<gq * P.occ[kQSp], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p); });
+      });
       timed(c, kPM3need, stream, [&] {
         if (seg)
-          crb::m3need_seg_kernel<<<gq * c->occ_q[kQM3needSeg], tcol, 0, stream>>>(c->d_frames, P.n, P.Q, cls);
+          tq(kQM3needSeg, [&] {
+            crb::m3need_seg_kernel<<<gq * P.occ[kQM3needSeg], tcol, 0, stream>>>(c->d_frames, P.n, P.Q, cls);
+          });
         else if (k == 1)
-          crb::m3need_kernel<true><<<gcol1m, tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, nullptr);
+          tq(kQM3needAll, [&] {
+            crb::m3need_kernel<true><<<gcol1m, tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, nullptr);
+          });
         else
-          crb::m3need_kernel<false><<<gcolm, tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, kcls);
+          tq(kQM3need, [&] {
+            crb::m3need_kernel<false><<<gcolm, tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q, kcls);
+          });
       });
-      timed(c, kPM3, stream, [&] { crb::m3_kernel<<<gq * c->occ_q[kQM3], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k); });
+      timed(c, kPM3, stream, [&] {
+        tq(kQM3, [&] { crb::m3_kernel<<<gq * P.occ[kQM3], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k); });
+      });
       timed(c, kPCand, stream, [&] {
-        crb::cand_test_kernel<<<gq * c->occ_q[kQCand], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
-        crb::cand_full_kernel<<<gq * c->occ_q[kQCandFull], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
+        tq(kQCand, [&] {
+          crb::cand_test_kernel<<<gq * P.occ[kQCand], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
+        });
+        tq(kQCandFull, [&] {
+          crb::cand_full_kernel<<<gq * P.occ[kQCandFull], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
+        });
       });
       timed(c, kPGrow, stream, [&] {
-        if (k == 1)
-          crb::grow_kernel<false><<<gq * c->occ_q[kQGrow], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
-        else
-          crb::grow_kernel<true><<<gq * c->occ_q[kQGrow], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
+        tq(kQGrow, [&] {
+          if (k == 1)
+            crb::grow_kernel<false><<<gq * P.occ[kQGrow], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
+          else
+            crb::grow_kernel<true><<<gq * P.occ[kQGrow], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
+        });
       });
       // the classes and changed pixels of iteration k+1 start at zero (those of iteration k-1 were read by now)
       if (k >= 3 && cls_next) {
@@ -438,14 +499,20 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
       }
       timed(c, kPRep, stream, [&] {
         if (k == 1)
-          crb::flagq_kernel<<<grid(kQFlagq, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q);
+          tq(kQFlagq, [&] {
+            crb::flagq_kernel<<<grid(kQFlagq, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q);
+          });
         else
-          crb::rq_kernel<<<gq * c->occ_q[kQRq], 256, 0, stream>>>(c->d_frames, P.n, P.Q);
-        crb::rep_compute_kernel<<<gq * c->occ_q[kQRepCompute], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k,
+          tq(kQRq, [&] { crb::rq_kernel<<<gq * P.occ[kQRq], 256, 0, stream>>>(c->d_frames, P.n, P.Q); });
+        tq(kQRepCompute, [&] {
+          crb::rep_compute_kernel<<<gq * P.occ[kQRepCompute], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k,
                                                                                 cls_next);
+        });
         if (k >= 2)
-          crb::rep_write_kernel<<<gq * c->occ_q[kQRepWrite], 256, 0, stream>>>(c->d_frames, P.n, P.Q, cls_next,
+          tq(kQRepWrite, [&] {
+            crb::rep_write_kernel<<<gq * P.occ[kQRepWrite], 256, 0, stream>>>(c->d_frames, P.n, P.Q, cls_next,
                                                                               k + 1, 1);
+          });
       });
       if (k == P.niter)
         timed(c, kPMask, stream, [&] {
@@ -616,6 +683,8 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
   P.bits_total = zero_bytes;
   P.ncounters = ncounters;
   P.rgrid = int(std::min<long long>(rtiles, (long long)c->num_sms * c->occ_replace));
+  std::copy(c->occ_q, c->occ_q + kQKernels, P.occ);
+  P.seg_from = crb::kSegFrom;
   P.nblocks = nblocks;
   P.npix = npix;
   P.ncells = ncells;
@@ -727,7 +796,7 @@ int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
   if (P.niter == 0)
     c->last_launches = 1;
   else if (P.queue)  // 2 uploads; iteration 1: 12 kernels, later ones 14 (15 with the segment list), plus the mask
-    c->last_launches = 2 + 12 + 14 * (P.niter - 1) + std::max(0, P.niter - (crb::kSegFrom - 1)) + 1;
+    c->last_launches = 2 + 12 + 14 * (P.niter - 1) + std::max(0, P.niter - (P.seg_from - 1)) + 1;
   else
     c->last_launches = 1 + (P.fuse ? P.niter + 1 : 2 * P.niter) + c->mprev_frames;
   return CRB_OK;
@@ -735,9 +804,11 @@ int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
 
 // Replays (or captures once) the work of plan P as a CUDA graph on `stream`.
 int launch_graph(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs, cudaStream_t stream) {
-  GraphKey key{P.n,      P.niter,      P.shape,      P.fuse,  P.queue, P.tiles,          P.rtiles,
-               P.nblocks, P.ncells,     P.npix,       P.bits_total, P.ncounters, P.dgrid, P.fgrid,
-               P.rgrid,   c->ws,        c->d_counters, c->d_frames, P.queue ? c->d_tab : nullptr};
+  long long occ_sig = 0;
+  for (int i = 0; i < kQKernels; ++i) occ_sig = occ_sig * 31 + P.occ[i];
+  GraphKey key{P.n,      P.niter,      P.shape,      P.fuse,  P.queue, P.seg_from,  occ_sig,      P.tiles,
+               P.rtiles, P.nblocks,    P.ncells,     P.npix,  P.bits_total, P.ncounters, P.dgrid, P.fgrid,
+               P.rgrid,  c->ws,        c->d_counters, c->d_frames, P.queue ? c->d_tab : nullptr};
   for (auto& g : c->graphs)
     if (g.first == key) {
       CRB_CUDA(cudaGraphLaunch(g.second, stream));
@@ -775,6 +846,123 @@ enum { kPipeAuto = 0, kPipeTile = 1, kPipeQueue = 2 };
 // 0.54-0.67 ms on queues, 2048x4096 in 0.99 ms against 0.72-0.85 ms.
 constexpr long long kAutoQueuePixels = 6000000;
 
+// ---- Autotuner of the queue pipeline (crb_options.autotune) --------------------------------------
+// The launch configuration does not change any result: every queue-pipeline
+// kernel walks its work with a grid-stride loop, so any grid size gives the
+// same outputs; the segment-list forms and the strip forms of the column
+// kernels give the same queues; both pipelines give the same clean. The tuner
+// therefore times trial cleans of the call's own frames and keeps the fastest
+// configuration for the call signature (frame sizes and niter).
+
+// Times one queue-pipeline clean of specs with blocks per SM occ[] and segment
+// lists from iteration seg_from, synchronising `stream`; per_kernel (if not
+// NULL) receives the device time of each kernel summed over its launches.
+int trial_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, const int* occ, int seg_from,
+                cudaStream_t stream, float* ms, double* per_kernel) {
+  Plan P;
+  int rc = prepare_queue(c, specs, niter, P);
+  if (rc) return rc;
+  std::copy(occ, occ + kQKernels, P.occ);
+  P.seg_from = seg_from;
+  rc = upload(c, P, stream);
+  if (rc) return rc;
+  cudaEvent_t a = take_event(c), b = take_event(c);
+  CRB_CUDA(cudaEventRecord(a, stream));
+  c->tuning = per_kernel != nullptr;
+  rc = enqueue_work(c, P, specs, stream);
+  c->tuning = false;
+  if (rc) return rc;
+  CRB_CUDA(cudaEventRecord(b, stream));
+  CRB_CUDA(cudaEventSynchronize(b));
+  CRB_CUDA(cudaEventElapsedTime(ms, a, b));
+  c->ev_pool.push_back(a);
+  c->ev_pool.push_back(b);
+  if (per_kernel) {
+    std::fill(per_kernel, per_kernel + kQKernels, 0.0);
+    for (auto& e : c->tune_ev) {
+      float t = 0.f;
+      CRB_CUDA(cudaEventElapsedTime(&t, e.second.first, e.second.second));
+      per_kernel[e.first] += t;
+      c->ev_pool.push_back(e.second.first);
+      c->ev_pool.push_back(e.second.second);
+    }
+    c->tune_ev.clear();
+  }
+  return CRB_OK;
+}
+
+// Times one tile-pipeline clean (tile shape 0), synchronising `stream`.
+int trial_tile(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, cudaStream_t stream, float* ms) {
+  Plan P;
+  int rc = prepare(c, specs, niter, false, 0, P);
+  if (rc == CRB_OK) rc = upload(c, P, stream);
+  if (rc) return rc;
+  cudaEvent_t a = take_event(c), b = take_event(c);
+  CRB_CUDA(cudaEventRecord(a, stream));
+  rc = enqueue_work(c, P, specs, stream);
+  if (rc) return rc;
+  CRB_CUDA(cudaEventRecord(b, stream));
+  CRB_CUDA(cudaEventSynchronize(b));
+  CRB_CUDA(cudaEventElapsedTime(ms, a, b));
+  c->ev_pool.push_back(a);
+  c->ev_pool.push_back(b);
+  return CRB_OK;
+}
+
+// Calls below this many pixels also try the tile pipeline.
+constexpr long long kTuneTilePixels = 1LL << 25;
+
+// Tunes the queue pipeline for specs: (1) four occupancy levels (all, 3/4, 1/2,
+// 1/4 of each kernel's largest blocks per SM), each kernel keeping the level at
+// which its own launches took least device time (the kernels run one after
+// another, so their times add up independently); (2) the first iteration of the
+// segment-list forms (2, 3, 4 or none), by the time of the whole clean (best
+// of two); (3) below kTuneTilePixels, the tile pipeline against the result.
+int tune_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, long long npix, bool may_tile,
+               cudaStream_t stream, crb_ctx::QTune& t) {
+  const int saved_profile = c->opt.profile;
+  c->opt.profile = 0;  // trials are not profiled
+  std::copy(c->occ_q, c->occ_q + kQKernels, t.occ);
+  t.seg_from = crb::kSegFrom;
+  t.tile = false;
+  float ms = 0.f;
+  int rc = trial_queue(c, specs, niter, t.occ, t.seg_from, stream, &ms, nullptr);  // workspace and caches
+  double best[kQKernels], pk[kQKernels];
+  std::fill(best, best + kQKernels, 1e30);
+  for (int lv = 4; lv >= 1 && rc == CRB_OK; --lv) {
+    int occ[kQKernels];
+    for (int i = 0; i < kQKernels; ++i) occ[i] = std::max(1, (c->occ_q[i] * lv + 3) / 4);
+    rc = trial_queue(c, specs, niter, occ, t.seg_from, stream, &ms, pk);
+    for (int i = 0; i < kQKernels && rc == CRB_OK; ++i)
+      if (pk[i] < best[i] - 1e-6) {  // a kernel that never runs keeps the first level
+        best[i] = pk[i];
+        t.occ[i] = occ[i];
+      }
+  }
+  float best_ms = 1e30f;
+  for (int sf = 2; sf <= niter + 1 && rc == CRB_OK; ++sf) {
+    float m = 1e30f;
+    for (int rep = 0; rep < 2 && rc == CRB_OK; ++rep) {
+      rc = trial_queue(c, specs, niter, t.occ, sf, stream, &ms, nullptr);
+      m = std::min(m, ms);
+    }
+    if (m < best_ms) {
+      best_ms = m;
+      t.seg_from = sf;
+    }
+  }
+  if (rc == CRB_OK && may_tile && npix < kTuneTilePixels) {
+    float m = 1e30f;
+    for (int rep = 0; rep < 2 && rc == CRB_OK; ++rep) {
+      rc = trial_tile(c, specs, niter, stream, &ms);
+      m = std::min(m, ms);
+    }
+    t.tile = m < best_ms;
+  }
+  c->opt.profile = saved_profile;
+  return rc;
+}
+
 // Enqueues the whole clean of `specs` (niter iterations) on `stream`.
 int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, cudaStream_t stream) {
   const int nshapes = int(detect_shapes().size());
@@ -783,8 +971,27 @@ int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, c
   for (const auto& s : specs) npix += (long long)s.w * s.h;
   const bool queue_ok = !maps && niter > 0 && npix < (1LL << 32) &&
                         std::all_of(specs.begin(), specs.end(), [](const FrameSpec& s) { return s.mprev == nullptr; });
-  const bool queue = queue_ok && (c->opt.pipeline == kPipeQueue ||
-                                  (c->opt.pipeline == kPipeAuto && npix >= kAutoQueuePixels));
+  bool queue = queue_ok && (c->opt.pipeline == kPipeQueue ||
+                            (c->opt.pipeline == kPipeAuto && npix >= kAutoQueuePixels));
+  const crb_ctx::QTune* tuned = nullptr;
+  if (c->opt.autotune && queue_ok && c->opt.pipeline != kPipeTile) {
+    std::vector<long long> sig{niter};
+    for (const auto& s : specs) {
+      sig.push_back(s.w);
+      sig.push_back(s.h);
+    }
+    for (const auto& t : c->qtuned)
+      if (t.sig == sig) tuned = &t;
+    if (!tuned) {
+      crb_ctx::QTune t;
+      t.sig = sig;
+      const int rc = tune_queue(c, specs, niter, npix, c->opt.pipeline == kPipeAuto, stream, t);
+      if (rc) return rc;
+      c->qtuned.push_back(t);
+      tuned = &c->qtuned.back();
+    }
+    queue = !tuned->tile;
+  }
   int shape = c->opt.tile_shape;
   if (shape >= nshapes) shape = 0;
   if (shape < 0 && !maps && !queue) {
@@ -836,6 +1043,13 @@ int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, c
   Plan P;
   int rc = queue ? prepare_queue(c, specs, niter, P) : prepare(c, specs, niter, maps, shape, P);
   if (rc) return rc;
+  if (queue && tuned) {
+    std::copy(tuned->occ, tuned->occ + kQKernels, P.occ);
+    P.seg_from = tuned->seg_from;
+  }
+  std::copy(P.occ, P.occ + kQKernels, c->last_occ);
+  c->last_seg_from = P.seg_from;
+  c->last_pipeline = queue ? kPipeQueue : kPipeTile;
   c->mprev_frames = int(std::count_if(specs.begin(), specs.end(), [](const FrameSpec& s) { return s.mprev; }));
   rc = upload(c, P, stream);
   if (rc) return rc;
@@ -1356,6 +1570,15 @@ int crb_alu_peak(double* ops2_per_s, double* ops3_per_s, cudaStream_t stream) {
     if (ops3_per_s) *ops3_per_s = best[1];
   }
   return rc;
+}
+
+int crb_tuned_config(const crb_ctx* c, int* blocks_per_sm, int max, int* seg_from, int* pipeline) {
+  if (!c || max < 0 || (max > 0 && !blocks_per_sm)) return fail(CRB_EINVAL, "crb_tuned_config: bad arguments");
+  const int k = std::min(max, int(kQKernels));
+  for (int i = 0; i < k; ++i) blocks_per_sm[i] = c->last_occ[i];
+  if (seg_from) *seg_from = c->last_seg_from;
+  if (pipeline) *pipeline = c->last_pipeline;
+  return k;
 }
 
 int crb_num_tile_shapes(void) { return int(detect_shapes().size()); }

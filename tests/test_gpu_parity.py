@@ -327,3 +327,36 @@ def test_batch_host_equals_device_batch(pinned, pipeline):
         for i in range(len(sizes)):
             assert np.array_equal(h_outs[i].numpy(), host(outs[i])), (rep, i)
             assert np.array_equal(h_masks[i].numpy(), host(masks[i])), (rep, i)
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_queue_autotune(graphs):
+    """The queue-pipeline autotuner (occupancies, segment-list start, queue or tile) changes no result:
+    call after call (the first tunes, the later ones reuse the choice, replayed from a graph or not),
+    on a single 2048x3072 frame and on an uneven batch, the outputs stay bit-identical to the FP32
+    oracle; the reported configuration is a valid one."""
+    c = Cleaner(niter=4, autotune=True, use_graphs=graphs)
+    img = synth.frame(2048, 3072, seed=13)
+    r32 = oracle.clean(img, params_of({}), 4, precision="f32")
+    for rep in range(3):
+        out, mask = gpu_clean(c, img)
+        assert np.array_equal(mask, r32.mask) and np.array_equal(out, r32.clean), rep
+    occ, seg_from, pipeline = c.tuned_config()
+    assert pipeline in ("tile", "queue") and 2 <= seg_from <= 5
+    if pipeline == "queue":
+        assert all(v >= 1 for v in occ.values()), occ
+    print(f"2048x3072: {pipeline}, segment lists from iteration {seg_from}, blocks per SM {occ}")
+    sizes = [(800, 800), (1024, 1024), (2048, 1024), (97, 211), (3000, 2500)]
+    imgs = [synth.frame(w, h, seed=31, index=i) for i, (w, h) in enumerate(sizes)]
+    refs = [oracle.clean(a, params_of({}), 4, precision="f32") for a in imgs[:4]]
+    plain = Cleaner(niter=4, pipeline="queue")
+    p_outs, p_masks = plain.clean_batch([dev(a) for a in imgs])
+    plain.sync()
+    for rep in range(2):
+        outs, masks = c.clean_batch([dev(a) for a in imgs])
+        c.sync()
+        for i in range(len(imgs)):
+            assert torch.equal(outs[i], p_outs[i]) and torch.equal(masks[i], p_masks[i]), (rep, i)
+            if i < 4:
+                assert np.array_equal(host(masks[i]), refs[i].mask) and np.array_equal(host(outs[i]), refs[i].clean)
+    assert c.tuned_config()[2] == "queue"  # 12.6 Mpix: the tile pipeline is slower
