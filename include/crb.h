@@ -250,9 +250,10 @@ int crb_last_work(crb_ctx* ctx, long long* out, int max_iter);
 
 /* Kernel launches the last crb_clean / crb_clean_batch / crb_iterate enqueued
  * (memsets and copies not counted; a graph replay counts its kernels). The
- * queue pipeline launches 2 descriptor uploads, 12 kernels in iteration 1, 14
- * in each later one (15 from the third on, with the segment list) and the
- * mask kernel; the fused tile pipeline 1 upload and niter + 1 kernels.
+ * queue pipeline launches 1 descriptor upload, 12 kernels in iteration 1, 14
+ * in each later one (15 with the segment list, from the iteration the autotuner
+ * or the default of 3 picks) and the mask kernel; the fused tile pipeline 1
+ * upload and niter + 1 kernels.
  * -1 for a NULL context. */
 int crb_last_launches(const crb_ctx* ctx);
 

@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
+
 #include "alu_peak.cuh"
 #include "crb.h"
 #include "kernels.cuh"
@@ -147,6 +149,7 @@ struct crb_ctx {
   struct DescSlot {
     crb::Frame* h_frames = nullptr;
     uint32_t* h_tab = nullptr;
+    CUtensorMap* h_maps = nullptr;  // tile pipeline: 3 per frame (capacity 3 * frames_cap)
     int frames_cap = 0;
     size_t tab_cap = 0;
     cudaEvent_t upload_ev = nullptr;
@@ -154,6 +157,10 @@ struct crb_ctx {
   int cur = 0;
   crb::Frame* d_frames = nullptr;  // device descriptors (capacity d_frames_cap)
   crb::Frame* h_frames = nullptr;  // pinned staging of the current slot
+  CUtensorMap* d_maps = nullptr;   // device tensor maps (capacity 3 * d_frames_cap)
+  CUtensorMap* h_maps = nullptr;   // pinned staging of the current slot
+  size_t maps_n = 0;               // tensor maps the current call uploads
+  unsigned int* d_status = nullptr;  // device status word: a kernel's bounded wait gave up
   uint32_t* d_tab = nullptr;       // device frame table (capacity d_tab_cap)
   uint32_t* h_tab = nullptr;
   int d_frames_cap = 0;
@@ -255,6 +262,8 @@ int init_ctx(crb_ctx* c) {
   for (auto& sl : c->slot) CRB_CUDA(cudaEventCreateWithFlags(&sl.upload_ev, cudaEventDisableTiming));
   c->upload_ev = c->slot[0].upload_ev;
   CRB_CUDA(cudaEventCreateWithFlags(&c->done_ev, cudaEventDisableTiming));
+  CRB_CUDA(cudaMalloc(&c->d_status, 256));
+  CRB_CUDA(cudaMemset(c->d_status, 0, 256));
   return CRB_OK;
 }
 
@@ -302,9 +311,12 @@ int next_desc_slot(crb_ctx* c, int n, size_t tab_entries) {
     CRB_CUDA(cudaDeviceSynchronize());
     if (n > S.frames_cap) {
       cudaFreeHost(S.h_frames);
+      cudaFreeHost(S.h_maps);
       S.h_frames = nullptr;
+      S.h_maps = nullptr;
       S.frames_cap = 0;
       CRB_CUDA(cudaMallocHost(&S.h_frames, sizeof(crb::Frame) * size_t(n)));
+      CRB_CUDA(cudaMallocHost(&S.h_maps, sizeof(CUtensorMap) * 3 * size_t(n)));
       S.frames_cap = n;
     }
     if (tab_entries > S.tab_cap) {
@@ -316,9 +328,12 @@ int next_desc_slot(crb_ctx* c, int n, size_t tab_entries) {
     }
     if (n > c->d_frames_cap) {
       cudaFree(c->d_frames);
+      cudaFree(c->d_maps);
       c->d_frames = nullptr;
+      c->d_maps = nullptr;
       c->d_frames_cap = 0;
       CRB_CUDA(cudaMalloc(&c->d_frames, sizeof(crb::Frame) * size_t(n)));
+      CRB_CUDA(cudaMalloc(&c->d_maps, sizeof(CUtensorMap) * 3 * size_t(n)));  // 256-byte aligned
       c->d_frames_cap = n;
     }
     if (tab_entries > c->d_tab_cap) {
@@ -331,6 +346,8 @@ int next_desc_slot(crb_ctx* c, int n, size_t tab_entries) {
   }
   CRB_CUDA(cudaEventSynchronize(S.upload_ev));  // the staging buffers are free again
   c->h_frames = S.h_frames;
+  c->h_maps = S.h_maps;
+  c->maps_n = 0;
   c->h_tab = S.h_tab;
   c->upload_ev = S.upload_ev;
   return CRB_OK;
@@ -644,6 +661,7 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
     f.maps = nullptr;
     f.counters = c->d_counters + size_t(2 + crb::kWork) * nit * i;
     f.work = f.counters + size_t(2) * nit;
+    f.status = c->d_status;
     f.w = s.w;
     f.h = s.h;
     f.wpr = (s.w + 31) / 32;
@@ -705,6 +723,55 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
   return CRB_OK;
 }
 
+// The tile pipeline loads the image region of a detection tile inside the
+// frame with one TMA box (crb::issue_tile_load).
+constexpr bool kTileTma = true;
+
+// cuTensorMapEncodeTiled from the driver (no link against libcuda), or nullptr.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return PFN_cuTensorMapEncodeTiled_v12000(nullptr);
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// Writes the tensor maps of frame f's three image buffers (img, out_clean,
+// ws) into host[0..2], each a 2-D float map of the frame with one box of the
+// detection tile's image region (ds.tw + 16) x (ds.th + 16); returns the
+// device address they are uploaded to, or nullptr when the frame does not
+// qualify (row pitch or a buffer off the 16-byte boundary TMA needs, frame
+// smaller than a box, or no encoder): its tiles then load element by element.
+const CUtensorMap* encode_tile_maps(const crb::Frame& f, const DetectShape& ds, CUtensorMap* host,
+                                    const CUtensorMap* dev) {
+  const auto enc = tensor_map_encoder();
+  const int bw = ds.tw + 16, bh = ds.th + 16;
+  if (!enc || f.w % 4 != 0 || f.w < bw || f.h < bh) return nullptr;
+  const void* bufs[3] = {f.img, f.out_clean, f.ws};
+  for (int j = 0; j < 3; ++j) {
+    if (!bufs[j]) {  // ws when niter < 2: never a source
+      std::memset(&host[j], 0, sizeof(CUtensorMap));
+      continue;
+    }
+    if ((reinterpret_cast<uintptr_t>(bufs[j]) & 15u) != 0) return nullptr;
+    const cuuint64_t dims[2] = {cuuint64_t(f.w), cuuint64_t(f.h)};
+    const cuuint64_t strides[1] = {cuuint64_t(f.w) * 4};
+    const cuuint32_t box[2] = {cuuint32_t(bw), cuuint32_t(bh)};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&host[j], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(bufs[j]), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return nullptr;
+  }
+  return dev;
+}
+
 // Lays out the workspace and writes the descriptors (host), for tile shape `shape`.
 int prepare(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, int shape, Plan& P) {
   const int n = int(specs.size());
@@ -749,6 +816,10 @@ int prepare(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool map
     f.wpr = (s.w + 31) / 32;
     f.gain = s.gain;
     f.rn = s.rn;
+    f.status = c->d_status;
+    f.tmap = (!maps && kTileTma) ? encode_tile_maps(f, ds, c->h_maps + 3 * size_t(i), c->d_maps + 3 * size_t(i))
+                                 : nullptr;
+    if (f.tmap) c->maps_n = 3 * size_t(i + 1);
     f.tiles_x = (s.w + ds.tw - 1) / ds.tw;
     f.rtiles_x = (s.w + kRW - 1) / kRW;
     f.tile0 = tiles;
@@ -772,22 +843,31 @@ int prepare(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool map
   return CRB_OK;
 }
 
-// Copies n 4-byte words from page-locked host memory, read directly by the
-// kernel: the descriptors reach the device without a copy engine, so they do
-// not queue behind large transfers of other streams (crb_clean_batch_host).
-__global__ void upload_kernel(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src, size_t n) {
-  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
-    dst[i] = src[i];
+// Copies n0 4-byte words src0 -> dst0 and n1 words src1 -> dst1 from
+// page-locked host memory, read directly by the kernel: the descriptors reach
+// the device without a copy engine, so they do not queue behind large
+// transfers of other streams (crb_clean_batch_host), and one launch carries
+// them all.
+__global__ void upload_kernel(uint32_t* __restrict__ dst0, const uint32_t* __restrict__ src0, size_t n0,
+                              uint32_t* __restrict__ dst1, const uint32_t* __restrict__ src1, size_t n1) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n0 + n1; i += size_t(gridDim.x) * blockDim.x)
+    if (i < n0)
+      dst0[i] = src0[i];
+    else
+      dst1[i - n0] = src1[i - n0];
+  // tensor maps among the words are read by TMA (the tensormap proxy) in later kernels
+  asm volatile("fence.proxy.tensormap::generic.release.gpu;" ::: "memory");
 }
 
 int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
-  static_assert(sizeof(crb::Frame) % 4 == 0, "whole words");
+  static_assert(sizeof(crb::Frame) % 4 == 0 && sizeof(CUtensorMap) % 4 == 0, "whole words");
   const size_t nf = sizeof(crb::Frame) * size_t(P.n) / 4;
-  upload_kernel<<<int(std::min<size_t>((nf + 255) / 256, 64)), 256, 0, stream>>>(
-      reinterpret_cast<uint32_t*>(c->d_frames), reinterpret_cast<const uint32_t*>(c->h_frames), nf);
-  if (P.queue)
-    upload_kernel<<<int(std::min<size_t>((c->tab_n + 255) / 256, 64)), 256, 0, stream>>>(c->d_tab, c->h_tab,
-                                                                                          c->tab_n);
+  // the second segment: the frame table of the queue pipeline, or the tile pipeline's tensor maps
+  uint32_t* d1 = P.queue ? c->d_tab : reinterpret_cast<uint32_t*>(c->d_maps);
+  const uint32_t* h1 = P.queue ? c->h_tab : reinterpret_cast<const uint32_t*>(c->h_maps);
+  const size_t n1 = P.queue ? c->tab_n : sizeof(CUtensorMap) * c->maps_n / 4;
+  upload_kernel<<<int(std::min<size_t>((nf + n1 + 255) / 256, 64)), 256, 0, stream>>>(
+      reinterpret_cast<uint32_t*>(c->d_frames), reinterpret_cast<const uint32_t*>(c->h_frames), nf, d1, h1, n1);
   CRB_CUDA(cudaGetLastError());
   CRB_CUDA(cudaEventRecord(c->upload_ev, stream));
   c->last_niter = P.niter;
@@ -795,8 +875,8 @@ int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
   // the launches of this upload and of enqueue_work for this plan (memsets and copies not counted)
   if (P.niter == 0)
     c->last_launches = 1;
-  else if (P.queue)  // 2 uploads; iteration 1: 12 kernels, later ones 14 (15 with the segment list), plus the mask
-    c->last_launches = 2 + 12 + 14 * (P.niter - 1) + std::max(0, P.niter - (P.seg_from - 1)) + 1;
+  else if (P.queue)  // the upload; iteration 1: 12 kernels, later ones 14 (15 with the segment list), the mask
+    c->last_launches = 1 + 12 + 14 * (P.niter - 1) + std::max(0, P.niter - (P.seg_from - 1)) + 1;
   else
     c->last_launches = 1 + (P.fuse ? P.niter + 1 : 2 * P.niter) + c->mprev_frames;
   return CRB_OK;
@@ -1138,9 +1218,12 @@ void crb_destroy(crb_ctx* c) {
   cudaFree(c->ws);
   cudaFree(c->d_rects);
   cudaFree(c->d_frames);
+  cudaFree(c->d_maps);
+  cudaFree(c->d_status);
   cudaFree(c->d_tab);
   for (auto& sl : c->slot) {
     if (sl.h_frames) cudaFreeHost(sl.h_frames);
+    if (sl.h_maps) cudaFreeHost(sl.h_maps);
     if (sl.h_tab) cudaFreeHost(sl.h_tab);
     if (sl.upload_ev) cudaEventDestroy(sl.upload_ev);
   }
@@ -1391,6 +1474,13 @@ int crb_sync_status(crb_ctx* c, cudaStream_t stream) {
   cudaError_t e = cudaStreamSynchronize(stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "device execution");
+  unsigned int st = 0;
+  CRB_CUDA(cudaMemcpy(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    CRB_CUDA(cudaMemset(c->d_status, 0, sizeof st));
+    c->latched = CRB_ETIMEOUT;
+    g_err = "a bounded device-side wait gave up (a tile's TMA load did not land)";
+  }
   const int s = c->latched;
   c->latched = CRB_OK;
   return s;

@@ -5,6 +5,9 @@
 //           shared memory. 6 is the dependency radius of the new flags on the
 //           input (S' and F need 4, the two growths add 2), the same as the
 //           overlap CRBLASTER gives its sub-images (BORDER = 6, Sec. 6.2).
+//           The staged region is the tile plus 8 pixels (the fused form needs
+//           them for the replacement in front): one TMA box for a tile inside
+//           the frame, clamped 4-byte copies at the frame's edges.
 // replace : stage (e) on a tile plus a 2-pixel halo.
 //
 // Edge rule: every map is filtered with its own coordinates clamped into the
@@ -19,6 +22,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>  // CUtensorMap
 #include <cuda_runtime.h>
 
 #include "networks.cuh"
@@ -50,6 +54,11 @@ struct Frame {
   float gain, rn;
   int tiles_x, rtiles_x;  // detect / replace tiles per row of tiles
   long long tile0, rtile0;  // first tile index of this frame in the launch
+  // tile pipeline: tensor maps of img, out_clean and ws (one box of the image
+  // region of a detection tile each) for TMA loads of interior tiles, or
+  // nullptr (every tile then loads element by element)
+  const CUtensorMap* tmap;
+  unsigned int* status;   // device status word of the call (nonzero: a bounded wait gave up)
   // queue pipeline (pipeline.cuh): bit planes (flag-word layout) and float maps
   uint32_t *hot, *act, *nsp, *test;
   uint32_t *sval, *m3val;  // positions whose mapS/mapN, mapM3 hold the current iteration's values
@@ -189,6 +198,53 @@ __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// TMA (cp.async.bulk.tensor) with an mbarrier: a box of a tensor map into
+// shared memory, its completion counted in bytes on the barrier.
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// Orders this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy (TMA) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Makes a tensor map written through the generic proxy (by an earlier kernel)
+// visible to this thread's TMA instructions.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m) : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* m, int x, int y, uint64_t* bar,
+                                            unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_addr(dst)), "l"(m), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+// Waits for phase `parity` of the barrier to complete, giving up after
+// `limit` polls; returns whether it completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned limit) {
+  for (unsigned i = 0; i < limit; ++i) {
+    unsigned done = 0;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+// Polls of a TMA wait before it gives up (each poll suspends the thread for a
+// while in hardware; a box lands in microseconds).
+constexpr unsigned kTmaWaitPolls = 1u << 22;
+// Value of Frame::status after a wait gave up.
+constexpr unsigned kStatusTimeout = 1u;
+
 // --------------------------------------------------------------------------------------------
 // detect: stages (a)-(d) for one output tile of TW x TH pixels, computed only
 // where they can change a flag.
@@ -227,9 +283,12 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <int TW, int TH, bool kFused = false>
 struct DetectLayout {
   static constexpr int JW = TW + 12, JH = TH + 12;  // R6
-  static constexpr int JP = kFused ? TW + 16 : TW + 12, JR = kFused ? TH + 16 : TH + 12;
-  static constexpr int JOFF = kFused ? 2 * JP + 2 : 0;  // R6 origin inside an image buffer
-  static constexpr int HALO = kFused ? 8 : 6;          // halo of the loaded image region
+  // The loaded image region is R8 (rows y0-8 .., columns x0-8 ..) in both
+  // forms, so that the first column (x0 - 8, x0 a multiple of 32) lies on a
+  // 16-byte boundary, as a TMA box must.
+  static constexpr int JP = TW + 16, JR = TH + 16;
+  static constexpr int JOFF = 2 * JP + 2;  // R6 origin inside an image buffer
+  static constexpr int HALO = 8;           // halo of the loaded image region
   static constexpr int W5 = TW + 10, H5 = TH + 10;
   static constexpr int W4 = TW + 8, H4 = TH + 8;
   static constexpr int W2 = TW + 4, H2 = TH + 4;
@@ -255,7 +314,9 @@ struct DetectLayout {
   static constexpr int oL1 = oL0 + round16(imax(W5 * H5, JW * JH) * 2);
   static constexpr int oL2 = oL1 + round16(W2 * H2 * 2);
   static constexpr int oCnt = oL2 + round16(W2 * H2 * 2);  // 16 ints: counters + scan scratch
-  static constexpr size_t bytes = size_t(oCnt + 16 * 4);
+  static constexpr int oBar = oCnt + 16 * 4;  // two mbarriers (one per image buffer), then the load flag
+  static constexpr size_t bytes = size_t(oBar + 32);
+  static_assert((JP * JR * 4) % 128 == 0, "both image buffers start on the 128-byte boundary a TMA box needs");
 };
 
 // bits of word j of bit-map row `row` (an R6 row) that lie in Rk and in the frame
@@ -342,23 +403,49 @@ __device__ __forceinline__ void bits_to_lists(FA wordA, uint16_t* listA, int& nA
   }
 }
 
+// Whether tile (x0, y0) of frame f loads its image region by TMA: the frame
+// has tensor maps and the whole region lies in the frame (no clamped reads).
+template <int TW, int TH>
+__device__ __forceinline__ bool tile_by_tma(const Frame& f, int x0, int y0) {
+  return f.tmap != nullptr && x0 - 8 >= 0 && x0 + TW + 8 <= f.w && y0 - 8 >= 0 && y0 + TH + 8 <= f.h;
+}
+
 // Issues the asynchronous load of tile t's image region (and, fused, the flag
-// words of an inner tile) into buffer b.
+// words of an inner tile) into buffer b: one TMA box for a tile inside the
+// frame (thread 0, completion on the buffer's mbarrier), else 4-byte copies of
+// clamped positions by every thread. Returns whether the box was used.
+// `acquired`: the tensor map thread 0 last made visible to its TMA loads.
 template <int TW, int TH, bool kFused>
-__device__ __forceinline__ void issue_tile_load(const Frame* __restrict__ frames, int nframes, long long t, int k,
-                                                int niter, char* smem, int b) {
+__device__ __forceinline__ bool issue_tile_load(const Frame* __restrict__ frames, int nframes, long long t, int k,
+                                                int niter, char* smem, int b, const CUtensorMap*& acquired) {
   using L = DetectLayout<TW, TH, kFused>;
   const int fi = frame_of<false>(frames, nframes, t);
   const Frame& f = frames[fi];
   const long long tile = t - f.tile0;
   const int ty = int(tile / f.tiles_x), tx = int(tile - (long long)ty * f.tiles_x);
   const int x0 = tx * TW, y0 = ty * TH, w = f.w, h = f.h;
-  const float* src = iter_src(f, kFused ? k - 1 : k, niter);
+  const int ks = kFused ? k - 1 : k;
+  const float* src = iter_src(f, ks, niter);
   float* buf = reinterpret_cast<float*>(smem) + (b ? L::oB1 : L::oB0);
-  for (int i = threadIdx.x; i < L::JP * L::JR; i += kThreads) {
-    const int iy = i / L::JP, ix = i - iy * L::JP;
-    const int gx = clampi(x0 - L::HALO + ix, 0, w - 1), gy = clampi(y0 - L::HALO + iy, 0, h - 1);
-    cp_async4(buf + i, src + size_t(gy) * w + gx);
+  const bool tma = tile_by_tma<TW, TH>(f, x0, y0);
+  if (tma) {
+    if (threadIdx.x == 0) {
+      // the source's map: img in iteration 1, then out_clean or ws as iter_src alternates them
+      const CUtensorMap* m = f.tmap + (ks == 1 ? 0 : (src == f.out_clean ? 1 : 2));
+      if (m != acquired) {  // once per map and block
+        tensormap_acquire(m);
+        acquired = m;
+      }
+      fence_proxy_async_smem();  // the block's earlier reads and writes of this buffer come first
+      tma_load_2d(buf, m, x0 - 8, y0 - 8, reinterpret_cast<uint64_t*>(smem + L::oBar) + b,
+                  unsigned(L::JP * L::JR * 4));
+    }
+  } else {
+    for (int i = threadIdx.x; i < L::JP * L::JR; i += kThreads) {
+      const int iy = i / L::JP, ix = i - iy * L::JP;
+      const int gx = clampi(x0 - L::HALO + ix, 0, w - 1), gy = clampi(y0 - L::HALO + iy, 0, h - 1);
+      cp_async4(buf + i, src + size_t(gy) * w + gx);
+    }
   }
   if (kFused && x0 - 8 >= 0 && x0 + TW + 8 <= w && y0 - 8 >= 0 && y0 + TH + 8 <= h) {
     const uint32_t* Mb = mask_bits(f, k - 1);
@@ -369,6 +456,7 @@ __device__ __forceinline__ void issue_tile_load(const Frame* __restrict__ frames
     }
   }
   cp_async_commit();
+  return tma;
 }
 
 template <int TW, int TH, bool kMaps, bool kFused>
@@ -750,17 +838,44 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
 template <int TW, int TH, bool kMaps, bool kFused = false>
 __global__ void __launch_bounds__(kThreads) detect_kernel(const Frame* __restrict__ frames, int nframes,
                                                           long long ntiles, Params p, int k, int niter) {
-  extern __shared__ __align__(16) char smem[];
+  extern __shared__ __align__(128) char smem[];
+  using L = DetectLayout<TW, TH, kFused>;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::oBar);
+  int* ok = reinterpret_cast<int*>(smem + L::oBar + 16);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+  unsigned phase = 0;  // thread 0: parity of the next completion of each buffer's barrier (bit b)
+  const CUtensorMap* acquired = nullptr;
   long long t = blockIdx.x;
-  if (t < ntiles) issue_tile_load<TW, TH, kFused>(frames, nframes, t, k, niter, smem, 0);
+  bool tma = t < ntiles && issue_tile_load<TW, TH, kFused>(frames, nframes, t, k, niter, smem, 0, acquired);
   for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+    const int b = it & 1;
     cp_async_wait_all();
-    __syncthreads();  // tile t's image region has landed in buffer it & 1
+    if (threadIdx.x == 0) {
+      bool landed = true;
+      if (tma) {
+        landed = mbar_wait(bar + b, (phase >> b) & 1u, kTmaWaitPolls);
+        phase ^= 1u << b;
+        if (!landed) {
+          if (frames[0].status) atomicOr(frames[0].status, kStatusTimeout);
+          mbar_wait(bar + b, ((phase >> b) & 1u) ^ 1u, kTmaWaitPolls);  // the box still in flight, bounded
+        }
+      }
+      *ok = landed ? 1 : 0;
+    }
+    __syncthreads();  // tile t's image region has landed in buffer b
+    if (!*ok) return;  // every thread of the block leaves together; the status reports it
     const long long tn = t + gridDim.x;
-    if (tn < ntiles) issue_tile_load<TW, TH, kFused>(frames, nframes, tn, k, niter, smem, (it + 1) & 1);
+    const bool tma_next =
+        tn < ntiles && issue_tile_load<TW, TH, kFused>(frames, nframes, tn, k, niter, smem, b ^ 1, acquired);
     const int fi = frame_of<false>(frames, nframes, t);
     const Frame f = frames[fi];
-    detect_tile<TW, TH, kMaps, kFused>(f, p, k, niter, t - f.tile0, smem, it & 1);
+    detect_tile<TW, TH, kMaps, kFused>(f, p, k, niter, t - f.tile0, smem, b);
+    tma = tma_next;
     __syncthreads();
   }
 }
@@ -914,7 +1029,7 @@ __device__ void replace_tile(const Frame& f, int k, int niter, int dense, long l
 template <int RW, int RH>
 __global__ void __launch_bounds__(kThreads) replace_kernel(const Frame* __restrict__ frames, int nframes,
                                                            long long ntiles, int k, int niter, int dense) {
-  extern __shared__ __align__(16) char smem[];
+  extern __shared__ __align__(128) char smem[];
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int fi = frame_of<true>(frames, nframes, t);
     const Frame f = frames[fi];
