@@ -296,6 +296,14 @@ int crb_fadd_peak(double* ops_per_s, cudaStream_t stream);
  * Returns the number of kinds written, or CRB_EINVAL. */
 int crb_profile_kernels(crb_ctx* ctx, double* ms, int* brackets, int max, int reset);
 
+/* Test aid for the device-side bounded waits (no counterpart in the paper):
+ * enqueues on `stream` a kernel that waits, polls times at most (1 <= polls <=
+ * 2^22), on a barrier that nothing completes -- as the tile kernels wait for
+ * their TMA loads -- and records the timeout in the context's device status,
+ * so that the next crb_sync_status returns CRB_ETIMEOUT. The context stays
+ * usable. Returns CRB_OK or CRB_EINVAL. */
+int crb_selftest_wait_timeout(crb_ctx* ctx, unsigned polls, cudaStream_t stream);
+
 /* The launch configuration of the context's last call: blocks per SM of the
  * queue-pipeline kernels, in the order bound (dense), need, S, S', m3need,
  * med3, candidate test, replacement, bound re-test, replacement queue,

@@ -63,6 +63,7 @@ SIGNATURES = {
     "crb_server_frame_bytes": (ctypes.c_size_t, [_ci, _ci]),
     "crb_server_destroy": (None, [_vp]),
     "crb_tuned_config": (_ci, [_vp, _PI, _ci, _PI, _PI]),
+    "crb_selftest_wait_timeout": (_ci, [_vp, ctypes.c_uint, _vp]),
     "crb_num_tile_shapes": (_ci, []),
     "crb_tile_shape": (_ci, [_ci, _PI, _PI]),
     "crb_partition": (_ci, [_ci, _ci, _ci, _ci, _ci, ctypes.POINTER(crb_rect), _ci, _PI, _PI]),

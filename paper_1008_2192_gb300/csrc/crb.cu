@@ -1662,6 +1662,28 @@ int crb_alu_peak(double* ops2_per_s, double* ops3_per_s, cudaStream_t stream) {
   return rc;
 }
 
+namespace {
+// Waits on an mbarrier that nothing arms, with the given poll limit, the way
+// the tile kernels wait for a TMA box; records the timeout in *status.
+__global__ void wait_selftest_kernel(unsigned polls, unsigned int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    crb::mbar_init(&bar, 1);
+    if (!crb::mbar_wait(&bar, 0, polls)) atomicOr(status, crb::kStatusTimeout);
+  }
+}
+}  // namespace
+
+int crb_selftest_wait_timeout(crb_ctx* c, unsigned polls, cudaStream_t stream) {
+  if (!c || polls == 0 || polls > (1u << 22)) return fail(CRB_EINVAL, "crb_selftest_wait_timeout: 1 <= polls <= 2^22");
+  if (c->any_call) CRB_CUDA(cudaStreamWaitEvent(stream, c->done_ev, 0));
+  wait_selftest_kernel<<<1, 32, 0, stream>>>(polls, c->d_status);
+  CRB_CUDA(cudaGetLastError());
+  CRB_CUDA(cudaEventRecord(c->done_ev, stream));
+  c->any_call = true;
+  return CRB_OK;
+}
+
 int crb_tuned_config(const crb_ctx* c, int* blocks_per_sm, int max, int* seg_from, int* pipeline) {
   if (!c || max < 0 || (max > 0 && !blocks_per_sm)) return fail(CRB_EINVAL, "crb_tuned_config: bad arguments");
   const int k = std::min(max, int(kQKernels));

@@ -360,3 +360,23 @@ def test_queue_autotune(graphs):
             if i < 4:
                 assert np.array_equal(host(masks[i]), refs[i].mask) and np.array_equal(host(outs[i]), refs[i].clean)
     assert c.tuned_config()[2] == "queue"  # 12.6 Mpix: the tile pipeline is slower
+
+
+def test_bounded_wait_reports_timeout():
+    """A device-side wait that runs out (on a barrier nothing completes, as a TMA wait would if its box
+    never landed) records CRB_ETIMEOUT in the context's status without faulting; crb_sync_status reports
+    it once, and the context keeps cleaning correctly."""
+    import ctypes
+    import paper_1008_2192_gb300._lib as L
+    c = Cleaner(niter=2, pipeline="tile")
+    lib = L.load()
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.crb_selftest_wait_timeout(c.handle, 1000, s) == L.CRB_OK
+    assert lib.crb_sync_status(c.handle, s) == L.CRB_ETIMEOUT
+    assert b"bounded device-side wait" in lib.crb_last_error()
+    assert lib.crb_sync_status(c.handle, s) == L.CRB_OK  # reported once
+    img = scene(256, 200, seed=17)
+    out, mask = gpu_clean(c, img)
+    r32 = oracle.clean(img, params_of({}), 2, precision="f32")
+    assert np.array_equal(mask, r32.mask) and np.array_equal(out, r32.clean)
+    assert lib.crb_selftest_wait_timeout(c.handle, 0, s) == L.CRB_EINVAL
