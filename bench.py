@@ -315,7 +315,7 @@ def measured_peaks():
         return {}
 
 
-def serve_run(torch, rate, nframes, seed=0, budget=64 << 30, max_inflight=2, max_batch=64):
+def serve_run(torch, rate, nframes, seed=0, budget=64 << 30, max_inflight=2, max_batch=64, fuse2=False):
     """Poisson arrivals at `rate` frames/s, sizes uniform over the batch sizes, through crb_server.
 
     A pool of 2 resident frames per size stands in for arriving data (their content does not change the
@@ -333,7 +333,7 @@ def serve_run(torch, rate, nframes, seed=0, budget=64 << 30, max_inflight=2, max
                 rr = dict(r, index=900000 + len(pool) * 2 + j)
                 imgs.append(torch.from_numpy(wl.make(rr)).cuda())
             pool[key] = {"imgs": imgs, "free": [], "n_alloc": 0}
-    srv = Server(niter=4, budget_bytes=budget, max_inflight=max_inflight, max_batch=max_batch)
+    srv = Server(niter=4, budget_bytes=budget, max_inflight=max_inflight, max_batch=max_batch, fuse2=fuse2)
     lat = [None] * nframes
     pix = 0
     busy = {}

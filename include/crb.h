@@ -106,6 +106,15 @@ typedef struct {
    * Later calls with the same signature reuse the choice (crb_tuned_config
    * reports it). The launch configuration changes no result. Default 0. */
   int autotune;
+  /* 1: in the tile pipeline, iterations 2 and 3 run as one launch (temporal
+   * fusion): each 64 x 16 tile first runs iteration 2 over itself widened by
+   * 32 columns and 8 rows each way (the halo iteration 3 needs: 6 for the
+   * flags, 2 for the replacement), keeping that result in shared memory, then
+   * iteration 3 on itself. One launch less, at the cost of recomputing the
+   * widened ring; the other launches of such a call use 64 x 16 tiles too.
+   * Needs niter >= 3 and fusion; otherwise ignored. Same results. The work
+   * counters then leave out iteration 2's detection. Default 0. */
+  int fuse2;
 } crb_options;
 
 /* Creates a context with the cleaning parameters (Sec. 5 lists gain, readn,

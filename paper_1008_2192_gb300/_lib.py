@@ -23,7 +23,8 @@ MAP_NAMES = ("m5", "lplus", "noise", "s", "sprime", "m3", "f", "r", "cand", "g1"
 class crb_options(ctypes.Structure):
     _fields_ = [("objlim_form", ctypes.c_int), ("early_exit", ctypes.c_int),
                 ("tile_shape", ctypes.c_int), ("use_graphs", ctypes.c_int), ("profile", ctypes.c_int),
-                ("no_fusion", ctypes.c_int), ("pipeline", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("no_fusion", ctypes.c_int), ("pipeline", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("fuse2", ctypes.c_int)]
 
 
 class crb_rect(ctypes.Structure):

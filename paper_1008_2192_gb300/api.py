@@ -38,10 +38,11 @@ class Cleaner:
 
     def __init__(self, gain=7.0, readnoise=5.0, sigclip=4.5, sigfrac=0.5, objlim=1.0, niter=4, *,
                  objlim_form=0, early_exit=False, tile_shape=0, use_graphs=False, profile=False,
-                 fusion=True, pipeline="auto", autotune=False):
+                 fusion=True, pipeline="auto", autotune=False, fuse2=False):
         lib = _lib.load()
         opt = _lib.crb_options(int(objlim_form), int(bool(early_exit)), int(tile_shape), int(bool(use_graphs)),
-                               int(bool(profile)), int(not fusion), PIPELINES[pipeline], int(bool(autotune)))
+                               int(bool(profile)), int(not fusion), PIPELINES[pipeline], int(bool(autotune)),
+                               int(bool(fuse2)))
         h = lib.crb_create_ex(gain, readnoise, sigclip, sigfrac, objlim, int(niter), ctypes.byref(opt))
         if not h:
             raise ValueError("crb_create_ex: " + lib.crb_last_error().decode())
@@ -272,9 +273,9 @@ class Server:
     """Continuous-batching server (crb_server_*): submit device frames, poll finished tags."""
 
     def __init__(self, gain=7.0, readnoise=5.0, sigclip=4.5, sigfrac=0.5, objlim=1.0, niter=4, *,
-                 budget_bytes=64 << 30, max_inflight=2, max_batch=64, objlim_form=0, tile_shape=0):
+                 budget_bytes=64 << 30, max_inflight=2, max_batch=64, objlim_form=0, tile_shape=0, fuse2=False):
         lib = _lib.load()
-        opt = _lib.crb_options(int(objlim_form), 0, int(tile_shape), 0, 0, 0, 0)
+        opt = _lib.crb_options(int(objlim_form), 0, int(tile_shape), 0, 0, 0, 0, 0, int(bool(fuse2)))
         h = lib.crb_server_create(gain, readnoise, sigclip, sigfrac, objlim, int(niter), ctypes.byref(opt),
                                   int(budget_bytes), int(max_inflight), int(max_batch))
         if not h:

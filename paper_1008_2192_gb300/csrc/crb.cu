@@ -66,6 +66,12 @@ constexpr int kRW = 64, kRH = 16;  // replacement tile
 const ReplaceFn kReplace = crb::replace_kernel<kRW, kRH>;
 constexpr size_t kReplaceSmem = crb::ReplaceLayout<kRW, kRH>::bytes;
 
+// Two iterations in one launch (crb_options.fuse2): 64 x 16 tiles, the tile
+// shape of index kFuse2Shape, for the other launches of such a call too.
+constexpr int kFuse2Shape = 2;
+const DetectFn kDetect2 = crb::detect2_kernel<64, 16>;
+constexpr size_t kDetect2Smem = crb::Detect2Layout<64, 16>::bytes;
+
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 // profiling kinds (crb_profile_kernels order); kinds below kProfReplace0 are detection
@@ -90,7 +96,7 @@ enum QK {
 
 struct GraphKey {
   int n, niter, shape;
-  bool fuse, queue;
+  bool fuse, fuse2, queue;
   int seg_from;
   long long occ_sig;  // the queue kernels' blocks per SM, packed
   long long tiles, rtiles, nblocks, ncells, npix;
@@ -101,7 +107,7 @@ struct GraphKey {
   void* frames;
   void* tab;
   bool operator==(const GraphKey& o) const {
-    return n == o.n && niter == o.niter && shape == o.shape && fuse == o.fuse && queue == o.queue &&
+    return n == o.n && niter == o.niter && shape == o.shape && fuse == o.fuse && fuse2 == o.fuse2 && queue == o.queue &&
            seg_from == o.seg_from && occ_sig == o.occ_sig &&
            tiles == o.tiles && nblocks == o.nblocks && ncells == o.ncells && npix == o.npix &&
            rtiles == o.rtiles && bits_total == o.bits_total && ncounters == o.ncounters && dgrid == o.dgrid &&
@@ -134,6 +140,7 @@ struct crb_ctx {
   std::vector<int> occ_detect, occ_detect_maps, occ_fused;
   int occ_q[kQKernels] = {};  // queue pipeline kernels (QK order)
   int occ_replace = 0;
+  int occ_detect2 = 0;
 
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -256,6 +263,9 @@ int init_ctx(crb_ctx* c) {
       c->occ_q[i] = o > 0 ? o : 1;
     }
   }
+  CRB_CUDA(cudaFuncSetAttribute(kDetect2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kDetect2Smem)));
+  CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_detect2, kDetect2, crb::kThreads, kDetect2Smem));
+  if (c->occ_detect2 < 1) c->occ_detect2 = 1;
   CRB_CUDA(cudaFuncSetAttribute(kReplace, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kReplaceSmem)));
   CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_replace, kReplace, crb::kThreads, kReplaceSmem));
   if (c->occ_replace < 1) c->occ_replace = 1;
@@ -381,6 +391,7 @@ int ensure_ws(crb_ctx* c, size_t bytes, int ncounters) {
 struct Plan {
   int n = 0, niter = 0, shape = 0;
   bool maps = false, fuse = false, queue = false;
+  bool fuse2 = false;  // tile pipeline: iterations 2 and 3 in one launch
   long long tiles = 0, rtiles = 0;
   size_t bits_total = 0;  // bytes from the start of the workspace that start at zero
   int ncounters = 0;
@@ -550,7 +561,14 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
     }
   }
   for (int k = 1; k <= P.niter; ++k) {
-    if (P.fuse && k >= 2) {  // replacement of iteration k-1 fused in front of detection k
+    if (P.fuse2 && k == 2) {  // iterations 2 and 3 in one launch (the replacements of 1 and 2 fused in)
+      timed(c, kPTileDetect, stream, [&] {
+        const int g = int(std::min<long long>(P.tiles, (long long)c->num_sms * c->occ_detect2));
+        kDetect2<<<g, crb::kThreads, kDetect2Smem, stream>>>(c->d_frames, P.n, P.tiles, c->p, k, P.niter);
+      });
+    } else if (P.fuse2 && k == 3) {
+      // done with iteration 2
+    } else if (P.fuse && k >= 2) {  // replacement of iteration k-1 fused in front of detection k
       timed(c, kPTileDetect, stream, [&] {
         ds.fn_fused<<<P.fgrid, crb::kThreads, ds.smem_fused, stream>>>(c->d_frames, P.n, P.tiles, c->p, k, P.niter);
       });
@@ -561,9 +579,10 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
       });
     }
     if (!P.fuse || k == P.niter) {
+      // a buffer's first write is dense: iterations 1 and 2, and 3 after a fused pair (I_1 is never stored)
+      const int dense = (k <= 2 || (P.fuse2 && k == 3)) ? 1 : 0;
       timed(c, kPTileReplace, stream, [&] {
-        kReplace<<<P.rgrid, crb::kThreads, kReplaceSmem, stream>>>(c->d_frames, P.n, P.rtiles, k, P.niter,
-                                                                   k <= 2 ? 1 : 0);
+        kReplace<<<P.rgrid, crb::kThreads, kReplaceSmem, stream>>>(c->d_frames, P.n, P.rtiles, k, P.niter, dense);
       });
     }
   }
@@ -662,6 +681,7 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
     f.counters = c->d_counters + size_t(2 + crb::kWork) * nit * i;
     f.work = f.counters + size_t(2) * nit;
     f.status = c->d_status;
+    f.flip_from = 1 << 30;
     f.w = s.w;
     f.h = s.h;
     f.wpr = (s.w + 31) / 32;
@@ -775,6 +795,8 @@ const CUtensorMap* encode_tile_maps(const crb::Frame& f, const DetectShape& ds, 
 // Lays out the workspace and writes the descriptors (host), for tile shape `shape`.
 int prepare(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, int shape, Plan& P) {
   const int n = int(specs.size());
+  // two iterations per launch: needs the fused form, iterations 2 and 3, and its own tile shape
+  const bool fuse2 = c->opt.fuse2 && !maps && !c->opt.no_fusion && niter >= 3 && shape == kFuse2Shape;
   const DetectShape& ds = detect_shapes()[size_t(shape)];
   std::vector<size_t> off_bits(static_cast<size_t>(n)), off_img(static_cast<size_t>(n));
   size_t total = 0;
@@ -817,6 +839,8 @@ int prepare(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool map
     f.gain = s.gain;
     f.rn = s.rn;
     f.status = c->d_status;
+    f.dense_upto = fuse2 ? 3 : 2;
+    f.flip_from = fuse2 ? 3 : (1 << 30);
     f.tmap = (!maps && kTileTma) ? encode_tile_maps(f, ds, c->h_maps + 3 * size_t(i), c->d_maps + 3 * size_t(i))
                                  : nullptr;
     if (f.tmap) c->maps_n = 3 * size_t(i + 1);
@@ -832,6 +856,7 @@ int prepare(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool map
   P.shape = shape;
   P.maps = maps;
   P.fuse = !maps && !c->opt.no_fusion;
+  P.fuse2 = fuse2;
   P.tiles = tiles;
   P.rtiles = rtiles;
   P.bits_total = bits_total;
@@ -878,7 +903,7 @@ int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
   else if (P.queue)  // the upload; iteration 1: 12 kernels, later ones 14 (15 with the segment list), the mask
     c->last_launches = 1 + 12 + 14 * (P.niter - 1) + std::max(0, P.niter - (P.seg_from - 1)) + 1;
   else
-    c->last_launches = 1 + (P.fuse ? P.niter + 1 : 2 * P.niter) + c->mprev_frames;
+    c->last_launches = 1 + (P.fuse ? P.niter + 1 : 2 * P.niter) - (P.fuse2 ? 1 : 0) + c->mprev_frames;
   return CRB_OK;
 }
 
@@ -886,7 +911,7 @@ int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
 int launch_graph(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs, cudaStream_t stream) {
   long long occ_sig = 0;
   for (int i = 0; i < kQKernels; ++i) occ_sig = occ_sig * 31 + P.occ[i];
-  GraphKey key{P.n,      P.niter,      P.shape,      P.fuse,  P.queue, P.seg_from,  occ_sig,      P.tiles,
+  GraphKey key{P.n,      P.niter,      P.shape,      P.fuse,  P.fuse2, P.queue, P.seg_from,  occ_sig,      P.tiles,
                P.rtiles, P.nblocks,    P.ncells,     P.npix,  P.bits_total, P.ncounters, P.dgrid, P.fgrid,
                P.rgrid,  c->ws,        c->d_counters, c->d_frames, P.queue ? c->d_tab : nullptr};
   for (auto& g : c->graphs)
@@ -1074,6 +1099,7 @@ int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, c
   }
   int shape = c->opt.tile_shape;
   if (shape >= nshapes) shape = 0;
+  if (c->opt.fuse2) shape = kFuse2Shape;
   if (shape < 0 && !maps && !queue) {
     // autotuning: the first call of a signature (frame sizes, niter) times every tile shape
     std::vector<long long> sig{niter};

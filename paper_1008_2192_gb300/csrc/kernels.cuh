@@ -59,6 +59,11 @@ struct Frame {
   // nullptr (every tile then loads element by element)
   const CUtensorMap* tmap;
   unsigned int* status;   // device status word of the call (nonzero: a bounded wait gave up)
+  // tile pipeline: the replacements of iterations up to dense_upto write their
+  // whole tile (the first write into each image buffer must), later ones only
+  // the flagged pixels; from iteration flip_from on, the flag planes of odd and
+  // even iterations swap (after a launch that fused two iterations)
+  int dense_upto, flip_from;
   // queue pipeline (pipeline.cuh): bit planes (flag-word layout) and float maps
   uint32_t *hot, *act, *nsp, *test;
   uint32_t *sval, *m3val;  // positions whose mapS/mapN, mapM3 hold the current iteration's values
@@ -89,7 +94,9 @@ __device__ __forceinline__ float* iter_dst(const Frame& f, int k, int niter) {
   return ((niter - k) % 2 == 0) ? f.out_clean : f.ws;
 }
 
-__device__ __forceinline__ uint32_t* mask_bits(const Frame& f, int k) { return (k & 1) ? f.bits_a : f.bits_b; }
+__device__ __forceinline__ uint32_t* mask_bits(const Frame& f, int k) {
+  return ((k & 1) != (k >= f.flip_from ? 1 : 0)) ? f.bits_a : f.bits_b;
+}
 
 // Finds the frame of global tile t (frames sorted by first tile index).
 template <bool kReplace>
@@ -280,7 +287,7 @@ constexpr unsigned kStatusTimeout = 1u;
 //   columns) column medians, aliased by sS (R4) S; sM3 (R5) med3; sN, sSp
 //   (R2) N and S' (-inf unless computed); fused: two flag buffers (R8 rows);
 //   9 bit maps; three position lists and small counters.
-template <int TW, int TH, bool kFused = false>
+template <int TW, int TH, bool kFused = false, bool kDouble = true>
 struct DetectLayout {
   static constexpr int JW = TW + 12, JH = TH + 12;  // R6
   // The loaded image region is R8 (rows y0-8 .., columns x0-8 ..) in both
@@ -299,7 +306,7 @@ struct DetectLayout {
   static_assert(TW % 32 == 0 && 32 * NW <= 256 && JH <= 255, "list entries pack (row << 8 | bit column)");
   static_assert(MW % 4 == 0, "bit maps are cleared as 16-byte vectors");
   static constexpr int oB0 = 0;  // floats
-  static constexpr int oB1 = oB0 + JP * JR;
+  static constexpr int oB1 = kDouble ? oB0 + JP * JR : oB0;  // kDouble = false: one image buffer
   static constexpr int oS = oB1 + JP * JR;
   static constexpr int oM3 = oS + imax(W4 * H4, H2 * W4);
   static constexpr int oN = oM3 + W5 * H5;
@@ -308,7 +315,7 @@ struct DetectLayout {
   static_assert(imax(W4 * H4, H2 * W4) + W5 * H5 >= JW * JH, "replacement values fit in the S/med3 area");
   static constexpr int kMaps = 9;  // hot, act, tmp, needS', needS, test, needM3, g1, g2
   static constexpr int oF0 = round16(nF * 4);  // bytes
-  static constexpr int oF1 = oF0 + round16(MWF * 4);
+  static constexpr int oF1 = kDouble ? oF0 + round16(MWF * 4) : oF0;
   static constexpr int oBits = oF1 + round16(MWF * 4);
   static constexpr int oL0 = round16(oBits + kMaps * MW * 4);
   static constexpr int oL1 = oL0 + round16(imax(W5 * H5, JW * JH) * 2);
@@ -459,9 +466,19 @@ __device__ __forceinline__ bool issue_tile_load(const Frame* __restrict__ frames
   return tma;
 }
 
-template <int TW, int TH, bool kMaps, bool kFused>
-__device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, long long tile, char* smem, int b) {
-  using L = DetectLayout<TW, TH, kFused>;
+// Passes of detect_tile: a tile of the launch (0); the super tile of a
+// two-step fused tile (1: iteration k over the tile widened to cover R8 of the
+// inner tile; its flags M_k go to mOut, its replaced image stays in shared
+// memory); the inner tile's second step (2: iteration k+1, whose replacement
+// input -- I_k's predecessor and M_k over R8 -- is already in shared memory).
+// New flags and pixels with no unflagged neighbour are counted only in the
+// region (cy0, cx0, cth, ctw) of the tile (rows and columns from its origin).
+enum { kPassTile = 0, kPassSuper = 1, kPassSecond = 2 };
+
+template <int TW, int TH, bool kMaps, bool kFused, int kPass = kPassTile, bool kDouble = true>
+__device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, int x0, int y0, char* smem, int b,
+                            uint32_t* mOut = nullptr, int cy0 = 0, int cx0 = 0, int cth = TH, int ctw = TW) {
+  using L = DetectLayout<TW, TH, kFused, kDouble>;
   float* sBuf = reinterpret_cast<float*>(smem) + (b ? L::oB1 : L::oB0);
   float* sJ = sBuf + L::JOFF;  // R6 of J, row pitch L::JP
   float* sS = reinterpret_cast<float*>(smem) + L::oS;
@@ -485,8 +502,6 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   int* cnt = reinterpret_cast<int*>(smem + L::oCnt);  // [0] cand tests; [4..] scan scratch
 
   const int w = f.w, h = f.h;
-  const int ty = int(tile / f.tiles_x), tx = int(tile - (long long)ty * f.tiles_x);
-  const int x0 = tx * TW, y0 = ty * TH;
   const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
   const float sigclip = p.sigclip, siglow = __fmul_rn(p.sigfrac, p.sigclip), objlim = p.objlim;
   const float tlow = fminf(siglow, sigclip);
@@ -501,14 +516,14 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
     reinterpret_cast<uint4*>(bits)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (tid < 4) cnt[tid] = 0;
   for (int i = tid; i < L::W2 * L::H2; i += kThreads) sSp[i] = -INFINITY;
-  if (kFused && !inner)
+  if (kFused && !inner && kPass != kPassSecond)
     for (int i = tid; i < L::MWF; i += kThreads) mFl[i] = 0u;
   __syncthreads();
 
   if (kFused) {
     // Iteration k-1's replacement on R6 from I_{k-2} (sBuf, R8) and M_{k-1} (mFl, R8 rows).
     const int kr = k - 1;
-    if (!inner) {  // clamped flag of every R8 position (replicate edge)
+    if (!inner && kPass != kPassSecond) {  // clamped flag of every R8 position (replicate edge)
       const uint32_t* __restrict__ Mb = mask_bits(f, kr);
       for (int i = tid; i < L::JP * L::JR; i += kThreads) {
         const int iy = i / L::JP, ix = i - iy * L::JP;
@@ -560,7 +575,7 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
 #pragma unroll
         for (int q = 0; q < 25; ++q) v[q] = sBuf[(cy - 2 + q / 5) * L::JP + cx - 2 + q % 5];
         out = floor_m5(sel_med25(v));
-        if (r6 >= 6 && r6 < 6 + TH && xb >= 32 && xb < 32 + TW) ++none_left;
+        if (r6 >= 6 + cy0 && r6 < 6 + cy0 + cth && xb >= 32 + cx0 && xb < 32 + cx0 + ctw) ++none_left;
       }
       val[j] = out;
     }
@@ -572,10 +587,10 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
       const int e = L0[j];
       const int r6 = e >> 8, xb = e & 255;
       sBuf[(r6 + 2) * L::JP + xb - 24] = val[j];
-      if (r6 >= 6 && r6 < 6 + TH && xb >= 32 && xb < 32 + TW)
+      if (kPass != kPassSuper && r6 >= 6 && r6 < 6 + TH && xb >= 32 && xb < 32 + TW)
         Dprev[size_t(y0 - 6 + r6) * w + (x0 - 32 + xb)] = val[j];
     }
-    if (kr <= 2) {  // the destination of iterations 1 and 2 is written densely
+    if (kPass != kPassSuper && kr <= f.dense_upto) {  // a buffer's first write is dense
       for (int i = tid; i < TW * TH; i += kThreads) {
         const int ly = i / TW, lx = i - ly * TW;
         const int gx = x0 + lx, gy = y0 + ly;
@@ -813,13 +828,17 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, l
   unsigned int new_flags = 0;
   for (int wi = tid; wi < kWordsPerRow * TH; wi += kThreads) {
     const int r = wi / kWordsPerRow, wc = wi - r * kWordsPerRow;
-    const int gy = y0 + r;
-    if (gy >= h || (x0 >> 5) + wc >= f.wpr) continue;
+    const int gy = y0 + r, gwc = (x0 >> 5) + wc;
+    if (gy < 0 || gy >= h || gwc < 0 || gwc >= f.wpr) continue;
     const uint32_t g2w = mG2[(r + 6) * L::NW + 1 + wc];  // x0 + 32 wc is word 1 + wc of the row
-    const size_t wo = size_t(gy) * f.wpr + (x0 >> 5) + wc;
-    const uint32_t prev = mask_bits(f, k - 1)[wo];
-    mask_bits(f, k)[wo] = prev | g2w;
-    new_flags += __popc(g2w & ~prev);
+    const size_t wo = size_t(gy) * f.wpr + gwc;
+    // M_{k-1}: in shared memory for the second step of a fused pair (R8 rows, word 1 = x0)
+    const uint32_t prev = (kPass == kPassSecond) ? mFl[(r + 8) * L::NW + 1 + wc] : mask_bits(f, k - 1)[wo];
+    if (kPass == kPassSuper)
+      mOut[r * kWordsPerRow + wc] = prev | g2w;
+    else
+      mask_bits(f, k)[wo] = prev | g2w;
+    if (r >= cy0 && r < cy0 + cth && 32 * wc >= cx0 && 32 * wc < cx0 + ctw) new_flags += __popc(g2w & ~prev);
     if (kMaps) {
       const uint32_t g1w = mG1[(r + 6) * L::NW + 1 + wc];
       for (int bb = 0; bb < 32; ++bb) {
@@ -874,8 +893,111 @@ __global__ void __launch_bounds__(kThreads) detect_kernel(const Frame* __restric
         tn < ntiles && issue_tile_load<TW, TH, kFused>(frames, nframes, tn, k, niter, smem, b ^ 1, acquired);
     const int fi = frame_of<false>(frames, nframes, t);
     const Frame f = frames[fi];
-    detect_tile<TW, TH, kMaps, kFused>(f, p, k, niter, t - f.tile0, smem, b);
+    const long long tile = t - f.tile0;
+    const int ty = int(tile / f.tiles_x), tx = int(tile - (long long)ty * f.tiles_x);
+    detect_tile<TW, TH, kMaps, kFused>(f, p, k, niter, tx * TW, ty * TH, smem, b);
     tma = tma_next;
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------------------------------------
+// detect2: iterations k and k+1 of a TW x TH tile in one launch (temporal
+// fusion with halo recompute). Iteration k+1's detection on the tile needs I_k
+// on R6 of the tile, whose replacement needs M_k on R8; so the block first
+// runs the fused iteration k (replacement of k-1, then detection) over the
+// super tile -- the tile widened by 32 columns (whole flag words) and 8 rows
+// each way -- from I_{k-2} and M_{k-1}, keeping its replaced image and its
+// flags in shared memory, then the fused iteration k+1 on the tile itself
+// from those. Each block recomputes the ring its neighbours also compute, and
+// no block reads what another writes in the launch: I_{k-1} and M_k never
+// leave shared memory, I_k and M_{k+1} go to buffers nobody reads here.
+template <int TW, int TH>
+struct Detect2Layout {
+  using LS = DetectLayout<TW + 64, TH + 16, true, false>;  // super tile, one image buffer
+  using LT = DetectLayout<TW, TH, true, false>;
+  static constexpr int oT = (int(LS::bytes) + 127) / 128 * 128;
+  static constexpr int oOut = oT + (int(LT::bytes) + 127) / 128 * 128;  // M_k of the super tile
+  static constexpr int kOutWords = (TH + 16) * (TW / 32 + 2);
+  static constexpr size_t bytes = size_t(oOut + kOutWords * 4);
+  static_assert(bytes <= 227 * 1024, "fits the shared memory of one block");
+};
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(kThreads) detect2_kernel(const Frame* __restrict__ frames, int nframes,
+                                                           long long ntiles, Params p, int k, int niter) {
+  using D = Detect2Layout<TW, TH>;
+  using LS = typename D::LS;
+  using LT = typename D::LT;
+  constexpr int SW = TW + 64, SH = TH + 16, NWT = LT::NW;
+  extern __shared__ __align__(128) char smem[];
+  char* smemT = smem + D::oT;
+  uint32_t* mOut = reinterpret_cast<uint32_t*>(smem + D::oOut);
+  const int tid = threadIdx.x;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int fi = frame_of<false>(frames, nframes, t);
+    const Frame f = frames[fi];
+    const long long tile = t - f.tile0;
+    const int ty = int(tile / f.tiles_x), tx = int(tile - (long long)ty * f.tiles_x);
+    const int x0 = tx * TW, y0 = ty * TH, w = f.w, h = f.h;
+    const int xs = x0 - 32, ys = y0 - 8;  // the super tile
+    // I_{k-2} over R8 of the super tile (clamped), M_{k-1} flag words of an inner super tile
+    {
+      const float* src = iter_src(f, k - 1, niter);
+      float* buf = reinterpret_cast<float*>(smem) + LS::oB0;
+      for (int i = tid; i < LS::JP * LS::JR; i += kThreads) {
+        const int iy = i / LS::JP, ix = i - iy * LS::JP;
+        const int gx = clampi(xs - 8 + ix, 0, w - 1), gy = clampi(ys - 8 + iy, 0, h - 1);
+        cp_async4(buf + i, src + size_t(gy) * w + gx);
+      }
+      if (xs - 8 >= 0 && xs + SW + 8 <= w && ys - 8 >= 0 && ys + SH + 8 <= h) {
+        const uint32_t* Mb = mask_bits(f, k - 1);
+        uint32_t* fl = reinterpret_cast<uint32_t*>(smem + LS::oF0);
+        for (int i = tid; i < LS::MWF; i += kThreads) {
+          const int row = i / LS::NW, j = i - row * LS::NW;
+          cp_async4(fl + i, Mb + size_t(ys - 8 + row) * f.wpr + (xs >> 5) - 1 + j);
+        }
+      }
+      cp_async_commit();
+      cp_async_wait_all();
+      __syncthreads();
+    }
+    // iteration k over the super tile; new flags and pixels with no unflagged neighbour counted on the tile
+    Frame fs = f;
+    fs.work = nullptr;
+    detect_tile<SW, SH, false, true, kPassSuper, false>(fs, p, k, niter, xs, ys, smem, 0, mOut, 8, 32, TH, TW);
+    __syncthreads();
+    // the tile's replacement input: I_{k-1} and M_k over its R8, clamped at the frame's edges
+    {
+      const float* sImg = reinterpret_cast<const float*>(smem) + LS::oB0;  // R8 of the super tile
+      float* tImg = reinterpret_cast<float*>(smemT) + LT::oB0;
+      uint32_t* tFl = reinterpret_cast<uint32_t*>(smemT + LT::oF0);
+      for (int i = tid; i < LT::JP * LT::JR; i += kThreads) {  // R8 of the tile lies in R6 of the super tile
+        const int iy = i / LT::JP, ix = i - iy * LT::JP;
+        tImg[i] = sImg[(iy + 8) * LS::JP + ix + 32];
+      }
+      const bool inner = x0 - 8 >= 0 && x0 + TW + 8 <= w && y0 - 8 >= 0 && y0 + TH + 8 <= h;
+      constexpr int kSWords = SW / 32;  // words per row of mOut; word j of a row covers xs + 32 j
+      if (inner) {  // the tile's flag word j of R8 row r (covering x0 - 32 + 32 j) is mOut's word j of row r
+        for (int i = tid; i < LT::MWF; i += kThreads) {
+          const int r = i / NWT, j = i - r * NWT;
+          tFl[i] = mOut[r * kSWords + j];
+        }
+      } else {  // the flag of the clamped position (replicate edge), bit ix + 24 of the row's words
+        for (int i = tid; i < LT::MWF; i += kThreads) tFl[i] = 0u;
+        __syncthreads();
+        for (int i = tid; i < LT::JP * LT::JR; i += kThreads) {
+          const int iy = i / LT::JP, ix = i - iy * LT::JP;
+          const int gx = clampi(x0 - 8 + ix, 0, w - 1), gy = clampi(y0 - 8 + iy, 0, h - 1);
+          const int sx = gx - xs, sy = gy - ys;  // inside the super tile
+          if ((mOut[sy * kSWords + (sx >> 5)] >> (sx & 31)) & 1u)
+            atomicOr(&tFl[iy * NWT + ((ix + 24) >> 5)], 1u << ((ix + 24) & 31));
+        }
+      }
+      __syncthreads();
+    }
+    // iteration k+1 on the tile: the replacement of iteration k, then detection -> I_k, M_{k+1}
+    detect_tile<TW, TH, false, true, kPassSecond, false>(f, p, k + 1, niter, x0, y0, smemT, 0);
     __syncthreads();
   }
 }

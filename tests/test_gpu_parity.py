@@ -100,8 +100,9 @@ def test_end_to_end_800(cl):
     print(f"800x800: mask flips vs FP64 {flips}, fragile pixels {nfragile}, flagged {int(mask.sum())}")
 
 
-PATHS = [dict(pipeline="queue"), dict(pipeline="tile", fusion=True), dict(pipeline="tile", fusion=False)]
-PATH_IDS = ["queue", "tile-fused", "tile-two-launch"]
+PATHS = [dict(pipeline="queue"), dict(pipeline="tile", fusion=True), dict(pipeline="tile", fusion=False),
+         dict(pipeline="tile", fuse2=True)]
+PATH_IDS = ["queue", "tile-fused", "tile-two-launch", "tile-two-iterations"]
 
 
 @pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
@@ -380,3 +381,25 @@ def test_bounded_wait_reports_timeout():
     r32 = oracle.clean(img, params_of({}), 2, precision="f32")
     assert np.array_equal(mask, r32.mask) and np.array_equal(out, r32.clean)
     assert lib.crb_selftest_wait_timeout(c.handle, 0, s) == L.CRB_EINVAL
+
+
+
+@pytest.mark.parametrize("niter", [3, 4, 5, 6])
+def test_two_iteration_fusion(niter):
+    """Iterations 2 and 3 in one launch (halo recompute over the widened tile): bit-identical to the FP32
+    oracle on the 800x800 workload and on an uneven batch (frame edges, ragged tiles, widths off the
+    16-byte boundary), with one launch fewer."""
+    img = workloads.make(workloads.single_800())
+    c = Cleaner(niter=niter, pipeline="tile", fuse2=True)
+    out, mask = gpu_clean(c, img)
+    r32 = oracle.clean(img, params_of({}), niter, precision="f32")
+    assert np.array_equal(mask, r32.mask) and np.array_equal(out, r32.clean)
+    assert [n for n, _ in c.last_counts()] == r32.n_new
+    assert c.last_launches() == 1 + niter + 1 - 1
+    sizes = [(333, 251), (64, 16), (65, 17), (200, 150), (1, 40), (97, 300)]
+    imgs = [scene(w, h, seed=70 + i) for i, (w, h) in enumerate(sizes)]
+    outs, masks = c.clean_batch([dev(a) for a in imgs])
+    c.sync()
+    for a, o, m in zip(imgs, outs, masks):
+        r = oracle.clean(a, params_of({}), niter, precision="f32")
+        assert np.array_equal(host(m), r.mask) and np.array_equal(host(o), r.clean), a.shape
