@@ -1029,9 +1029,11 @@ constexpr long long kTuneTilePixels = 1LL << 25;
 // Tunes the queue pipeline for specs: (1) four occupancy levels (all, 3/4, 1/2,
 // 1/4 of each kernel's largest blocks per SM), each kernel keeping the level at
 // which its own launches took least device time (the kernels run one after
-// another, so their times add up independently); (2) the first iteration of the
-// segment-list forms (2, 3, 4 or none), by the time of the whole clean (best
-// of two); (3) below kTuneTilePixels, the tile pipeline against the result.
+// another, so their times add up independently), a lower level only if it wins
+// by 2 %; (2) the first iteration of the segment-list forms (2, 3, 4 or none),
+// by the time of the whole clean (best of two), another than the default only
+// if it wins by 1 %; (3) below kTuneTilePixels, the tile pipeline against the
+// result. The margins keep timing noise from deciding.
 int tune_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, long long npix, bool may_tile,
                cudaStream_t stream, crb_ctx::QTune& t) {
   const int saved_profile = c->opt.profile;
@@ -1048,19 +1050,24 @@ int tune_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, long 
     for (int i = 0; i < kQKernels; ++i) occ[i] = std::max(1, (c->occ_q[i] * lv + 3) / 4);
     rc = trial_queue(c, specs, niter, occ, t.seg_from, stream, &ms, pk);
     for (int i = 0; i < kQKernels && rc == CRB_OK; ++i)
-      if (pk[i] < best[i] - 1e-6) {  // a kernel that never runs keeps the first level
+      // a lower level must win by 2 % (a kernel that never runs keeps the first level)
+      if (lv == 4 ? pk[i] < best[i] : pk[i] < 0.98 * best[i]) {
         best[i] = pk[i];
         t.occ[i] = occ[i];
       }
   }
+  // the default start first; another must win by 1 % of the whole clean
+  const int def_sf = std::min(crb::kSegFrom, niter + 1);
   float best_ms = 1e30f;
-  for (int sf = 2; sf <= niter + 1 && rc == CRB_OK; ++sf) {
+  for (int j = 0; j <= niter && rc == CRB_OK; ++j) {
+    const int sf = j == 0 ? def_sf : j + 1;
+    if (j > 0 && sf == def_sf) continue;
     float m = 1e30f;
     for (int rep = 0; rep < 2 && rc == CRB_OK; ++rep) {
       rc = trial_queue(c, specs, niter, t.occ, sf, stream, &ms, nullptr);
       m = std::min(m, ms);
     }
-    if (m < best_ms) {
+    if (j == 0 ? true : m < 0.99f * best_ms) {
       best_ms = m;
       t.seg_from = sf;
     }
