@@ -76,7 +76,7 @@ struct Frame {
   long long cell0; // first cell (one word x kCH rows) of this frame
   int bx;          // word blocks per row of blocks
   int ncy;         // rows of cells
-  long long u0;    // first strip (32 words x 32 rows) of this frame
+  long long u0;    // first strip (32 words x kSH rows) of this frame
   long long word0; // first word (32 px of a row) of this frame
   int ugx;         // strips per row of strips
 };

@@ -91,13 +91,13 @@ size_t frame_bytes(int w, int h) {
   // the caller's input, cleaned output and mask (resident while queued), and the
   // workspace of the queue pipeline: 4 float maps, 5 queue entries per pixel,
   // 12 bit planes (2 of them changed-pixel planes), 2 words per cell of one
-  // word x 8 rows (the class arrays) and 3 words per segment of 32 words x 32
-  // rows' strip column (the segment lists)
+  // word x 8 rows (the class arrays) and 3 words per segment of one word x 16
+  // rows (the segment lists)
   const size_t n = size_t(w) * size_t(h);
   const size_t wpr = size_t(w + 31) / 32;
   const size_t plane = wpr * size_t(h) * 4;
   const size_t cells = wpr * ((size_t(h) + 7) / 8);
-  const size_t segs = 32 * ((wpr + 31) / 32) * ((size_t(h) + 31) / 32);
+  const size_t segs = 32 * ((wpr + 31) / 32) * ((size_t(h) + 15) / 16);
   return n * (4 + 4 + 1) + n * 4 * 4 + n * 5 * 4 + 12 * plane + 2 * 4 * cells + 3 * 4 * segs;
 }
 
