@@ -88,11 +88,6 @@ constexpr int kStageSlots = 4, kStageChunks = 8;
 // descriptor buffers per context
 constexpr int kDescSlots = 4;
 
-// The dense bound pass of iteration 1 with four pixels per lane (bound4_kernel,
-// two warps per block) rather than two (bound_kernel, four warps per block).
-constexpr bool kBound4 = true;
-constexpr int kBoundThreads = kBound4 ? 64 : 128;
-
 // queue pipeline kernels, for the occupancy table
 enum QK {
   kQBound, kQNeed, kQS, kQSp, kQM3need, kQM3, kQCand, kQRepCompute, kQBoundSparse, kQRq, kQRepWrite, kQD2,
@@ -249,8 +244,7 @@ int init_ctx(crb_ctx* c) {
   }
   {
     const void* fns[kQKernels] = {
-        kBound4 ? reinterpret_cast<const void*>(crb::bound4_kernel) : reinterpret_cast<const void*>(crb::bound_kernel),
-        reinterpret_cast<const void*>(crb::need_kernel),
+        reinterpret_cast<const void*>(crb::bound4_kernel),      reinterpret_cast<const void*>(crb::need_kernel),
         reinterpret_cast<const void*>(crb::s_kernel),           reinterpret_cast<const void*>(crb::sp_kernel),
         reinterpret_cast<const void*>(crb::m3need_kernel<false>), reinterpret_cast<const void*>(crb::m3_kernel),
         reinterpret_cast<const void*>(crb::cand_test_kernel),   reinterpret_cast<const void*>(crb::rep_compute_kernel),
@@ -264,7 +258,7 @@ int init_ctx(crb_ctx* c) {
       int o = 0;
       const bool col = i == kQNeed || i == kQM3need || i == kQD2 || i == kQD2Seg || i == kQNeedSeg ||
                        i == kQM3needSeg || i == kQM3needAll;
-      const int threads = i == kQBound ? kBoundThreads : col ? crb::kColWarps * 32 : 256;
+      const int threads = i == kQBound ? 64 : col ? crb::kColWarps * 32 : 256;
       CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[i], threads, 0));
       c->occ_q[i] = o > 0 ? o : 1;
     }
@@ -456,10 +450,7 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
       timed(c, kPBound, stream, [&] {
         if (k == 1) {
           tq(kQBound, [&] {
-            if (kBound4)
-              crb::bound4_kernel<<<grid(kQBound, P.nblocks), 64, 0, stream>>>(c->d_frames, P.n, P.nblocks, c->p);
-            else
-              crb::bound_kernel<<<grid(kQBound, P.nblocks), 128, 0, stream>>>(c->d_frames, P.n, P.nblocks, c->p);
+            crb::bound4_kernel<<<grid(kQBound, P.nblocks), 64, 0, stream>>>(c->d_frames, P.n, P.nblocks, c->p);
           });
         } else {  // the pixels within 2 px of a change, re-tested one by one
           if (seg) {

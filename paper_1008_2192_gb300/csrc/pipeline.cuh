@@ -148,7 +148,7 @@ __device__ __forceinline__ void group_append(uint32_t g, uint32_t* q, unsigned i
 // bound: per pixel L+ and the lower bound of m5 (smallest of the five column
 // medians) -> bits of S+ > sigclip and S+ > min(sigclip, sigfrac*sigclip) (see detect_tile
 // for the bound and its margin). In iteration 1 a warp walks down a strip of
-// two word columns, two rows per step, keeping the rows of its columns (and of
+// four word columns, two rows per step, keeping the rows of its columns (and of
 // the halo columns, held by lanes 0-3) in registers.
 //
 // Sliding column medians: the windows of rows y and y+1 share the four values
@@ -156,9 +156,6 @@ __device__ __forceinline__ void group_append(uint32_t g, uint32_t* q, unsigned i
 // median of the four and one more value e is min(max(e, c1), c2).
 
 __device__ __forceinline__ float clamp_med(float e, float c1, float c2) { return fminf(fmaxf(e, c1), c2); }
-
-// The dense bound pass loads the rows of its next step one step ahead.
-constexpr bool kBoundPrefetch = true;
 
 // thresholds of the bound test: S+ > sigclip (hot), S+ > min(sigclip, sigfrac*sigclip) (act)
 __device__ __forceinline__ void bound_consts(const Params& p, float& chot, float& clow) {
@@ -194,136 +191,14 @@ __device__ __forceinline__ void col_step(Col4& s, float e, float g, float& m0, f
   m1 = clamp_med(g, c1, c2);
 }
 
-// hot/act bits of the two word columns wc, wc+1 (wc even), rows [y0, y1), of
-// frame f (whole warp). Lane l holds the pixel pair x0+2l, x0+2l+1, so one
-// shuffle brings two neighbours; lanes 0-3 also hold the halo columns x0-2,
-// x0-1, x0+64, x0+65. copy != nullptr also copies the pixels of J there.
-__device__ __forceinline__ void bound_span2(const Frame& f, const float* __restrict__ J, int wc, int y0, int y1,
-                                            float chot, float clow, float* __restrict__ copy) {
-  const int lane = threadIdx.x & 31;
-  const int w = f.w, h = f.h;
-  const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
-  const int x0 = wc * 32, xa = x0 + 2 * lane, xb = xa + 1;
-  const int ca = min(xa, w - 1), cb = min(xb, w - 1);
-  const int hx = lane < 2 ? x0 - 2 + lane : x0 + 62 + lane;  // halo columns (lanes 0-3)
-  const int hc = clampi(hx, 0, w - 1);
-  // one 8-byte load for the pair when the row pitch and the base keep it aligned
-  const bool vec = ((reinterpret_cast<uintptr_t>(J) & 7u) == 0) && ((w & 1) == 0) && (xb < w);
-  const int src_h0 = lane == 0 ? 0 : 2, src_h1 = lane == 0 ? 1 : 3, src_hl = lane == 0 ? 1 : 2;
-  auto row = [&](int yy) { return J + size_t(clampi(yy, 0, h - 1)) * size_t(w); };
-  auto ld = [&](int yy, float& va, float& vb, float& vh) {
-    const float* r = row(yy);
-    if (vec) {
-      const float2 t = __ldg(reinterpret_cast<const float2*>(r + xa));
-      va = t.x;
-      vb = t.y;
-    } else {
-      va = __ldg(r + ca);
-      vb = __ldg(r + cb);
-    }
-    vh = __ldg(r + hc);
-  };
-  Col4 A, B, H;
-  ld(y0 - 2, A.a, B.a, H.a);
-  ld(y0 - 1, A.b, B.b, H.b);
-  ld(y0, A.c, B.c, H.c);
-  ld(y0 + 1, A.d, B.d, H.d);
-  // the two rows below the current step are loaded one step ahead, so their
-  // latency overlaps the current step's arithmetic
-  float na, nb, nh, pa, pb, ph;
-  if (kBoundPrefetch) {
-    ld(y0 + 2, na, nb, nh);
-    ld(y0 + 3, pa, pb, ph);
-  }
-  for (int y = y0; y < y1; y += 2) {
-    float ea, eb, eh, ga, gb, gh;
-    if (kBoundPrefetch) {
-      ea = na, eb = nb, eh = nh, ga = pa, gb = pb, gh = ph;
-      if (y + 2 < y1) {
-        ld(y + 4, na, nb, nh);
-        ld(y + 5, pa, pb, ph);
-      }
-    } else {
-      ld(y + 2, ea, eb, eh);
-      ld(y + 3, ga, gb, gh);
-    }
-    float ma[2], mb[2], mh[2];
-    col_step(A, ea, ga, ma[0], ma[1]);
-    col_step(B, eb, gb, mb[0], mb[1]);
-    col_step(H, eh, gh, mh[0], mh[1]);
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const int yy = y + s;
-      if (yy >= y1) break;
-      const float cmA = ma[s], cmB = mb[s];
-      // column medians of the neighbouring pairs (lane-1: pA pB, lane+1: nA nB); halo at the ends
-      float pA = __shfl_up_sync(0xffffffffu, cmA, 1), pB = __shfl_up_sync(0xffffffffu, cmB, 1);
-      float nA = __shfl_down_sync(0xffffffffu, cmA, 1), nB = __shfl_down_sync(0xffffffffu, cmB, 1);
-      const float hX = __shfl_sync(0xffffffffu, mh[s], src_h0), hY = __shfl_sync(0xffffffffu, mh[s], src_h1);
-      if (lane == 0) {
-        pA = hX;
-        pB = hY;
-      }
-      if (lane == 31) {
-        nA = hX;
-        nB = hY;
-      }
-      const float mlowA = min3f(min3f(pA, pB, cmA), cmB, nA);
-      const float mlowB = min3f(min3f(pB, cmA, cmB), nA, nB);
-      // L+ of both pixels: rows of the step, row neighbours within the pair or one lane away
-      const float ccA = s ? A.d : A.c, upA = s ? A.c : A.b, dnA = s ? ea : A.d;
-      const float ccB = s ? B.d : B.c, upB = s ? B.c : B.b, dnB = s ? eb : B.d;
-      const float hcc = s ? H.d : H.c;
-      const float hL = __shfl_sync(0xffffffffu, hcc, src_hl);
-      float lB = __shfl_up_sync(0xffffffffu, ccB, 1), rA = __shfl_down_sync(0xffffffffu, ccA, 1);
-      if (lane == 0) lB = hL;
-      if (lane == 31) rA = hL;
-      const float lpA = lplus(ccA, upA, dnA, lB, ccB);
-      const float lpB = lplus(ccB, upB, dnB, ccA, rA);
-      if (copy) {
-        float* o = copy + size_t(yy) * w;
-        if (xa < w) o[xa] = ccA;
-        if (xb < w) o[xb] = ccB;
-      }
-      bool actA, hotA, actB, hotB;
-      bound_test(lpA, mlowA, gain, rn2, g2, clow, chot, actA, hotA);
-      bound_test(lpB, mlowB, gain, rn2, g2, clow, chot, actB, hotB);
-      // word wc holds lanes 0-15 (bits 2l, 2l+1), word wc+1 lanes 16-31: each half
-      // ORs its lanes' bit pairs, shifted into place
-      const int sh = 2 * (lane & 15);
-      const uint32_t va = (uint32_t(xa < w && actA) | (uint32_t(xb < w && actB) << 1)) << sh;
-      const uint32_t vh = (uint32_t(xa < w && hotA) | (uint32_t(xb < w && hotB) << 1)) << sh;
-      const uint32_t vz = (uint32_t(xa < w && lpA == 0.f) | (uint32_t(xb < w && lpB == 0.f) << 1)) << sh;
-      uint32_t act, hot, lz;
-      if (lane < 16) {
-        act = __reduce_or_sync(0x0000ffffu, va);
-        hot = __reduce_or_sync(0x0000ffffu, vh);
-        lz = __reduce_or_sync(0x0000ffffu, vz);
-      } else {
-        act = __reduce_or_sync(0xffff0000u, va);
-        hot = __reduce_or_sync(0xffff0000u, vh);
-        lz = __reduce_or_sync(0xffff0000u, vz);
-      }
-      if ((lane & 15) == 0 && wc + (lane >> 4) < f.wpr) {
-        const size_t o = size_t(yy) * f.wpr + wc + (lane >> 4);
-        f.act[o] = act;
-        f.hot[o] = hot;
-        f.lpz[o] = lz;
-      }
-    }
-    A = Col4{A.c, A.d, ea, ga};
-    B = Col4{B.c, B.d, eb, gb};
-    H = Col4{H.c, H.d, eh, gh};
-  }
-}
-
 // hot/act/lpz bits of the four word columns wc .. wc+3 (wc a multiple of 4),
-// rows [y0, y1), of frame f (whole warp), as bound_span2 with four pixels per
-// lane: lane l holds x0+4l .. x0+4l+3 (one 16-byte load per row when the row
+// rows [y0, y1), of frame f (whole warp), four pixels per lane: lane l holds x0+4l .. x0+4l+3 (one 16-byte load per row when the row
 // pitch and the base allow), so a shuffle brings two neighbours of four
 // pixels; lanes 0-3 also hold the halo columns x0-2, x0-1, x0+128, x0+129. Each
 // group of 8 lanes forms one word of every plane by OR-ing its lanes' 4-bit
-// nibbles in three shuffles. The values and their roundings are bound_span2's.
+// nibbles in three shuffles. The re-test (bound_sparse_kernel) forms the same
+// values with the same roundings (bound_test), so a re-tested pixel whose
+// window did not change keeps its bits.
 __device__ __forceinline__ void bound_span4(const Frame& f, const float* __restrict__ J, int wc, int y0, int y1,
                                             float chot, float clow, float* __restrict__ copy) {
   const int lane = threadIdx.x & 31;
@@ -473,27 +348,6 @@ __global__ void __launch_bounds__(64, 12) bound4_kernel(const Frame* __restrict_
     if (wc >= f.wpr) continue;  // whole warp
     const int y0 = bys * kBH;
     bound_span4(f, f.img, wc, y0, min(y0 + kBH, f.h), chot, clow, f.out_clean);
-  }
-}
-
-// bound_kernel (iteration 1): pairs of word columns of every frame, blocks of
-// kBW words x kBH rows, 4 warps of 2 words; the image buffer starts as a copy of
-// I0. Later iterations re-test only the words with a pixel within 2 px of a
-// change (d2_kernel or d2_seg_kernel, then bound_sparse_kernel).
-__global__ void __launch_bounds__(128) bound_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
-                                                    Params p) {
-  const int warp = threadIdx.x >> 5;
-  float chot, clow;
-  bound_consts(p, chot, clow);
-  for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
-    const int fi = frame_of_block(frames, nframes, b);
-    const Frame& f = frames[fi];
-    const long long lb = b - f.blk0;
-    const int bys = int(lb / f.bx), bxs = int(lb - (long long)bys * f.bx);
-    const int wc = bxs * kBW + 2 * warp;
-    if (wc >= f.wpr) continue;  // whole warp
-    const int y0 = bys * kBH;
-    bound_span2(f, f.img, wc, y0, min(y0 + kBH, f.h), chot, clow, f.out_clean);
   }
 }
 
@@ -1464,8 +1318,8 @@ __global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frame
 // bound_sparse_kernel (iteration >= 2): the bound test of the pixels listed in
 // q2 (within 2 px of a change), by groups of four pixels x .. x+3 that hold a
 // listed one: one thread forms the column medians of the eight columns x-2 ..
-// x+5 (rows and columns clamped at the frame's edges, as in the sliding pass),
-// then per pixel the minimum of five of them and L+: the sliding pass's
+// x+5 (rows and columns clamped at the frame's edges, as in the dense pass),
+// then per pixel the minimum of five of them and L+: the dense pass's
 // values. The whole group is rewritten (an unlisted pixel gets the value it
 // holds, its window being unchanged). The warp merges its groups per word and
 // writes them with one AND and one OR per plane and word, so warps sharing a
