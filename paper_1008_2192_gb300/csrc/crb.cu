@@ -244,7 +244,7 @@ int init_ctx(crb_ctx* c) {
   }
   {
     const void* fns[kQKernels] = {
-        reinterpret_cast<const void*>(crb::bound4_kernel),      reinterpret_cast<const void*>(crb::need_kernel),
+        reinterpret_cast<const void*>(crb::bound_dense_kernel),      reinterpret_cast<const void*>(crb::need_kernel),
         reinterpret_cast<const void*>(crb::s_kernel),           reinterpret_cast<const void*>(crb::sp_kernel),
         reinterpret_cast<const void*>(crb::m3need_kernel<false>), reinterpret_cast<const void*>(crb::m3_kernel),
         reinterpret_cast<const void*>(crb::cand_test_kernel),   reinterpret_cast<const void*>(crb::rep_compute_kernel),
@@ -258,7 +258,7 @@ int init_ctx(crb_ctx* c) {
       int o = 0;
       const bool col = i == kQNeed || i == kQM3need || i == kQD2 || i == kQD2Seg || i == kQNeedSeg ||
                        i == kQM3needSeg || i == kQM3needAll;
-      const int threads = i == kQBound ? 64 : col ? crb::kColWarps * 32 : 256;
+      const int threads = i == kQBound ? crb::kBoundThreads : col ? crb::kColWarps * 32 : 256;
       CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[i], threads, 0));
       c->occ_q[i] = o > 0 ? o : 1;
     }
@@ -450,7 +450,8 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
       timed(c, kPBound, stream, [&] {
         if (k == 1) {
           tq(kQBound, [&] {
-            crb::bound4_kernel<<<grid(kQBound, P.nblocks), 64, 0, stream>>>(c->d_frames, P.n, P.nblocks, c->p);
+            crb::bound_dense_kernel<<<grid(kQBound, P.nblocks), crb::kBoundThreads, 0, stream>>>(c->d_frames, P.n,
+                                                                                         P.nblocks, c->p);
           });
         } else {  // the pixels within 2 px of a change, re-tested one by one
           if (seg) {

@@ -191,119 +191,131 @@ __device__ __forceinline__ void col_step(Col4& s, float e, float g, float& m0, f
   m1 = clamp_med(g, c1, c2);
 }
 
-// hot/act/lpz bits of the four word columns wc .. wc+3 (wc a multiple of 4),
-// rows [y0, y1), of frame f (whole warp), four pixels per lane: lane l holds x0+4l .. x0+4l+3 (one 16-byte load per row when the row
-// pitch and the base allow), so a shuffle brings two neighbours of four
-// pixels; lanes 0-3 also hold the halo columns x0-2, x0-1, x0+128, x0+129. Each
-// group of 8 lanes forms one word of every plane by OR-ing its lanes' 4-bit
-// nibbles in three shuffles. The re-test (bound_sparse_kernel) forms the same
-// values with the same roundings (bound_test), so a re-tested pixel whose
-// window did not change keeps its bits.
-__device__ __forceinline__ void bound_span4(const Frame& f, const float* __restrict__ J, int wc, int y0, int y1,
-                                            float chot, float clow, float* __restrict__ copy) {
+// hot/act/lpz bits of the NP word columns wc .. wc+NP-1 (wc a multiple of NP),
+// rows [y0, y1), of frame f (whole warp), NP pixels per lane (NP = 4 or 8):
+// lane l holds x0+NP*l .. x0+NP*l+NP-1 (16-byte loads per row when the row
+// pitch and the base allow), so a shuffle brings two neighbours of NP pixels;
+// lanes 0-3 also hold the halo columns x0-2, x0-1, x0+32NP, x0+32NP+1. Each
+// group of 32/NP lanes forms one word of every plane by OR-ing its lanes'
+// NP-bit fields in log2(32/NP) shuffles. The re-test (bound_sparse_kernel)
+// forms the same values with the same roundings (bound_test), so a re-tested
+// pixel whose window did not change keeps its bits.
+template <int NP>
+__device__ __forceinline__ void bound_span(const Frame& f, const float* __restrict__ J, int wc, int y0, int y1,
+                                           float chot, float clow, float* __restrict__ copy) {
+  static_assert(NP == 4 || NP == 8, "whole 16-byte vectors, whole words per lane group");
+  constexpr int kLanesPerWord = 32 / NP;
   const int lane = threadIdx.x & 31;
   const int w = f.w, h = f.h;
   const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
-  const int x0 = wc * 32, xp = x0 + 4 * lane;
-  int cx[4];
+  const int x0 = wc * 32, xp = x0 + NP * lane;
+  int cx[NP];
+  uint32_t valid = 0;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) cx[i] = min(xp + i, w - 1);
-  const uint32_t valid = (xp < w ? 1u : 0u) | (xp + 1 < w ? 2u : 0u) | (xp + 2 < w ? 4u : 0u) | (xp + 3 < w ? 8u : 0u);
-  const int hx = lane < 2 ? x0 - 2 + lane : x0 + 126 + lane;  // halo columns (lanes 0-3)
+  for (int i = 0; i < NP; ++i) {
+    cx[i] = min(xp + i, w - 1);
+    valid |= (xp + i < w ? 1u : 0u) << i;
+  }
+  const int hx = lane < 2 ? x0 - 2 + lane : x0 + 32 * NP - 2 + lane;  // halo columns (lanes 0-3)
   const int hc = clampi(hx, 0, w - 1);
-  const bool vec = ((reinterpret_cast<uintptr_t>(J) & 15u) == 0) && ((w & 3) == 0) && (xp + 3 < w);
+  const bool vec = ((reinterpret_cast<uintptr_t>(J) & 15u) == 0) && ((w & 3) == 0) && (xp + NP - 1 < w);
   const bool vcopy = vec && ((reinterpret_cast<uintptr_t>(copy) & 15u) == 0);
   const int src_h0 = lane == 0 ? 0 : 2, src_h1 = lane == 0 ? 1 : 3, src_hl = lane == 0 ? 1 : 2;
-  auto ld = [&](int yy, float (&v)[4], float& vh) {
+  auto ld = [&](int yy, float (&v)[NP], float& vh) {
     const float* r = J + size_t(clampi(yy, 0, h - 1)) * size_t(w);
     if (vec) {
-      const float4 t = __ldg(reinterpret_cast<const float4*>(r + xp));
-      v[0] = t.x;
-      v[1] = t.y;
-      v[2] = t.z;
-      v[3] = t.w;
+#pragma unroll
+      for (int q = 0; q < NP / 4; ++q) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(r + xp) + q);
+        v[4 * q] = t.x;
+        v[4 * q + 1] = t.y;
+        v[4 * q + 2] = t.z;
+        v[4 * q + 3] = t.w;
+      }
     } else {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) v[i] = __ldg(r + cx[i]);
+      for (int i = 0; i < NP; ++i) v[i] = __ldg(r + cx[i]);
     }
     vh = __ldg(r + hc);
   };
-  Col4 A[4], H;
+  Col4 A[NP], H;
   {
-    float v[4];
+    float v[NP];
     ld(y0 - 2, v, H.a);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) A[i].a = v[i];
+    for (int i = 0; i < NP; ++i) A[i].a = v[i];
     ld(y0 - 1, v, H.b);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) A[i].b = v[i];
+    for (int i = 0; i < NP; ++i) A[i].b = v[i];
     ld(y0, v, H.c);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) A[i].c = v[i];
+    for (int i = 0; i < NP; ++i) A[i].c = v[i];
     ld(y0 + 1, v, H.d);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) A[i].d = v[i];
+    for (int i = 0; i < NP; ++i) A[i].d = v[i];
   }
-  const int sh = 4 * (lane & 7);
+  const int sh = NP * (lane % kLanesPerWord);
   for (int y = y0; y < y1; y += 2) {
-    float e[4], g[4], eh, gh;
+    float e[NP], g[NP], eh, gh;
     ld(y + 2, e, eh);
     ld(y + 3, g, gh);
-    float m[4][2], mh[2];
+    float m[NP][2], mh[2];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) col_step(A[i], e[i], g[i], m[i][0], m[i][1]);
+    for (int i = 0; i < NP; ++i) col_step(A[i], e[i], g[i], m[i][0], m[i][1]);
     col_step(H, eh, gh, mh[0], mh[1]);
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       const int yy = y + s;
       if (yy >= y1) break;
-      // column medians x-2, x-1 (lane-1) and x+4, x+5 (lane+1) of the lane's four; halo at the ends
-      float l2 = __shfl_up_sync(0xffffffffu, m[2][s], 1), l3 = __shfl_up_sync(0xffffffffu, m[3][s], 1);
-      float r0 = __shfl_down_sync(0xffffffffu, m[0][s], 1), r1 = __shfl_down_sync(0xffffffffu, m[1][s], 1);
+      // column medians x-2, x-1 (lane-1) and x+NP, x+NP+1 (lane+1) of the lane's NP; halo at the ends
+      float c[NP + 4];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) c[i + 2] = m[i][s];
+      c[0] = __shfl_up_sync(0xffffffffu, m[NP - 2][s], 1);
+      c[1] = __shfl_up_sync(0xffffffffu, m[NP - 1][s], 1);
+      c[NP + 2] = __shfl_down_sync(0xffffffffu, m[0][s], 1);
+      c[NP + 3] = __shfl_down_sync(0xffffffffu, m[1][s], 1);
       const float hX = __shfl_sync(0xffffffffu, mh[s], src_h0), hY = __shfl_sync(0xffffffffu, mh[s], src_h1);
       if (lane == 0) {
-        l2 = hX;
-        l3 = hY;
+        c[0] = hX;
+        c[1] = hY;
       }
       if (lane == 31) {
-        r0 = hX;
-        r1 = hY;
+        c[NP + 2] = hX;
+        c[NP + 3] = hY;
       }
-      const float c0 = m[0][s], c1 = m[1][s], c2 = m[2][s], c3 = m[3][s];
-      float mlow[4];
-      mlow[0] = min3f(min3f(l2, l3, c0), c1, c2);
-      mlow[1] = min3f(min3f(l3, c0, c1), c2, c3);
-      mlow[2] = min3f(min3f(c0, c1, c2), c3, r0);
-      mlow[3] = min3f(min3f(c1, c2, c3), r0, r1);
       // the rows of the step: centre, above, below
-      float cc[4], up[4], dn[4];
+      float cc[NP], up[NP], dn[NP];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < NP; ++i) {
         cc[i] = s ? A[i].d : A[i].c;
         up[i] = s ? A[i].c : A[i].b;
         dn[i] = s ? e[i] : A[i].d;
       }
       const float hcc = s ? H.d : H.c;
       const float hL = __shfl_sync(0xffffffffu, hcc, src_hl);
-      float lft = __shfl_up_sync(0xffffffffu, cc[3], 1), rgt = __shfl_down_sync(0xffffffffu, cc[0], 1);
+      float lft = __shfl_up_sync(0xffffffffu, cc[NP - 1], 1), rgt = __shfl_down_sync(0xffffffffu, cc[0], 1);
       if (lane == 0) lft = hL;
       if (lane == 31) rgt = hL;
       if (copy) {
         float* o = copy + size_t(yy) * w;
         if (vcopy) {
-          *reinterpret_cast<float4*>(o + xp) = make_float4(cc[0], cc[1], cc[2], cc[3]);
+#pragma unroll
+          for (int q = 0; q < NP / 4; ++q)
+            reinterpret_cast<float4*>(o + xp)[q] = make_float4(cc[4 * q], cc[4 * q + 1], cc[4 * q + 2], cc[4 * q + 3]);
         } else {
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < NP; ++i)
             if (xp + i < w) o[xp + i] = cc[i];
         }
       }
       uint32_t va = 0, vh = 0, vz = 0;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float lp = lplus(cc[i], up[i], dn[i], i == 0 ? lft : cc[i - 1], i == 3 ? rgt : cc[i + 1]);
+      for (int i = 0; i < NP; ++i) {
+        const float mlow = min3f(min3f(c[i], c[i + 1], c[i + 2]), c[i + 3], c[i + 4]);
+        const float lp = lplus(cc[i], up[i], dn[i], i == 0 ? lft : cc[i - 1], i == NP - 1 ? rgt : cc[i + 1]);
         bool act, hot;
-        bound_test(lp, mlow[i], gain, rn2, g2, clow, chot, act, hot);
+        bound_test(lp, mlow, gain, rn2, g2, clow, chot, act, hot);
         va |= uint32_t(act) << i;
         vh |= uint32_t(hot) << i;
         vz |= uint32_t(lp == 0.f) << i;
@@ -312,13 +324,13 @@ __device__ __forceinline__ void bound_span4(const Frame& f, const float* __restr
       vh = (vh & valid) << sh;
       vz = (vz & valid) << sh;
 #pragma unroll
-      for (int o = 1; o < 8; o <<= 1) {
+      for (int o = 1; o < kLanesPerWord; o <<= 1) {
         va |= __shfl_xor_sync(0xffffffffu, va, o);
         vh |= __shfl_xor_sync(0xffffffffu, vh, o);
         vz |= __shfl_xor_sync(0xffffffffu, vz, o);
       }
-      const int wo = wc + (lane >> 3);
-      if ((lane & 7) == 0 && wo < f.wpr) {
+      const int wo = wc + lane / kLanesPerWord;
+      if (lane % kLanesPerWord == 0 && wo < f.wpr) {
         const size_t o = size_t(yy) * f.wpr + wo;
         f.act[o] = va;
         f.hot[o] = vh;
@@ -326,16 +338,21 @@ __device__ __forceinline__ void bound_span4(const Frame& f, const float* __restr
       }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) A[i] = Col4{A[i].c, A[i].d, e[i], g[i]};
+    for (int i = 0; i < NP; ++i) A[i] = Col4{A[i].c, A[i].d, e[i], g[i]};
     H = Col4{H.c, H.d, eh, gh};
   }
 }
 
-// bound4_kernel (iteration 1): the dense bound pass by groups of four word
-// columns, blocks of kBW words x kBH rows, 2 warps of 4 words (80 registers,
-// twelve blocks per SM: spans of 64 or 128 rows per warp measured slower).
-__global__ void __launch_bounds__(64, 12) bound4_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
-                                                    Params p) {
+// bound_dense_kernel (iteration 1): the dense bound pass, blocks of kBW words
+// x kBH rows, warps of kBoundNP words (kBoundNP pixels per lane). Eight pixels
+// per lane (126 registers, sixteen one-warp blocks per SM) measured 10 % faster
+// than four (80 registers, twelve two-warp blocks); spans of 64 or 128 rows per
+// warp measured slower than 32.
+constexpr int kBoundNP = 8;
+constexpr int kBoundThreads = 32 * kBW / kBoundNP;
+
+__global__ void __launch_bounds__(kBoundThreads, kBoundNP == 4 ? 12 : 16)
+    bound_dense_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks, Params p) {
   const int warp = threadIdx.x >> 5;
   float chot, clow;
   bound_consts(p, chot, clow);
@@ -344,10 +361,10 @@ __global__ void __launch_bounds__(64, 12) bound4_kernel(const Frame* __restrict_
     const Frame& f = frames[fi];
     const long long lb = b - f.blk0;
     const int bys = int(lb / f.bx), bxs = int(lb - (long long)bys * f.bx);
-    const int wc = bxs * kBW + 4 * warp;
+    const int wc = bxs * kBW + kBoundNP * warp;
     if (wc >= f.wpr) continue;  // whole warp
     const int y0 = bys * kBH;
-    bound_span4(f, f.img, wc, y0, min(y0 + kBH, f.h), chot, clow, f.out_clean);
+    bound_span<kBoundNP>(f, f.img, wc, y0, min(y0 + kBH, f.h), chot, clow, f.out_clean);
   }
 }
 
