@@ -202,6 +202,9 @@ def network_minmax():
             m = re.match(r"// rank \d+ \(0-based\) of (\d+) values; \d+ two-input min/max, (\d+) instructions", line)
             if m:
                 counts[int(m.group(1))] = int(m.group(2))
+            m = re.match(r"// row group: (\d+) medians of 5x5 windows; \d+ two-input min/max, (\d+) instructions", line)
+            if m:
+                counts["row25"] = int(m.group(2)) / int(m.group(1))  # per median
     return counts
 
 
@@ -753,7 +756,9 @@ def main():
         roofline = {"bound": "latency", "kernel": dom, "achieved": None, "peak": None, "unit": None, "frac": None,
                     "traffic": None}
     # context: the selection networks over all detection kernels
-    minmax = sum(w[0] * net[25] + w[1] * net[25] + w[2] * net[9] + w[3] * (7 * net[7] + 12) + w[4] * net[49]
+    # the queue kernels take S and S' medians by groups of four adjacent windows
+    m25 = net["row25"] if tuned[2] == "queue" else net[25]
+    minmax = sum(w[0] * m25 + w[1] * m25 + w[2] * net[9] + w[3] * (7 * net[7] + 12) + w[4] * net[49]
                  + w[5] * BOUND_TEST_MINMAX for w in work)
     roofline.update({
         "kernels": kernels,

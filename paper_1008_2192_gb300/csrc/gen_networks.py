@@ -14,6 +14,19 @@ inputs iff it does so for all 0/1 inputs (the 0-1 principle, Knuth TAOCP
 random real inputs for every n; the pruning itself only removes operations
 that cannot reach the output.
 
+Row groups: the 5x5 medians of G horizontally adjacent windows share columns.
+Each of the G + 4 columns is sorted once; sorted lists are then merged
+(odd-even merge of two sorted lists of any lengths) in a tree per window, and
+merges shared by several windows are built once. A merged list of n < 25 values
+of a window keeps only its ranks max(0, n - 13) .. min(n - 1, 12): a value of
+rank s among them has a window rank between s and s + 25 - n, so it can be the
+median (rank 12) only inside that range. A dropped low value ranks below every
+kept value of any merge above it (its rank in the union of two lists is below
+n - 13 of the union), so a parent's ranks shift down by its children's low
+drops. The generator checks the whole network on every 0/1 input whose columns
+are already sorted, and the column sorter on every 0/1 input: together they
+cover all 0/1 inputs, since the merges read only sorted columns.
+
 Usage: python gen_networks.py OUT.cuh [--quick]   (--quick: random checks only)
 """
 
@@ -170,15 +183,18 @@ def fuse3(d, order, out):
     """Pairs a min (max) node with a single-use min (max) operand: op(op(a, b), c) = op3(a, b, c).
 
     Returns {node: (op, operands)} for every emitted node; operands has 2 or 3 entries.
-    The three-input form issues at the rate of the two-input one on sm_103a.
+    The three-input form issues at the rate of the two-input one on sm_103a. `out` is
+    one output node or a list of them.
     """
+    outs = out if isinstance(out, list) else [out]
     uses = {}
     for v in order:
         k = d.defs[v]
         if k[0] in ("min", "max"):
             for u in k[1:]:
                 uses[u] = uses.get(u, 0) + 1
-    uses[out] = uses.get(out, 0) + 1
+    for o in outs:
+        uses[o] = uses.get(o, 0) + 1
     absorbed = set()
     emitted = {}
     for v in reversed(order):  # from the output down, so a fused operand is never emitted twice
@@ -219,6 +235,154 @@ def emit(name, n, rank, d, order, out):
     return "\n".join(lines)
 
 
+def live_order(d, outs):
+    """The nodes the outputs depend on, in topological (id) order."""
+    live, stack = set(), list(outs)
+    while stack:
+        v = stack.pop()
+        if v in live:
+            continue
+        live.add(v)
+        k = d.defs[v]
+        if k[0] in ("min", "max"):
+            stack += [k[1], k[2]]
+    return [v for v in range(len(d.defs)) if v in live]
+
+
+def merge_sorted(d, a, b):
+    """Odd-even merge (Batcher 1968) of two sorted lists of nodes, any lengths: the evens and the odds
+    of both lists are merged recursively, then neighbouring odd/even outputs are compared."""
+    if not a:
+        return list(b)
+    if not b:
+        return list(a)
+    if len(a) == 1 and len(b) == 1:
+        return [d.minmax("min", a[0], b[0]), d.minmax("max", a[0], b[0])]
+    e = merge_sorted(d, a[0::2], b[0::2])
+    o = merge_sorted(d, a[1::2], b[1::2])
+    out, i = [e[0]], 0
+    while i < len(o) and i + 1 < len(e):
+        out += [d.minmax("min", o[i], e[i + 1]), d.minmax("max", o[i], e[i + 1])]
+        i += 1
+    return out + o[i:] + e[i + 1:]
+
+
+def sort_nodes(d, xs):
+    """Odd-even merge sort of a list of nodes."""
+    if len(xs) <= 1:
+        return list(xs)
+    h = len(xs) // 2
+    return merge_sorted(d, sort_nodes(d, xs[:h]), sort_nodes(d, xs[h:]))
+
+
+ROW_D, ROW_MED = 5, 12  # 5x5 windows, median = rank 12 of 25
+
+
+def row_network(g):
+    """Medians of the g (even) adjacent 5x5 windows over a 5 x (g + 4) block; input ("in", r*(g+4)+c) is
+    row r, column c; window i covers columns i .. i+4. Outputs 2j and 2j+1 share the merge of columns
+    2j+1 .. 2j+4 (two pair merges); output 2j adds column 2j, output 2j+1 column 2j+5. For g = 4 an
+    exhaustive search over every merge tree of the four windows finds no cheaper network."""
+    assert g % 2 == 0
+    d = Dag()
+    ncol = g + 4
+    cols = [sort_nodes(d, [d.node(("in", r * ncol + c)) for r in range(ROW_D)]) for c in range(ncol)]
+
+    def kept_range(n):
+        # the ranks of n values of a window that can be its median
+        return max(0, n - (ROW_MED + 1)), min(n - 1, ROW_MED)
+
+    def merge_kept(a, na, b, nb):
+        # a, b: the kept lists of na and nb window values; returns the kept list of the na + nb values
+        shift = kept_range(na)[0] + kept_range(nb)[0]
+        lo, hi = kept_range(na + nb)
+        return merge_sorted(d, a, b)[lo - shift: hi - shift + 1]
+
+    pair = {c: merge_kept(cols[c], ROW_D, cols[c + 1], ROW_D) for c in range(1, ncol - 2, 2)}
+    outs = []
+    for j in range(g // 2):
+        c = 2 * j + 1
+        quad = merge_kept(pair[c], 2 * ROW_D, pair[c + 2], 2 * ROW_D)
+        for extra in (c - 1, c + 4):
+            # one more column completes the window: its median is the one kept rank of 25 values
+            outs.append(merge_kept(cols[extra], ROW_D, quad, 4 * ROW_D)[0])
+    return d, live_order(d, outs), outs
+
+
+def evaluate_many(d, order, outs, X):
+    vals = {}
+    boolean = X.dtype == bool
+    for v in order:
+        k = d.defs[v]
+        if k[0] == "in":
+            vals[v] = X[:, k[1]]
+        elif k[0] == "const":
+            raise AssertionError("constant survived pruning")
+        elif k[0] == "min":
+            vals[v] = (vals[k[1]] & vals[k[2]]) if boolean else np.minimum(vals[k[1]], vals[k[2]])
+        else:
+            vals[v] = (vals[k[1]] | vals[k[2]]) if boolean else np.maximum(vals[k[1]], vals[k[2]])
+    return [vals[o] for o in outs]
+
+
+def verify_row(g, d, order, outs, exhaustive=True):
+    ncol = g + 4
+    rng = np.random.default_rng(1)
+    X = rng.normal(size=(20000, ROW_D * ncol))
+    X[:5000] = rng.integers(0, 3, size=(5000, ROW_D * ncol))  # ties
+    got = evaluate_many(d, order, outs, X)
+    blk = X.reshape(-1, ROW_D, ncol)
+    for i in range(g):
+        exp = np.sort(blk[:, :, i:i + ROW_D].reshape(len(X), -1), axis=1)[:, ROW_MED]
+        assert np.array_equal(got[i], exp), f"row network, real inputs, window {i}"
+    if not exhaustive:
+        return
+    # the column sorter on every 0/1 input
+    ds = Dag()
+    srt = sort_nodes(ds, [ds.node(("in", r)) for r in range(ROW_D)])
+    Z = ((np.arange(1 << ROW_D)[:, None] >> np.arange(ROW_D)[None, :]) & 1).astype(bool)
+    res = np.stack(evaluate_many(ds, live_order(ds, srt), srt, Z), axis=1)
+    assert np.array_equal(res, np.sort(Z, axis=1)), "column sorter"
+    # the network on every 0/1 input with sorted columns: column c holds k_c ones at its bottom rows
+    nconf = (ROW_D + 1) ** ncol
+    idx = np.arange(nconf)
+    counts = np.stack([(idx // (ROW_D + 1) ** c) % (ROW_D + 1) for c in range(ncol)], axis=1)
+    rows = np.arange(ROW_D)
+    X = (rows[None, :, None] >= (ROW_D - counts)[:, None, :]).reshape(nconf, -1)
+    got = evaluate_many(d, order, outs, X)
+    for i in range(g):
+        exp = counts[:, i:i + ROW_D].sum(axis=1) >= ROW_D * ROW_D - ROW_MED
+        assert np.array_equal(got[i], exp), f"row network, 0/1 inputs, window {i}"
+
+
+def emit_row(name, g, d, order, outs):
+    fused = fuse3(d, order, outs)
+    two = sum(1 for v in order if d.defs[v][0] in ("min", "max"))
+    ncol = g + 4
+    lines = [f"// row group: {g} medians of 5x5 windows; {two} two-input min/max, {len(fused)} instructions "
+             "with three-input forms",
+             f"// m[i] = median of v[0..4][i..i+4] (rank 12 of 25)",
+             f"__device__ __forceinline__ void {name}(const float (&v)[5][{ncol}], float (&m)[{g}]) {{"]
+    names, t = {}, 0
+    for v in order:
+        k = d.defs[v]
+        if k[0] == "in":
+            names[v] = f"v[{k[1] // ncol}][{k[1] % ncol}]"
+        elif v in fused:
+            op, ops = fused[v]
+            args = ", ".join(names[u] for u in ops)
+            fn = ("fminf" if op == "min" else "fmaxf") if len(ops) == 2 else ("min3f" if op == "min" else "max3f")
+            names[v] = f"t{t}"
+            lines.append(f"  const float t{t} = {fn}({args});")
+            t += 1
+    for i, o in enumerate(outs):
+        lines.append(f"  m[{i}] = {names[o]};")
+    lines.append("}")
+    return "\n".join(lines), two, len(fused)
+
+
+ROW_SPECS = [("med25_row2", 2), ("med25_row4", 4)]
+
 SPECS = [("sel_med5", 5, 2), ("sel_med7", 7, 3), ("sel_med9", 9, 4), ("sel_med25", 25, 12),
          ("sel_med49", 49, 24)]
 
@@ -246,6 +410,13 @@ def main(path, exhaustive=True):
         parts.append(emit(name, n, rank, d, order, out))
         parts.append("")
         print(f"{name}: {c} ops", file=sys.stderr)
+    for (name, g) in ROW_SPECS:
+        d, order, outs = row_network(g)
+        verify_row(g, d, order, outs, exhaustive)
+        text, two, ins = emit_row(name, g, d, order, outs)
+        parts.append(text)
+        parts.append("")
+        print(f"{name}: {two} ops, {ins} instructions", file=sys.stderr)
     with open(path, "w") as f:
         f.write("\n".join(parts))
 

@@ -1248,55 +1248,175 @@ struct WarpLists {
   }
 };
 
-// s_kernel: at QS, m5 (floored), N, L+ and S of J.
-__global__ void __launch_bounds__(256, 4) s_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k) {
-  expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNS],
-               [&](bool valid, int fi, int x, int y) {
-                 if (!valid) return;
-                 const Frame& f = frames[fi];
-                 float v[25];
-                 load_window<2>(qsrc(f, k), x, y, f.w, f.h, v);
-                 const float lp = lplus(v[12], v[7], v[17], v[11], v[13]);
-                 const float m5f = floor_m5(sel_med25(v));
-                 const float nn = noise_of(m5f, f.gain, __fmul_rn(f.rn, f.rn));
-                 const size_t o = size_t(y) * f.w + x;
-                 f.mapS[o] = __fdiv_rn(lp, __fmul_rn(2.f, nn));
-                 f.mapN[o] = nn;
-               });
+// Rows y-2 .. y+2 and columns x0-2 .. x0+3 of a (clamped at the frame's
+// edges, as load_window) for a pair of pixels, x0 even: away from the edges,
+// three aligned 8-byte loads per row.
+__device__ __forceinline__ void load_pair_span(const float* __restrict__ a, int x0, int y, int w, int h,
+                                               float (&v)[5][6]) {
+  const bool vec = x0 >= 2 && x0 + 4 <= w && (w & 1) == 0 && (reinterpret_cast<uintptr_t>(a) & 7u) == 0;
+#pragma unroll
+  for (int dy = 0; dy < 5; ++dy) {
+    const float* __restrict__ r = a + size_t(clampi(y - 2 + dy, 0, h - 1)) * size_t(w);
+    if (vec) {
+      const float2 A = __ldg(reinterpret_cast<const float2*>(r + x0 - 2));
+      const float2 M = __ldg(reinterpret_cast<const float2*>(r + x0));
+      const float2 C = __ldg(reinterpret_cast<const float2*>(r + x0 + 2));
+      v[dy][0] = A.x, v[dy][1] = A.y, v[dy][2] = M.x, v[dy][3] = M.y, v[dy][4] = C.x, v[dy][5] = C.y;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) v[dy][c] = __ldg(r + clampi(x0 - 2 + c, 0, w - 1));
+    }
+  }
 }
 
-// sp_kernel: at QSP, S' = S - med5(S); S' > sigclip -> test bit.
+// The 5x5 window rows of G adjacent pixels x0 .. x0+G-1 (columns x0-2 ..
+// x0+G+1) and their G medians, from the network over the G+4 sorted columns.
+template <int G>
+__device__ __forceinline__ void group_med25(const float* __restrict__ a, int x0, int y, int w, int h,
+                                            float (&v)[5][G + 4], float (&m)[G]) {
+  static_assert(G == 2 || G == 4, "networks exist for pairs and groups of four");
+  if constexpr (G == 2) {
+    load_pair_span(a, x0, y, w, h, v);
+    med25_row2(v, m);
+  } else {
+    load_span<2>(a, x0, y, w, h, v);
+    med25_row4(v, m);
+  }
+}
+
+// Group width of s_kernel and sp_kernel: 1 takes each listed pixel's 5x5
+// median alone (sel_med25); 2 and 4 take those of the listed pixel's aligned
+// group of G at once from the group's G+4 sorted columns (med25_row2/4), which
+// loads and sorts each column once instead of five times, at the cost of the
+// group's unlisted pixels.
+constexpr int kSGroup = 2;
+
+// s_kernel: at QS, m5 (floored), N, L+ and S of J.
+template <int G>
+__global__ void __launch_bounds__(256, G == 4 ? 3 : 4) s_kernel(const Frame* __restrict__ frames, int nframes,
+                                                                 Queues Q, int k) {
+  if constexpr (G == 1) {
+    expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNS],
+                 [&](bool valid, int fi, int x, int y) {
+                   if (!valid) return;
+                   const Frame& f = frames[fi];
+                   float v[25];
+                   load_window<2>(qsrc(f, k), x, y, f.w, f.h, v);
+                   const float lp = lplus(v[12], v[7], v[17], v[11], v[13]);
+                   const float m5f = floor_m5(sel_med25(v));
+                   const float nn = noise_of(m5f, f.gain, __fmul_rn(f.rn, f.rn));
+                   const size_t o = size_t(y) * f.w + x;
+                   f.mapS[o] = __fdiv_rn(lp, __fmul_rn(2.f, nn));
+                   f.mapN[o] = nn;
+                 });
+  } else {
+    expand_words<G>(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNS],
+                    [&](bool valid, int fi, int x0, int y, uint32_t bits) {
+                      if (!valid) return;
+                      const Frame& f = frames[fi];
+                      float v[5][G + 4], m5[G];
+                      group_med25<G>(qsrc(f, k), x0, y, f.w, f.h, v, m5);
+                      const float rn2 = __fmul_rn(f.rn, f.rn);
+                      const size_t o = size_t(y) * f.w + x0;
+#pragma unroll
+                      for (int i = 0; i < G; ++i) {
+                        if (!((bits >> i) & 1u)) continue;
+                        const float lp = lplus(v[2][i + 2], v[1][i + 2], v[3][i + 2], v[2][i + 1], v[2][i + 3]);
+                        const float nn = noise_of(floor_m5(m5[i]), f.gain, rn2);
+                        f.mapS[o + i] = __fdiv_rn(lp, __fmul_rn(2.f, nn));
+                        f.mapN[o + i] = nn;
+                      }
+                    });
+  }
+}
+
+// Bits of columns xs .. xs+7 of row qy of a bit plane (bit c = column xs + c),
+// for 0 <= xs and xs + 7 < w: at most two words.
+__device__ __forceinline__ uint32_t plane_bits8(const uint32_t* __restrict__ plane, int wpr, int xs, int qy) {
+  const size_t ro = size_t(qy) * wpr + (xs >> 5);
+  const int sh = xs & 31;
+  uint64_t pair = plane[ro];
+  if (sh > 24) pair |= uint64_t(plane[ro + 1]) << 32;
+  return uint32_t(pair >> sh) & 0xffu;
+}
+
+// sp_kernel: at QSP, S' = S - med5(S); S' > sigclip -> test bit. S is exactly
+// 0 where L+ = 0 (the lpz plane), where mapS is not written.
+template <int G>
 __global__ void __launch_bounds__(256) sp_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p) {
-  expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q1), Q.n[kNSP],
-               [&](bool valid, int fi, int x, int y) {
-                 if (!valid) return;
-                 const Frame& f = frames[fi];
-                 float v[25];
-                 load_window<2>(f.mapS, x, y, f.w, f.h, v);
-                 // S is exactly 0 where L+ = 0; mapS is not written there
-                 if (x >= 2 && x < f.w - 2) {
+  if constexpr (G == 1) {
+    expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q1), Q.n[kNSP],
+                 [&](bool valid, int fi, int x, int y) {
+                   if (!valid) return;
+                   const Frame& f = frames[fi];
+                   float v[25];
+                   load_window<2>(f.mapS, x, y, f.w, f.h, v);
+                   if (x >= 2 && x < f.w - 2) {
 #pragma unroll
-                   for (int dy = 0; dy < 5; ++dy) {
-                     const uint32_t z = plane_bits5(f.lpz, f.wpr, f.w, x - 2, clampi(y - 2 + dy, 0, f.h - 1));
+                     for (int dy = 0; dy < 5; ++dy) {
+                       const uint32_t z = plane_bits5(f.lpz, f.wpr, f.w, x - 2, clampi(y - 2 + dy, 0, f.h - 1));
 #pragma unroll
-                     for (int dx = 0; dx < 5; ++dx)
-                       if ((z >> dx) & 1u) v[dy * 5 + dx] = 0.f;
-                   }
-                 } else {
+                       for (int dx = 0; dx < 5; ++dx)
+                         if ((z >> dx) & 1u) v[dy * 5 + dx] = 0.f;
+                     }
+                   } else {
 #pragma unroll
-                   for (int dy = 0; dy < 5; ++dy) {
-                     const size_t ro = size_t(clampi(y - 2 + dy, 0, f.h - 1)) * f.wpr;
+                     for (int dy = 0; dy < 5; ++dy) {
+                       const size_t ro = size_t(clampi(y - 2 + dy, 0, f.h - 1)) * f.wpr;
 #pragma unroll
-                     for (int dx = 0; dx < 5; ++dx) {
-                       const int xx = clampi(x - 2 + dx, 0, f.w - 1);
-                       if ((f.lpz[ro + (xx >> 5)] >> (xx & 31)) & 1u) v[dy * 5 + dx] = 0.f;
+                       for (int dx = 0; dx < 5; ++dx) {
+                         const int xx = clampi(x - 2 + dx, 0, f.w - 1);
+                         if ((f.lpz[ro + (xx >> 5)] >> (xx & 31)) & 1u) v[dy * 5 + dx] = 0.f;
+                       }
                      }
                    }
-                 }
-                 const float sp = __fsub_rn(v[12], sel_med25(v));
-                 f.mapSp[size_t(y) * f.w + x] = sp;
-                 if (sp > p.sigclip) atomicOr(&f.test[size_t(y) * f.wpr + (x >> 5)], 1u << (x & 31));
-               });
+                   const float sp = __fsub_rn(v[12], sel_med25(v));
+                   f.mapSp[size_t(y) * f.w + x] = sp;
+                   if (sp > p.sigclip) atomicOr(&f.test[size_t(y) * f.wpr + (x >> 5)], 1u << (x & 31));
+                 });
+  } else {
+    // the group's test bits go out with one atomic OR
+    expand_words<G>(frames, nframes, reinterpret_cast<const uint2*>(Q.q1), Q.n[kNSP],
+                    [&](bool valid, int fi, int x0, int y, uint32_t bits) {
+                      if (!valid) return;
+                      const Frame& f = frames[fi];
+                      constexpr int C = G + 4;
+                      float v[5][C], med[G];
+                      if constexpr (G == 2) load_pair_span(f.mapS, x0, y, f.w, f.h, v);
+                      else load_span<2>(f.mapS, x0, y, f.w, f.h, v);
+                      if (x0 >= 2 && x0 + 5 < f.w) {
+#pragma unroll
+                        for (int dy = 0; dy < 5; ++dy) {
+                          const uint32_t z = plane_bits8(f.lpz, f.wpr, x0 - 2, clampi(y - 2 + dy, 0, f.h - 1));
+#pragma unroll
+                          for (int c = 0; c < C; ++c)
+                            if ((z >> c) & 1u) v[dy][c] = 0.f;
+                        }
+                      } else {
+#pragma unroll
+                        for (int dy = 0; dy < 5; ++dy) {
+                          const size_t ro = size_t(clampi(y - 2 + dy, 0, f.h - 1)) * f.wpr;
+#pragma unroll
+                          for (int c = 0; c < C; ++c) {
+                            const int xx = clampi(x0 - 2 + c, 0, f.w - 1);
+                            if ((f.lpz[ro + (xx >> 5)] >> (xx & 31)) & 1u) v[dy][c] = 0.f;
+                          }
+                        }
+                      }
+                      if constexpr (G == 2) med25_row2(v, med);
+                      else med25_row4(v, med);
+                      float* __restrict__ out = f.mapSp + size_t(y) * f.w + x0;
+                      uint32_t tb = 0;
+#pragma unroll
+                      for (int i = 0; i < G; ++i) {
+                        if (!((bits >> i) & 1u)) continue;
+                        const float sp = __fsub_rn(v[2][i + 2], med[i]);
+                        out[i] = sp;
+                        tb |= uint32_t(sp > p.sigclip) << i;
+                      }
+                      if (tb) atomicOr(&f.test[size_t(y) * f.wpr + (x0 >> 5)], tb << (x0 & 31));
+                    });
+  }
 }
 
 // m3_kernel: at QM3, med3 of J, by groups of four pixels x0 .. x0+3 that hold

@@ -59,7 +59,9 @@ def test_null_context_and_strerror():
 
 
 def test_networks_exhaustive_zero_one():
-    """The 9- and 25-input selection networks are correct on every 0/1 input (0-1 principle)."""
+    """The selection networks (5 to 25 inputs) are correct on every 0/1 input (0-1 principle); the
+    row-group network of four adjacent 5x5 medians on every 0/1 input with sorted columns, and its
+    column sorter on every 0/1 input; all of them on random real inputs with ties."""
     import importlib.util
     spec = importlib.util.spec_from_file_location(
         "gen_networks", os.path.join(ROOT, "paper_1008_2192_gb300", "csrc", "gen_networks.py"))
@@ -68,6 +70,37 @@ def test_networks_exhaustive_zero_one():
     for (_, n, rank) in g.SPECS:
         c, d, order, out = g.best_network(n, rank)
         g.verify(n, rank, d, order, out, exhaustive=True)
+    for (_, groups) in g.ROW_SPECS:
+        d, order, outs = g.row_network(groups)
+        g.verify_row(groups, d, order, outs, exhaustive=True)
+
+
+def test_row_network_mutants_are_caught():
+    """The row-group checks catch a wrong root and an unsorted column: an output replaced by one operand
+    of its last comparison, and a network whose columns skip their sort, both fail verify_row."""
+    import importlib.util
+    import pytest
+    spec = importlib.util.spec_from_file_location(
+        "gen_networks", os.path.join(ROOT, "paper_1008_2192_gb300", "csrc", "gen_networks.py"))
+    g = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(g)
+    d, order, outs = g.row_network(4)
+    # an output replaced by one operand of its last comparison
+    k = d.defs[outs[1]]
+    assert k[0] in ("min", "max")
+    bad = list(outs)
+    bad[1] = k[1]
+    with pytest.raises(AssertionError):
+        g.verify_row(4, d, g.live_order(d, bad), bad, exhaustive=False)
+    # columns merged unsorted
+    orig = g.sort_nodes
+    try:
+        g.sort_nodes = lambda dd, xs: list(xs) if len(xs) == g.ROW_D else orig(dd, xs)
+        d2, order2, outs2 = g.row_network(4)
+    finally:
+        g.sort_nodes = orig
+    with pytest.raises(AssertionError):
+        g.verify_row(4, d2, order2, outs2, exhaustive=False)
 
 
 def test_server_rejects_invalid_arguments():
