@@ -444,6 +444,8 @@ __device__ __forceinline__ uint32_t cell_class(const uint32_t* __restrict__ cls,
 // queue words wait in shared memory until the warp has counted them: one
 // atomic per warp and queue, then one coalesced entry per nonzero word.
 constexpr int kColWarps = 4;
+// rows per load chunk of the strip kernels: a chunk's loads are issued together
+constexpr int kColChunk = 4;
 
 struct ColWords {
   uint32_t w[kColWarps][kSH][2][32];  // per warp, row, queue: the word of each lane
@@ -527,12 +529,13 @@ __global__ void __launch_bounds__(kColWarps * 32) need_kernel(const Frame* __res
     uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0, n4 = 0;  // own nsp, rows r-6 .. r-2
     uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0, m4 = 0;  // halo nsp
     unsigned int ents[2] = {0u, 0u}, pix[2] = {0u, 0u};
-    // rows y0-4 .. y0+kSH+3 in chunks of 8: the chunk's loads are issued together
-    static_assert((kSH + 8) % 8 == 0, "whole chunks");
-    for (int rc = y0 - 4; rc < y0 + kSH + 4; rc += 8) {
-      uint32_t Lh[8], La[8], Lgh[8], Lga[8], Lc[8], Ls[8], Lz[8];
+    // rows y0-4 .. y0+kSH+3 in chunks of kColChunk: the chunk's loads are issued together
+    static_assert((kSH + 8) % kColChunk == 0, "whole chunks");
+    for (int rc = y0 - 4; rc < y0 + kSH + 4; rc += kColChunk) {
+      uint32_t Lh[kColChunk], La[kColChunk], Lgh[kColChunk], Lga[kColChunk], Lc[kColChunk], Ls[kColChunk],
+          Lz[kColChunk];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < kColChunk; ++i) {
         const int r = rc + i, yo = r - 4;
         const bool rin = r >= 0 && r < f.h;
         const size_t ro = size_t(rin ? r : 0) * f.wpr;
@@ -546,7 +549,7 @@ __global__ void __launch_bounds__(kColWarps * 32) need_kernel(const Frame* __res
         Lz[i] = (out && Lc[i] >= 2u) ? f.lpz[size_t(yo) * f.wpr + wc] : 0u;
       }
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < kColChunk; ++i) {
         h0 = h1; h1 = h2; h2 = h3; h3 = h4; h4 = Lh[i];
         g0 = g1; g1 = g2; g2 = g3; g3 = g4; g4 = Lgh[i];
         a0 = a1; a1 = a2; a2 = La[i];
@@ -623,11 +626,11 @@ __global__ void __launch_bounds__(kColWarps * 32) m3need_kernel(const Frame* __r
     uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0;  // own QT words, rows r-6 .. r
     uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0, s6 = 0;  // halo QT words
     unsigned int ents[2] = {0u, 0u}, pix[2] = {0u, 0u};
-    // rows y0-3 .. y0+kSH+2 in chunks of 8 (the last chunk runs 2 rows past the end)
-    for (int rc = y0 - 3; rc < y0 + kSH + 3; rc += 8) {
-      uint32_t Lq[8], Lg[8], Lm[8], Lc4[8];
+    // rows y0-3 .. y0+kSH+2 in chunks of kColChunk (the last chunk runs past the end)
+    for (int rc = y0 - 3; rc < y0 + kSH + 3; rc += kColChunk) {
+      uint32_t Lq[kColChunk], Lg[kColChunk], Lm[kColChunk], Lc4[kColChunk];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < kColChunk; ++i) {
         const int r = rc + i, yo = r - 3;
         const bool rin = r >= 0 && r < f.h && r < y0 + kSH + 3;
         const size_t ro = size_t(rin ? r : 0) * f.wpr;
@@ -638,7 +641,7 @@ __global__ void __launch_bounds__(kColWarps * 32) m3need_kernel(const Frame* __r
         Lm[i] = (out && !Lc4[i]) ? f.m3val[size_t(yo) * f.wpr + wc] : 0u;
       }
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < kColChunk; ++i) {
         t0 = t1; t1 = t2; t2 = t3; t3 = t4; t4 = t5; t5 = t6; t6 = Lq[i];
         s0 = s1; s1 = s2; s2 = s3; s3 = s4; s4 = s5; s5 = s6; s6 = Lg[i];
         const int yo = rc + i - 3;
@@ -694,10 +697,10 @@ __global__ void __launch_bounds__(kColWarps * 32) d2_kernel(const Frame* __restr
     const uint32_t fmask = inw ? frame_word(wc, f.w) : 0u;
     uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, e0 = 0, e1 = 0, e2 = 0, e3 = 0, e4 = 0;
     unsigned int ents[2] = {0u, 0u}, pix[2] = {0u, 0u};
-    for (int rc = y0 - 2; rc < y0 + kSH + 2; rc += 8) {  // 36 rows: chunks of 8, the last one partly past the end
-      uint32_t L[8], G[8];
+    for (int rc = y0 - 2; rc < y0 + kSH + 2; rc += kColChunk) {  // the last chunk may run past the end
+      uint32_t L[kColChunk], G[kColChunk];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < kColChunk; ++i) {
         const int r = rc + i;
         const bool rin = r >= 0 && r < f.h && r < y0 + kSH + 2;
         const size_t ro = size_t(rin ? r : 0) * f.wpr;
@@ -705,7 +708,7 @@ __global__ void __launch_bounds__(kColWarps * 32) d2_kernel(const Frame* __restr
         G[i] = (rin && hin) ? chg[ro + hw] : 0u;
       }
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < kColChunk; ++i) {
         c0 = c1; c1 = c2; c2 = c3; c3 = c4; c4 = L[i];
         e0 = e1; e1 = e2; e2 = e3; e3 = e4; e4 = G[i];
         const int yo = rc + i - 2;
