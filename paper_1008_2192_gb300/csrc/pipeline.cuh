@@ -1461,62 +1461,47 @@ __global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frame
 // x+5 (rows and columns clamped at the frame's edges, as in the dense pass),
 // then per pixel the minimum of five of them and L+: the dense pass's
 // values. The whole group is rewritten (an unlisted pixel gets the value it
-// holds, its window being unchanged). The warp merges its groups per word and
-// writes them with one AND and one OR per plane and word, so warps sharing a
-// word touch disjoint bits.
+// holds, its window being unchanged). A group's bits belong to it alone during
+// the kernel, so the thread reads the plane words and XORs in only the bits
+// that changed, with no atomic where none did (most re-tests change nothing);
+// XORs of disjoint bits by other groups of the word commute with it.
 __global__ void __launch_bounds__(256) bound_sparse_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
                                                            Params p) {
   float chot, clow;
   bound_consts(p, chot, clow);
-  const int lane = threadIdx.x & 31;
   expand_words<4>(frames, nframes, reinterpret_cast<const uint2*>(Q.q2), Q.n[kNB],
                   [&](bool valid, int fi, int x0, int y, uint32_t) {
-                    uint32_t hb = 0, ab = 0, zb = 0, gm = 0;
-                    unsigned long long key = ~0ull;
-                    if (valid) {
-                      const Frame& f = frames[fi];
-                      const int w = f.w, h = f.h;
-                      float v[5][8];  // rows y-2 .. y+2, columns x0-2 .. x0+5
-                      load_span<2>(f.out_clean, x0, y, w, h, v);
-                      float cm[8];
+                    if (!valid) return;
+                    const Frame& f = frames[fi];
+                    const int w = f.w, h = f.h;
+                    float v[5][8];  // rows y-2 .. y+2, columns x0-2 .. x0+5
+                    load_span<2>(f.out_clean, x0, y, w, h, v);
+                    float cm[8];
 #pragma unroll
-                      for (int c = 0; c < 8; ++c) {
-                        const float col[5] = {v[0][c], v[1][c], v[2][c], v[3][c], v[4][c]};
-                        cm[c] = sel_med5(col);
-                      }
-                      const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
+                    for (int c = 0; c < 8; ++c) {
+                      const float col[5] = {v[0][c], v[1][c], v[2][c], v[3][c], v[4][c]};
+                      cm[c] = sel_med5(col);
+                    }
+                    const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
+                    uint32_t hb = 0, ab = 0, zb = 0;
 #pragma unroll
-                      for (int i = 0; i < 4; ++i) {
-                        const float mlow = min3f(min3f(cm[i], cm[i + 1], cm[i + 2]), cm[i + 3], cm[i + 4]);
-                        const float lp = lplus(v[2][i + 2], v[1][i + 2], v[3][i + 2], v[2][i + 1], v[2][i + 3]);
-                        bool act, hot;
-                        bound_test(lp, mlow, gain, rn2, g2, clow, chot, act, hot);
-                        ab |= uint32_t(act) << i;
-                        hb |= uint32_t(hot) << i;
-                        zb |= uint32_t(lp == 0.f) << i;
-                      }
-                      const int sh = x0 & 31;
-                      gm = (15u << sh) & frame_word(x0 >> 5, w);
-                      ab = (ab << sh) & gm;
-                      hb = (hb << sh) & gm;
-                      zb = (zb << sh) & gm;
-                      key = (static_cast<unsigned long long>(fi) << 40) | (size_t(y) * f.wpr + (x0 >> 5));
+                    for (int i = 0; i < 4; ++i) {
+                      const float mlow = min3f(min3f(cm[i], cm[i + 1], cm[i + 2]), cm[i + 3], cm[i + 4]);
+                      const float lp = lplus(v[2][i + 2], v[1][i + 2], v[3][i + 2], v[2][i + 1], v[2][i + 3]);
+                      bool act, hot;
+                      bound_test(lp, mlow, gain, rn2, g2, clow, chot, act, hot);
+                      ab |= uint32_t(act) << i;
+                      hb |= uint32_t(hot) << i;
+                      zb |= uint32_t(lp == 0.f) << i;
                     }
-                    const unsigned grp = __match_any_sync(0xffffffffu, key);
-                    const uint32_t m = __reduce_or_sync(grp, gm);
-                    const uint32_t hw = __reduce_or_sync(grp, hb);
-                    const uint32_t aw = __reduce_or_sync(grp, ab);
-                    const uint32_t zw = __reduce_or_sync(grp, zb);
-                    if (valid && lane == __ffs(grp) - 1) {
-                      const Frame& f = frames[fi];
-                      const size_t wo = size_t(y) * f.wpr + (x0 >> 5);
-                      atomicAnd(f.hot + wo, ~(m & ~hw));
-                      atomicOr(f.hot + wo, hw);
-                      atomicAnd(f.act + wo, ~(m & ~aw));
-                      atomicOr(f.act + wo, aw);
-                      atomicAnd(f.lpz + wo, ~(m & ~zw));
-                      atomicOr(f.lpz + wo, zw);
-                    }
+                    const int sh = x0 & 31;
+                    const uint32_t gm = (15u << sh) & frame_word(x0 >> 5, w);
+                    const size_t wo = size_t(y) * f.wpr + (x0 >> 5);
+                    const uint32_t dh = (f.hot[wo] ^ (hb << sh)) & gm, da = (f.act[wo] ^ (ab << sh)) & gm,
+                                   dz = (f.lpz[wo] ^ (zb << sh)) & gm;
+                    if (dh) atomicXor(f.hot + wo, dh);
+                    if (da) atomicXor(f.act + wo, da);
+                    if (dz) atomicXor(f.lpz + wo, dz);
                   });
 }
 
