@@ -245,7 +245,7 @@ int init_ctx(crb_ctx* c) {
   {
     const void* fns[kQKernels] = {
         reinterpret_cast<const void*>(crb::bound_dense_kernel),      reinterpret_cast<const void*>(crb::need_kernel),
-        reinterpret_cast<const void*>(crb::s_kernel<crb::kSGroup>), reinterpret_cast<const void*>(crb::sp_kernel<crb::kSGroup>),
+        reinterpret_cast<const void*>(crb::s_kernel),           reinterpret_cast<const void*>(crb::sp_kernel),
         reinterpret_cast<const void*>(crb::m3need_kernel<false>), reinterpret_cast<const void*>(crb::m3_kernel),
         reinterpret_cast<const void*>(crb::cand_test_kernel),   reinterpret_cast<const void*>(crb::rep_compute_kernel),
         reinterpret_cast<const void*>(crb::bound_sparse_kernel),   reinterpret_cast<const void*>(crb::rq_kernel),
@@ -483,10 +483,10 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
           });
       });
       timed(c, kPS, stream, [&] {
-        tq(kQS, [&] { crb::s_kernel<crb::kSGroup><<<gq * P.occ[kQS], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k); });
+        tq(kQS, [&] { crb::s_kernel<<<gq * P.occ[kQS], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k); });
       });
       timed(c, kPSp, stream, [&] {
-        tq(kQSp, [&] { crb::sp_kernel<crb::kSGroup><<<gq * P.occ[kQSp], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p); });
+        tq(kQSp, [&] { crb::sp_kernel<<<gq * P.occ[kQSp], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p); });
       });
       timed(c, kPM3need, stream, [&] {
         if (seg)

@@ -1272,65 +1272,32 @@ __device__ __forceinline__ void load_pair_span(const float* __restrict__ a, int 
   }
 }
 
-// The 5x5 window rows of G adjacent pixels x0 .. x0+G-1 (columns x0-2 ..
-// x0+G+1) and their G medians, from the network over the G+4 sorted columns.
-template <int G>
-__device__ __forceinline__ void group_med25(const float* __restrict__ a, int x0, int y, int w, int h,
-                                            float (&v)[5][G + 4], float (&m)[G]) {
-  static_assert(G == 2 || G == 4, "networks exist for pairs and groups of four");
-  if constexpr (G == 2) {
-    load_pair_span(a, x0, y, w, h, v);
-    med25_row2(v, m);
-  } else {
-    load_span<2>(a, x0, y, w, h, v);
-    med25_row4(v, m);
-  }
-}
-
-// Group width of s_kernel and sp_kernel: 1 takes each listed pixel's 5x5
-// median alone (sel_med25); 2 and 4 take those of the listed pixel's aligned
-// group of G at once from the group's G+4 sorted columns (med25_row2/4), which
-// loads and sorts each column once instead of five times, at the cost of the
-// group's unlisted pixels.
-constexpr int kSGroup = 2;
-
-// s_kernel: at QS, m5 (floored), N, L+ and S of J.
-template <int G>
-__global__ void __launch_bounds__(256, G == 4 ? 3 : 4) s_kernel(const Frame* __restrict__ frames, int nframes,
-                                                                 Queues Q, int k) {
-  if constexpr (G == 1) {
-    expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNS],
-                 [&](bool valid, int fi, int x, int y) {
-                   if (!valid) return;
-                   const Frame& f = frames[fi];
-                   float v[25];
-                   load_window<2>(qsrc(f, k), x, y, f.w, f.h, v);
-                   const float lp = lplus(v[12], v[7], v[17], v[11], v[13]);
-                   const float m5f = floor_m5(sel_med25(v));
-                   const float nn = noise_of(m5f, f.gain, __fmul_rn(f.rn, f.rn));
-                   const size_t o = size_t(y) * f.w + x;
-                   f.mapS[o] = __fdiv_rn(lp, __fmul_rn(2.f, nn));
-                   f.mapN[o] = nn;
-                 });
-  } else {
-    expand_words<G>(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNS],
-                    [&](bool valid, int fi, int x0, int y, uint32_t bits) {
-                      if (!valid) return;
-                      const Frame& f = frames[fi];
-                      float v[5][G + 4], m5[G];
-                      group_med25<G>(qsrc(f, k), x0, y, f.w, f.h, v, m5);
-                      const float rn2 = __fmul_rn(f.rn, f.rn);
-                      const size_t o = size_t(y) * f.w + x0;
+// s_kernel: at QS, m5 (floored), N, L+ and S of J, by aligned pairs of pixels
+// x0, x0+1 that hold a listed one: both 5x5 medians come from one network over
+// the pair's six sorted columns x0-2 .. x0+3 (med25_row2), which loads and
+// sorts each column once instead of five times. A pair's unlisted pixel is
+// computed but not written. (QS is mostly small isolated 5x5 blobs: aligned
+// groups of four would hold 1.9 listed pixels on average, and measured slower
+// than single medians; a run of five listed pixels fills three pairs.)
+__global__ void __launch_bounds__(256, 4) s_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k) {
+  expand_words<2>(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNS],
+                  [&](bool valid, int fi, int x0, int y, uint32_t bits) {
+                    if (!valid) return;
+                    const Frame& f = frames[fi];
+                    float v[5][6], m5[2];
+                    load_pair_span(qsrc(f, k), x0, y, f.w, f.h, v);
+                    med25_row2(v, m5);
+                    const float rn2 = __fmul_rn(f.rn, f.rn);
+                    const size_t o = size_t(y) * f.w + x0;
 #pragma unroll
-                      for (int i = 0; i < G; ++i) {
-                        if (!((bits >> i) & 1u)) continue;
-                        const float lp = lplus(v[2][i + 2], v[1][i + 2], v[3][i + 2], v[2][i + 1], v[2][i + 3]);
-                        const float nn = noise_of(floor_m5(m5[i]), f.gain, rn2);
-                        f.mapS[o + i] = __fdiv_rn(lp, __fmul_rn(2.f, nn));
-                        f.mapN[o + i] = nn;
-                      }
-                    });
-  }
+                    for (int i = 0; i < 2; ++i) {
+                      if (!((bits >> i) & 1u)) continue;
+                      const float lp = lplus(v[2][i + 2], v[1][i + 2], v[3][i + 2], v[2][i + 1], v[2][i + 3]);
+                      const float nn = noise_of(floor_m5(m5[i]), f.gain, rn2);
+                      f.mapS[o + i] = __fdiv_rn(lp, __fmul_rn(2.f, nn));
+                      f.mapN[o + i] = nn;
+                    }
+                  });
 }
 
 // Bits of columns xs .. xs+7 of row qy of a bit plane (bit c = column xs + c),
@@ -1343,83 +1310,47 @@ __device__ __forceinline__ uint32_t plane_bits8(const uint32_t* __restrict__ pla
   return uint32_t(pair >> sh) & 0xffu;
 }
 
-// sp_kernel: at QSP, S' = S - med5(S); S' > sigclip -> test bit. S is exactly
-// 0 where L+ = 0 (the lpz plane), where mapS is not written.
-template <int G>
+// sp_kernel: at QSP, S' = S - med5(S); S' > sigclip -> test bit. By aligned
+// pairs as s_kernel (S is exactly 0 where L+ = 0, the lpz plane, where mapS is
+// not written); the pair's test bits go out with one atomic OR.
 __global__ void __launch_bounds__(256) sp_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p) {
-  if constexpr (G == 1) {
-    expand_words(frames, nframes, reinterpret_cast<const uint2*>(Q.q1), Q.n[kNSP],
-                 [&](bool valid, int fi, int x, int y) {
-                   if (!valid) return;
-                   const Frame& f = frames[fi];
-                   float v[25];
-                   load_window<2>(f.mapS, x, y, f.w, f.h, v);
-                   if (x >= 2 && x < f.w - 2) {
+  expand_words<2>(frames, nframes, reinterpret_cast<const uint2*>(Q.q1), Q.n[kNSP],
+                  [&](bool valid, int fi, int x0, int y, uint32_t bits) {
+                    if (!valid) return;
+                    const Frame& f = frames[fi];
+                    float v[5][6], med[2];
+                    load_pair_span(f.mapS, x0, y, f.w, f.h, v);
+                    if (x0 >= 2 && x0 + 5 < f.w) {
 #pragma unroll
-                     for (int dy = 0; dy < 5; ++dy) {
-                       const uint32_t z = plane_bits5(f.lpz, f.wpr, f.w, x - 2, clampi(y - 2 + dy, 0, f.h - 1));
+                      for (int dy = 0; dy < 5; ++dy) {
+                        const uint32_t z = plane_bits8(f.lpz, f.wpr, x0 - 2, clampi(y - 2 + dy, 0, f.h - 1));
 #pragma unroll
-                       for (int dx = 0; dx < 5; ++dx)
-                         if ((z >> dx) & 1u) v[dy * 5 + dx] = 0.f;
-                     }
-                   } else {
+                        for (int c = 0; c < 6; ++c)
+                          if ((z >> c) & 1u) v[dy][c] = 0.f;
+                      }
+                    } else {
 #pragma unroll
-                     for (int dy = 0; dy < 5; ++dy) {
-                       const size_t ro = size_t(clampi(y - 2 + dy, 0, f.h - 1)) * f.wpr;
+                      for (int dy = 0; dy < 5; ++dy) {
+                        const size_t ro = size_t(clampi(y - 2 + dy, 0, f.h - 1)) * f.wpr;
 #pragma unroll
-                       for (int dx = 0; dx < 5; ++dx) {
-                         const int xx = clampi(x - 2 + dx, 0, f.w - 1);
-                         if ((f.lpz[ro + (xx >> 5)] >> (xx & 31)) & 1u) v[dy * 5 + dx] = 0.f;
-                       }
-                     }
-                   }
-                   const float sp = __fsub_rn(v[12], sel_med25(v));
-                   f.mapSp[size_t(y) * f.w + x] = sp;
-                   if (sp > p.sigclip) atomicOr(&f.test[size_t(y) * f.wpr + (x >> 5)], 1u << (x & 31));
-                 });
-  } else {
-    // the group's test bits go out with one atomic OR
-    expand_words<G>(frames, nframes, reinterpret_cast<const uint2*>(Q.q1), Q.n[kNSP],
-                    [&](bool valid, int fi, int x0, int y, uint32_t bits) {
-                      if (!valid) return;
-                      const Frame& f = frames[fi];
-                      constexpr int C = G + 4;
-                      float v[5][C], med[G];
-                      if constexpr (G == 2) load_pair_span(f.mapS, x0, y, f.w, f.h, v);
-                      else load_span<2>(f.mapS, x0, y, f.w, f.h, v);
-                      if (x0 >= 2 && x0 + 5 < f.w) {
-#pragma unroll
-                        for (int dy = 0; dy < 5; ++dy) {
-                          const uint32_t z = plane_bits8(f.lpz, f.wpr, x0 - 2, clampi(y - 2 + dy, 0, f.h - 1));
-#pragma unroll
-                          for (int c = 0; c < C; ++c)
-                            if ((z >> c) & 1u) v[dy][c] = 0.f;
-                        }
-                      } else {
-#pragma unroll
-                        for (int dy = 0; dy < 5; ++dy) {
-                          const size_t ro = size_t(clampi(y - 2 + dy, 0, f.h - 1)) * f.wpr;
-#pragma unroll
-                          for (int c = 0; c < C; ++c) {
-                            const int xx = clampi(x0 - 2 + c, 0, f.w - 1);
-                            if ((f.lpz[ro + (xx >> 5)] >> (xx & 31)) & 1u) v[dy][c] = 0.f;
-                          }
+                        for (int c = 0; c < 6; ++c) {
+                          const int xx = clampi(x0 - 2 + c, 0, f.w - 1);
+                          if ((f.lpz[ro + (xx >> 5)] >> (xx & 31)) & 1u) v[dy][c] = 0.f;
                         }
                       }
-                      if constexpr (G == 2) med25_row2(v, med);
-                      else med25_row4(v, med);
-                      float* __restrict__ out = f.mapSp + size_t(y) * f.w + x0;
-                      uint32_t tb = 0;
+                    }
+                    med25_row2(v, med);
+                    float* __restrict__ out = f.mapSp + size_t(y) * f.w + x0;
+                    uint32_t tb = 0;
 #pragma unroll
-                      for (int i = 0; i < G; ++i) {
-                        if (!((bits >> i) & 1u)) continue;
-                        const float sp = __fsub_rn(v[2][i + 2], med[i]);
-                        out[i] = sp;
-                        tb |= uint32_t(sp > p.sigclip) << i;
-                      }
-                      if (tb) atomicOr(&f.test[size_t(y) * f.wpr + (x0 >> 5)], tb << (x0 & 31));
-                    });
-  }
+                    for (int i = 0; i < 2; ++i) {
+                      if (!((bits >> i) & 1u)) continue;
+                      const float sp = __fsub_rn(v[2][i + 2], med[i]);
+                      out[i] = sp;
+                      tb |= uint32_t(sp > p.sigclip) << i;
+                    }
+                    if (tb) atomicOr(&f.test[size_t(y) * f.wpr + (x0 >> 5)], tb << (x0 & 31));
+                  });
 }
 
 // m3_kernel: at QM3, med3 of J, by groups of four pixels x0 .. x0+3 that hold
