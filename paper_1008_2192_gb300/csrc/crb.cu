@@ -688,6 +688,7 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
     f.wpr = (s.w + 31) / 32;
     f.gain = s.gain;
     f.rn = s.rn;
+    crb::bound_thresholds(c->p, s.gain, f.bkl, f.bkh);
     f.rtiles_x = (s.w + kRW - 1) / kRW;
     f.rtile0 = rtiles;
     rtiles += (long long)f.rtiles_x * ((s.h + kRH - 1) / kRH);

@@ -68,6 +68,7 @@ struct Frame {
   uint32_t *hot, *act, *nsp, *test;
   uint32_t *sval, *m3val;  // positions whose mapS/mapN, mapM3 hold the current iteration's values
   uint32_t* lpz;           // L+ == 0 (then S == 0 exactly, and no median is needed)
+  float bkl, bkh;          // bound test thresholds over gain^2 (bound_thresholds)
   uint32_t *rq, *fb;       // queued for replacement; known to have a fully flagged window
   uint32_t* chg[2];        // pixels the replacement changed, for even / odd next iterations
   float *mapS, *mapN, *mapSp, *mapM3;
@@ -120,15 +121,21 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v,
 // below FLT_MAX/2 (an add with an operand modifier instead of a min/max
 // instruction); the doubled partial sums round exactly as the plain ones, so
 // 1/8 of their sum equals 1/4 of the sum of the clips in every bit.
-__device__ __forceinline__ float lplus(float c, float up, float down, float left, float right) {
-  const float dn = __fsub_rn(c, up), ds = __fsub_rn(c, down);
-  const float dw = __fsub_rn(c, left), de = __fsub_rn(c, right);
+// L+ from the four differences dn = c - up, ds = c - down, dw = c - left,
+// de = c - right. A difference that is the negation of another (c(i) - c(i+1)
+// = -(c(i+1) - c(i)) exactly) may differ from it only in the sign of a zero,
+// which the clipping t + |t| removes, so callers may share differences
+// between neighbours and get the same value.
+__device__ __forceinline__ float lplus_d(float dn, float ds, float dw, float de) {
   const float t0 = __fadd_rn(dn, dw), t1 = __fadd_rn(dn, de), t2 = __fadd_rn(ds, dw), t3 = __fadd_rn(ds, de);
   float acc = __fadd_rn(t0, fabsf(t0));
   acc = __fadd_rn(acc, __fadd_rn(t1, fabsf(t1)));
   acc = __fadd_rn(acc, __fadd_rn(t2, fabsf(t2)));
   acc = __fadd_rn(acc, __fadd_rn(t3, fabsf(t3)));
   return __fmul_rn(0.125f, acc);
+}
+__device__ __forceinline__ float lplus(float c, float up, float down, float left, float right) {
+  return lplus_d(__fsub_rn(c, up), __fsub_rn(c, down), __fsub_rn(c, left), __fsub_rn(c, right));
 }
 
 // (b) floored 5x5 median -> noise N.

@@ -157,23 +157,28 @@ __device__ __forceinline__ void group_append(uint32_t g, uint32_t* q, unsigned i
 
 __device__ __forceinline__ float clamp_med(float e, float c1, float c2) { return fminf(fmaxf(e, c1), c2); }
 
-// thresholds of the bound test: S+ > sigclip (hot), S+ > min(sigclip, sigfrac*sigclip) (act)
-__device__ __forceinline__ void bound_consts(const Params& p, float& chot, float& clow) {
-  const float sigclip = p.sigclip, tlow = fminf(__fmul_rn(p.sigfrac, p.sigclip), sigclip);
-  chot = 4.f * sigclip * sigclip * 0.9999f;
-  clow = 4.f * tlow * tlow * 0.9999f;
+// Thresholds of the bound test of a frame: S+ = L+ / (2 N-) with N- from the
+// floored lower bound mlow of m5, so S+ > t is L+^2 > 4 t^2 / gain^2 * (gain *
+// max(mlow, 0) + rn^2). kh uses t = sigclip (hot), kl t = min(sigclip,
+// sigfrac*sigclip) (act); the factor 0.9999 keeps the test conservative
+// against the roundings of both sides. Computed once per frame on the host,
+// so the dense pass and the re-test compare against the same values.
+__host__ __device__ inline void bound_thresholds(const Params& p, float gain, float& kl, float& kh) {
+  const float sigclip = p.sigclip, tlow = fminf(p.sigfrac * p.sigclip, sigclip), g2 = gain * gain;
+  kh = 4.f * sigclip * sigclip * 0.9999f / g2;
+  kl = 4.f * tlow * tlow * 0.9999f / g2;
 }
 
 // The two bound tests of one pixel from its L+ and the smallest of its five
 // column medians, with every rounding spelled out: the dense pass and the
 // re-test share it, so a pixel re-tested with an unchanged window keeps its
 // bits exactly.
-__device__ __forceinline__ void bound_test(float lp, float mlow, float gain, float rn2, float g2, float clow,
-                                           float chot, bool& act, bool& hot) {
+__device__ __forceinline__ void bound_test(float lp, float mlow, float gain, float rn2, float kl, float kh, bool& act,
+                                           bool& hot) {
   const float den = __fmaf_rn(gain, mlow > 0.f ? mlow : 0.f, rn2);
-  const float lhs = __fmul_rn(__fmul_rn(lp, lp), g2);
-  act = lhs > __fmul_rn(clow, den);
-  hot = lhs > __fmul_rn(chot, den);
+  const float lhs = __fmul_rn(lp, lp);
+  act = lhs > __fmul_rn(kl, den);
+  hot = lhs > __fmul_rn(kh, den);
 }
 
 // Sliding column-median state of one column: rows r-2 .. r+1 of the current step.
@@ -202,12 +207,12 @@ __device__ __forceinline__ void col_step(Col4& s, float e, float g, float& m0, f
 // pixel whose window did not change keeps its bits.
 template <int NP>
 __device__ __forceinline__ void bound_span(const Frame& f, const float* __restrict__ J, int wc, int y0, int y1,
-                                           float chot, float clow, float* __restrict__ copy) {
+                                           float* __restrict__ copy) {
   static_assert(NP == 4 || NP == 8, "whole 16-byte vectors, whole words per lane group");
   constexpr int kLanesPerWord = 32 / NP;
   const int lane = threadIdx.x & 31;
   const int w = f.w, h = f.h;
-  const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
+  const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), kl = f.bkl, kh = f.bkh;
   const int x0 = wc * 32, xp = x0 + NP * lane;
   int cx[NP];
   uint32_t valid = 0;
@@ -263,6 +268,10 @@ __device__ __forceinline__ void bound_span(const Frame& f, const float* __restri
 #pragma unroll
     for (int i = 0; i < NP; ++i) col_step(A[i], e[i], g[i], m[i][0], m[i][1]);
     col_step(H, eh, gh, mh[0], mh[1]);
+    // vertical differences: the first row's c - down is minus the second row's c - up
+    float vd[NP];  // rows y+1 - y
+#pragma unroll
+    for (int i = 0; i < NP; ++i) vd[i] = __fsub_rn(A[i].d, A[i].c);
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       const int yy = y + s;
@@ -284,13 +293,13 @@ __device__ __forceinline__ void bound_span(const Frame& f, const float* __restri
         c[NP + 2] = hX;
         c[NP + 3] = hY;
       }
-      // the rows of the step: centre, above, below
-      float cc[NP], up[NP], dn[NP];
+      // the row of the step and its differences to the rows above and below
+      float cc[NP], du[NP], dd[NP];
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
         cc[i] = s ? A[i].d : A[i].c;
-        up[i] = s ? A[i].c : A[i].b;
-        dn[i] = s ? e[i] : A[i].d;
+        du[i] = s ? vd[i] : __fsub_rn(A[i].c, A[i].b);
+        dd[i] = s ? __fsub_rn(A[i].d, e[i]) : -vd[i];
       }
       const float hcc = s ? H.d : H.c;
       const float hL = __shfl_sync(0xffffffffu, hcc, src_hl);
@@ -309,13 +318,19 @@ __device__ __forceinline__ void bound_span(const Frame& f, const float* __restri
             if (xp + i < w) o[xp + i] = cc[i];
         }
       }
+      // horizontal differences: pixel i's c - left is dh[i], its c - right is -dh[i + 1]
+      float dh[NP + 1];
+      dh[0] = __fsub_rn(cc[0], lft);
+#pragma unroll
+      for (int i = 1; i < NP; ++i) dh[i] = __fsub_rn(cc[i], cc[i - 1]);
+      dh[NP] = __fsub_rn(rgt, cc[NP - 1]);
       uint32_t va = 0, vh = 0, vz = 0;
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
         const float mlow = min3f(min3f(c[i], c[i + 1], c[i + 2]), c[i + 3], c[i + 4]);
-        const float lp = lplus(cc[i], up[i], dn[i], i == 0 ? lft : cc[i - 1], i == NP - 1 ? rgt : cc[i + 1]);
+        const float lp = lplus_d(du[i], dd[i], dh[i], -dh[i + 1]);
         bool act, hot;
-        bound_test(lp, mlow, gain, rn2, g2, clow, chot, act, hot);
+        bound_test(lp, mlow, gain, rn2, kl, kh, act, hot);
         va |= uint32_t(act) << i;
         vh |= uint32_t(hot) << i;
         vz |= uint32_t(lp == 0.f) << i;
@@ -354,8 +369,6 @@ constexpr int kBoundThreads = 32 * kBW / kBoundNP;
 __global__ void __launch_bounds__(kBoundThreads, kBoundNP == 4 ? 12 : 16)
     bound_dense_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks, Params p) {
   const int warp = threadIdx.x >> 5;
-  float chot, clow;
-  bound_consts(p, chot, clow);
   for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
     const int fi = frame_of_block(frames, nframes, b);
     const Frame& f = frames[fi];
@@ -364,7 +377,7 @@ __global__ void __launch_bounds__(kBoundThreads, kBoundNP == 4 ? 12 : 16)
     const int wc = bxs * kBW + kBoundNP * warp;
     if (wc >= f.wpr) continue;  // whole warp
     const int y0 = bys * kBH;
-    bound_span<kBoundNP>(f, f.img, wc, y0, min(y0 + kBH, f.h), chot, clow, f.out_clean);
+    bound_span<kBoundNP>(f, f.img, wc, y0, min(y0 + kBH, f.h), f.out_clean);
   }
 }
 
@@ -1396,10 +1409,8 @@ __global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frame
 // the kernel, so the thread reads the plane words and XORs in only the bits
 // that changed, with no atomic where none did (most re-tests change nothing);
 // XORs of disjoint bits by other groups of the word commute with it.
-__global__ void __launch_bounds__(256) bound_sparse_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
+__global__ void __launch_bounds__(256, 4) bound_sparse_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
                                                            Params p) {
-  float chot, clow;
-  bound_consts(p, chot, clow);
   expand_words<4>(frames, nframes, reinterpret_cast<const uint2*>(Q.q2), Q.n[kNB],
                   [&](bool valid, int fi, int x0, int y, uint32_t) {
                     if (!valid) return;
@@ -1413,14 +1424,14 @@ __global__ void __launch_bounds__(256) bound_sparse_kernel(const Frame* __restri
                       const float col[5] = {v[0][c], v[1][c], v[2][c], v[3][c], v[4][c]};
                       cm[c] = sel_med5(col);
                     }
-                    const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), g2 = __fmul_rn(f.gain, f.gain);
+                    const float gain = f.gain, rn2 = __fmul_rn(f.rn, f.rn), kl = f.bkl, kh = f.bkh;
                     uint32_t hb = 0, ab = 0, zb = 0;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                       const float mlow = min3f(min3f(cm[i], cm[i + 1], cm[i + 2]), cm[i + 3], cm[i + 4]);
                       const float lp = lplus(v[2][i + 2], v[1][i + 2], v[3][i + 2], v[2][i + 1], v[2][i + 3]);
                       bool act, hot;
-                      bound_test(lp, mlow, gain, rn2, g2, clow, chot, act, hot);
+                      bound_test(lp, mlow, gain, rn2, kl, kh, act, hot);
                       ab |= uint32_t(act) << i;
                       hb |= uint32_t(hot) << i;
                       zb |= uint32_t(lp == 0.f) << i;
