@@ -196,6 +196,16 @@ __device__ __forceinline__ void col_step(Col4& s, float e, float g, float& m0, f
   m1 = clamp_med(g, c1, c2);
 }
 
+// The three values sorted: lo <= mi <= hi.
+__device__ __forceinline__ void sort3(float a, float b, float c, float& lo, float& mi, float& hi) {
+  const float s0 = fminf(a, b), s1 = fmaxf(a, b);
+  hi = fmaxf(s1, c);
+  const float t = fminf(s1, c);
+  lo = fminf(s0, t);
+  mi = fmaxf(s0, t);
+}
+__device__ __forceinline__ float med3f(float a, float b, float c) { return fmaxf(fminf(a, b), fminf(fmaxf(a, b), c)); }
+
 // hot/act/lpz bits of the NP word columns wc .. wc+NP-1 (wc a multiple of NP),
 // rows [y0, y1), of frame f (whole warp), NP pixels per lane (NP = 4 or 8):
 // lane l holds x0+NP*l .. x0+NP*l+NP-1 (16-byte loads per row when the row
@@ -207,7 +217,7 @@ __device__ __forceinline__ void col_step(Col4& s, float e, float g, float& m0, f
 // pixel whose window did not change keeps its bits.
 template <int NP>
 __device__ __forceinline__ void bound_span(const Frame& f, const float* __restrict__ J, int wc, int y0, int y1,
-                                           float* __restrict__ copy) {
+                                           float* __restrict__ copy, float* __restrict__ m3out) {
   static_assert(NP == 4 || NP == 8, "whole 16-byte vectors, whole words per lane group");
   constexpr int kLanesPerWord = 32 / NP;
   const int lane = threadIdx.x & 31;
@@ -225,6 +235,7 @@ __device__ __forceinline__ void bound_span(const Frame& f, const float* __restri
   const int hc = clampi(hx, 0, w - 1);
   const bool vec = ((reinterpret_cast<uintptr_t>(J) & 15u) == 0) && ((w & 3) == 0) && (xp + NP - 1 < w);
   const bool vcopy = vec && ((reinterpret_cast<uintptr_t>(copy) & 15u) == 0);
+  const bool vm3 = vec && ((reinterpret_cast<uintptr_t>(m3out) & 15u) == 0);
   const int src_h0 = lane == 0 ? 0 : 2, src_h1 = lane == 0 ? 1 : 3, src_hl = lane == 0 ? 1 : 2;
   auto ld = [&](int yy, float (&v)[NP], float& vh) {
     const float* r = J + size_t(clampi(yy, 0, h - 1)) * size_t(w);
@@ -318,6 +329,45 @@ __device__ __forceinline__ void bound_span(const Frame& f, const float* __restri
             if (xp + i < w) o[xp + i] = cc[i];
         }
       }
+      if (m3out) {
+        // med3 of the row (as m3_kernel): each column's three rows sorted, then the median of the
+        // largest column minimum, the median of the column medians and the smallest column maximum;
+        // columns x-1 and x+NP from the neighbour lanes, x0-1 and x0+32*NP from the halo lanes 1, 2
+        float lo[NP + 2], mi[NP + 2], hi[NP + 2];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) sort3(s ? A[i].c : A[i].b, cc[i], s ? e[i] : A[i].d, lo[i + 1], mi[i + 1], hi[i + 1]);
+        float tl, tm, th;
+        sort3(s ? H.c : H.b, s ? H.d : H.c, s ? eh : H.d, tl, tm, th);
+        tl = __shfl_sync(0xffffffffu, tl, src_hl);
+        tm = __shfl_sync(0xffffffffu, tm, src_hl);
+        th = __shfl_sync(0xffffffffu, th, src_hl);
+        lo[0] = __shfl_up_sync(0xffffffffu, lo[NP], 1);
+        mi[0] = __shfl_up_sync(0xffffffffu, mi[NP], 1);
+        hi[0] = __shfl_up_sync(0xffffffffu, hi[NP], 1);
+        lo[NP + 1] = __shfl_down_sync(0xffffffffu, lo[1], 1);
+        mi[NP + 1] = __shfl_down_sync(0xffffffffu, mi[1], 1);
+        hi[NP + 1] = __shfl_down_sync(0xffffffffu, hi[1], 1);
+        if (lane == 0) lo[0] = tl, mi[0] = tm, hi[0] = th;
+        if (lane == 31) lo[NP + 1] = tl, mi[NP + 1] = tm, hi[NP + 1] = th;
+        float m3v[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          const float pl = max3f(lo[i], lo[i + 1], lo[i + 2]);
+          const float pm = med3f(mi[i], mi[i + 1], mi[i + 2]);
+          const float ph = min3f(hi[i], hi[i + 1], hi[i + 2]);
+          m3v[i] = med3f(pl, pm, ph);
+        }
+        float* o = m3out + size_t(yy) * w;
+        if (vm3) {
+#pragma unroll
+          for (int q = 0; q < NP / 4; ++q)
+            reinterpret_cast<float4*>(o + xp)[q] = make_float4(m3v[4 * q], m3v[4 * q + 1], m3v[4 * q + 2], m3v[4 * q + 3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < NP; ++i)
+            if (xp + i < w) o[xp + i] = m3v[i];
+        }
+      }
       // horizontal differences: pixel i's c - left is dh[i], its c - right is -dh[i + 1]
       float dh[NP + 1];
       dh[0] = __fsub_rn(cc[0], lft);
@@ -377,7 +427,7 @@ __global__ void __launch_bounds__(kBoundThreads, kBoundNP == 4 ? 12 : 16)
     const int wc = bxs * kBW + kBoundNP * warp;
     if (wc >= f.wpr) continue;  // whole warp
     const int y0 = bys * kBH;
-    bound_span<kBoundNP>(f, f.img, wc, y0, min(y0 + kBH, f.h), f.out_clean);
+    bound_span<kBoundNP>(f, f.img, wc, y0, min(y0 + kBH, f.h), f.out_clean, f.mapM3);
   }
 }
 
@@ -614,11 +664,12 @@ __global__ void __launch_bounds__(kColWarps * 32) need_kernel(const Frame* __res
   }
 }
 
-// m3need_kernel: QT = the test bits of cells of class >= 2 (iteration 1: all),
-// needM3 = dilate3(QT) within the frame -> queue QT, and queue QM3 where M3 is
-// not current (m3val; cleared in cells of class 4); bit plane m3val. Column
-// kernel: rows y0-3 .. y0+kSH+2 feed the seven-row window of QT.
-// kAll (iteration 1): every cell counts as changed and cls is not read.
+// m3need_kernel: QT = the test bits of cells of class >= 2, needM3 = dilate3(QT)
+// within the frame -> queue QT, and queue QM3 where M3 is not current (m3val;
+// cleared in cells of class 4); bit plane m3val. Column kernel: rows y0-3 ..
+// y0+kSH+2 feed the seven-row window of QT. kAll (iteration 1): every cell
+// counts as changed and cls is not read; the dense bound pass has written M3
+// on the whole frame, so QM3 is empty and m3val full.
 template <bool kAll>
 __global__ void __launch_bounds__(kColWarps * 32) m3need_kernel(const Frame* __restrict__ frames, int nframes,
                                                                 long long nunits, Queues Q,
@@ -636,6 +687,28 @@ __global__ void __launch_bounds__(kColWarps * 32) m3need_kernel(const Frame* __r
     const bool hin = (lane == 0 || lane == 31) && hw >= 0 && hw < f.wpr;
     const uint32_t fmask = inw ? frame_word(wc, f.w) : 0u;
     if (cls && !__any_sync(0xffffffffu, strip_has_class2(cls, f, wc, inw, hw, hin, y0, 1))) continue;
+    if constexpr (kAll) {
+      // iteration 1: the dense bound pass wrote M3 everywhere, so M3 is current on the whole frame and
+      // nothing is queued for m3; QT = the test words
+      unsigned int ents[2] = {0u, 0u}, pix[2] = {0u, 0u};
+      uint32_t tq[kSH];
+#pragma unroll
+      for (int t = 0; t < kSH; ++t) tq[t] = (inw && y0 + t < f.h) ? f.test[size_t(y0 + t) * f.wpr + wc] : 0u;
+#pragma unroll
+      for (int t = 0; t < kSH; ++t) {
+        if (inw && y0 + t < f.h) f.m3val[size_t(y0 + t) * f.wpr + wc] = fmask;
+        sw.w[warp][t][0][lane] = 0u;
+        sw.w[warp][t][1][lane] = tq[t];
+        col_count(tq[t], ents[1], pix[1]);
+      }
+      unsigned int base[2];
+      col_reserve(ents, pix, Q.n + kNM3, Q.n + kNT, Q.n + kNM3px, Q.n + kNTpx, base);
+      __syncwarp();
+      col_write(sw, warp, 1, uint32_t(f.word0 + (long long)y0 * f.wpr + wc), f.wpr, base[1],
+                reinterpret_cast<uint2*>(Q.q2));
+      __syncwarp();
+      continue;
+    }
     uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0;  // own QT words, rows r-6 .. r
     uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0, s6 = 0;  // halo QT words
     unsigned int ents[2] = {0u, 0u}, pix[2] = {0u, 0u};
