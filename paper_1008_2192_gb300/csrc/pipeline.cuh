@@ -607,9 +607,10 @@ __global__ void __launch_bounds__(kColWarps * 32) need_kernel(const Frame* __res
         Lgh[i] = (rin && hin) ? f.hot[ro + hw] : 0u;
         Lga[i] = (rin && hin) ? f.act[ro + hw] : 0u;
         const bool out = yo >= y0 && yo < f.h && inw;
+        // the sval and lpz loads do not wait for the class: it masks them afterwards
         Lc[i] = out ? cell_class(cls, f, wc, yo) : 0u;
-        Ls[i] = (out && Lc[i] >= 2u && Lc[i] < 4u) ? f.sval[size_t(yo) * f.wpr + wc] : 0u;
-        Lz[i] = (out && Lc[i] >= 2u) ? f.lpz[size_t(yo) * f.wpr + wc] : 0u;
+        Ls[i] = (out && cls) ? f.sval[size_t(yo) * f.wpr + wc] : 0u;
+        Lz[i] = out ? f.lpz[size_t(yo) * f.wpr + wc] : 0u;
       }
 #pragma unroll
       for (int i = 0; i < kColChunk; ++i) {
@@ -645,8 +646,8 @@ __global__ void __launch_bounds__(kColWarps * 32) need_kernel(const Frame* __res
             f.nsp[o] = qsp;
             f.test[o] = 0u;
           }
-          const uint32_t sv = Ls[i];  // 0 in cells of class 4
-          qs = needS & ~sv & ~Lz[i];  // S = 0 exactly where L+ = 0: no median needed
+          const uint32_t sv = cl >= 4u ? 0u : Ls[i];  // nothing is current in cells of class 4
+          qs = needS & ~sv & ~Lz[i];                  // S = 0 exactly where L+ = 0: no median needed
           if ((sv | needS) != sv || cl >= 4u) f.sval[o] = sv | needS;
         }
         sw.w[warp][yo - y0][0][lane] = qs;
