@@ -4,15 +4,16 @@
 // Detection (stages a-d) of iteration k:
 //   bound          L+ and the upper bound S+ of every pixel -> bit planes hot
 //                  (S+ > sigclip), act (S+ > min(sigclip, sigfrac*sigclip))
-//                  and lpz (L+ = 0, where S = 0 exactly);
+//                  and lpz (L+ = 0, where S = 0 exactly); in iteration 1 (the
+//                  dense pass) also med3 of every pixel -> map M3;
 //   need           nsp = needS' = dilate5(hot) & act, needS = dilate5(nsp)
 //                  -> queues QS (S to compute) and QSP (S' to compute);
 //   s              at QS: m5, N, L+, S -> maps N, S;
 //   sp             at QSP: S' = S - med5(S) -> map S'; S' > sigclip -> bit
 //                  plane test;
 //   m3need         QT = the test bits to (re)test, needM3 = dilate3(QT) ->
-//                  queues QT and QM3;
-//   m3             at QM3: med3 -> map M3;
+//                  queues QT and QM3 (iteration 1: QT only, M3 is whole);
+//   m3             at QM3: med3 -> map M3 (iterations >= 2);
 //   cand_test      at QT: the objlim test from bounds of med7(m3) (smallest
 //                  and largest column median), decided exactly where they
 //                  suffice -> candidates; otherwise -> open tests;
