@@ -1400,8 +1400,9 @@ __device__ __forceinline__ uint32_t plane_bits8(const uint32_t* __restrict__ pla
 
 // sp_kernel: at QSP, S' = S - med5(S); S' > sigclip -> test bit. By aligned
 // pairs as s_kernel (S is exactly 0 where L+ = 0, the lpz plane, where mapS is
-// not written); the pair's test bits go out with one atomic OR.
-__global__ void __launch_bounds__(256) sp_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p) {
+// not written); the pair's test bits go out with one atomic OR. Three blocks
+// per SM (80 registers, 20 B of spills) measured 4 % faster than two (103).
+__global__ void __launch_bounds__(256, 3) sp_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p) {
   expand_words<2>(frames, nframes, reinterpret_cast<const uint2*>(Q.q1), Q.n[kNSP],
                   [&](bool valid, int fi, int x0, int y, uint32_t bits) {
                     if (!valid) return;
