@@ -179,8 +179,8 @@ class Cleaner:
         return [tuple(int(buf[6 * i + j]) for j in range(6)) for i in range(k)]
 
     QUEUE_KERNELS = ("bound", "need", "s", "sprime", "m3need", "m3", "cand_test", "rep_compute", "bound_sparse",
-                     "rq", "rep_write", "d2", "cand_full", "grow", "flagq_mask", "seg_list", "d2_seg", "need_seg",
-                     "m3need_seg", "m3need_first")
+                     "rq", "rep_write", "d2", "cand_full", "grow", "mask", "seg_list", "d2_seg", "need_seg",
+                     "m3need_seg", "m3need_first", "grow_first")
 
     def tuned_config(self):
         """Launch configuration of the last call: ({kernel: blocks per SM}, first segment-list iteration,

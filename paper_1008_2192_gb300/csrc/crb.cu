@@ -91,7 +91,7 @@ constexpr int kDescSlots = 4;
 // queue pipeline kernels, for the occupancy table
 enum QK {
   kQBound, kQNeed, kQS, kQSp, kQM3need, kQM3, kQCand, kQRepCompute, kQBoundSparse, kQRq, kQRepWrite, kQD2,
-  kQCandFull, kQGrow, kQFlagq, kQSegList, kQD2Seg, kQNeedSeg, kQM3needSeg, kQM3needAll, kQKernels
+  kQCandFull, kQGrow, kQMask, kQSegList, kQD2Seg, kQNeedSeg, kQM3needSeg, kQM3needAll, kQGrowFirst, kQKernels
 };
 
 struct GraphKey {
@@ -250,14 +250,15 @@ int init_ctx(crb_ctx* c) {
         reinterpret_cast<const void*>(crb::cand_test_kernel),   reinterpret_cast<const void*>(crb::rep_compute_kernel),
         reinterpret_cast<const void*>(crb::bound_sparse_kernel),   reinterpret_cast<const void*>(crb::rq_kernel),
         reinterpret_cast<const void*>(crb::rep_write_kernel),   reinterpret_cast<const void*>(crb::d2_kernel),
-        reinterpret_cast<const void*>(crb::cand_full_kernel),   reinterpret_cast<const void*>(crb::grow_kernel<true>),
-        reinterpret_cast<const void*>(crb::flagq_kernel),       reinterpret_cast<const void*>(crb::seg_list_kernel),
+        reinterpret_cast<const void*>(crb::cand_full_kernel),   reinterpret_cast<const void*>(crb::grow_kernel),
+        reinterpret_cast<const void*>(crb::mask_kernel),        reinterpret_cast<const void*>(crb::seg_list_kernel),
         reinterpret_cast<const void*>(crb::d2_seg_kernel),      reinterpret_cast<const void*>(crb::need_seg_kernel),
-        reinterpret_cast<const void*>(crb::m3need_seg_kernel),  reinterpret_cast<const void*>(crb::m3need_kernel<true>)};
+        reinterpret_cast<const void*>(crb::m3need_seg_kernel),  reinterpret_cast<const void*>(crb::m3need_kernel<true>),
+        reinterpret_cast<const void*>(crb::grow_first_kernel)};
     for (int i = 0; i < kQKernels; ++i) {
       int o = 0;
       const bool col = i == kQNeed || i == kQM3need || i == kQD2 || i == kQD2Seg || i == kQNeedSeg ||
-                       i == kQM3needSeg || i == kQM3needAll;
+                       i == kQM3needSeg || i == kQM3needAll || i == kQGrowFirst;
       const int threads = i == kQBound ? crb::kBoundThreads : col ? crb::kColWarps * 32 : 256;
       CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[i], threads, 0));
       c->occ_q[i] = o > 0 ? o : 1;
@@ -486,7 +487,7 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
         tq(kQS, [&] { crb::s_kernel<<<gq * P.occ[kQS], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k); });
       });
       timed(c, kPSp, stream, [&] {
-        tq(kQSp, [&] { crb::sp_kernel<<<gq * P.occ[kQSp], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p); });
+        tq(kQSp, [&] { crb::sp_kernel<<<gq * P.occ[kQSp], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k); });
       });
       timed(c, kPM3need, stream, [&] {
         if (seg)
@@ -507,19 +508,21 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
       });
       timed(c, kPCand, stream, [&] {
         tq(kQCand, [&] {
-          crb::cand_test_kernel<<<gq * P.occ[kQCand], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
+          crb::cand_test_kernel<<<gq * P.occ[kQCand], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
         });
         tq(kQCandFull, [&] {
-          crb::cand_full_kernel<<<gq * P.occ[kQCandFull], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p);
+          crb::cand_full_kernel<<<gq * P.occ[kQCandFull], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
         });
       });
       timed(c, kPGrow, stream, [&] {
-        tq(kQGrow, [&] {
-          if (k == 1)
-            crb::grow_kernel<false><<<gq * P.occ[kQGrow], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
-          else
-            crb::grow_kernel<true><<<gq * P.occ[kQGrow], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
-        });
+        if (k == 1)  // both growths from the bit planes; flags counted and queued for the replacement
+          tq(kQGrowFirst, [&] {
+            crb::grow_first_kernel<<<grid(kQGrowFirst, ucol), tcol, 0, stream>>>(c->d_frames, P.n, P.nunits, P.Q);
+          });
+        else
+          tq(kQGrow, [&] {
+            crb::grow_kernel<<<gq * P.occ[kQGrow], 256, 0, stream>>>(c->d_frames, P.n, P.Q, c->p, k);
+          });
       });
       // the classes and changed pixels of iteration k+1 start at zero (those of iteration k-1 were read by now)
       if (k >= 3 && cls_next) {
@@ -527,11 +530,7 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
         CRB_CUDA(cudaMemsetAsync(P.chg[(k + 1) & 1], 0, P.chg_bytes, stream));
       }
       timed(c, kPRep, stream, [&] {
-        if (k == 1)
-          tq(kQFlagq, [&] {
-            crb::flagq_kernel<<<grid(kQFlagq, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks, P.Q);
-          });
-        else
+        if (k >= 2)
           tq(kQRq, [&] { crb::rq_kernel<<<gq * P.occ[kQRq], 256, 0, stream>>>(c->d_frames, P.n, P.Q); });
         tq(kQRepCompute, [&] {
           crb::rep_compute_kernel<<<gq * P.occ[kQRepCompute], 256, 0, stream>>>(c->d_frames, P.n, P.Q, k,
@@ -545,7 +544,7 @@ int enqueue_work(crb_ctx* c, const Plan& P, const std::vector<FrameSpec>& specs,
       });
       if (k == P.niter)
         timed(c, kPMask, stream, [&] {
-          crb::mask_kernel<<<grid(kQFlagq, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks);
+          crb::mask_kernel<<<grid(kQMask, P.nblocks), 256, 0, stream>>>(c->d_frames, P.n, P.nblocks);
         });
       timed(c, kPWork, stream, [&] { crb::queue_work_kernel<<<1, 32, 0, stream>>>(c->d_frames, P.Q, k, P.npix); });
     }
@@ -611,7 +610,7 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
   for (int i = 0; i < n; ++i) {
     const auto& s = specs[size_t(i)];
     off_zero[size_t(i)] = total;
-    total += 3 * align256(size_t(s.w + 31) / 32 * size_t(s.h) * 4);
+    total += 5 * align256(size_t(s.w + 31) / 32 * size_t(s.h) * 4);
   }
   const size_t off_cells = total;
   total += 2 * align256(size_t(ncells) * 4);
@@ -664,6 +663,8 @@ int prepare_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, Pl
     f.bits_a = f.bits_b = reinterpret_cast<uint32_t*>(pz);  // one plane, updated in place
     f.rq = reinterpret_cast<uint32_t*>(pz + plane);
     f.fb = reinterpret_cast<uint32_t*>(pz + 2 * plane);
+    f.cand = reinterpret_cast<uint32_t*>(pz + 3 * plane);
+    f.low = reinterpret_cast<uint32_t*>(pz + 4 * plane);
     f.chg[0] = reinterpret_cast<uint32_t*>(ws + off_chg0 + off_chg[size_t(i)]);
     f.chg[1] = reinterpret_cast<uint32_t*>(ws + off_chg0 + chg_bytes + off_chg[size_t(i)]);
     f.hot = reinterpret_cast<uint32_t*>(pb);
@@ -902,8 +903,8 @@ int upload(crb_ctx* c, const Plan& P, cudaStream_t stream) {
   // the launches of this upload and of enqueue_work for this plan (memsets and copies not counted)
   if (P.niter == 0)
     c->last_launches = 1;
-  else if (P.queue)  // the upload; iteration 1: 12 kernels, later ones 14 (15 with the segment list), the mask
-    c->last_launches = 1 + 12 + 14 * (P.niter - 1) + std::max(0, P.niter - (P.seg_from - 1)) + 1;
+  else if (P.queue)  // the upload; iteration 1: 11 kernels, later ones 14 (15 with the segment list), the mask
+    c->last_launches = 1 + 11 + 14 * (P.niter - 1) + std::max(0, P.niter - (P.seg_from - 1)) + 1;
   else
     c->last_launches = 1 + (P.fuse ? P.niter + 1 : 2 * P.niter) - (P.fuse2 ? 1 : 0) + c->mprev_frames;
   return CRB_OK;

@@ -68,6 +68,7 @@ struct Frame {
   uint32_t *hot, *act, *nsp, *test;
   uint32_t *sval, *m3val;  // positions whose mapS/mapN, mapM3 hold the current iteration's values
   uint32_t* lpz;           // L+ == 0 (then S == 0 exactly, and no median is needed)
+  uint32_t *cand, *low;    // iteration 1: candidates; S' > sigfrac*sigclip (at the nsp pixels)
   float bkl, bkh;          // bound test thresholds over gain^2 (bound_thresholds)
   uint32_t *rq, *fb;       // queued for replacement; known to have a fully flagged window
   uint32_t* chg[2];        // pixels the replacement changed, for even / odd next iterations

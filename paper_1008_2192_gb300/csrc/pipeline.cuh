@@ -1398,11 +1398,14 @@ __device__ __forceinline__ uint32_t plane_bits8(const uint32_t* __restrict__ pla
   return uint32_t(pair >> sh) & 0xffu;
 }
 
-// sp_kernel: at QSP, S' = S - med5(S); S' > sigclip -> test bit. By aligned
+// sp_kernel: at QSP, S' = S - med5(S); S' > sigclip -> test bit (in iteration
+// 1 also S' > sigfrac*sigclip -> low bit, for grow_first_kernel). By aligned
 // pairs as s_kernel (S is exactly 0 where L+ = 0, the lpz plane, where mapS is
-// not written); the pair's test bits go out with one atomic OR. Three blocks
+// not written); the pair's bits go out with one atomic OR per plane. Three blocks
 // per SM (80 registers, 20 B of spills) measured 4 % faster than two (103).
-__global__ void __launch_bounds__(256, 3) sp_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p) {
+__global__ void __launch_bounds__(256, 3) sp_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p,
+                                                    int k) {
+  const float siglow = __fmul_rn(p.sigfrac, p.sigclip);
   expand_words<2>(frames, nframes, reinterpret_cast<const uint2*>(Q.q1), Q.n[kNSP],
                   [&](bool valid, int fi, int x0, int y, uint32_t bits) {
                     if (!valid) return;
@@ -1430,15 +1433,17 @@ __global__ void __launch_bounds__(256, 3) sp_kernel(const Frame* __restrict__ fr
                     }
                     med25_row2(v, med);
                     float* __restrict__ out = f.mapSp + size_t(y) * f.w + x0;
-                    uint32_t tb = 0;
+                    uint32_t tb = 0, lb = 0;
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
                       if (!((bits >> i) & 1u)) continue;
                       const float sp = __fsub_rn(v[2][i + 2], med[i]);
                       out[i] = sp;
                       tb |= uint32_t(sp > p.sigclip) << i;
+                      lb |= uint32_t(sp > siglow) << i;
                     }
                     if (tb) atomicOr(&f.test[size_t(y) * f.wpr + (x0 >> 5)], tb << (x0 & 31));
+                    if (k == 1 && lb) atomicOr(&f.low[size_t(y) * f.wpr + (x0 >> 5)], lb << (x0 & 31));
                   });
 }
 
@@ -1539,7 +1544,7 @@ __device__ __forceinline__ float objlim_stat(const Params& p, float fval, float 
 // med7(m3) from below (above). Tests the bounds decide go to the candidates
 // (pass) or are dropped; the rest to the open tests.
 __global__ void __launch_bounds__(256) cand_test_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
-                                                           Params p) {
+                                                           Params p, int k) {
   __shared__ WarpLists<2, 128> wl;
   wl.init();
   uint32_t* const lists[2] = {Q.q0, Q.q1};
@@ -1569,8 +1574,9 @@ __global__ void __launch_bounds__(256) cand_test_kernel(const Frame* __restrict_
                    const float rhigh = objlim_stat(p, __fsub_rn(mc, hi), nn, sv, spv);  // F at its smallest
                    pass = rlow > p.objlim;
                    open = !pass && rhigh > p.objlim;
+                   if (k == 1 && pass) atomicOr(&f.cand[size_t(y) * f.wpr + (x >> 5)], 1u << (x & 31));
                  }
-                 const bool put[2] = {pass, open};
+                 const bool put[2] = {pass && k != 1, open};  // iteration 1: candidates as bits
                  wl.put(put, g, lists, Q.n + kNPass);
                });
   wl.flush(lists, Q.n + kNPass);
@@ -1579,7 +1585,7 @@ __global__ void __launch_bounds__(256) cand_test_kernel(const Frame* __restrict_
 // cand_full_kernel: at the open tests, the exact F = m3 - med7(m3) and the
 // objlim test -> candidates.
 __global__ void __launch_bounds__(256) cand_full_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
-                                                        Params p) {
+                                                        Params p, int k) {
   __shared__ WarpLists<1, 128> wl;
   wl.init();
   uint32_t* const lists[1] = {Q.q0};
@@ -1598,20 +1604,110 @@ __global__ void __launch_bounds__(256) cand_full_kernel(const Frame* __restrict_
       const size_t o = size_t(g - uint32_t(f.pix0));
       const float fval = __fsub_rn(u[24], sel_med49(u));
       pass = objlim_stat(p, fval, f.mapN[o], f.mapS[o], f.mapSp[o]) > p.objlim;
+      if (k == 1 && pass) atomicOr(&f.cand[size_t(P.y) * f.wpr + (P.x >> 5)], 1u << (P.x & 31));
     }
-    const bool put[1] = {pass};
+    const bool put[1] = {pass && k != 1};  // iteration 1: candidates as bits
     wl.put(put, g, lists, Q.n + kNPass);
   }
   wl.flush(lists, Q.n + kNPass);
 }
 
-// grow_kernel: for each candidate c, the first growth g1 (S' > sigclip in the
-// 3x3 around c) and the second (S' > sigfrac*sigclip in the 3x3 around g1), as
-// bit masks over the 5x5 around c, ORed into the flag bits of M_k; counts the
-// new flags of each frame and, for kFresh, lists them. S' is read only where
-// the bit plane nsp says it is current; elsewhere it cannot pass either
-// threshold.
-template <bool kFresh>
+// grow_first_kernel (iteration 1): both growths as bit-plane algebra,
+// M_1 = dilate3(dilate3(cand) & T) & L, where T (the test plane) holds
+// S' > sigclip and L (low) S' > sigfrac*sigclip, both set by sp_kernel at the
+// nsp pixels (the only pixels whose S' can pass either threshold), and cand
+// the candidates. This is the union of every candidate's growth (the 3x3 of
+// T around it, then the 3x3 of L around those). One warp per strip (lane =
+// word) walks rows y0-2 .. y0+kSH+1; lanes 0 and 31 also form the words beyond
+// the strip. Writes M_1 (no flag exists before), counts it per frame, and
+// queues its pixels for the replacement, all of them being new.
+__global__ void __launch_bounds__(kColWarps * 32) grow_first_kernel(const Frame* __restrict__ frames, int nframes,
+                                                                    long long nunits, Queues Q) {
+  __shared__ ColWords sw;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (long long u = (long long)blockIdx.x * kColWarps + warp; u < nunits; u += (long long)gridDim.x * kColWarps) {
+    const Frame& f = frames[frame_of_unit(frames, nframes, u)];
+    const long long lu = u - f.u0;
+    const int uy = int(lu / f.ugx), ux = int(lu - (long long)uy * f.ugx);
+    const int wc0 = ux * 32, y0 = uy * kSH, wc = wc0 + lane;
+    const bool inw = wc < f.wpr;
+    const int hw = lane == 0 ? wc0 - 1 : wc0 + 32;  // the word beyond the strip (lanes 0 and 31)
+    const bool hin = (lane == 0 || lane == 31) && hw >= 0 && hw < f.wpr;
+    const uint32_t fmask = inw ? frame_word(wc, f.w) : 0u;
+    uint32_t c0 = 0, c1 = 0, c2 = 0, e0 = 0, e1 = 0, e2 = 0;  // cand, rows r-2 .. r (own, beyond)
+    uint32_t tp = 0, etp = 0;                                  // T of row r-1 (own, beyond)
+    uint32_t a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;  // g1, rows r-3 .. r-1 (own, beyond)
+    uint32_t l0 = 0, l1 = 0, l2 = 0;                           // L, rows r-2 .. r (own)
+    unsigned int cnt = 0;
+    for (int r = y0 - 2; r < y0 + kSH + 2; ++r) {
+      const bool rin = r >= 0 && r < f.h;
+      const size_t ro = size_t(rin ? r : 0) * f.wpr;
+      const uint32_t cr = (rin && inw) ? f.cand[ro + wc] : 0u, er = (rin && hin) ? f.cand[ro + hw] : 0u;
+      const uint32_t tr = (rin && inw) ? f.test[ro + wc] : 0u, etr = (rin && hin) ? f.test[ro + hw] : 0u;
+      const uint32_t lr = (rin && inw) ? f.low[ro + wc] : 0u;
+      c0 = c1; c1 = c2; c2 = cr;
+      e0 = e1; e1 = e2; e2 = er;
+      l0 = l1; l1 = l2; l2 = lr;
+      // g1 of row r-1
+      const uint32_t vc = c0 | c1 | c2, evc = e0 | e1 | e2;
+      uint32_t left = __shfl_up_sync(0xffffffffu, vc, 1), right = __shfl_down_sync(0xffffffffu, vc, 1);
+      if (lane == 0) left = evc;
+      if (lane == 31) right = evc;
+      const uint32_t g1 = hdil<1>(left, vc, right) & tp;
+      const uint32_t eg1 = (lane == 0 ? hdil<1>(0u, evc, vc) : hdil<1>(vc, evc, 0u)) & etp;
+      tp = tr;
+      etp = etr;
+      a0 = a1; a1 = a2; a2 = g1;
+      b0 = b1; b1 = b2; b2 = eg1;
+      // M_1 of row r-2
+      const int yo = r - 2;
+      if (yo < y0) continue;  // whole warp
+      const uint32_t vg = a0 | a1 | a2, evg = b0 | b1 | b2;
+      uint32_t gl = __shfl_up_sync(0xffffffffu, vg, 1), gr = __shfl_down_sync(0xffffffffu, vg, 1);
+      if (lane == 0) gl = evg;
+      if (lane == 31) gr = evg;
+      const uint32_t m = (yo < f.h) ? (hdil<1>(gl, vg, gr) & l0 & fmask) : 0u;
+      if (yo < f.h && inw) f.bits_a[size_t(yo) * f.wpr + wc] = m;
+      sw.w[warp][yo - y0][0][lane] = m;
+      cnt += unsigned(__popc(m));
+    }
+    // the strip's flags: one count per frame, then the replacement queue, one atomic per warp
+    unsigned int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned int base = 0;
+    if (lane == 0 && total) {
+      base = atomicAdd(Q.n + kNRep, total);
+      atomicAdd(f.counters + 0, (unsigned long long)total);
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    __syncwarp();
+    unsigned int o = base + incl - cnt;
+    if (inw) {
+      for (int rr = 0; rr < kSH; ++rr) {
+        uint32_t v = sw.w[warp][rr][0][lane];
+        const uint32_t row = uint32_t(f.pix0 + (long long)(y0 + rr) * f.w + 32 * wc);
+        while (v) {
+          const int bb = __ffs(v) - 1;
+          v &= v - 1u;
+          Q.q1[o++] = row + bb;
+        }
+      }
+    }
+    __syncwarp();  // the shared words are refilled for the next strip
+  }
+}
+
+// grow_kernel (iterations 2 on): for each candidate c, the first growth g1
+// (S' > sigclip in the 3x3 around c) and the second (S' > sigfrac*sigclip in
+// the 3x3 around g1), as bit masks over the 5x5 around c, ORed into the flag
+// bits of M_k; counts the new flags of each frame and lists them. S' is read
+// only where the bit plane nsp says it is current; elsewhere it cannot pass
+// either threshold.
 __global__ void __launch_bounds__(256, 4) grow_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p,
                                                    int k) {
   const unsigned int n = Q.n[kNPass];
@@ -1680,17 +1776,7 @@ __global__ void __launch_bounds__(256, 4) grow_kernel(const Frame* __restrict__ 
         mm[r] = sh[r] >= 0 ? (uint64_t(m) << sh[r]) : (uint64_t(m) >> -sh[r]);
         wp[r] = f.bits_a + size_t(clampi(P.y + r - 2, 0, h - 1)) * f.wpr + w0;
       }
-      if (!kFresh) {
-        // iteration 1: no flag exists before, so the new flags are counted from
-        // M_1 afterwards (flagq) and the ORs need no reply
-#pragma unroll
-        for (int r = 0; r < 5; ++r)
-#pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            const uint32_t part = uint32_t(mm[r] >> (32 * j));
-            if (part) atomicOr(wp[r] + j, part);
-          }
-      } else {
+      {
         uint32_t old[5][2];
 #pragma unroll
         for (int r = 0; r < 5; ++r)
@@ -1707,7 +1793,7 @@ __global__ void __launch_bounds__(256, 4) grow_kernel(const Frame* __restrict__ 
         if (fm) atomicAdd(f.counters + 2 * (k - 1), (unsigned long long)__popc(fm));
       }
     }
-    if (kFresh) {  // list the new flags: one atomic per warp
+    {  // list the new flags: one atomic per warp
       const int c = __popc(fm);
       int x = c;
 #pragma unroll
@@ -1734,29 +1820,6 @@ __global__ void __launch_bounds__(256, 4) grow_kernel(const Frame* __restrict__ 
 
 // ---------------------------------------------------------------------------------------------
 // Replacement (stage e).
-
-// flagq_kernel (iteration 1): every flagged pixel -> the replacement queue; all
-// of them are new flags of iteration 1, counted per frame (one atomic per block).
-__global__ void __launch_bounds__(256) flagq_kernel(const Frame* __restrict__ frames, int nframes, long long nblocks,
-                                                    Queues Q) {
-  __shared__ int ws[kThreads / 32 + 1];
-  __shared__ unsigned int bcount;
-  const int t = threadIdx.x;
-  for (long long b = blockIdx.x; b < nblocks; b += gridDim.x) {
-    const int fi = frame_of_block(frames, nframes, b);
-    const Frame& f = frames[fi];
-    const long long lb = b - f.blk0;
-    const int bys = int(lb / f.bx), bxs = int(lb - (long long)bys * f.bx);
-    const int y = bys * kBH + t / kBW, wc = bxs * kBW + t % kBW;
-    const uint32_t v = (y < f.h && wc < f.wpr) ? (f.bits_a[size_t(y) * f.wpr + wc] & frame_word(wc, f.w)) : 0u;
-    if (t == 0) bcount = 0u;
-    __syncthreads();
-    const unsigned int wsum = __reduce_add_sync(0xffffffffu, unsigned(__popc(v)));
-    if ((t & 31) == 0 && wsum) atomicAdd(&bcount, wsum);
-    emit_word(v, f, wc, y, Q.q1, Q.n + kNRep, ws);  // ends with a barrier
-    if (t == 0 && bcount) atomicAdd(f.counters + 0, (unsigned long long)bcount);
-  }
-}
 
 // ORs a 5x5 mask (bit r*5 + dx = column xs + dx of row y0 + r; only in-frame
 // positions set) into a bit plane, one atomic per row and word, and returns the

@@ -275,13 +275,13 @@ def test_graphs_and_autotune(graphs, shape, pipeline):
 
 @pytest.mark.parametrize("niter", [1, 2, 4])
 def test_launch_counts(niter):
-    """crb_last_launches reports the kernels a call enqueues: 1 descriptor upload + 12 + 14 (niter - 1) + 1
+    """crb_last_launches reports the kernels a call enqueues: 1 descriptor upload + 11 + 14 (niter - 1) + 1
     on the queue pipeline, plus the segment list of each iteration from the third on, and 1 upload +
     niter + 1 on the fused tile pipeline."""
     img = scene(120, 90, seed=9)
     cq = Cleaner(niter=niter, pipeline="queue")
     gpu_clean(cq, img)
-    assert cq.last_launches() == 1 + 12 + 14 * (niter - 1) + max(0, niter - 2) + 1
+    assert cq.last_launches() == 1 + 11 + 14 * (niter - 1) + max(0, niter - 2) + 1
     ct = Cleaner(niter=niter, pipeline="tile")
     gpu_clean(ct, img)
     assert ct.last_launches() == 1 + niter + 1
@@ -291,11 +291,11 @@ def test_launch_counts(niter):
 
 
 def test_auto_takes_the_queue_pipeline_for_large_calls():
-    """From 6,000,000 pixels per call the automatic choice is the queue pipeline (58 launches at niter 4)."""
+    """From 6,000,000 pixels per call the automatic choice is the queue pipeline (57 launches at niter 4)."""
     img = synth.frame(2048, 3072, seed=3)
     ca = Cleaner(niter=4)
     out, mask = gpu_clean(ca, img)
-    assert ca.last_launches() == 1 + 12 + 14 * 3 + 2 + 1
+    assert ca.last_launches() == 1 + 11 + 14 * 3 + 2 + 1
     ct = Cleaner(niter=4, pipeline="tile")
     o2, m2 = gpu_clean(ct, img)
     assert np.array_equal(out, o2) and np.array_equal(mask, m2)
