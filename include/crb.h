@@ -360,7 +360,7 @@ int crb_server_poll(crb_server* srv, uint64_t* done_tags, double* latency_s, int
 
 /* Device bytes a w x h frame counts against the server budget: 9 per pixel of
  * the caller's buffers, 36 per pixel of workspace (4 float maps, 5 queue
- * entries), 12 bit planes, 8 bytes per cell of 32 x 8 pixels and 12 per
+ * entries), 14 bit planes, 8 bytes per cell of 32 x 8 pixels and 12 per
  * segment of 32 x 16 pixels (0 for invalid sizes). */
 size_t crb_server_frame_bytes(int w, int h);
 

@@ -90,7 +90,7 @@ namespace {
 size_t frame_bytes(int w, int h) {
   // the caller's input, cleaned output and mask (resident while queued), and the
   // workspace of the queue pipeline: 4 float maps, 5 queue entries per pixel,
-  // 12 bit planes (2 of them changed-pixel planes), 2 words per cell of one
+  // 14 bit planes (2 of them changed-pixel planes), 2 words per cell of one
   // word x 8 rows (the class arrays) and 3 words per segment of one word x 16
   // rows (the segment lists)
   const size_t n = size_t(w) * size_t(h);
@@ -98,7 +98,7 @@ size_t frame_bytes(int w, int h) {
   const size_t plane = wpr * size_t(h) * 4;
   const size_t cells = wpr * ((size_t(h) + 7) / 8);
   const size_t segs = 32 * ((wpr + 31) / 32) * ((size_t(h) + 15) / 16);
-  return n * (4 + 4 + 1) + n * 4 * 4 + n * 5 * 4 + 12 * plane + 2 * 4 * cells + 3 * 4 * segs;
+  return n * (4 + 4 + 1) + n * 4 * 4 + n * 5 * 4 + 14 * plane + 2 * 4 * cells + 3 * 4 * segs;
 }
 
 // Enqueues one wave on slot `slot`. Called by the worker with the server lock
