@@ -1583,13 +1583,15 @@ __global__ void __launch_bounds__(256, 3) cand_test_kernel(const Frame* __restri
                       const Frame& f = frames[fi];
                       const size_t o = size_t(y) * f.w + x0;
                       g = uint32_t(f.pix0 + (long long)o);
+                      // only the statistic's numerator is loaded: 2S (article form) or S'
+                      const bool form1 = p.objlim_form == 1;
                       float nn[2], sv[2], spv[2];
 #pragma unroll
                       for (int i = 0; i < 2; ++i) {
                         const bool on = (bits >> i) & 1u;
                         nn[i] = on ? f.mapN[o + i] : 1.f;
-                        sv[i] = on ? f.mapS[o + i] : 0.f;
-                        spv[i] = on ? f.mapSp[o + i] : 0.f;
+                        sv[i] = (on && form1) ? f.mapS[o + i] : 0.f;
+                        spv[i] = (on && !form1) ? f.mapSp[o + i] : 0.f;
                       }
                       float v[7][8], cm[8];
                       load_pair_span7(f.mapM3, x0, y, f.w, f.h, v);
@@ -1649,7 +1651,8 @@ __global__ void __launch_bounds__(256) cand_full_kernel(const Frame* __restrict_
       load_window<3>(f.mapM3, P.x, P.y, f.w, f.h, u);
       const size_t o = size_t(g - uint32_t(f.pix0));
       const float fval = __fsub_rn(u[24], sel_med49(u));
-      pass = objlim_stat(p, fval, f.mapN[o], f.mapS[o], f.mapSp[o]) > p.objlim;
+      const bool form1 = p.objlim_form == 1;  // only the numerator is loaded: 2S, else S'
+      pass = objlim_stat(p, fval, f.mapN[o], form1 ? f.mapS[o] : 0.f, form1 ? 0.f : f.mapSp[o]) > p.objlim;
       if (k == 1 && pass) atomicOr(&f.cand[size_t(P.y) * f.wpr + (P.x >> 5)], 1u << (P.x & 31));
     }
     const bool put[1] = {pass && k != 1};  // iteration 1: candidates as bits
