@@ -116,6 +116,26 @@ def test_clean_sizes(w, h, niter, path):
     assert np.array_equal(mask, r32.mask) and np.array_equal(out, r32.clean)
 
 
+def test_flags_across_strip_and_word_edges():
+    """Cosmic-ray hits planted on both sides of the edges of 32-px words and of the column kernels'
+    strips (32 words = 1024 px wide, 16 rows high), at the frame's borders and in a ragged last strip
+    in both directions: the queue pipeline is bit-identical to the FP32 oracle at every niter, and
+    the hits are flagged."""
+    w, h = 2080, 50
+    img = scene(w, h, seed=5)
+    rng = np.random.default_rng(11)
+    xs = [0, 1, 31, 32, 1022, 1023, 1024, 1025, 2046, 2047, 2048, 2079]
+    ys = [0, 1, 15, 16, 31, 32, 47, 48, 49]
+    for x in xs:
+        for y in ys:
+            img[y, x] += np.float32(rng.uniform(500.0, 3000.0))
+    for niter in (1, 2, 4):
+        out, mask = gpu_clean(Cleaner(niter=niter, pipeline="queue"), img)
+        r32 = oracle.clean(img, params_of({}), niter, precision="f32")
+        assert mask[np.ix_(ys, xs)].mean() > 0.5
+        assert np.array_equal(mask, r32.mask) and np.array_equal(out, r32.clean), niter
+
+
 def test_niter_zero_copies():
     img = scene(50, 40)
     c = Cleaner(niter=0)
