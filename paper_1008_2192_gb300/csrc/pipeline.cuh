@@ -1247,8 +1247,10 @@ __device__ __forceinline__ uint32_t group_mask(uint32_t m) {
 // waiting on its loads holds back no other. Every lane of the warp runs every
 // round and calls body(valid, frame, x, y) with x the item's first pixel
 // (grouped: body(valid, frame, x, y, bits), bits = the listed pixels of the
-// group, bit i for pixel x + i), so body may hold warp-wide steps.
-template <int kGran = 1, typename F>
+// group, bit i for pixel x + i), so body may hold warp-wide steps. kRev takes
+// the entries from the end of the queue first: a kernel that reads what the
+// previous one wrote last (still in L2) then starts with it.
+template <int kGran = 1, bool kRev = false, typename F>
 __device__ __forceinline__ void expand_words(const Frame* __restrict__ frames, int nframes, const uint2* __restrict__ q,
                                              unsigned int n, F&& body) {
   const int lane = threadIdx.x & 31;
@@ -1257,7 +1259,7 @@ __device__ __forceinline__ void expand_words(const Frame* __restrict__ frames, i
     uint32_t m = 0, pm = 0;
     int fi = 0, y = 0, x0 = 0;
     if (c0 + lane < n) {
-      const uint2 e = q[c0 + lane];
+      const uint2 e = q[kRev ? n - 1u - (c0 + lane) : c0 + lane];
       pm = e.y;
       m = group_mask<kGran>(e.y);
       decode_word(frames, nframes, e.x, fi, y, x0);
@@ -1406,7 +1408,7 @@ __device__ __forceinline__ uint32_t plane_bits8(const uint32_t* __restrict__ pla
 __global__ void __launch_bounds__(256, 3) sp_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, Params p,
                                                     int k) {
   const float siglow = __fmul_rn(p.sigfrac, p.sigclip);
-  expand_words<2>(frames, nframes, reinterpret_cast<const uint2*>(Q.q1), Q.n[kNSP],
+  expand_words<2, true>(frames, nframes, reinterpret_cast<const uint2*>(Q.q1), Q.n[kNSP],
                   [&](bool valid, int fi, int x0, int y, uint32_t bits) {
                     if (!valid) return;
                     const Frame& f = frames[fi];
@@ -1575,7 +1577,7 @@ __global__ void __launch_bounds__(256, 3) cand_test_kernel(const Frame* __restri
   __shared__ WarpLists<2, 128> wl;
   wl.init();
   uint32_t* const lists[2] = {Q.q0, Q.q1};
-  expand_words<2>(frames, nframes, reinterpret_cast<const uint2*>(Q.q2), Q.n[kNT],
+  expand_words<2, true>(frames, nframes, reinterpret_cast<const uint2*>(Q.q2), Q.n[kNT],
                   [&](bool valid, int fi, int x0, int y, uint32_t bits) {
                     bool pass[2] = {false, false}, open[2] = {false, false};
                     uint32_t g = 0;
