@@ -1175,21 +1175,6 @@ __device__ __forceinline__ uint32_t plane_bits5(const uint32_t* __restrict__ pla
   return b;
 }
 
-// Position of the r-th (0-based) set bit of w (r < popc(w)).
-__device__ __forceinline__ int select_bit(uint32_t w, int r) {
-  int p = 0;
-#pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
-    const int c = __popc(w & ((1u << s) - 1u));
-    if (r >= c) {
-      r -= c;
-      w >>= s;
-      p += s;
-    }
-  }
-  return p;
-}
-
 // Frame, row and first column of global word gw (frames sorted by first word).
 __device__ __forceinline__ void decode_word(const Frame* frames, int nframes, uint32_t gw, int& fi, int& y, int& x0) {
   int lo = 0, hi = nframes - 1;
@@ -1241,21 +1226,24 @@ __device__ __forceinline__ uint32_t group_mask(uint32_t m) {
 
 // Expands a queue of n word entries into items of kGran pixels (1: pixels; 4:
 // the groups of four with a listed pixel), one warp at a time: the warp takes
-// 32 entries, scans their item counts across its lanes, then hands one item
-// per lane per round, found by a binary search over the lanes' prefixes and a
-// bit select in the entry's item mask. There is no block barrier, so a warp
-// waiting on its loads holds back no other. Every lane of the warp runs every
-// round and calls body(valid, frame, x, y) with x the item's first pixel
-// (grouped: body(valid, frame, x, y, bits), bits = the listed pixels of the
-// group, bit i for pixel x + i), so body may hold warp-wide steps. kRev takes
-// the entries from the end of the queue first: a kernel that reads what the
-// previous one wrote last (still in L2) then starts with it.
+// 32 entries, each lane writes the items of its entry (entry lane, group
+// index) to the warp's list in shared memory at its exclusive prefix, and the
+// warp then hands one item per lane per round from that list. There is no
+// block barrier, so a warp waiting on its loads holds back no other. Every
+// lane of the warp runs every round and calls body(valid, frame, x, y) with x
+// the item's first pixel (grouped: body(valid, frame, x, y, bits), bits = the
+// listed pixels of the group, bit i for pixel x + i), so body may hold
+// warp-wide steps. kRev takes the entries from the end of the queue first: a
+// kernel that reads what the previous one wrote last (still in L2) then starts
+// with it. Blocks of kThreads threads.
 template <int kGran = 1, bool kRev = false, typename F>
 __device__ __forceinline__ void expand_words(const Frame* __restrict__ frames, int nframes, const uint2* __restrict__ q,
                                              unsigned int n, F&& body) {
-  const int lane = threadIdx.x & 31;
+  constexpr int kPer = 32 / kGran;  // items per entry at most
+  __shared__ uint16_t items[kThreads / 32][32 * kPer];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned int wpb = blockDim.x >> 5;
-  for (unsigned int c0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * 32u; c0 < n; c0 += gridDim.x * wpb * 32u) {
+  for (unsigned int c0 = (blockIdx.x * wpb + warp) * 32u; c0 < n; c0 += gridDim.x * wpb * 32u) {
     uint32_t m = 0, pm = 0;
     int fi = 0, y = 0, x0 = 0;
     if (c0 + lane < n) {
@@ -1264,25 +1252,31 @@ __device__ __forceinline__ void expand_words(const Frame* __restrict__ frames, i
       m = group_mask<kGran>(e.y);
       decode_word(frames, nframes, e.x, fi, y, x0);
     }
-    int incl = __popc(m);  // inclusive prefix of the item counts over the lanes
+    const int cnt = __popc(m);
+    int incl = cnt;  // inclusive prefix of the item counts over the lanes
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int t = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += t;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
+    {
+      int pos = incl - cnt;
+      uint32_t mm = m;
+      while (mm) {
+        const int b = __ffs(mm) - 1;
+        mm &= mm - 1u;
+        items[warp][pos++] = uint16_t((lane << 5) | b);
+      }
+    }
+    __syncwarp();
     for (int r0 = 0; r0 < total; r0 += 32) {
       const int j = r0 + lane;
-      int k = 0;  // first entry whose inclusive prefix exceeds j
-#pragma unroll
-      for (int s = 16; s >= 1; s >>= 1)
-        if (__shfl_sync(0xffffffffu, incl, k + s - 1) <= j) k += s;
       const bool valid = j < total;
-      const uint32_t mk = __shfl_sync(0xffffffffu, m, k);
-      const int ik = __shfl_sync(0xffffffffu, incl, k);
+      const int code = valid ? int(items[warp][j]) : 0;
+      const int k = code >> 5, bit = code & 31;
       const int fk = __shfl_sync(0xffffffffu, fi, k), yk = __shfl_sync(0xffffffffu, y, k);
       const int xk = __shfl_sync(0xffffffffu, x0, k);
-      const int bit = valid ? select_bit(mk, j - (ik - __popc(mk))) : 0;
       if constexpr (kGran == 1) {
         body(valid, fk, xk + bit, yk);
       } else {
@@ -1291,6 +1285,7 @@ __device__ __forceinline__ void expand_words(const Frame* __restrict__ frames, i
         body(valid, fk, xk + kGran * bit, yk, bits);
       }
     }
+    __syncwarp();  // the list is refilled for the next entries
   }
 }
 
