@@ -1365,7 +1365,7 @@ __device__ __forceinline__ void load_pair_span(const float* __restrict__ a, int 
 // groups of four would hold 1.9 listed pixels on average, and measured slower
 // than single medians; a run of five listed pixels fills three pairs.)
 __global__ void __launch_bounds__(256, 4) s_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k) {
-  expand_words<2>(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNS],
+  expand_words<2, true>(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNS],
                   [&](bool valid, int fi, int x0, int y, uint32_t bits) {
                     if (!valid) return;
                     const Frame& f = frames[fi];
@@ -1450,7 +1450,7 @@ __global__ void __launch_bounds__(256, 3) sp_kernel(const Frame* __restrict__ fr
 // largest of its column minima, the median of its column medians and the
 // smallest of its column maxima (an exact selection of the fifth of nine).
 __global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frames, int nframes, Queues Q, int k) {
-  expand_words<4>(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNM3],
+  expand_words<4, true>(frames, nframes, reinterpret_cast<const uint2*>(Q.q0), Q.n[kNM3],
                   [&](bool valid, int fi, int x0, int y, uint32_t bits) {
                     if (!valid) return;
                     const Frame& f = frames[fi];
@@ -1489,7 +1489,7 @@ __global__ void __launch_bounds__(256) m3_kernel(const Frame* __restrict__ frame
 // XORs of disjoint bits by other groups of the word commute with it.
 __global__ void __launch_bounds__(256, 4) bound_sparse_kernel(const Frame* __restrict__ frames, int nframes, Queues Q,
                                                            Params p) {
-  expand_words<4>(frames, nframes, reinterpret_cast<const uint2*>(Q.q2), Q.n[kNB],
+  expand_words<4, true>(frames, nframes, reinterpret_cast<const uint2*>(Q.q2), Q.n[kNB],
                   [&](bool valid, int fi, int x0, int y, uint32_t) {
                     if (!valid) return;
                     const Frame& f = frames[fi];
