@@ -1665,8 +1665,9 @@ __global__ void __launch_bounds__(256) cand_full_kernel(const Frame* __restrict_
 // the candidates. This is the union of every candidate's growth (the 3x3 of
 // T around it, then the 3x3 of L around those). One warp per strip (lane =
 // word) walks rows y0-2 .. y0+kSH+1; lanes 0 and 31 also form the words beyond
-// the strip. Writes M_1 (no flag exists before), counts it per frame, and
-// queues its pixels for the replacement, all of them being new.
+// the strip. Writes M_1 (no flag exists before: the queue pipeline takes no
+// explicit previous mask), counts it per frame, and queues its pixels for the
+// replacement, all of them being new.
 __global__ void __launch_bounds__(kColWarps * 32) grow_first_kernel(const Frame* __restrict__ frames, int nframes,
                                                                     long long nunits, Queues Q) {
   __shared__ ColWords sw;
