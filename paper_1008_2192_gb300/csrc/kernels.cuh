@@ -1031,11 +1031,6 @@ struct ReplaceLayout {
   static constexpr size_t bytes = size_t(oCnt + 16);
 };
 
-// flag of (x, y) in M_k (k = the replacement's iteration; see replace_tile)
-__device__ __forceinline__ bool flag_at(const uint32_t* __restrict__ M, const Frame& f, int x, int y) {
-  return (M[size_t(y) * f.wpr + (x >> 5)] >> (x & 31)) & 1u;
-}
-
 template <int RW, int RH>
 __device__ void replace_tile(const Frame& f, int k, int niter, int dense, long long tile, char* smem) {
   using L = ReplaceLayout<RW, RH>;

@@ -451,25 +451,6 @@ __device__ __forceinline__ uint32_t frame_word(int wc, int w) {
   return lim >= 32 ? 0xffffffffu : (lim <= 0 ? 0u : ((1u << lim) - 1u));
 }
 
-// Appends, for each thread's word `v` at (wc, y) of frame f, the set bits as
-// global pixel indices to queue q (counter *n); one atomic per block.
-__device__ __forceinline__ void emit_word(uint32_t v, const Frame& f, int wc, int y, uint32_t* q, unsigned int* n,
-                                          int* ws) {
-  int total = 0;
-  const int off = block_excl_scan(__popc(v), ws, total);
-  __shared__ unsigned int base;
-  if (threadIdx.x == 0) base = total ? atomicAdd(n, (unsigned int)total) : 0u;
-  __syncthreads();
-  unsigned int o = base + off;
-  const uint32_t row = uint32_t(f.pix0 + (long long)y * f.w + 32 * wc);
-  while (v) {
-    const int bb = __ffs(v) - 1;
-    v &= v - 1u;
-    q[o++] = row + bb;
-  }
-  __syncthreads();
-}
-
 // Appends g to each list j with put[j] (NL <= 3 lists, counters n[0..NL-1]),
 // in thread order; one atomic per block and list. Every thread of the block
 // calls it; ws holds kThreads/32 + 1 ints, sbase NL.
