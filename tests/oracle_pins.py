@@ -11,7 +11,10 @@ What pins what:
                        Laplacian, clip, 2x2 mean) built here; analytic planes
                        and quadratics;
   * replacement (e) -- brute-force sorted lists per flagged pixel;
-  * whole iteration -- the closed form of a hot pixel on a flat sky;
+  * whole iteration -- the closed form of a hot pixel on a flat sky, of a
+                       hot pixel with a weaker neighbour, of a plateau, and of
+                       stripes (the med3 -> med7 chain); strict thresholds at
+                       binary-exact statistics;
                        physics checks (noise-only field, hot pixel, FWHM-2
                        star); invariants (monotone mask, untouched unflagged
                        pixels, transpose/flip equivariance, fixed point);
@@ -276,6 +279,73 @@ def pin_block_closed_form(orc):
     assert np.array_equal(r.Mk.astype(bool), per)
 
 
+def pin_strict_thresholds(orc):
+    """Every threshold comparison is strict: a statistic equal to its threshold does not pass.
+
+    With gain 1, read noise 0 and a flat sky b = 16, N = sqrt(16)/1 = 4 exactly, so the closed
+    forms above give exact binary values. A hot pixel b+A has S' = 2A/(2N) = A/4 and F = 0, so
+    R = S'/0.01: A = 18 puts S' at 4.5 = sigclip, A = 20 puts R at 500 (S' = 5). A hot pixel
+    p = b+400 with its east neighbour q = b+d has S'(q) = d/(2N) = d/8 (the dN, dS, dE terms of
+    L+(q) are d, dW = d-400): d = 36 puts S'(q) at sigclip, d = 18 at sigfrac*sigclip = 2.25.
+    Each case is run at the threshold (the statistic must fail) and at the next float32 below it
+    (it must pass), in both precisions.
+    """
+    b = 16.0
+    below = lambda v: float(np.nextafter(np.float32(v), np.float32(0)))  # noqa: E731
+    p, q = (7, 8), (7, 9)
+    only_p = np.zeros((15, 17), np.uint8)
+    only_p[p] = 1
+    p_and_q = only_p.copy()
+    p_and_q[q] = 1
+    for prec in ("f64", "f32"):
+        def run(A, d, **kw):
+            J = np.full((15, 17), b, np.float32)
+            J[p] = b + A
+            if d:
+                J[q] = b + d
+            return orc.iterate(J, None, Params(gain=1.0, readnoise=0.0, **kw), precision=prec, maps=True)
+        # S' = sigclip at a lone hot pixel: no candidate
+        r = run(18.0, 0.0)
+        assert r.maps["sprime"][p] == 4.5 and r.Mk.sum() == 0 and r.maps["cand"].sum() == 0, prec
+        assert np.array_equal(run(18.0, 0.0, sigclip=below(4.5)).Mk, only_p), prec
+        # R = objlim at a lone hot pixel with S' = 5 > sigclip: no candidate
+        r = run(20.0, 0.0, objlim=500.0)
+        assert r.maps["r"][p] == 500.0 and r.Mk.sum() == 0, prec
+        assert np.array_equal(run(20.0, 0.0, objlim=below(500.0)).Mk, only_p), prec
+        # S'(q) = sigclip next to a candidate: q is outside the first growth
+        r = run(400.0, 36.0)
+        assert r.maps["sprime"][q] == 4.5 and r.maps["cand"][p] == 1, prec
+        assert r.maps["g1"][q] == 0 and r.maps["g1"][p] == 1, prec
+        assert run(400.0, 36.0, sigclip=below(4.5)).maps["g1"][q] == 1, prec
+        # S'(q) = sigfrac*sigclip next to a grown pixel: q is outside M_1
+        r = run(400.0, 18.0)
+        assert r.maps["sprime"][q] == 2.25 and np.array_equal(r.Mk, only_p), prec
+        assert np.array_equal(run(400.0, 18.0, sigfrac=below(0.5)).Mk, p_and_q), prec
+
+
+def pin_fine_structure_stripes(orc):
+    """Vertical stripes J = b + A [x even], no noise: med3 and the med3 -> med7 chain in closed form.
+
+    A 3x3 window centred on an even column holds 3 raised values of 9, one centred on an odd
+    column 6, so med3 inverts the stripes: m3 = b + A [x odd] (columns 1 .. w-2, whose windows
+    reach no clamped column). A 7x7 window of m3 centred on an even column spans four odd columns
+    (28 raised values of 49), one centred on an odd column three (21), so med7(m3) = b + A [x even]
+    and F = m3 - med7(m3) = +A on odd and -A on even columns (columns 4 .. w-5). The 7x7 median of
+    J itself would be b + A [x odd] there, giving F = 0. Rows are identical, so the vertical clamp
+    changes nothing.
+    """
+    b, A = 20.0, 64.0
+    w, h = 23, 12
+    x = np.arange(w)
+    J = np.tile(np.where(x % 2 == 0, b + A, b).astype(np.float32), (h, 1))
+    for prec in ("f64", "f32"):
+        m = orc.iterate(J, None, Params(), precision=prec, maps=True).maps
+        m3 = np.where(x % 2 == 1, b + A, b)
+        assert np.array_equal(m["m3"][:, 1:w - 1], np.tile(m3[1:w - 1], (h, 1))), prec
+        f = np.where(x % 2 == 1, A, -A)
+        assert np.array_equal(m["f"][:, 4:w - 4], np.tile(f[4:w - 4], (h, 1))), prec
+
+
 # ----------------------------------------------------------------------------- physics
 def pin_flat_field_empty(orc):
     """Flat fields. Noiseless: nothing flagged, output identical. Noise-only (Poisson sky 100 e-,
@@ -360,6 +430,7 @@ def pin_invariants(orc):
         r = orc.iterate(J, M, P)
         assert np.all(r.Mk >= M)                                  # monotone flags
         assert np.array_equal(r.Ik[r.Mk == 0], img[r.Mk == 0])     # unflagged pixels keep I0
+        assert r.n_new == int(r.Mk.sum()) - int(M.sum())          # the count of new flags
         J, M = r.Ik, r.Mk
     full = orc.clean(img, P, 4, fragile=True)
     assert np.array_equal(full.mask, M) and np.array_equal(full.clean, J)

@@ -48,6 +48,22 @@ MUTANTS = {
     "replace_window3": ("for (int dy = -2; dy <= 2; ++dy)\n        for (int dx = -2; dx <= 2; ++dx)\n          if (!Mk",
                         "for (int dy = -1; dy <= 1; ++dy)\n        for (int dx = -1; dx <= 1; ++dx)\n          if (!Mk"),
     "m5_floor_missing": ("if (v <= T(0)) v = T(0.0001);\n  Map<T> noise", "if (v < T(-1e30)) v = T(0.0001);\n  Map<T> noise"),
+    "m5_floor_value": ("if (v <= T(0)) v = T(0.0001);", "if (v <= T(0)) v = T(0.01);"),
+    "noise_median_radius": ("Map<T> m5 = median_filter(J, 2);", "Map<T> m5 = median_filter(J, 1);"),
+    "sprime_median_radius": ("Map<T> s_med = median_filter(s, 2);", "Map<T> s_med = median_filter(s, 1);"),
+    "med7_of_image": ("Map<T> m37 = median_filter(m3, 3);", "Map<T> m37 = median_filter(J, 3);"),
+    "f_sign": ("f.v[i] = m3.v[i] - m37.v[i];", "f.v[i] = m37.v[i] - m3.v[i];"),
+    "r_uses_s": ("sp.v[i] / fn;", "s.v[i] / fn;"),
+    "sigfrac_added": ("const T sigcliplow = sigfrac * sigclip;", "const T sigcliplow = sigfrac + sigclip;"),
+    "dilate_radius2": ("for (int dy = -1; dy <= 1; ++dy)\n        for (int dx = -1; dx <= 1; ++dx) any |= in.clamped",
+                       "for (int dy = -2; dy <= 2; ++dy)\n        for (int dx = -2; dx <= 2; ++dx) any |= in.clamped"),
+    # strictness of each of the four threshold comparisons
+    "cand_sigclip_nonstrict": ("(sp.v[i] > sigclip && r.v[i] > objlim)", "(sp.v[i] >= sigclip && r.v[i] > objlim)"),
+    "cand_objlim_nonstrict": ("(sp.v[i] > sigclip && r.v[i] > objlim)", "(sp.v[i] > sigclip && r.v[i] >= objlim)"),
+    "grow1_nonstrict": ("g1.v[i] = (g1.v[i] && sp.v[i] > sigclip)", "g1.v[i] = (g1.v[i] && sp.v[i] >= sigclip)"),
+    "grow2_nonstrict": ("g2.v[i] = (g2.v[i] && sp.v[i] > sigcliplow)", "g2.v[i] = (g2.v[i] && sp.v[i] >= sigcliplow)"),
+    "none_left_keeps_pixel": ("out.v[i] = m5.v[i];\n        ++none_left;", "out.v[i] = J.v[i];\n        ++none_left;"),
+    "new_count_includes_old": ("o.n_new += (g2.v[i] && !prev) ? 1 : 0;", "o.n_new += g2.v[i] ? 1 : 0;"),
     # the fragile map: its tolerance, its cone, and each of its three threshold conditions
     "fragile_tol": ("const double tol = 1e-4;", "const double tol = 10;"),
     "fragile_tol_loose": ("const double tol = 1e-4;", "const double tol = 2e-4;"),
