@@ -347,9 +347,11 @@ crb_server* crb_server_create(float gain, float readnoise, float sigclip, float 
                               const crb_options* opts, size_t budget_bytes, int max_inflight, int max_batch);
 
 /* Queues one frame (device pointers, as crb_clean) with its own gain and read
- * noise under an opaque tag. Returns CRB_OK, CRB_EINVAL, or CRB_EBUSY when
- * admitting it would exceed the budget (poll, then submit again); an earlier
- * device failure of the server is returned as its status. Thread-safe. */
+ * noise under an opaque tag. Returns CRB_OK; CRB_EBUSY when admitting it now
+ * would exceed the budget (poll, then submit again); CRB_EINVAL for invalid
+ * arguments and for a frame whose crb_server_frame_bytes alone exceed the
+ * whole budget (it could never be admitted). An earlier device failure of the
+ * server is returned as its status. Thread-safe. */
 int crb_server_submit(crb_server* srv, const float* img, int w, int h, float gain, float readnoise,
                       float* out_clean, uint8_t* out_mask, uint64_t tag);
 

@@ -264,6 +264,12 @@ int crb_server_submit(crb_server* s, const float* img, int w, int h, float gain,
     return CRB_EINVAL;
   }
   const size_t need = frame_bytes(w, h);
+  if (need > s->budget) {  // could never be admitted: refusing it as busy would have the caller retry forever
+    crb_detail_set_error(("crb_server_submit: a " + std::to_string(w) + "x" + std::to_string(h) + " frame counts " +
+                          std::to_string(need) + " bytes, more than the whole budget of " + std::to_string(s->budget))
+                             .c_str());
+    return CRB_EINVAL;
+  }
   const double t0 = now_s();
   std::lock_guard<std::mutex> lk(s->mu);
   s->max_submit_wait_s = std::max(s->max_submit_wait_s, now_s() - t0);

@@ -68,16 +68,24 @@ def test_budget_admission():
     per_frame = L.load().crb_server_frame_bytes(512, 512)
     assert per_frame >= 512 * 512 * (9 + 32)
     small = Server(niter=2, budget_bytes=per_frame - 1, max_inflight=1, max_batch=4)
-    assert not small.submit(img, o, m, tag=1, gain=7.0, readnoise=5.0)  # would exceed the budget
-    assert small.stats()["rejected"] == 1
+    with pytest.raises(L.CrbError) as e:  # more than the whole budget: never admissible, not busy
+        small.submit(img, o, m, tag=1, gain=7.0, readnoise=5.0)
+    assert e.value.status == L.CRB_EINVAL
+    assert b"more than the whole budget" in L.load().crb_last_error()
+    assert small.stats()["rejected"] == 0 and small.stats()["submitted"] == 0
     small.close()
     one = Server(niter=2, budget_bytes=per_frame, max_inflight=1, max_batch=4)
     assert one.submit(img, o, m, tag=7, gain=7.0, readnoise=5.0)
-    got = []
+    # refused as busy while tag 7 is resident (admitted only if tag 7 already finished)
+    o2, m2 = torch.empty_like(img), torch.empty(img.shape, dtype=torch.uint8, device="cuda")
+    second = one.submit(img, o2, m2, tag=9, gain=7.0, readnoise=5.0)
+    assert one.stats()["rejected"] == (0 if second else 1)
+    want = {7, 9} if second else {7}
+    got = {}
     t0 = time.time()
-    while not got and time.time() - t0 < 30:
-        got = one.poll(block_ms=100)
-    assert got and got[0][0] == 7 and got[0][2] == 0
+    while len(got) < len(want) and time.time() - t0 < 30:
+        got.update({t: st for t, _, st in one.poll(block_ms=100)})
+    assert got == {t: 0 for t in want}
     assert one.stats()["resident_bytes"] == 0
     assert one.submit(img, o, m, tag=8, gain=7.0, readnoise=5.0)  # budget released
     t0 = time.time()
