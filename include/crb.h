@@ -66,6 +66,9 @@ typedef struct {
    * output is identical to running all niter iterations. Default 0.            */
   int early_exit;
   /* Tile shape of the detection kernel (index of crb_tile_shape; default 0).
+   * 0 takes 64 x 32 tiles, or the 64 x 28 tiles of index 5 (one image buffer,
+   * three blocks per SM) when all of a call's tiles then fit in one round of
+   * resident blocks and the 64 x 32 tiles do not (one 800 x 800 frame).
    * -1 = autotune: the first call with a new signature (the list of frame
    * sizes and niter) runs the clean once per compiled shape, timing each on
    * the stream (that call synchronises the stream), and keeps the fastest for

@@ -55,12 +55,29 @@ DetectShape make_detect() {
                      crb::DetectLayout<TW, TH, true>::bytes};
 }
 
+// One image buffer and three resident blocks per SM (at most 80 registers and
+// 75 KB of shared memory each): for calls whose tiles all fit in one round.
+template <int TW, int TH>
+DetectShape make_detect_single() {
+  return DetectShape{TW, TH, crb::detect1_kernel<TW, TH, false, false>, crb::detect1_kernel<TW, TH, true, false>,
+                     crb::detect1_kernel<TW, TH, false, true>,
+                     crb::DetectLayout<TW, TH, false, false>::bytes, crb::DetectLayout<TW, TH, true, false>::bytes};
+}
+
 const std::vector<DetectShape>& detect_shapes() {
   static const std::vector<DetectShape> v = {make_detect<64, 32>(), make_detect<32, 32>(),
                                              make_detect<64, 16>(), make_detect<128, 32>(),
-                                             make_detect<64, 64>()};
+                                             make_detect<64, 64>(), make_detect_single<64, 28>()};
   return v;
 }
+
+// tile_shape 0 takes 64 x 32 tiles, or the single-buffered 64 x 28 tiles when
+// all of those fit in one round of resident blocks and the 64 x 32 tiles do
+// not. A tile's detection is a chain of block-wide phases whose latency, not
+// an issue or memory rate, bounds the launch, so a second round of a few tiles
+// costs nearly a whole tile latency (one 800 x 800 frame: 325 tiles of 64 x 32
+// on 152 SMs x 2 blocks; 377 tiles of 64 x 28 on 152 x 3).
+constexpr int kOneRoundShape = 5;
 
 constexpr int kRW = 64, kRH = 16;  // replacement tile
 const ReplaceFn kReplace = crb::replace_kernel<kRW, kRH>;
@@ -238,6 +255,10 @@ int init_ctx(crb_ctx* c) {
     CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, s.fn, crb::kThreads, s.smem));
     CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occm, s.fn_maps, crb::kThreads, s.smem));
     CRB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occf, s.fn_fused, crb::kThreads, s.smem_fused));
+    if (&s == &detect_shapes()[kOneRoundShape])  // three blocks need the largest shared-memory carveout
+      for (DetectFn fn : {s.fn, s.fn_maps, s.fn_fused})
+        CRB_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      int(cudaSharedmemCarveoutMaxShared)));
     c->occ_detect.push_back(occ > 0 ? occ : 1);
     c->occ_detect_maps.push_back(occm > 0 ? occm : 1);
     c->occ_fused.push_back(occf > 0 ? occf : 1);
@@ -1000,9 +1021,23 @@ int trial_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, cons
 }
 
 // Times one tile-pipeline clean (tile shape 0), synchronising `stream`.
+// The tile shape that tile_shape 0 takes for a call (see kOneRoundShape).
+int default_shape(const crb_ctx* c, const std::vector<FrameSpec>& specs) {
+  const auto& v = detect_shapes();
+  auto tiles = [&](const DetectShape& d) {
+    long long t = 0;
+    for (const auto& s : specs) t += (long long)((s.w + d.tw - 1) / d.tw) * ((s.h + d.th - 1) / d.th);
+    return t;
+  };
+  auto slots = [&](int i) {
+    return (long long)c->num_sms * std::min(c->occ_detect[size_t(i)], c->occ_fused[size_t(i)]);
+  };
+  return (tiles(v[kOneRoundShape]) <= slots(kOneRoundShape) && tiles(v[0]) > slots(0)) ? kOneRoundShape : 0;
+}
+
 int trial_tile(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, cudaStream_t stream, float* ms) {
   Plan P;
-  int rc = prepare(c, specs, niter, false, 0, P);
+  int rc = prepare(c, specs, niter, false, c->opt.tile_shape == 0 ? default_shape(c, specs) : 0, P);
   if (rc == CRB_OK) rc = upload(c, P, stream);
   if (rc) return rc;
   cudaEvent_t a = take_event(c), b = take_event(c);
@@ -1156,6 +1191,7 @@ int run(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, bool maps, c
     }
   }
   if (shape < 0) shape = 0;
+  if (shape == 0 && c->opt.tile_shape == 0 && !maps && !queue) shape = default_shape(c, specs);
   Plan P;
   int rc = queue ? prepare_queue(c, specs, niter, P) : prepare(c, specs, niter, maps, shape, P);
   if (rc) return rc;

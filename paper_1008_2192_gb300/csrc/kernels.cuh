@@ -430,10 +430,10 @@ __device__ __forceinline__ bool tile_by_tma(const Frame& f, int x0, int y0) {
 // frame (thread 0, completion on the buffer's mbarrier), else 4-byte copies of
 // clamped positions by every thread. Returns whether the box was used.
 // `acquired`: the tensor map thread 0 last made visible to its TMA loads.
-template <int TW, int TH, bool kFused>
+template <int TW, int TH, bool kFused, bool kDouble = true>
 __device__ __forceinline__ bool issue_tile_load(const Frame* __restrict__ frames, int nframes, long long t, int k,
                                                 int niter, char* smem, int b, const CUtensorMap*& acquired) {
-  using L = DetectLayout<TW, TH, kFused>;
+  using L = DetectLayout<TW, TH, kFused, kDouble>;
   const int fi = frame_of<false>(frames, nframes, t);
   const Frame& f = frames[fi];
   const long long tile = t - f.tile0;
@@ -862,11 +862,15 @@ __device__ void detect_tile(const Frame& f, const Params& p, int k, int niter, i
   if ((tid & 31) == 0 && new_flags) atomicAdd(f.counters + 2 * (k - 1), (unsigned long long)new_flags);
 }
 
-template <int TW, int TH, bool kMaps, bool kFused = false>
-__global__ void __launch_bounds__(kThreads) detect_kernel(const Frame* __restrict__ frames, int nframes,
-                                                          long long ntiles, Params p, int k, int niter) {
+// The tiles of a detection launch, block-strided. kDouble: two image
+// buffers, the next tile's region loading while this tile is computed; else
+// one buffer, loaded after the tile (for launches in which a block has about
+// one tile, at three resident blocks per SM: detect1_kernel).
+template <int TW, int TH, bool kMaps, bool kFused, bool kDouble>
+__device__ __forceinline__ void detect_tiles(const Frame* __restrict__ frames, int nframes, long long ntiles,
+                                             Params p, int k, int niter) {
   extern __shared__ __align__(128) char smem[];
-  using L = DetectLayout<TW, TH, kFused>;
+  using L = DetectLayout<TW, TH, kFused, kDouble>;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::oBar);
   int* ok = reinterpret_cast<int*>(smem + L::oBar + 16);
   if (threadIdx.x == 0) {
@@ -878,9 +882,9 @@ __global__ void __launch_bounds__(kThreads) detect_kernel(const Frame* __restric
   unsigned phase = 0;  // thread 0: parity of the next completion of each buffer's barrier (bit b)
   const CUtensorMap* acquired = nullptr;
   long long t = blockIdx.x;
-  bool tma = t < ntiles && issue_tile_load<TW, TH, kFused>(frames, nframes, t, k, niter, smem, 0, acquired);
+  bool tma = t < ntiles && issue_tile_load<TW, TH, kFused, kDouble>(frames, nframes, t, k, niter, smem, 0, acquired);
   for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
-    const int b = it & 1;
+    const int b = kDouble ? (it & 1) : 0;
     cp_async_wait_all();
     if (threadIdx.x == 0) {
       bool landed = true;
@@ -897,16 +901,35 @@ __global__ void __launch_bounds__(kThreads) detect_kernel(const Frame* __restric
     __syncthreads();  // tile t's image region has landed in buffer b
     if (!*ok) return;  // every thread of the block leaves together; the status reports it
     const long long tn = t + gridDim.x;
-    const bool tma_next =
-        tn < ntiles && issue_tile_load<TW, TH, kFused>(frames, nframes, tn, k, niter, smem, b ^ 1, acquired);
+    bool tma_next = false;
+    if (kDouble)
+      tma_next = tn < ntiles && issue_tile_load<TW, TH, kFused, kDouble>(frames, nframes, tn, k, niter, smem, b ^ 1,
+                                                                         acquired);
     const int fi = frame_of<false>(frames, nframes, t);
     const Frame f = frames[fi];
     const long long tile = t - f.tile0;
     const int ty = int(tile / f.tiles_x), tx = int(tile - (long long)ty * f.tiles_x);
-    detect_tile<TW, TH, kMaps, kFused>(f, p, k, niter, tx * TW, ty * TH, smem, b);
+    detect_tile<TW, TH, kMaps, kFused, kPassTile, kDouble>(f, p, k, niter, tx * TW, ty * TH, smem, b);
+    __syncthreads();  // the block is done with buffer b
+    if (!kDouble)
+      tma_next = tn < ntiles && issue_tile_load<TW, TH, kFused, kDouble>(frames, nframes, tn, k, niter, smem, 0,
+                                                                         acquired);
     tma = tma_next;
-    __syncthreads();
   }
+}
+
+template <int TW, int TH, bool kMaps, bool kFused = false>
+__global__ void __launch_bounds__(kThreads) detect_kernel(const Frame* __restrict__ frames, int nframes,
+                                                          long long ntiles, Params p, int k, int niter) {
+  detect_tiles<TW, TH, kMaps, kFused, true>(frames, nframes, ntiles, p, k, niter);
+}
+
+// One image buffer, at most 80 registers: three blocks per SM where the
+// shared memory of a block is at most 75 KB (64 x 28 tiles).
+template <int TW, int TH, bool kMaps, bool kFused = false>
+__global__ void __launch_bounds__(kThreads, 3) detect1_kernel(const Frame* __restrict__ frames, int nframes,
+                                                              long long ntiles, Params p, int k, int niter) {
+  detect_tiles<TW, TH, kMaps, kFused, false>(frames, nframes, ntiles, p, k, niter);
 }
 
 // --------------------------------------------------------------------------------------------

@@ -157,7 +157,7 @@ def test_parameters_and_objlim_forms(form, pset, pipeline):
 
 
 @pytest.mark.parametrize("fusion", [True, False], ids=["fused", "two-launch"])
-@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5])
 def test_tile_shapes_agree(shape, fusion):
     img = scene(300, 230, seed=11)
     ref = oracle.clean(img, params_of({}), 4, precision="f32")
