@@ -1020,7 +1020,6 @@ int trial_queue(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, cons
   return CRB_OK;
 }
 
-// Times one tile-pipeline clean (tile shape 0), synchronising `stream`.
 // The tile shape that tile_shape 0 takes for a call (see kOneRoundShape).
 int default_shape(const crb_ctx* c, const std::vector<FrameSpec>& specs) {
   const auto& v = detect_shapes();
@@ -1035,6 +1034,8 @@ int default_shape(const crb_ctx* c, const std::vector<FrameSpec>& specs) {
   return (tiles(v[kOneRoundShape]) <= slots(kOneRoundShape) && tiles(v[0]) > slots(0)) ? kOneRoundShape : 0;
 }
 
+// Times one tile-pipeline clean (with the shape tile_shape 0 takes when that is
+// the option, else 64 x 32), synchronising `stream`.
 int trial_tile(crb_ctx* c, const std::vector<FrameSpec>& specs, int niter, cudaStream_t stream, float* ms) {
   Plan P;
   int rc = prepare(c, specs, niter, false, c->opt.tile_shape == 0 ? default_shape(c, specs) : 0, P);
