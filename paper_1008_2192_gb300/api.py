@@ -29,6 +29,21 @@ def _check_img(t, name="img"):
         raise ValueError(f"{name} must be a contiguous 2-D float32 CUDA tensor")
 
 
+def _check_out(t, like, dtype, name):
+    """An output the library writes w*h elements into: a contiguous CUDA tensor of `dtype` with the
+    shape of `like` on its device (the C ABI cannot see a device buffer's size)."""
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()
+            and t.shape == like.shape and t.device == like.device):
+        raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor of shape {tuple(like.shape)} "
+                         f"on {like.device}")
+
+
+def _check_lengths(n, **arrays):
+    for name, a in arrays.items():
+        if a is not None and len(a) != n:
+            raise ValueError(f"{name} has {len(a)} entries for {n} frames")
+
+
 # crb_options.pipeline: "auto" picks by the pixels of each call (queue from 6 Mpix on)
 PIPELINES = {"auto": 0, "tile": 1, "queue": 2}
 
@@ -67,6 +82,8 @@ class Cleaner:
 
     def clean_into(self, img, out_clean, out_mask, stream=None):
         _check_img(img)
+        _check_out(out_clean, img, torch.float32, "out_clean")
+        _check_out(out_mask, img, torch.uint8, "out_mask")
         h, w = img.shape
         rc = _lib.load().crb_clean(self._h, _ptr(img), w, h, _ptr(out_clean), _ptr(out_mask), _stream(stream))
         check(rc, "crb_clean")
@@ -81,8 +98,11 @@ class Cleaner:
 
     def clean_batch_into(self, imgs, outs, masks, gains=None, readnoises=None, stream=None):
         n = len(imgs)
-        for t in imgs:
+        _check_lengths(n, outs=outs, masks=masks, gains=gains, readnoises=readnoises)
+        for t, o, m in zip(imgs, outs, masks):
             _check_img(t)
+            _check_out(o, t, torch.float32, "each out")
+            _check_out(m, t, torch.uint8, "each mask")
         P = ctypes.c_void_p * n
         I = ctypes.c_int * n
         F = ctypes.c_float * n
@@ -100,12 +120,14 @@ class Cleaner:
         """crb_clean_batch_host: frames, outputs and masks are CPU tensors (pinned memory lets the copies
         overlap the work); the outputs are valid once `stream` (default: the current stream) is synchronised."""
         n = len(imgs)
+        _check_lengths(n, outs=outs, masks=masks, gains=gains, readnoises=readnoises)
         for t, o, m in zip(imgs, outs, masks):
             if t.device.type != "cpu" or o.device.type != "cpu" or m.device.type != "cpu":
                 raise ValueError("clean_batch_host_into takes CPU tensors")
             if t.dtype != torch.float32 or o.dtype != torch.float32 or m.dtype != torch.uint8:
                 raise ValueError("frames and outputs float32, masks uint8")
-            if t.dim() != 2 or not t.is_contiguous() or o.shape != t.shape or m.shape != t.shape:
+            if (t.dim() != 2 or not t.is_contiguous() or not o.is_contiguous() or not m.is_contiguous()
+                or o.shape != t.shape or m.shape != t.shape):
                 raise ValueError("contiguous 2-D frames with outputs of the same shape")
         P = ctypes.c_void_p * n
         I = ctypes.c_int * n
@@ -126,6 +148,8 @@ class Cleaner:
         written into out_clean / out_mask."""
         from .partition import to_c
         _check_img(img)
+        _check_out(out_clean, img, torch.float32, "out_clean")
+        _check_out(out_mask, img, torch.uint8, "out_mask")
         h, w = img.shape
         arr = to_c(rects)
         rc = _lib.load().crb_clean_rects(self._h, _ptr(img), w, h, len(rects), arr, _ptr(out_clean),
@@ -148,6 +172,8 @@ class Cleaner:
     def iterate(self, J, Mprev=None, maps=False, stream=None):
         """One iteration from (J, Mprev). Returns (I_k, M_k, maps dict or None)."""
         _check_img(J, "J")
+        if Mprev is not None:
+            _check_out(Mprev, J, torch.uint8, "Mprev")
         h, w = J.shape
         outJ = torch.empty_like(J)
         outM = torch.empty(J.shape, dtype=torch.uint8, device=J.device)
@@ -286,6 +312,8 @@ class Server:
     def submit(self, img, out, mask, tag, gain, readnoise):
         """Queues a frame; returns False when the memory budget refuses it (CRB_EBUSY)."""
         _check_img(img)
+        _check_out(out, img, torch.float32, "out")
+        _check_out(mask, img, torch.uint8, "mask")
         h, w = img.shape
         rc = _lib.load().crb_server_submit(self._h, _ptr(img), w, h, float(gain), float(readnoise), _ptr(out),
                                            _ptr(mask), int(tag))

@@ -111,3 +111,18 @@ def test_server_rejects_invalid_arguments():
     assert not lib.crb_server_create(7.0, 5.0, 4.5, 0.5, 1.0, 4, None, 0, 2, 8)
     assert lib.crb_server_submit(None, None, 1, 1, 7.0, 5.0, None, None, 0) == L.CRB_EINVAL
     assert lib.crb_server_poll(None, None, None, None, 0, 0) == -1
+
+
+def test_binding_checks_outputs_before_the_call():
+    """The C ABI cannot see how large a device buffer is, so the torch binding checks every output it
+    passes (a contiguous CUDA tensor of the right dtype, shape and device) and the lengths of the
+    per-frame arrays, raising before any library call."""
+    torch = pytest.importorskip("torch")
+    from paper_1008_2192_gb300 import api
+    like = torch.zeros((3, 4))
+    for bad in (torch.zeros((3, 4)), torch.zeros((4, 3)), torch.zeros((3, 4), dtype=torch.uint8), None):
+        with pytest.raises(ValueError):
+            api._check_out(bad, like, torch.float32, "out")  # host tensors are never valid outputs
+    api._check_lengths(2, outs=[1, 2], masks=(3, 4), gains=None)
+    with pytest.raises(ValueError, match="gains has 1 entries for 2 frames"):
+        api._check_lengths(2, outs=[1, 2], gains=[7.0])
