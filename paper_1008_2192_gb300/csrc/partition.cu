@@ -56,6 +56,7 @@ extern "C" int crb_partition(int w, int h, int nparts, int cols, int context, cr
       return -CRB_EINVAL;
     }
   }
+  if (context > w || context > h) context = w > h ? w : h;  // no wider than the frame (and no overflow below)
   const int best_r = nparts / best_c;
   if (out_cols) *out_cols = best_c;
   if (out_rows) *out_rows = best_r;

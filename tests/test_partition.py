@@ -60,7 +60,7 @@ def test_paper_two_by_four_and_primes():
 
 
 @pytest.mark.parametrize("w,h,n,ctx", [(1, 1, 1, 0), (17, 5, 4, 3), (100, 77, 6, 16), (64, 640, 8, 32),
-                                       (333, 129, 12, 8), (5, 40, 8, 2)])
+                                       (333, 129, 12, 8), (5, 40, 8, 2), (100, 77, 6, 2**31 - 1)])
 def test_rectangles_tile_the_frame(w, h, n, ctx):
     """Interiors tile the frame exactly once; contexts are the interiors widened by ctx, clipped."""
     cols, rows, rects = partition.plan(w, h, n, ctx)
