@@ -1476,9 +1476,10 @@ int crb_clean_rects(crb_ctx* c, const float* img, int w, int h, int n, const crb
   size_t need = 0;
   for (int i = 0; i < n; ++i) {
     const crb_rect& r = rects[i];
+    using ll = long long;  // sums of caller-given ints: no overflow can pass the checks
     const bool ok = r.w >= 1 && r.h >= 1 && r.cx0 >= 0 && r.cy0 >= 0 && r.cx0 <= r.x0 && r.cy0 <= r.y0 &&
-                    r.x0 + r.w <= r.cx0 + r.cw && r.y0 + r.h <= r.cy0 + r.ch && r.cx0 + r.cw <= w &&
-                    r.cy0 + r.ch <= h;
+                    ll(r.x0) + r.w <= ll(r.cx0) + r.cw && ll(r.y0) + r.h <= ll(r.cy0) + r.ch &&
+                    ll(r.cx0) + r.cw <= w && ll(r.cy0) + r.ch <= h;
     if (!ok)
       return fail(CRB_EINVAL, "crb_clean_rects: rectangle " + std::to_string(i) +
                                   ": the context region must contain the interior and lie in the frame");
