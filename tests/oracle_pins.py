@@ -515,7 +515,8 @@ def pin_fragile_closed_form(orc):
     S' = 9 > sigclip, R = objlim (1 + d) by setting objlim = 900 (1 + d). A statistic within 1e-4
     (relative) of its threshold marks the clamped 5x5 box around it, so the fragile map is
     exactly that box for |d| = 5e-5 (either side) and empty for |d| = 1.5e-4. The corner position
-    of p checks the clamp of the box.
+    of p checks the clamp of the box. R near objlim marks nothing where S' is clearly below sigclip
+    (S' = 3 or 1), since no candidate can form there.
     """
     b = 20.0
     N = math.sqrt(7.0 * b + 25.0) / 7.0
@@ -533,6 +534,14 @@ def pin_fragile_closed_form(orc):
                 assert abs(got_sp / s_target - 1) < 1e-6, (name, got_sp, s_target)
                 exp = _cone(shape, py, px) if inside else np.zeros(shape, np.uint8)
                 assert np.array_equal(r.fragile, exp), (name, d, (py, px), int(r.fragile.sum()))
+    # R within the tolerance of objlim where S' is clearly below sigclip (between the two growth
+    # thresholds, or below both) decides nothing: no pixel is fragile
+    for s_target in (3.0, 1.0):
+        J = np.full(shape, b, np.float32)
+        J[7, 8] = np.float32(b + s_target * N)
+        r = orc.iterate(J, None, Params(objlim=100.0 * s_target * (1 + 5e-5)), maps=True, fragile=True)
+        assert abs(r.maps["r"][7, 8] / (100.0 * s_target) - 1) < 1e-6
+        assert r.fragile.sum() == 0 and r.Mk.sum() == 0, s_target
     # the end-to-end fragile map is the union over the iterations
     J = np.full(shape, b, np.float32)
     J[7, 8] = np.float32(b + 4.5 * (1 + 5e-5) * N)

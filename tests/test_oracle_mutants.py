@@ -64,6 +64,8 @@ MUTANTS = {
     "grow2_nonstrict": ("g2.v[i] = (g2.v[i] && sp.v[i] > sigcliplow)", "g2.v[i] = (g2.v[i] && sp.v[i] >= sigcliplow)"),
     "none_left_keeps_pixel": ("out.v[i] = m5.v[i];\n        ++none_left;", "out.v[i] = J.v[i];\n        ++none_left;"),
     "new_count_includes_old": ("o.n_new += (g2.v[i] && !prev) ? 1 : 0;", "o.n_new += g2.v[i] ? 1 : 0;"),
+    "clean_forgets_flags": ("iterate<T>(J.data(), M.data(), w, h, *p, o, false, fragile_any != nullptr);",
+                            "iterate<T>(J.data(), nullptr, w, h, *p, o, false, fragile_any != nullptr);"),
     # the fragile map: its tolerance, its cone, and each of its three threshold conditions
     "fragile_tol": ("const double tol = 1e-4;", "const double tol = 10;"),
     "fragile_tol_loose": ("const double tol = 1e-4;", "const double tol = 2e-4;"),
@@ -75,6 +77,11 @@ MUTANTS = {
     "fragile_no_sigfrac": ("const bool b = std::fabs(spv - c2) <= tol * c2;", "const bool b = false;"),
     "fragile_no_objlim": ("const bool d = spv > c * (1.0 - tol) && std::fabs(rv - ol) <= tol * ol;",
                           "const bool d = false;"),
+    "fragile_objlim_ungated": ("const bool d = spv > c * (1.0 - tol) && std::fabs(rv - ol) <= tol * ol;",
+                               "const bool d = std::fabs(rv - ol) <= tol * ol;"),
+    "fragile_objlim_gated_low": ("const bool d = spv > c * (1.0 - tol) && std::fabs(rv - ol) <= tol * ol;",
+                                 "const bool d = spv > c2 * (1.0 - tol) && std::fabs(rv - ol) <= tol * ol;"),
+    "fragile_union_last": ("fragile_any[i] |= o.fragile[i];", "fragile_any[i] = o.fragile[i];"),
 }
 
 
