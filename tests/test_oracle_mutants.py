@@ -64,6 +64,17 @@ MUTANTS = {
     "grow2_nonstrict": ("g2.v[i] = (g2.v[i] && sp.v[i] > sigcliplow)", "g2.v[i] = (g2.v[i] && sp.v[i] >= sigcliplow)"),
     "none_left_keeps_pixel": ("out.v[i] = m5.v[i];\n        ++none_left;", "out.v[i] = J.v[i];\n        ++none_left;"),
     "new_count_includes_old": ("o.n_new += (g2.v[i] && !prev) ? 1 : 0;", "o.n_new += g2.v[i] ? 1 : 0;"),
+    "clamp_y_to_width": ("y = std::min(std::max(y, 0), h - 1);", "y = std::min(std::max(y, 0), w - 1);"),
+    "f_floor_unnormalised": ("std::max(f.v[i] / noise.v[i], T(0.01));", "std::max(f.v[i], T(0.01));"),
+    "dilate_without_centre": ("for (int dx = -1; dx <= 1; ++dx) any |= in.clamped(x + dx, y + dy);",
+                              "for (int dx = -1; dx <= 1; ++dx) if (dx || dy) any |= in.clamped(x + dx, y + dy);"),
+    "grow2_from_candidates": ("Map<uint8_t> g2 = dilate3(g1);", "Map<uint8_t> g2 = dilate3(cand);"),
+    "article_form_factor": ("r.v[i] = (p.objlim_form == 1) ? (T(2) * s.v[i]) / fn : sp.v[i] / fn;",
+                            "r.v[i] = (p.objlim_form == 1) ? s.v[i] / fn : sp.v[i] / fn;"),
+    "sprime_median_of_lplus": ("Map<T> s_med = median_filter(s, 2);", "Map<T> s_med = median_filter(lp, 2);"),
+    "noise_from_pixel": ("std::sqrt(gain * m5.v[i] + rn2) / gain;", "std::sqrt(gain * J.v[i] + rn2) / gain;"),
+    "replace_reads_output": ("if (!Mk.clamped(x + dx, y + dy)) vals.push_back(J.clamped(x + dx, y + dy));",
+                             "if (!Mk.clamped(x + dx, y + dy)) vals.push_back(out.clamped(x + dx, y + dy));"),
     "clean_forgets_flags": ("iterate<T>(J.data(), M.data(), w, h, *p, o, false, fragile_any != nullptr);",
                             "iterate<T>(J.data(), nullptr, w, h, *p, o, false, fragile_any != nullptr);"),
     # the fragile map: its tolerance, its cone, and each of its three threshold conditions
