@@ -286,15 +286,17 @@ constexpr unsigned kStatusTimeout = 1u;
 // e) on R6 from I_{k-2} and M_{k-1} over R8, writes the tile's I_{k-1}, and
 // then detects on the result.
 //
-// A persistent CTA walks its tiles; the image region (and, fused, the flag
-// words) of the next tile is prefetched with cp.async into the second of two
-// buffers while the current tile is processed.
+// A persistent CTA walks its tiles; in detect_kernel the image region (and,
+// fused, the flag words) of the next tile is loaded into the second of two
+// buffers while the current tile is processed; detect1_kernel keeps one buffer
+// and loads the next region after the tile.
 //
 // Shared memory, regions centred on the tile ("Rk" = tile grown by k px):
-//   two image buffers (R6 of J, or fused R8 of I_{k-2}); sCM (R2 rows x R4
-//   columns) column medians, aliased by sS (R4) S; sM3 (R5) med3; sN, sSp
-//   (R2) N and S' (-inf unless computed); fused: two flag buffers (R8 rows);
-//   9 bit maps; three position lists and small counters.
+//   two image buffers, one in detect1_kernel (R8 of J, or fused of I_{k-2});
+//   sCM (R2 rows x R4 columns) column medians, aliased by sS (R4) S; sM3 (R5)
+//   med3; sN, sSp (R2) N and S' (-inf unless computed); fused: a flag buffer
+//   (R8 rows) per image buffer; 9 bit maps; three position lists and small
+//   counters.
 template <int TW, int TH, bool kFused = false, bool kDouble = true>
 struct DetectLayout {
   static constexpr int JW = TW + 12, JH = TH + 12;  // R6
