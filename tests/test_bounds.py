@@ -73,3 +73,24 @@ def test_screen_never_rejects_a_pixel_above_the_threshold():
         if S > th and not hot:
             rejected_above += 1
     assert rejected_above == 0
+
+
+def test_objlim_statistic_is_monotone_in_med7():
+    """R = S' / max((m3 - med7) / N, 0.01) in float32 (the oracle's order) does not decrease as med7
+    grows, for S' > 0 and N > 0: every step is a monotone IEEE operation. So the values of R at the
+    smallest and the largest column median of the 7x7 window bracket R at the true med7."""
+    rng = np.random.default_rng(3)
+    n = 200_000
+    m3 = rng.uniform(-100, 5000, n).astype(F)
+    N = rng.uniform(0.5, 40, n).astype(F)
+    sp = rng.uniform(1e-3, 500, n).astype(F)
+    a = (m3 + rng.normal(0, 30, n)).astype(F)
+    b = (a + np.abs(rng.normal(0, 30, n)) * (rng.random(n) < 0.9)).astype(F)  # b >= a, some equal
+
+    def R(med7):
+        f = (m3 - med7).astype(F)
+        fn = np.maximum((f / N).astype(F), F(0.01))
+        return (sp / fn).astype(F)
+
+    assert np.all(b >= a)
+    assert np.all(R(a) <= R(b))
