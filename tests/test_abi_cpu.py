@@ -52,10 +52,16 @@ def test_null_context_and_strerror():
     assert lib.crb_strerror(L.CRB_EALIAS) == b"output overlaps input"
     assert lib.crb_strerror(99) == b"unknown status"
     tw, th = ctypes.c_int(), ctypes.c_int()
+    shapes = []
     for i in range(lib.crb_num_tile_shapes()):
         assert lib.crb_tile_shape(i, ctypes.byref(tw), ctypes.byref(th)) == 0
         assert tw.value % 32 == 0 and th.value > 0
+        shapes.append((tw.value, th.value))
+    # index 0 is the default 64 x 32; index 5 the single-buffered 64 x 28 that tile_shape 0 takes when
+    # its tiles fit one round of resident blocks and those of 64 x 32 do not
+    assert shapes[0] == (64, 32) and shapes[5] == (64, 28)
     assert lib.crb_tile_shape(-1, None, None) == L.CRB_EINVAL
+    assert lib.crb_tile_shape(len(shapes), None, None) == L.CRB_EINVAL
 
 
 def test_networks_exhaustive_zero_one():
