@@ -150,3 +150,23 @@ def test_workload_recipes():
     assert abs(gaps.mean() * 500.0 - 1) < 0.06 and abs(gaps.std() / gaps.mean() - 1) < 0.08  # exponential
     counts = [sum((r["w"], r["h"]) == s for r in rec) for s in wl.BATCH_SIZES]
     assert min(counts) > 900 and max(counts) < 1100  # sizes uniform over the four
+
+
+def test_frames_do_not_depend_on_the_thread_count():
+    """Each row of the noise pass draws from its own stream, so a frame is the same bytes whatever the
+    number of OpenMP threads (the GPU tests and the oracle's may run on hosts with different cores)."""
+    import hashlib
+    import os
+    import subprocess
+    import sys
+    code = ("import hashlib, synth; "
+            "print(hashlib.sha256(synth.frame(517, 333, seed=9, index=4).tobytes()).hexdigest())")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    digests = set()
+    for threads in ("1", "3", "8"):
+        env = dict(os.environ, OMP_NUM_THREADS=threads)
+        out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
+                             check=True)
+        digests.add(out.stdout.strip())
+    digests.add(hashlib.sha256(synth.frame(517, 333, seed=9, index=4).tobytes()).hexdigest())
+    assert len(digests) == 1
